@@ -1,0 +1,196 @@
+"""Joint log-likelihood of one parameter sample (oracle, FP64).
+
+Eq. chi_general / Eq. Posterior_LD: the joint chi^2 of the terms built here is
+chi^2 = chi^2_pix (Eq. chi2 of lens_light over the whole extended image) +
+chi^2_dyn (Eq. chi2_dyn) + chi^2_tmd (Eq. chi2_tmd), and logL = -chi^2/2 (the
+Gaussian normalisation constant is dropped, as chi^2_LD has none).
+
+Dynamics chain (Sect. 3.2 and App. A): 1-D MGE of the App. C convergence and of
+each lens-light Sersic -> a black-hole Gaussian (sigma_BH, M_BH = f_BH * M_*,
+M_* = Upsilon * L_tot, L_tot the total light of the tracer MGE in
+convergence units via L_scale) -> deprojection -> pair-form JAM on the
+sub-sampled sky grid -> PSF_kin, binning, v_rms.
+
+An invalid sample (parameter outside its domain, impossible deprojection
+cos^2 i >= q'^2 (App. A), or a non-positive deprojected density at the probe
+radii, Sect. 3.3) returns logL = -inf and a non-zero status.
+"""
+import math
+
+import numpy as np
+
+from paper_2504_01302_b300 import synth
+from . import cosmo, imaging, jam, kin, lens, mge, tdelay
+
+IDX = synth.IDX
+
+ST_OK, ST_DOMAIN, ST_DEPROJ, ST_NEGDENS, ST_NONFINITE = 0, 1, 2, 3, 4
+
+
+def check_domain(th):
+    g = th[IDX["gamma"]]
+    q = th[IDX["q"]]
+    inc = th[IDX["inc"]]
+    ok = (np.all(np.isfinite(th)) and th[IDX["theta_E"]] > 0 and 1.0 < g < 3.0 and 0.0 < q <= 1.0
+          and th[IDX["R_e_src"]] > 0 and th[IDX["n_src"]] > 0 and th[IDX["R_e_ll"]] > 0
+          and th[IDX["I_e_ll"]] > 0
+          and 0.0 < inc <= math.pi / 2 + 1e-12 and th[IDX["beta"]] < 1.0
+          and th[IDX["upsilon"]] >= 0 and th[IDX["f_bh"]] >= 0 and th[IDX["H0"]] > 0)
+    return bool(ok)
+
+
+def light_mge(th, sysd):
+    """Tracer MGE: one 1-D MGE per lens-light Sersic, all sharing centre and PA."""
+    P = sysd["mge_P"]
+    comps = [(th[IDX["I_e_ll"]], th[IDX["R_e_ll"]], sysd["ll_n"], sysd["ll_q"])]
+    comps += [tuple(r) for r in np.asarray(sysd["ll2"]).reshape(-1, 4)]
+    I0, sig, qp = [], [], []
+    for (I_e, R_e, n, q), N in zip(comps, sysd["n_mge_light"]):
+        s, A = mge.mge_1d(mge.sersic_profile(I_e, R_e, n), sysd["light_rmin"],
+                          sysd["light_rmax"], N, P)
+        I0.append(A)
+        sig.append(s)
+        qp.append(np.full(N, q))
+    return dict(I0=np.concatenate(I0), sig=np.concatenate(sig), qp=np.concatenate(qp))
+
+
+def mass_mge(th, sysd, L_tot):
+    s, A = mge.mge_1d(mge.epl_profile(th[IDX["theta_E"]], th[IDX["gamma"]], th[IDX["q"]],
+                                      sysd["r_soft"]),
+                      sysd["mass_rmin"], sysd["mass_rmax"], sysd["n_mge_mass"], sysd["mge_P"])
+    qp = np.full(len(s), th[IDX["q"]])
+    if sysd["has_bh"]:
+        m_star = th[IDX["upsilon"]] * L_tot * sysd["L_scale"]
+        m_bh = th[IDX["f_bh"]] * m_star
+        sb = sysd["bh_sigma"]
+        A = np.append(A, m_bh / (2 * math.pi * sb * sb))
+        s = np.append(s, sb)
+        qp = np.append(qp, 1.0)
+    return dict(kap0=A, sig=s, qp=qp)
+
+
+def positive_density(tr, ms, inc):
+    """Deprojected mass and tracer densities are positive on probe points
+    (R = sigma_n in the equatorial plane and z = q sigma_n on the axis)."""
+    for G, key in ((ms, "kap0"), (tr, "I0")):
+        rho0, q = jam.deproject(G[key], G["sig"], G["qp"], inc)
+        for s in G["sig"]:
+            if np.sum(rho0 * np.exp(-s * s / (2 * G["sig"] ** 2))) <= 0:
+                return False
+            if np.sum(rho0 * np.exp(-s * s / (2 * G["sig"] ** 2 * q * q))) <= 0:
+                return False
+    return True
+
+
+def sky_geometry(sysd):
+    X, Y = kin.sky_subsamples(sysd["kx"], sysd["ky"], sysd["kss"], sysd["kpix"])
+    return X, Y, float(np.max(np.hypot(X, Y)))
+
+
+def dynamics(th, sysd, want_maps=False):
+    """v_rms per bin (and intermediate maps).  Returns (v_pre, status, extra)."""
+    inc = th[IDX["inc"]]
+    tr = light_mge(th, sysd)
+    L_tot = float(np.sum(2 * math.pi * tr["I0"] * tr["sig"] ** 2 * tr["qp"]))
+    ms = mass_mge(th, sysd, L_tot)
+    qmin = min(np.min(tr["qp"]), np.min(ms["qp"]))
+    if math.cos(inc) ** 2 >= qmin ** 2:
+        return None, ST_DEPROJ, {}
+    if not positive_density(tr, ms, inc):
+        return None, ST_NEGDENS, {}
+    v2u = cosmo.v2_unit(sysd["z_d"], sysd["z_s"], sysd["omega_m"], sysd["kappa_ext"])
+    X, Y, r_max = sky_geometry(sysd)
+    xp, yp = lens.frame(X, Y, th[IDX["x_c"]], th[IDX["y_c"]], th[IDX["phi"]])
+    tab = jam.table(tr, ms, inc, th[IDX["beta"]], v2u, r_max, sysd["n_gl"])
+    sv2 = jam.sigma_v2_fast(xp, yp, tab).reshape(X.shape)
+    sb = jam.surface_brightness(xp, yp, tr)
+    num, den = kin.bin_moments(sv2, sb, sysd)
+    v = np.sqrt(num / den)
+    extra = dict(tr=tr, ms=ms, v2u=v2u, r_max=r_max, num=num, den=den)
+    if want_maps:
+        extra.update(sv2=sv2, sb=sb, xp=xp, yp=yp, tab=tab)
+    return v, ST_OK, extra
+
+
+def evaluate(th, sysd, want=False):
+    """Full evaluation: dict with logL, the three chi^2 terms, image, v_rms, delays, status."""
+    th = np.asarray(th, np.float64)
+    out = dict(logL=-np.inf, chi2_pix=np.nan, chi2_dyn=np.nan, chi2_tmd=np.nan, status=ST_OK)
+    if not check_domain(th):
+        out["status"] = ST_DOMAIN
+        return out
+    v, st, extra = dynamics(th, sysd, want_maps=want)
+    if st != ST_OK:
+        out["status"] = st
+        return out
+    img = imaging.model_image(th, sysd)
+    dt = tdelay.delays(th, sysd)
+    c_pix = imaging.chi2_pix(img, sysd)
+    c_dyn = kin.chi2_dyn(v, sysd)
+    c_tmd = tdelay.chi2_tmd(dt, sysd)
+    logL = -0.5 * (c_pix + c_dyn + c_tmd)
+    if not np.isfinite(logL):
+        out["status"] = ST_NONFINITE
+        return out
+    out.update(logL=logL, chi2_pix=c_pix, chi2_dyn=c_dyn, chi2_tmd=c_tmd, image=img, vrms=v,
+               delays=dt, extra=extra)
+    return out
+
+
+def loglike(th, sysd):
+    return evaluate(th, sysd)["logL"]
+
+
+def grad_fd(th, sysd, h_rel=1e-6, which=None):
+    """Central finite differences of logL with h = h_rel * parameter scale (FP64)."""
+    th = np.asarray(th, np.float64)
+    g = np.zeros(len(th))
+    idx = range(len(th)) if which is None else which
+    for i in idx:
+        h = h_rel * synth.THETA_SCALE[i]
+        tp, tm = th.copy(), th.copy()
+        tp[i] += h
+        tm[i] -= h
+        g[i] = (loglike(tp, sysd) - loglike(tm, sysd)) / (2 * h)
+    return g
+
+
+# ---------------------------------------------------------------------------
+# mock systems: data = oracle model at the truth + seeded noise
+# ---------------------------------------------------------------------------
+
+def build_system(base, theta_true, noise):
+    """Fill data, kinematics and delays of a fixed system from the oracle model."""
+    s = dict(base)
+    s["data"] = np.zeros((s["ny"], s["nx"]), np.float32)
+    s["v_obs"] = np.ones(s["n_bins"], np.float32)
+    s["v_sig"] = np.ones(s["n_bins"], np.float32)
+    # quasar images: Newton solution of the lens equation for the quasar source point
+    guesses = synth.ring_images(theta_true[IDX["theta_E"]], s["qso_beta"])
+    img = lens.solve_images(s["qso_beta"], theta_true, s["sis"], guesses)
+    s["img_xy"] = img
+    s["dt_obs"] = np.zeros(len(img) - 1)
+    s["dt_sig"] = np.ones(len(img) - 1)
+    ev = evaluate(theta_true, s)
+    assert ev["status"] == ST_OK, ev["status"]
+    m = ev["image"]
+    s["data"] = (m + np.asarray(s["sigma"], np.float64) * noise["img"]).astype(np.float32)
+    v = ev["vrms"]
+    s["v_sig"] = (0.02 * v).astype(np.float32)
+    s["v_obs"] = (v + 0.02 * v * noise["kin"]).astype(np.float32)
+    dt = ev["delays"]
+    sig = 0.016 * np.abs(dt) + 0.1
+    s["dt_sig"] = sig
+    s["dt_obs"] = dt + sig * noise["dt"][:len(dt)]
+    return s
+
+
+def workload(w, small=False):
+    """Mock systems, parameter samples and system ids of workload w."""
+    bases, B = synth.workload_systems(w)
+    systems = []
+    for si, b in enumerate(bases):
+        truth = synth.theta_truth(0 if w == 0 else 1)
+        systems.append(build_system(b, truth, synth.noise_draws(b, 1000 * w + si + 500)))
+    th, sid = synth.workload_thetas(w, B, len(systems))
+    return systems, th, sid

@@ -1,0 +1,365 @@
+"""Pins of the FP64 oracle against printed values, closed forms, invariants and
+brute force (no GPU).  Each test names what fixes the expected value."""
+import math
+import os
+
+import mpmath
+import numpy as np
+import pytest
+from scipy.integrate import quad
+from scipy.special import erf, gammaincinv
+
+from oracle import cosmo, imaging, jam, kin, lens, light, mge, model, tdelay
+from paper_2504_01302_b300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    out = {}
+    for line in open(os.path.join(GOLD, name)):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, v, tol = line.split()
+        out[k] = (float(v), float(tol))
+    return out
+
+
+# ---------------------------------------------------------------- cosmology
+
+def test_distances_table2():
+    g = _golden("table2_distances.txt")
+    D_d, _, _, D_dt = cosmo.distances(g["z_d"][0], g["z_s"][0], g["H0"][0], g["omega_m"][0])
+    assert abs(D_d - g["D_d"][0]) <= g["D_d"][1]
+    assert abs(D_dt - g["D_dt"][0]) <= g["D_dt"][1]
+    # Table 2: D_dt,int = 1823 = (1 - kappa_ext) D_dt with kappa_ext = 0.079
+    assert abs(1823.0 / D_dt - g["D_dt_int_over_D_dt_kappa_ext_0.079"][0]) < 1e-3
+
+
+def test_time_delay_distance_inverse_H0():
+    a = cosmo.distances(0.295, 0.654, 60.0, 0.27)[3]
+    b = cosmo.distances(0.295, 0.654, 90.0, 0.27)[3]
+    assert abs(a * 60.0 - b * 90.0) < 1e-9 * a * 60
+
+
+# ---------------------------------------------------------------- EPL
+
+@pytest.mark.parametrize("tE,g,q,x,y", [(1.3, 2.1, 0.7, 0.7, -0.4), (1.65, 1.8, 0.85, -1.2, 0.9),
+                                         (0.9, 2.3, 0.55, 0.05, 1.4)])
+def test_epl_series_matches_hyp2f1(tE, g, q, x, y):
+    t = g - 1
+    ax, ay = lens.epl_alpha_frame(np.array([x]), np.array([y]), tE, g, q)
+    b = q * lens.epl_b(tE, g, q)
+    R = math.hypot(q * x, y)
+    w = complex(q * x, y) / R
+    f = (1 - q) / (1 + q)
+    F = complex(mpmath.hyp2f1(1, t / 2, 2 - t / 2, -f * w * w))
+    a = 2 * b / (1 + q) * (b / R) ** (t - 1) * w * F
+    assert abs(complex(ax[0], ay[0]) - a) < 1e-13 * abs(a)
+
+
+def test_epl_reduces_to_sie_closed_form():
+    # g = 2: 2F1(1, 1/2; 3/2; -z^2) = arctan(z)/z, z^2 = f e^{2 i phi}
+    q, tE = 0.7, 1.4
+    x, y = 0.8, -0.5
+    ax, ay = lens.epl_alpha_frame(np.array([x]), np.array([y]), tE, 2.0, q)
+    b = q * lens.epl_b(tE, 2.0, q)
+    R = math.hypot(q * x, y)
+    w = complex(q * x, y) / R
+    f = (1 - q) / (1 + q)
+    z = np.sqrt(f * w * w)
+    a = 2 * b / (1 + q) * w * np.arctan(z) / z
+    assert abs(complex(ax[0], ay[0]) - a) < 1e-13 * abs(a)
+
+
+def test_epl_circular_power_law():
+    # q = 1: |alpha| = b (b/R)^(t-1), radial
+    tE, g = 1.2, 2.25
+    x, y = np.array([0.3, -1.1]), np.array([0.9, 0.2])
+    ax, ay = lens.epl_alpha_frame(x, y, tE, g, 1.0)
+    R = np.hypot(x, y)
+    mag = tE * (tE / R) ** (g - 2)
+    assert np.allclose(np.hypot(ax, ay), mag, rtol=1e-14)
+    assert np.allclose(ax * y - ay * x, 0, atol=1e-14)
+
+
+@pytest.mark.parametrize("g,q", [(2.0, 0.8), (1.8, 0.6), (2.2, 0.9)])
+def test_epl_divergence_and_curl(g, q):
+    tE, h = 1.5, 1e-5
+    for x, y in [(0.7, -0.4), (-1.3, 0.2), (0.2, 1.7)]:
+        A = lambda a, b: lens.epl_alpha_frame(np.array([a]), np.array([b]), tE, g, q)
+        div = (A(x + h, y)[0] - A(x - h, y)[0] + A(x, y + h)[1] - A(x, y - h)[1]) / (2 * h)
+        curl = (A(x + h, y)[1] - A(x - h, y)[1] - A(x, y + h)[0] + A(x, y - h)[0]) / (2 * h)
+        k = lens.epl_kappa_frame(x, y, tE, g, q)
+        assert abs(div[0] - 2 * k) < 1e-7 * k
+        assert abs(curl[0]) < 1e-7 * k
+
+
+@pytest.mark.parametrize("g,q", [(2.0, 0.8), (1.85, 0.65)])
+def test_epl_mean_convergence_one_inside_b(g, q):
+    # Gauss: flux of alpha through the ellipse R = b equals 2 * (pi q b^2) * mean kappa,
+    # and App. C gives mean kappa inside R=b equal to 1.
+    tE = 1.65
+    b = lens.epl_b(tE, g, q)
+    n = 4000
+    s = (np.arange(n) + 0.5) / n * 2 * math.pi
+    x, y = b * np.cos(s), q * b * np.sin(s)
+    ax, ay = lens.epl_alpha_frame(x, y, tE, g, q)
+    # outward normal * dl = (dy/ds, -dx/ds) ds
+    flux = np.sum(ax * q * b * np.cos(s) + ay * b * np.sin(s)) * (2 * math.pi / n)
+    mean_kappa = flux / (2 * math.pi * q * b * b)
+    assert abs(mean_kappa - 1.0) < 1e-10
+
+
+def test_psi_gradient_is_alpha_and_jacobian():
+    th = synth.theta_truth(1).copy()
+    th[1], th[2] = 2.15, 0.72
+    sis = np.array([[0.2, -0.3, 0.6]])
+    h = 1e-5
+    for x, y in [(1.2, 0.7), (-0.9, -1.3)]:
+        P = lambda a, b: lens.psi_total(np.array([a]), np.array([b]), th, sis)[0]
+        gx = (P(x + h, y) - P(x - h, y)) / (2 * h)
+        gy = (P(x, y + h) - P(x, y - h)) / (2 * h)
+        ax, ay = lens.alpha_total(np.array([x]), np.array([y]), th, sis)
+        assert abs(gx - ax[0]) < 1e-8 and abs(gy - ay[0]) < 1e-8
+        A = lambda a, b: np.array(lens.alpha_total(np.array([a]), np.array([b]), th, sis))[:, 0]
+        J = lens.jac_total(np.array([x]), np.array([y]), th, sis)
+        dx = (A(x + h, y) - A(x - h, y)) / (2 * h)
+        dy = (A(x, y + h) - A(x, y - h)) / (2 * h)
+        assert np.allclose([J[0][0], J[1][0], J[2][0], J[3][0]], [dx[0], dy[0], dx[1], dy[1]],
+                           atol=1e-8)
+
+
+def test_shear_has_no_convergence_and_sis_is_isothermal():
+    h = 1e-5
+    A = lambda a, b: lens.shear_alpha(a, b, 0.09, 1.42)
+    div = (A(0.3 + h, 0.2)[0] - A(0.3 - h, 0.2)[0] + A(0.3, 0.2 + h)[1] - A(0.3, 0.2 - h)[1]) / (2 * h)
+    assert abs(div) < 1e-10
+    ax, ay = lens.sis_alpha(np.array([1.0, -0.2]), np.array([0.4, 0.9]), 0.2, -0.3, 0.6)
+    assert np.allclose(np.hypot(ax, ay), 0.2, rtol=1e-15)
+
+
+def test_lens_equation_round_trip():
+    th = synth.theta_truth(1)
+    sis = np.array([[0.2, -0.3, 0.6]])
+    beta = np.array([0.03, -0.02])
+    img = lens.solve_images(beta, th, sis, synth.ring_images(th[0], beta))
+    assert len(np.unique(np.round(img, 6), axis=0)) == 4
+    ax, ay = lens.alpha_total(img[:, 0], img[:, 1], th, sis)
+    assert np.max(np.abs(img[:, 0] - ax - beta[0])) < 1e-10
+    assert np.max(np.abs(img[:, 1] - ay - beta[1])) < 1e-10
+
+
+# ---------------------------------------------------------------- Sersic
+
+@pytest.mark.parametrize("n", [0.5, 1.0, 1.5, 4.0, 6.0])
+def test_sersic_bn_against_exact_root(n):
+    # the 4th-order asymptotic series of Ciotti & Bertin (1999) errs by ~2.5e-5 n^-4
+    exact = gammaincinv(2 * n, 0.5)
+    assert abs(light.sersic_bn(n) / exact - 1) < 4e-5 * n ** -4
+
+
+# ---------------------------------------------------------------- MGE
+
+@pytest.mark.parametrize("a", [0.3, 0.7, 2.0])
+def test_euler_inversion_closed_form(a):
+    # F(R) = 1/(1 + R^2/(2a^2)) is the Laplace transform (in R^2) of g(s) = 2a^2 exp(-2a^2 s).
+    F = lambda z: 1.0 / (1.0 + z * z / (2 * a * a))
+    for s in [0.05, 0.3, 1.0, 4.0]:
+        sig = 1 / math.sqrt(2 * s)
+        g = mge.f_sigma(F, np.array([sig]), 10)[0] / (2 * s * math.sqrt(2 * math.pi))
+        ref = 2 * a * a * math.exp(-2 * a * a * s)
+        assert abs(g - ref) < 3e-6 * 2 * a * a
+
+
+def test_mge_reconstructs_sersic_and_power_law():
+    # Sect. 3.2: 21 Gaussians recover the profile within ~0.5 %.
+    F = mge.sersic_profile(1.0, 1.0, 4.0)
+    sig, A = mge.mge_1d(F, 0.005, 20.0, 21, 10)
+    R = np.logspace(math.log10(0.05), math.log10(2.0), 40)
+    assert np.max(np.abs(mge.mge_eval(R, sig, A) / light.sersic_R(R, 1, 1, 4) - 1)) < 5e-3
+    # isothermal (t = 1) convergence: the discrete mixture stops at sigma_max, which
+    # drops the tail int_{sigma_max}^inf, a fraction erf(R/(sqrt(2) sigma_max)) of F(R).
+    F = mge.epl_profile(1.65, 2.0, 0.8, 0.0)
+    sig, A = mge.mge_1d(F, 0.01, 100.0, 21, 10)
+    R = np.logspace(-1, math.log10(20.0), 40)
+    pred = 1.0 - erf(R / (math.sqrt(2) * 100.0))
+    assert np.max(np.abs(mge.mge_eval(R, sig, A) / F(R).real - pred)) < 5e-3
+
+
+def test_mge_power_law_density_is_power_law():
+    # F = R^-t is scale free, so f(sigma) is proportional to sigma^-t.
+    t = 0.9
+    F = lambda z: z ** (-t)
+    s = np.array([0.1, 1.0, 10.0])
+    f = mge.f_sigma(F, s, 10)
+    assert np.allclose(f * s ** t, f[0] * s[0] ** t, rtol=1e-6)
+
+
+# ---------------------------------------------------------------- deprojection & JAM
+
+def test_deprojection_projects_back():
+    inc = math.radians(65)
+    I0, sig, qp = np.array([2.0]), np.array([0.7]), np.array([0.75])
+    rho0, q = jam.deproject(I0, sig, qp, inc)
+    for xp, yp in [(0.3, 0.4), (1.0, -0.2)]:
+        def f(zp):
+            x, y, z = xp, yp * math.cos(inc) - zp * math.sin(inc), yp * math.sin(inc) + zp * math.cos(inc)
+            return rho0[0] * math.exp(-(x * x + y * y + z * z / q[0] ** 2) / (2 * sig[0] ** 2))
+        val = quad(f, -20, 20, epsabs=0, epsrel=1e-13)[0]
+        ref = I0[0] * math.exp(-(xp ** 2 + yp ** 2 / qp[0] ** 2) / (2 * sig[0] ** 2))
+        assert abs(val / ref - 1) < 1e-10
+
+
+TR = dict(I0=np.array([1.0, 0.5, 0.2]), sig=np.array([0.1, 0.5, 2.0]), qp=np.ones(3))
+MS = dict(kap0=np.array([50., 3.0, 0.5, 0.05]), sig=np.array([0.01, 0.2, 1.0, 10.]), qp=np.ones(4))
+
+
+@pytest.mark.parametrize("n_gl,tol", [(32, 1e-8), (64, 1e-12)])
+def test_jam_spherical_isotropic_limit(n_gl, tol):
+    tab = jam.table(TR, MS, math.radians(70), 0.0, 1.0, 1.5, n_gl)
+    R = np.array([0.02, 0.1, 0.4, 1.0, 1.4])
+    fast = jam.sigma_v2_fast(R * 0.6, R * 0.8, tab)
+    ref = np.array([jam.sigma_v2_spherical_1d(r, TR, MS, 1.0) for r in R])
+    assert np.max(np.abs(fast / ref - 1)) < tol
+
+
+TRF = dict(I0=np.array([1.0, 0.3]), sig=np.array([0.3, 1.2]), qp=np.array([0.8, 0.7]))
+MSF = dict(kap0=np.array([5., 0.8, 20.]), sig=np.array([0.2, 1.5, 0.01]), qp=np.array([0.75, 0.85, 1.0]))
+
+
+@pytest.mark.slow
+def test_jam_pair_form_equals_jeans_definition():
+    inc, beta = math.radians(65), 0.2
+    tab = jam.table(TRF, MSF, inc, beta, 1.0, 1.5, 64)
+    pj = jam.PlainJeans(TRF, MSF, inc, beta, 1.0)
+    for x, y in [(0.3, 0.2), (0.7, -0.1)]:
+        f = jam.sigma_v2_fast(np.array([x]), np.array([y]), tab)[0]
+        assert abs(f / pj.sigma_v2(x, y) - 1) < 1e-8
+
+
+def test_jam_invariants():
+    inc, beta = math.radians(65), 0.2
+    tab = jam.table(TRF, MSF, inc, beta, 1.0, 1.5, 32)
+    x, y = np.array([0.3, 0.05, 0.6]), np.array([0.2, 0.4, -0.3])
+    v2 = jam.sigma_v2_fast(x, y, tab) / jam.surface_brightness(x, y, TRF)
+    # 4-fold symmetry
+    for sx, sy in [(-1, 1), (1, -1), (-1, -1)]:
+        v2s = jam.sigma_v2_fast(sx * x, sy * y, tab) / jam.surface_brightness(sx * x, sy * y, TRF)
+        assert np.allclose(v2s, v2, rtol=1e-14)
+    # v^2 proportional to the mass scale; independent of the tracer amplitude
+    m2 = dict(MSF, kap0=MSF["kap0"] * 3.7)
+    t2 = dict(TRF, I0=TRF["I0"] * 0.21)
+    tab2 = jam.table(t2, m2, inc, beta, 1.0, 1.5, 32)
+    v2b = jam.sigma_v2_fast(x, y, tab2) / jam.surface_brightness(x, y, t2)
+    assert np.allclose(v2b, 3.7 * v2, rtol=1e-13)
+
+
+def test_jam_gl32_discretisation_error():
+    # the fixed 32-node rule against an adaptive u integral (cf. the 1e-5 of Sect. 3.2)
+    inc, beta = math.radians(84), 0.15
+    tab = jam.table(TRF, MSF, inc, beta, 1.0, 1.42, 32)
+    for x, y in [(0.02, 0.01), (0.4, 0.3), (0.9, -0.8)]:
+        f = jam.sigma_v2_fast(np.array([x]), np.array([y]), tab)[0]
+        c = jam.sigma_v2_converged(x, y, TRF, MSF, inc, beta, 1.0)
+        assert abs(f / c - 1) < 1e-6
+
+
+# ---------------------------------------------------------------- convolution, bins
+
+def test_convolution_delta_flux_and_brute_force():
+    rng = np.random.default_rng(3)
+    img = rng.random((9, 11))
+    d = np.zeros((5, 5))
+    d[2, 2] = 1
+    assert np.array_equal(imaging.convolve_same(img, d), img)
+    P = rng.random((5, 5))
+    P /= P.sum()
+    comp = np.zeros((15, 15))
+    comp[5:10, 5:10] = rng.random((5, 5))
+    assert abs(imaging.convolve_same(comp, P).sum() - comp.sum()) < 1e-12
+    out = imaging.convolve_same(img, P)
+    ref = np.zeros_like(img)
+    for i in range(9):
+        for j in range(11):
+            for a in range(5):
+                for b in range(5):
+                    ii, jj = i - (a - 2), j - (b - 2)
+                    if 0 <= ii < 9 and 0 <= jj < 11:
+                        ref[i, j] += P[a, b] * img[ii, jj]
+    assert np.allclose(out, ref, rtol=1e-14, atol=1e-15)
+
+
+def test_bin_moments_brute_force():
+    rng = np.random.default_rng(5)
+    sysd = dict(kpsf=synth.truncated_gaussian_psf(2.5), kss=2, n_bins=3,
+                bins=np.array([[-1, -1, -1, -1], [-1, 0, 1, -1], [-1, 2, 2, -1], [-1, -1, -1, -1]]))
+    a, b = rng.random((8, 8)), rng.random((8, 8))
+    num, den = kin.bin_moments(a, b, sysd)
+    k = sysd["kpsf"].astype(np.float64)
+    ca = imaging.convolve_same(a, k)
+    lab = kin.subsample_bins(sysd["bins"], 2)
+    for l in range(3):
+        tot = sum(ca[i, j] for i in range(8) for j in range(8) if lab[i, j] == l)
+        assert abs(num[l] - tot) < 1e-12
+
+
+# ---------------------------------------------------------------- delays, likelihood
+
+@pytest.fixture(scope="module")
+def w0():
+    systems, th, sid = model.workload(0)
+    return systems[0], th[0]
+
+
+def test_delays_inverse_H0_and_exact_images(w0):
+    s, th = w0
+    d1 = tdelay.delays(th, s)
+    t2 = th.copy()
+    t2[synth.IDX["H0"]] *= 1.5
+    assert np.allclose(tdelay.delays(t2, s) * 1.5, d1, rtol=1e-12)
+    # images are exact solutions for qso_beta: beta_hat is the true source and grad phi = 0
+    bh = tdelay.beta_hat(th, s["sis"], s["img_xy"])
+    assert np.max(np.abs(bh - s["qso_beta"])) < 1e-10
+    h = 1e-6
+    for x, y in s["img_xy"]:
+        F = lambda a, b: tdelay.fermat(th, s["sis"], np.array([[a, b]]), bh)[0]
+        assert abs((F(x + h, y) - F(x - h, y)) / (2 * h)) < 1e-8
+        assert abs((F(x, y + h) - F(x, y - h)) / (2 * h)) < 1e-8
+
+
+def test_chi2_at_truth_matches_noise(w0):
+    s, th = w0
+    ev = model.evaluate(th, s)
+    n = int(np.sum(s["mask"]))
+    assert abs(ev["chi2_pix"] - n) < 5 * math.sqrt(2 * n)
+    nb = s["n_bins"]
+    assert abs(ev["chi2_dyn"] - nb) < 5 * math.sqrt(2 * nb)
+
+
+def test_dynamics_independent_of_H0_and_sqrt_mass(w0):
+    s, th = w0
+    v1 = model.evaluate(th, s)["vrms"]
+    t2 = th.copy()
+    t2[synth.IDX["H0"]] = 55.0
+    assert np.allclose(model.evaluate(t2, s)["vrms"], v1, rtol=1e-13)
+
+
+def test_fd_gradient_H0_matches_closed_form(w0):
+    s, th = w0
+    th = th.copy()
+    th[synth.IDX["H0"]] = 70.0
+    g = model.grad_fd(th, s, which=[synth.IDX["H0"]])[synth.IDX["H0"]]
+    dt = tdelay.delays(th, s)
+    ref = -0.5 * np.sum(2 * (dt - s["dt_obs"]) / s["dt_sig"] ** 2 * (-dt / th[synth.IDX["H0"]]))
+    assert abs(g - ref) < 1e-6 * abs(ref)
+
+
+def test_invalid_samples(w0):
+    s, th = w0
+    for name, val, st in [("q", 1.2, model.ST_DOMAIN), ("gamma", 3.5, model.ST_DOMAIN),
+                          ("inc", math.radians(20), model.ST_DEPROJ), ("beta", 1.5, model.ST_DOMAIN)]:
+        t = th.copy()
+        t[synth.IDX[name]] = val
+        ev = model.evaluate(t, s)
+        assert ev["status"] == st and ev["logL"] == -np.inf
