@@ -1,0 +1,370 @@
+"""Throughput of the batched joint lensing + dynamics log-likelihood on B300.
+
+Default workload: the RXJ1131-scale system (200x200 image at 2x supersampling, EPL +
+shear + SIS, two lens-light Sersics + Sersic source, 21x21 PSF; JAM with 20 mass +
+2x10 light Gaussians + BH, 60x60 sky at 4x sub-sampling, GL32, 50 bins, 4 images),
+a batch of 256 samples from the priors.  One step = one glad_loglike call over the
+batch (every kernel of the path).  With --grad the step is glad_loglike_grad over
+a batch of 64 samples.
+
+Data: seeded synthetic inputs; the image and the binned v_rms are the library's own
+model at the truth plus seeded noise, the quasar images sit on the Einstein ring.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 oracle instead, on
+the host cores, over a bounded sample of the same workload.
+"""
+import argparse
+import ctypes as C
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2504_01302_b300 import synth  # noqa: E402
+
+METRIC = "joint logL evals/sec and logL+grad evals/sec at 1 B300, at stated FP64-oracle accuracy"
+N_SM = 148
+# ex2.approx results per clock per SM on B300 (MUFU), measured by a throughput probe
+# (profiles/mufu_ffma_rates_b300.md): 32.3-32.8 ex2/clk/SM.
+MUFU_EX2_PER_CLK_SM = 32
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="glad", choices=["glad", "reference"])
+    p.add_argument("--workload", type=int, default=1)
+    p.add_argument("--grad", action="store_true", help="time logL + gradient (batch 64)")
+    p.add_argument("--batch", type=int, default=0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def workload_name(w, grad, B):
+    names = {0: "w0: 64^2 SIE+shear, 10+10 MGE, 32^2 sky, GL32, 20 annuli",
+             1: "RXJ1131-scale: 200^2 x2ss, 21^2 PSF, EPL+shear+SIS, 2 lens-light + source Sersic, "
+                "JAM 20+2x10+BH, 60^2 sky x4ss, GL32, 50 bins, 4 images",
+             3: "8 uneven systems (64..256 px, ss 1-3, 8-30 Gaussians, 20-120 bins, GL 24-64)",
+             4: "IFU-scale: 400^2 x3ss, 31^2 PSF, EPL+shear+2 SIS, JAM 40+2x20+BH, 128^2 sky x4, "
+                "GL64, 400 bins"}
+    n = names.get(w, str(w)) + f"; B={B}"
+    if grad:
+        n += " (forward + gradient)"
+    return n
+
+
+def bench_systems(w):
+    """Fixed geometry from the seeded generators; data filled in later."""
+    bases, B = synth.workload_systems(w)
+    out = []
+    for b in bases:
+        s = dict(b)
+        truth = synth.theta_truth(0 if w == 0 else 1)
+        s["img_xy"] = synth.ring_images(truth[0], s["qso_beta"])
+        s["data"] = np.zeros((s["ny"], s["nx"]), np.float32)
+        s["v_obs"] = np.ones(s["n_bins"], np.float32)
+        s["v_sig"] = np.ones(s["n_bins"], np.float32)
+        s["dt_obs"] = np.array([-8.0, 3.5, -12.7, 5.0, 2.0, 1.0, 1.0][:len(s["img_xy"]) - 1])
+        s["dt_sig"] = np.full(len(s["img_xy"]) - 1, 0.5)
+        out.append(s)
+    return out, B
+
+
+def fill_data_with_gpu_model(systems, w, torch, GladContext):
+    ctx = GladContext(systems)
+    truth = torch.as_tensor(synth.theta_truth(0 if w == 0 else 1), device="cuda")
+    for i, s in enumerate(systems):
+        nz = synth.noise_draws(s, 1000 * w + i + 500)
+        img = ctx.model_image(truth, i).cpu().numpy().astype(np.float64)
+        v = ctx.vrms(truth, i).cpu().numpy().astype(np.float64)
+        s["data"] = (img + np.asarray(s["sigma"], np.float64) * nz["img"]).astype(np.float32)
+        s["v_sig"] = (0.02 * v).astype(np.float32)
+        s["v_obs"] = (v + 0.02 * v * nz["kin"]).astype(np.float32)
+    ctx.close()
+    return systems
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx = float(r[1])
+                for n, v in zip(self.NAMES, r[3:7]):
+                    if "Active" in v and "Not" not in v:
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                pass
+        loaded = [x for x in sm if x > 0.5 * (mx or 1)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _oracle_eval(s, th):
+    sys.path.insert(0, ROOT)
+    from oracle import model
+    return model.loglike(th, s)
+
+
+def cpu_baseline(systems, thetas, sids):
+    """The FP64 oracle, as it stands, over a bounded sample of the workload on all host cores."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    n = cores
+    t0 = time.time()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.starmap(_oracle_eval, [(systems[sids[i % len(sids)]], thetas[i % len(thetas)])
+                                          for i in range(n)])
+    dt = time.time() - t0
+    return {"value": n / dt, "unit": "logL/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} samples of the same workload, one per core (spawn pool), {dt:.1f} s wall",
+            "finite": int(sum(np.isfinite(res)))}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: host cores, bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import model
+    w = args.workload
+    systems, B = bench_systems(w)
+    for i, s in enumerate(systems):
+        truth = synth.theta_truth(0 if w == 0 else 1)
+        s.update(model.build_system(s, truth, synth.noise_draws(s, 1000 * w + i + 500)))
+    B = args.batch or (64 if args.grad else B)
+    th, sid = synth.workload_thetas(w, B, len(systems))
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    per_step = cores
+    times = []
+    with mp.get_context("spawn").Pool(cores) as pool:
+        for step in range(args.warmup + args.steps):
+            idx = [(step * per_step + i) % B for i in range(per_step)]
+            t0 = time.time()
+            pool.starmap(_oracle_eval, [(systems[sid[i]], th[i]) for i in idx])
+            if step >= args.warmup:
+                times.append(time.time() - t0)
+    T = sum(times)
+    val = per_step * len(times) / T
+    unit = "logL/s"
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": unit, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * T / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(w, False, B), "samples_per_step": per_step},
+            "cpu_baseline": {"value": val, "unit": unit, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} samples per step, one per host core"},
+            "e2e": {"value": val, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2504_01302_b300 import build as _b
+    if not _b.up_to_date() and rank == 0:
+        _b.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2504_01302_b300 import _lib
+    from paper_2504_01302_b300.glad import GladContext
+
+    w = args.workload
+    systems, B = bench_systems(w)
+    systems = fill_data_with_gpu_model(systems, w, torch, GladContext)
+    B = args.batch or (64 if args.grad else B)
+    th_np, sid_np = synth.workload_thetas(w, B, len(systems))
+    ctx = GladContext(systems)
+    lib = ctx.lib
+    theta = torch.as_tensor(th_np, device="cuda")
+    sid = torch.as_tensor(sid_np, device="cuda")
+    logL = torch.empty(B, dtype=torch.float64, device="cuda")
+    status = torch.empty(B, dtype=torch.int32, device="cuda")
+    grad = torch.empty(B, 20, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    hs = C.c_void_p(stream.cuda_stream)
+    P = lambda t: C.c_void_p(t.data_ptr())
+
+    def step():
+        if args.grad:
+            rc = lib.glad_loglike_grad(ctx.handle, P(sid), P(theta), B, P(logL), P(grad), P(status),
+                                       None, hs)
+        else:
+            rc = lib.glad_loglike(ctx.handle, P(sid), P(theta), B, P(logL), P(status), None, hs)
+        _lib.check(rc, "step")
+
+    # L2 flush buffer (256 MB > 126 MB L2), written before each timed step, outside its events
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    n_valid = int((status == 0).sum())
+
+    # ---- device-resident timing: K steps, events on the launching stream
+    nk = lib.glad_kernel_times(ctx.handle, 0, None, None)
+    kms = (C.c_double * nk)()
+    kl = (C.c_int * nk)()
+    lib.glad_profile(ctx.handle, 1)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    lib.glad_profile(ctx.handle, 0)
+    lib.glad_kernel_times(ctx.handle, nk, kms, kl)
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        t = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t[0])
+        dist.barrier()
+    value = world * B * args.steps / (t_ms / 1000.0)
+
+    # ---- end to end through the public API with pinned host buffers
+    th_h = torch.as_tensor(th_np).pin_memory()
+    sid_h = torch.as_tensor(sid_np).pin_memory()
+    out_h = torch.empty(B, dtype=torch.float64).pin_memory()
+    st_h = torch.empty(B, dtype=torch.int32).pin_memory()
+    gr_h = torch.empty(B, 20, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        theta.copy_(th_h, non_blocking=True)
+        sid.copy_(sid_h, non_blocking=True)
+        step()
+        out_h.copy_(logL, non_blocking=True)
+        st_h.copy_(status, non_blocking=True)
+        if args.grad:
+            gr_h.copy_(grad, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t[0])
+    h2d = th_h.numel() * 8 + sid_h.numel() * 4
+    d2h = out_h.numel() * 8 + st_h.numel() * 4 + (gr_h.numel() * 8 if args.grad else 0)
+
+    if rank != 0:
+        ctx.close()
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (JAM pair sum): integrand evaluations per launch,
+    # one ex2 each, against the MUFU ex2 rate
+    names = [lib.glad_kernel_name(i).decode() for i in range(nk)]
+    per_kernel = {names[i]: kms[i] / max(kl[i], 1) for i in range(nk) if kl[i]}
+    jam_id = names.index("k_jam_fwd_grad") if args.grad and kl[names.index("k_jam_fwd_grad")] \
+        else names.index("k_jam")
+    jam_ms = kms[jam_id] / max(kl[jam_id], 1)
+    evals = 0
+    for b in range(B):
+        s = systems[sid_np[b]]
+        nl = sum(s["n_mge_light"])
+        nm = s["n_mge_mass"] + (1 if s["has_bh"] else 0)
+        evals += (s["kx"] * s["kss"]) * (s["ky"] * s["kss"]) * nl * nm * s["n_gl"]
+    achieved = evals / (jam_ms / 1000.0) / 1e9
+    clocks = clk.summary()
+    sm_max = clocks["sm_max_mhz"] or 2032.0
+    peak = N_SM * MUFU_EX2_PER_CLK_SM * sm_max * 1e6 / 1e9
+    unit = "logL+grad/s" if args.grad else "logL/s"
+    line = {
+        "metric": METRIC, "value": value, "unit": unit,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(w, args.grad, B), "batch_per_gpu": B,
+                   "precision": "f32 bulk; f64 MGE, tables and chi^2 reductions",
+                   "l2": "flushed (256 MB write) before each timed step", "valid_samples": n_valid},
+        "roofline": {"bound": "alu", "kernel": names[jam_id], "achieved": achieved, "peak": peak,
+                     "unit": "Gexp2/s", "frac": achieved / peak, "traffic": None,
+                     "algorithmic_units": f"{evals} JAM integrand evaluations per launch (1 ex2 each)",
+                     "peak_basis": f"{N_SM} SM x {MUFU_EX2_PER_CLK_SM} ex2/clk/SM (measured) x "
+                                   f"{sm_max:.0f} MHz max SM clock"},
+        "kernels_ms_per_step": per_kernel,
+        "e2e": {"value": world * B * args.steps / (e2e_ms / 1000.0), "unit": unit,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        # k_image and k_conv are timed as one unit: count both launches
+        "gpu_launches": int(sum(kl[i] for i in range(nk))) + int(kl[names.index("k_image+k_conv")]),
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(systems, th_np, sid_np)
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

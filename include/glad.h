@@ -1,0 +1,160 @@
+/*
+ * glad.h -- C ABI of libglad.so: the batched joint lensing + dynamics
+ * log-likelihood of GLaD (arXiv:2504.01302) and its gradient, on one NVIDIA
+ * B300 (sm_103a).
+ *
+ * Conventions shared by every entry point
+ *  - Pointers marked [host] are read during the call and may be freed after it.
+ *    Pointers marked [dev] are CUDA device memory owned by the caller; the library
+ *    never frees them.  A context owns every array it stages on the device.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls enqueue work on it and return without synchronising; the return code
+ *    reports argument and launch errors only.  Kernel-time problems of one sample
+ *    (invalid parameters) are NOT errors: that sample gets logL = -inf,
+ *    gradient 0 and a non-zero status.
+ *  - One context is not thread-safe: serialise calls that use it.
+ *  - On a non-zero return, glad_last_error() holds a message (thread-local).
+ *
+ * Parameter vector theta (20 float64 per sample, angles in radians):
+ *   0 theta_E  1 gamma'  2 q  3 phi (PA, counter-clockwise from +x)  4 x_c  5 y_c
+ *   6 gamma_ext  7 phi_ext  8 I_e,src  9 R_e,src  10 n_src  11 x_src  12 y_src
+ *   13 I_e,ll  14 R_e,ll  15 inclination i  16 beta (= beta_z)  17 Upsilon (M/L)
+ *   18 f_BH = M_BH/M_*  19 H0 [km/s/Mpc]
+ */
+#ifndef GLAD_H
+#define GLAD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GLAD_NTHETA 20
+
+typedef enum {
+  GLAD_OK = 0,
+  GLAD_EINVAL = 1,      /* bad argument or system descriptor */
+  GLAD_ENOMEM = 2,      /* device allocation failed */
+  GLAD_ECUDA = 3,       /* a CUDA call or kernel launch failed */
+  GLAD_ETIMEOUT = 4,    /* a bounded device-side wait gave up */
+  GLAD_EUNSUPPORTED = 5 /* size outside what the kernels support */
+} glad_status;
+
+/* Per-sample status written by the likelihood calls. */
+enum {
+  GLAD_SAMPLE_OK = 0,
+  GLAD_SAMPLE_DOMAIN = 1,     /* parameter outside its domain (q not in (0,1], gamma' not in (1,3), ...) */
+  GLAD_SAMPLE_DEPROJ = 2,     /* cos^2 i >= q'^2 of some Gaussian: no oblate deprojection (App. A) */
+  GLAD_SAMPLE_NEGDENS = 3,    /* deprojected density <= 0 at a probe radius (Sect. 3.3) */
+  GLAD_SAMPLE_NONFINITE = 4   /* a chi^2 term came out NaN or infinite */
+};
+
+/*
+ * One mock or observed system, read at glad_create (all pointers [host]).
+ *
+ * Imaging (Sect. 3.1.1, Table 1): an ny x nx image (row-major, pixel (i,j) centred at
+ * x = (j-(nx-1)/2) pix, y = (i-(ny-1)/2) pix arcsec), each pixel split into ss x ss
+ * sub-pixels that are ray-shot and averaged, then blurred by the psf_k x psf_k PSF
+ * (odd size, unit sum, discrete convolution, zero outside the image).  chi^2_pix runs
+ * over mask != 0 (Eq. chi2 of lens_light).
+ *
+ * Dynamics (Sect. 2.4, Eqs. binned, Vrms, chi2_dyn): a ky x kx spaxel grid of kpix
+ * arcsec centred on the origin, each spaxel split into kss x kss sub-samples at which
+ * the JAM moment is evaluated; kpsf (kpsf_k^2, odd, unit sum) blurs the two sub-sample
+ * maps; bins[ky*kx] gives each spaxel's bin (0..n_bins-1, -1 = unused).  Bins must hold
+ * only spaxels whose sub-samples lie at least (kpsf_k-1)/2 sub-samples from the edge.
+ *
+ * MGE (Sect. 3.2): the App. C convergence is expanded into n_mge_mass Gaussians
+ * log-spaced on [mass_rmin, mass_rmax]; lens-light component c into n_mge_light[c]
+ * Gaussians on [light_rmin, light_rmax]; Euler order mge_P.  has_bh adds a spherical
+ * black-hole Gaussian of dispersion bh_sigma and mass f_BH * Upsilon * L_tot * L_scale
+ * (L_tot = total light of the tracer MGE).  n_gl: Gauss-Legendre order of the JAM u
+ * integral.
+ *
+ * Delays (Eqs. fermat potential, chi2_tmd): n_img observed image positions
+ * (img_xy[n_img*2]) and n_img-1 delays relative to image 0 (dt_obs, dt_sig, days).
+ */
+typedef struct glad_system_desc {
+  int nx, ny, ss;
+  double pix;
+  const float *data, *sigma;       /* [ny*nx] */
+  const unsigned char *mask;       /* [ny*nx], 0 = excluded */
+  int psf_k;
+  const float *psf;                /* [psf_k*psf_k] */
+  double src_q, src_phi;           /* Sersic source axis ratio and PA */
+  double ll_n, ll_q;               /* first lens light: Sersic index and axis ratio */
+  int n_ll2;
+  const double *ll2;               /* [n_ll2*4]: I_e, R_e, n, q of further lens lights */
+  int n_sis;
+  const double *sis;               /* [n_sis*3]: theta_E, x, y of SIS perturbers */
+  double r_soft;                   /* App. C softening radius of the MGE'd convergence */
+  int kx, ky, kss;
+  double kpix;
+  int kpsf_k;
+  const float *kpsf;               /* [kpsf_k*kpsf_k] */
+  const int *bins;                 /* [ky*kx] */
+  int n_bins;
+  const float *v_obs, *v_sig;      /* [n_bins] km/s */
+  int n_mge_mass;
+  const int *n_mge_light;          /* [1 + n_ll2] */
+  int mge_P, n_gl;
+  double mass_rmin, mass_rmax, light_rmin, light_rmax;
+  int has_bh;
+  double bh_sigma, L_scale;
+  int n_img;
+  const double *img_xy, *dt_obs, *dt_sig;
+  double z_d, z_s, omega_m, kappa_ext;
+} glad_system_desc;
+
+typedef struct glad_ctx glad_ctx;
+
+/* Validate n_sys descriptors, precompute per-system constants (distances, Gauss-Legendre
+ * nodes, Euler coefficients, the binning-after-PSF operator) and stage them on the current
+ * device.  *out receives the context.  Errors: GLAD_EINVAL, GLAD_ENOMEM, GLAD_ECUDA,
+ * GLAD_EUNSUPPORTED (a size above the kernels' limits). */
+glad_status glad_create(const glad_system_desc *sys, int n_sys, glad_ctx **out);
+
+/* Free everything the context staged (synchronises the device first). */
+void glad_destroy(glad_ctx *ctx);
+
+/* Batched joint log-likelihood, Eq. chi_general / Eq. Posterior_LD:
+ *   logL[b] = -(chi2_pix + chi2_dyn + chi2_tmd)/2   for sample b in [0, B).
+ * sys_id [dev, int32 B], theta [dev, float64 B*20], logL [dev, float64 B],
+ * sample_status [dev, int32 B], terms [dev, float64 B*3] or NULL: the three chi^2 terms.
+ * The per-sample workspace is allocated (cudaMalloc) the first time a batch of this
+ * size is seen and kept by the context.
+ * Errors: GLAD_EINVAL (B < 1, NULL output), GLAD_ENOMEM (workspace), GLAD_ECUDA. */
+glad_status glad_loglike(glad_ctx *ctx, const int *sys_id, const double *theta, int B,
+                         double *logL, int *sample_status, double *terms, void *stream);
+
+/* As glad_loglike, plus the gradient grad [dev, float64 B*20] = d logL / d theta from
+ * hand-written adjoint kernels.  Invalid samples get grad = 0. */
+glad_status glad_loglike_grad(glad_ctx *ctx, const int *sys_id, const double *theta, int B,
+                              double *logL, double *grad, int *sample_status, double *terms,
+                              void *stream);
+
+/* PSF-blurred model image (Eq. dpre with the parametric source) of one sample of
+ * system `sys`: theta [dev, 20 float64], image [dev, float32 ny*nx]. */
+glad_status glad_model_image(glad_ctx *ctx, int sys, const double *theta, float *image,
+                             void *stream);
+
+/* Binned model v_rms (Eqs. binned and Vrms) of one sample of system `sys`:
+ * theta [dev, 20 float64], vrms [dev, float32 n_bins] km/s. */
+glad_status glad_vrms(glad_ctx *ctx, int sys, const double *theta, float *vrms, void *stream);
+
+/* Kernel-level timing, for benchmarks.  glad_profile(ctx, 1) makes every later call
+ * record a CUDA event pair on its stream around each kernel it launches (0 stops it).
+ * glad_kernel_times(ctx, n, ms, launches) waits for those events, adds the elapsed
+ * milliseconds and the launch count of kernel id k (0 <= k < n) into ms[k] and
+ * launches[k] [host arrays of n], and forgets the recorded pairs.  Returns the number
+ * of kernel ids (call with n = 0 to query it).  glad_kernel_name(k) names id k. */
+int glad_profile(glad_ctx *ctx, int enable);
+int glad_kernel_times(glad_ctx *ctx, int n, double *ms, int *launches);
+const char *glad_kernel_name(int k);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *glad_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GLAD_H */

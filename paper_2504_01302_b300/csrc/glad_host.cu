@@ -1,0 +1,583 @@
+// C ABI of libglad: context creation (host-side FP64 precomputation and staging),
+// workspace management and the launch sequences of the likelihood calls.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <string>
+#include <vector>
+
+#include "glad_internal.cuh"
+
+cudaError_t launch_grad(glad_ctx *c, const int *sys_id, const double *theta, int B, double *grad,
+                        cudaStream_t st);
+cudaError_t grad_ws_ensure(glad_ctx *c, int B);
+void grad_ws_free(glad_ctx *c);
+
+namespace {
+
+thread_local std::string g_err;
+
+glad_status fail(glad_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+const double C_KMS = 299792.458;
+const double ARCSEC = PI_D / 648000.0;
+const double MPC_KM = 3.0856775814913673e19;
+const double DAY_S = 86400.0;
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n (n >= 2).
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  auto legendre = [n](double z, double &p_n, double &p_nm1) {
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    p_n = p1;
+    p_nm1 = p0;
+  };
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = cos(PI_D * (i + 0.75) / (n + 0.5));
+    double pn, pm, dp;
+    for (int it = 0; it < 100; ++it) {
+      legendre(z, pn, pm);
+      dp = n * (z * pn - pm) / (z * z - 1.0);
+      const double dz = pn / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    legendre(z, pn, pm);
+    dp = n * (z * pn - pm) / (z * z - 1.0);
+    x[i] = -z;
+    x[n - 1 - i] = z;
+    w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// flat LambdaCDM comoving distance [Mpc] by 96-point Gauss-Legendre (smooth integrand)
+double comoving(double z, double H0, double om) {
+  std::vector<double> x, w;
+  gauss_legendre(96, x, w);
+  double s = 0.0;
+  for (size_t i = 0; i < x.size(); ++i) {
+    const double zz = 0.5 * z * (x[i] + 1.0);
+    s += w[i] / sqrt(om * pow(1.0 + zz, 3) + 1.0 - om);
+  }
+  return C_KMS / H0 * 0.5 * z * s;
+}
+
+template <class T>
+T *upload(SysHost &sh, const T *src, size_t n) {
+  T *d = nullptr;
+  if (n == 0) n = 1;
+  if (cudaMalloc(&d, n * sizeof(T)) != cudaSuccess) {
+    sh.allocs.push_back(nullptr);
+    return nullptr;
+  }
+  sh.allocs.push_back(d);
+  if (src && cudaMemcpy(d, src, n * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) return nullptr;
+  return d;
+}
+
+glad_status validate(const glad_system_desc &d, int idx) {
+#define REQ(cond, ...) \
+  if (!(cond)) return fail(GLAD_EINVAL, "system %d: " __VA_ARGS__)
+  REQ(d.nx > 0 && d.ny > 0 && d.ss > 0 && d.pix > 0, "bad image geometry", idx);
+  REQ(d.data && d.sigma && d.mask && d.psf, "missing image arrays", idx);
+  REQ(d.psf_k > 0 && d.psf_k % 2 == 1, "psf_k must be odd", idx);
+  REQ(d.kx > 0 && d.ky > 0 && d.kss > 0 && d.kpix > 0, "bad sky geometry", idx);
+  REQ(d.kpsf && d.kpsf_k > 0 && d.kpsf_k % 2 == 1, "kpsf_k must be odd", idx);
+  REQ(d.bins && d.v_obs && d.v_sig && d.n_bins > 0, "missing kinematic arrays", idx);
+  REQ(d.n_mge_mass >= 2 && d.n_mge_light, "bad MGE sizes", idx);
+  REQ(d.mge_P > 0 && d.n_gl >= 2, "bad MGE order or quadrature order", idx);
+  REQ(d.mass_rmin > 0 && d.mass_rmax > d.mass_rmin && d.light_rmin > 0 &&
+          d.light_rmax > d.light_rmin, "bad MGE ranges", idx);
+  REQ(d.n_img >= 2 && d.img_xy && d.dt_obs && d.dt_sig, "need >= 2 images with delays", idx);
+  REQ(d.n_ll2 >= 0 && (d.n_ll2 == 0 || d.ll2), "bad extra lens lights", idx);
+  REQ(d.n_sis >= 0 && (d.n_sis == 0 || d.sis), "bad SIS list", idx);
+  REQ(d.z_s > d.z_d && d.z_d > 0 && d.omega_m > 0 && d.omega_m < 1, "bad cosmology", idx);
+#undef REQ
+#define SUP(cond, ...) \
+  if (!(cond)) return fail(GLAD_EUNSUPPORTED, "system %d: " __VA_ARGS__)
+  SUP(d.psf_k <= GLAD_MAX_PSF, "psf_k > %d", idx, GLAD_MAX_PSF);
+  SUP(d.n_bins <= GLAD_MAX_BINS, "n_bins > %d", idx, GLAD_MAX_BINS);
+  SUP(d.n_mge_mass <= GLAD_MAX_MASS, "n_mge_mass > %d", idx, GLAD_MAX_MASS);
+  SUP(d.mge_P <= GLAD_MAX_P, "mge_P > %d", idx, GLAD_MAX_P);
+  SUP(d.n_img <= GLAD_MAX_IMG, "n_img > %d", idx, GLAD_MAX_IMG);
+  SUP(1 + d.n_ll2 <= 4, "more than 4 lens-light components", idx);
+  int nl = 0;
+  for (int c = 0; c < 1 + d.n_ll2; ++c) {
+    if (d.n_mge_light[c] < 2) return fail(GLAD_EINVAL, "system %d: n_mge_light < 2", idx);
+    nl += d.n_mge_light[c];
+  }
+  SUP(nl <= GLAD_MAX_LIGHT, "tracer Gaussians > %d", idx, GLAD_MAX_LIGHT);
+  for (int i = 0; i < d.kx * d.ky; ++i)
+    if (d.bins[i] >= d.n_bins) return fail(GLAD_EINVAL, "system %d: bin index >= n_bins", idx);
+#undef SUP
+  return GLAD_OK;
+}
+
+glad_status build_system(int idx, const glad_system_desc &d, SysHost &sh, SysDev &sd) {
+  memset(&sd, 0, sizeof sd);
+  sh.d = d;
+  const int npix = d.nx * d.ny;
+  sh.npix = npix;
+  sd.nx = d.nx;
+  sd.ny = d.ny;
+  sd.ss = d.ss;
+  sd.npix = npix;
+  sd.pix = (float)d.pix;
+  std::vector<float> wgt(npix);
+  for (int i = 0; i < npix; ++i) wgt[i] = d.mask[i] ? 1.0f / d.sigma[i] : 0.0f;
+  sd.data = upload(sh, d.data, npix);
+  sd.wgt = upload(sh, wgt.data(), npix);
+  sd.psf_k = d.psf_k;
+  sd.psf = upload(sh, d.psf, (size_t)d.psf_k * d.psf_k);
+  sd.src_q = (float)d.src_q;
+  sd.src_cphi = (float)cos(d.src_phi);
+  sd.src_sphi = (float)sin(d.src_phi);
+  sd.n_lcomp = 1 + d.n_ll2;
+  std::vector<double> lcomp(4 * sd.n_lcomp);
+  lcomp[0] = 0.0;
+  lcomp[1] = 0.0;
+  lcomp[2] = d.ll_n;
+  lcomp[3] = d.ll_q;
+  for (int k = 0; k < d.n_ll2; ++k)
+    for (int m = 0; m < 4; ++m) lcomp[4 * (k + 1) + m] = d.ll2[4 * k + m];
+  sd.lcomp = upload(sh, lcomp.data(), lcomp.size());
+  sd.n_sis = d.n_sis;
+  sd.sis = upload(sh, d.sis, (size_t)3 * d.n_sis);
+  sd.r_soft = d.r_soft;
+  // sky sub-grid
+  sd.nsx = d.kx * d.kss;
+  sd.nsy = d.ky * d.kss;
+  sd.n_sub = sd.nsx * sd.nsy;
+  sh.n_sub = sd.n_sub;
+  sd.dsub = (float)(d.kpix / d.kss);
+  // binning-after-PSF operator: W_l(s') = sum_{s in bin l} P(s - s')
+  {
+    const int K = d.kpsf_k, h = (K - 1) / 2, nsx = sd.nsx, nsy = sd.nsy;
+    std::vector<int> off(sd.n_sub + 1, 0);
+    std::vector<int> wb;
+    std::vector<float> wv;
+    std::vector<int> taps_a, taps_b;
+    std::vector<double> taps_v;
+    for (int a = 0; a < K; ++a)
+      for (int bb = 0; bb < K; ++bb)
+        if (d.kpsf[a * K + bb] != 0.0f) {
+          taps_a.push_back(a - h);
+          taps_b.push_back(bb - h);
+          taps_v.push_back(d.kpsf[a * K + bb]);
+        }
+    std::vector<double> accw(d.n_bins, 0.0);
+    std::vector<int> touched;
+    for (int I = 0; I < nsy; ++I)
+      for (int J = 0; J < nsx; ++J) {
+        touched.clear();
+        for (size_t t = 0; t < taps_v.size(); ++t) {
+          // s = s' + (a-h, b-h) receives P[a,b] * m(s')
+          const int si = I + taps_a[t], sj = J + taps_b[t];
+          if (si < 0 || si >= nsy || sj < 0 || sj >= nsx) continue;
+          const int l = d.bins[(si / d.kss) * d.kx + (sj / d.kss)];
+          if (l < 0) continue;
+          if (accw[l] == 0.0) touched.push_back(l);
+          accw[l] += taps_v[t];
+        }
+        std::sort(touched.begin(), touched.end());
+        for (int l : touched) {
+          wb.push_back(l);
+          wv.push_back((float)accw[l]);
+          accw[l] = 0.0;
+        }
+        off[I * nsx + J + 1] = (int)wb.size();
+      }
+    sd.w_off = upload(sh, off.data(), off.size());
+    sd.w_bin = upload(sh, wb.data(), wb.size());
+    sd.w_val = upload(sh, wv.data(), wv.size());
+  }
+  sd.n_bins = d.n_bins;
+  sd.v_obs = upload(sh, d.v_obs, d.n_bins);
+  sd.v_sig = upload(sh, d.v_sig, d.n_bins);
+  // MGE Gaussians
+  const int nM = d.n_mge_mass;
+  const int nMt = nM + (d.has_bh ? 1 : 0);
+  std::vector<double> sig_m(nMt), mw_m(nM);
+  {
+    const double lo = log(d.mass_rmin), hi = log(d.mass_rmax), dl = (hi - lo) / (nM - 1);
+    for (int j = 0; j < nM; ++j) {
+      sig_m[j] = exp(lo + dl * j);
+      mw_m[j] = (j == 0 || j == nM - 1 ? 0.5 : 1.0) * dl / SQRT2PI_D;
+    }
+    if (d.has_bh) sig_m[nM] = d.bh_sigma;
+  }
+  std::vector<double> sig_l, mw_l, qp_l;
+  std::vector<int> comp_of;
+  for (int cc = 0; cc < 1 + d.n_ll2; ++cc) {
+    const int N = d.n_mge_light[cc];
+    const double lo = log(d.light_rmin), hi = log(d.light_rmax), dl = (hi - lo) / (N - 1);
+    const double q = cc == 0 ? d.ll_q : d.ll2[4 * (cc - 1) + 3];
+    for (int k = 0; k < N; ++k) {
+      sig_l.push_back(exp(lo + dl * k));
+      mw_l.push_back((k == 0 || k == N - 1 ? 0.5 : 1.0) * dl / SQRT2PI_D);
+      qp_l.push_back(q);
+      comp_of.push_back(cc);
+    }
+  }
+  const int nL = (int)sig_l.size();
+  sd.n_mass = nM;
+  sd.n_mass_tot = nMt;
+  sd.n_light = nL;
+  sh.n_mass_tot = nMt;
+  sh.n_light = nL;
+  sd.lcomp_of = upload(sh, comp_of.data(), nL);
+  sd.sig_mass = upload(sh, sig_m.data(), nMt);
+  sd.sig_light = upload(sh, sig_l.data(), nL);
+  sd.mw_mass = upload(sh, mw_m.data(), nM);
+  sd.mw_light = upload(sh, mw_l.data(), nL);
+  sd.qp_light = upload(sh, qp_l.data(), nL);
+  // Euler coefficients (Abate & Whitt 2006) in the Gaussian-mixture scaling of Sect. 3.2
+  {
+    const int P = d.mge_P;
+    std::vector<double> xi(2 * P + 1, 0.0), eta(2 * P + 1);
+    std::vector<double2> chi(2 * P + 1);
+    xi[0] = 0.5;
+    for (int m = 1; m <= P; ++m) xi[m] = 1.0;
+    xi[2 * P] = pow(2.0, -P);
+    double binom = 1.0;  // C(P, k)
+    for (int k = 1; k < P; ++k) {
+      binom = binom * (P - k + 1) / k;
+      xi[2 * P - k] = xi[2 * P - k + 1] + pow(2.0, -P) * binom;
+    }
+    const double A = 2.0 * P * log(10.0) / 3.0;
+    for (int m = 0; m <= 2 * P; ++m) {
+      eta[m] = (m % 2 ? -1.0 : 1.0) * 2.0 * SQRT2PI_D * pow(10.0, P / 3.0) * xi[m];
+      // principal square root of A + 2 pi i m
+      const double re = A, im = 2.0 * PI_D * m;
+      const double r = sqrt(hypot(re, im));
+      const double th = 0.5 * atan2(im, re);
+      chi[m] = make_double2(r * cos(th), r * sin(th));
+    }
+    sd.mge_P = P;
+    sd.eta = upload(sh, eta.data(), eta.size());
+    sd.chi = upload(sh, chi.data(), chi.size());
+  }
+  // JAM u nodes with the per-pair map u = u_s (exp(lam t) - 1), lam = ln(1 + 1/u_s),
+  // u_s = min(1, sigma_j / max(r_max, sigma_k))
+  {
+    const int G = d.n_gl;
+    std::vector<double> x, w;
+    gauss_legendre(G, x, w);
+    double r_max = 0.0;
+    for (int I = 0; I < sd.nsy; ++I)
+      for (int J = 0; J < sd.nsx; ++J) {
+        const double xx = (J - 0.5 * (sd.nsx - 1)) * (d.kpix / d.kss);
+        const double yy = (I - 0.5 * (sd.nsy - 1)) * (d.kpix / d.kss);
+        r_max = std::max(r_max, hypot(xx, yy));
+      }
+    const int n_ent = nL * nMt * G;
+    std::vector<double> gu(n_ent), gw(n_ent);
+    for (int k = 0; k < nL; ++k)
+      for (int j = 0; j < nMt; ++j) {
+        const double us = std::min(1.0, sig_m[j] / std::max(r_max, sig_l[k]));
+        const double lam = log1p(1.0 / us);
+        for (int g = 0; g < G; ++g) {
+          const double t = 0.5 * (x[g] + 1.0), wt = 0.5 * w[g];
+          const double e = exp(lam * t);
+          gu[(k * nMt + j) * G + g] = us * (e - 1.0);
+          gw[(k * nMt + j) * G + g] = wt * us * lam * e;
+        }
+      }
+    sd.n_gl = G;
+    sd.n_ent = n_ent;
+    sh.n_ent = n_ent;
+    sd.gl_u = upload(sh, gu.data(), n_ent);
+    sd.gl_wu = upload(sh, gw.data(), n_ent);
+  }
+  {
+    std::vector<float> cx(nL), cy(nL);
+    for (int k = 0; k < nL; ++k) {
+      cx[k] = (float)(LOG2E_D / (2.0 * sig_l[k] * sig_l[k]));
+      cy[k] = (float)(LOG2E_D / (2.0 * sig_l[k] * sig_l[k] * qp_l[k] * qp_l[k]));
+    }
+    sd.sb_cx = upload(sh, cx.data(), nL);
+    sd.sb_cy = upload(sh, cy.data(), nL);
+  }
+  sd.has_bh = d.has_bh;
+  sd.bh_sigma = d.bh_sigma;
+  sd.L_scale = d.L_scale;
+  // distances: v^2 unit = c^2/(4 pi) D_dt,int / ((1+z_d) D_d) arcsec (independent of H0);
+  // delay per arcsec^2 of Fermat potential = D_dt,int / c * arcsec^2 (proportional to 1/H0)
+  {
+    const double H = 70.0;
+    const double cd = comoving(d.z_d, H, d.omega_m), cs = comoving(d.z_s, H, d.omega_m);
+    const double D_d = cd / (1 + d.z_d), D_s = cs / (1 + d.z_s), D_ds = (cs - cd) / (1 + d.z_s);
+    const double D_dt = (1 + d.z_d) * D_d * D_s / D_ds;
+    const double D_int = (1.0 - d.kappa_ext) * D_dt;
+    sd.v2unit = C_KMS * C_KMS / (4.0 * PI_D) * D_int / ((1 + d.z_d) * D_d) * ARCSEC;
+    sd.dt_per_arcsec2_H0 = D_int * H * MPC_KM / C_KMS * ARCSEC * ARCSEC / DAY_S;
+  }
+  sd.n_img = d.n_img;
+  sd.img_xy = upload(sh, d.img_xy, 2 * (size_t)d.n_img);
+  sd.dt_obs = upload(sh, d.dt_obs, d.n_img - 1);
+  sd.dt_sig = upload(sh, d.dt_sig, d.n_img - 1);
+  sd.n_img_tiles = (npix + LENS_THREADS - 1) / LENS_THREADS;
+  sd.n_sky_tiles = (sd.n_sub + JAM_TILE - 1) / JAM_TILE;
+  sd.n_tab_blocks = (sd.n_ent + TAB_THREADS - 1) / TAB_THREADS;
+  for (void *p : sh.allocs)
+    if (!p) return fail(GLAD_ENOMEM, "system %d: device allocation failed", idx);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(GLAD_ECUDA, "system %d: upload failed: %s", idx, cudaGetErrorString(e));
+  return GLAD_OK;
+}
+
+void ws_free(Workspace &w) {
+  for (void *p : w.allocs) cudaFree(p);
+  w.allocs.clear();
+  w.d = WsDev{};
+  w.B = 0;
+}
+
+template <class T>
+bool ws_alloc(Workspace &w, T *&p, size_t n) {
+  void *d = nullptr;
+  if (cudaMalloc(&d, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) return false;
+  w.allocs.push_back(d);
+  p = (T *)d;
+  return true;
+}
+
+glad_status ws_ensure(glad_ctx *c, int B) {
+  if (c->ws.B >= B) return GLAD_OK;
+  cudaDeviceSynchronize();
+  ws_free(c->ws);
+  Workspace &w = c->ws;
+  const size_t b = B;
+  bool ok = ws_alloc(w, w.d.lp, b) && ws_alloc(w, w.d.dp, b) &&
+            ws_alloc(w, w.d.nu0, b * c->max_light) && ws_alloc(w, w.d.c0, b * c->max_light) &&
+            ws_alloc(w, w.d.Cj, b * c->max_mass_tot) && ws_alloc(w, w.d.e2, b * c->max_mass_tot) &&
+            ws_alloc(w, w.d.I0f, b * c->max_light) && ws_alloc(w, w.d.tab, b * c->max_ent) &&
+            ws_alloc(w, w.d.img, b * c->max_pix) && ws_alloc(w, w.d.binacc, b * c->max_bins * 2) &&
+            ws_alloc(w, w.d.terms, b * 3) && ws_alloc(w, w.d.status, b);
+  if (!ok) {
+    ws_free(w);
+    return fail(GLAD_ENOMEM, "workspace for B=%d does not fit on the device", B);
+  }
+  w.B = B;
+  return GLAD_OK;
+}
+
+glad_status forward(glad_ctx *c, const int *sys_id, const double *theta, int B, cudaStream_t st,
+                    float *image_out, float *vrms_out) {
+  glad_status s = ws_ensure(c, B);
+  if (s != GLAD_OK) return s;
+  cudaError_t e;
+  e = cudaMemsetAsync(c->ws.d.terms, 0, sizeof(double) * 3 * B, st);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(c->ws.d.binacc, 0, sizeof(double) * 2 * c->max_bins * (size_t)B, st);
+  if (e == cudaSuccess) e = GLAD_PROF(c, st, KID_PREP, launch_prep(c, sys_id, theta, B, st));
+  if (e == cudaSuccess && !image_out)
+    e = GLAD_PROF(c, st, KID_TABLE, launch_table(c, sys_id, B, st));
+  if (e == cudaSuccess && !vrms_out)
+    e = GLAD_PROF(c, st, KID_IMAGE_CONV, launch_lens(c, sys_id, B, image_out, st));
+  if (e == cudaSuccess && !image_out) e = GLAD_PROF(c, st, KID_JAM, launch_jam(c, sys_id, B, st));
+  if (e == cudaSuccess && !image_out)
+    e = GLAD_PROF(c, st, KID_KIN, launch_kin_finalize(c, sys_id, B, vrms_out, st));
+  if (e != cudaSuccess) return fail(GLAD_ECUDA, "launch failed: %s", cudaGetErrorString(e));
+  return GLAD_OK;
+}
+
+const char *kKernelNames[KID_N] = {
+    "k_prep", "k_table", "k_image+k_conv", "k_jam", "k_kin_finalize", "k_combine",
+    "k_grad_lens", "k_jam_fwd_grad", "k_jam_adjoint", "k_grad_chain"};
+
+}  // namespace
+
+cudaError_t prof_begin(glad_ctx *c, cudaStream_t st, cudaEvent_t *a) {
+  *a = nullptr;
+  if (!c->prof) return cudaSuccess;
+  if (c->ev_pool.empty()) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    c->ev_pool.push_back(e);
+  }
+  *a = c->ev_pool.back();
+  c->ev_pool.pop_back();
+  return cudaEventRecord(*a, st);
+}
+
+cudaError_t prof_end(glad_ctx *c, cudaStream_t st, int id, cudaEvent_t a) {
+  if (!c->prof || !a) return cudaSuccess;
+  cudaEvent_t b;
+  if (c->ev_pool.empty()) {
+    cudaError_t r = cudaEventCreate(&b);
+    if (r != cudaSuccess) return r;
+  } else {
+    b = c->ev_pool.back();
+    c->ev_pool.pop_back();
+  }
+  c->recs.push_back({id, a, b});
+  return cudaEventRecord(b, st);
+}
+
+extern "C" {
+
+const char *glad_last_error(void) { return g_err.c_str(); }
+
+int glad_profile(glad_ctx *c, int enable) {
+  if (!c) return -1;
+  c->prof = enable ? 1 : 0;
+  return 0;
+}
+
+int glad_kernel_times(glad_ctx *c, int n, double *ms, int *launches) {
+  if (!c) return -1;
+  if (n > 0 && ms && launches) {
+    for (auto &r : c->recs) {
+      cudaEventSynchronize(r.b);
+      float t = 0.0f;
+      cudaEventElapsedTime(&t, r.a, r.b);
+      if (r.id < n) {
+        ms[r.id] += t;
+        launches[r.id] += 1;
+      }
+    }
+  }
+  for (auto &r : c->recs) {
+    c->ev_pool.push_back(r.a);
+    c->ev_pool.push_back(r.b);
+  }
+  c->recs.clear();
+  return KID_N;
+}
+
+const char *glad_kernel_name(int k) { return (k >= 0 && k < KID_N) ? kKernelNames[k] : ""; }
+
+glad_status glad_create(const glad_system_desc *sys, int n_sys, glad_ctx **out) {
+  g_err.clear();
+  if (!sys || n_sys < 1 || !out) return fail(GLAD_EINVAL, "glad_create: bad arguments");
+  *out = nullptr;
+  for (int i = 0; i < n_sys; ++i) {
+    glad_status s = validate(sys[i], i);
+    if (s != GLAD_OK) return s;
+  }
+  glad_ctx *c = new glad_ctx();
+  c->n_sys = n_sys;
+  c->sys.resize(n_sys);
+  c->h_sysdev.resize(n_sys);
+  for (int i = 0; i < n_sys; ++i) {
+    glad_status s = build_system(i, sys[i], c->sys[i], c->h_sysdev[i]);
+    if (s != GLAD_OK) {
+      glad_destroy(c);
+      return s;
+    }
+    const SysDev &d = c->h_sysdev[i];
+    c->max_light = std::max(c->max_light, d.n_light);
+    c->max_mass_tot = std::max(c->max_mass_tot, d.n_mass_tot);
+    c->max_ent = std::max(c->max_ent, d.n_ent);
+    c->max_pix = std::max(c->max_pix, d.npix);
+    c->max_bins = std::max(c->max_bins, d.n_bins);
+    c->max_sub = std::max(c->max_sub, d.n_sub);
+    c->max_img_tiles = std::max(c->max_img_tiles, d.n_img_tiles);
+    c->max_sky_tiles = std::max(c->max_sky_tiles, d.n_sky_tiles);
+    c->max_tab_blocks = std::max(c->max_tab_blocks, d.n_tab_blocks);
+  }
+  if (cudaMalloc(&c->d_sys, sizeof(SysDev) * n_sys) != cudaSuccess ||
+      cudaMemcpy(c->d_sys, c->h_sysdev.data(), sizeof(SysDev) * n_sys, cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMalloc(&c->d_one_sys, sizeof(int) * n_sys) != cudaSuccess) {
+    glad_destroy(c);
+    return fail(GLAD_ENOMEM, "glad_create: device allocation failed");
+  }
+  std::vector<int> ids(n_sys);
+  for (int i = 0; i < n_sys; ++i) ids[i] = i;
+  cudaMemcpy(c->d_one_sys, ids.data(), sizeof(int) * n_sys, cudaMemcpyHostToDevice);
+  set_conv_smem_limit();
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    glad_destroy(c);
+    return fail(GLAD_ECUDA, "glad_create: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return GLAD_OK;
+}
+
+void glad_destroy(glad_ctx *c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  ws_free(c->ws);
+  grad_ws_free(c);
+  for (auto &s : c->sys)
+    for (void *p : s.allocs)
+      if (p) cudaFree(p);
+  cudaFree(c->d_sys);
+  cudaFree(c->d_one_sys);
+  for (auto &r : c->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+}
+
+glad_status glad_loglike(glad_ctx *c, const int *sys_id, const double *theta, int B, double *logL,
+                         int *sample_status, double *terms, void *stream) {
+  g_err.clear();
+  if (!c || !sys_id || !theta || !logL || !sample_status || B < 1)
+    return fail(GLAD_EINVAL, "glad_loglike: bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  glad_status s = forward(c, sys_id, theta, B, st, nullptr, nullptr);
+  if (s != GLAD_OK) return s;
+  cudaError_t e =
+      GLAD_PROF(c, st, KID_COMBINE, launch_combine(c, B, logL, sample_status, terms, st));
+  if (e != cudaSuccess) return fail(GLAD_ECUDA, "launch failed: %s", cudaGetErrorString(e));
+  return GLAD_OK;
+}
+
+glad_status glad_loglike_grad(glad_ctx *c, const int *sys_id, const double *theta, int B,
+                              double *logL, double *grad, int *sample_status, double *terms,
+                              void *stream) {
+  g_err.clear();
+  if (!c || !sys_id || !theta || !logL || !grad || !sample_status || B < 1)
+    return fail(GLAD_EINVAL, "glad_loglike_grad: bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (grad_ws_ensure(c, B) != cudaSuccess)
+    return fail(GLAD_ENOMEM, "gradient workspace for B=%d does not fit", B);
+  glad_status s = forward(c, sys_id, theta, B, st, nullptr, nullptr);
+  if (s != GLAD_OK) return s;
+  cudaError_t e = launch_grad(c, sys_id, theta, B, grad, st);
+  if (e == cudaSuccess)
+    e = GLAD_PROF(c, st, KID_COMBINE, launch_combine(c, B, logL, sample_status, terms, st));
+  if (e != cudaSuccess) return fail(GLAD_ECUDA, "gradient launch failed: %s", cudaGetErrorString(e));
+  return GLAD_OK;
+}
+
+glad_status glad_model_image(glad_ctx *c, int sys, const double *theta, float *image,
+                             void *stream) {
+  g_err.clear();
+  if (!c || !theta || !image || sys < 0 || sys >= c->n_sys)
+    return fail(GLAD_EINVAL, "glad_model_image: bad arguments");
+  return forward(c, c->d_one_sys + sys, theta, 1, (cudaStream_t)stream, image, nullptr);
+}
+
+glad_status glad_vrms(glad_ctx *c, int sys, const double *theta, float *vrms, void *stream) {
+  g_err.clear();
+  if (!c || !theta || !vrms || sys < 0 || sys >= c->n_sys)
+    return fail(GLAD_EINVAL, "glad_vrms: bad arguments");
+  return forward(c, c->d_one_sys + sys, theta, 1, (cudaStream_t)stream, nullptr, vrms);
+}
+
+}  // extern "C"

@@ -1,0 +1,190 @@
+// Internal declarations of libglad: device-side system layout, per-sample
+// workspace, small math helpers and the kernel launchers of each .cu file.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/glad.h"
+
+#define GLAD_MAX_TM 64        // EPL series terms kept in the per-sample block
+#define GLAD_MAX_BINS 1024    // kinematic bins per system (shared-memory bin accumulators)
+#define GLAD_MAX_LIGHT 128    // tracer Gaussians per system
+#define GLAD_MAX_MASS 127     // mass Gaussians per system (without the black hole)
+#define GLAD_MAX_PSF 63       // imaging PSF side
+#define GLAD_MAX_P 20         // Euler order
+#define GLAD_MAX_IMG 8        // quasar images
+
+// ---------------------------------------------------------------------------
+// device-resident description of one system (all pointers are device memory)
+// ---------------------------------------------------------------------------
+struct SysDev {
+  // imaging
+  int nx, ny, ss, npix;
+  float pix;
+  const float *data;     // [npix]
+  const float *wgt;      // [npix] mask / sigma
+  int psf_k;
+  const float *psf;      // [psf_k^2]
+  float src_q, src_cphi, src_sphi;
+  int n_lcomp;           // lens-light components (1 + n_ll2)
+  const double *lcomp;   // [n_lcomp*4]: I_e, R_e, n, q (row 0: I_e, R_e from theta)
+  int n_sis;
+  const double *sis;     // [n_sis*3]
+  double r_soft;
+  // kinematics: sub-sampled sky grid and the binning-after-PSF operator (CSR by sub-sample)
+  int nsx, nsy, n_sub;
+  float dsub;
+  const int *w_off;      // [n_sub+1]
+  const int *w_bin;      // [nnz]
+  const float *w_val;    // [nnz]
+  int n_bins;
+  const float *v_obs, *v_sig;
+  // MGE
+  int n_mass, n_mass_tot, n_light;
+  const int *lcomp_of;   // [n_light]
+  const double *sig_mass, *sig_light;      // [n_mass_tot], [n_light]
+  const double *mw_mass, *mw_light;        // w_n * dln(sigma) / sqrt(2 pi)
+  const double *qp_light;                  // [n_light]
+  int mge_P;
+  const double *eta;                        // [2P+1]
+  const double2 *chi;                       // [2P+1]
+  // JAM pair table geometry
+  int n_gl, n_ent;                          // n_ent = n_light * n_mass_tot * n_gl
+  const double *gl_u, *gl_wu;               // [n_ent]: u node, weight * du/dt
+  const float *sb_cx, *sb_cy;               // [n_light]: log2(e)/(2 s^2), log2(e)/(2 s^2 q'^2)
+  int has_bh;
+  double bh_sigma, L_scale;
+  double v2unit;                            // km^2/s^2 per (kappa * arcsec)
+  double dt_per_arcsec2_H0;                 // days per arcsec^2 times H0
+  int n_img;
+  const double *img_xy, *dt_obs, *dt_sig;
+  // tile counts
+  int n_img_tiles, n_sky_tiles, n_tab_blocks;
+};
+
+// per-sample lensing parameters (FP32), written by the prep kernel
+struct LensP {
+  float xc, yc, cphi, sphi;
+  float q, t, pref, pad0;        // alpha' = pref * R^(1-t) * sum Omega_n
+  float g1, g2;                  // external shear
+  int nterms, valid;
+  float src_Ie, src_Rei, src_ninv, src_bn, src_x, src_y;
+  float ll_Ie[4], ll_Rei[4], ll_ninv[4], ll_bn[4], ll_qi2[4];
+  float rho[GLAD_MAX_TM];        // Omega_n = rho_n e^{2 i ph} Omega_{n-1}
+};
+
+// per-sample dynamics scalars (FP64)
+struct DynP {
+  double s2, c2, b;      // sin^2 i, cos^2 i, 1/(1-beta)
+  double xc, yc, cphi, sphi;
+};
+
+// ---------------------------------------------------------------------------
+// host-side context
+// ---------------------------------------------------------------------------
+struct SysHost {
+  glad_system_desc d;      // scalars (pointer fields are not kept)
+  int n_mass_tot, n_light, n_ent, n_sub, npix;
+  std::vector<void *> allocs;
+};
+
+struct WsDev {
+  LensP *lp;
+  DynP *dp;
+  double *nu0, *c0, *Cj, *e2;  // [B*max_light] / [B*max_mass_tot]
+  float *I0f;                  // [B*max_light]
+  float4 *tab;                 // [B*max_ent]
+  float *img;                  // [B*max_pix]
+  double *binacc;              // [B*max_bins*2]
+  double *terms;               // [B*3]
+  int *status;                 // [B]
+};
+
+struct Workspace {
+  int B = 0;
+  WsDev d{};
+  std::vector<void *> allocs;
+};
+
+struct GradWs;  // gradient workspace (k_grad.cu)
+
+struct glad_ctx {
+  int n_sys = 0;
+  std::vector<SysHost> sys;
+  SysDev *d_sys = nullptr;       // [n_sys]
+  std::vector<SysDev> h_sysdev;  // host copy of the device descriptors
+  int max_light = 0, max_mass_tot = 0, max_ent = 0, max_pix = 0, max_bins = 0, max_sub = 0;
+  int max_img_tiles = 0, max_sky_tiles = 0, max_tab_blocks = 0;
+  Workspace ws;
+  GradWs *gws = nullptr;
+  int *d_one_sys = nullptr;      // scratch sys id for single-sample calls
+  // kernel timing (glad_profile)
+  int prof = 0;
+  struct Rec {
+    int id;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> ev_pool;
+};
+
+// kernel ids for glad_kernel_times
+enum {
+  KID_PREP = 0, KID_TABLE, KID_IMAGE_CONV, KID_JAM, KID_KIN, KID_COMBINE,
+  KID_GRAD_LENS, KID_GRAD_JAM_FWD, KID_GRAD_JAM_ADJ, KID_GRAD_CHAIN, KID_N
+};
+
+// record an event pair around `call` when profiling is on
+cudaError_t prof_begin(glad_ctx *c, cudaStream_t st, cudaEvent_t *a);
+cudaError_t prof_end(glad_ctx *c, cudaStream_t st, int id, cudaEvent_t a);
+#define GLAD_PROF(c, st, id, call)               \
+  [&]() -> cudaError_t {                         \
+    cudaEvent_t _a = nullptr;                    \
+    cudaError_t _e = prof_begin((c), (st), &_a); \
+    if (_e != cudaSuccess) return _e;            \
+    _e = (call);                                 \
+    if (_e != cudaSuccess) return _e;            \
+    return prof_end((c), (st), (id), _a);        \
+  }()
+
+// ---------------------------------------------------------------------------
+// launchers (one per kernel file)
+// ---------------------------------------------------------------------------
+cudaError_t launch_prep(glad_ctx *c, const int *sys_id, const double *theta, int B,
+                        cudaStream_t st);
+cudaError_t launch_table(glad_ctx *c, const int *sys_id, int B, cudaStream_t st);
+cudaError_t launch_lens(glad_ctx *c, const int *sys_id, int B, float *image_out,
+                        cudaStream_t st);
+cudaError_t launch_jam(glad_ctx *c, const int *sys_id, int B, cudaStream_t st);
+cudaError_t launch_kin_finalize(glad_ctx *c, const int *sys_id, int B, float *vrms_out,
+                                cudaStream_t st);
+cudaError_t launch_combine(glad_ctx *c, int B, double *logL, int *status, double *terms,
+                           cudaStream_t st);
+void set_conv_smem_limit();
+
+// tile shapes (shared by launchers and the workspace sizing)
+#define JAM_THREADS 256
+#define JAM_PTS 4
+#define JAM_TILE (JAM_THREADS * JAM_PTS)
+#define JAM_CHUNK 512
+#define LENS_THREADS 256
+#define TAB_THREADS 256
+#define CONV_TX 32
+#define CONV_TY 8
+
+// ---------------------------------------------------------------------------
+// math helpers usable from host and device
+// ---------------------------------------------------------------------------
+#define LOG2E_D 1.4426950408889634
+#define SQRT2PI_D 2.5066282746310002
+#define PI_D 3.141592653589793
+
+__host__ __device__ inline double sersic_bn_d(double n) {
+  // Ciotti & Bertin (1999) asymptotic series, 4th order in 1/n
+  double i1 = 1.0 / n;
+  return 2.0 * n - 1.0 / 3.0 + i1 * (4.0 / 405.0 + i1 * (46.0 / 25515.0 +
+         i1 * (131.0 / 1148175.0 - i1 * (2194697.0 / 30690717750.0))));
+}

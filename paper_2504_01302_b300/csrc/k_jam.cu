@@ -1,0 +1,181 @@
+// Dynamics half of the likelihood.
+//  k_jam: Sigma v_los^2 at every sub-sample of the sky grid by the (tracer k, mass j,
+//    Gauss-Legendre node g) pair sum of the cylindrically aligned JAM solution,
+//      Sigma v^2(x', y') = sum_e (Q0_e + Q1_e x'^2) 2^(ax_e x'^2 + ay_e y'^2),
+//    with the table streamed through shared memory in chunks and FP32 partial
+//    sums flushed to FP64 per chunk; the tracer surface brightness (Eq. sb_mge_2D)
+//    at the same points; then both maps go straight through the binning-after-PSF
+//    operator W (bin sums of the PSF_kin-blurred maps, Eq. binned) into per-bin
+//    FP64 accumulators, so the maps are never stored.
+//  k_kin_finalize: v_rms,l = sqrt(num_l/den_l) (Eq. Vrms) and chi^2_dyn (Eq. chi2_dyn).
+//  k_combine: logL = -(chi2_pix + chi2_dyn + chi2_tmd)/2 (Eq. chi_general).
+#include "glad_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__global__ void __launch_bounds__(JAM_THREADS) k_jam(const SysDev *__restrict__ sysv,
+                                                     const int *__restrict__ sys_id, WsDev ws,
+                                                     int max_light, int max_ent, int max_bins) {
+  const int b = blockIdx.y;
+  if (ws.status[b] != GLAD_SAMPLE_OK) return;
+  const SysDev &S = sysv[sys_id[b]];
+  const int tile0 = blockIdx.x * JAM_TILE;
+  if (tile0 >= S.n_sub) return;
+  __shared__ float4 tab[2][JAM_CHUNK];
+  __shared__ float bnum[GLAD_MAX_BINS], bden[GLAD_MAX_BINS];
+  __shared__ float sI0[GLAD_MAX_LIGHT], scx[GLAD_MAX_LIGHT], scy[GLAD_MAX_LIGHT];
+  const int tid = threadIdx.x;
+  const DynP dp = ws.dp[b];
+  for (int l = tid; l < S.n_bins; l += JAM_THREADS) {
+    bnum[l] = 0.0f;
+    bden[l] = 0.0f;
+  }
+  for (int k = tid; k < S.n_light; k += JAM_THREADS) {
+    sI0[k] = ws.I0f[(size_t)b * max_light + k];
+    scx[k] = S.sb_cx[k];
+    scy[k] = S.sb_cy[k];
+  }
+  // sky points of this thread (strided so that neighbouring threads are neighbours)
+  float X[JAM_PTS], Y[JAM_PTS];
+  float acc[JAM_PTS];
+  double accd[JAM_PTS];
+  const float cphi = (float)dp.cphi, sphi = (float)dp.sphi;
+  const float xc = (float)dp.xc, yc = (float)dp.yc;
+#pragma unroll
+  for (int i = 0; i < JAM_PTS; ++i) {
+    const int s = tile0 + tid + i * JAM_THREADS;
+    const int si = s < S.n_sub ? s : 0;
+    const int I = si / S.nsx, J = si - I * S.nsx;
+    const float x = (J - 0.5f * (S.nsx - 1)) * S.dsub - xc;
+    const float y = (I - 0.5f * (S.nsy - 1)) * S.dsub - yc;
+    const float xp = cphi * x + sphi * y, yp = -sphi * x + cphi * y;
+    X[i] = xp * xp;
+    Y[i] = yp * yp;
+    acc[i] = 0.0f;
+    accd[i] = 0.0;
+  }
+  const float4 *gt = ws.tab + (size_t)b * max_ent;
+  const int n_ent = S.n_ent;
+  const int n_chunks = (n_ent + JAM_CHUNK - 1) / JAM_CHUNK;
+  // prologue: chunk 0
+  for (int e = tid; e < JAM_CHUNK; e += JAM_THREADS)
+    tab[0][e] = e < n_ent ? gt[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  for (int ch = 0; ch < n_chunks; ++ch) {
+    const int cur = ch & 1;
+    // stage the next chunk into the other buffer while this one is consumed
+    if (ch + 1 < n_chunks) {
+      const int base = (ch + 1) * JAM_CHUNK;
+      for (int e = tid; e < JAM_CHUNK; e += JAM_THREADS)
+        tab[cur ^ 1][e] = base + e < n_ent ? gt[base + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float4 *t = tab[cur];
+#pragma unroll 4
+    for (int e = 0; e < JAM_CHUNK; ++e) {
+      const float4 c = t[e];
+#pragma unroll
+      for (int i = 0; i < JAM_PTS; ++i) {
+        const float E = ex2(fmaf(c.y, Y[i], c.x * X[i]));
+        acc[i] = fmaf(fmaf(c.w, X[i], c.z), E, acc[i]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < JAM_PTS; ++i) {
+      accd[i] += (double)acc[i];
+      acc[i] = 0.0f;
+    }
+    __syncthreads();
+  }
+  // tracer surface brightness and the binning-after-PSF scatter
+#pragma unroll
+  for (int i = 0; i < JAM_PTS; ++i) {
+    const int s = tile0 + tid + i * JAM_THREADS;
+    if (s >= S.n_sub) continue;
+    float sb = 0.0f;
+    for (int k = 0; k < S.n_light; ++k) sb = fmaf(sI0[k], ex2(-fmaf(scy[k], Y[i], scx[k] * X[i])), sb);
+    const float v = (float)accd[i];
+    for (int e = S.w_off[s]; e < S.w_off[s + 1]; ++e) {
+      const int l = S.w_bin[e];
+      const float w = S.w_val[e];
+      atomicAdd(&bnum[l], w * v);
+      atomicAdd(&bden[l], w * sb);
+    }
+  }
+  __syncthreads();
+  double *acc_g = ws.binacc + (size_t)b * max_bins * 2;
+  for (int l = tid; l < S.n_bins; l += JAM_THREADS) {
+    if (bnum[l] != 0.0f) atomicAdd(&acc_g[2 * l], (double)bnum[l]);
+    if (bden[l] != 0.0f) atomicAdd(&acc_g[2 * l + 1], (double)bden[l]);
+  }
+}
+
+__global__ void k_kin_finalize(const SysDev *__restrict__ sysv, const int *__restrict__ sys_id,
+                               WsDev ws, int max_bins, float *vrms_out) {
+  const int b = blockIdx.x;
+  if (ws.status[b] != GLAD_SAMPLE_OK) return;
+  const SysDev &S = sysv[sys_id[b]];
+  const double *acc = ws.binacc + (size_t)b * max_bins * 2;
+  double chi = 0.0;
+  for (int l = threadIdx.x; l < S.n_bins; l += blockDim.x) {
+    const double v = sqrt(acc[2 * l] / acc[2 * l + 1]);
+    if (vrms_out) vrms_out[l] = (float)v;
+    const double r = ((double)S.v_obs[l] - v) / (double)S.v_sig[l];
+    chi += r * r;
+  }
+  for (int off = 16; off > 0; off >>= 1) chi += __shfl_down_sync(0xffffffffu, chi, off);
+  __shared__ double red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = chi;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += red[w];
+    ws.terms[3 * (size_t)b + 1] = t;
+  }
+}
+
+__global__ void k_combine(WsDev ws, int B, double *logL, int *status, double *terms) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  int st = ws.status[b];
+  const double t0 = ws.terms[3 * b], t1 = ws.terms[3 * b + 1], t2 = ws.terms[3 * b + 2];
+  double L = -INFINITY;
+  if (st == GLAD_SAMPLE_OK) {
+    const double s = t0 + t1 + t2;
+    if (isfinite(s)) L = -0.5 * s;
+    else st = GLAD_SAMPLE_NONFINITE;
+  }
+  logL[b] = L;
+  status[b] = st;
+  if (terms) {
+    terms[3 * b] = st == GLAD_SAMPLE_OK ? t0 : NAN;
+    terms[3 * b + 1] = st == GLAD_SAMPLE_OK ? t1 : NAN;
+    terms[3 * b + 2] = st == GLAD_SAMPLE_OK ? t2 : NAN;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_jam(glad_ctx *c, const int *sys_id, int B, cudaStream_t st) {
+  dim3 grid(c->max_sky_tiles, B);
+  k_jam<<<grid, JAM_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_light, c->max_ent,
+                                      c->max_bins);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kin_finalize(glad_ctx *c, const int *sys_id, int B, float *vrms_out,
+                                cudaStream_t st) {
+  k_kin_finalize<<<B, 256, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_bins, vrms_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine(glad_ctx *c, int B, double *logL, int *status, double *terms,
+                           cudaStream_t st) {
+  k_combine<<<(B + 127) / 128, 128, 0, st>>>(c->ws.d, B, logL, status, terms);
+  return cudaGetLastError();
+}

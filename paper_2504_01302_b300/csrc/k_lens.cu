@@ -1,0 +1,174 @@
+// Lensing half of the likelihood (FP32 bulk, FP64 chi^2):
+//  k_image: one thread per image pixel; each of its ss x ss sub-pixels is ray-shot
+//    through EPL + shear + SIS (lens equation beta = theta - alpha, Sect. 3.1.1),
+//    the Sersic source is evaluated at beta and the lens-light Sersics at theta,
+//    and the average is stored.
+//  k_conv: PSF blurring (discrete convolution, zero outside the image) of a 32x8
+//    output tile staged with its halo in shared memory, and the masked pixel chi^2
+//    (Eq. chi2 of lens_light) reduced in FP64 per sample.
+#include "glad_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ float sersic_f(float R2_scaled, float Ie, float ninv, float bn) {
+  // Ie * exp(-bn * (R^(1/n) - 1)) with R2_scaled = (R/Re)^2
+  const float w = exp2f(0.5f * ninv * log2f(R2_scaled));
+  return Ie * expf(-bn * (w - 1.0f));
+}
+
+__global__ void __launch_bounds__(LENS_THREADS) k_image(const SysDev *__restrict__ sysv,
+                                                        const int *__restrict__ sys_id, WsDev ws,
+                                                        int max_pix) {
+  const int b = blockIdx.y;
+  if (ws.status[b] != GLAD_SAMPLE_OK) return;
+  const SysDev &S = sysv[sys_id[b]];
+  const int p = blockIdx.x * LENS_THREADS + threadIdx.x;
+  __shared__ LensP L;
+  {
+    const int *src = reinterpret_cast<const int *>(&ws.lp[b]);
+    int *dst = reinterpret_cast<int *>(&L);
+    for (int i = threadIdx.x; i < (int)(sizeof(LensP) / 4); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  if (p >= S.npix) return;
+  const int i = p / S.nx, j = p - i * S.nx;
+  const int ss = S.ss;
+  const float pix = S.pix;
+  const float x0 = (j - 0.5f * (S.nx - 1)) * pix;
+  const float y0 = (i - 0.5f * (S.ny - 1)) * pix;
+  const float q = L.q, omt = 1.0f - L.t;
+  float acc = 0.0f;
+  for (int my = 0; my < ss; ++my) {
+    const float y = y0 + ((my + 0.5f) / ss - 0.5f) * pix;
+    for (int mx = 0; mx < ss; ++mx) {
+      const float x = x0 + ((mx + 0.5f) / ss - 0.5f) * pix;
+      const float dx = x - L.xc, dy = y - L.yc;
+      const float xp = L.cphi * dx + L.sphi * dy, yp = -L.sphi * dx + L.cphi * dy;
+      // EPL (Tessore & Metcalf series)
+      const float R = sqrtf(q * q * xp * xp + yp * yp);
+      const float iR = 1.0f / R;
+      const float wr = q * xp * iR, wi = yp * iR;
+      const float w2r = wr * wr - wi * wi, w2i = 2.0f * wr * wi;
+      float omr = wr, omi = wi, Sr = wr, Si = wi;
+      for (int n = 0; n < L.nterms; ++n) {
+        const float rr = L.rho[n];
+        const float nr = rr * (w2r * omr - w2i * omi);
+        const float ni = rr * (w2r * omi + w2i * omr);
+        omr = nr;
+        omi = ni;
+        Sr += omr;
+        Si += omi;
+      }
+      const float amp = L.pref * exp2f(omt * log2f(R));
+      const float apx = amp * Sr, apy = amp * Si;
+      float ax = L.cphi * apx - L.sphi * apy;
+      float ay = L.sphi * apx + L.cphi * apy;
+      ax += L.g1 * dx + L.g2 * dy;
+      ay += L.g2 * dx - L.g1 * dy;
+      for (int k = 0; k < S.n_sis; ++k) {
+        const float te = (float)S.sis[3 * k];
+        const float sx = x - (float)S.sis[3 * k + 1], sy = y - (float)S.sis[3 * k + 2];
+        const float ir = rsqrtf(sx * sx + sy * sy);
+        ax += te * sx * ir;
+        ay += te * sy * ir;
+      }
+      // source at beta
+      const float bx = x - ax - L.src_x, by = y - ay - L.src_y;
+      const float xs = S.src_cphi * bx + S.src_sphi * by, ys = -S.src_sphi * bx + S.src_cphi * by;
+      const float Rs2 = (xs * xs + ys * ys / (S.src_q * S.src_q)) * (L.src_Rei * L.src_Rei);
+      float v = sersic_f(Rs2, L.src_Ie, L.src_ninv, L.src_bn);
+      // lens light (same centre and PA as the mass)
+      for (int c = 0; c < S.n_lcomp; ++c) {
+        const float R2 = (xp * xp + yp * yp * L.ll_qi2[c]) * (L.ll_Rei[c] * L.ll_Rei[c]);
+        v += sersic_f(R2, L.ll_Ie[c], L.ll_ninv[c], L.ll_bn[c]);
+      }
+      acc += v;
+    }
+  }
+  ws.img[(size_t)b * max_pix + p] = acc / (float)(ss * ss);
+}
+
+__global__ void __launch_bounds__(CONV_TX *CONV_TY) k_conv(const SysDev *__restrict__ sysv,
+                                                           const int *__restrict__ sys_id, WsDev ws,
+                                                           int max_pix, float *image_out) {
+  const int b = blockIdx.y;
+  if (ws.status[b] != GLAD_SAMPLE_OK) return;
+  const SysDev &S = sysv[sys_id[b]];
+  const int ntx = (S.nx + CONV_TX - 1) / CONV_TX;
+  const int nty = (S.ny + CONV_TY - 1) / CONV_TY;
+  if ((int)blockIdx.x >= ntx * nty) return;
+  const int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;
+  const int K = S.psf_k, h = (K - 1) / 2;
+  const int W = CONV_TX + 2 * h, H = CONV_TY + 2 * h;
+  extern __shared__ float sm[];
+  float *tile = sm;            // [H*W]
+  float *psf = sm + H * W;     // [K*K]
+  const int tid = threadIdx.y * CONV_TX + threadIdx.x;
+  const int i0 = ty * CONV_TY - h, j0 = tx * CONV_TX - h;
+  const float *img = ws.img + (size_t)b * max_pix;
+  for (int e = tid; e < H * W; e += CONV_TX * CONV_TY) {
+    const int li = e / W, lj = e - li * W;
+    const int gi = i0 + li, gj = j0 + lj;
+    tile[e] = (gi >= 0 && gi < S.ny && gj >= 0 && gj < S.nx) ? img[gi * S.nx + gj] : 0.0f;
+  }
+  for (int e = tid; e < K * K; e += CONV_TX * CONV_TY) psf[e] = S.psf[e];
+  __syncthreads();
+  const int oi = ty * CONV_TY + threadIdx.y, oj = tx * CONV_TX + threadIdx.x;
+  double chi = 0.0;
+  if (oi < S.ny && oj < S.nx) {
+    // m[i,j] = sum_{a,c} P[a,c] img[i-(a-h), j-(c-h)]; tile row of image row r is r - i0
+    double m = 0.0;
+    for (int a = 0; a < K; ++a) {
+      const float *trow = tile + (threadIdx.y + 2 * h - a) * W + threadIdx.x + 2 * h;
+      const float *prow = psf + a * K;
+      float rs = 0.0f;
+      for (int c = 0; c < K; ++c) rs = fmaf(prow[c], trow[-c], rs);
+      m += (double)rs;
+    }
+    const int o = oi * S.nx + oj;
+    if (image_out) {
+      image_out[o] = (float)m;
+    } else {
+      const double r = ((double)S.data[o] - m) * (double)S.wgt[o];
+      chi = r * r;
+    }
+  }
+  if (image_out) return;
+  // block reduction of chi^2 in FP64
+  for (int off = 16; off > 0; off >>= 1) chi += __shfl_down_sync(0xffffffffu, chi, off);
+  __shared__ double red[CONV_TX * CONV_TY / 32];
+  if ((tid & 31) == 0) red[tid >> 5] = chi;
+  __syncthreads();
+  if (tid < 32) {
+    double v = tid < CONV_TX * CONV_TY / 32 ? red[tid] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (tid == 0 && v != 0.0) atomicAdd(&ws.terms[3 * (size_t)b], v);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_lens(glad_ctx *c, const int *sys_id, int B, float *image_out, cudaStream_t st) {
+  dim3 g1(c->max_img_tiles, B);
+  k_image<<<g1, LENS_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_pix);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int max_conv_tiles = 0, max_k = 1;
+  for (auto &s : c->sys) {
+    const int t = ((s.d.nx + CONV_TX - 1) / CONV_TX) * ((s.d.ny + CONV_TY - 1) / CONV_TY);
+    if (t > max_conv_tiles) max_conv_tiles = t;
+    if (s.d.psf_k > max_k) max_k = s.d.psf_k;
+  }
+  const int h = (max_k - 1) / 2;
+  const size_t smem = sizeof(float) * ((CONV_TX + 2 * h) * (CONV_TY + 2 * h) + max_k * max_k);
+  dim3 g2(max_conv_tiles, B);
+  k_conv<<<g2, dim3(CONV_TX, CONV_TY), smem, st>>>(c->d_sys, sys_id, c->ws.d, c->max_pix,
+                                                   image_out);
+  return cudaGetLastError();
+}
+
+void set_conv_smem_limit() {
+  const int h = (GLAD_MAX_PSF - 1) / 2;
+  const int smem = sizeof(float) * ((CONV_TX + 2 * h) * (CONV_TY + 2 * h) + GLAD_MAX_PSF * GLAD_MAX_PSF);
+  cudaFuncSetAttribute(k_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}

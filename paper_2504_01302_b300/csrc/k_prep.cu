@@ -1,0 +1,314 @@
+// Per-sample preparation (one CTA per sample, FP64):
+//  * domain checks of the parameter vector;
+//  * 1-D MGE of each lens-light Sersic and of the App. C convergence by the Euler
+//    inversion of Sect. 3.2:  A_n = w_n dln(sigma) / sqrt(2 pi) * sum_m eta_m Re F(sigma_n chi_m);
+//  * black-hole Gaussian, M_BH = f_BH * Upsilon * L_tot * L_scale;
+//  * deprojection (App. A): q = sqrt(q'^2 - cos^2 i)/sin i, needs cos^2 i < q'^2,
+//    and a positivity check of both densities at probe radii (Sect. 3.3);
+//  * per-Gaussian JAM inputs nu_k, 1/(2 s_k^2 q_k^2), C_j = 4 pi G rho_j q_j s_j^2, e_j^2;
+//  * FP32 lensing parameter block (EPL series coefficients, shear, light);
+//  * time delays (Eqs. fermat potential, time delay between multiple images, chi2_tmd)
+//    with the magnification-weighted source estimate of Sect. 3.1.1.
+// A second kernel expands the (tracer k, mass j, node g) JAM coefficient table.
+#include "glad_internal.cuh"
+#include "lensmath.cuh"
+
+namespace {
+
+struct cplx {
+  double r, i;
+};
+__device__ inline cplx cmul(cplx a, cplx b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
+__device__ inline cplx cexp_(cplx a) {
+  double s, c;
+  sincos(a.i, &s, &c);
+  const double e = exp(a.r);
+  return {e * c, e * s};
+}
+__device__ inline cplx clog_(cplx a) { return {log(hypot(a.r, a.i)), atan2(a.i, a.r)}; }
+
+// Sersic profile at complex radius z
+__device__ inline double sersic_re(cplx z, double Ie, double Re, double n, double bn) {
+  cplx l = clog_({z.r / Re, z.i / Re});
+  cplx w = cexp_({l.r / n, l.i / n});
+  cplx F = cexp_({-bn * (w.r - 1.0), -bn * w.i});
+  return Ie * F.r;
+}
+
+// App. C convergence at complex radius z: coef * (z^2 + rs^2)^(-(g-1)/2)
+__device__ inline double epl_kappa_re(cplx z, double coef, double g, double rs2) {
+  cplx z2 = cmul(z, z);
+  z2.r += rs2;
+  cplx l = clog_(z2);
+  const double e = -0.5 * (g - 1.0);
+  cplx F = cexp_({e * l.r, e * l.i});
+  return coef * F.r;
+}
+
+__device__ inline int domain_ok(const double *th) {
+  bool ok = true;
+  for (int i = 0; i < GLAD_NTHETA; ++i) ok = ok && isfinite(th[i]);
+  const double g = th[1], q = th[2], inc = th[15];
+  ok = ok && th[0] > 0.0 && g > 1.0 && g < 3.0 && q > 0.0 && q <= 1.0 && th[9] > 0.0 &&
+       th[10] > 0.0 && th[14] > 0.0 && th[13] > 0.0 && inc > 0.0 &&
+       inc <= 1.5707963267948966 + 1e-12 && th[16] < 1.0 && th[17] >= 0.0 && th[18] >= 0.0 &&
+       th[19] > 0.0;
+  return ok ? 1 : 0;
+}
+
+__global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
+                                              const int *__restrict__ sys_id,
+                                              const double *__restrict__ theta, WsDev ws,
+                                              int max_light, int max_mass) {
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x;
+  const SysDev &S = sysv[sys_id[b]];
+  const double *th = theta + (size_t)GLAD_NTHETA * b;
+  __shared__ double sh_A[GLAD_MAX_LIGHT + GLAD_MAX_MASS + 1];
+  __shared__ double sh_rho[GLAD_MAX_LIGHT + GLAD_MAX_MASS + 1];
+  __shared__ double sh_q[GLAD_MAX_LIGHT + GLAD_MAX_MASS + 1];
+  __shared__ int sh_flag;
+
+  const int ok = domain_ok(th);
+  if (!ok) {
+    if (tid == 0) {
+      ws.status[b] = GLAD_SAMPLE_DOMAIN;
+      ws.lp[b].valid = 0;
+    }
+    return;
+  }
+  const double tE = th[0], g = th[1], q = th[2], inc = th[15];
+  double si, ci;
+  sincos(inc, &si, &ci);
+  const double s2 = si * si, c2 = ci * ci;
+  const int nL = S.n_light, nM = S.n_mass, nMt = S.n_mass_tot;
+  const int P2 = 2 * S.mge_P + 1;
+
+  // ---- 1-D MGE (Euler inversion), FP64
+  for (int k = tid; k < nL + nM; k += blockDim.x) {
+    double f = 0.0;
+    if (k < nL) {
+      const int c = S.lcomp_of[k];
+      const double Ie = c == 0 ? th[13] : S.lcomp[4 * c];
+      const double Re = c == 0 ? th[14] : S.lcomp[4 * c + 1];
+      const double n = S.lcomp[4 * c + 2];
+      const double bn = sersic_bn_d(n);
+      const double sg = S.sig_light[k];
+      for (int m = 0; m < P2; ++m) {
+        const double2 ch = S.chi[m];
+        f += S.eta[m] * sersic_re({sg * ch.x, sg * ch.y}, Ie, Re, n, bn);
+      }
+      sh_A[k] = S.mw_light[k] * f;
+      sh_q[k] = S.qp_light[k];
+    } else {
+      const int j = k - nL;
+      // (3-g)/2 b^(g-1) with b = (2/(1+q))^(1/(g-1)) theta_E
+      const double coef = (3.0 - g) / (1.0 + q) * pow(tE, g - 1.0);
+      const double sg = S.sig_mass[j];
+      for (int m = 0; m < P2; ++m) {
+        const double2 ch = S.chi[m];
+        f += S.eta[m] * epl_kappa_re({sg * ch.x, sg * ch.y}, coef, g, S.r_soft * S.r_soft);
+      }
+      sh_A[k] = S.mw_mass[j] * f;
+      sh_q[k] = q;
+    }
+  }
+  if (tid == 0) sh_flag = 0;
+  __syncthreads();
+  if (tid == 0) {
+    double L = 0.0;
+    for (int k = 0; k < nL; ++k) L += 2.0 * PI_D * sh_A[k] * S.sig_light[k] * S.sig_light[k] * sh_q[k];
+    if (S.has_bh) {
+      const double mbh = th[18] * th[17] * L * S.L_scale;
+      sh_A[nL + nM] = mbh / (2.0 * PI_D * S.bh_sigma * S.bh_sigma);
+      sh_q[nL + nM] = 1.0;
+    }
+    // deprojection needs cos^2 i < q'^2 for every Gaussian (App. A)
+    double qmin = q;
+    for (int k = 0; k < nL; ++k) qmin = fmin(qmin, sh_q[k]);
+    if (c2 >= qmin * qmin) sh_flag = GLAD_SAMPLE_DEPROJ;
+  }
+  __syncthreads();
+  if (sh_flag) {
+    if (tid == 0) {
+      ws.status[b] = sh_flag;
+      ws.lp[b].valid = 0;
+    }
+    return;
+  }
+  const int nG = nL + nMt;
+  // ---- deprojection; densities rho0 (tracer nu0 and mass rho0) and intrinsic q
+  for (int k = tid; k < nG; k += blockDim.x) {
+    const double sg = k < nL ? S.sig_light[k] : S.sig_mass[k - nL];
+    const double qp = sh_q[k];
+    const double qi = sqrt(qp * qp - c2) / si;
+    sh_rho[k] = qp * sh_A[k] / (SQRT2PI_D * sg * qi);
+    const size_t bl = (size_t)b * max_light, bm = (size_t)b * max_mass;
+    if (k < nL) {
+      ws.nu0[bl + k] = sh_rho[k];
+      ws.c0[bl + k] = 1.0 / (2.0 * sg * sg * qi * qi);
+      ws.I0f[bl + k] = (float)sh_A[k];
+    } else {
+      const int j = k - nL;
+      ws.Cj[bm + j] = 2.0 * SQRT2PI_D * S.v2unit * qp * sh_A[k] * sg;
+      ws.e2[bm + j] = 1.0 - qi * qi;
+    }
+  }
+  __syncthreads();
+  // ---- positivity at probe radii: equatorial R = sigma_n and on the axis z = sigma_n
+  for (int k = tid; k < nG; k += blockDim.x) {
+    const bool light = k < nL;
+    const double s = light ? S.sig_light[k] : S.sig_mass[k - nL];
+    const int lo = light ? 0 : nL, hi = light ? nL : nG;
+    double eq = 0.0, ax = 0.0;
+    for (int m = lo; m < hi; ++m) {
+      const double sg = m < nL ? S.sig_light[m] : S.sig_mass[m - nL];
+      const double qp = sh_q[m];
+      const double qi2 = (qp * qp - c2) / s2;
+      eq += sh_rho[m] * exp(-s * s / (2.0 * sg * sg));
+      ax += sh_rho[m] * exp(-s * s / (2.0 * sg * sg * qi2));
+    }
+    if (!(eq > 0.0) || !(ax > 0.0)) atomicOr(&sh_flag, 1);
+  }
+  __syncthreads();
+  if (sh_flag) {
+    if (tid == 0) {
+      ws.status[b] = GLAD_SAMPLE_NEGDENS;
+      ws.lp[b].valid = 0;
+    }
+    return;
+  }
+
+  if (tid == 0) {
+    ws.status[b] = GLAD_SAMPLE_OK;
+    // ---- dynamics scalars
+    DynP dp;
+    dp.s2 = s2;
+    dp.c2 = c2;
+    dp.b = 1.0 / (1.0 - th[16]);
+    dp.xc = th[4];
+    dp.yc = th[5];
+    sincos(th[3], &dp.sphi, &dp.cphi);
+    ws.dp[b] = dp;
+    // ---- FP32 lensing block
+    LensP &L = ws.lp[b];
+    const double t = g - 1.0;
+    const double bb = pow(2.0 / (1.0 + q), 1.0 / t) * tE;
+    const double bt = q * bb;
+    const double f = (1.0 - q) / (1.0 + q);
+    int nt = 0;
+    if (f > 0.0) nt = (int)ceil(log(1e-9) / log(f));
+    if (nt > GLAD_MAX_TM) nt = GLAD_MAX_TM;
+    L.xc = (float)th[4];
+    L.yc = (float)th[5];
+    L.cphi = (float)dp.cphi;
+    L.sphi = (float)dp.sphi;
+    L.q = (float)q;
+    L.t = (float)t;
+    L.pref = (float)(2.0 * bt / (1.0 + q) * pow(bt, t - 1.0));
+    L.nterms = nt;
+    for (int n = 1; n <= nt; ++n)
+      L.rho[n - 1] = (float)(-f * (2.0 * n - (2.0 - t)) / (2.0 * n + (2.0 - t)));
+    double s2p, c2p;
+    sincos(2.0 * th[7], &s2p, &c2p);
+    L.g1 = (float)(th[6] * c2p);
+    L.g2 = (float)(th[6] * s2p);
+    L.src_Ie = (float)th[8];
+    L.src_Rei = (float)(1.0 / th[9]);
+    L.src_ninv = (float)(1.0 / th[10]);
+    L.src_bn = (float)sersic_bn_d(th[10]);
+    L.src_x = (float)th[11];
+    L.src_y = (float)th[12];
+    for (int c = 0; c < S.n_lcomp && c < 4; ++c) {
+      const double Ie = c == 0 ? th[13] : S.lcomp[4 * c];
+      const double Re = c == 0 ? th[14] : S.lcomp[4 * c + 1];
+      const double n = S.lcomp[4 * c + 2], ql = S.lcomp[4 * c + 3];
+      L.ll_Ie[c] = (float)Ie;
+      L.ll_Rei[c] = (float)(1.0 / Re);
+      L.ll_ninv[c] = (float)(1.0 / n);
+      L.ll_bn[c] = (float)sersic_bn_d(n);
+      L.ll_qi2[c] = (float)(1.0 / (ql * ql));
+    }
+    L.valid = 1;
+    // ---- time delays (FP64)
+    const int ni = S.n_img;
+    double w[GLAD_MAX_IMG], bx[GLAD_MAX_IMG], by[GLAD_MAX_IMG], psi[GLAD_MAX_IMG];
+    double wsum = 0.0, bhx = 0.0, bhy = 0.0;
+    for (int i = 0; i < ni; ++i) {
+      const double x = S.img_xy[2 * i], y = S.img_xy[2 * i + 1];
+      LensEval e = lens_eval_d(x, y, th, S.sis, S.n_sis);
+      const double det = (1.0 - e.a11) * (1.0 - e.a22) - e.a12 * e.a21;
+      w[i] = 1.0 / fabs(det);
+      bx[i] = x - e.ax;
+      by[i] = y - e.ay;
+      psi[i] = e.psi;
+      wsum += w[i];
+      bhx += w[i] * bx[i];
+      bhy += w[i] * by[i];
+    }
+    bhx /= wsum;
+    bhy /= wsum;
+    const double kdt = S.dt_per_arcsec2_H0 / th[19];
+    double phi0 = 0.0, chi2 = 0.0;
+    for (int i = 0; i < ni; ++i) {
+      const double x = S.img_xy[2 * i], y = S.img_xy[2 * i + 1];
+      const double ph = 0.5 * ((x - bhx) * (x - bhx) + (y - bhy) * (y - bhy)) - psi[i];
+      if (i == 0) {
+        phi0 = ph;
+      } else {
+        const double dt = kdt * (ph - phi0);
+        const double r = (S.dt_obs[i - 1] - dt) / S.dt_sig[i - 1];
+        chi2 += r * r;
+      }
+    }
+    ws.terms[3 * (size_t)b + 2] = chi2;
+  }
+}
+
+// (k, j, g) coefficient table: exponent coefficients in log2 units and the two
+// prefactor terms of the pair form of the cylindrically aligned JAM integral.
+__global__ void __launch_bounds__(TAB_THREADS) k_table(const SysDev *__restrict__ sysv,
+                                                       const int *__restrict__ sys_id, WsDev ws,
+                                                       int max_light, int max_mass, int max_ent) {
+  const int b = blockIdx.y;
+  if (ws.status[b] != GLAD_SAMPLE_OK) return;
+  const SysDev &S = sysv[sys_id[b]];
+  const int e = blockIdx.x * TAB_THREADS + threadIdx.x;
+  if (e >= S.n_ent) return;
+  const int kj = e / S.n_gl;
+  const int j = kj % S.n_mass_tot;
+  const int k = kj / S.n_mass_tot;
+  const DynP dp = ws.dp[b];
+  const double u = S.gl_u[e], wu = S.gl_wu[e];
+  const double sj = S.sig_mass[j], sk = S.sig_light[k];
+  const double e2 = ws.e2[(size_t)b * max_mass + j];
+  const double a = u * u / (2.0 * sj * sj);
+  const double h = 1.0 - e2 * u * u;
+  const double p = 1.0 / (2.0 * sk * sk) + a;
+  const double c = ws.c0[(size_t)b * max_light + k] + a / h;
+  const double al = p * dp.s2 + c * dp.c2;
+  const double sh = sqrt(h);
+  const double A = a / (h * sh * c);
+  const double P0 = A * (dp.b * dp.s2 + dp.c2);
+  const double P1 = dp.s2 * (2.0 * a / sh - 2.0 * p * dp.b * A);
+  const double T = ws.nu0[(size_t)b * max_light + k] * ws.Cj[(size_t)b * max_mass + j] * wu *
+                   sqrt(PI_D / al);
+  ws.tab[(size_t)b * max_ent + e] =
+      make_float4((float)(-p * LOG2E_D), (float)(-p * c / al * LOG2E_D), (float)(T * P0),
+                  (float)(T * P1));
+}
+
+}  // namespace
+
+cudaError_t launch_prep(glad_ctx *c, const int *sys_id, const double *theta, int B,
+                        cudaStream_t st) {
+  k_prep<<<B, 128, 0, st>>>(c->d_sys, sys_id, theta, c->ws.d, c->max_light, c->max_mass_tot);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_table(glad_ctx *c, const int *sys_id, int B, cudaStream_t st) {
+  dim3 grid(c->max_tab_blocks, B);
+  k_table<<<grid, TAB_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_light, c->max_mass_tot,
+                                        c->max_ent);
+  return cudaGetLastError();
+}
