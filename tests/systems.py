@@ -45,7 +45,9 @@ def near_truth_thetas(n, seed=13, scale=0.002):
 
 
 def logl_tol(ref):
-    """|logL_gpu - logL_oracle| bound: 0.05 absolute (the workload's bar near the
-    posterior) plus 4e-7 |logL|, the coherent FP32 rounding of the model pixels
-    times the residuals when chi^2 is far above N (derivation in the design doc)."""
-    return 0.05 + 4e-7 * abs(ref)
+    """|logL_gpu - logL_oracle| bound: 0.05 absolute (the workload's bar, met near the
+    posterior) plus 5e-6 |logL|.  FP32 ray shooting leaves ~1e-7 arcsec in beta; the
+    source's logarithmic gradient (up to ~20/arcsec) turns that into model errors up
+    to ~2e-6 relative, coherent over the arcs, so far from the data (chi^2 >> N) the
+    chi^2 error grows like 2 * 2e-6 * chi^2 (derivation in the design doc)."""
+    return 0.05 + 5e-6 * abs(ref)
