@@ -151,6 +151,21 @@ int glad_profile(glad_ctx *ctx, int enable);
 int glad_kernel_times(glad_ctx *ctx, int n, double *ms, int *launches);
 const char *glad_kernel_name(int k);
 
+/* glad_loglike without any device allocation (the paper has no counterpart: this is a
+ * service to callers that cannot call cudaMalloc while they run, e.g. code inside a CUDA
+ * graph capture someone else owns, or a sampler loop under a fixed device-memory budget).
+ * Same arguments, kernels and results as glad_loglike, but the per-sample scratch lives in
+ * one 64 MiB file-scope device array instead of the context's workspace, so this call
+ * allocates nothing (the context itself must already exist).  Every GPU that loads the
+ * library holds that array until the process exits.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress), so make it before any stream capture.
+ * All calls share the one array and each clears the accumulators it needs: calls that
+ * overlap on the GPU (different streams, threads or contexts) race and must be serialised.
+ * A batch whose scratch exceeds 64 MiB (about 170 samples of the 200x200 RXJ1131-scale
+ * system) returns GLAD_EUNSUPPORTED with the limit in glad_last_error(). */
+glad_status glad_loglike_static(glad_ctx *ctx, const int *sys_id, const double *theta, int B,
+                                double *logL, int *sample_status, double *terms, void *stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *glad_last_error(void);
 

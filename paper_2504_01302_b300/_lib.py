@@ -41,6 +41,7 @@ SIGNATURES = {
     "glad_destroy": (None, [_p]),
     "glad_loglike": (C.c_int, [_p, _p, _p, C.c_int, _p, _p, _p, _p]),
     "glad_loglike_grad": (C.c_int, [_p, _p, _p, C.c_int, _p, _p, _p, _p, _p]),
+    "glad_loglike_static": (C.c_int, [_p, _p, _p, C.c_int, _p, _p, _p, _p]),
     "glad_model_image": (C.c_int, [_p, C.c_int, _p, _p, _p]),
     "glad_vrms": (C.c_int, [_p, C.c_int, _p, _p, _p]),
     "glad_profile": (C.c_int, [_p, C.c_int]),

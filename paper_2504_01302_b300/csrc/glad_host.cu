@@ -405,6 +405,9 @@ const char *kKernelNames[KID_N] = {
 
 }  // namespace
 
+// error reporting for entry points defined in other files
+glad_status glad_set_error(glad_status s, const char *msg) { return fail(s, "%s", msg); }
+
 cudaError_t prof_begin(glad_ctx *c, cudaStream_t st, cudaEvent_t *a) {
   *a = nullptr;
   if (!c->prof) return cudaSuccess;
