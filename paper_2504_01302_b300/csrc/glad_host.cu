@@ -15,6 +15,9 @@ cudaError_t launch_grad(glad_ctx *c, const int *sys_id, const double *theta, int
                         cudaStream_t st);
 cudaError_t grad_ws_ensure(glad_ctx *c, int B);
 void grad_ws_free(glad_ctx *c);
+float *grad_resid_buffer(glad_ctx *c);
+cudaError_t launch_jam_fg(glad_ctx *c, const int *sys_id, int B, cudaStream_t st);
+void set_grad_smem_limit();
 
 namespace {
 
@@ -379,8 +382,10 @@ glad_status ws_ensure(glad_ctx *c, int B) {
   return GLAD_OK;
 }
 
+// Forward launch sequence.  With `grad`, k_conv also leaves the residual weights and the
+// JAM pass keeps the per-point derivatives that the adjoint kernels need.
 glad_status forward(glad_ctx *c, const int *sys_id, const double *theta, int B, cudaStream_t st,
-                    float *image_out, float *vrms_out) {
+                    float *image_out, float *vrms_out, bool grad = false) {
   glad_status s = ws_ensure(c, B);
   if (s != GLAD_OK) return s;
   cudaError_t e;
@@ -391,8 +396,12 @@ glad_status forward(glad_ctx *c, const int *sys_id, const double *theta, int B, 
   if (e == cudaSuccess && !image_out)
     e = GLAD_PROF(c, st, KID_TABLE, launch_table(c, sys_id, B, st));
   if (e == cudaSuccess && !vrms_out)
-    e = GLAD_PROF(c, st, KID_IMAGE_CONV, launch_lens(c, sys_id, B, image_out, st));
-  if (e == cudaSuccess && !image_out) e = GLAD_PROF(c, st, KID_JAM, launch_jam(c, sys_id, B, st));
+    e = GLAD_PROF(c, st, KID_IMAGE_CONV,
+                  launch_lens(c, sys_id, B, image_out, st, grad ? grad_resid_buffer(c) : nullptr));
+  if (e == cudaSuccess && !image_out) {
+    if (grad) e = GLAD_PROF(c, st, KID_GRAD_JAM_FWD, launch_jam_fg(c, sys_id, B, st));
+    else e = GLAD_PROF(c, st, KID_JAM, launch_jam(c, sys_id, B, st));
+  }
   if (e == cudaSuccess && !image_out)
     e = GLAD_PROF(c, st, KID_KIN, launch_kin_finalize(c, sys_id, B, vrms_out, st));
   if (e != cudaSuccess) return fail(GLAD_ECUDA, "launch failed: %s", cudaGetErrorString(e));
@@ -509,6 +518,7 @@ glad_status glad_create(const glad_system_desc *sys, int n_sys, glad_ctx **out) 
   for (int i = 0; i < n_sys; ++i) ids[i] = i;
   cudaMemcpy(c->d_one_sys, ids.data(), sizeof(int) * n_sys, cudaMemcpyHostToDevice);
   set_conv_smem_limit();
+  set_grad_smem_limit();
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     glad_destroy(c);
@@ -559,7 +569,7 @@ glad_status glad_loglike_grad(glad_ctx *c, const int *sys_id, const double *thet
   cudaStream_t st = (cudaStream_t)stream;
   if (grad_ws_ensure(c, B) != cudaSuccess)
     return fail(GLAD_ENOMEM, "gradient workspace for B=%d does not fit", B);
-  glad_status s = forward(c, sys_id, theta, B, st, nullptr, nullptr);
+  glad_status s = forward(c, sys_id, theta, B, st, nullptr, nullptr, true);
   if (s != GLAD_OK) return s;
   cudaError_t e = launch_grad(c, sys_id, theta, B, grad, st);
   if (e == cudaSuccess)

@@ -74,6 +74,11 @@ struct LensP {
   float src_Ie, src_Rei, src_ninv, src_bn, src_x, src_y;
   float ll_Ie[4], ll_Rei[4], ll_ninv[4], ll_bn[4], ll_qi2[4];
   float rho[GLAD_MAX_TM];        // Omega_n = rho_n e^{2 i ph} Omega_{n-1}
+  // derivatives used by the gradient kernels
+  float drho_t[GLAD_MAX_TM], drho_q[GLAD_MAX_TM];  // d rho_n / d t, d rho_n / d q
+  float pref_d[3];               // d pref / d (theta_E, t, q)
+  float gext, c2pe, s2pe;        // shear strength and cos/sin(2 phi_ext)
+  float src_bnp;                 // d b_n / d n of the source
 };
 
 // per-sample dynamics scalars (FP64)
@@ -157,7 +162,7 @@ cudaError_t launch_prep(glad_ctx *c, const int *sys_id, const double *theta, int
                         cudaStream_t st);
 cudaError_t launch_table(glad_ctx *c, const int *sys_id, int B, cudaStream_t st);
 cudaError_t launch_lens(glad_ctx *c, const int *sys_id, int B, float *image_out,
-                        cudaStream_t st);
+                        cudaStream_t st, float *resid_out = nullptr);
 cudaError_t launch_jam(glad_ctx *c, const int *sys_id, int B, cudaStream_t st);
 cudaError_t launch_kin_finalize(glad_ctx *c, const int *sys_id, int B, float *vrms_out,
                                 cudaStream_t st);

@@ -1,10 +1,817 @@
-// Gradient of the joint log-likelihood (adjoint kernels).
+// Gradient d logL / d theta (hand-written adjoint of the forward kernels).
+//
+// logL = -(chi2_pix + chi2_dyn + chi2_tmd)/2 (Eq. chi_general).  The adjoint runs:
+//  * lensing: k_conv leaves r_o = mask (d_o - m_o)/sigma_o^2 = d logL/d m_o; k_conv_adj
+//    correlates it with the PSF (the transpose of the blurring) into d logL / d img_p;
+//    k_image_grad propagates that through every sub-pixel with forward-mode duals over
+//    the 8 lens parameters (EPL series, shear) plus analytic Sersic partials for the
+//    source (I_e, R_e, n, centre) and lens light (I_e, R_e).
+//  * dynamics: k_jam_fg repeats the JAM pair sum while also keeping dV/dx'^2, dV/dy'^2
+//    per sky point; k_kin_adj turns the bin adjoints of chi2_dyn (v = sqrt(N/D)) into
+//    per-point weights g_N, g_D through the binning-after-PSF operator W and adds the
+//    point-coordinate terms (x_c, y_c, phi) and the tracer-amplitude adjoints;
+//    k_jam_adj (one thread per table entry, sky points streamed through shared memory)
+//    sums the adjoints of each entry (Q0, Q1, a_y); k_grad_chain carries them through the
+//    table formula, deprojection (App. A), BH mass and the 1-D MGE (Sect. 3.2) to theta,
+//    and adds the delay term by duals through the FP64 lens model.
+// The MGE and table quantities are recomputed here, never stored from the forward pass.
+#include "dual.cuh"
 #include "glad_internal.cuh"
+#include "lensmath.cuh"
 
+struct GradWs {
+  int B = 0;
+  float *resid = nullptr;    // [B*max_pix]  d logL / d m (blurred model)
+  float *gpix = nullptr;     // [B*max_pix]  d logL / d img (unblurred)
+  float4 *pt = nullptr;      // [B*max_sub]  V, dV/dX, dV/dY (X = x'^2, Y = y'^2)
+  float4 *adjpt = nullptr;   // [B*max_sub]  X, Y, X*Y, g_N
+  double *entadj = nullptr;  // [B*max_ent*3] d logL / d (Q0, Q1, a_y)
+  double *adjI0 = nullptr;   // [B*max_light] d logL / d I0_k (tracer amplitudes)
+  std::vector<void *> allocs;
+};
+
+namespace {
+
+constexpr float LN2F = 0.6931471805599453f;
+constexpr double LN2D = 0.6931471805599453;
+
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ void load_lensp(const LensP *src, LensP &dst) {
+  const int *s = reinterpret_cast<const int *>(src);
+  int *d = reinterpret_cast<int *>(&dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(LensP) / 4); i += blockDim.x) d[i] = s[i];
+}
+
+// ------------------------------------------------------------------ lensing adjoint
+
+// d logL / d img_p = sum_o r_o P(o - p): correlation of the residual weights with the PSF
+__global__ void __launch_bounds__(CONV_TX *CONV_TY) k_conv_adj(const SysDev *__restrict__ sysv,
+                                                               const int *__restrict__ sys_id,
+                                                               WsDev ws, GradWs g, int max_pix) {
+  const int b = blockIdx.y;
+  if (ws.status[b] != GLAD_SAMPLE_OK) return;
+  const SysDev &S = sysv[sys_id[b]];
+  const int ntx = (S.nx + CONV_TX - 1) / CONV_TX;
+  const int nty = (S.ny + CONV_TY - 1) / CONV_TY;
+  if ((int)blockIdx.x >= ntx * nty) return;
+  const int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;
+  const int K = S.psf_k, h = (K - 1) / 2;
+  const int W = CONV_TX + 2 * h, H = CONV_TY + 2 * h;
+  extern __shared__ float sm[];
+  float *tile = sm;
+  float *psf = sm + H * W;
+  const int tid = threadIdx.y * CONV_TX + threadIdx.x;
+  const int i0 = ty * CONV_TY - h, j0 = tx * CONV_TX - h;
+  const float *r = g.resid + (size_t)b * max_pix;
+  for (int e = tid; e < H * W; e += CONV_TX * CONV_TY) {
+    const int li = e / W, lj = e - li * W;
+    const int gi = i0 + li, gj = j0 + lj;
+    tile[e] = (gi >= 0 && gi < S.ny && gj >= 0 && gj < S.nx) ? r[gi * S.nx + gj] : 0.0f;
+  }
+  for (int e = tid; e < K * K; e += CONV_TX * CONV_TY) psf[e] = S.psf[e];
+  __syncthreads();
+  const int pi = ty * CONV_TY + threadIdx.y, pj = tx * CONV_TX + threadIdx.x;
+  if (pi >= S.ny || pj >= S.nx) return;
+  // o = p + (a - h, c - h); tile row of residual row rr is rr - i0
+  float acc = 0.0f;
+  for (int a = 0; a < K; ++a) {
+    const float *trow = tile + (threadIdx.y + a) * W + threadIdx.x;
+    const float *prow = psf + a * K;
+    for (int c = 0; c < K; ++c) acc = fmaf(prow[c], trow[c], acc);
+  }
+  g.gpix[(size_t)b * max_pix + pi * S.nx + pj] = acc;
+}
+
+typedef Dual<8, float> D8;  // tangents: theta_E, gamma', q, phi, x_c, y_c, gamma_ext, phi_ext
+
+// Sersic value and its partials: I = Ie exp(-bn (w - 1)), w = (R2)^(ninv/2), R2 = (R/Re)^2
+struct SersicD {
+  float I, dI_dR2, w;
+};
+__device__ __forceinline__ SersicD sersic_d(float R2, float Ie, float ninv, float bn) {
+  SersicD s;
+  s.w = exp2f(0.5f * ninv * log2f(R2));
+  s.I = Ie * expf(-bn * (s.w - 1.0f));
+  s.dI_dR2 = R2 > 1e-30f ? -s.I * bn * s.w * ninv * 0.5f / R2 : 0.0f;
+  return s;
+}
+
+#define NGL 15  // lensing parameters theta[0..14]
+
+__global__ void __launch_bounds__(LENS_THREADS) k_image_grad(const SysDev *__restrict__ sysv,
+                                                             const int *__restrict__ sys_id,
+                                                             WsDev ws, GradWs gw, int max_pix,
+                                                             double *grad) {
+  const int b = blockIdx.y;
+  if (ws.status[b] != GLAD_SAMPLE_OK) return;
+  const SysDev &S = sysv[sys_id[b]];
+  const int p = blockIdx.x * LENS_THREADS + threadIdx.x;
+  __shared__ LensP L;
+  __shared__ float red[LENS_THREADS / 32][NGL];
+  load_lensp(&ws.lp[b], L);
+  __syncthreads();
+  float acc[NGL];
+#pragma unroll
+  for (int i = 0; i < NGL; ++i) acc[i] = 0.0f;
+  if (p < S.npix) {
+    const int i = p / S.nx, j = p - i * S.nx;
+    const int ss = S.ss;
+    const float pix = S.pix;
+    const float wpix = gw.gpix[(size_t)b * max_pix + p] / (float)(ss * ss);
+    const float x0 = (j - 0.5f * (S.nx - 1)) * pix;
+    const float y0 = (i - 0.5f * (S.ny - 1)) * pix;
+    D8 cphi(L.cphi), sphi(L.sphi), q = D8::var(L.q, 2), t = D8::var(L.t, 1);
+    cphi.d[3] = -L.sphi;
+    sphi.d[3] = L.cphi;
+    D8 pref(L.pref);
+    pref.d[0] = L.pref_d[0];
+    pref.d[1] = L.pref_d[1];
+    pref.d[2] = L.pref_d[2];
+    D8 g1(L.g1), g2(L.g2);
+    g1.d[6] = L.c2pe;
+    g1.d[7] = -2.0f * L.gext * L.s2pe;
+    g2.d[6] = L.s2pe;
+    g2.d[7] = 2.0f * L.gext * L.c2pe;
+    for (int my = 0; my < ss; ++my) {
+      const float y = y0 + ((my + 0.5f) / ss - 0.5f) * pix;
+      for (int mx = 0; mx < ss; ++mx) {
+        const float x = x0 + ((mx + 0.5f) / ss - 0.5f) * pix;
+        D8 dx(x - L.xc), dy(y - L.yc);
+        dx.d[4] = -1.0f;
+        dy.d[5] = -1.0f;
+        const D8 xp = cphi * dx + sphi * dy, yp = cphi * dy - sphi * dx;
+        // EPL deflection, Tessore & Metcalf series, with tangents
+        const D8 R = dsqrt(q * q * xp * xp + yp * yp);
+        const D8 iR = 1.0f / R;
+        const D8 wr = q * xp * iR, wi = yp * iR;
+        const D8 w2r = wr * wr - wi * wi, w2i = 2.0f * wr * wi;
+        D8 omr = wr, omi = wi, Sr = wr, Si = wi;
+        for (int n = 0; n < L.nterms; ++n) {
+          D8 rr(L.rho[n]);
+          rr.d[1] = L.drho_t[n];
+          rr.d[2] = L.drho_q[n];
+          const D8 nr = rr * (w2r * omr - w2i * omi);
+          const D8 ni = rr * (w2r * omi + w2i * omr);
+          omr = nr;
+          omi = ni;
+          Sr = Sr + omr;
+          Si = Si + omi;
+        }
+        const D8 amp = pref * dexp2((1.0f - t) * dlog2(R));
+        const D8 apx = amp * Sr, apy = amp * Si;
+        D8 ax = cphi * apx - sphi * apy;
+        D8 ay = sphi * apx + cphi * apy;
+        ax = ax + g1 * dx + g2 * dy;
+        ay = ay + g2 * dx - g1 * dy;
+        for (int k = 0; k < S.n_sis; ++k) {
+          const float te = (float)S.sis[3 * k];
+          const float sx = x - (float)S.sis[3 * k + 1], sy = y - (float)S.sis[3 * k + 2];
+          const float ir = rsqrtf(sx * sx + sy * sy);
+          ax.v += te * sx * ir;
+          ay.v += te * sy * ir;
+        }
+        // source at beta: d beta / d theta_i = -d alpha / d theta_i (i < 8); centre: -1
+        const float bx = x - ax.v - L.src_x, by = y - ay.v - L.src_y;
+        const float cs = S.src_cphi, sn = S.src_sphi, iq2 = 1.0f / (S.src_q * S.src_q);
+        const float xs = cs * bx + sn * by, ys = -sn * bx + cs * by;
+        const float Re2i = L.src_Rei * L.src_Rei;
+        const float Rs2 = (xs * xs + ys * ys * iq2) * Re2i;
+        const SersicD sd = sersic_d(Rs2, L.src_Ie, L.src_ninv, L.src_bn);
+        const float dI_dbx = sd.dI_dR2 * Re2i * 2.0f * (xs * cs - ys * iq2 * sn);
+        const float dI_dby = sd.dI_dR2 * Re2i * 2.0f * (xs * sn + ys * iq2 * cs);
+        float gsub[NGL];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) gsub[k] = -(dI_dbx * ax.d[k] + dI_dby * ay.d[k]);
+        gsub[8] = sd.I / L.src_Ie;
+        gsub[9] = -sd.dI_dR2 * 2.0f * Rs2 / L.src_Rei * Re2i;  // dR2/dRe = -2 R2 / Re
+        {
+          // d/dn: bn(n) and w = (R/Re)^(1/n)
+          const float lnr = Rs2 > 1e-30f ? 0.5f * logf(Rs2) : 0.0f;
+          const float dw_dn = -sd.w * lnr * L.src_ninv * L.src_ninv;
+          gsub[10] = sd.I * (-L.src_bnp * (sd.w - 1.0f) - L.src_bn * dw_dn);
+        }
+        gsub[11] = -dI_dbx;
+        gsub[12] = -dI_dby;
+        gsub[13] = 0.0f;
+        gsub[14] = 0.0f;
+        // lens light: depends on phi, x_c, y_c through (x', y') and on I_e, R_e of component 0
+        for (int c = 0; c < S.n_lcomp; ++c) {
+          const float Re2 = L.ll_Rei[c] * L.ll_Rei[c];
+          const float R2 = (xp.v * xp.v + yp.v * yp.v * L.ll_qi2[c]) * Re2;
+          const SersicD ld = sersic_d(R2, L.ll_Ie[c], L.ll_ninv[c], L.ll_bn[c]);
+          const float dxp = ld.dI_dR2 * Re2 * 2.0f * xp.v;
+          const float dyp = ld.dI_dR2 * Re2 * 2.0f * yp.v * L.ll_qi2[c];
+#pragma unroll
+          for (int k = 3; k < 6; ++k) gsub[k] += dxp * xp.d[k] + dyp * yp.d[k];
+          if (c == 0) {
+            gsub[13] = ld.I / L.ll_Ie[0];
+            gsub[14] = -ld.dI_dR2 * 2.0f * R2 / L.ll_Rei[0] * Re2;
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < NGL; ++k) acc[k] = fmaf(wpix, gsub[k], acc[k]);
+      }
+    }
+  }
+  // block reduction, then one FP64 atomic per parameter per block
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NGL; ++k) {
+    float v = acc[k];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NGL) {
+    double s = 0.0;
+    for (int w = 0; w < LENS_THREADS / 32; ++w) s += (double)red[w][threadIdx.x];
+    atomicAdd(&grad[(size_t)b * GLAD_NTHETA + threadIdx.x], s);
+  }
+}
+
+// ------------------------------------------------------------------ dynamics adjoint
+
+// JAM pair sum with dV/dX and dV/dY per point (X = x'^2, Y = y'^2), plus the same bin
+// scatter as the forward kernel so that v_rms and chi2_dyn come out of this pass too.
+__global__ void __launch_bounds__(JAM_THREADS) k_jam_fg(const SysDev *__restrict__ sysv,
+                                                        const int *__restrict__ sys_id, WsDev ws,
+                                                        GradWs gw, int max_light, int max_ent,
+                                                        int max_bins, int max_sub) {
+  const int b = blockIdx.y;
+  if (ws.status[b] != GLAD_SAMPLE_OK) return;
+  const SysDev &S = sysv[sys_id[b]];
+  const int tile0 = blockIdx.x * JAM_TILE;
+  if (tile0 >= S.n_sub) return;
+  __shared__ float4 tab[2][JAM_CHUNK];
+  __shared__ float bnum[GLAD_MAX_BINS], bden[GLAD_MAX_BINS];
+  __shared__ float sI0[GLAD_MAX_LIGHT], scx[GLAD_MAX_LIGHT], scy[GLAD_MAX_LIGHT];
+  const int tid = threadIdx.x;
+  const DynP dp = ws.dp[b];
+  for (int l = tid; l < S.n_bins; l += JAM_THREADS) {
+    bnum[l] = 0.0f;
+    bden[l] = 0.0f;
+  }
+  for (int k = tid; k < S.n_light; k += JAM_THREADS) {
+    sI0[k] = ws.I0f[(size_t)b * max_light + k];
+    scx[k] = S.sb_cx[k];
+    scy[k] = S.sb_cy[k];
+  }
+  float X[JAM_PTS], Y[JAM_PTS];
+  float aV[JAM_PTS], a1[JAM_PTS], a2[JAM_PTS], a3[JAM_PTS];
+  double dV[JAM_PTS], d1[JAM_PTS], d2[JAM_PTS], d3[JAM_PTS];
+  const float cphi = (float)dp.cphi, sphi = (float)dp.sphi;
+  const float xc = (float)dp.xc, yc = (float)dp.yc;
+#pragma unroll
+  for (int i = 0; i < JAM_PTS; ++i) {
+    const int s = tile0 + tid + i * JAM_THREADS;
+    const int si = s < S.n_sub ? s : 0;
+    const int I = si / S.nsx, J = si - I * S.nsx;
+    const float x = (J - 0.5f * (S.nsx - 1)) * S.dsub - xc;
+    const float y = (I - 0.5f * (S.nsy - 1)) * S.dsub - yc;
+    const float xp = cphi * x + sphi * y, yp = -sphi * x + cphi * y;
+    X[i] = xp * xp;
+    Y[i] = yp * yp;
+    aV[i] = a1[i] = a2[i] = a3[i] = 0.0f;
+    dV[i] = d1[i] = d2[i] = d3[i] = 0.0;
+  }
+  const float4 *gt = ws.tab + (size_t)b * max_ent;
+  const int n_ent = S.n_ent;
+  const int n_chunks = (n_ent + JAM_CHUNK - 1) / JAM_CHUNK;
+  for (int e = tid; e < JAM_CHUNK; e += JAM_THREADS)
+    tab[0][e] = e < n_ent ? gt[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  for (int ch = 0; ch < n_chunks; ++ch) {
+    const int cur = ch & 1;
+    if (ch + 1 < n_chunks) {
+      const int base = (ch + 1) * JAM_CHUNK;
+      for (int e = tid; e < JAM_CHUNK; e += JAM_THREADS)
+        tab[cur ^ 1][e] = base + e < n_ent ? gt[base + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float4 *tt = tab[cur];
+#pragma unroll 2
+    for (int e = 0; e < JAM_CHUNK; ++e) {
+      const float4 c = tt[e];
+#pragma unroll
+      for (int i = 0; i < JAM_PTS; ++i) {
+        const float E = ex2(fmaf(c.y, Y[i], c.x * X[i]));
+        const float tv = fmaf(c.w, X[i], c.z) * E;
+        aV[i] += tv;
+        a1[i] = fmaf(c.w, E, a1[i]);
+        a2[i] = fmaf(c.x, tv, a2[i]);
+        a3[i] = fmaf(c.y, tv, a3[i]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < JAM_PTS; ++i) {
+      dV[i] += aV[i];
+      d1[i] += a1[i];
+      d2[i] += a2[i];
+      d3[i] += a3[i];
+      aV[i] = a1[i] = a2[i] = a3[i] = 0.0f;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < JAM_PTS; ++i) {
+    const int s = tile0 + tid + i * JAM_THREADS;
+    if (s >= S.n_sub) continue;
+    float sb = 0.0f;
+    for (int k = 0; k < S.n_light; ++k) sb = fmaf(sI0[k], ex2(-fmaf(scy[k], Y[i], scx[k] * X[i])), sb);
+    const float v = (float)dV[i];
+    // coefficients are in log2 units: d/dX 2^(ax X) = ln2 ax 2^(ax X)
+    gw.pt[(size_t)b * max_sub + s] =
+        make_float4(v, (float)(d1[i] + LN2D * d2[i]), (float)(LN2D * d3[i]), sb);
+    for (int e = S.w_off[s]; e < S.w_off[s + 1]; ++e) {
+      const int l = S.w_bin[e];
+      const float w = S.w_val[e];
+      atomicAdd(&bnum[l], w * v);
+      atomicAdd(&bden[l], w * sb);
+    }
+  }
+  __syncthreads();
+  double *acc_g = ws.binacc + (size_t)b * max_bins * 2;
+  for (int l = tid; l < S.n_bins; l += JAM_THREADS) {
+    if (bnum[l] != 0.0f) atomicAdd(&acc_g[2 * l], (double)bnum[l]);
+    if (bden[l] != 0.0f) atomicAdd(&acc_g[2 * l + 1], (double)bden[l]);
+  }
+}
+
+// Per sky point: g_N = sum_l W_l gN_l, g_D = sum_l W_l gD_l with gN_l = d logL/d N_l,
+// gD_l = d logL/d D_l of v_l = sqrt(N_l/D_l); coordinate and tracer-amplitude adjoints.
+__global__ void __launch_bounds__(JAM_THREADS) k_kin_adj(const SysDev *__restrict__ sysv,
+                                                         const int *__restrict__ sys_id, WsDev ws,
+                                                         GradWs gw, int max_light, int max_bins,
+                                                         int max_sub, double *grad) {
+  const int b = blockIdx.y;
+  if (ws.status[b] != GLAD_SAMPLE_OK) return;
+  const SysDev &S = sysv[sys_id[b]];
+  const int tile0 = blockIdx.x * JAM_TILE;
+  if (tile0 >= S.n_sub) return;
+  __shared__ float gN[GLAD_MAX_BINS], gD[GLAD_MAX_BINS];
+  __shared__ float sI0[GLAD_MAX_LIGHT], scx[GLAD_MAX_LIGHT], scy[GLAD_MAX_LIGHT];
+  __shared__ float aI0[GLAD_MAX_LIGHT];
+  __shared__ float red[JAM_THREADS / 32][3];
+  const int tid = threadIdx.x;
+  const double *acc = ws.binacc + (size_t)b * max_bins * 2;
+  for (int l = tid; l < S.n_bins; l += JAM_THREADS) {
+    const double N = acc[2 * l], D = acc[2 * l + 1];
+    const double v = sqrt(N / D);
+    const double sg = (double)S.v_sig[l];
+    const double dv = ((double)S.v_obs[l] - v) / (sg * sg);  // d logL / d v
+    gN[l] = (float)(dv / (2.0 * v * D));
+    gD[l] = (float)(-dv * v / (2.0 * D));
+  }
+  for (int k = tid; k < S.n_light; k += JAM_THREADS) {
+    sI0[k] = ws.I0f[(size_t)b * max_light + k];
+    scx[k] = S.sb_cx[k];
+    scy[k] = S.sb_cy[k];
+    aI0[k] = 0.0f;
+  }
+  __syncthreads();
+  const DynP dp = ws.dp[b];
+  const float cphi = (float)dp.cphi, sphi = (float)dp.sphi;
+  const float xc = (float)dp.xc, yc = (float)dp.yc;
+  float gphi = 0.0f, gxc = 0.0f, gyc = 0.0f;
+  for (int i = 0; i < JAM_PTS; ++i) {
+    const int s = tile0 + tid + i * JAM_THREADS;
+    if (s >= S.n_sub) continue;
+    const int I = s / S.nsx, J = s - I * S.nsx;
+    const float x = (J - 0.5f * (S.nsx - 1)) * S.dsub - xc;
+    const float y = (I - 0.5f * (S.nsy - 1)) * S.dsub - yc;
+    const float xp = cphi * x + sphi * y, yp = -sphi * x + cphi * y;
+    const float X = xp * xp, Y = yp * yp;
+    float gn = 0.0f, gd = 0.0f;
+    for (int e = S.w_off[s]; e < S.w_off[s + 1]; ++e) {
+      const int l = S.w_bin[e];
+      const float w = S.w_val[e];
+      gn = fmaf(w, gN[l], gn);
+      gd = fmaf(w, gD[l], gd);
+    }
+    const float4 pv = gw.pt[(size_t)b * max_sub + s];
+    // tracer surface brightness derivatives
+    float dsx = 0.0f, dsy = 0.0f;
+    if (gd != 0.0f) {
+      for (int k = 0; k < S.n_light; ++k) {
+        const float E = ex2(-fmaf(scy[k], Y, scx[k] * X));
+        atomicAdd(&aI0[k], gd * E);
+        dsx = fmaf(sI0[k] * scx[k], E, dsx);
+        dsy = fmaf(sI0[k] * scy[k], E, dsy);
+      }
+    }
+    const float aX = gn * pv.y - gd * LN2F * dsx;
+    const float aY = gn * pv.z - gd * LN2F * dsy;
+    // X = x'^2, Y = y'^2; dx'/dphi = y', dy'/dphi = -x'; dx'/dxc = -c, dy'/dxc = s;
+    // dx'/dyc = -s, dy'/dyc = -c
+    gphi += 2.0f * xp * yp * (aX - aY);
+    gxc += aX * (-2.0f * xp * cphi) + aY * (2.0f * yp * sphi);
+    gyc += aX * (-2.0f * xp * sphi) + aY * (-2.0f * yp * cphi);
+    gw.adjpt[(size_t)b * max_sub + s] = make_float4(X, Y, X * Y, gn);
+  }
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int off = 16; off > 0; off >>= 1) {
+    gphi += __shfl_down_sync(0xffffffffu, gphi, off);
+    gxc += __shfl_down_sync(0xffffffffu, gxc, off);
+    gyc += __shfl_down_sync(0xffffffffu, gyc, off);
+  }
+  if (lane == 0) {
+    red[warp][0] = gphi;
+    red[warp][1] = gxc;
+    red[warp][2] = gyc;
+  }
+  __syncthreads();
+  if (tid < 3) {
+    double s = 0.0;
+    for (int w = 0; w < JAM_THREADS / 32; ++w) s += (double)red[w][tid];
+    atomicAdd(&grad[(size_t)b * GLAD_NTHETA + 3 + tid], s);  // phi, x_c, y_c = theta[3..5]
+  }
+  for (int k = tid; k < S.n_light; k += JAM_THREADS)
+    if (aI0[k] != 0.0f) atomicAdd(&gw.adjI0[(size_t)b * max_light + k], (double)aI0[k]);
+}
+
+#define ADJ_EPT 4          // table entries per thread
+#define ADJ_THREADS 256
+#define ADJ_PCHUNK 512     // sky points per shared-memory chunk
+
+// d logL / d (Q0, Q1, a_y) of each table entry: sums over every sky point of
+// g_N(s) E(s) {1, X, (Q0 + Q1 X) Y} with E = 2^(ax X + ay Y).
+__global__ void __launch_bounds__(ADJ_THREADS) k_jam_adj(const SysDev *__restrict__ sysv,
+                                                         const int *__restrict__ sys_id, WsDev ws,
+                                                         GradWs gw, int max_ent, int max_sub) {
+  const int b = blockIdx.y;
+  if (ws.status[b] != GLAD_SAMPLE_OK) return;
+  const SysDev &S = sysv[sys_id[b]];
+  const int e0 = blockIdx.x * ADJ_THREADS * ADJ_EPT;
+  if (e0 >= S.n_ent) return;
+  __shared__ float4 pts[2][ADJ_PCHUNK];
+  const int tid = threadIdx.x;
+  float ax[ADJ_EPT], ay[ADJ_EPT];
+  float s0[ADJ_EPT], sx[ADJ_EPT], sy[ADJ_EPT], sxy[ADJ_EPT];
+  double S0[ADJ_EPT], SX[ADJ_EPT], SY[ADJ_EPT], SXY[ADJ_EPT];
+  const float4 *gt = ws.tab + (size_t)b * max_ent;
+#pragma unroll
+  for (int k = 0; k < ADJ_EPT; ++k) {
+    const int e = e0 + tid + k * ADJ_THREADS;
+    const float4 c = e < S.n_ent ? gt[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+    ax[k] = c.x;
+    ay[k] = c.y;
+    s0[k] = sx[k] = sy[k] = sxy[k] = 0.0f;
+    S0[k] = SX[k] = SY[k] = SXY[k] = 0.0;
+  }
+  const float4 *gp = gw.adjpt + (size_t)b * max_sub;
+  const int n = S.n_sub;
+  const int n_chunks = (n + ADJ_PCHUNK - 1) / ADJ_PCHUNK;
+  for (int i = tid; i < ADJ_PCHUNK; i += ADJ_THREADS)
+    pts[0][i] = i < n ? gp[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  for (int ch = 0; ch < n_chunks; ++ch) {
+    const int cur = ch & 1;
+    if (ch + 1 < n_chunks) {
+      const int base = (ch + 1) * ADJ_PCHUNK;
+      for (int i = tid; i < ADJ_PCHUNK; i += ADJ_THREADS)
+        pts[cur ^ 1][i] = base + i < n ? gp[base + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float4 *pp = pts[cur];
+#pragma unroll 2
+    for (int i = 0; i < ADJ_PCHUNK; ++i) {
+      const float4 P = pp[i];  // X, Y, XY, g_N (g_N = 0 on padding)
+#pragma unroll
+      for (int k = 0; k < ADJ_EPT; ++k) {
+        const float tg = P.w * ex2(fmaf(ay[k], P.y, ax[k] * P.x));
+        s0[k] += tg;
+        sx[k] = fmaf(tg, P.x, sx[k]);
+        sy[k] = fmaf(tg, P.y, sy[k]);
+        sxy[k] = fmaf(tg, P.z, sxy[k]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < ADJ_EPT; ++k) {
+      S0[k] += s0[k];
+      SX[k] += sx[k];
+      SY[k] += sy[k];
+      SXY[k] += sxy[k];
+      s0[k] = sx[k] = sy[k] = sxy[k] = 0.0f;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < ADJ_EPT; ++k) {
+    const int e = e0 + tid + k * ADJ_THREADS;
+    if (e >= S.n_ent) continue;
+    const float4 c = gt[e];
+    double *o = gw.entadj + ((size_t)b * max_ent + e) * 3;
+    o[0] = S0[k];
+    o[1] = SX[k];
+    o[2] = (double)c.z * SY[k] + (double)c.w * SXY[k];  // natural-units a_y adjoint
+  }
+}
+
+// ------------------------------------------------------------------ per-sample chain to theta
+
+typedef Dual<5, double> D5;   // tangents: c0_k, e2_j, s2, c2, b
+typedef Dual<9, double> D9;   // tangents: theta 0,1,2,13,14,15,16,17,18
+typedef Dual<9, double> DT;   // tangents: theta 0..7 and H0 (delays)
+
+struct cplx {
+  double r, i;
+};
+__device__ inline cplx cmul(cplx a, cplx b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
+__device__ inline cplx cexp_(cplx a) {
+  double s, c;
+  sincos(a.i, &s, &c);
+  const double e = exp(a.r);
+  return {e * c, e * s};
+}
+__device__ inline cplx clog_(cplx a) { return {log(hypot(a.r, a.i)), atan2(a.i, a.r)}; }
+
+__global__ void __launch_bounds__(256) k_grad_chain(const SysDev *__restrict__ sysv,
+                                                    const int *__restrict__ sys_id,
+                                                    const double *__restrict__ theta, WsDev ws,
+                                                    GradWs gw, int max_light, int max_mass,
+                                                    int max_ent, double *grad) {
+  const int b = blockIdx.x;
+  if (ws.status[b] != GLAD_SAMPLE_OK) return;
+  const SysDev &S = sysv[sys_id[b]];
+  const double *th = theta + (size_t)GLAD_NTHETA * b;
+  const int tid = threadIdx.x;
+  __shared__ double a_nu0[GLAD_MAX_LIGHT], a_c0[GLAD_MAX_LIGHT];
+  __shared__ double a_C[GLAD_MAX_MASS + 1], a_e2[GLAD_MAX_MASS + 1];
+  __shared__ double a_glob[3];
+  __shared__ double gsm[GLAD_NTHETA];
+  __shared__ double Ad[GLAD_MAX_LIGHT][10];  // light amplitudes with tangents (I_e, R_e in slots 3, 4)
+  const int nL = S.n_light, nM = S.n_mass, nMt = S.n_mass_tot;
+  for (int k = tid; k < nL; k += blockDim.x) a_nu0[k] = a_c0[k] = 0.0;
+  for (int j = tid; j < nMt; j += blockDim.x) a_C[j] = a_e2[j] = 0.0;
+  if (tid < 3) a_glob[tid] = 0.0;
+  if (tid < GLAD_NTHETA) gsm[tid] = 0.0;
+  __syncthreads();
+  const DynP dp = ws.dp[b];
+  const size_t bl = (size_t)b * max_light, bm = (size_t)b * max_mass;
+
+  // (a) table entries: adjoints of (Q0, Q1, a_y) -> nu0_k, c0_k, C_j, e2_j, sin^2 i, cos^2 i, b
+  {
+    const D5 s2 = D5::var(dp.s2, 2), c2 = D5::var(dp.c2, 3), bb = D5::var(dp.b, 4);
+    for (int e = tid; e < S.n_ent; e += blockDim.x) {
+      const int kj = e / S.n_gl;
+      const int j = kj % nMt, k = kj / nMt;
+      const double *ga = gw.entadj + ((size_t)b * max_ent + e) * 3;
+      const double GQ0 = ga[0], GQ1 = ga[1], Gay = ga[2];
+      const double u = S.gl_u[e], wu = S.gl_wu[e];
+      const double sj = S.sig_mass[j], sk = S.sig_light[k];
+      const D5 e2 = D5::var(ws.e2[bm + j], 1);
+      const D5 c0 = D5::var(ws.c0[bl + k], 0);
+      const double a = u * u / (2.0 * sj * sj);
+      const D5 h = 1.0 - e2 * (u * u);
+      const double p = 1.0 / (2.0 * sk * sk) + a;
+      const D5 c = c0 + a / h;
+      const D5 al = p * s2 + c * c2;
+      const D5 sh = dsqrt(h);
+      const D5 A = a / (h * sh * c);
+      const D5 P0 = A * (bb * s2 + c2);
+      const D5 P1 = s2 * (2.0 * a / sh - 2.0 * p * bb * A);
+      const D5 wsq = wu * dsqrt(PI_D / al);
+      const D5 R0 = wsq * P0, R1 = wsq * P1;
+      const D5 ayn = -p * c / al;
+      const double nu = ws.nu0[bl + k], Cj = ws.Cj[bm + j];
+      const double gR = GQ0 * R0.v + GQ1 * R1.v;
+      atomicAdd(&a_nu0[k], Cj * gR);
+      atomicAdd(&a_C[j], nu * gR);
+      const double nc = nu * Cj;
+      double d[5];
+#pragma unroll
+      for (int i = 0; i < 5; ++i) d[i] = nc * (GQ0 * R0.d[i] + GQ1 * R1.d[i]) + Gay * ayn.d[i];
+      atomicAdd(&a_c0[k], d[0]);
+      atomicAdd(&a_e2[j], d[1]);
+      atomicAdd(&a_glob[0], d[2]);
+      atomicAdd(&a_glob[1], d[3]);
+      atomicAdd(&a_glob[2], d[4]);
+    }
+  }
+  __syncthreads();
+
+  // (b) per Gaussian: MGE amplitudes (analytic partials of F), deprojection, C_j, e2_j
+  const double tE = th[0], g = th[1], q = th[2], inc = th[15];
+  const D9 Di = D9::var(inc, 5);
+  const D9 si = dsin(Di), ci = dcos(Di);
+  const D9 S2 = si * si, C2 = ci * ci;
+  const int P2 = 2 * S.mge_P + 1;
+  for (int k = tid; k < nL; k += blockDim.x) {
+    const int cc = S.lcomp_of[k];
+    const double Ie = cc == 0 ? th[13] : S.lcomp[4 * cc];
+    const double Re = cc == 0 ? th[14] : S.lcomp[4 * cc + 1];
+    const double n = S.lcomp[4 * cc + 2];
+    const double bn = sersic_bn_d(n);
+    const double sg = S.sig_light[k];
+    double f = 0.0, fRe = 0.0;
+    for (int m = 0; m < P2; ++m) {
+      const double2 ch = S.chi[m];
+      const cplx z = {sg * ch.x, sg * ch.y};
+      const cplx l = clog_({z.r / Re, z.i / Re});
+      const cplx w = cexp_({l.r / n, l.i / n});
+      const cplx F = cexp_({-bn * (w.r - 1.0), -bn * w.i});
+      // dF/dRe = F bn w / (n Re)
+      const cplx Fw = cmul(F, w);
+      f += S.eta[m] * Ie * F.r;
+      fRe += S.eta[m] * Ie * Fw.r * bn / (n * Re);
+    }
+    D9 A(S.mw_light[k] * f);
+    if (cc == 0) {
+      A.d[3] = S.mw_light[k] * f / Ie;
+      A.d[4] = S.mw_light[k] * fRe;
+    }
+    for (int i = 0; i < 10; ++i) Ad[k][i] = i == 0 ? A.v : A.d[i - 1];
+    const double qp = S.qp_light[k];
+    const D9 qi = dsqrt(qp * qp - C2) / si;
+    const D9 nu0 = qp * A / (SQRT2PI_D * sg * qi);
+    const D9 c0 = 1.0 / (2.0 * sg * sg * qi * qi);
+    const double aI = gw.adjI0[bl + k];
+    for (int i = 0; i < 9; ++i) {
+      const double v = a_nu0[k] * nu0.d[i] + a_c0[k] * c0.d[i] + aI * A.d[i];
+      if (v != 0.0) {
+        const int t = i < 3 ? i : (i < 5 ? 10 + i : 10 + i);  // 0,1,2,13,14,15,16,17,18
+        atomicAdd(&gsm[t], v);
+      }
+    }
+  }
+  for (int j = tid; j < nM; j += blockDim.x) {
+    const double sg = S.sig_mass[j];
+    const double coef = (3.0 - g) / (1.0 + q) * pow(tE, g - 1.0);
+    const double rs2 = S.r_soft * S.r_soft;
+    double f = 0.0, fg = 0.0;
+    for (int m = 0; m < P2; ++m) {
+      const double2 ch = S.chi[m];
+      const cplx z = {sg * ch.x, sg * ch.y};
+      cplx z2 = cmul(z, z);
+      z2.r += rs2;
+      const cplx lz = clog_(z2);
+      const double ex = -0.5 * (g - 1.0);
+      const cplx F = cexp_({ex * lz.r, ex * lz.i});
+      // dF/dg = F (-1/(3-g) + ln tE - log(z^2 + rs^2)/2)
+      const cplx fac = {-1.0 / (3.0 - g) + log(tE) - 0.5 * lz.r, -0.5 * lz.i};
+      const cplx Fg = cmul(F, fac);
+      f += S.eta[m] * coef * F.r;
+      fg += S.eta[m] * coef * Fg.r;
+    }
+    D9 A(S.mw_mass[j] * f);
+    A.d[0] = A.v * (g - 1.0) / tE;
+    A.d[1] = S.mw_mass[j] * fg;
+    A.d[2] = -A.v / (1.0 + q);
+    const D9 qp = D9::var(q, 2);
+    const D9 qi2 = (qp * qp - C2) / S2;
+    const D9 Cj = 2.0 * SQRT2PI_D * S.v2unit * sg * qp * A;
+    const D9 e2 = 1.0 - qi2;
+    for (int i = 0; i < 9; ++i) {
+      const double v = a_C[j] * Cj.d[i] + a_e2[j] * e2.d[i];
+      if (v != 0.0) atomicAdd(&gsm[i < 3 ? i : 10 + i], v);
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    // black hole: A_BH = f_BH Upsilon L_tot L_scale / (2 pi s^2), L_tot = sum 2 pi A_k s_k^2 q'_k
+    if (S.has_bh) {
+      D9 L(0.0);
+      for (int k = 0; k < nL; ++k) {
+        D9 A;
+        A.v = Ad[k][0];
+        for (int i = 0; i < 9; ++i) A.d[i] = Ad[k][i + 1];
+        L = L + (2.0 * PI_D * S.sig_light[k] * S.sig_light[k] * S.qp_light[k]) * A;
+      }
+      const D9 ups = D9::var(th[17], 7), fbh = D9::var(th[18], 8);
+      const double sb = S.bh_sigma;
+      const D9 A = fbh * ups * L * (S.L_scale / (2.0 * PI_D * sb * sb));
+      const D9 qi2 = (1.0 - C2) / S2;
+      const D9 Cj = 2.0 * SQRT2PI_D * S.v2unit * sb * A;
+      const D9 e2 = 1.0 - qi2;
+      for (int i = 0; i < 9; ++i) {
+        const double v = a_C[nM] * Cj.d[i] + a_e2[nM] * e2.d[i];
+        if (v != 0.0) gsm[i < 3 ? i : 10 + i] += v;
+      }
+    }
+    // globals: sin^2 i, cos^2 i (theta 15) and b = 1/(1-beta) (theta 16)
+    gsm[15] += a_glob[0] * S2.d[5] + a_glob[1] * C2.d[5];
+    const double bb = 1.0 / (1.0 - th[16]);
+    gsm[16] += a_glob[2] * bb * bb;
+  }
+  if (tid == 32) {
+    // time delays: -chi2_tmd/2 by duals through the FP64 lens model
+    DT tt[8];
+    for (int i = 0; i < 8; ++i) tt[i] = DT::var(th[i], i);
+    const DT h0 = DT::var(th[19], 8);
+    const DT chi = chi2_tmd_t<DT>(tt, h0, S.img_xy, S.n_img, S.dt_obs, S.dt_sig,
+                                  S.dt_per_arcsec2_H0, S.sis, S.n_sis);
+    for (int i = 0; i < 8; ++i) atomicAdd(&gsm[i], -0.5 * chi.d[i]);
+    atomicAdd(&gsm[19], -0.5 * chi.d[8]);
+  }
+  __syncthreads();
+  if (tid < GLAD_NTHETA) grad[(size_t)b * GLAD_NTHETA + tid] += gsm[tid];
+}
+
+__global__ void k_grad_zero_invalid(const WsDev ws, int B, double *grad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B * GLAD_NTHETA) return;
+  if (ws.status[i / GLAD_NTHETA] != GLAD_SAMPLE_OK) grad[i] = 0.0;
+}
+
+template <class T>
+bool galloc(GradWs &w, T *&p, size_t n) {
+  void *d = nullptr;
+  if (cudaMalloc(&d, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) return false;
+  w.allocs.push_back(d);
+  p = (T *)d;
+  return true;
+}
+
+}  // namespace
+
+void grad_ws_free(glad_ctx *c) {
+  if (!c->gws) return;
+  for (void *p : c->gws->allocs) cudaFree(p);
+  delete c->gws;
+  c->gws = nullptr;
+}
+
+cudaError_t grad_ws_ensure(glad_ctx *c, int B) {
+  if (c->gws && c->gws->B >= B) return cudaSuccess;
+  cudaDeviceSynchronize();
+  grad_ws_free(c);
+  c->gws = new GradWs();
+  GradWs &w = *c->gws;
+  const size_t b = B;
+  const bool ok = galloc(w, w.resid, b * c->max_pix) && galloc(w, w.gpix, b * c->max_pix) &&
+                  galloc(w, w.pt, b * c->max_sub) && galloc(w, w.adjpt, b * c->max_sub) &&
+                  galloc(w, w.entadj, b * c->max_ent * 3) && galloc(w, w.adjI0, b * c->max_light);
+  if (!ok) {
+    grad_ws_free(c);
+    return cudaErrorMemoryAllocation;
+  }
+  w.B = B;
+  return cudaSuccess;
+}
+
+float *grad_resid_buffer(glad_ctx *c) { return c->gws ? c->gws->resid : nullptr; }
+
+cudaError_t launch_jam_fg(glad_ctx *c, const int *sys_id, int B, cudaStream_t st) {
+  dim3 grid(c->max_sky_tiles, B);
+  k_jam_fg<<<grid, JAM_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, *c->gws, c->max_light,
+                                         c->max_ent, c->max_bins, c->max_sub);
+  return cudaGetLastError();
+}
+
+// after the forward pass (with k_jam_fg and the residual output of k_conv)
 cudaError_t launch_grad(glad_ctx *c, const int *sys_id, const double *theta, int B, double *grad,
                         cudaStream_t st) {
-  (void)c; (void)sys_id; (void)theta; (void)B; (void)grad; (void)st;
-  return cudaErrorNotSupported;
+  GradWs &g = *c->gws;
+  cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(double) * GLAD_NTHETA * (size_t)B, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g.adjI0, 0, sizeof(double) * c->max_light * (size_t)B, st);
+  if (e != cudaSuccess) return e;
+  // lensing
+  e = GLAD_PROF(c, st, KID_GRAD_LENS, ([&]() -> cudaError_t {
+    int max_conv_tiles = 0, max_k = 1;
+    for (auto &s : c->sys) {
+      const int t = ((s.d.nx + CONV_TX - 1) / CONV_TX) * ((s.d.ny + CONV_TY - 1) / CONV_TY);
+      max_conv_tiles = std::max(max_conv_tiles, t);
+      max_k = std::max(max_k, s.d.psf_k);
+    }
+    const int h = (max_k - 1) / 2;
+    const size_t smem = sizeof(float) * ((CONV_TX + 2 * h) * (CONV_TY + 2 * h) + max_k * max_k);
+    k_conv_adj<<<dim3(max_conv_tiles, B), dim3(CONV_TX, CONV_TY), smem, st>>>(
+        c->d_sys, sys_id, c->ws.d, g, c->max_pix);
+    cudaError_t r = cudaGetLastError();
+    if (r != cudaSuccess) return r;
+    k_image_grad<<<dim3(c->max_img_tiles, B), LENS_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, g,
+                                                                     c->max_pix, grad);
+    return cudaGetLastError();
+  }()));
+  if (e != cudaSuccess) return e;
+  // dynamics
+  k_kin_adj<<<dim3(c->max_sky_tiles, B), JAM_THREADS, 0, st>>>(
+      c->d_sys, sys_id, c->ws.d, g, c->max_light, c->max_bins, c->max_sub, grad);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = GLAD_PROF(c, st, KID_GRAD_JAM_ADJ, ([&]() -> cudaError_t {
+    const int nb = (c->max_ent + ADJ_THREADS * ADJ_EPT - 1) / (ADJ_THREADS * ADJ_EPT);
+    k_jam_adj<<<dim3(nb, B), ADJ_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, g, c->max_ent,
+                                                   c->max_sub);
+    return cudaGetLastError();
+  }()));
+  if (e != cudaSuccess) return e;
+  e = GLAD_PROF(c, st, KID_GRAD_CHAIN, ([&]() -> cudaError_t {
+    k_grad_chain<<<B, 256, 0, st>>>(c->d_sys, sys_id, theta, c->ws.d, g, c->max_light,
+                                    c->max_mass_tot, c->max_ent, grad);
+    cudaError_t r = cudaGetLastError();
+    if (r != cudaSuccess) return r;
+    k_grad_zero_invalid<<<(B * GLAD_NTHETA + 255) / 256, 256, 0, st>>>(c->ws.d, B, grad);
+    return cudaGetLastError();
+  }()));
+  return e;
 }
-cudaError_t grad_ws_ensure(glad_ctx *c, int B) { (void)c; (void)B; return cudaSuccess; }
-void grad_ws_free(glad_ctx *c) { (void)c; }
+
+void set_grad_smem_limit() {
+  const int h = (GLAD_MAX_PSF - 1) / 2;
+  const int smem = sizeof(float) * ((CONV_TX + 2 * h) * (CONV_TY + 2 * h) + GLAD_MAX_PSF * GLAD_MAX_PSF);
+  cudaFuncSetAttribute(k_conv_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}

@@ -90,7 +90,8 @@ __global__ void __launch_bounds__(LENS_THREADS) k_image(const SysDev *__restrict
 
 __global__ void __launch_bounds__(CONV_TX *CONV_TY) k_conv(const SysDev *__restrict__ sysv,
                                                            const int *__restrict__ sys_id, WsDev ws,
-                                                           int max_pix, float *image_out) {
+                                                           int max_pix, float *image_out,
+                                                           float *resid_out) {
   const int b = blockIdx.y;
   if (ws.status[b] != GLAD_SAMPLE_OK) return;
   const SysDev &S = sysv[sys_id[b]];
@@ -131,6 +132,8 @@ __global__ void __launch_bounds__(CONV_TX *CONV_TY) k_conv(const SysDev *__restr
     } else {
       const double r = ((double)S.data[o] - m) * (double)S.wgt[o];
       chi = r * r;
+      // d logL / d m = mask (d - m) / sigma^2, for the adjoint
+      if (resid_out) resid_out[(size_t)b * max_pix + o] = (float)(r * (double)S.wgt[o]);
     }
   }
   if (image_out) return;
@@ -148,7 +151,8 @@ __global__ void __launch_bounds__(CONV_TX *CONV_TY) k_conv(const SysDev *__restr
 
 }  // namespace
 
-cudaError_t launch_lens(glad_ctx *c, const int *sys_id, int B, float *image_out, cudaStream_t st) {
+cudaError_t launch_lens(glad_ctx *c, const int *sys_id, int B, float *image_out, cudaStream_t st,
+                        float *resid_out) {
   dim3 g1(c->max_img_tiles, B);
   k_image<<<g1, LENS_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_pix);
   cudaError_t e = cudaGetLastError();
@@ -163,7 +167,7 @@ cudaError_t launch_lens(glad_ctx *c, const int *sys_id, int B, float *image_out,
   const size_t smem = sizeof(float) * ((CONV_TX + 2 * h) * (CONV_TY + 2 * h) + max_k * max_k);
   dim3 g2(max_conv_tiles, B);
   k_conv<<<g2, dim3(CONV_TX, CONV_TY), smem, st>>>(c->d_sys, sys_id, c->ws.d, c->max_pix,
-                                                   image_out);
+                                                   image_out, resid_out);
   return cudaGetLastError();
 }
 

@@ -207,12 +207,32 @@ __global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
     L.t = (float)t;
     L.pref = (float)(2.0 * bt / (1.0 + q) * pow(bt, t - 1.0));
     L.nterms = nt;
-    for (int n = 1; n <= nt; ++n)
-      L.rho[n - 1] = (float)(-f * (2.0 * n - (2.0 - t)) / (2.0 * n + (2.0 - t)));
+    for (int n = 1; n <= nt; ++n) {
+      const double num = 2.0 * n - (2.0 - t), den = 2.0 * n + (2.0 - t);
+      L.rho[n - 1] = (float)(-f * num / den);
+      L.drho_t[n - 1] = (float)(-f * 4.0 * n / (den * den));
+      L.drho_q[n - 1] = (float)(2.0 * num / (den * (1.0 + q) * (1.0 + q)));
+    }
+    {
+      // ln pref = ln 2 + t ln b_TM - ln(1+q), b_TM = q (2/(1+q))^(1/t) theta_E
+      const double pref = 2.0 * bt / (1.0 + q) * pow(bt, t - 1.0);
+      L.pref_d[0] = (float)(pref * t / tE);
+      L.pref_d[1] = (float)(pref * (log(bt) - log(2.0 / (1.0 + q)) / t));
+      L.pref_d[2] = (float)(pref * (t / q - 2.0 / (1.0 + q)));
+    }
     double s2p, c2p;
     sincos(2.0 * th[7], &s2p, &c2p);
     L.g1 = (float)(th[6] * c2p);
     L.g2 = (float)(th[6] * s2p);
+    L.gext = (float)th[6];
+    L.c2pe = (float)c2p;
+    L.s2pe = (float)s2p;
+    {
+      const double n = th[10];
+      L.src_bnp = (float)(2.0 - 4.0 / (405.0 * n * n) - 92.0 / (25515.0 * n * n * n) -
+                          393.0 / (1148175.0 * n * n * n * n) +
+                          4.0 * 2194697.0 / (30690717750.0 * n * n * n * n * n));
+    }
     L.src_Ie = (float)th[8];
     L.src_Rei = (float)(1.0 / th[9]);
     L.src_ninv = (float)(1.0 / th[10]);
@@ -231,36 +251,8 @@ __global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
     }
     L.valid = 1;
     // ---- time delays (FP64)
-    const int ni = S.n_img;
-    double w[GLAD_MAX_IMG], bx[GLAD_MAX_IMG], by[GLAD_MAX_IMG], psi[GLAD_MAX_IMG];
-    double wsum = 0.0, bhx = 0.0, bhy = 0.0;
-    for (int i = 0; i < ni; ++i) {
-      const double x = S.img_xy[2 * i], y = S.img_xy[2 * i + 1];
-      LensEval e = lens_eval_d(x, y, th, S.sis, S.n_sis);
-      const double det = (1.0 - e.a11) * (1.0 - e.a22) - e.a12 * e.a21;
-      w[i] = 1.0 / fabs(det);
-      bx[i] = x - e.ax;
-      by[i] = y - e.ay;
-      psi[i] = e.psi;
-      wsum += w[i];
-      bhx += w[i] * bx[i];
-      bhy += w[i] * by[i];
-    }
-    bhx /= wsum;
-    bhy /= wsum;
-    const double kdt = S.dt_per_arcsec2_H0 / th[19];
-    double phi0 = 0.0, chi2 = 0.0;
-    for (int i = 0; i < ni; ++i) {
-      const double x = S.img_xy[2 * i], y = S.img_xy[2 * i + 1];
-      const double ph = 0.5 * ((x - bhx) * (x - bhx) + (y - bhy) * (y - bhy)) - psi[i];
-      if (i == 0) {
-        phi0 = ph;
-      } else {
-        const double dt = kdt * (ph - phi0);
-        const double r = (S.dt_obs[i - 1] - dt) / S.dt_sig[i - 1];
-        chi2 += r * r;
-      }
-    }
+    const double chi2 = chi2_tmd_t<double>(th, th[19], S.img_xy, S.n_img, S.dt_obs, S.dt_sig,
+                                           S.dt_per_arcsec2_H0, S.sis, S.n_sis);
     ws.terms[3 * (size_t)b + 2] = chi2;
   }
 }
