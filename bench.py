@@ -251,6 +251,8 @@ def main():
             rc = lib.glad_loglike(ctx.handle, P(sid), P(theta), B, P(logL), P(status), None, hs)
         _lib.check(rc, "step")
 
+    # launch shapes picked by the library's autotuner on this batch (untimed)
+    tuning = ctx.autotune(theta, sid, with_grad=args.grad)
     # L2 flush buffer (256 MB > 126 MB L2), written before each timed step, outside its events
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
@@ -344,7 +346,8 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name(w, args.grad, B), "batch_per_gpu": B,
                    "precision": "f32 bulk; f64 MGE, tables and chi^2 reductions",
-                   "l2": "flushed (256 MB write) before each timed step", "valid_samples": n_valid},
+                   "l2": "flushed (256 MB write) before each timed step", "valid_samples": n_valid,
+                   "tuning": tuning},
         "roofline": {"bound": "alu", "kernel": names[jam_id], "achieved": achieved, "peak": peak,
                      "unit": "Gexp2/s", "frac": achieved / peak, "traffic": None,
                      "algorithmic_units": f"{evals} JAM integrand evaluations per launch (1 ex2 each)",

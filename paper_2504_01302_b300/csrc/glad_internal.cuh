@@ -125,6 +125,11 @@ struct glad_ctx {
   int max_img_tiles = 0, max_sky_tiles = 0, max_tab_blocks = 0;
   Workspace ws;
   GradWs *gws = nullptr;
+  // launch shapes chosen by glad_autotune (defaults until it runs)
+  struct Tune {
+    int jam_pts = 8;      // sky points per thread in the JAM pair-sum kernels
+    int adj_ept = 4;      // table entries per thread in the JAM adjoint
+  } tune;
   int *d_one_sys = nullptr;      // scratch sys id for single-sample calls
   // kernel timing (glad_profile)
   int prof = 0;

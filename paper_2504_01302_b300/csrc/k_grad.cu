@@ -24,7 +24,7 @@ struct GradWs {
   float *resid = nullptr;    // [B*max_pix]  d logL / d m (blurred model)
   float *gpix = nullptr;     // [B*max_pix]  d logL / d img (unblurred)
   float4 *pt = nullptr;      // [B*max_sub]  V, dV/dX, dV/dY (X = x'^2, Y = y'^2)
-  float4 *adjpt = nullptr;   // [B*max_sub]  X, Y, X*Y, g_N
+  float4 *adjpt = nullptr;   // [B*max_sub*2] (X, X, Y, Y), (XY, XY, g_N, g_N)
   double *entadj = nullptr;  // [B*max_ent*3] d logL / d (Q0, Q1, a_y)
   double *adjI0 = nullptr;   // [B*max_light] d logL / d I0_k (tracer amplitudes)
   std::vector<void *> allocs;
@@ -261,8 +261,9 @@ __global__ void __launch_bounds__(JAM_THREADS) k_jam_fg(const SysDev *__restrict
     scx[k] = S.sb_cx[k];
     scy[k] = S.sb_cy[k];
   }
-  float X[JAM_PTS], Y[JAM_PTS];
-  float aV[JAM_PTS], a1[JAM_PTS], a2[JAM_PTS], a3[JAM_PTS];
+  constexpr int NP = JAM_PTS / 2;
+  float2 X[NP], Y[NP];
+  float2 aV[NP], a1[NP], a2[NP], a3[NP];
   double dV[JAM_PTS], d1[JAM_PTS], d2[JAM_PTS], d3[JAM_PTS];
   const float cphi = (float)dp.cphi, sphi = (float)dp.sphi;
   const float xc = (float)dp.xc, yc = (float)dp.yc;
@@ -274,11 +275,18 @@ __global__ void __launch_bounds__(JAM_THREADS) k_jam_fg(const SysDev *__restrict
     const float x = (J - 0.5f * (S.nsx - 1)) * S.dsub - xc;
     const float y = (I - 0.5f * (S.nsy - 1)) * S.dsub - yc;
     const float xp = cphi * x + sphi * y, yp = -sphi * x + cphi * y;
-    X[i] = xp * xp;
-    Y[i] = yp * yp;
-    aV[i] = a1[i] = a2[i] = a3[i] = 0.0f;
+    if (i & 1) {
+      X[i >> 1].y = xp * xp;
+      Y[i >> 1].y = yp * yp;
+    } else {
+      X[i >> 1].x = xp * xp;
+      Y[i >> 1].x = yp * yp;
+    }
     dV[i] = d1[i] = d2[i] = d3[i] = 0.0;
   }
+  const float2 z2 = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int p = 0; p < NP; ++p) aV[p] = a1[p] = a2[p] = a3[p] = z2;
   const float4 *gt = ws.tab + (size_t)b * max_ent;
   const int n_ent = S.n_ent;
   const int n_chunks = (n_ent + JAM_CHUNK - 1) / JAM_CHUNK;
@@ -296,23 +304,30 @@ __global__ void __launch_bounds__(JAM_THREADS) k_jam_fg(const SysDev *__restrict
 #pragma unroll 2
     for (int e = 0; e < JAM_CHUNK; ++e) {
       const float4 c = tt[e];
+      const float2 cx = make_float2(c.x, c.x), cy = make_float2(c.y, c.y);
+      const float2 cz = make_float2(c.z, c.z), cw = make_float2(c.w, c.w);
 #pragma unroll
-      for (int i = 0; i < JAM_PTS; ++i) {
-        const float E = ex2(fmaf(c.y, Y[i], c.x * X[i]));
-        const float tv = fmaf(c.w, X[i], c.z) * E;
-        aV[i] += tv;
-        a1[i] = fmaf(c.w, E, a1[i]);
-        a2[i] = fmaf(c.x, tv, a2[i]);
-        a3[i] = fmaf(c.y, tv, a3[i]);
+      for (int p = 0; p < NP; ++p) {
+        const float2 arg = __ffma2_rn(cy, Y[p], __fmul2_rn(cx, X[p]));
+        const float2 E = make_float2(ex2(arg.x), ex2(arg.y));
+        const float2 tv = __fmul2_rn(__ffma2_rn(cw, X[p], cz), E);
+        aV[p] = __fadd2_rn(aV[p], tv);
+        a1[p] = __ffma2_rn(cw, E, a1[p]);
+        a2[p] = __ffma2_rn(cx, tv, a2[p]);
+        a3[p] = __ffma2_rn(cy, tv, a3[p]);
       }
     }
 #pragma unroll
-    for (int i = 0; i < JAM_PTS; ++i) {
-      dV[i] += aV[i];
-      d1[i] += a1[i];
-      d2[i] += a2[i];
-      d3[i] += a3[i];
-      aV[i] = a1[i] = a2[i] = a3[i] = 0.0f;
+    for (int p = 0; p < NP; ++p) {
+      dV[2 * p] += aV[p].x;
+      dV[2 * p + 1] += aV[p].y;
+      d1[2 * p] += a1[p].x;
+      d1[2 * p + 1] += a1[p].y;
+      d2[2 * p] += a2[p].x;
+      d2[2 * p + 1] += a2[p].y;
+      d3[2 * p] += a3[p].x;
+      d3[2 * p + 1] += a3[p].y;
+      aV[p] = a1[p] = a2[p] = a3[p] = z2;
     }
     __syncthreads();
   }
@@ -320,8 +335,10 @@ __global__ void __launch_bounds__(JAM_THREADS) k_jam_fg(const SysDev *__restrict
   for (int i = 0; i < JAM_PTS; ++i) {
     const int s = tile0 + tid + i * JAM_THREADS;
     if (s >= S.n_sub) continue;
+    const float Xi = (i & 1) ? X[i >> 1].y : X[i >> 1].x;
+    const float Yi = (i & 1) ? Y[i >> 1].y : Y[i >> 1].x;
     float sb = 0.0f;
-    for (int k = 0; k < S.n_light; ++k) sb = fmaf(sI0[k], ex2(-fmaf(scy[k], Y[i], scx[k] * X[i])), sb);
+    for (int k = 0; k < S.n_light; ++k) sb = fmaf(sI0[k], ex2(-fmaf(scy[k], Yi, scx[k] * Xi)), sb);
     const float v = (float)dV[i];
     // coefficients are in log2 units: d/dX 2^(ax X) = ln2 ax 2^(ax X)
     gw.pt[(size_t)b * max_sub + s] =
@@ -410,7 +427,8 @@ __global__ void __launch_bounds__(JAM_THREADS) k_kin_adj(const SysDev *__restric
     gphi += 2.0f * xp * yp * (aX - aY);
     gxc += aX * (-2.0f * xp * cphi) + aY * (2.0f * yp * sphi);
     gyc += aX * (-2.0f * xp * sphi) + aY * (-2.0f * yp * cphi);
-    gw.adjpt[(size_t)b * max_sub + s] = make_float4(X, Y, X * Y, gn);
+    gw.adjpt[2 * ((size_t)b * max_sub + s)] = make_float4(X, X, Y, Y);
+    gw.adjpt[2 * ((size_t)b * max_sub + s) + 1] = make_float4(X * Y, X * Y, gn, gn);
   }
   const int lane = tid & 31, warp = tid >> 5;
   for (int off = 16; off > 0; off >>= 1) {
@@ -433,73 +451,85 @@ __global__ void __launch_bounds__(JAM_THREADS) k_kin_adj(const SysDev *__restric
     if (aI0[k] != 0.0f) atomicAdd(&gw.adjI0[(size_t)b * max_light + k], (double)aI0[k]);
 }
 
-#define ADJ_EPT 4          // table entries per thread
 #define ADJ_THREADS 256
-#define ADJ_PCHUNK 512     // sky points per shared-memory chunk
+#define ADJ_PCHUNK 256     // sky points per shared-memory chunk
 
 // d logL / d (Q0, Q1, a_y) of each table entry: sums over every sky point of
-// g_N(s) E(s) {1, X, (Q0 + Q1 X) Y} with E = 2^(ax X + ay Y).
+// g_N(s) E(s) {1, X, (Q0 + Q1 X) Y} with E = 2^(ax X + ay Y).  Each thread owns EPT entries,
+// handled as EPT/2 packed pairs against the pre-duplicated point data.
+template <int EPT>
 __global__ void __launch_bounds__(ADJ_THREADS) k_jam_adj(const SysDev *__restrict__ sysv,
                                                          const int *__restrict__ sys_id, WsDev ws,
                                                          GradWs gw, int max_ent, int max_sub) {
+  constexpr int NP = EPT / 2;
   const int b = blockIdx.y;
   if (ws.status[b] != GLAD_SAMPLE_OK) return;
   const SysDev &S = sysv[sys_id[b]];
-  const int e0 = blockIdx.x * ADJ_THREADS * ADJ_EPT;
+  const int e0 = blockIdx.x * ADJ_THREADS * EPT;
   if (e0 >= S.n_ent) return;
-  __shared__ float4 pts[2][ADJ_PCHUNK];
+  __shared__ float4 pts[2][2 * ADJ_PCHUNK];
   const int tid = threadIdx.x;
-  float ax[ADJ_EPT], ay[ADJ_EPT];
-  float s0[ADJ_EPT], sx[ADJ_EPT], sy[ADJ_EPT], sxy[ADJ_EPT];
-  double S0[ADJ_EPT], SX[ADJ_EPT], SY[ADJ_EPT], SXY[ADJ_EPT];
+  // entry pair p of the thread: entries e0 + tid + (2p) * T and e0 + tid + (2p+1) * T
+  float2 ax[NP], ay[NP], s0[NP], sx[NP], sy[NP], sxy[NP];
+  double S0[EPT], SX[EPT], SY[EPT], SXY[EPT];
   const float4 *gt = ws.tab + (size_t)b * max_ent;
+  const float2 z2 = make_float2(0.f, 0.f);
 #pragma unroll
-  for (int k = 0; k < ADJ_EPT; ++k) {
-    const int e = e0 + tid + k * ADJ_THREADS;
-    const float4 c = e < S.n_ent ? gt[e] : make_float4(0.f, 0.f, 0.f, 0.f);
-    ax[k] = c.x;
-    ay[k] = c.y;
-    s0[k] = sx[k] = sy[k] = sxy[k] = 0.0f;
-    S0[k] = SX[k] = SY[k] = SXY[k] = 0.0;
+  for (int p = 0; p < NP; ++p) {
+    const int ea = e0 + tid + (2 * p) * ADJ_THREADS, eb = ea + ADJ_THREADS;
+    const float4 ca = ea < S.n_ent ? gt[ea] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 cb = eb < S.n_ent ? gt[eb] : make_float4(0.f, 0.f, 0.f, 0.f);
+    ax[p] = make_float2(ca.x, cb.x);
+    ay[p] = make_float2(ca.y, cb.y);
+    s0[p] = sx[p] = sy[p] = sxy[p] = z2;
   }
-  const float4 *gp = gw.adjpt + (size_t)b * max_sub;
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) S0[k] = SX[k] = SY[k] = SXY[k] = 0.0;
+  const float4 *gp = gw.adjpt + 2 * (size_t)b * max_sub;
   const int n = S.n_sub;
   const int n_chunks = (n + ADJ_PCHUNK - 1) / ADJ_PCHUNK;
-  for (int i = tid; i < ADJ_PCHUNK; i += ADJ_THREADS)
-    pts[0][i] = i < n ? gp[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int i = tid; i < 2 * ADJ_PCHUNK; i += ADJ_THREADS) pts[0][i] = i < 2 * n ? gp[i] : z4;
   __syncthreads();
   for (int ch = 0; ch < n_chunks; ++ch) {
     const int cur = ch & 1;
     if (ch + 1 < n_chunks) {
-      const int base = (ch + 1) * ADJ_PCHUNK;
-      for (int i = tid; i < ADJ_PCHUNK; i += ADJ_THREADS)
-        pts[cur ^ 1][i] = base + i < n ? gp[base + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const int base = 2 * (ch + 1) * ADJ_PCHUNK;
+      for (int i = tid; i < 2 * ADJ_PCHUNK; i += ADJ_THREADS)
+        pts[cur ^ 1][i] = base + i < 2 * n ? gp[base + i] : z4;
     }
     const float4 *pp = pts[cur];
 #pragma unroll 2
     for (int i = 0; i < ADJ_PCHUNK; ++i) {
-      const float4 P = pp[i];  // X, Y, XY, g_N (g_N = 0 on padding)
+      const float4 A = pp[2 * i], Bq = pp[2 * i + 1];  // (X, X, Y, Y), (XY, XY, g, g)
+      const float2 X2 = make_float2(A.x, A.y), Y2 = make_float2(A.z, A.w);
+      const float2 XY2 = make_float2(Bq.x, Bq.y), G2 = make_float2(Bq.z, Bq.w);
 #pragma unroll
-      for (int k = 0; k < ADJ_EPT; ++k) {
-        const float tg = P.w * ex2(fmaf(ay[k], P.y, ax[k] * P.x));
-        s0[k] += tg;
-        sx[k] = fmaf(tg, P.x, sx[k]);
-        sy[k] = fmaf(tg, P.y, sy[k]);
-        sxy[k] = fmaf(tg, P.z, sxy[k]);
+      for (int p = 0; p < NP; ++p) {
+        const float2 arg = __ffma2_rn(ay[p], Y2, __fmul2_rn(ax[p], X2));
+        const float2 tg = __fmul2_rn(G2, make_float2(ex2(arg.x), ex2(arg.y)));
+        s0[p] = __fadd2_rn(s0[p], tg);
+        sx[p] = __ffma2_rn(tg, X2, sx[p]);
+        sy[p] = __ffma2_rn(tg, Y2, sy[p]);
+        sxy[p] = __ffma2_rn(tg, XY2, sxy[p]);
       }
     }
 #pragma unroll
-    for (int k = 0; k < ADJ_EPT; ++k) {
-      S0[k] += s0[k];
-      SX[k] += sx[k];
-      SY[k] += sy[k];
-      SXY[k] += sxy[k];
-      s0[k] = sx[k] = sy[k] = sxy[k] = 0.0f;
+    for (int p = 0; p < NP; ++p) {
+      S0[2 * p] += s0[p].x;
+      S0[2 * p + 1] += s0[p].y;
+      SX[2 * p] += sx[p].x;
+      SX[2 * p + 1] += sx[p].y;
+      SY[2 * p] += sy[p].x;
+      SY[2 * p + 1] += sy[p].y;
+      SXY[2 * p] += sxy[p].x;
+      SXY[2 * p + 1] += sxy[p].y;
+      s0[p] = sx[p] = sy[p] = sxy[p] = z2;
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int k = 0; k < ADJ_EPT; ++k) {
+  for (int k = 0; k < EPT; ++k) {
     const int e = e0 + tid + k * ADJ_THREADS;
     if (e >= S.n_ent) continue;
     const float4 c = gt[e];
@@ -742,7 +772,7 @@ cudaError_t grad_ws_ensure(glad_ctx *c, int B) {
   GradWs &w = *c->gws;
   const size_t b = B;
   const bool ok = galloc(w, w.resid, b * c->max_pix) && galloc(w, w.gpix, b * c->max_pix) &&
-                  galloc(w, w.pt, b * c->max_sub) && galloc(w, w.adjpt, b * c->max_sub) &&
+                  galloc(w, w.pt, b * c->max_sub) && galloc(w, w.adjpt, 2 * b * c->max_sub) &&
                   galloc(w, w.entadj, b * c->max_ent * 3) && galloc(w, w.adjI0, b * c->max_light);
   if (!ok) {
     grad_ws_free(c);
@@ -793,9 +823,14 @@ cudaError_t launch_grad(glad_ctx *c, const int *sys_id, const double *theta, int
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = GLAD_PROF(c, st, KID_GRAD_JAM_ADJ, ([&]() -> cudaError_t {
-    const int nb = (c->max_ent + ADJ_THREADS * ADJ_EPT - 1) / (ADJ_THREADS * ADJ_EPT);
-    k_jam_adj<<<dim3(nb, B), ADJ_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, g, c->max_ent,
-                                                   c->max_sub);
+    const int ept = c->tune.adj_ept;
+    const int nb = (c->max_ent + ADJ_THREADS * ept - 1) / (ADJ_THREADS * ept);
+    if (ept == 2)
+      k_jam_adj<2><<<dim3(nb, B), ADJ_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, g, c->max_ent,
+                                                        c->max_sub);
+    else
+      k_jam_adj<4><<<dim3(nb, B), ADJ_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, g, c->max_ent,
+                                                        c->max_sub);
     return cudaGetLastError();
   }()));
   if (e != cudaSuccess) return e;
@@ -808,6 +843,20 @@ cudaError_t launch_grad(glad_ctx *c, const int *sys_id, const double *theta, int
     return cudaGetLastError();
   }()));
   return e;
+}
+
+// the entry-parallel adjoint alone, with the context's current shape (for the autotuner)
+cudaError_t time_jam_adj(glad_ctx *c, const int *sys_id, int B, cudaStream_t st) {
+  GradWs &g = *c->gws;
+  const int ept = c->tune.adj_ept;
+  const int nb = (c->max_ent + ADJ_THREADS * ept - 1) / (ADJ_THREADS * ept);
+  if (ept == 2)
+    k_jam_adj<2><<<dim3(nb, B), ADJ_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, g, c->max_ent,
+                                                      c->max_sub);
+  else
+    k_jam_adj<4><<<dim3(nb, B), ADJ_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, g, c->max_ent,
+                                                      c->max_sub);
+  return cudaGetLastError();
 }
 
 void set_grad_smem_limit() {

@@ -19,13 +19,18 @@ __device__ __forceinline__ float ex2(float x) {
   return y;
 }
 
+// PTS sky points per thread, processed as PTS/2 packed pairs: one FFMA2/FMUL2 issues the
+// arithmetic of two points, so an evaluation costs ~3 issue slots next to its MUFU.EX2.
+template <int PTS>
 __global__ void __launch_bounds__(JAM_THREADS) k_jam(const SysDev *__restrict__ sysv,
                                                      const int *__restrict__ sys_id, WsDev ws,
                                                      int max_light, int max_ent, int max_bins) {
+  constexpr int NP = PTS / 2;
+  constexpr int TILE = JAM_THREADS * PTS;
   const int b = blockIdx.y;
   if (ws.status[b] != GLAD_SAMPLE_OK) return;
   const SysDev &S = sysv[sys_id[b]];
-  const int tile0 = blockIdx.x * JAM_TILE;
+  const int tile0 = blockIdx.x * TILE;
   if (tile0 >= S.n_sub) return;
   __shared__ float4 tab[2][JAM_CHUNK];
   __shared__ float bnum[GLAD_MAX_BINS], bden[GLAD_MAX_BINS];
@@ -41,25 +46,31 @@ __global__ void __launch_bounds__(JAM_THREADS) k_jam(const SysDev *__restrict__ 
     scx[k] = S.sb_cx[k];
     scy[k] = S.sb_cy[k];
   }
-  // sky points of this thread (strided so that neighbouring threads are neighbours)
-  float X[JAM_PTS], Y[JAM_PTS];
-  float acc[JAM_PTS];
-  double accd[JAM_PTS];
+  // sky points of this thread (strided so that neighbouring threads are neighbours):
+  // point i of the thread is tile0 + tid + i * JAM_THREADS; pair p holds points 2p, 2p+1
+  float2 X[NP], Y[NP], acc[NP];
+  double accd[PTS];
   const float cphi = (float)dp.cphi, sphi = (float)dp.sphi;
   const float xc = (float)dp.xc, yc = (float)dp.yc;
 #pragma unroll
-  for (int i = 0; i < JAM_PTS; ++i) {
+  for (int i = 0; i < PTS; ++i) {
     const int s = tile0 + tid + i * JAM_THREADS;
     const int si = s < S.n_sub ? s : 0;
     const int I = si / S.nsx, J = si - I * S.nsx;
     const float x = (J - 0.5f * (S.nsx - 1)) * S.dsub - xc;
     const float y = (I - 0.5f * (S.nsy - 1)) * S.dsub - yc;
     const float xp = cphi * x + sphi * y, yp = -sphi * x + cphi * y;
-    X[i] = xp * xp;
-    Y[i] = yp * yp;
-    acc[i] = 0.0f;
+    if (i & 1) {
+      X[i >> 1].y = xp * xp;
+      Y[i >> 1].y = yp * yp;
+    } else {
+      X[i >> 1].x = xp * xp;
+      Y[i >> 1].x = yp * yp;
+    }
     accd[i] = 0.0;
   }
+#pragma unroll
+  for (int p = 0; p < NP; ++p) acc[p] = make_float2(0.f, 0.f);
   const float4 *gt = ws.tab + (size_t)b * max_ent;
   const int n_ent = S.n_ent;
   const int n_chunks = (n_ent + JAM_CHUNK - 1) / JAM_CHUNK;
@@ -76,29 +87,35 @@ __global__ void __launch_bounds__(JAM_THREADS) k_jam(const SysDev *__restrict__ 
         tab[cur ^ 1][e] = base + e < n_ent ? gt[base + e] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     const float4 *t = tab[cur];
-#pragma unroll 4
+#pragma unroll 2
     for (int e = 0; e < JAM_CHUNK; ++e) {
       const float4 c = t[e];
+      const float2 cx = make_float2(c.x, c.x), cy = make_float2(c.y, c.y);
+      const float2 cz = make_float2(c.z, c.z), cw = make_float2(c.w, c.w);
 #pragma unroll
-      for (int i = 0; i < JAM_PTS; ++i) {
-        const float E = ex2(fmaf(c.y, Y[i], c.x * X[i]));
-        acc[i] = fmaf(fmaf(c.w, X[i], c.z), E, acc[i]);
+      for (int p = 0; p < NP; ++p) {
+        const float2 arg = __ffma2_rn(cy, Y[p], __fmul2_rn(cx, X[p]));
+        const float2 E = make_float2(ex2(arg.x), ex2(arg.y));
+        acc[p] = __ffma2_rn(__ffma2_rn(cw, X[p], cz), E, acc[p]);
       }
     }
 #pragma unroll
-    for (int i = 0; i < JAM_PTS; ++i) {
-      accd[i] += (double)acc[i];
-      acc[i] = 0.0f;
+    for (int p = 0; p < NP; ++p) {
+      accd[2 * p] += (double)acc[p].x;
+      accd[2 * p + 1] += (double)acc[p].y;
+      acc[p] = make_float2(0.f, 0.f);
     }
     __syncthreads();
   }
   // tracer surface brightness and the binning-after-PSF scatter
 #pragma unroll
-  for (int i = 0; i < JAM_PTS; ++i) {
+  for (int i = 0; i < PTS; ++i) {
     const int s = tile0 + tid + i * JAM_THREADS;
     if (s >= S.n_sub) continue;
+    const float Xi = (i & 1) ? X[i >> 1].y : X[i >> 1].x;
+    const float Yi = (i & 1) ? Y[i >> 1].y : Y[i >> 1].x;
     float sb = 0.0f;
-    for (int k = 0; k < S.n_light; ++k) sb = fmaf(sI0[k], ex2(-fmaf(scy[k], Y[i], scx[k] * X[i])), sb);
+    for (int k = 0; k < S.n_light; ++k) sb = fmaf(sI0[k], ex2(-fmaf(scy[k], Yi, scx[k] * Xi)), sb);
     const float v = (float)accd[i];
     for (int e = S.w_off[s]; e < S.w_off[s + 1]; ++e) {
       const int l = S.w_bin[e];
@@ -162,9 +179,23 @@ __global__ void k_combine(WsDev ws, int B, double *logL, int *status, double *te
 }  // namespace
 
 cudaError_t launch_jam(glad_ctx *c, const int *sys_id, int B, cudaStream_t st) {
-  dim3 grid(c->max_sky_tiles, B);
-  k_jam<<<grid, JAM_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_light, c->max_ent,
-                                      c->max_bins);
+  const int pts = c->tune.jam_pts;
+  const int tiles = (c->max_sub + JAM_THREADS * pts - 1) / (JAM_THREADS * pts);
+  dim3 grid(tiles, B);
+  switch (pts) {
+    case 4:
+      k_jam<4><<<grid, JAM_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_light, c->max_ent,
+                                             c->max_bins);
+      break;
+    case 16:
+      k_jam<16><<<grid, JAM_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_light, c->max_ent,
+                                              c->max_bins);
+      break;
+    default:
+      k_jam<8><<<grid, JAM_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_light, c->max_ent,
+                                             c->max_bins);
+      break;
+  }
   return cudaGetLastError();
 }
 

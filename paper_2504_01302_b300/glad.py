@@ -134,6 +134,15 @@ class GladContext:
         _lib.check(self.lib.glad_vrms(self.handle, sys, _dptr(theta), _dptr(v), _stream()), "glad_vrms")
         return v
 
+    def autotune(self, theta, sys_id=None, with_grad=False):
+        """Time the JAM launch shapes on this batch and keep the fastest (glad_autotune)."""
+        theta, sys_id, B = self._check_theta(theta, sys_id)
+        _lib.check(self.lib.glad_autotune(self.handle, _dptr(sys_id), _dptr(theta), B,
+                                          1 if with_grad else 0, _stream()), "glad_autotune")
+        a, b = C.c_int(), C.c_int()
+        self.lib.glad_tuning(self.handle, C.byref(a), C.byref(b))
+        return {"jam_pts": a.value, "adj_ept": b.value}
+
     def kernel_times(self):
         """{kernel name: (ms, launches)} recorded since profiling was enabled."""
         n = self.lib.glad_kernel_times(self.handle, 0, None, None)
