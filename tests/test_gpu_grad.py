@@ -82,7 +82,8 @@ def test_autograd_function(small):
     w = torch.tensor([0.3, -1.7], dtype=torch.float64, device="cuda")
     (GladLogL.apply(th, ctx) * w).sum().backward()
     _, g, _ = ctx.loglike_grad(th.detach())
-    assert torch.allclose(th.grad, w[:, None] * g, rtol=1e-6, atol=0)  # atomics reorder between calls
+    # FP64 atomics reorder between the two calls: compare with a floor at the gradient scale
+    assert torch.allclose(th.grad, w[:, None] * g, rtol=1e-6, atol=1e-7 * float(g.abs().max()))
 
 
 def test_grad_mixed_systems():
