@@ -167,13 +167,15 @@ glad_status glad_loglike_static(glad_ctx *ctx, const int *sys_id, const double *
                                 double *logL, int *sample_status, double *terms, void *stream);
 
 /* Autotuner (the project's own, no counterpart in the paper): times the candidate
- * launch shapes of the JAM kernels -- sky points per thread of the pair sum (4, 8, 16)
+ * launch shapes of the JAM kernels -- sky points per thread of the pair sum (4, 8, 16,
+ * and for 8 register caps allowing 5 or 6 CTAs per SM)
  * and, with with_grad, table entries per thread of its adjoint (2, 4) -- on this batch
  * (arguments as glad_loglike), keeps the fastest in the context for later calls, and
  * when the environment variable GLAD_TUNE_CACHE names a file, appends the choice there
  * keyed by device name and batch shape (later calls with the same key read it back and
  * skip the timing).  Synchronises the stream; allocates a few small scratch arrays.
- * glad_tuning reports the current choice. */
+ * glad_tuning reports the current choice: *jam_pts = 100 * points per thread + the
+ * minimum CTAs per SM the variant was compiled for, *adj_ept = entries per thread. */
 glad_status glad_autotune(glad_ctx *ctx, const int *sys_id, const double *theta, int B,
                           int with_grad, void *stream);
 int glad_tuning(glad_ctx *ctx, int *jam_pts, int *adj_ept);

@@ -128,6 +128,7 @@ struct glad_ctx {
   // launch shapes chosen by glad_autotune (defaults until it runs)
   struct Tune {
     int jam_pts = 8;      // sky points per thread in the JAM pair-sum kernels
+    int jam_minb = 1;     // minimum resident CTAs per SM requested from the compiler (8 points)
     int adj_ept = 4;      // table entries per thread in the JAM adjoint
   } tune;
   int *d_one_sys = nullptr;      // scratch sys id for single-sample calls

@@ -1,5 +1,6 @@
 // Autotuner for the launch shapes of the JAM kernels: sky points per thread of the
-// pair-sum kernel (4, 8, 16) and table entries per thread of its adjoint (2, 4).  Each
+// pair-sum kernel (4, 8, 16; for 8 also a register cap that allows 5 or 6 CTAs per SM)
+// and table entries per thread of its adjoint (2, 4).  Each
 // candidate is timed with CUDA events on the caller's batch; the fastest is kept in the
 // context and, when GLAD_TUNE_CACHE names a file, stored there keyed by the batch shape
 // and the device name so later processes skip the timing.
@@ -86,8 +87,10 @@ extern "C" glad_status glad_autotune(glad_ctx *c, const int *sys_id, const doubl
   cudaStream_t st = (cudaStream_t)stream;
   const std::string key = tune_key(c, B);
   int pts = 8, ept = 4;
-  if (cache_lookup(key, &pts, &ept)) {
-    c->tune.jam_pts = pts;
+  int code = 0;
+  if (cache_lookup(key, &code, &ept)) {
+    c->tune.jam_pts = code / 100;
+    c->tune.jam_minb = code % 100;
     c->tune.adj_ept = ept;
     return GLAD_OK;
   }
@@ -111,17 +114,22 @@ extern "C" glad_status glad_autotune(glad_ctx *c, const int *sys_id, const doubl
   s = with_grad ? glad_loglike_grad(c, sys_id, theta, B, logL, grad, status, nullptr, stream)
                 : glad_loglike(c, sys_id, theta, B, logL, status, nullptr, stream);
   if (s == GLAD_OK) {
-    const int cand_pts[3] = {4, 8, 16};
+    // (points per thread, minimum CTAs per SM asked of the register allocator)
+    const int cand[5][2] = {{4, 1}, {8, 1}, {8, 5}, {8, 6}, {16, 1}};
     float best = 1e30f;
-    for (int p : cand_pts) {
-      c->tune.jam_pts = p;
+    int minb = 1;
+    for (auto &cd : cand) {
+      c->tune.jam_pts = cd[0];
+      c->tune.jam_minb = cd[1];
       const float ms = time_ms(st, [&]() { launch_jam(c, sys_id, B, st); }, 2);
       if (ms < best) {
         best = ms;
-        pts = p;
+        pts = cd[0];
+        minb = cd[1];
       }
     }
     c->tune.jam_pts = pts;
+    c->tune.jam_minb = minb;
     if (with_grad) {
       const int cand_ept[2] = {2, 4};
       best = 1e30f;
@@ -137,7 +145,7 @@ extern "C" glad_status glad_autotune(glad_ctx *c, const int *sys_id, const doubl
     }
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) s = glad_set_error(GLAD_ECUDA, cudaGetErrorString(e));
-    else cache_store(key, pts, ept);
+    else cache_store(key, c->tune.jam_pts * 100 + c->tune.jam_minb, c->tune.adj_ept);
   }
   cudaFree(logL);
   cudaFree(status);
@@ -147,7 +155,7 @@ extern "C" glad_status glad_autotune(glad_ctx *c, const int *sys_id, const doubl
 
 extern "C" int glad_tuning(glad_ctx *c, int *jam_pts, int *adj_ept) {
   if (!c) return -1;
-  if (jam_pts) *jam_pts = c->tune.jam_pts;
+  if (jam_pts) *jam_pts = c->tune.jam_pts * 100 + c->tune.jam_minb;
   if (adj_ept) *adj_ept = c->tune.adj_ept;
   return 0;
 }

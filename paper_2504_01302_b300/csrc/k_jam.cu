@@ -21,8 +21,8 @@ __device__ __forceinline__ float ex2(float x) {
 
 // PTS sky points per thread, processed as PTS/2 packed pairs: one FFMA2/FMUL2 issues the
 // arithmetic of two points, so an evaluation costs ~3 issue slots next to its MUFU.EX2.
-template <int PTS>
-__global__ void __launch_bounds__(JAM_THREADS) k_jam(const SysDev *__restrict__ sysv,
+template <int PTS, int MINB>
+__global__ void __launch_bounds__(JAM_THREADS, MINB) k_jam(const SysDev *__restrict__ sysv,
                                                      const int *__restrict__ sys_id, WsDev ws,
                                                      int max_light, int max_ent, int max_bins) {
   constexpr int NP = PTS / 2;
@@ -182,20 +182,16 @@ cudaError_t launch_jam(glad_ctx *c, const int *sys_id, int B, cudaStream_t st) {
   const int pts = c->tune.jam_pts;
   const int tiles = (c->max_sub + JAM_THREADS * pts - 1) / (JAM_THREADS * pts);
   dim3 grid(tiles, B);
-  switch (pts) {
-    case 4:
-      k_jam<4><<<grid, JAM_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_light, c->max_ent,
-                                             c->max_bins);
-      break;
-    case 16:
-      k_jam<16><<<grid, JAM_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_light, c->max_ent,
-                                              c->max_bins);
-      break;
-    default:
-      k_jam<8><<<grid, JAM_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_light, c->max_ent,
-                                             c->max_bins);
-      break;
-  }
+  const int minb = c->tune.jam_minb;
+#define GLAD_JAM_LAUNCH(P, M)                                                               \
+  k_jam<P, M><<<grid, JAM_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_light, c->max_ent, \
+                                            c->max_bins)
+  if (pts == 4) GLAD_JAM_LAUNCH(4, 1);
+  else if (pts == 16) GLAD_JAM_LAUNCH(16, 1);
+  else if (minb == 5) GLAD_JAM_LAUNCH(8, 5);
+  else if (minb == 6) GLAD_JAM_LAUNCH(8, 6);
+  else GLAD_JAM_LAUNCH(8, 1);
+#undef GLAD_JAM_LAUNCH
   return cudaGetLastError();
 }
 

@@ -18,7 +18,7 @@ def test_autotune_keeps_results(tmp_path, monkeypatch):
     before = ctx.loglike(th)[0].cpu().numpy()
     g_before = ctx.loglike_grad(th)[1].cpu().numpy()
     t = ctx.autotune(th, with_grad=True)
-    assert t["jam_pts"] in (4, 8, 16) and t["adj_ept"] in (2, 4)
+    assert t["jam_pts"] in (401, 801, 805, 806, 1601) and t["adj_ept"] in (2, 4)
     after = ctx.loglike(th)[0].cpu().numpy()
     g_after = ctx.loglike_grad(th)[1].cpu().numpy()
     assert np.all(np.abs(after - before) < 1e-6 * np.abs(before))
