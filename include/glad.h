@@ -174,11 +174,17 @@ glad_status glad_loglike_static(glad_ctx *ctx, const int *sys_id, const double *
  * when the environment variable GLAD_TUNE_CACHE names a file, appends the choice there
  * keyed by device name and batch shape (later calls with the same key read it back and
  * skip the timing).  Synchronises the stream; allocates a few small scratch arrays.
- * glad_tuning reports the current choice: *jam_pts = 100 * points per thread + the
- * minimum CTAs per SM the variant was compiled for, *adj_ept = entries per thread. */
+ * It also times the chosen shape as one persistent launch over a (sample, tile) work
+ * list and keeps that form when faster.  glad_tuning reports the current choice:
+ * *jam_pts = 10000 * persistent + 100 * points per thread + the minimum CTAs per SM the
+ * variant was compiled for; *adj_ept = entries per thread. */
 glad_status glad_autotune(glad_ctx *ctx, const int *sys_id, const double *theta, int B,
                           int with_grad, void *stream);
 int glad_tuning(glad_ctx *ctx, int *jam_pts, int *adj_ept);
+/* Pin a launch shape instead of tuning (codes as reported by glad_tuning; jam codes
+ * 401, 801, 805, 806, 1601, each optionally + 10000 for the persistent form; adj_ept 2
+ * or 4).  GLAD_EINVAL for other values. */
+glad_status glad_set_tuning(glad_ctx *ctx, int jam_code, int adj_ept);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *glad_last_error(void);

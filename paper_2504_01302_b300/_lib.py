@@ -49,6 +49,7 @@ SIGNATURES = {
     "glad_kernel_name": (C.c_char_p, [C.c_int]),
     "glad_autotune": (C.c_int, [_p, _p, _p, C.c_int, C.c_int, _p]),
     "glad_tuning": (C.c_int, [_p, _i, _i]),
+    "glad_set_tuning": (C.c_int, [_p, C.c_int, C.c_int]),
     "glad_last_error": (C.c_char_p, []),
 }
 

@@ -373,7 +373,8 @@ glad_status ws_ensure(glad_ctx *c, int B) {
             ws_alloc(w, w.d.Cj, b * c->max_mass_tot) && ws_alloc(w, w.d.e2, b * c->max_mass_tot) &&
             ws_alloc(w, w.d.I0f, b * c->max_light) && ws_alloc(w, w.d.tab, b * c->max_ent) &&
             ws_alloc(w, w.d.img, b * c->max_pix) && ws_alloc(w, w.d.binacc, b * c->max_bins * 2) &&
-            ws_alloc(w, w.d.terms, b * 3) && ws_alloc(w, w.d.status, b);
+            ws_alloc(w, w.d.terms, b * 3) && ws_alloc(w, w.d.status, b) &&
+            ws_alloc(w, w.d.wl_off, b + 1) && ws_alloc(w, w.d.wl_counter, 1);
   if (!ok) {
     ws_free(w);
     return fail(GLAD_ENOMEM, "workspace for B=%d does not fit on the device", B);

@@ -106,6 +106,8 @@ struct WsDev {
   double *binacc;              // [B*max_bins*2]
   double *terms;               // [B*3]
   int *status;                 // [B]
+  int *wl_off;                 // [B+1] persistent JAM work list (first item of each sample)
+  int *wl_counter;             // [1]   next work item
 };
 
 struct Workspace {
@@ -129,6 +131,7 @@ struct glad_ctx {
   struct Tune {
     int jam_pts = 8;      // sky points per thread in the JAM pair-sum kernels
     int jam_minb = 1;     // minimum resident CTAs per SM requested from the compiler (8 points)
+    int jam_persistent = 0;  // 1: one persistent launch over a (sample, tile) work list
     int adj_ept = 4;      // table entries per thread in the JAM adjoint
   } tune;
   int *d_one_sys = nullptr;      // scratch sys id for single-sample calls

@@ -89,8 +89,9 @@ extern "C" glad_status glad_autotune(glad_ctx *c, const int *sys_id, const doubl
   int pts = 8, ept = 4;
   int code = 0;
   if (cache_lookup(key, &code, &ept)) {
-    c->tune.jam_pts = code / 100;
+    c->tune.jam_pts = (code % 10000) / 100;
     c->tune.jam_minb = code % 100;
+    c->tune.jam_persistent = code / 10000;
     c->tune.adj_ept = ept;
     return GLAD_OK;
   }
@@ -130,6 +131,10 @@ extern "C" glad_status glad_autotune(glad_ctx *c, const int *sys_id, const doubl
     }
     c->tune.jam_pts = pts;
     c->tune.jam_minb = minb;
+    // the same shape as one persistent launch over the (sample, tile) work list
+    c->tune.jam_persistent = 1;
+    const float ms_p = time_ms(st, [&]() { launch_jam(c, sys_id, B, st); }, 2);
+    c->tune.jam_persistent = ms_p < best ? 1 : 0;
     if (with_grad) {
       const int cand_ept[2] = {2, 4};
       best = 1e30f;
@@ -145,7 +150,9 @@ extern "C" glad_status glad_autotune(glad_ctx *c, const int *sys_id, const doubl
     }
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) s = glad_set_error(GLAD_ECUDA, cudaGetErrorString(e));
-    else cache_store(key, c->tune.jam_pts * 100 + c->tune.jam_minb, c->tune.adj_ept);
+    else
+      cache_store(key, c->tune.jam_persistent * 10000 + c->tune.jam_pts * 100 + c->tune.jam_minb,
+                  c->tune.adj_ept);
   }
   cudaFree(logL);
   cudaFree(status);
@@ -155,7 +162,22 @@ extern "C" glad_status glad_autotune(glad_ctx *c, const int *sys_id, const doubl
 
 extern "C" int glad_tuning(glad_ctx *c, int *jam_pts, int *adj_ept) {
   if (!c) return -1;
-  if (jam_pts) *jam_pts = c->tune.jam_pts * 100 + c->tune.jam_minb;
+  if (jam_pts) *jam_pts = c->tune.jam_persistent * 10000 + c->tune.jam_pts * 100 + c->tune.jam_minb;
   if (adj_ept) *adj_ept = c->tune.adj_ept;
   return 0;
+}
+
+extern "C" glad_status glad_set_tuning(glad_ctx *c, int jam_code, int adj_ept) {
+  if (!c) return glad_set_error(GLAD_EINVAL, "glad_set_tuning: null context");
+  const int pers = jam_code / 10000, pts = (jam_code % 10000) / 100, minb = jam_code % 100;
+  const bool ok_jam = (pers == 0 || pers == 1) &&
+                      ((pts == 4 && minb == 1) || (pts == 16 && minb == 1) ||
+                       (pts == 8 && (minb == 1 || minb == 5 || minb == 6)));
+  if (!ok_jam || (adj_ept != 2 && adj_ept != 4))
+    return glad_set_error(GLAD_EINVAL, "glad_set_tuning: unsupported launch shape");
+  c->tune.jam_persistent = pers;
+  c->tune.jam_pts = pts;
+  c->tune.jam_minb = minb;
+  c->tune.adj_ept = adj_ept;
+  return GLAD_OK;
 }

@@ -19,32 +19,29 @@ __device__ __forceinline__ float ex2(float x) {
   return y;
 }
 
-// PTS sky points per thread, processed as PTS/2 packed pairs: one FFMA2/FMUL2 issues the
-// arithmetic of two points, so an evaluation costs ~3 issue slots next to its MUFU.EX2.
-template <int PTS, int MINB>
-__global__ void __launch_bounds__(JAM_THREADS, MINB) k_jam(const SysDev *__restrict__ sysv,
-                                                     const int *__restrict__ sys_id, WsDev ws,
-                                                     int max_light, int max_ent, int max_bins) {
+// One tile of TILE = 256 * PTS sky sub-samples of sample b.  PTS points per thread are
+// processed as PTS/2 packed pairs: one FFMA2/FMUL2 issues the arithmetic of two points, so
+// an evaluation costs ~3 issue slots next to its MUFU.EX2.
+struct JamSmem {
+  float4 tab[2][JAM_CHUNK];
+  float bnum[GLAD_MAX_BINS], bden[GLAD_MAX_BINS];
+  float sI0[GLAD_MAX_LIGHT], scx[GLAD_MAX_LIGHT], scy[GLAD_MAX_LIGHT];
+};
+
+template <int PTS>
+__device__ __forceinline__ void jam_tile(const SysDev &S, const WsDev &ws, JamSmem &sm, int b,
+                                         int tile0, int max_light, int max_ent, int max_bins) {
   constexpr int NP = PTS / 2;
-  constexpr int TILE = JAM_THREADS * PTS;
-  const int b = blockIdx.y;
-  if (ws.status[b] != GLAD_SAMPLE_OK) return;
-  const SysDev &S = sysv[sys_id[b]];
-  const int tile0 = blockIdx.x * TILE;
-  if (tile0 >= S.n_sub) return;
-  __shared__ float4 tab[2][JAM_CHUNK];
-  __shared__ float bnum[GLAD_MAX_BINS], bden[GLAD_MAX_BINS];
-  __shared__ float sI0[GLAD_MAX_LIGHT], scx[GLAD_MAX_LIGHT], scy[GLAD_MAX_LIGHT];
   const int tid = threadIdx.x;
   const DynP dp = ws.dp[b];
   for (int l = tid; l < S.n_bins; l += JAM_THREADS) {
-    bnum[l] = 0.0f;
-    bden[l] = 0.0f;
+    sm.bnum[l] = 0.0f;
+    sm.bden[l] = 0.0f;
   }
   for (int k = tid; k < S.n_light; k += JAM_THREADS) {
-    sI0[k] = ws.I0f[(size_t)b * max_light + k];
-    scx[k] = S.sb_cx[k];
-    scy[k] = S.sb_cy[k];
+    sm.sI0[k] = ws.I0f[(size_t)b * max_light + k];
+    sm.scx[k] = S.sb_cx[k];
+    sm.scy[k] = S.sb_cy[k];
   }
   // sky points of this thread (strided so that neighbouring threads are neighbours):
   // point i of the thread is tile0 + tid + i * JAM_THREADS; pair p holds points 2p, 2p+1
@@ -76,7 +73,7 @@ __global__ void __launch_bounds__(JAM_THREADS, MINB) k_jam(const SysDev *__restr
   const int n_chunks = (n_ent + JAM_CHUNK - 1) / JAM_CHUNK;
   // prologue: chunk 0
   for (int e = tid; e < JAM_CHUNK; e += JAM_THREADS)
-    tab[0][e] = e < n_ent ? gt[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+    sm.tab[0][e] = e < n_ent ? gt[e] : make_float4(0.f, 0.f, 0.f, 0.f);
   __syncthreads();
   for (int ch = 0; ch < n_chunks; ++ch) {
     const int cur = ch & 1;
@@ -84,9 +81,9 @@ __global__ void __launch_bounds__(JAM_THREADS, MINB) k_jam(const SysDev *__restr
     if (ch + 1 < n_chunks) {
       const int base = (ch + 1) * JAM_CHUNK;
       for (int e = tid; e < JAM_CHUNK; e += JAM_THREADS)
-        tab[cur ^ 1][e] = base + e < n_ent ? gt[base + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+        sm.tab[cur ^ 1][e] = base + e < n_ent ? gt[base + e] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    const float4 *t = tab[cur];
+    const float4 *t = sm.tab[cur];
 #pragma unroll 2
     for (int e = 0; e < JAM_CHUNK; ++e) {
       const float4 c = t[e];
@@ -115,20 +112,104 @@ __global__ void __launch_bounds__(JAM_THREADS, MINB) k_jam(const SysDev *__restr
     const float Xi = (i & 1) ? X[i >> 1].y : X[i >> 1].x;
     const float Yi = (i & 1) ? Y[i >> 1].y : Y[i >> 1].x;
     float sb = 0.0f;
-    for (int k = 0; k < S.n_light; ++k) sb = fmaf(sI0[k], ex2(-fmaf(scy[k], Yi, scx[k] * Xi)), sb);
+    for (int k = 0; k < S.n_light; ++k)
+      sb = fmaf(sm.sI0[k], ex2(-fmaf(sm.scy[k], Yi, sm.scx[k] * Xi)), sb);
     const float v = (float)accd[i];
     for (int e = S.w_off[s]; e < S.w_off[s + 1]; ++e) {
       const int l = S.w_bin[e];
       const float w = S.w_val[e];
-      atomicAdd(&bnum[l], w * v);
-      atomicAdd(&bden[l], w * sb);
+      atomicAdd(&sm.bnum[l], w * v);
+      atomicAdd(&sm.bden[l], w * sb);
     }
   }
   __syncthreads();
   double *acc_g = ws.binacc + (size_t)b * max_bins * 2;
   for (int l = tid; l < S.n_bins; l += JAM_THREADS) {
-    if (bnum[l] != 0.0f) atomicAdd(&acc_g[2 * l], (double)bnum[l]);
-    if (bden[l] != 0.0f) atomicAdd(&acc_g[2 * l + 1], (double)bden[l]);
+    if (sm.bnum[l] != 0.0f) atomicAdd(&acc_g[2 * l], (double)sm.bnum[l]);
+    if (sm.bden[l] != 0.0f) atomicAdd(&acc_g[2 * l + 1], (double)sm.bden[l]);
+  }
+  __syncthreads();  // the shared arrays are reused by the next tile of a persistent CTA
+}
+
+// one CTA per (tile, sample) of the largest system; tiles beyond a sample's system exit
+template <int PTS, int MINB>
+__global__ void __launch_bounds__(JAM_THREADS, MINB) k_jam(const SysDev *__restrict__ sysv,
+                                                           const int *__restrict__ sys_id, WsDev ws,
+                                                           int max_light, int max_ent, int max_bins) {
+  const int b = blockIdx.y;
+  if (ws.status[b] != GLAD_SAMPLE_OK) return;
+  const SysDev &S = sysv[sys_id[b]];
+  const int tile0 = blockIdx.x * (JAM_THREADS * PTS);
+  if (tile0 >= S.n_sub) return;
+  __shared__ JamSmem sm;
+  jam_tile<PTS>(S, ws, sm, b, tile0, max_light, max_ent, max_bins);
+}
+
+// Work list for the persistent form: wl_off[b] = first item of sample b, wl_off[B] = total,
+// items of a sample = its tiles (none for invalid samples).  One CTA; resets the counter.
+__global__ void k_worklist(const SysDev *__restrict__ sysv, const int *__restrict__ sys_id,
+                           WsDev ws, int B, int tile) {
+  __shared__ int part[1024];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < B; base += blockDim.x) {
+    const int b = base + threadIdx.x;
+    int n = 0;
+    if (b < B && ws.status[b] == GLAD_SAMPLE_OK) n = (sysv[sys_id[b]].n_sub + tile - 1) / tile;
+    part[threadIdx.x] = n;
+    __syncthreads();
+    // inclusive scan (Hillis-Steele) over the block
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+      const int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+      __syncthreads();
+      part[threadIdx.x] += v;
+      __syncthreads();
+    }
+    if (b < B) ws.wl_off[b] = carry + part[threadIdx.x] - n;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry += part[threadIdx.x];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    ws.wl_off[B] = carry;
+    *ws.wl_counter = 0;
+  }
+}
+
+// Persistent form: a fixed grid of SM-count x occupancy CTAs takes (sample, tile) items
+// from a global counter until the list is exhausted, so uneven batches leave no idle slots.
+template <int PTS, int MINB>
+__global__ void __launch_bounds__(JAM_THREADS, MINB) k_jam_persist(
+    const SysDev *__restrict__ sysv, const int *__restrict__ sys_id, WsDev ws, int B,
+    int max_light, int max_ent, int max_bins) {
+  __shared__ JamSmem sm;
+  __shared__ int item_s, b_s;
+  const int total = ws.wl_off[B];
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int it = atomicAdd(ws.wl_counter, 1);
+      int bb = -1;
+      if (it < total) {
+        // last sample whose first item is <= it
+        int lo = 0, hi = B - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (ws.wl_off[mid] <= it) lo = mid;
+          else hi = mid - 1;
+        }
+        bb = lo;
+      }
+      item_s = it;
+      b_s = bb;
+    }
+    __syncthreads();
+    const int it = item_s, b = b_s;
+    __syncthreads();
+    if (b < 0) return;
+    const SysDev &S = sysv[sys_id[b]];
+    const int tile0 = (it - ws.wl_off[b]) * (JAM_THREADS * PTS);
+    jam_tile<PTS>(S, ws, sm, b, tile0, max_light, max_ent, max_bins);
   }
 }
 
@@ -180,9 +261,30 @@ __global__ void k_combine(WsDev ws, int B, double *logL, int *status, double *te
 
 cudaError_t launch_jam(glad_ctx *c, const int *sys_id, int B, cudaStream_t st) {
   const int pts = c->tune.jam_pts;
+  const int minb = c->tune.jam_minb;
+  if (c->tune.jam_persistent && c->ws.d.wl_off) {
+    k_worklist<<<1, 1024, 0, st>>>(c->d_sys, sys_id, c->ws.d, B, JAM_THREADS * pts);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+#define GLAD_JAM_PERSIST(P, M)                                                                \
+  do {                                                                                        \
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jam_persist<P, M>, JAM_THREADS, 0); \
+    k_jam_persist<P, M><<<nsm * (occ > 0 ? occ : 1), JAM_THREADS, 0, st>>>(                   \
+        c->d_sys, sys_id, c->ws.d, B, c->max_light, c->max_ent, c->max_bins);                 \
+  } while (0)
+    if (pts == 4) GLAD_JAM_PERSIST(4, 1);
+    else if (pts == 16) GLAD_JAM_PERSIST(16, 1);
+    else if (minb == 5) GLAD_JAM_PERSIST(8, 5);
+    else if (minb == 6) GLAD_JAM_PERSIST(8, 6);
+    else GLAD_JAM_PERSIST(8, 1);
+#undef GLAD_JAM_PERSIST
+    return cudaGetLastError();
+  }
   const int tiles = (c->max_sub + JAM_THREADS * pts - 1) / (JAM_THREADS * pts);
   dim3 grid(tiles, B);
-  const int minb = c->tune.jam_minb;
 #define GLAD_JAM_LAUNCH(P, M)                                                               \
   k_jam<P, M><<<grid, JAM_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_light, c->max_ent, \
                                             c->max_bins)

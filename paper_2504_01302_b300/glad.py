@@ -143,6 +143,10 @@ class GladContext:
         self.lib.glad_tuning(self.handle, C.byref(a), C.byref(b))
         return {"jam_pts": a.value, "adj_ept": b.value}
 
+    def set_tuning(self, jam_code, adj_ept):
+        """Pin the JAM launch shapes (glad_set_tuning)."""
+        _lib.check(self.lib.glad_set_tuning(self.handle, int(jam_code), int(adj_ept)), "glad_set_tuning")
+
     def kernel_times(self):
         """{kernel name: (ms, launches)} recorded since profiling was enabled."""
         n = self.lib.glad_kernel_times(self.handle, 0, None, None)
