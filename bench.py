@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--grad", action="store_true", help="time logL + gradient (batch 64)")
     p.add_argument("--batch", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--graph", type=int, default=-1,
+                   help="1: replay the step as a captured CUDA graph (default: on for workload 3)")
     return p.parse_args()
 
 
@@ -207,6 +209,13 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def names_idx(name, lib, nk):
+    for i in range(nk):
+        if lib.glad_kernel_name(i).decode() == name:
+            return i
+    raise KeyError(name)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -261,21 +270,42 @@ def main():
     n_valid = int((status == 0).sum())
 
     # ---- device-resident timing: K steps, events on the launching stream
+    use_graph = args.graph == 1 or (args.graph == -1 and w == 3)
+    graph = None
+    if use_graph:
+        # the whole step (every kernel of the path) captured once and replayed
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        torch.cuda.synchronize()
+        graph.replay()
+        torch.cuda.synchronize()
     nk = lib.glad_kernel_times(ctx.handle, 0, None, None)
     kms = (C.c_double * nk)()
     kl = (C.c_int * nk)()
-    lib.glad_profile(ctx.handle, 1)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
+    if not use_graph:
+        lib.glad_profile(ctx.handle, 1)
     with ClockSampler(local) as clk:
         for k in range(args.steps):
             flush.fill_(float(k))
             ev[k][0].record(stream)
-            step()
+            if use_graph:
+                graph.replay()
+            else:
+                step()
             ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    if use_graph:
+        # per-kernel times from separate profiled (non-graph) steps
+        lib.glad_profile(ctx.handle, 1)
+        for k in range(min(args.steps, 3)):
+            flush.fill_(float(k))
+            step()
         torch.cuda.synchronize()
     lib.glad_profile(ctx.handle, 0)
     lib.glad_kernel_times(ctx.handle, nk, kms, kl)
@@ -321,6 +351,12 @@ def main():
             dist.destroy_process_group()
         return
 
+    prof_steps = min(args.steps, 3) if use_graph else args.steps
+    extra = kl[names_idx("k_image+k_conv", lib, nk)] + kl[names_idx("k_grad_lens", lib, nk)] + \
+        (kl[names_idx("k_jam", lib, nk)] if tuning["jam_pts"] >= 10000 else 0)
+    launches_per_step = (int(sum(kl[i] for i in range(nk))) + int(extra)) // max(prof_steps, 1)
+    if args.grad:
+        launches_per_step += 2  # k_kin_adj and k_grad_zero_invalid run untimed by the profiler
     # ---- roofline of the dominant kernel (JAM pair sum): integrand evaluations per launch,
     # one ex2 each, against the MUFU ex2 rate
     names = [lib.glad_kernel_name(i).decode() for i in range(nk)]
@@ -347,7 +383,7 @@ def main():
         "config": {"workload": workload_name(w, args.grad, B), "batch_per_gpu": B,
                    "precision": "f32 bulk; f64 MGE, tables and chi^2 reductions",
                    "l2": "flushed (256 MB write) before each timed step", "valid_samples": n_valid,
-                   "tuning": tuning},
+                   "tuning": tuning, "cuda_graph": bool(use_graph)},
         "roofline": {"bound": "alu", "kernel": names[jam_id], "achieved": achieved, "peak": peak,
                      "unit": "Gexp2/s", "frac": achieved / peak, "traffic": None,
                      "algorithmic_units": f"{evals} JAM integrand evaluations per launch (1 ex2 each)",
@@ -356,8 +392,10 @@ def main():
         "kernels_ms_per_step": per_kernel,
         "e2e": {"value": world * B * args.steps / (e2e_ms / 1000.0), "unit": unit,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        # k_image and k_conv are timed as one unit: count both launches
-        "gpu_launches": int(sum(kl[i] for i in range(nk))) + int(kl[names.index("k_image+k_conv")]),
+        # launches of the library's kernels inside the timed region (per-step count from the
+        # profiled steps: k_image and k_conv are one timed unit, the gradient's lensing unit
+        # is k_conv_adj + k_image_grad, the persistent JAM form adds k_worklist)
+        "gpu_launches": args.steps * launches_per_step,
         "clocks": clocks,
     }
     if not args.no_cpu_baseline and world == 1:
