@@ -249,10 +249,11 @@ def main():
     status = torch.empty(B, dtype=torch.int32, device="cuda")
     grad = torch.empty(B, 20, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
-    hs = C.c_void_p(stream.cuda_stream)
     P = lambda t: C.c_void_p(t.data_ptr())
 
     def step():
+        # the stream current at call time: torch.cuda.graph captures on its own stream
+        hs = C.c_void_p(torch.cuda.current_stream().cuda_stream)
         if args.grad:
             rc = lib.glad_loglike_grad(ctx.handle, P(sid), P(theta), B, P(logL), P(grad), P(status),
                                        None, hs)
@@ -278,8 +279,11 @@ def main():
         with torch.cuda.graph(graph):
             step()
         torch.cuda.synchronize()
+        logL.fill_(0.0)
         graph.replay()
         torch.cuda.synchronize()
+        # the replay must reproduce the eager step's results
+        assert int((status == 0).sum()) == n_valid and bool(torch.isfinite(logL[status == 0]).all())
     nk = lib.glad_kernel_times(ctx.handle, 0, None, None)
     kms = (C.c_double * nk)()
     kl = (C.c_int * nk)()

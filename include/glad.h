@@ -167,8 +167,8 @@ glad_status glad_loglike_static(glad_ctx *ctx, const int *sys_id, const double *
                                 double *logL, int *sample_status, double *terms, void *stream);
 
 /* Autotuner (the project's own, no counterpart in the paper): times the candidate
- * launch shapes of the JAM kernels -- sky points per thread of the pair sum (4, 8, 16,
- * and for 8 register caps allowing 5 or 6 CTAs per SM)
+ * launch shapes of the JAM kernels -- (sky points per thread, minimum resident CTAs per SM)
+ * of the pair sum: (4,6), (8,3), (8,4), (8,5), (16,2)
  * and, with with_grad, table entries per thread of its adjoint (2, 4) -- on this batch
  * (arguments as glad_loglike), keeps the fastest in the context for later calls, and
  * when the environment variable GLAD_TUNE_CACHE names a file, appends the choice there
@@ -182,7 +182,7 @@ glad_status glad_autotune(glad_ctx *ctx, const int *sys_id, const double *theta,
                           int with_grad, void *stream);
 int glad_tuning(glad_ctx *ctx, int *jam_pts, int *adj_ept);
 /* Pin a launch shape instead of tuning (codes as reported by glad_tuning; jam codes
- * 401, 801, 805, 806, 1601, each optionally + 10000 for the persistent form; adj_ept 2
+ * 406, 803, 804, 805, 1602, each optionally + 10000 for the persistent form; adj_ept 2
  * or 4).  GLAD_EINVAL for other values. */
 glad_status glad_set_tuning(glad_ctx *ctx, int jam_code, int adj_ept);
 

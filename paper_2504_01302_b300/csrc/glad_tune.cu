@@ -1,6 +1,7 @@
 // Autotuner for the launch shapes of the JAM kernels: sky points per thread of the
-// pair-sum kernel (4, 8, 16; for 8 also a register cap that allows 5 or 6 CTAs per SM)
-// and table entries per thread of its adjoint (2, 4).  Each
+// pair-sum kernel with a register cap for a minimum number of resident CTAs per SM
+// (the candidate list in k_jam.cu), grid or persistent form, and table entries per
+// thread of its adjoint (2, 4).  Each
 // candidate is timed with CUDA events on the caller's batch; the fastest is kept in the
 // context and, when GLAD_TUNE_CACHE names a file, stored there keyed by the batch shape
 // and the device name so later processes skip the timing.
@@ -116,10 +117,12 @@ extern "C" glad_status glad_autotune(glad_ctx *c, const int *sys_id, const doubl
                 : glad_loglike(c, sys_id, theta, B, logL, status, nullptr, stream);
   if (s == GLAD_OK) {
     // (points per thread, minimum CTAs per SM asked of the register allocator)
-    const int cand[5][2] = {{4, 1}, {8, 1}, {8, 5}, {8, 6}, {16, 1}};
+    int cand[16][2];
+    const int ncand = jam_shape_list(cand, 16);
     float best = 1e30f;
-    int minb = 1;
-    for (auto &cd : cand) {
+    int minb = 4;
+    for (int ic = 0; ic < ncand; ++ic) {
+      const int *cd = cand[ic];
       c->tune.jam_pts = cd[0];
       c->tune.jam_minb = cd[1];
       const float ms = time_ms(st, [&]() { launch_jam(c, sys_id, B, st); }, 2);
@@ -170,9 +173,7 @@ extern "C" int glad_tuning(glad_ctx *c, int *jam_pts, int *adj_ept) {
 extern "C" glad_status glad_set_tuning(glad_ctx *c, int jam_code, int adj_ept) {
   if (!c) return glad_set_error(GLAD_EINVAL, "glad_set_tuning: null context");
   const int pers = jam_code / 10000, pts = (jam_code % 10000) / 100, minb = jam_code % 100;
-  const bool ok_jam = (pers == 0 || pers == 1) &&
-                      ((pts == 4 && minb == 1) || (pts == 16 && minb == 1) ||
-                       (pts == 8 && (minb == 1 || minb == 5 || minb == 6)));
+  const bool ok_jam = (pers == 0 || pers == 1) && jam_shape_supported(pts, minb);
   if (!ok_jam || (adj_ept != 2 && adj_ept != 4))
     return glad_set_error(GLAD_EINVAL, "glad_set_tuning: unsupported launch shape");
   c->tune.jam_persistent = pers;

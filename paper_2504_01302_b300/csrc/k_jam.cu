@@ -22,8 +22,11 @@ __device__ __forceinline__ float ex2(float x) {
 // One tile of TILE = 256 * PTS sky sub-samples of sample b.  PTS points per thread are
 // processed as PTS/2 packed pairs: one FFMA2/FMUL2 issues the arithmetic of two points, so
 // an evaluation costs ~3 issue slots next to its MUFU.EX2.
+// table chunks are staged in shared memory already duplicated into register-pair order,
+// (ax, ax, ay, ay) and (Q0, Q0, Q1, Q1), so the packed FMAs read them without moves
+#define JAM_SCHUNK 256
 struct JamSmem {
-  float4 tab[2][JAM_CHUNK];
+  float4 tab[2][2 * JAM_SCHUNK];
   float bnum[GLAD_MAX_BINS], bden[GLAD_MAX_BINS];
   float sI0[GLAD_MAX_LIGHT], scx[GLAD_MAX_LIGHT], scy[GLAD_MAX_LIGHT];
 };
@@ -70,25 +73,27 @@ __device__ __forceinline__ void jam_tile(const SysDev &S, const WsDev &ws, JamSm
   for (int p = 0; p < NP; ++p) acc[p] = make_float2(0.f, 0.f);
   const float4 *gt = ws.tab + (size_t)b * max_ent;
   const int n_ent = S.n_ent;
-  const int n_chunks = (n_ent + JAM_CHUNK - 1) / JAM_CHUNK;
+  const int n_chunks = (n_ent + JAM_SCHUNK - 1) / JAM_SCHUNK;
+  auto stage = [&](int buf, int base) {
+    for (int e = tid; e < JAM_SCHUNK; e += JAM_THREADS) {
+      const float4 c = base + e < n_ent ? gt[base + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+      sm.tab[buf][2 * e] = make_float4(c.x, c.x, c.y, c.y);
+      sm.tab[buf][2 * e + 1] = make_float4(c.z, c.z, c.w, c.w);
+    }
+  };
   // prologue: chunk 0
-  for (int e = tid; e < JAM_CHUNK; e += JAM_THREADS)
-    sm.tab[0][e] = e < n_ent ? gt[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+  stage(0, 0);
   __syncthreads();
   for (int ch = 0; ch < n_chunks; ++ch) {
     const int cur = ch & 1;
     // stage the next chunk into the other buffer while this one is consumed
-    if (ch + 1 < n_chunks) {
-      const int base = (ch + 1) * JAM_CHUNK;
-      for (int e = tid; e < JAM_CHUNK; e += JAM_THREADS)
-        sm.tab[cur ^ 1][e] = base + e < n_ent ? gt[base + e] : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    if (ch + 1 < n_chunks) stage(cur ^ 1, (ch + 1) * JAM_SCHUNK);
     const float4 *t = sm.tab[cur];
 #pragma unroll 2
-    for (int e = 0; e < JAM_CHUNK; ++e) {
-      const float4 c = t[e];
-      const float2 cx = make_float2(c.x, c.x), cy = make_float2(c.y, c.y);
-      const float2 cz = make_float2(c.z, c.z), cw = make_float2(c.w, c.w);
+    for (int e = 0; e < JAM_SCHUNK; ++e) {
+      const float4 ca = t[2 * e], cb = t[2 * e + 1];
+      const float2 cx = make_float2(ca.x, ca.y), cy = make_float2(ca.z, ca.w);
+      const float2 cz = make_float2(cb.x, cb.y), cw = make_float2(cb.z, cb.w);
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
         const float2 arg = __ffma2_rn(cy, Y[p], __fmul2_rn(cx, X[p]));
@@ -259,9 +264,34 @@ __global__ void k_combine(WsDev ws, int B, double *logL, int *status, double *te
 
 }  // namespace
 
+// candidate launch shapes of the JAM pair sum: (points per thread, minimum CTAs per SM
+// requested from the register allocator); the tuner times these and the persistent forms
+#define GLAD_JAM_SHAPES(X) X(4, 6) X(8, 3) X(8, 4) X(8, 5) X(16, 2)
+
+bool jam_shape_supported(int pts, int minb) {
+#define GLAD_JAM_MATCH(P, M) if (pts == P && minb == M) return true;
+  GLAD_JAM_SHAPES(GLAD_JAM_MATCH)
+#undef GLAD_JAM_MATCH
+  return false;
+}
+
+int jam_shape_list(int (*out)[2], int cap) {
+  int n = 0;
+#define GLAD_JAM_LIST(P, M) \
+  if (n < cap) {            \
+    out[n][0] = P;          \
+    out[n][1] = M;          \
+  }                         \
+  ++n;
+  GLAD_JAM_SHAPES(GLAD_JAM_LIST)
+#undef GLAD_JAM_LIST
+  return n;
+}
+
 cudaError_t launch_jam(glad_ctx *c, const int *sys_id, int B, cudaStream_t st) {
   const int pts = c->tune.jam_pts;
   const int minb = c->tune.jam_minb;
+  if (!jam_shape_supported(pts, minb)) return cudaErrorInvalidConfiguration;
   if (c->tune.jam_persistent && c->ws.d.wl_off) {
     k_worklist<<<1, 1024, 0, st>>>(c->d_sys, sys_id, c->ws.d, B, JAM_THREADS * pts);
     cudaError_t e = cudaGetLastError();
@@ -269,30 +299,23 @@ cudaError_t launch_jam(glad_ctx *c, const int *sys_id, int B, cudaStream_t st) {
     int dev = 0, nsm = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-#define GLAD_JAM_PERSIST(P, M)                                                                \
-  do {                                                                                        \
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jam_persist<P, M>, JAM_THREADS, 0); \
-    k_jam_persist<P, M><<<nsm * (occ > 0 ? occ : 1), JAM_THREADS, 0, st>>>(                   \
-        c->d_sys, sys_id, c->ws.d, B, c->max_light, c->max_ent, c->max_bins);                 \
-  } while (0)
-    if (pts == 4) GLAD_JAM_PERSIST(4, 1);
-    else if (pts == 16) GLAD_JAM_PERSIST(16, 1);
-    else if (minb == 5) GLAD_JAM_PERSIST(8, 5);
-    else if (minb == 6) GLAD_JAM_PERSIST(8, 6);
-    else GLAD_JAM_PERSIST(8, 1);
+#define GLAD_JAM_PERSIST(P, M)                                                                  \
+  if (pts == P && minb == M) {                                                                  \
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jam_persist<P, M>, JAM_THREADS, 0);   \
+    k_jam_persist<P, M><<<nsm * (occ > 0 ? occ : 1), JAM_THREADS, 0, st>>>(                     \
+        c->d_sys, sys_id, c->ws.d, B, c->max_light, c->max_ent, c->max_bins);                   \
+  }
+    GLAD_JAM_SHAPES(GLAD_JAM_PERSIST)
 #undef GLAD_JAM_PERSIST
     return cudaGetLastError();
   }
   const int tiles = (c->max_sub + JAM_THREADS * pts - 1) / (JAM_THREADS * pts);
   dim3 grid(tiles, B);
-#define GLAD_JAM_LAUNCH(P, M)                                                               \
-  k_jam<P, M><<<grid, JAM_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_light, c->max_ent, \
-                                            c->max_bins)
-  if (pts == 4) GLAD_JAM_LAUNCH(4, 1);
-  else if (pts == 16) GLAD_JAM_LAUNCH(16, 1);
-  else if (minb == 5) GLAD_JAM_LAUNCH(8, 5);
-  else if (minb == 6) GLAD_JAM_LAUNCH(8, 6);
-  else GLAD_JAM_LAUNCH(8, 1);
+#define GLAD_JAM_LAUNCH(P, M)                                                                   \
+  if (pts == P && minb == M)                                                                    \
+    k_jam<P, M><<<grid, JAM_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_light,          \
+                                              c->max_ent, c->max_bins);
+  GLAD_JAM_SHAPES(GLAD_JAM_LAUNCH)
 #undef GLAD_JAM_LAUNCH
   return cudaGetLastError();
 }
