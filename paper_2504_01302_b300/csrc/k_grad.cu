@@ -247,8 +247,7 @@ __global__ void __launch_bounds__(JAM_THREADS) k_jam_fg(const SysDev *__restrict
   const SysDev &S = sysv[sys_id[b]];
   const int tile0 = blockIdx.x * JAM_TILE;
   if (tile0 >= S.n_sub) return;
-  constexpr int SCH = 256;  // entries per chunk, staged as (ax, ax, ay, ay), (Q0, Q0, Q1, Q1)
-  __shared__ float4 tab[2][2 * SCH];
+  __shared__ float4 tab[2][JAM_CHUNK];
   __shared__ float bnum[GLAD_MAX_BINS], bden[GLAD_MAX_BINS];
   __shared__ float sI0[GLAD_MAX_LIGHT], scx[GLAD_MAX_LIGHT], scy[GLAD_MAX_LIGHT];
   const int tid = threadIdx.x;
@@ -290,25 +289,23 @@ __global__ void __launch_bounds__(JAM_THREADS) k_jam_fg(const SysDev *__restrict
   for (int p = 0; p < NP; ++p) aV[p] = a1[p] = a2[p] = a3[p] = z2;
   const float4 *gt = ws.tab + (size_t)b * max_ent;
   const int n_ent = S.n_ent;
-  const int n_chunks = (n_ent + SCH - 1) / SCH;
-  auto stage = [&](int buf, int base) {
-    for (int e = tid; e < SCH; e += JAM_THREADS) {
-      const float4 c = base + e < n_ent ? gt[base + e] : make_float4(0.f, 0.f, 0.f, 0.f);
-      tab[buf][2 * e] = make_float4(c.x, c.x, c.y, c.y);
-      tab[buf][2 * e + 1] = make_float4(c.z, c.z, c.w, c.w);
-    }
-  };
-  stage(0, 0);
+  const int n_chunks = (n_ent + JAM_CHUNK - 1) / JAM_CHUNK;
+  for (int e = tid; e < JAM_CHUNK; e += JAM_THREADS)
+    tab[0][e] = e < n_ent ? gt[e] : make_float4(0.f, 0.f, 0.f, 0.f);
   __syncthreads();
   for (int ch = 0; ch < n_chunks; ++ch) {
     const int cur = ch & 1;
-    if (ch + 1 < n_chunks) stage(cur ^ 1, (ch + 1) * SCH);
+    if (ch + 1 < n_chunks) {
+      const int base = (ch + 1) * JAM_CHUNK;
+      for (int e = tid; e < JAM_CHUNK; e += JAM_THREADS)
+        tab[cur ^ 1][e] = base + e < n_ent ? gt[base + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     const float4 *tt = tab[cur];
 #pragma unroll 2
-    for (int e = 0; e < SCH; ++e) {
-      const float4 ca = tt[2 * e], cb = tt[2 * e + 1];
-      const float2 cx = make_float2(ca.x, ca.y), cy = make_float2(ca.z, ca.w);
-      const float2 cz = make_float2(cb.x, cb.y), cw = make_float2(cb.z, cb.w);
+    for (int e = 0; e < JAM_CHUNK; ++e) {
+      const float4 c = tt[e];
+      const float2 cx = make_float2(c.x, c.x), cy = make_float2(c.y, c.y);
+      const float2 cz = make_float2(c.z, c.z), cw = make_float2(c.w, c.w);
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
         const float2 arg = __ffma2_rn(cy, Y[p], __fmul2_rn(cx, X[p]));

@@ -22,11 +22,8 @@ __device__ __forceinline__ float ex2(float x) {
 // One tile of TILE = 256 * PTS sky sub-samples of sample b.  PTS points per thread are
 // processed as PTS/2 packed pairs: one FFMA2/FMUL2 issues the arithmetic of two points, so
 // an evaluation costs ~3 issue slots next to its MUFU.EX2.
-// table chunks are staged in shared memory already duplicated into register-pair order,
-// (ax, ax, ay, ay) and (Q0, Q0, Q1, Q1), so the packed FMAs read them without moves
-#define JAM_SCHUNK 256
 struct JamSmem {
-  float4 tab[2][2 * JAM_SCHUNK];
+  float4 tab[2][JAM_CHUNK];
   float bnum[GLAD_MAX_BINS], bden[GLAD_MAX_BINS];
   float sI0[GLAD_MAX_LIGHT], scx[GLAD_MAX_LIGHT], scy[GLAD_MAX_LIGHT];
 };
@@ -73,27 +70,25 @@ __device__ __forceinline__ void jam_tile(const SysDev &S, const WsDev &ws, JamSm
   for (int p = 0; p < NP; ++p) acc[p] = make_float2(0.f, 0.f);
   const float4 *gt = ws.tab + (size_t)b * max_ent;
   const int n_ent = S.n_ent;
-  const int n_chunks = (n_ent + JAM_SCHUNK - 1) / JAM_SCHUNK;
-  auto stage = [&](int buf, int base) {
-    for (int e = tid; e < JAM_SCHUNK; e += JAM_THREADS) {
-      const float4 c = base + e < n_ent ? gt[base + e] : make_float4(0.f, 0.f, 0.f, 0.f);
-      sm.tab[buf][2 * e] = make_float4(c.x, c.x, c.y, c.y);
-      sm.tab[buf][2 * e + 1] = make_float4(c.z, c.z, c.w, c.w);
-    }
-  };
+  const int n_chunks = (n_ent + JAM_CHUNK - 1) / JAM_CHUNK;
   // prologue: chunk 0
-  stage(0, 0);
+  for (int e = tid; e < JAM_CHUNK; e += JAM_THREADS)
+    sm.tab[0][e] = e < n_ent ? gt[e] : make_float4(0.f, 0.f, 0.f, 0.f);
   __syncthreads();
   for (int ch = 0; ch < n_chunks; ++ch) {
     const int cur = ch & 1;
     // stage the next chunk into the other buffer while this one is consumed
-    if (ch + 1 < n_chunks) stage(cur ^ 1, (ch + 1) * JAM_SCHUNK);
+    if (ch + 1 < n_chunks) {
+      const int base = (ch + 1) * JAM_CHUNK;
+      for (int e = tid; e < JAM_CHUNK; e += JAM_THREADS)
+        sm.tab[cur ^ 1][e] = base + e < n_ent ? gt[base + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     const float4 *t = sm.tab[cur];
 #pragma unroll 2
-    for (int e = 0; e < JAM_SCHUNK; ++e) {
-      const float4 ca = t[2 * e], cb = t[2 * e + 1];
-      const float2 cx = make_float2(ca.x, ca.y), cy = make_float2(ca.z, ca.w);
-      const float2 cz = make_float2(cb.x, cb.y), cw = make_float2(cb.z, cb.w);
+    for (int e = 0; e < JAM_CHUNK; ++e) {
+      const float4 c = t[e];
+      const float2 cx = make_float2(c.x, c.x), cy = make_float2(c.y, c.y);
+      const float2 cz = make_float2(c.z, c.z), cw = make_float2(c.w, c.w);
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
         const float2 arg = __ffma2_rn(cy, Y[p], __fmul2_rn(cx, X[p]));
