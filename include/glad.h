@@ -167,23 +167,22 @@ glad_status glad_loglike_static(glad_ctx *ctx, const int *sys_id, const double *
                                 double *logL, int *sample_status, double *terms, void *stream);
 
 /* Autotuner (the project's own, no counterpart in the paper): times the candidate
- * launch shapes of the JAM kernels -- (sky points per thread, minimum resident CTAs per SM)
- * of the pair sum: (4,6), (8,3), (8,4), (8,5), (16,2)
- * and, with with_grad, table entries per thread of its adjoint (2, 4) -- on this batch
- * (arguments as glad_loglike), keeps the fastest in the context for later calls, and
- * when the environment variable GLAD_TUNE_CACHE names a file, appends the choice there
- * keyed by device name and batch shape (later calls with the same key read it back and
- * skip the timing).  Synchronises the stream; allocates a few small scratch arrays.
- * It also times the chosen shape as one persistent launch over a (sample, tile) work
- * list and keeps that form when faster.  glad_tuning reports the current choice:
- * *jam_pts = 10000 * persistent + 100 * points per thread + the minimum CTAs per SM the
- * variant was compiled for; *adj_ept = entries per thread. */
+ * launch shapes of the JAM kernels on this batch (arguments as glad_loglike) -- for the
+ * pair sum: points per thread, minimum resident CTAs per SM asked of the register
+ * allocator, unroll of the table-entry loop, grid or persistent form; with with_grad,
+ * table entries per thread of its adjoint (2 or 4) -- and keeps the fastest in the
+ * context for later calls.  When the environment variable GLAD_TUNE_CACHE names a file,
+ * the choice is appended there keyed by device name and batch shape, and later calls
+ * with the same key read it back and skip the timing.  Synchronises the stream and
+ * allocates a few small scratch arrays.  glad_tuning reports the current choice:
+ * *jam_code = 100000 * persistent + 1000 * points + 10 * min CTAs + unroll,
+ * *adj_ept = entries per thread. */
 glad_status glad_autotune(glad_ctx *ctx, const int *sys_id, const double *theta, int B,
                           int with_grad, void *stream);
-int glad_tuning(glad_ctx *ctx, int *jam_pts, int *adj_ept);
-/* Pin a launch shape instead of tuning (codes as reported by glad_tuning; jam codes
- * 406, 803, 804, 805, 1602, each optionally + 10000 for the persistent form; adj_ept 2
- * or 4).  GLAD_EINVAL for other values. */
+int glad_tuning(glad_ctx *ctx, int *jam_code, int *adj_ept);
+/* Pin a launch shape instead of tuning (codes as reported by glad_tuning: shapes
+ * 4064, 8032, 8041, 8042, 8044, 8052, 16021, each optionally + 100000 for the persistent
+ * form; adj_ept 2 or 4).  GLAD_EINVAL for other values. */
 glad_status glad_set_tuning(glad_ctx *ctx, int jam_code, int adj_ept);
 
 /* Message of the last failing call on this thread ("" if none). */

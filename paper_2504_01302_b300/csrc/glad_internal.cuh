@@ -131,6 +131,7 @@ struct glad_ctx {
   struct Tune {
     int jam_pts = 8;      // sky points per thread in the JAM pair-sum kernels
     int jam_minb = 4;     // minimum resident CTAs per SM requested from the register allocator
+    int jam_unroll = 2;   // unroll of the table-entry loop
     int jam_persistent = 0;  // 1: one persistent launch over a (sample, tile) work list
     int adj_ept = 4;      // table entries per thread in the JAM adjoint
   } tune;
@@ -178,8 +179,8 @@ cudaError_t launch_kin_finalize(glad_ctx *c, const int *sys_id, int B, float *vr
 cudaError_t launch_combine(glad_ctx *c, int B, double *logL, int *status, double *terms,
                            cudaStream_t st);
 void set_conv_smem_limit();
-bool jam_shape_supported(int pts, int minb);
-int jam_shape_list(int (*out)[2], int cap);
+bool jam_shape_supported(int pts, int minb, int unr);
+int jam_shape_list(int (*out)[3], int cap);
 
 // tile shapes (shared by launchers and the workspace sizing)
 #define JAM_THREADS 256

@@ -23,6 +23,13 @@ cudaError_t time_jam_adj(glad_ctx *c, const int *sys_id, int B, cudaStream_t st)
 
 namespace {
 
+// launch shape of the JAM pair sum as one integer:
+// 100000 * persistent + 1000 * points per thread + 10 * min CTAs per SM + unroll
+int jam_code(const glad_ctx *c) {
+  return c->tune.jam_persistent * 100000 + c->tune.jam_pts * 1000 + c->tune.jam_minb * 10 +
+         c->tune.jam_unroll;
+}
+
 std::string tune_key(glad_ctx *c, int B) {
   cudaDeviceProp prop;
   int dev = 0;
@@ -90,9 +97,10 @@ extern "C" glad_status glad_autotune(glad_ctx *c, const int *sys_id, const doubl
   int pts = 8, ept = 4;
   int code = 0;
   if (cache_lookup(key, &code, &ept)) {
-    c->tune.jam_pts = (code % 10000) / 100;
-    c->tune.jam_minb = code % 100;
-    c->tune.jam_persistent = code / 10000;
+    c->tune.jam_persistent = code / 100000;
+    c->tune.jam_pts = (code % 100000) / 1000;
+    c->tune.jam_minb = (code % 1000) / 10;
+    c->tune.jam_unroll = code % 10;
     c->tune.adj_ept = ept;
     return GLAD_OK;
   }
@@ -117,23 +125,26 @@ extern "C" glad_status glad_autotune(glad_ctx *c, const int *sys_id, const doubl
                 : glad_loglike(c, sys_id, theta, B, logL, status, nullptr, stream);
   if (s == GLAD_OK) {
     // (points per thread, minimum CTAs per SM asked of the register allocator)
-    int cand[16][2];
-    const int ncand = jam_shape_list(cand, 16);
+    int cand[32][3];
+    const int ncand = jam_shape_list(cand, 32);
     float best = 1e30f;
-    int minb = 4;
+    int minb = 4, unr = 2;
     for (int ic = 0; ic < ncand; ++ic) {
       const int *cd = cand[ic];
       c->tune.jam_pts = cd[0];
       c->tune.jam_minb = cd[1];
+      c->tune.jam_unroll = cd[2];
       const float ms = time_ms(st, [&]() { launch_jam(c, sys_id, B, st); }, 2);
       if (ms < best) {
         best = ms;
         pts = cd[0];
         minb = cd[1];
+        unr = cd[2];
       }
     }
     c->tune.jam_pts = pts;
     c->tune.jam_minb = minb;
+    c->tune.jam_unroll = unr;
     // the same shape as one persistent launch over the (sample, tile) work list
     c->tune.jam_persistent = 1;
     const float ms_p = time_ms(st, [&]() { launch_jam(c, sys_id, B, st); }, 2);
@@ -154,8 +165,7 @@ extern "C" glad_status glad_autotune(glad_ctx *c, const int *sys_id, const doubl
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) s = glad_set_error(GLAD_ECUDA, cudaGetErrorString(e));
     else
-      cache_store(key, c->tune.jam_persistent * 10000 + c->tune.jam_pts * 100 + c->tune.jam_minb,
-                  c->tune.adj_ept);
+      cache_store(key, jam_code(c), c->tune.adj_ept);
   }
   cudaFree(logL);
   cudaFree(status);
@@ -165,20 +175,22 @@ extern "C" glad_status glad_autotune(glad_ctx *c, const int *sys_id, const doubl
 
 extern "C" int glad_tuning(glad_ctx *c, int *jam_pts, int *adj_ept) {
   if (!c) return -1;
-  if (jam_pts) *jam_pts = c->tune.jam_persistent * 10000 + c->tune.jam_pts * 100 + c->tune.jam_minb;
+  if (jam_pts) *jam_pts = jam_code(c);
   if (adj_ept) *adj_ept = c->tune.adj_ept;
   return 0;
 }
 
 extern "C" glad_status glad_set_tuning(glad_ctx *c, int jam_code, int adj_ept) {
   if (!c) return glad_set_error(GLAD_EINVAL, "glad_set_tuning: null context");
-  const int pers = jam_code / 10000, pts = (jam_code % 10000) / 100, minb = jam_code % 100;
-  const bool ok_jam = (pers == 0 || pers == 1) && jam_shape_supported(pts, minb);
+  const int pers = jam_code / 100000, pts = (jam_code % 100000) / 1000;
+  const int minb = (jam_code % 1000) / 10, unr = jam_code % 10;
+  const bool ok_jam = (pers == 0 || pers == 1) && jam_shape_supported(pts, minb, unr);
   if (!ok_jam || (adj_ept != 2 && adj_ept != 4))
     return glad_set_error(GLAD_EINVAL, "glad_set_tuning: unsupported launch shape");
   c->tune.jam_persistent = pers;
   c->tune.jam_pts = pts;
   c->tune.jam_minb = minb;
+  c->tune.jam_unroll = unr;
   c->tune.adj_ept = adj_ept;
   return GLAD_OK;
 }

@@ -28,7 +28,7 @@ struct JamSmem {
   float sI0[GLAD_MAX_LIGHT], scx[GLAD_MAX_LIGHT], scy[GLAD_MAX_LIGHT];
 };
 
-template <int PTS>
+template <int PTS, int UNR>
 __device__ __forceinline__ void jam_tile(const SysDev &S, const WsDev &ws, JamSmem &sm, int b,
                                          int tile0, int max_light, int max_ent, int max_bins) {
   constexpr int NP = PTS / 2;
@@ -84,7 +84,7 @@ __device__ __forceinline__ void jam_tile(const SysDev &S, const WsDev &ws, JamSm
         sm.tab[cur ^ 1][e] = base + e < n_ent ? gt[base + e] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     const float4 *t = sm.tab[cur];
-#pragma unroll 2
+#pragma unroll UNR
     for (int e = 0; e < JAM_CHUNK; ++e) {
       const float4 c = t[e];
       const float2 cx = make_float2(c.x, c.x), cy = make_float2(c.y, c.y);
@@ -132,7 +132,7 @@ __device__ __forceinline__ void jam_tile(const SysDev &S, const WsDev &ws, JamSm
 }
 
 // one CTA per (tile, sample) of the largest system; tiles beyond a sample's system exit
-template <int PTS, int MINB>
+template <int PTS, int MINB, int UNR>
 __global__ void __launch_bounds__(JAM_THREADS, MINB) k_jam(const SysDev *__restrict__ sysv,
                                                            const int *__restrict__ sys_id, WsDev ws,
                                                            int max_light, int max_ent, int max_bins) {
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(JAM_THREADS, MINB) k_jam(const SysDev *__restr
   const int tile0 = blockIdx.x * (JAM_THREADS * PTS);
   if (tile0 >= S.n_sub) return;
   __shared__ JamSmem sm;
-  jam_tile<PTS>(S, ws, sm, b, tile0, max_light, max_ent, max_bins);
+  jam_tile<PTS, UNR>(S, ws, sm, b, tile0, max_light, max_ent, max_bins);
 }
 
 // Work list for the persistent form: wl_off[b] = first item of sample b, wl_off[B] = total,
@@ -179,7 +179,7 @@ __global__ void k_worklist(const SysDev *__restrict__ sysv, const int *__restric
 
 // Persistent form: a fixed grid of SM-count x occupancy CTAs takes (sample, tile) items
 // from a global counter until the list is exhausted, so uneven batches leave no idle slots.
-template <int PTS, int MINB>
+template <int PTS, int MINB, int UNR>
 __global__ void __launch_bounds__(JAM_THREADS, MINB) k_jam_persist(
     const SysDev *__restrict__ sysv, const int *__restrict__ sys_id, WsDev ws, int B,
     int max_light, int max_ent, int max_bins) {
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(JAM_THREADS, MINB) k_jam_persist(
     if (b < 0) return;
     const SysDev &S = sysv[sys_id[b]];
     const int tile0 = (it - ws.wl_off[b]) * (JAM_THREADS * PTS);
-    jam_tile<PTS>(S, ws, sm, b, tile0, max_light, max_ent, max_bins);
+    jam_tile<PTS, UNR>(S, ws, sm, b, tile0, max_light, max_ent, max_bins);
   }
 }
 
@@ -260,23 +260,25 @@ __global__ void k_combine(WsDev ws, int B, double *logL, int *status, double *te
 }  // namespace
 
 // candidate launch shapes of the JAM pair sum: (points per thread, minimum CTAs per SM
-// requested from the register allocator); the tuner times these and the persistent forms
-#define GLAD_JAM_SHAPES(X) X(4, 6) X(8, 3) X(8, 4) X(8, 5) X(16, 2)
+// requested from the register allocator, unroll of the table-entry loop); the tuner times
+// these and the persistent forms
+#define GLAD_JAM_SHAPES(X) X(4, 6, 4) X(8, 3, 2) X(8, 4, 1) X(8, 4, 2) X(8, 4, 4) X(8, 5, 2) X(16, 2, 1)
 
-bool jam_shape_supported(int pts, int minb) {
-#define GLAD_JAM_MATCH(P, M) if (pts == P && minb == M) return true;
+bool jam_shape_supported(int pts, int minb, int unr) {
+#define GLAD_JAM_MATCH(P, M, U) if (pts == P && minb == M && unr == U) return true;
   GLAD_JAM_SHAPES(GLAD_JAM_MATCH)
 #undef GLAD_JAM_MATCH
   return false;
 }
 
-int jam_shape_list(int (*out)[2], int cap) {
+int jam_shape_list(int (*out)[3], int cap) {
   int n = 0;
-#define GLAD_JAM_LIST(P, M) \
-  if (n < cap) {            \
-    out[n][0] = P;          \
-    out[n][1] = M;          \
-  }                         \
+#define GLAD_JAM_LIST(P, M, U) \
+  if (n < cap) {               \
+    out[n][0] = P;             \
+    out[n][1] = M;             \
+    out[n][2] = U;             \
+  }                            \
   ++n;
   GLAD_JAM_SHAPES(GLAD_JAM_LIST)
 #undef GLAD_JAM_LIST
@@ -286,7 +288,8 @@ int jam_shape_list(int (*out)[2], int cap) {
 cudaError_t launch_jam(glad_ctx *c, const int *sys_id, int B, cudaStream_t st) {
   const int pts = c->tune.jam_pts;
   const int minb = c->tune.jam_minb;
-  if (!jam_shape_supported(pts, minb)) return cudaErrorInvalidConfiguration;
+  const int unr = c->tune.jam_unroll;
+  if (!jam_shape_supported(pts, minb, unr)) return cudaErrorInvalidConfiguration;
   if (c->tune.jam_persistent && c->ws.d.wl_off) {
     k_worklist<<<1, 1024, 0, st>>>(c->d_sys, sys_id, c->ws.d, B, JAM_THREADS * pts);
     cudaError_t e = cudaGetLastError();
@@ -294,11 +297,11 @@ cudaError_t launch_jam(glad_ctx *c, const int *sys_id, int B, cudaStream_t st) {
     int dev = 0, nsm = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-#define GLAD_JAM_PERSIST(P, M)                                                                  \
-  if (pts == P && minb == M) {                                                                  \
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jam_persist<P, M>, JAM_THREADS, 0);   \
-    k_jam_persist<P, M><<<nsm * (occ > 0 ? occ : 1), JAM_THREADS, 0, st>>>(                     \
-        c->d_sys, sys_id, c->ws.d, B, c->max_light, c->max_ent, c->max_bins);                   \
+#define GLAD_JAM_PERSIST(P, M, U)                                                                \
+  if (pts == P && minb == M && unr == U) {                                                       \
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jam_persist<P, M, U>, JAM_THREADS, 0); \
+    k_jam_persist<P, M, U><<<nsm * (occ > 0 ? occ : 1), JAM_THREADS, 0, st>>>(                   \
+        c->d_sys, sys_id, c->ws.d, B, c->max_light, c->max_ent, c->max_bins);                    \
   }
     GLAD_JAM_SHAPES(GLAD_JAM_PERSIST)
 #undef GLAD_JAM_PERSIST
@@ -306,10 +309,10 @@ cudaError_t launch_jam(glad_ctx *c, const int *sys_id, int B, cudaStream_t st) {
   }
   const int tiles = (c->max_sub + JAM_THREADS * pts - 1) / (JAM_THREADS * pts);
   dim3 grid(tiles, B);
-#define GLAD_JAM_LAUNCH(P, M)                                                                   \
-  if (pts == P && minb == M)                                                                    \
-    k_jam<P, M><<<grid, JAM_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_light,          \
-                                              c->max_ent, c->max_bins);
+#define GLAD_JAM_LAUNCH(P, M, U)                                                                \
+  if (pts == P && minb == M && unr == U)                                                        \
+    k_jam<P, M, U><<<grid, JAM_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_light,       \
+                                                 c->max_ent, c->max_bins);
   GLAD_JAM_SHAPES(GLAD_JAM_LAUNCH)
 #undef GLAD_JAM_LAUNCH
   return cudaGetLastError();
