@@ -146,7 +146,8 @@ glad_status glad_vrms(glad_ctx *ctx, int sys, const double *theta, float *vrms, 
  * glad_kernel_times(ctx, n, ms, launches) waits for those events, adds the elapsed
  * milliseconds and the launch count of kernel id k (0 <= k < n) into ms[k] and
  * launches[k] [host arrays of n], and forgets the recorded pairs.  Returns the number
- * of kernel ids (call with n = 0 to query it).  glad_kernel_name(k) names id k. */
+ * of kernel ids; with n = 0 (or NULL arrays) it only returns that number and keeps the
+ * recorded pairs.  glad_kernel_name(k) names id k. */
 int glad_profile(glad_ctx *ctx, int enable);
 int glad_kernel_times(glad_ctx *ctx, int n, double *ms, int *launches);
 const char *glad_kernel_name(int k);

@@ -458,7 +458,8 @@ int glad_profile(glad_ctx *c, int enable) {
 
 int glad_kernel_times(glad_ctx *c, int n, double *ms, int *launches) {
   if (!c) return -1;
-  if (n > 0 && ms && launches) {
+  if (n <= 0 || !ms || !launches) return KID_N;  // count query: keep the recorded pairs
+  {
     for (auto &r : c->recs) {
       cudaEventSynchronize(r.b);
       float t = 0.0f;
