@@ -9,6 +9,8 @@
 //    FP64 accumulators, so the maps are never stored.
 //  k_kin_finalize: v_rms,l = sqrt(num_l/den_l) (Eq. Vrms) and chi^2_dyn (Eq. chi2_dyn).
 //  k_combine: logL = -(chi2_pix + chi2_dyn + chi2_tmd)/2 (Eq. chi_general).
+#include <algorithm>
+
 #include "glad_internal.cuh"
 
 namespace {
@@ -19,21 +21,40 @@ __device__ __forceinline__ float ex2(float x) {
   return y;
 }
 
-// One tile of TILE = 256 * PTS sky sub-samples of sample b.  PTS points per thread are
-// processed as PTS/2 packed pairs: one FFMA2/FMUL2 issues the arithmetic of two points, so
-// an evaluation costs ~3 issue slots next to its MUFU.EX2.
+// Sky tiles are JAM_TW columns x (8 * PTS) rows of sub-samples; each warp covers JAM_TW
+// columns and PTS consecutive rows, each thread one column.  For a tile, a lower bound of
+// x'^2 and y'^2 over its points (from its corners: x', y' are linear in the pixel indices)
+// bounds every exponent ax x'^2 + ay y'^2 (ax, ay < 0) from above; table entries whose bound
+// is below -130 give 2^arg < 2^-130, which ex2.approx.ftz flushes to exactly 0, so they are
+// dropped while staging the chunk.  The kept entries keep their order and the chunk
+// boundaries of the FP32 partial sums are unchanged: every point's sum is bit-identical to
+// the one without skipping.
+#define JAM_TW 32
+#define JAM_SKIP_LOG2 (-130.0f)
+
 struct JamSmem {
   float4 tab[2][JAM_CHUNK];
+  int wcount[2][2][JAM_THREADS / 32];  // [buffer][half of the chunk][warp]
+  int n_kept[2];
   float bnum[GLAD_MAX_BINS], bden[GLAD_MAX_BINS];
   float sI0[GLAD_MAX_LIGHT], scx[GLAD_MAX_LIGHT], scy[GLAD_MAX_LIGHT];
 };
 
+__host__ __device__ inline int jam_tiles(int nsx, int nsy, int pts) {
+  return ((nsx + JAM_TW - 1) / JAM_TW) * ((nsy + (JAM_THREADS / JAM_TW) * pts - 1) /
+                                         ((JAM_THREADS / JAM_TW) * pts));
+}
+
 template <int PTS, int UNR>
 __device__ __forceinline__ void jam_tile(const SysDev &S, const WsDev &ws, JamSmem &sm, int b,
-                                         int tile0, int max_light, int max_ent, int max_bins) {
+                                         int tile, int max_light, int max_ent, int max_bins) {
   constexpr int NP = PTS / 2;
-  const int tid = threadIdx.x;
+  constexpr int TH = (JAM_THREADS / JAM_TW) * PTS;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const DynP dp = ws.dp[b];
+  const int ntx = (S.nsx + JAM_TW - 1) / JAM_TW;
+  const int c0 = (tile % ntx) * JAM_TW, r0 = (tile / ntx) * TH;
+  const int c1 = min(c0 + JAM_TW, S.nsx) - 1, r1 = min(r0 + TH, S.nsy) - 1;
   for (int l = tid; l < S.n_bins; l += JAM_THREADS) {
     sm.bnum[l] = 0.0f;
     sm.bden[l] = 0.0f;
@@ -43,19 +64,36 @@ __device__ __forceinline__ void jam_tile(const SysDev &S, const WsDev &ws, JamSm
     sm.scx[k] = S.sb_cx[k];
     sm.scy[k] = S.sb_cy[k];
   }
-  // sky points of this thread (strided so that neighbouring threads are neighbours):
-  // point i of the thread is tile0 + tid + i * JAM_THREADS; pair p holds points 2p, 2p+1
-  float2 X[NP], Y[NP], acc[NP];
-  double accd[PTS];
   const float cphi = (float)dp.cphi, sphi = (float)dp.sphi;
   const float xc = (float)dp.xc, yc = (float)dp.yc;
+  const float hx = 0.5f * (S.nsx - 1), hy = 0.5f * (S.nsy - 1);
+  // lower bounds of x'^2 and y'^2 over the tile, slightly lowered against rounding
+  float Xmin, Ymin;
+  {
+    float xmn = 1e30f, xmx = -1e30f, ymn = 1e30f, ymx = -1e30f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float x = ((q & 1 ? c1 : c0) - hx) * S.dsub - xc;
+      const float y = ((q & 2 ? r1 : r0) - hy) * S.dsub - yc;
+      const float xp = cphi * x + sphi * y, yp = -sphi * x + cphi * y;
+      xmn = fminf(xmn, xp);
+      xmx = fmaxf(xmx, xp);
+      ymn = fminf(ymn, yp);
+      ymx = fmaxf(ymx, yp);
+    }
+    Xmin = (xmn <= 0.0f && xmx >= 0.0f) ? 0.0f : 0.999f * fminf(xmn * xmn, xmx * xmx);
+    Ymin = (ymn <= 0.0f && ymx >= 0.0f) ? 0.0f : 0.999f * fminf(ymn * ymn, ymx * ymx);
+  }
+  // this thread's points: column col, rows row0 .. row0 + PTS - 1 (clamped into the tile)
+  const int col = c0 + (tid % JAM_TW);
+  const int row0 = r0 + (tid / JAM_TW) * PTS;
+  float2 X[NP], Y[NP], acc[NP];
+  double accd[PTS];
 #pragma unroll
   for (int i = 0; i < PTS; ++i) {
-    const int s = tile0 + tid + i * JAM_THREADS;
-    const int si = s < S.n_sub ? s : 0;
-    const int I = si / S.nsx, J = si - I * S.nsx;
-    const float x = (J - 0.5f * (S.nsx - 1)) * S.dsub - xc;
-    const float y = (I - 0.5f * (S.nsy - 1)) * S.dsub - yc;
+    const int J = min(col, c1), I = min(row0 + i, r1);
+    const float x = (J - hx) * S.dsub - xc;
+    const float y = (I - hy) * S.dsub - yc;
     const float xp = cphi * x + sphi * y, yp = -sphi * x + cphi * y;
     if (i & 1) {
       X[i >> 1].y = xp * xp;
@@ -71,21 +109,51 @@ __device__ __forceinline__ void jam_tile(const SysDev &S, const WsDev &ws, JamSm
   const float4 *gt = ws.tab + (size_t)b * max_ent;
   const int n_ent = S.n_ent;
   const int n_chunks = (n_ent + JAM_CHUNK - 1) / JAM_CHUNK;
-  // prologue: chunk 0
-  for (int e = tid; e < JAM_CHUNK; e += JAM_THREADS)
-    sm.tab[0][e] = e < n_ent ? gt[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  // staging of a chunk, phase 1: load two entries per thread and count the kept ones per warp
+  float4 v0, v1;
+  bool k0, k1;
+  auto stage_count = [&](int buf, int base) {
+    const int e0 = base + tid, e1 = base + tid + JAM_THREADS;
+    v0 = e0 < n_ent ? gt[e0] : zero4;
+    v1 = e1 < n_ent ? gt[e1] : zero4;
+    k0 = e0 < n_ent && fmaf(v0.y, Ymin, v0.x * Xmin) >= JAM_SKIP_LOG2;
+    k1 = e1 < n_ent && fmaf(v1.y, Ymin, v1.x * Xmin) >= JAM_SKIP_LOG2;
+    const unsigned m0 = __ballot_sync(0xffffffffu, k0), m1 = __ballot_sync(0xffffffffu, k1);
+    if (lane == 0) {
+      sm.wcount[buf][0][warp] = __popc(m0);
+      sm.wcount[buf][1][warp] = __popc(m1);
+    }
+  };
+  // phase 2 (after a barrier): write the kept entries in their original order
+  auto stage_write = [&](int buf) {
+    const unsigned lt = (1u << lane) - 1u;
+    const unsigned m0 = __ballot_sync(0xffffffffu, k0), m1 = __ballot_sync(0xffffffffu, k1);
+    int off0 = 0, tot0 = 0, off1 = 0, tot1 = 0;
+#pragma unroll
+    for (int w = 0; w < JAM_THREADS / 32; ++w) {
+      const int a0 = sm.wcount[buf][0][w], a1 = sm.wcount[buf][1][w];
+      off0 += w < warp ? a0 : 0;
+      off1 += w < warp ? a1 : 0;
+      tot0 += a0;
+      tot1 += a1;
+    }
+    if (k0) sm.tab[buf][off0 + __popc(m0 & lt)] = v0;
+    if (k1) sm.tab[buf][tot0 + off1 + __popc(m1 & lt)] = v1;
+    if (tid == 0) sm.n_kept[buf] = tot0 + tot1;
+  };
+  stage_count(0, 0);
+  __syncthreads();
+  stage_write(0);
   __syncthreads();
   for (int ch = 0; ch < n_chunks; ++ch) {
     const int cur = ch & 1;
-    // stage the next chunk into the other buffer while this one is consumed
-    if (ch + 1 < n_chunks) {
-      const int base = (ch + 1) * JAM_CHUNK;
-      for (int e = tid; e < JAM_CHUNK; e += JAM_THREADS)
-        sm.tab[cur ^ 1][e] = base + e < n_ent ? gt[base + e] : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    const bool more = ch + 1 < n_chunks;
+    if (more) stage_count(cur ^ 1, (ch + 1) * JAM_CHUNK);
     const float4 *t = sm.tab[cur];
+    const int nk = sm.n_kept[cur];
 #pragma unroll UNR
-    for (int e = 0; e < JAM_CHUNK; ++e) {
+    for (int e = 0; e < nk; ++e) {
       const float4 c = t[e];
       const float2 cx = make_float2(c.x, c.x), cy = make_float2(c.y, c.y);
       const float2 cz = make_float2(c.z, c.z), cw = make_float2(c.w, c.w);
@@ -103,12 +171,14 @@ __device__ __forceinline__ void jam_tile(const SysDev &S, const WsDev &ws, JamSm
       acc[p] = make_float2(0.f, 0.f);
     }
     __syncthreads();
+    if (more) stage_write(cur ^ 1);
+    __syncthreads();
   }
   // tracer surface brightness and the binning-after-PSF scatter
 #pragma unroll
   for (int i = 0; i < PTS; ++i) {
-    const int s = tile0 + tid + i * JAM_THREADS;
-    if (s >= S.n_sub) continue;
+    if (col > c1 || row0 + i > r1) continue;
+    const int s = (row0 + i) * S.nsx + col;
     const float Xi = (i & 1) ? X[i >> 1].y : X[i >> 1].x;
     const float Yi = (i & 1) ? Y[i >> 1].y : Y[i >> 1].x;
     float sb = 0.0f;
@@ -139,16 +209,15 @@ __global__ void __launch_bounds__(JAM_THREADS, MINB) k_jam(const SysDev *__restr
   const int b = blockIdx.y;
   if (ws.status[b] != GLAD_SAMPLE_OK) return;
   const SysDev &S = sysv[sys_id[b]];
-  const int tile0 = blockIdx.x * (JAM_THREADS * PTS);
-  if (tile0 >= S.n_sub) return;
+  if ((int)blockIdx.x >= jam_tiles(S.nsx, S.nsy, PTS)) return;
   __shared__ JamSmem sm;
-  jam_tile<PTS, UNR>(S, ws, sm, b, tile0, max_light, max_ent, max_bins);
+  jam_tile<PTS, UNR>(S, ws, sm, b, blockIdx.x, max_light, max_ent, max_bins);
 }
 
 // Work list for the persistent form: wl_off[b] = first item of sample b, wl_off[B] = total,
 // items of a sample = its tiles (none for invalid samples).  One CTA; resets the counter.
 __global__ void k_worklist(const SysDev *__restrict__ sysv, const int *__restrict__ sys_id,
-                           WsDev ws, int B, int tile) {
+                           WsDev ws, int B, int pts) {
   __shared__ int part[1024];
   __shared__ int carry;
   if (threadIdx.x == 0) carry = 0;
@@ -156,7 +225,10 @@ __global__ void k_worklist(const SysDev *__restrict__ sysv, const int *__restric
   for (int base = 0; base < B; base += blockDim.x) {
     const int b = base + threadIdx.x;
     int n = 0;
-    if (b < B && ws.status[b] == GLAD_SAMPLE_OK) n = (sysv[sys_id[b]].n_sub + tile - 1) / tile;
+    if (b < B && ws.status[b] == GLAD_SAMPLE_OK) {
+      const SysDev &S = sysv[sys_id[b]];
+      n = jam_tiles(S.nsx, S.nsy, pts);
+    }
     part[threadIdx.x] = n;
     __syncthreads();
     // inclusive scan (Hillis-Steele) over the block
@@ -208,8 +280,7 @@ __global__ void __launch_bounds__(JAM_THREADS, MINB) k_jam_persist(
     __syncthreads();
     if (b < 0) return;
     const SysDev &S = sysv[sys_id[b]];
-    const int tile0 = (it - ws.wl_off[b]) * (JAM_THREADS * PTS);
-    jam_tile<PTS, UNR>(S, ws, sm, b, tile0, max_light, max_ent, max_bins);
+    jam_tile<PTS, UNR>(S, ws, sm, b, it - ws.wl_off[b], max_light, max_ent, max_bins);
   }
 }
 
@@ -291,7 +362,7 @@ cudaError_t launch_jam(glad_ctx *c, const int *sys_id, int B, cudaStream_t st) {
   const int unr = c->tune.jam_unroll;
   if (!jam_shape_supported(pts, minb, unr)) return cudaErrorInvalidConfiguration;
   if (c->tune.jam_persistent && c->ws.d.wl_off) {
-    k_worklist<<<1, 1024, 0, st>>>(c->d_sys, sys_id, c->ws.d, B, JAM_THREADS * pts);
+    k_worklist<<<1, 1024, 0, st>>>(c->d_sys, sys_id, c->ws.d, B, pts);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0, occ = 0;
@@ -307,7 +378,8 @@ cudaError_t launch_jam(glad_ctx *c, const int *sys_id, int B, cudaStream_t st) {
 #undef GLAD_JAM_PERSIST
     return cudaGetLastError();
   }
-  const int tiles = (c->max_sub + JAM_THREADS * pts - 1) / (JAM_THREADS * pts);
+  int tiles = 0;
+  for (auto &sd : c->h_sysdev) tiles = std::max(tiles, jam_tiles(sd.nsx, sd.nsy, pts));
   dim3 grid(tiles, B);
 #define GLAD_JAM_LAUNCH(P, M, U)                                                                \
   if (pts == P && minb == M && unr == U)                                                        \
