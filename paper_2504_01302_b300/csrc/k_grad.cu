@@ -15,8 +15,11 @@
 //    table formula, deprojection (App. A), BH mass and the 1-D MGE (Sect. 3.2) to theta,
 //    and adds the delay term by duals through the FP64 lens model.
 // The MGE and table quantities are recomputed here, never stored from the forward pass.
+#include <algorithm>
+
 #include "dual.cuh"
 #include "glad_internal.cuh"
+#include "jam_common.cuh"
 #include "lensmath.cuh"
 
 struct GradWs {
@@ -238,42 +241,48 @@ __global__ void __launch_bounds__(LENS_THREADS) k_image_grad(const SysDev *__res
 
 // JAM pair sum with dV/dX and dV/dY per point (X = x'^2, Y = y'^2), plus the same bin
 // scatter as the forward kernel so that v_rms and chi2_dyn come out of this pass too.
-__global__ void __launch_bounds__(JAM_THREADS) k_jam_fg(const SysDev *__restrict__ sysv,
+// Same 2-D sky tiles and exact skipping of entries flushed to zero as the forward kernel
+// (4 points per thread).
+__global__ void __launch_bounds__(JAM_THREADS, 3) k_jam_fg(const SysDev *__restrict__ sysv,
                                                         const int *__restrict__ sys_id, WsDev ws,
                                                         GradWs gw, int max_light, int max_ent,
                                                         int max_bins, int max_sub) {
+  constexpr int PTS = 4, NP = PTS / 2, TH = (JAM_THREADS / JAM_TW) * PTS;
   const int b = blockIdx.y;
   if (ws.status[b] != GLAD_SAMPLE_OK) return;
   const SysDev &S = sysv[sys_id[b]];
-  const int tile0 = blockIdx.x * JAM_TILE;
-  if (tile0 >= S.n_sub) return;
-  __shared__ float4 tab[2][JAM_CHUNK];
-  __shared__ float bnum[GLAD_MAX_BINS], bden[GLAD_MAX_BINS];
-  __shared__ float sI0[GLAD_MAX_LIGHT], scx[GLAD_MAX_LIGHT], scy[GLAD_MAX_LIGHT];
+  const int tile = blockIdx.x;
+  if (tile >= jam_tiles(S.nsx, S.nsy, PTS)) return;
+  __shared__ JamSmem sm;
   const int tid = threadIdx.x;
   const DynP dp = ws.dp[b];
+  const int ntx = (S.nsx + JAM_TW - 1) / JAM_TW;
+  const int c0 = (tile % ntx) * JAM_TW, r0 = (tile / ntx) * TH;
+  const int c1 = min(c0 + JAM_TW, S.nsx) - 1, r1 = min(r0 + TH, S.nsy) - 1;
   for (int l = tid; l < S.n_bins; l += JAM_THREADS) {
-    bnum[l] = 0.0f;
-    bden[l] = 0.0f;
+    sm.bnum[l] = 0.0f;
+    sm.bden[l] = 0.0f;
   }
   for (int k = tid; k < S.n_light; k += JAM_THREADS) {
-    sI0[k] = ws.I0f[(size_t)b * max_light + k];
-    scx[k] = S.sb_cx[k];
-    scy[k] = S.sb_cy[k];
+    sm.sI0[k] = ws.I0f[(size_t)b * max_light + k];
+    sm.scx[k] = S.sb_cx[k];
+    sm.scy[k] = S.sb_cy[k];
   }
-  constexpr int NP = JAM_PTS / 2;
-  float2 X[NP], Y[NP];
-  float2 aV[NP], a1[NP], a2[NP], a3[NP];
-  double dV[JAM_PTS], d1[JAM_PTS], d2[JAM_PTS], d3[JAM_PTS];
+  float Xmin, Ymin;
+  jam_tile_bounds(S, dp, c0, c1, r0, r1, Xmin, Ymin);
   const float cphi = (float)dp.cphi, sphi = (float)dp.sphi;
   const float xc = (float)dp.xc, yc = (float)dp.yc;
+  const float hx = 0.5f * (S.nsx - 1), hy = 0.5f * (S.nsy - 1);
+  const int col = c0 + (tid % JAM_TW);
+  const int row0 = r0 + (tid / JAM_TW) * PTS;
+  float2 X[NP], Y[NP];
+  float2 aV[NP], a1[NP], a2[NP], a3[NP];
+  double dV[PTS], d1[PTS], d2[PTS], d3[PTS];
 #pragma unroll
-  for (int i = 0; i < JAM_PTS; ++i) {
-    const int s = tile0 + tid + i * JAM_THREADS;
-    const int si = s < S.n_sub ? s : 0;
-    const int I = si / S.nsx, J = si - I * S.nsx;
-    const float x = (J - 0.5f * (S.nsx - 1)) * S.dsub - xc;
-    const float y = (I - 0.5f * (S.nsy - 1)) * S.dsub - yc;
+  for (int i = 0; i < PTS; ++i) {
+    const int J = min(col, c1), I = min(row0 + i, r1);
+    const float x = (J - hx) * S.dsub - xc;
+    const float y = (I - hy) * S.dsub - yc;
     const float xp = cphi * x + sphi * y, yp = -sphi * x + cphi * y;
     if (i & 1) {
       X[i >> 1].y = xp * xp;
@@ -290,26 +299,26 @@ __global__ void __launch_bounds__(JAM_THREADS) k_jam_fg(const SysDev *__restrict
   const float4 *gt = ws.tab + (size_t)b * max_ent;
   const int n_ent = S.n_ent;
   const int n_chunks = (n_ent + JAM_CHUNK - 1) / JAM_CHUNK;
-  for (int e = tid; e < JAM_CHUNK; e += JAM_THREADS)
-    tab[0][e] = e < n_ent ? gt[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+  JamStager stg;
+  stg.count(gt, n_ent, 0, Xmin, Ymin, sm.wcount[0]);
+  __syncthreads();
+  stg.write(sm.tab[0], sm.wcount[0], &sm.n_kept[0]);
   __syncthreads();
   for (int ch = 0; ch < n_chunks; ++ch) {
     const int cur = ch & 1;
-    if (ch + 1 < n_chunks) {
-      const int base = (ch + 1) * JAM_CHUNK;
-      for (int e = tid; e < JAM_CHUNK; e += JAM_THREADS)
-        tab[cur ^ 1][e] = base + e < n_ent ? gt[base + e] : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    const float4 *tt = tab[cur];
+    const bool more = ch + 1 < n_chunks;
+    if (more) stg.count(gt, n_ent, (ch + 1) * JAM_CHUNK, Xmin, Ymin, sm.wcount[cur ^ 1]);
+    const float4 *tt = sm.tab[cur];
+    const int nk = sm.n_kept[cur];
 #pragma unroll 2
-    for (int e = 0; e < JAM_CHUNK; ++e) {
+    for (int e = 0; e < nk; ++e) {
       const float4 c = tt[e];
       const float2 cx = make_float2(c.x, c.x), cy = make_float2(c.y, c.y);
       const float2 cz = make_float2(c.z, c.z), cw = make_float2(c.w, c.w);
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
         const float2 arg = __ffma2_rn(cy, Y[p], __fmul2_rn(cx, X[p]));
-        const float2 E = make_float2(ex2(arg.x), ex2(arg.y));
+        const float2 E = make_float2(jam_ex2(arg.x), jam_ex2(arg.y));
         const float2 tv = __fmul2_rn(__ffma2_rn(cw, X[p], cz), E);
         aV[p] = __fadd2_rn(aV[p], tv);
         a1[p] = __ffma2_rn(cw, E, a1[p]);
@@ -330,15 +339,18 @@ __global__ void __launch_bounds__(JAM_THREADS) k_jam_fg(const SysDev *__restrict
       aV[p] = a1[p] = a2[p] = a3[p] = z2;
     }
     __syncthreads();
+    if (more) stg.write(sm.tab[cur ^ 1], sm.wcount[cur ^ 1], &sm.n_kept[cur ^ 1]);
+    __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < JAM_PTS; ++i) {
-    const int s = tile0 + tid + i * JAM_THREADS;
-    if (s >= S.n_sub) continue;
+  for (int i = 0; i < PTS; ++i) {
+    if (col > c1 || row0 + i > r1) continue;
+    const int s = (row0 + i) * S.nsx + col;
     const float Xi = (i & 1) ? X[i >> 1].y : X[i >> 1].x;
     const float Yi = (i & 1) ? Y[i >> 1].y : Y[i >> 1].x;
     float sb = 0.0f;
-    for (int k = 0; k < S.n_light; ++k) sb = fmaf(sI0[k], ex2(-fmaf(scy[k], Yi, scx[k] * Xi)), sb);
+    for (int k = 0; k < S.n_light; ++k)
+      sb = fmaf(sm.sI0[k], jam_ex2(-fmaf(sm.scy[k], Yi, sm.scx[k] * Xi)), sb);
     const float v = (float)dV[i];
     // coefficients are in log2 units: d/dX 2^(ax X) = ln2 ax 2^(ax X)
     gw.pt[(size_t)b * max_sub + s] =
@@ -346,15 +358,15 @@ __global__ void __launch_bounds__(JAM_THREADS) k_jam_fg(const SysDev *__restrict
     for (int e = S.w_off[s]; e < S.w_off[s + 1]; ++e) {
       const int l = S.w_bin[e];
       const float w = S.w_val[e];
-      atomicAdd(&bnum[l], w * v);
-      atomicAdd(&bden[l], w * sb);
+      atomicAdd(&sm.bnum[l], w * v);
+      atomicAdd(&sm.bden[l], w * sb);
     }
   }
   __syncthreads();
   double *acc_g = ws.binacc + (size_t)b * max_bins * 2;
   for (int l = tid; l < S.n_bins; l += JAM_THREADS) {
-    if (bnum[l] != 0.0f) atomicAdd(&acc_g[2 * l], (double)bnum[l]);
-    if (bden[l] != 0.0f) atomicAdd(&acc_g[2 * l + 1], (double)bden[l]);
+    if (sm.bnum[l] != 0.0f) atomicAdd(&acc_g[2 * l], (double)sm.bnum[l]);
+    if (sm.bden[l] != 0.0f) atomicAdd(&acc_g[2 * l + 1], (double)sm.bden[l]);
   }
 }
 
@@ -785,7 +797,9 @@ cudaError_t grad_ws_ensure(glad_ctx *c, int B) {
 float *grad_resid_buffer(glad_ctx *c) { return c->gws ? c->gws->resid : nullptr; }
 
 cudaError_t launch_jam_fg(glad_ctx *c, const int *sys_id, int B, cudaStream_t st) {
-  dim3 grid(c->max_sky_tiles, B);
+  int tiles = 0;
+  for (auto &sd : c->h_sysdev) tiles = std::max(tiles, jam_tiles(sd.nsx, sd.nsy, 4));
+  dim3 grid(tiles, B);
   k_jam_fg<<<grid, JAM_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, *c->gws, c->max_light,
                                          c->max_ent, c->max_bins, c->max_sub);
   return cudaGetLastError();

@@ -12,6 +12,7 @@
 #include <algorithm>
 
 #include "glad_internal.cuh"
+#include "jam_common.cuh"
 
 namespace {
 
@@ -19,30 +20,6 @@ __device__ __forceinline__ float ex2(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
-}
-
-// Sky tiles are JAM_TW columns x (8 * PTS) rows of sub-samples; each warp covers JAM_TW
-// columns and PTS consecutive rows, each thread one column.  For a tile, a lower bound of
-// x'^2 and y'^2 over its points (from its corners: x', y' are linear in the pixel indices)
-// bounds every exponent ax x'^2 + ay y'^2 (ax, ay < 0) from above; table entries whose bound
-// is below -130 give 2^arg < 2^-130, which ex2.approx.ftz flushes to exactly 0, so they are
-// dropped while staging the chunk.  The kept entries keep their order and the chunk
-// boundaries of the FP32 partial sums are unchanged: every point's sum is bit-identical to
-// the one without skipping.
-#define JAM_TW 32
-#define JAM_SKIP_LOG2 (-130.0f)
-
-struct JamSmem {
-  float4 tab[2][JAM_CHUNK];
-  int wcount[2][2][JAM_THREADS / 32];  // [buffer][half of the chunk][warp]
-  int n_kept[2];
-  float bnum[GLAD_MAX_BINS], bden[GLAD_MAX_BINS];
-  float sI0[GLAD_MAX_LIGHT], scx[GLAD_MAX_LIGHT], scy[GLAD_MAX_LIGHT];
-};
-
-__host__ __device__ inline int jam_tiles(int nsx, int nsy, int pts) {
-  return ((nsx + JAM_TW - 1) / JAM_TW) * ((nsy + (JAM_THREADS / JAM_TW) * pts - 1) /
-                                         ((JAM_THREADS / JAM_TW) * pts));
 }
 
 template <int PTS, int UNR>
@@ -67,23 +44,8 @@ __device__ __forceinline__ void jam_tile(const SysDev &S, const WsDev &ws, JamSm
   const float cphi = (float)dp.cphi, sphi = (float)dp.sphi;
   const float xc = (float)dp.xc, yc = (float)dp.yc;
   const float hx = 0.5f * (S.nsx - 1), hy = 0.5f * (S.nsy - 1);
-  // lower bounds of x'^2 and y'^2 over the tile, slightly lowered against rounding
   float Xmin, Ymin;
-  {
-    float xmn = 1e30f, xmx = -1e30f, ymn = 1e30f, ymx = -1e30f;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float x = ((q & 1 ? c1 : c0) - hx) * S.dsub - xc;
-      const float y = ((q & 2 ? r1 : r0) - hy) * S.dsub - yc;
-      const float xp = cphi * x + sphi * y, yp = -sphi * x + cphi * y;
-      xmn = fminf(xmn, xp);
-      xmx = fmaxf(xmx, xp);
-      ymn = fminf(ymn, yp);
-      ymx = fmaxf(ymx, yp);
-    }
-    Xmin = (xmn <= 0.0f && xmx >= 0.0f) ? 0.0f : 0.999f * fminf(xmn * xmn, xmx * xmx);
-    Ymin = (ymn <= 0.0f && ymx >= 0.0f) ? 0.0f : 0.999f * fminf(ymn * ymn, ymx * ymx);
-  }
+  jam_tile_bounds(S, dp, c0, c1, r0, r1, Xmin, Ymin);
   // this thread's points: column col, rows row0 .. row0 + PTS - 1 (clamped into the tile)
   const int col = c0 + (tid % JAM_TW);
   const int row0 = r0 + (tid / JAM_TW) * PTS;
@@ -109,47 +71,15 @@ __device__ __forceinline__ void jam_tile(const SysDev &S, const WsDev &ws, JamSm
   const float4 *gt = ws.tab + (size_t)b * max_ent;
   const int n_ent = S.n_ent;
   const int n_chunks = (n_ent + JAM_CHUNK - 1) / JAM_CHUNK;
-  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  // staging of a chunk, phase 1: load two entries per thread and count the kept ones per warp
-  float4 v0, v1;
-  bool k0, k1;
-  auto stage_count = [&](int buf, int base) {
-    const int e0 = base + tid, e1 = base + tid + JAM_THREADS;
-    v0 = e0 < n_ent ? gt[e0] : zero4;
-    v1 = e1 < n_ent ? gt[e1] : zero4;
-    k0 = e0 < n_ent && fmaf(v0.y, Ymin, v0.x * Xmin) >= JAM_SKIP_LOG2;
-    k1 = e1 < n_ent && fmaf(v1.y, Ymin, v1.x * Xmin) >= JAM_SKIP_LOG2;
-    const unsigned m0 = __ballot_sync(0xffffffffu, k0), m1 = __ballot_sync(0xffffffffu, k1);
-    if (lane == 0) {
-      sm.wcount[buf][0][warp] = __popc(m0);
-      sm.wcount[buf][1][warp] = __popc(m1);
-    }
-  };
-  // phase 2 (after a barrier): write the kept entries in their original order
-  auto stage_write = [&](int buf) {
-    const unsigned lt = (1u << lane) - 1u;
-    const unsigned m0 = __ballot_sync(0xffffffffu, k0), m1 = __ballot_sync(0xffffffffu, k1);
-    int off0 = 0, tot0 = 0, off1 = 0, tot1 = 0;
-#pragma unroll
-    for (int w = 0; w < JAM_THREADS / 32; ++w) {
-      const int a0 = sm.wcount[buf][0][w], a1 = sm.wcount[buf][1][w];
-      off0 += w < warp ? a0 : 0;
-      off1 += w < warp ? a1 : 0;
-      tot0 += a0;
-      tot1 += a1;
-    }
-    if (k0) sm.tab[buf][off0 + __popc(m0 & lt)] = v0;
-    if (k1) sm.tab[buf][tot0 + off1 + __popc(m1 & lt)] = v1;
-    if (tid == 0) sm.n_kept[buf] = tot0 + tot1;
-  };
-  stage_count(0, 0);
+  JamStager stg;
+  stg.count(gt, n_ent, 0, Xmin, Ymin, sm.wcount[0]);
   __syncthreads();
-  stage_write(0);
+  stg.write(sm.tab[0], sm.wcount[0], &sm.n_kept[0]);
   __syncthreads();
   for (int ch = 0; ch < n_chunks; ++ch) {
     const int cur = ch & 1;
     const bool more = ch + 1 < n_chunks;
-    if (more) stage_count(cur ^ 1, (ch + 1) * JAM_CHUNK);
+    if (more) stg.count(gt, n_ent, (ch + 1) * JAM_CHUNK, Xmin, Ymin, sm.wcount[cur ^ 1]);
     const float4 *t = sm.tab[cur];
     const int nk = sm.n_kept[cur];
 #pragma unroll UNR
@@ -171,7 +101,7 @@ __device__ __forceinline__ void jam_tile(const SysDev &S, const WsDev &ws, JamSm
       acc[p] = make_float2(0.f, 0.f);
     }
     __syncthreads();
-    if (more) stage_write(cur ^ 1);
+    if (more) stg.write(sm.tab[cur ^ 1], sm.wcount[cur ^ 1], &sm.n_kept[cur ^ 1]);
     __syncthreads();
   }
   // tracer surface brightness and the binning-after-PSF scatter
