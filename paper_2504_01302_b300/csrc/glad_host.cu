@@ -308,6 +308,18 @@ glad_status build_system(int idx, const glad_system_desc &d, SysHost &sh, SysDev
     sh.n_ent = n_ent;
     sd.gl_u = upload(sh, gu.data(), n_ent);
     sd.gl_wu = upload(sh, gw.data(), n_ent);
+    // entry order for the adjoint: ascending p = 1/(2 s_k^2) + u^2/(2 s_j^2)
+    std::vector<double> pe(n_ent);
+    for (int k = 0; k < nL; ++k)
+      for (int j = 0; j < nMt; ++j)
+        for (int g = 0; g < G; ++g) {
+          const int e = (k * nMt + j) * G + g;
+          pe[e] = 1.0 / (2.0 * sig_l[k] * sig_l[k]) + gu[e] * gu[e] / (2.0 * sig_m[j] * sig_m[j]);
+        }
+    std::vector<int> perm(n_ent);
+    for (int e = 0; e < n_ent; ++e) perm[e] = e;
+    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return pe[a] < pe[b]; });
+    sd.adj_perm = upload(sh, perm.data(), n_ent);
   }
   {
     std::vector<float> cx(nL), cy(nL);
@@ -336,6 +348,8 @@ glad_status build_system(int idx, const glad_system_desc &d, SysHost &sh, SysDev
   sd.img_xy = upload(sh, d.img_xy, 2 * (size_t)d.n_img);
   sd.dt_obs = upload(sh, d.dt_obs, d.n_img - 1);
   sd.dt_sig = upload(sh, d.dt_sig, d.n_img - 1);
+  sd.atx = (sd.nsx + 15) / 16;
+  sd.n_atile = sd.atx * ((sd.nsy + 15) / 16);
   sd.n_img_tiles = (npix + LENS_THREADS - 1) / LENS_THREADS;
   sd.n_sky_tiles = (sd.n_sub + JAM_TILE - 1) / JAM_TILE;
   sd.n_tab_blocks = (sd.n_ent + TAB_THREADS - 1) / TAB_THREADS;
@@ -508,6 +522,7 @@ glad_status glad_create(const glad_system_desc *sys, int n_sys, glad_ctx **out) 
     c->max_img_tiles = std::max(c->max_img_tiles, d.n_img_tiles);
     c->max_sky_tiles = std::max(c->max_sky_tiles, d.n_sky_tiles);
     c->max_tab_blocks = std::max(c->max_tab_blocks, d.n_tab_blocks);
+    c->max_apts = std::max(c->max_apts, d.n_atile * 256);
   }
   if (cudaMalloc(&c->d_sys, sizeof(SysDev) * n_sys) != cudaSuccess ||
       cudaMemcpy(c->d_sys, c->h_sysdev.data(), sizeof(SysDev) * n_sys, cudaMemcpyHostToDevice) !=

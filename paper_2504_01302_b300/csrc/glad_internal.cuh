@@ -63,6 +63,10 @@ struct SysDev {
   const double *img_xy, *dt_obs, *dt_sig;
   // tile counts
   int n_img_tiles, n_sky_tiles, n_tab_blocks;
+  // gradient adjoint: table entries in ascending order of their x exponent p (fixed per
+  // system) and the sky grid in 16 x 16 point tiles (atx across, n_atile in all)
+  const int *adj_perm;                      // [n_ent]
+  int atx, n_atile;
 };
 
 // per-sample lensing parameters (FP32), written by the prep kernel
@@ -124,6 +128,7 @@ struct glad_ctx {
   SysDev *d_sys = nullptr;       // [n_sys]
   std::vector<SysDev> h_sysdev;  // host copy of the device descriptors
   int max_light = 0, max_mass_tot = 0, max_ent = 0, max_pix = 0, max_bins = 0, max_sub = 0;
+  int max_apts = 0;  // largest 16 x 16-tiled sky grid (points, padded)
   int max_img_tiles = 0, max_sky_tiles = 0, max_tab_blocks = 0;
   Workspace ws;
   GradWs *gws = nullptr;

@@ -27,7 +27,7 @@ struct GradWs {
   float *resid = nullptr;    // [B*max_pix]  d logL / d m (blurred model)
   float *gpix = nullptr;     // [B*max_pix]  d logL / d img (unblurred)
   float4 *pt = nullptr;      // [B*max_sub]  V, dV/dX, dV/dY (X = x'^2, Y = y'^2)
-  float4 *adjpt = nullptr;   // [B*max_sub*2] (X, X, Y, Y), (XY, XY, g_N, g_N)
+  float4 *adjpt = nullptr;   // [B*max_apts*2] (X, X, Y, Y), (XY, XY, g_N, g_N), 16x16-tile order
   double *entadj = nullptr;  // [B*max_ent*3] d logL / d (Q0, Q1, a_y)
   double *adjI0 = nullptr;   // [B*max_light] d logL / d I0_k (tracer amplitudes)
   std::vector<void *> allocs;
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(JAM_THREADS, 3) k_jam_fg(const SysDev *__restr
 __global__ void __launch_bounds__(JAM_THREADS) k_kin_adj(const SysDev *__restrict__ sysv,
                                                          const int *__restrict__ sys_id, WsDev ws,
                                                          GradWs gw, int max_light, int max_bins,
-                                                         int max_sub, double *grad) {
+                                                         int max_sub, int max_apts, double *grad) {
   const int b = blockIdx.y;
   if (ws.status[b] != GLAD_SAMPLE_OK) return;
   const SysDev &S = sysv[sys_id[b]];
@@ -439,8 +439,11 @@ __global__ void __launch_bounds__(JAM_THREADS) k_kin_adj(const SysDev *__restric
     gphi += 2.0f * xp * yp * (aX - aY);
     gxc += aX * (-2.0f * xp * cphi) + aY * (2.0f * yp * sphi);
     gyc += aX * (-2.0f * xp * sphi) + aY * (-2.0f * yp * cphi);
-    gw.adjpt[2 * ((size_t)b * max_sub + s)] = make_float4(X, X, Y, Y);
-    gw.adjpt[2 * ((size_t)b * max_sub + s) + 1] = make_float4(X * Y, X * Y, gn, gn);
+    // position in 16 x 16 point tiles (tile-major), the adjoint's chunk order
+    const size_t pos = (size_t)b * max_apts +
+                       (size_t)((I >> 4) * S.atx + (J >> 4)) * 256 + (I & 15) * 16 + (J & 15);
+    gw.adjpt[2 * pos] = make_float4(X, X, Y, Y);
+    gw.adjpt[2 * pos + 1] = make_float4(X * Y, X * Y, gn, gn);
   }
   const int lane = tid & 31, warp = tid >> 5;
   for (int off = 16; off > 0; off >>= 1) {
@@ -464,15 +467,18 @@ __global__ void __launch_bounds__(JAM_THREADS) k_kin_adj(const SysDev *__restric
 }
 
 #define ADJ_THREADS 256
-#define ADJ_PCHUNK 256     // sky points per shared-memory chunk
+#define ADJ_PCHUNK 256     // sky points per shared-memory chunk: one 16 x 16 tile
 
 // d logL / d (Q0, Q1, a_y) of each table entry: sums over every sky point of
 // g_N(s) E(s) {1, X, (Q0 + Q1 X) Y} with E = 2^(ax X + ay Y).  Each thread owns EPT entries,
-// handled as EPT/2 packed pairs against the pre-duplicated point data.
+// handled as EPT/2 packed pairs against the pre-duplicated point data.  Entries are taken in
+// ascending order of p (adj_perm) so that a warp's entries decay alike; a warp skips a
+// 16 x 16 point tile for an entry pair when the exponent bound of every lane's pair over the
+// tile is below -130 (all those E flush to exactly 0, as in the forward kernel).
 template <int EPT>
 __global__ void __launch_bounds__(ADJ_THREADS) k_jam_adj(const SysDev *__restrict__ sysv,
                                                          const int *__restrict__ sys_id, WsDev ws,
-                                                         GradWs gw, int max_ent, int max_sub) {
+                                                         GradWs gw, int max_ent, int max_apts) {
   constexpr int NP = EPT / 2;
   const int b = blockIdx.y;
   if (ws.status[b] != GLAD_SAMPLE_OK) return;
@@ -481,45 +487,64 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_jam_adj(const SysDev *__restric
   if (e0 >= S.n_ent) return;
   __shared__ float4 pts[2][2 * ADJ_PCHUNK];
   const int tid = threadIdx.x;
-  // entry pair p of the thread: entries e0 + tid + (2p) * T and e0 + tid + (2p+1) * T
+  const DynP dp = ws.dp[b];
+  // entry pair p of the thread: sorted positions e0 + tid + (2p) * T and e0 + tid + (2p+1) * T
+  int ent[EPT];
   float2 ax[NP], ay[NP], s0[NP], sx[NP], sy[NP], sxy[NP];
   double S0[EPT], SX[EPT], SY[EPT], SXY[EPT];
   const float4 *gt = ws.tab + (size_t)b * max_ent;
   const float2 z2 = make_float2(0.f, 0.f);
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    const int o = e0 + tid + k * ADJ_THREADS;
+    ent[k] = o < S.n_ent ? S.adj_perm[o] : -1;
+  }
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
-    const int ea = e0 + tid + (2 * p) * ADJ_THREADS, eb = ea + ADJ_THREADS;
-    const float4 ca = ea < S.n_ent ? gt[ea] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 cb = eb < S.n_ent ? gt[eb] : make_float4(0.f, 0.f, 0.f, 0.f);
-    ax[p] = make_float2(ca.x, cb.x);
-    ay[p] = make_float2(ca.y, cb.y);
+    const float4 ca = ent[2 * p] >= 0 ? gt[ent[2 * p]] : z4;
+    const float4 cb = ent[2 * p + 1] >= 0 ? gt[ent[2 * p + 1]] : z4;
+    // padding entries get a hugely negative exponent so that they never keep a tile alive
+    ax[p] = make_float2(ent[2 * p] >= 0 ? ca.x : -1e30f, ent[2 * p + 1] >= 0 ? cb.x : -1e30f);
+    ay[p] = make_float2(ent[2 * p] >= 0 ? ca.y : -1e30f, ent[2 * p + 1] >= 0 ? cb.y : -1e30f);
     s0[p] = sx[p] = sy[p] = sxy[p] = z2;
   }
 #pragma unroll
   for (int k = 0; k < EPT; ++k) S0[k] = SX[k] = SY[k] = SXY[k] = 0.0;
-  const float4 *gp = gw.adjpt + 2 * (size_t)b * max_sub;
-  const int n = S.n_sub;
-  const int n_chunks = (n + ADJ_PCHUNK - 1) / ADJ_PCHUNK;
-  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int i = tid; i < 2 * ADJ_PCHUNK; i += ADJ_THREADS) pts[0][i] = i < 2 * n ? gp[i] : z4;
+  const float4 *gp = gw.adjpt + 2 * (size_t)b * max_apts;
+  const int n_chunks = S.n_atile;
+  for (int i = tid; i < 2 * ADJ_PCHUNK; i += ADJ_THREADS) pts[0][i] = gp[i];
   __syncthreads();
   for (int ch = 0; ch < n_chunks; ++ch) {
     const int cur = ch & 1;
     if (ch + 1 < n_chunks) {
       const int base = 2 * (ch + 1) * ADJ_PCHUNK;
-      for (int i = tid; i < 2 * ADJ_PCHUNK; i += ADJ_THREADS)
-        pts[cur ^ 1][i] = base + i < 2 * n ? gp[base + i] : z4;
+      for (int i = tid; i < 2 * ADJ_PCHUNK; i += ADJ_THREADS) pts[cur ^ 1][i] = gp[base + i];
+    }
+    // which entry pairs this warp needs on this tile
+    float Xm, Ym;
+    {
+      const int c0 = (ch % S.atx) * 16, r0 = (ch / S.atx) * 16;
+      jam_tile_bounds(S, dp, c0, min(c0 + 15, S.nsx - 1), r0, min(r0 + 15, S.nsy - 1), Xm, Ym);
+    }
+    bool need[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const bool mine = fmaf(ay[p].x, Ym, ax[p].x * Xm) >= JAM_SKIP_LOG2 ||
+                        fmaf(ay[p].y, Ym, ax[p].y * Xm) >= JAM_SKIP_LOG2;
+      need[p] = __any_sync(0xffffffffu, mine);
     }
     const float4 *pp = pts[cur];
-#pragma unroll 2
-    for (int i = 0; i < ADJ_PCHUNK; ++i) {
-      const float4 A = pp[2 * i], Bq = pp[2 * i + 1];  // (X, X, Y, Y), (XY, XY, g, g)
-      const float2 X2 = make_float2(A.x, A.y), Y2 = make_float2(A.z, A.w);
-      const float2 XY2 = make_float2(Bq.x, Bq.y), G2 = make_float2(Bq.z, Bq.w);
 #pragma unroll
-      for (int p = 0; p < NP; ++p) {
+    for (int p = 0; p < NP; ++p) {
+      if (!need[p]) continue;  // warp-uniform
+#pragma unroll 4
+      for (int i = 0; i < ADJ_PCHUNK; ++i) {
+        const float4 A = pp[2 * i], Bq = pp[2 * i + 1];  // (X, X, Y, Y), (XY, XY, g, g)
+        const float2 X2 = make_float2(A.x, A.y), Y2 = make_float2(A.z, A.w);
+        const float2 XY2 = make_float2(Bq.x, Bq.y), G2 = make_float2(Bq.z, Bq.w);
         const float2 arg = __ffma2_rn(ay[p], Y2, __fmul2_rn(ax[p], X2));
-        const float2 tg = __fmul2_rn(G2, make_float2(ex2(arg.x), ex2(arg.y)));
+        const float2 tg = __fmul2_rn(G2, make_float2(jam_ex2(arg.x), jam_ex2(arg.y)));
         s0[p] = __fadd2_rn(s0[p], tg);
         sx[p] = __ffma2_rn(tg, X2, sx[p]);
         sy[p] = __ffma2_rn(tg, Y2, sy[p]);
@@ -542,8 +567,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_jam_adj(const SysDev *__restric
   }
 #pragma unroll
   for (int k = 0; k < EPT; ++k) {
-    const int e = e0 + tid + k * ADJ_THREADS;
-    if (e >= S.n_ent) continue;
+    const int e = ent[k];
+    if (e < 0) continue;
     const float4 c = gt[e];
     double *o = gw.entadj + ((size_t)b * max_ent + e) * 3;
     o[0] = S0[k];
@@ -784,7 +809,7 @@ cudaError_t grad_ws_ensure(glad_ctx *c, int B) {
   GradWs &w = *c->gws;
   const size_t b = B;
   const bool ok = galloc(w, w.resid, b * c->max_pix) && galloc(w, w.gpix, b * c->max_pix) &&
-                  galloc(w, w.pt, b * c->max_sub) && galloc(w, w.adjpt, 2 * b * c->max_sub) &&
+                  galloc(w, w.pt, b * c->max_sub) && galloc(w, w.adjpt, 2 * b * c->max_apts) &&
                   galloc(w, w.entadj, b * c->max_ent * 3) && galloc(w, w.adjI0, b * c->max_light);
   if (!ok) {
     grad_ws_free(c);
@@ -811,6 +836,8 @@ cudaError_t launch_grad(glad_ctx *c, const int *sys_id, const double *theta, int
   GradWs &g = *c->gws;
   cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(double) * GLAD_NTHETA * (size_t)B, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(g.adjI0, 0, sizeof(double) * c->max_light * (size_t)B, st);
+  // tile padding beyond the sky grid must read as g_N = 0
+  if (e == cudaSuccess) e = cudaMemsetAsync(g.adjpt, 0, sizeof(float4) * 2 * c->max_apts * (size_t)B, st);
   if (e != cudaSuccess) return e;
   // lensing
   e = GLAD_PROF(c, st, KID_GRAD_LENS, ([&]() -> cudaError_t {
@@ -833,7 +860,7 @@ cudaError_t launch_grad(glad_ctx *c, const int *sys_id, const double *theta, int
   if (e != cudaSuccess) return e;
   // dynamics
   k_kin_adj<<<dim3(c->max_sky_tiles, B), JAM_THREADS, 0, st>>>(
-      c->d_sys, sys_id, c->ws.d, g, c->max_light, c->max_bins, c->max_sub, grad);
+      c->d_sys, sys_id, c->ws.d, g, c->max_light, c->max_bins, c->max_sub, c->max_apts, grad);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = GLAD_PROF(c, st, KID_GRAD_JAM_ADJ, ([&]() -> cudaError_t {
@@ -841,10 +868,10 @@ cudaError_t launch_grad(glad_ctx *c, const int *sys_id, const double *theta, int
     const int nb = (c->max_ent + ADJ_THREADS * ept - 1) / (ADJ_THREADS * ept);
     if (ept == 2)
       k_jam_adj<2><<<dim3(nb, B), ADJ_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, g, c->max_ent,
-                                                        c->max_sub);
+                                                        c->max_apts);
     else
       k_jam_adj<4><<<dim3(nb, B), ADJ_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, g, c->max_ent,
-                                                        c->max_sub);
+                                                        c->max_apts);
     return cudaGetLastError();
   }()));
   if (e != cudaSuccess) return e;
@@ -866,10 +893,10 @@ cudaError_t time_jam_adj(glad_ctx *c, const int *sys_id, int B, cudaStream_t st)
   const int nb = (c->max_ent + ADJ_THREADS * ept - 1) / (ADJ_THREADS * ept);
   if (ept == 2)
     k_jam_adj<2><<<dim3(nb, B), ADJ_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, g, c->max_ent,
-                                                      c->max_sub);
+                                                      c->max_apts);
   else
     k_jam_adj<4><<<dim3(nb, B), ADJ_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, g, c->max_ent,
-                                                      c->max_sub);
+                                                      c->max_apts);
   return cudaGetLastError();
 }
 

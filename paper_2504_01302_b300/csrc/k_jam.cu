@@ -27,7 +27,7 @@ __device__ __forceinline__ void jam_tile(const SysDev &S, const WsDev &ws, JamSm
                                          int tile, int max_light, int max_ent, int max_bins) {
   constexpr int NP = PTS / 2;
   constexpr int TH = (JAM_THREADS / JAM_TW) * PTS;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   const DynP dp = ws.dp[b];
   const int ntx = (S.nsx + JAM_TW - 1) / JAM_TW;
   const int c0 = (tile % ntx) * JAM_TW, r0 = (tile / ntx) * TH;
