@@ -14,6 +14,7 @@ Prints one JSON line (rank 0).  --impl reference times the FP64 oracle instead, 
 the host cores, over a bounded sample of the same workload.
 """
 import argparse
+import hashlib
 import ctypes as C
 import json
 import os
@@ -47,9 +48,41 @@ def parse():
     p.add_argument("--grad", action="store_true", help="time logL + gradient (batch 64)")
     p.add_argument("--batch", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--tuning", default="",
+                   help="JAMCODE,EPT: pin the JAM launch shapes instead of autotuning")
     p.add_argument("--graph", type=int, default=-1,
                    help="1: replay the step as a captured CUDA graph (default: on for workload 3)")
     return p.parse_args()
+
+
+def ncu_traffic(kernel, w, grad, B):
+    """DRAM bytes (read + write) per launch of the timed kernel ``kernel`` from the committed
+    ncu summary that captured it on this workload, scaled from the captured batch to B by
+    samples (each sample reads its own coefficient table and writes its own accumulators).
+    None when no summary matches or when the kernel's sources have changed since the capture:
+    each record carries the sha256 of the source files it was built from."""
+    here = os.path.dirname(os.path.abspath(__file__))
+    pdir = os.path.join(here, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    for fn in sorted(os.listdir(pdir)):
+        if not fn.endswith(".md"):
+            continue
+        for ln in open(os.path.join(pdir, fn)):
+            ln = ln.strip().strip("`")
+            if not ln.startswith("traffic-record:"):
+                continue
+            rec = dict(kv.split("=", 1) for kv in ln.split()[1:])
+            if rec["kernel"] != kernel or int(rec["workload"]) != w or int(rec["grad"]) != int(grad):
+                continue
+            h = hashlib.sha256()
+            for f in rec["sources"].split(","):
+                with open(os.path.join(here, f), "rb") as fh:
+                    h.update(fh.read())
+            if h.hexdigest() != rec["sha256"]:
+                return None
+            return int(rec["dram_bytes"]) * B / int(rec["batch"])
+    return None
 
 
 def workload_name(w, grad, B):
@@ -261,8 +294,13 @@ def main():
             rc = lib.glad_loglike(ctx.handle, P(sid), P(theta), B, P(logL), P(status), None, hs)
         _lib.check(rc, "step")
 
-    # launch shapes picked by the library's autotuner on this batch (untimed)
-    tuning = ctx.autotune(theta, sid, with_grad=args.grad)
+    # launch shapes picked by the library's autotuner on this batch (untimed), or pinned
+    if args.tuning:
+        jc, ept = (int(v) for v in args.tuning.split(","))
+        ctx.set_tuning(jc, ept)
+        tuning = {"jam_pts": jc, "adj_ept": ept}
+    else:
+        tuning = ctx.autotune(theta, sid, with_grad=args.grad)
     # L2 flush buffer (256 MB > 126 MB L2), written before each timed step, outside its events
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
@@ -389,7 +427,10 @@ def main():
                    "l2": "flushed (256 MB write) before each timed step", "valid_samples": n_valid,
                    "tuning": tuning, "cuda_graph": bool(use_graph)},
         "roofline": {"bound": "alu", "kernel": names[jam_id], "achieved": achieved, "peak": peak,
-                     "unit": "Gexp2/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "Gexp2/s", "frac": achieved / peak,
+                     "traffic": ncu_traffic(names[jam_id], w, args.grad, B),
+                     "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                      "small-batch capture, scaled by samples to this batch",
                      "algorithmic_units": f"{evals} JAM integrand evaluations per launch (1 ex2 each)",
                      "peak_basis": f"{N_SM} SM x {MUFU_EX2_PER_CLK_SM} ex2/clk/SM (measured) x "
                                    f"{sm_max:.0f} MHz max SM clock"},
