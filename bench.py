@@ -34,7 +34,7 @@ from paper_2504_01302_b300 import synth  # noqa: E402
 METRIC = "joint logL evals/sec and logL+grad evals/sec at 1 B300, at stated FP64-oracle accuracy"
 N_SM = 148
 # ex2.approx results per clock per SM on B300 (MUFU), measured by a throughput probe
-# (profiles/mufu_ffma_rates_b300.md): 32.3-32.8 ex2/clk/SM.
+# (paper_2504_01302_b300/rates/probe_rates.cu): 32.3-32.8 ex2/clk/SM.
 MUFU_EX2_PER_CLK_SM = 32
 
 
@@ -384,6 +384,32 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t[0])
     h2d = th_h.numel() * 8 + sid_h.numel() * 4
+
+    # ---- the plain form: the same kernels called once per sample (B = 1), no graph,
+    # on the first n_plain samples of the batch, L2 not flushed between calls
+    n_plain = min(B, 32)
+
+    def plain_call(b):
+        hs = C.c_void_p(stream.cuda_stream)
+        if args.grad:
+            rc = lib.glad_loglike_grad(ctx.handle, P(sid[b:b + 1]), P(theta[b:b + 1]), 1,
+                                       P(logL[b:b + 1]), P(grad[b:b + 1]), P(status[b:b + 1]),
+                                       None, hs)
+        else:
+            rc = lib.glad_loglike(ctx.handle, P(sid[b:b + 1]), P(theta[b:b + 1]), 1,
+                                  P(logL[b:b + 1]), P(status[b:b + 1]), None, hs)
+        _lib.check(rc, "plain step")
+
+    for b in range(min(n_plain, 3)):
+        plain_call(b)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for b in range(n_plain):
+        plain_call(b)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = p0.elapsed_time(p1)
     d2h = out_h.numel() * 8 + st_h.numel() * 4 + (gr_h.numel() * 8 if args.grad else 0)
 
     if rank != 0:
@@ -435,6 +461,8 @@ def main():
                      "peak_basis": f"{N_SM} SM x {MUFU_EX2_PER_CLK_SM} ex2/clk/SM (measured) x "
                                    f"{sm_max:.0f} MHz max SM clock"},
         "kernels_ms_per_step": per_kernel,
+        "plain_form": {"value": n_plain / (plain_ms / 1000.0), "unit": unit, "samples": n_plain,
+                       "form": "one sample per call (B = 1), same kernels, no graph"},
         "e2e": {"value": world * B * args.steps / (e2e_ms / 1000.0), "unit": unit,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         # launches of the library's kernels inside the timed region (per-step count from the

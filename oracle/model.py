@@ -87,29 +87,60 @@ def sky_geometry(sysd):
     return X, Y, float(np.max(np.hypot(X, Y)))
 
 
-def dynamics(th, sysd, want_maps=False):
-    """v_rms per bin (and intermediate maps).  Returns (v_pre, status, extra)."""
+def dynamics_setup(th, sysd):
+    """Steps of the dynamics chain up to the pair table: (status, pieces)."""
     inc = th[IDX["inc"]]
     tr = light_mge(th, sysd)
     L_tot = float(np.sum(2 * math.pi * tr["I0"] * tr["sig"] ** 2 * tr["qp"]))
     ms = mass_mge(th, sysd, L_tot)
     qmin = min(np.min(tr["qp"]), np.min(ms["qp"]))
     if math.cos(inc) ** 2 >= qmin ** 2:
-        return None, ST_DEPROJ, {}
+        return ST_DEPROJ, None
     if not positive_density(tr, ms, inc):
-        return None, ST_NEGDENS, {}
+        return ST_NEGDENS, None
     v2u = cosmo.v2_unit(sysd["z_d"], sysd["z_s"], sysd["omega_m"], sysd["kappa_ext"])
     X, Y, r_max = sky_geometry(sysd)
     xp, yp = lens.frame(X, Y, th[IDX["x_c"]], th[IDX["y_c"]], th[IDX["phi"]])
     tab = jam.table(tr, ms, inc, th[IDX["beta"]], v2u, r_max, sysd["n_gl"])
-    sv2 = jam.sigma_v2_fast(xp, yp, tab).reshape(X.shape)
+    return ST_OK, dict(tr=tr, ms=ms, v2u=v2u, r_max=r_max, X=X, xp=xp, yp=yp, tab=tab)
+
+
+def dynamics(th, sysd, want_maps=False):
+    """v_rms per bin (and intermediate maps).  Returns (v_pre, status, extra)."""
+    st, d = dynamics_setup(th, sysd)
+    if st != ST_OK:
+        return None, st, {}
+    xp, yp, tr, tab = d["xp"], d["yp"], d["tr"], d["tab"]
+    sv2 = jam.sigma_v2_fast(xp, yp, tab).reshape(d["X"].shape)
     sb = jam.surface_brightness(xp, yp, tr)
     num, den = kin.bin_moments(sv2, sb, sysd)
     v = np.sqrt(num / den)
-    extra = dict(tr=tr, ms=ms, v2u=v2u, r_max=r_max, num=num, den=den)
+    extra = dict(tr=tr, ms=d["ms"], v2u=d["v2u"], r_max=d["r_max"], num=num, den=den)
     if want_maps:
         extra.update(sv2=sv2, sb=sb, xp=xp, yp=yp, tab=tab)
     return v, ST_OK, extra
+
+
+def vrms_bins(th, sysd, which, chunk=64):
+    """v_rms of the bins listed in ``which`` only (for grids whose full maps are out of
+    reach): the same chain as dynamics(), with Sigma v_los^2 and the tracer surface
+    brightness evaluated only on the sub-samples that PSF_kin carries into those bins
+    (the bins' sub-samples dilated by the kernel half-width) and zero elsewhere.  The
+    convolved maps on the bins' own sub-samples, and so their bin sums, are unchanged.
+    Returns (v[len(which)], status)."""
+    from scipy.ndimage import maximum_filter
+    st, d = dynamics_setup(th, sysd)
+    if st != ST_OK:
+        return None, st
+    lab = kin.subsample_bins(sysd["bins"], sysd["kss"])
+    K = np.asarray(sysd["kpsf"]).shape[0]
+    sup = maximum_filter(np.isin(lab, list(which)).astype(np.uint8), size=K, mode="constant") > 0
+    sv2 = np.zeros(lab.shape)
+    sb = np.zeros(lab.shape)
+    sv2[sup] = jam.sigma_v2_fast(d["xp"][sup], d["yp"][sup], d["tab"], chunk=chunk)
+    sb[sup] = jam.surface_brightness(d["xp"][sup], d["yp"][sup], d["tr"])
+    num, den = kin.bin_moments(sv2, sb, sysd)
+    return np.sqrt(num[list(which)] / den[list(which)]), ST_OK
 
 
 def evaluate(th, sysd, want=False):

@@ -49,5 +49,34 @@ def logl_tol(ref):
     posterior) plus 5e-6 |logL|.  FP32 ray shooting leaves ~1e-7 arcsec in beta; the
     source's logarithmic gradient (up to ~20/arcsec) turns that into model errors up
     to ~2e-6 relative, coherent over the arcs, so far from the data (chi^2 >> N) the
-    chi^2 error grows like 2 * 2e-6 * chi^2 (derivation in the design doc)."""
+    chi^2 error grows like 2 * 2e-6 * chi^2."""
     return 0.05 + 5e-6 * abs(ref)
+
+
+@functools.lru_cache(maxsize=None)
+def ifu_system():
+    """The IFU-scale system (400^2 x 3 image, 31^2 PSF, EPL + shear + 2 SIS, 40 + 2 x 20 MGE
+    + BH, 128^2 x 4 sky, 400 bins, GL64) with imaging data and delays from the oracle at the
+    truth.  The oracle's full v_rms map is out of reach at this size (2.75e10 integrand
+    evaluations), so v_obs is a seeded draw around 300 km/s with 2 % errors: the parity
+    checks compare the two paths on the same data, not the fit."""
+    from oracle import imaging, lens, tdelay
+    bases, _ = synth.workload_systems(4)
+    s = dict(bases[0])
+    truth = synth.theta_truth(1)
+    nz = synth.noise_draws(s, 4500)
+    s["img_xy"] = lens.solve_images(s["qso_beta"], truth, s["sis"],
+                                    synth.ring_images(truth[synth.IDX["theta_E"]], s["qso_beta"]))
+    m = imaging.model_image(truth, s)
+    s["data"] = (m + np.asarray(s["sigma"], np.float64) * nz["img"]).astype(np.float32)
+    rng = np.random.Generator(np.random.PCG64(4501))
+    v = 300.0 * (1.0 + 0.05 * rng.standard_normal(s["n_bins"]))
+    s["v_obs"] = v.astype(np.float32)
+    s["v_sig"] = (0.02 * v).astype(np.float32)
+    s["dt_obs"] = np.zeros(len(s["img_xy"]) - 1)
+    s["dt_sig"] = np.ones(len(s["img_xy"]) - 1)
+    dt = tdelay.delays(truth, s)
+    sig = 0.016 * np.abs(dt) + 0.1
+    s["dt_sig"] = sig
+    s["dt_obs"] = dt + sig * nz["dt"][:len(dt)]
+    return s
