@@ -96,7 +96,10 @@ extern "C" glad_status glad_autotune(glad_ctx *c, const int *sys_id, const doubl
   const std::string key = tune_key(c, B);
   int pts = 8, ept = 4;
   int code = 0;
-  if (cache_lookup(key, &code, &ept)) {
+  // a cached choice counts only while this build still has that launch shape
+  if (cache_lookup(key, &code, &ept) &&
+      jam_shape_supported((code % 100000) / 1000, (code % 1000) / 10, code % 10) &&
+      (ept == 2 || ept == 4)) {
     c->tune.jam_persistent = code / 100000;
     c->tune.jam_pts = (code % 100000) / 1000;
     c->tune.jam_minb = (code % 1000) / 10;
