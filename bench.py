@@ -425,6 +425,10 @@ def main():
     launches_per_step = (int(sum(kl[i] for i in range(nk))) + int(extra)) // max(prof_steps, 1)
     if args.grad:
         launches_per_step += 2  # k_kin_adj and k_grad_zero_invalid run untimed by the profiler
+    # integrand evaluations the JAM kernels actually execute per step (exact and negligible
+    # terms skipped), from one more untimed full-batch step
+    step()
+    n_exec = ctx.jam_evaluations()
     # ---- roofline of the dominant kernel (JAM pair sum): integrand evaluations per launch,
     # one ex2 each, against the MUFU ex2 rate
     names = [lib.glad_kernel_name(i).decode() for i in range(nk)]
@@ -451,13 +455,18 @@ def main():
         "config": {"workload": workload_name(w, args.grad, B), "batch_per_gpu": B,
                    "precision": "f32 bulk; f64 MGE, tables and chi^2 reductions",
                    "l2": "flushed (256 MB write) before each timed step", "valid_samples": n_valid,
-                   "tuning": tuning, "cuda_graph": bool(use_graph)},
+                   "tuning": tuning, "cuda_graph": bool(use_graph),
+                   "jam_skipping": "terms that underflow to 0 over a sky tile, and (forward pass) "
+                                   "terms whose bound over the tile stays below 2^-26 of its "
+                                   "smallest sum (checked after the sum)"},
         "roofline": {"bound": "alu", "kernel": names[jam_id], "achieved": achieved, "peak": peak,
                      "unit": "Gexp2/s", "frac": achieved / peak,
                      "traffic": ncu_traffic(names[jam_id], w, args.grad, B),
                      "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
                                       "small-batch capture, scaled by samples to this batch",
                      "algorithmic_units": f"{evals} JAM integrand evaluations per launch (1 ex2 each)",
+                     "executed_evaluations": n_exec,
+                     "executed_frac": n_exec / (jam_ms / 1000.0) / 1e9 / peak,
                      "peak_basis": f"{N_SM} SM x {MUFU_EX2_PER_CLK_SM} ex2/clk/SM (measured) x "
                                    f"{sm_max:.0f} MHz max SM clock"},
         "kernels_ms_per_step": per_kernel,

@@ -182,9 +182,27 @@ glad_status glad_autotune(glad_ctx *ctx, const int *sys_id, const double *theta,
                           int with_grad, void *stream);
 int glad_tuning(glad_ctx *ctx, int *jam_code, int *adj_ept);
 /* Pin a launch shape instead of tuning (codes as reported by glad_tuning: shapes
- * 4064, 8032, 8041, 8042, 8044, 8052, 16021, each optionally + 100000 for the persistent
+ * 4052, 4054, 4064, 8032, 8042, 8044, 16021, each optionally + 100000 for the persistent
  * form; adj_ept 2 or 4).  GLAD_EINVAL for other values. */
 glad_status glad_set_tuning(glad_ctx *ctx, int jam_code, int adj_ept);
+
+/* Negligible terms in the forward JAM pair sum (the project's own, no counterpart in the
+ * paper).  For every sky tile the full sum at the tile's four corners gives a reference
+ * value; a table entry whose term stays below 2^-(30 + log2 n_entries) of that reference
+ * over the whole tile is not evaluated there, and the summed bound of everything left out
+ * must come to at most 2^-26 of the smallest |Sigma v^2| in the tile (below the FP32
+ * rounding of each sum), else the tile is summed again with only the exact skipping of
+ * entries that underflow to zero.  mode 0: exact skipping only; 1 (the default): with
+ * negligible terms left out; 2: as 1 but every tile's check is failed (for tests: the
+ * tiles are summed twice and the results equal mode 0).  Applies to glad_loglike,
+ * glad_loglike_static, glad_vrms; the gradient pass uses exact skipping only.
+ * GLAD_EINVAL for other modes. */
+glad_status glad_set_negligible(glad_ctx *ctx, int mode);
+
+/* Integrand evaluations the JAM pair-sum kernels executed in the last glad_loglike,
+ * glad_loglike_grad or glad_vrms call on this context (skipped terms excluded).
+ * Synchronises the device. */
+glad_status glad_jam_evaluations(glad_ctx *ctx, unsigned long long *count);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *glad_last_error(void);

@@ -388,7 +388,8 @@ glad_status ws_ensure(glad_ctx *c, int B) {
             ws_alloc(w, w.d.I0f, b * c->max_light) && ws_alloc(w, w.d.tab, b * c->max_ent) &&
             ws_alloc(w, w.d.img, b * c->max_pix) && ws_alloc(w, w.d.binacc, b * c->max_bins * 2) &&
             ws_alloc(w, w.d.terms, b * 3) && ws_alloc(w, w.d.status, b) &&
-            ws_alloc(w, w.d.wl_off, b + 1) && ws_alloc(w, w.d.wl_counter, 1);
+            ws_alloc(w, w.d.wl_off, b + 1) && ws_alloc(w, w.d.wl_counter, 1) &&
+            ws_alloc(w, w.d.evals, 1);
   if (!ok) {
     ws_free(w);
     return fail(GLAD_ENOMEM, "workspace for B=%d does not fit on the device", B);
@@ -404,7 +405,9 @@ glad_status forward(glad_ctx *c, const int *sys_id, const double *theta, int B, 
   glad_status s = ws_ensure(c, B);
   if (s != GLAD_OK) return s;
   cudaError_t e;
+  c->ws.d.neg_mode = c->tune.neg_mode;
   e = cudaMemsetAsync(c->ws.d.terms, 0, sizeof(double) * 3 * B, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->ws.d.evals, 0, sizeof(unsigned long long), st);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(c->ws.d.binacc, 0, sizeof(double) * 2 * c->max_bins * (size_t)B, st);
   if (e == cudaSuccess) e = GLAD_PROF(c, st, KID_PREP, launch_prep(c, sys_id, theta, B, st));
@@ -463,6 +466,23 @@ cudaError_t prof_end(glad_ctx *c, cudaStream_t st, int id, cudaEvent_t a) {
 extern "C" {
 
 const char *glad_last_error(void) { return g_err.c_str(); }
+
+glad_status glad_set_negligible(glad_ctx *c, int mode) {
+  if (!c || mode < 0 || mode > 2) return fail(GLAD_EINVAL, "glad_set_negligible: mode %d", mode);
+  c->tune.neg_mode = mode;
+  return GLAD_OK;
+}
+
+glad_status glad_jam_evaluations(glad_ctx *c, unsigned long long *count) {
+  if (!c || !count) return fail(GLAD_EINVAL, "glad_jam_evaluations: bad arguments");
+  *count = 0;
+  if (!c->ws.d.evals) return GLAD_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess)
+    e = cudaMemcpy(count, c->ws.d.evals, sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(GLAD_ECUDA, "glad_jam_evaluations: %s", cudaGetErrorString(e));
+  return GLAD_OK;
+}
 
 int glad_profile(glad_ctx *c, int enable) {
   if (!c) return -1;

@@ -112,6 +112,9 @@ struct WsDev {
   int *status;                 // [B]
   int *wl_off;                 // [B+1] persistent JAM work list (first item of each sample)
   int *wl_counter;             // [1]   next work item
+  unsigned long long *evals;   // [1]   JAM integrand evaluations executed (null: not counted)
+  int neg_mode;                // negligible-term skipping in the forward JAM pass: 0 off,
+                               // 1 on, 2 on with every tile's check failed (summed again)
 };
 
 struct Workspace {
@@ -134,6 +137,7 @@ struct glad_ctx {
   GradWs *gws = nullptr;
   // launch shapes chosen by glad_autotune (defaults until it runs)
   struct Tune {
+    int neg_mode = 1;     // negligible-term skipping of the forward JAM pass (see WsDev)
     int jam_pts = 8;      // sky points per thread in the JAM pair-sum kernels
     int jam_minb = 4;     // minimum resident CTAs per SM requested from the register allocator
     int jam_unroll = 2;   // unroll of the table-entry loop

@@ -91,6 +91,7 @@ extern "C" glad_status glad_loglike_static(glad_ctx *c, const int *sys_id, const
     return glad_set_error(GLAD_ECUDA, m.c_str());
   }
   carve(c, B, (unsigned char *)base, &w);
+  w.neg_mode = c->tune.neg_mode;  // same JAM summation as glad_loglike; evaluations not counted
   cudaStream_t st = (cudaStream_t)stream;
   // the launchers read the context's workspace view: point it at the scratch for the
   // duration of the launches (kernel arguments are copied at launch) and restore it

@@ -19,11 +19,21 @@ __device__ __forceinline__ float jam_ex2(float x) {
 // the one without skipping.
 #define JAM_TW 32
 #define JAM_SKIP_LOG2 (-130.0f)
+// Negligible terms (forward pair sum): a term is left out when its largest magnitude over
+// the tile is below 2^-(JAM_REL_MARGIN + log2 n_ent) of the tile's reference sum, and the
+// bound on everything left out must come to at most 2^-JAM_REL_CHECK of the smallest |sum|
+// in the tile (2^-26: below the FP32 rounding of each sum), else the tile is summed again
+// without it.
+#define JAM_REL_MARGIN 30.0f
+#define JAM_REL_CHECK 26.0f
 
 struct JamSmem {
   float4 tab[2][JAM_CHUNK];
   int wcount[2][2][JAM_THREADS / 32];  // [buffer][half of the chunk][warp]
   int n_kept[2];
+  float red[4][JAM_THREADS / 32];      // block reductions of the negligible-term test
+  int flag;
+  float tb[5];                         // tile constants: Xmin, Ymin, Xmax, lref, lrel
   float bnum[GLAD_MAX_BINS], bden[GLAD_MAX_BINS];
   float sI0[GLAD_MAX_LIGHT], scx[GLAD_MAX_LIGHT], scy[GLAD_MAX_LIGHT];
 };
@@ -57,6 +67,23 @@ __device__ __forceinline__ void jam_tile_bounds(const SysDev &S, const DynP &dp,
   Ymin = (ymn <= 0.0f && ymx >= 0.0f) ? 0.0f : 0.999f * fminf(ymn * ymn, ymx * ymx);
 }
 
+// Upper bound of x'^2 over the same tile (the extremes of x' sit at the corners).
+__device__ __forceinline__ float jam_tile_xmax(const SysDev &S, const DynP &dp, int c0, int c1,
+                                               int r0, int r1) {
+  const float cphi = (float)dp.cphi, sphi = (float)dp.sphi;
+  const float xc = (float)dp.xc, yc = (float)dp.yc;
+  const float hx = 0.5f * (S.nsx - 1), hy = 0.5f * (S.nsy - 1);
+  float m = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float x = ((q & 1 ? c1 : c0) - hx) * S.dsub - xc;
+    const float y = ((q & 2 ? r1 : r0) - hy) * S.dsub - yc;
+    const float xp = cphi * x + sphi * y;
+    m = fmaxf(m, xp * xp);
+  }
+  return 1.001f * m;
+}
+
 // Order-preserving compaction of one JAM_CHUNK of table entries into shared memory, keeping
 // the entries whose exponent bound over the tile is >= JAM_SKIP_LOG2.  count() loads two
 // entries per thread and publishes per-warp counts; after a barrier write() stores the kept
@@ -77,6 +104,35 @@ struct JamStager {
     if (lane == 0) {
       wcount[0][warp] = __popc(m0);
       wcount[1][warp] = __popc(m1);
+    }
+  }
+  // count() with the negligible-term criterion as well: an entry is also dropped when
+  // 2^(bound) (|Q0| + |Q1| Xmax), the largest magnitude its term reaches over the tile,
+  // is below 2^lrel (lrel relative to a reference value of the tile's sums); the dropped
+  // magnitudes, relative to that reference, are added to drel.
+  // (tb: Xmin, Ymin, Xmax, lref, lrel of the tile, in shared memory)
+  __device__ __forceinline__ void count_rel(const float4 *gt, int n_ent, int base,
+                                            const volatile float *tb,
+                                            int (*wcount)[JAM_THREADS / 32], float &drel) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float Xmin = tb[0], Ymin = tb[1], Xmax = tb[2], lref = tb[3], lrel = tb[4];
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int e0 = base + tid, e1 = base + tid + JAM_THREADS;
+    v0 = e0 < n_ent ? gt[e0] : z;
+    v1 = e1 < n_ent ? gt[e1] : z;
+    const float b0 = fmaf(v0.y, Ymin, v0.x * Xmin), b1 = fmaf(v1.y, Ymin, v1.x * Xmin);
+    // log2 of the term's largest magnitude relative to the reference
+    const float m0 = b0 + __log2f(fabsf(v0.z) + fabsf(v0.w) * Xmax) - lref;
+    const float m1 = b1 + __log2f(fabsf(v1.z) + fabsf(v1.w) * Xmax) - lref;
+    const bool x0 = e0 < n_ent && b0 >= JAM_SKIP_LOG2, x1 = e1 < n_ent && b1 >= JAM_SKIP_LOG2;
+    k0 = x0 && m0 >= lrel;
+    k1 = x1 && m1 >= lrel;
+    if (x0 && !k0) drel += jam_ex2(m0);
+    if (x1 && !k1) drel += jam_ex2(m1);
+    const unsigned c0 = __ballot_sync(0xffffffffu, k0), c1 = __ballot_sync(0xffffffffu, k1);
+    if (lane == 0) {
+      wcount[0][warp] = __popc(c0);
+      wcount[1][warp] = __popc(c1);
     }
   }
   __device__ __forceinline__ void write(float4 *tab, int (*wcount)[JAM_THREADS / 32], int *n_kept) {

@@ -299,6 +299,8 @@ __global__ void __launch_bounds__(JAM_THREADS, 3) k_jam_fg(const SysDev *__restr
   const float4 *gt = ws.tab + (size_t)b * max_ent;
   const int n_ent = S.n_ent;
   const int n_chunks = (n_ent + JAM_CHUNK - 1) / JAM_CHUNK;
+  const unsigned long long npts = (unsigned long long)(c1 - c0 + 1) * (unsigned long long)(r1 - r0 + 1);
+  unsigned long long n_eval = 0;  // evaluations this tile executes (thread 0 keeps the count)
   JamStager stg;
   stg.count(gt, n_ent, 0, Xmin, Ymin, sm.wcount[0]);
   __syncthreads();
@@ -310,6 +312,7 @@ __global__ void __launch_bounds__(JAM_THREADS, 3) k_jam_fg(const SysDev *__restr
     if (more) stg.count(gt, n_ent, (ch + 1) * JAM_CHUNK, Xmin, Ymin, sm.wcount[cur ^ 1]);
     const float4 *tt = sm.tab[cur];
     const int nk = sm.n_kept[cur];
+    n_eval += (unsigned long long)nk * npts;
 #pragma unroll 2
     for (int e = 0; e < nk; ++e) {
       const float4 c = tt[e];
@@ -342,6 +345,7 @@ __global__ void __launch_bounds__(JAM_THREADS, 3) k_jam_fg(const SysDev *__restr
     if (more) stg.write(sm.tab[cur ^ 1], sm.wcount[cur ^ 1], &sm.n_kept[cur ^ 1]);
     __syncthreads();
   }
+  if (tid == 0 && ws.evals) atomicAdd(ws.evals, n_eval);
 #pragma unroll
   for (int i = 0; i < PTS; ++i) {
     if (col > c1 || row0 + i > r1) continue;

@@ -46,6 +46,67 @@ __device__ __forceinline__ void jam_tile(const SysDev &S, const WsDev &ws, JamSm
   const float hx = 0.5f * (S.nsx - 1), hy = 0.5f * (S.nsy - 1);
   float Xmin, Ymin;
   jam_tile_bounds(S, dp, c0, c1, r0, r1, Xmin, Ymin);
+  const float Xmax = jam_tile_xmax(S, dp, c0, c1, r0, r1);
+  const float4 *gt = ws.tab + (size_t)b * max_ent;
+  const int n_ent = S.n_ent;
+  const int n_chunks = (n_ent + JAM_CHUNK - 1) / JAM_CHUNK;
+  const int lane = tid & 31, warp = tid >> 5;
+  // Reference value of the tile's sums: the full sum at its four corners (their minimum).
+  // Terms whose magnitude stays below 2^-(JAM_REL_MARGIN + log2 n_ent) of it over the whole
+  // tile are left out; after the sum, the left-out magnitudes (a bound on their total) must
+  // stay below 2^-JAM_REL_CHECK of the smallest |sum| in the tile, else the tile is summed
+  // again with only the exact skipping.
+  float lref = 0.0f, lrel = -INFINITY;
+  if (ws.neg_mode != 0) {
+    float cX[4], cY[4], cv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float x = ((q & 1 ? c1 : c0) - hx) * S.dsub - xc;
+      const float y = ((q & 2 ? r1 : r0) - hy) * S.dsub - yc;
+      const float xp = cphi * x + sphi * y, yp = -sphi * x + cphi * y;
+      cX[q] = xp * xp;
+      cY[q] = yp * yp;
+      cv[q] = 0.0f;
+    }
+    for (int e = tid; e < n_ent; e += JAM_THREADS) {
+      const float4 c = gt[e];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        cv[q] = fmaf(fmaf(c.w, cX[q], c.z), ex2(fmaf(c.y, cY[q], c.x * cX[q])), cv[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      for (int off = 16; off > 0; off >>= 1) cv[q] += __shfl_xor_sync(0xffffffffu, cv[q], off);
+      if (lane == 0) sm.red[q][warp] = cv[q];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float ref = 3.4e38f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float t = 0.0f;
+        for (int w = 0; w < JAM_THREADS / 32; ++w) t += sm.red[q][w];
+        ref = fminf(ref, t);
+      }
+      sm.flag = (ref > 0.0f && ref < 3.4e38f) ? __float_as_int(__log2f(ref)) : 0x7fffffff;
+    }
+    __syncthreads();
+    const int f = sm.flag;
+    lref = f == 0x7fffffff ? 0.0f : __int_as_float(f);
+    // threshold relative to the reference; -inf (no usable reference): exact skipping only
+    lrel = f == 0x7fffffff ? -INFINITY : -(JAM_REL_MARGIN + __log2f((float)max(n_ent, 1)));
+  }
+  if (tid == 0) {
+    sm.tb[0] = Xmin;
+    sm.tb[1] = Ymin;
+    sm.tb[2] = Xmax;
+    sm.tb[3] = lref;
+    sm.tb[4] = lrel;
+  }
+  __syncthreads();
+  // evaluations this tile executes (thread 0 keeps the count)
+  const unsigned long long npts = (unsigned long long)(c1 - c0 + 1) * (unsigned long long)(r1 - r0 + 1);
+  unsigned long long n_eval = 0;
   // this thread's points: column col, rows row0 .. row0 + PTS - 1 (clamped into the tile)
   const int col = c0 + (tid % JAM_TW);
   const int row0 = r0 + (tid / JAM_TW) * PTS;
@@ -64,46 +125,81 @@ __device__ __forceinline__ void jam_tile(const SysDev &S, const WsDev &ws, JamSm
       X[i >> 1].x = xp * xp;
       Y[i >> 1].x = yp * yp;
     }
-    accd[i] = 0.0;
   }
+  for (;;) {
 #pragma unroll
-  for (int p = 0; p < NP; ++p) acc[p] = make_float2(0.f, 0.f);
-  const float4 *gt = ws.tab + (size_t)b * max_ent;
-  const int n_ent = S.n_ent;
-  const int n_chunks = (n_ent + JAM_CHUNK - 1) / JAM_CHUNK;
-  JamStager stg;
-  stg.count(gt, n_ent, 0, Xmin, Ymin, sm.wcount[0]);
-  __syncthreads();
-  stg.write(sm.tab[0], sm.wcount[0], &sm.n_kept[0]);
-  __syncthreads();
-  for (int ch = 0; ch < n_chunks; ++ch) {
-    const int cur = ch & 1;
-    const bool more = ch + 1 < n_chunks;
-    if (more) stg.count(gt, n_ent, (ch + 1) * JAM_CHUNK, Xmin, Ymin, sm.wcount[cur ^ 1]);
-    const float4 *t = sm.tab[cur];
-    const int nk = sm.n_kept[cur];
+    for (int i = 0; i < PTS; ++i) accd[i] = 0.0;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) acc[p] = make_float2(0.f, 0.f);
+    float drel = 0.0f;
+    JamStager stg;
+    stg.count_rel(gt, n_ent, 0, sm.tb, sm.wcount[0], drel);
+    __syncthreads();
+    stg.write(sm.tab[0], sm.wcount[0], &sm.n_kept[0]);
+    __syncthreads();
+    for (int ch = 0; ch < n_chunks; ++ch) {
+      const int cur = ch & 1;
+      const bool more = ch + 1 < n_chunks;
+      if (more)
+        stg.count_rel(gt, n_ent, (ch + 1) * JAM_CHUNK, sm.tb, sm.wcount[cur ^ 1], drel);
+      const float4 *t = sm.tab[cur];
+      const int nk = sm.n_kept[cur];
+      n_eval += (unsigned long long)nk * npts;
 #pragma unroll UNR
-    for (int e = 0; e < nk; ++e) {
-      const float4 c = t[e];
-      const float2 cx = make_float2(c.x, c.x), cy = make_float2(c.y, c.y);
-      const float2 cz = make_float2(c.z, c.z), cw = make_float2(c.w, c.w);
+      for (int e = 0; e < nk; ++e) {
+        const float4 c = t[e];
+        const float2 cx = make_float2(c.x, c.x), cy = make_float2(c.y, c.y);
+        const float2 cz = make_float2(c.z, c.z), cw = make_float2(c.w, c.w);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+          const float2 arg = __ffma2_rn(cy, Y[p], __fmul2_rn(cx, X[p]));
+          const float2 E = make_float2(ex2(arg.x), ex2(arg.y));
+          acc[p] = __ffma2_rn(__ffma2_rn(cw, X[p], cz), E, acc[p]);
+        }
+      }
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
-        const float2 arg = __ffma2_rn(cy, Y[p], __fmul2_rn(cx, X[p]));
-        const float2 E = make_float2(ex2(arg.x), ex2(arg.y));
-        acc[p] = __ffma2_rn(__ffma2_rn(cw, X[p], cz), E, acc[p]);
+        accd[2 * p] += (double)acc[p].x;
+        accd[2 * p + 1] += (double)acc[p].y;
+        acc[p] = make_float2(0.f, 0.f);
       }
+      __syncthreads();
+      if (more) stg.write(sm.tab[cur ^ 1], sm.wcount[cur ^ 1], &sm.n_kept[cur ^ 1]);
+      __syncthreads();
     }
+    if (lrel == -INFINITY) break;
+    // a-posteriori check: left-out magnitudes against the smallest |sum| of the tile
+    float vmin = 3.4e38f;
 #pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      accd[2 * p] += (double)acc[p].x;
-      accd[2 * p + 1] += (double)acc[p].y;
-      acc[p] = make_float2(0.f, 0.f);
+    for (int i = 0; i < PTS; ++i)
+      if (col <= c1 && row0 + i <= r1) vmin = fminf(vmin, fabsf((float)accd[i]));
+    for (int off = 16; off > 0; off >>= 1) {
+      vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, off));
+      drel += __shfl_xor_sync(0xffffffffu, drel, off);
+    }
+    if (lane == 0) {
+      sm.red[0][warp] = vmin;
+      sm.red[1][warp] = drel;
     }
     __syncthreads();
-    if (more) stg.write(sm.tab[cur ^ 1], sm.wcount[cur ^ 1], &sm.n_kept[cur ^ 1]);
+    if (tid == 0) {
+      float vm = 3.4e38f, dr = 0.0f;
+      for (int w = 0; w < JAM_THREADS / 32; ++w) {
+        vm = fminf(vm, sm.red[0][w]);
+        dr += sm.red[1][w];
+      }
+      // dropped total <= dr * 2^lref; accept when that is <= 2^-JAM_REL_CHECK * vm
+      sm.flag = (ws.neg_mode == 1 && __log2f(dr) + lref <= __log2f(vm) - JAM_REL_CHECK) ? 1 : 0;
+    }
+    __syncthreads();
+    const bool ok = sm.flag != 0;
+    __syncthreads();
+    if (ok) break;
+    lrel = -INFINITY;  // sum the tile again with the exact skipping only
+    if (tid == 0) sm.tb[4] = -INFINITY;
     __syncthreads();
   }
+  if (tid == 0 && ws.evals) atomicAdd(ws.evals, n_eval);
   // tracer surface brightness and the binning-after-PSF scatter
 #pragma unroll
   for (int i = 0; i < PTS; ++i) {
@@ -263,7 +359,7 @@ __global__ void k_combine(WsDev ws, int B, double *logL, int *status, double *te
 // candidate launch shapes of the JAM pair sum: (points per thread, minimum CTAs per SM
 // requested from the register allocator, unroll of the table-entry loop); the tuner times
 // these and the persistent forms
-#define GLAD_JAM_SHAPES(X) X(4, 6, 4) X(8, 3, 2) X(8, 4, 1) X(8, 4, 2) X(8, 4, 4) X(8, 5, 2) X(16, 2, 1)
+#define GLAD_JAM_SHAPES(X) X(4, 5, 2) X(4, 5, 4) X(4, 6, 4) X(8, 3, 2) X(8, 4, 2) X(8, 4, 4) X(16, 2, 1)
 
 bool jam_shape_supported(int pts, int minb, int unr) {
 #define GLAD_JAM_MATCH(P, M, U) if (pts == P && minb == M && unr == U) return true;

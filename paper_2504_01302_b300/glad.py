@@ -147,6 +147,16 @@ class GladContext:
         """Pin the JAM launch shapes (glad_set_tuning)."""
         _lib.check(self.lib.glad_set_tuning(self.handle, int(jam_code), int(adj_ept)), "glad_set_tuning")
 
+    def set_negligible(self, mode):
+        """Negligible-term skipping of the forward JAM pass (glad_set_negligible)."""
+        _lib.check(self.lib.glad_set_negligible(self.handle, int(mode)), "glad_set_negligible")
+
+    def jam_evaluations(self):
+        """Integrand evaluations the JAM kernels executed in the last call."""
+        n = C.c_ulonglong()
+        _lib.check(self.lib.glad_jam_evaluations(self.handle, C.byref(n)), "glad_jam_evaluations")
+        return n.value
+
     def kernel_times(self):
         """{kernel name: (ms, launches)} recorded since profiling was enabled."""
         n = self.lib.glad_kernel_times(self.handle, 0, None, None)
