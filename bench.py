@@ -29,7 +29,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_2504_01302_b300 import synth  # noqa: E402
+from paper_2504_01302_b300 import shard, synth  # noqa: E402
 
 METRIC = "joint logL evals/sec and logL+grad evals/sec at 1 B300, at stated FP64-oracle accuracy"
 N_SM = 148
@@ -273,7 +273,8 @@ def main():
     systems, B = bench_systems(w)
     systems = fill_data_with_gpu_model(systems, w, torch, GladContext)
     B = args.batch or (64 if args.grad else B)
-    th_np, sid_np = synth.workload_thetas(w, B, len(systems))
+    # this rank's share of a global batch of world * B samples (no collective on the data)
+    th_np, sid_np = shard.shard(*synth.workload_thetas(w, world * B, len(systems)), rank, world)
     ctx = GladContext(systems)
     lib = ctx.lib
     theta = torch.as_tensor(th_np, device="cuda")
@@ -353,9 +354,7 @@ def main():
     lib.glad_kernel_times(ctx.handle, nk, kms, kl)
     t_ms = sum(a.elapsed_time(b) for a, b in ev)
     if world > 1:
-        t = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t[0])
+        t_ms = shard.max_over_ranks(t_ms, dist, "cuda")
         dist.barrier()
     value = world * B * args.steps / (t_ms / 1000.0)
 
@@ -380,9 +379,7 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
     if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t[0])
+        e2e_ms = shard.max_over_ranks(e2e_ms, dist, "cuda")
     h2d = th_h.numel() * 8 + sid_h.numel() * 4
 
     # ---- the plain form: the same kernels called once per sample (B = 1), no graph,
