@@ -149,6 +149,16 @@ glad_status build_system(int idx, const glad_system_desc &d, SysHost &sh, SysDev
   sd.wgt = upload(sh, wgt.data(), npix);
   sd.psf_k = d.psf_k;
   sd.psf = upload(sh, d.psf, (size_t)d.psf_k * d.psf_k);
+  // the blocked convolution's copy: centred in the next supported side, transposed
+  sd.psf_km = d.psf_k <= 11 ? 11 : d.psf_k <= 21 ? 21 : d.psf_k <= 31 ? 31 : 0;
+  sd.psf_t = nullptr;
+  if (sd.psf_km) {
+    const int km = sd.psf_km, pt = CONV_PT(km), off = (km - d.psf_k) / 2;
+    std::vector<float> t((size_t)km * pt, 0.0f);
+    for (int a = 0; a < d.psf_k; ++a)
+      for (int cc = 0; cc < d.psf_k; ++cc) t[(size_t)(cc + off) * pt + (a + off)] = d.psf[a * d.psf_k + cc];
+    sd.psf_t = upload(sh, t.data(), t.size());
+  }
   sd.src_q = (float)d.src_q;
   sd.src_cphi = (float)cos(d.src_phi);
   sd.src_sphi = (float)sin(d.src_phi);

@@ -28,6 +28,9 @@ struct SysDev {
   const float *wgt;      // [npix] mask / sigma
   int psf_k;
   const float *psf;      // [psf_k^2]
+  int psf_km;            // padded side of psf_t (11, 21 or 31; 0 above 31)
+  const float *psf_t;    // [psf_km * CONV_PT(psf_km)]: psf centred in psf_km^2 zeros,
+                         // transposed (column c of the PSF is row c here), rows padded to 4
   float src_q, src_cphi, src_sphi;
   int n_lcomp;           // lens-light components (1 + n_ll2)
   const double *lcomp;   // [n_lcomp*4]: I_e, R_e, n, q (row 0: I_e, R_e from theta)
@@ -200,6 +203,8 @@ int jam_shape_list(int (*out)[3], int cap);
 #define TAB_THREADS 256
 #define CONV_TX 32
 #define CONV_TY 8
+#define CONV_PT(km) (((km) + 3) / 4 * 4)  // row stride of the transposed padded PSF
+#define CONV_R 8                          // output rows per thread in the blocked convolution
 
 // ---------------------------------------------------------------------------
 // math helpers usable from host and device

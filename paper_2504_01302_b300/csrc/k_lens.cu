@@ -6,6 +6,8 @@
 //  k_conv: PSF blurring (discrete convolution, zero outside the image) of a 32x8
 //    output tile staged with its halo in shared memory, and the masked pixel chi^2
 //    (Eq. chi2 of lens_light) reduced in FP64 per sample.
+#include <algorithm>
+
 #include "glad_internal.cuh"
 
 namespace {
@@ -95,6 +97,7 @@ __global__ void __launch_bounds__(CONV_TX *CONV_TY) k_conv(const SysDev *__restr
   const int b = blockIdx.y;
   if (ws.status[b] != GLAD_SAMPLE_OK) return;
   const SysDev &S = sysv[sys_id[b]];
+  if (S.psf_km != 0) return;  // blurred by k_conv_r
   const int ntx = (S.nx + CONV_TX - 1) / CONV_TX;
   const int nty = (S.ny + CONV_TY - 1) / CONV_TY;
   if ((int)blockIdx.x >= ntx * nty) return;
@@ -149,6 +152,101 @@ __global__ void __launch_bounds__(CONV_TX *CONV_TY) k_conv(const SysDev *__restr
   }
 }
 
+// Register-blocked PSF blurring for PSF sides up to KM (the PSF centred in KM x KM zeros:
+// the extra taps add exact zeros).  A CTA of 32 x 8 threads owns 32 columns x 8*CONV_R rows
+// of output; each thread one column and CONV_R consecutive rows.  For each PSF column c the
+// thread loads the CONV_R + KM - 1 tile values its outputs need (a vertical window, lanes on
+// consecutive columns: conflict-free) and the column of taps (float4 broadcasts), then does
+// CONV_R x KM FMAs from registers.  Per-column FP32 partial sums are added with Kahan
+// compensation; chi^2 as in k_conv.
+template <int KM>
+__global__ void __launch_bounds__(CONV_TX *CONV_TY) k_conv_r(const SysDev *__restrict__ sysv,
+                                                             const int *__restrict__ sys_id,
+                                                             WsDev ws, int max_pix,
+                                                             float *image_out, float *resid_out) {
+  constexpr int R = CONV_R, TR = CONV_TY * R, W = CONV_TX + KM - 1, H = TR + KM - 1;
+  constexpr int PT = CONV_PT(KM);
+  const int b = blockIdx.y;
+  if (ws.status[b] != GLAD_SAMPLE_OK) return;
+  const SysDev &S = sysv[sys_id[b]];
+  if (S.psf_km != KM) return;
+  const int ntx = (S.nx + CONV_TX - 1) / CONV_TX;
+  const int nty = (S.ny + TR - 1) / TR;
+  if ((int)blockIdx.x >= ntx * nty) return;
+  const int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;
+  constexpr int h = (KM - 1) / 2;
+  __shared__ float tile[H * W];
+  __shared__ __align__(16) float pt[KM * PT];
+  const int lane = threadIdx.x, warp = threadIdx.y;
+  const int tid = warp * CONV_TX + lane;
+  const int i0 = ty * TR - h, j0 = tx * CONV_TX - h;
+  const float *img = ws.img + (size_t)b * max_pix;
+  for (int e = tid; e < H * W; e += CONV_TX * CONV_TY) {
+    const int li = e / W, lj = e - li * W;
+    const int gi = i0 + li, gj = j0 + lj;
+    tile[e] = (gi >= 0 && gi < S.ny && gj >= 0 && gj < S.nx) ? img[gi * S.nx + gj] : 0.0f;
+  }
+  for (int e = tid; e < KM * PT; e += CONV_TX * CONV_TY) pt[e] = S.psf_t[e];
+  __syncthreads();
+  // output (i0 + h + warp*R + r, j0 + h + lane) = sum_{a,c} P[a][c] tile[warp*R + r + KM-1-a][lane + KM-1-c]
+  float sum[R], cmp[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) sum[r] = cmp[r] = 0.0f;
+  for (int c = 0; c < KM; ++c) {
+    float w[R + KM - 1];
+    const float *col = tile + warp * R * W + lane + KM - 1 - c;
+#pragma unroll
+    for (int q = 0; q < R + KM - 1; ++q) w[q] = col[q * W];
+    float p[PT];
+    const float4 *pc = reinterpret_cast<const float4 *>(pt + c * PT);
+#pragma unroll
+    for (int a4 = 0; a4 < PT / 4; ++a4) {
+      const float4 v = pc[a4];
+      p[4 * a4] = v.x;
+      p[4 * a4 + 1] = v.y;
+      p[4 * a4 + 2] = v.z;
+      p[4 * a4 + 3] = v.w;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      float part = 0.0f;
+#pragma unroll
+      for (int a = 0; a < KM; ++a) part = fmaf(p[a], w[r + KM - 1 - a], part);
+      // Kahan: sum - cmp carries the column partials
+      const float y = part - cmp[r];
+      const float t = sum[r] + y;
+      cmp[r] = (t - sum[r]) - y;
+      sum[r] = t;
+    }
+  }
+  double chi = 0.0;
+  const int oj = tx * CONV_TX + lane;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int oi = ty * TR + warp * R + r;
+    if (oi >= S.ny || oj >= S.nx) continue;
+    const double m = (double)sum[r] - (double)cmp[r];
+    const int o = oi * S.nx + oj;
+    if (image_out) {
+      image_out[o] = (float)m;
+    } else {
+      const double rr = ((double)S.data[o] - m) * (double)S.wgt[o];
+      chi += rr * rr;
+      if (resid_out) resid_out[(size_t)b * max_pix + o] = (float)(rr * (double)S.wgt[o]);
+    }
+  }
+  if (image_out) return;
+  for (int off = 16; off > 0; off >>= 1) chi += __shfl_down_sync(0xffffffffu, chi, off);
+  __shared__ double red[CONV_TX * CONV_TY / 32];
+  if (lane == 0) red[warp] = chi;
+  __syncthreads();
+  if (tid < 32) {
+    double v = tid < CONV_TX * CONV_TY / 32 ? red[tid] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (tid == 0 && v != 0.0) atomicAdd(&ws.terms[3 * (size_t)b], v);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_lens(glad_ctx *c, const int *sys_id, int B, float *image_out, cudaStream_t st,
@@ -157,17 +255,36 @@ cudaError_t launch_lens(glad_ctx *c, const int *sys_id, int B, float *image_out,
   k_image<<<g1, LENS_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_pix);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  int max_conv_tiles = 0, max_k = 1;
-  for (auto &s : c->sys) {
-    const int t = ((s.d.nx + CONV_TX - 1) / CONV_TX) * ((s.d.ny + CONV_TY - 1) / CONV_TY);
-    if (t > max_conv_tiles) max_conv_tiles = t;
-    if (s.d.psf_k > max_k) max_k = s.d.psf_k;
+  // one blocked launch per padded PSF side present (samples of other systems exit at
+  // once); systems with a PSF side above 31 go through the general kernel
+  int tiles_r[3] = {0, 0, 0}, max_conv_tiles = 0, max_k = 0;
+  for (auto &sd : c->h_sysdev) {
+    const int t = ((sd.nx + CONV_TX - 1) / CONV_TX) * ((sd.ny + CONV_TY * CONV_R - 1) / (CONV_TY * CONV_R));
+    if (sd.psf_km == 11) tiles_r[0] = std::max(tiles_r[0], t);
+    if (sd.psf_km == 21) tiles_r[1] = std::max(tiles_r[1], t);
+    if (sd.psf_km == 31) tiles_r[2] = std::max(tiles_r[2], t);
+    if (sd.psf_km == 0) {
+      max_conv_tiles = std::max(max_conv_tiles, ((sd.nx + CONV_TX - 1) / CONV_TX) *
+                                                    ((sd.ny + CONV_TY - 1) / CONV_TY));
+      max_k = std::max(max_k, sd.psf_k);
+    }
   }
-  const int h = (max_k - 1) / 2;
-  const size_t smem = sizeof(float) * ((CONV_TX + 2 * h) * (CONV_TY + 2 * h) + max_k * max_k);
-  dim3 g2(max_conv_tiles, B);
-  k_conv<<<g2, dim3(CONV_TX, CONV_TY), smem, st>>>(c->d_sys, sys_id, c->ws.d, c->max_pix,
-                                                   image_out, resid_out);
+  const dim3 blk(CONV_TX, CONV_TY);
+  if (tiles_r[0])
+    k_conv_r<11><<<dim3(tiles_r[0], B), blk, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_pix,
+                                                      image_out, resid_out);
+  if (tiles_r[1])
+    k_conv_r<21><<<dim3(tiles_r[1], B), blk, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_pix,
+                                                      image_out, resid_out);
+  if (tiles_r[2])
+    k_conv_r<31><<<dim3(tiles_r[2], B), blk, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_pix,
+                                                      image_out, resid_out);
+  if (max_conv_tiles) {
+    const int h = (max_k - 1) / 2;
+    const size_t smem = sizeof(float) * ((CONV_TX + 2 * h) * (CONV_TY + 2 * h) + max_k * max_k);
+    k_conv<<<dim3(max_conv_tiles, B), blk, smem, st>>>(c->d_sys, sys_id, c->ws.d, c->max_pix,
+                                                       image_out, resid_out);
+  }
   return cudaGetLastError();
 }
 

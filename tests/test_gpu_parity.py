@@ -147,6 +147,22 @@ def test_mixed_systems_in_one_batch():
         assert abs(logL[b] - ev["logL"]) < 0.05, (b, logL[b], ev["logL"])
 
 
+def test_psf_sides_in_every_convolution_form():
+    # PSF sides 5 and 21 (blocked kernel, padded to 11 and 21), 31 (blocked, exact side) and
+    # 35 (general kernel) in one batch: model images and logL against the oracle
+    sys_list = [systems.small_system(20 + k, n_px=48 if k < 35 else 64, psf_k=k, n_bins=9)
+                for k in (5, 21, 31, 35)]
+    ctx = _ctx(sys_list)
+    th = systems.near_truth_thetas(4, seed=9)
+    sid = np.arange(4, dtype=np.int32)
+    logL, st = ctx.loglike(_th(th), torch.as_tensor(sid, device="cuda"))
+    logL = logL.cpu().numpy()
+    for b, s in enumerate(sys_list):
+        ev = model.evaluate(th[b], s)
+        assert abs(logL[b] - ev["logL"]) < 0.05, (s["psf"].shape, logL[b], ev["logL"])
+        assert_image_close(ctx.model_image(_th(th[b]), b).cpu().numpy(), ev["image"])
+
+
 def test_batch_independence(small):
     # a sample's logL does not depend on which other samples share the launch
     s, ctx = small
