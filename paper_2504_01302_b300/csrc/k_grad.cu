@@ -30,6 +30,10 @@ struct GradWs {
   float4 *adjpt = nullptr;   // [B*max_apts*2] (X, X, Y, Y), (XY, XY, g_N, g_N), 16x16-tile order
   double *entadj = nullptr;  // [B*max_ent*3] d logL / d (Q0, Q1, a_y)
   double *adjI0 = nullptr;   // [B*max_light] d logL / d I0_k (tracer amplitudes)
+  // per sample, the table adjoint carried to the per-Gaussian JAM inputs: d logL / d nu0_k,
+  // c0_k [max_light each], C_j, e2_j [max_mass_tot each], sin^2 i, cos^2 i, b [3]
+  double *tadj = nullptr;    // [B*tstride]
+  int tstride = 0;
   std::vector<void *> allocs;
 };
 
@@ -599,6 +603,79 @@ __device__ inline cplx cexp_(cplx a) {
 }
 __device__ inline cplx clog_(cplx a) { return {log(hypot(a.r, a.i)), atan2(a.i, a.r)}; }
 
+// Table adjoint -> per-Gaussian JAM inputs.  One warp per (tracer k, mass j) pair, lanes
+// over the Gauss-Legendre nodes; FP64 duals through the table formula (tangents c0_k, e2_j,
+// sin^2 i, cos^2 i, b); warp sums, then one global atomic per quantity and warp.
+__global__ void __launch_bounds__(256) k_table_adj(const SysDev *__restrict__ sysv,
+                                                   const int *__restrict__ sys_id, WsDev ws,
+                                                   GradWs gw, int max_light, int max_mass,
+                                                   int max_ent) {
+  const int b = blockIdx.y;
+  if (ws.status[b] != GLAD_SAMPLE_OK) return;
+  const SysDev &S = sysv[sys_id[b]];
+  const int nMt = S.n_mass_tot;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int kj = blockIdx.x * 8 + warp;
+  __shared__ double gsum[8][3];
+  double G[7] = {0, 0, 0, 0, 0, 0, 0};  // sum gR, d0 .. d4 (d2..d4 global), unused slot
+  const DynP dp = ws.dp[b];
+  const size_t bl = (size_t)b * max_light, bm = (size_t)b * max_mass;
+  int k = 0, j = 0;
+  if (kj < S.n_light * nMt) {
+    j = kj % nMt;
+    k = kj / nMt;
+    const D5 s2 = D5::var(dp.s2, 2), c2 = D5::var(dp.c2, 3), bb = D5::var(dp.b, 4);
+    const double sj = S.sig_mass[j], sk = S.sig_light[k];
+    const D5 e2 = D5::var(ws.e2[bm + j], 1);
+    const D5 c0 = D5::var(ws.c0[bl + k], 0);
+    const double nc = ws.nu0[bl + k] * ws.Cj[bm + j];
+    for (int g = lane; g < S.n_gl; g += 32) {
+      const int e = kj * S.n_gl + g;
+      const double *ga = gw.entadj + ((size_t)b * max_ent + e) * 3;
+      const double GQ0 = ga[0], GQ1 = ga[1], Gay = ga[2];
+      const double u = S.gl_u[e], wu = S.gl_wu[e];
+      const double a = u * u / (2.0 * sj * sj);
+      const D5 h = 1.0 - e2 * (u * u);
+      const double p = 1.0 / (2.0 * sk * sk) + a;
+      const D5 c = c0 + a / h;
+      const D5 al = p * s2 + c * c2;
+      const D5 sh = dsqrt(h);
+      const D5 A = a / (h * sh * c);
+      const D5 P0 = A * (bb * s2 + c2);
+      const D5 P1 = s2 * (2.0 * a / sh - 2.0 * p * bb * A);
+      const D5 wsq = wu * dsqrt(PI_D / al);
+      const D5 R0 = wsq * P0, R1 = wsq * P1;
+      const D5 ayn = -p * c / al;
+      G[0] += GQ0 * R0.v + GQ1 * R1.v;
+#pragma unroll
+      for (int i = 0; i < 5; ++i) G[1 + i] += nc * (GQ0 * R0.d[i] + GQ1 * R1.d[i]) + Gay * ayn.d[i];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+    for (int off = 16; off > 0; off >>= 1) G[i] += __shfl_xor_sync(0xffffffffu, G[i], off);
+  double *t = gw.tadj + (size_t)b * gw.tstride;
+  const int ML = max_light, MM = max_mass;
+  if (lane == 0) {
+    if (kj < S.n_light * nMt) {
+      // a_nu0[k] += C_j sum gR, a_C[j] += nu0_k sum gR, a_c0[k], a_e2[j]
+      atomicAdd(&t[k], ws.Cj[bm + j] * G[0]);
+      atomicAdd(&t[ML + k], G[1]);
+      atomicAdd(&t[2 * ML + j], ws.nu0[bl + k] * G[0]);
+      atomicAdd(&t[2 * ML + MM + j], G[2]);
+    }
+    gsum[warp][0] = G[3];
+    gsum[warp][1] = G[4];
+    gsum[warp][2] = G[5];
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double v = 0.0;
+    for (int w = 0; w < 8; ++w) v += gsum[w][threadIdx.x];
+    if (v != 0.0) atomicAdd(&t[2 * ML + 2 * MM + threadIdx.x], v);
+  }
+}
+
 __global__ void __launch_bounds__(256) k_grad_chain(const SysDev *__restrict__ sysv,
                                                     const int *__restrict__ sys_id,
                                                     const double *__restrict__ theta, WsDev ws,
@@ -615,54 +692,23 @@ __global__ void __launch_bounds__(256) k_grad_chain(const SysDev *__restrict__ s
   __shared__ double gsm[GLAD_NTHETA];
   __shared__ double Ad[GLAD_MAX_LIGHT][10];  // light amplitudes with tangents (I_e, R_e in slots 3, 4)
   const int nL = S.n_light, nM = S.n_mass, nMt = S.n_mass_tot;
-  for (int k = tid; k < nL; k += blockDim.x) a_nu0[k] = a_c0[k] = 0.0;
-  for (int j = tid; j < nMt; j += blockDim.x) a_C[j] = a_e2[j] = 0.0;
-  if (tid < 3) a_glob[tid] = 0.0;
+  // (a) the table adjoint, carried to nu0_k, c0_k, C_j, e2_j, sin^2 i, cos^2 i, b by k_table_adj
+  {
+    const double *t = gw.tadj + (size_t)b * gw.tstride;
+    const int ML = max_light, MM = max_mass;
+    for (int k = tid; k < nL; k += blockDim.x) {
+      a_nu0[k] = t[k];
+      a_c0[k] = t[ML + k];
+    }
+    for (int j = tid; j < nMt; j += blockDim.x) {
+      a_C[j] = t[2 * ML + j];
+      a_e2[j] = t[2 * ML + MM + j];
+    }
+    if (tid < 3) a_glob[tid] = t[2 * ML + 2 * MM + tid];
+  }
   if (tid < GLAD_NTHETA) gsm[tid] = 0.0;
   __syncthreads();
-  const DynP dp = ws.dp[b];
-  const size_t bl = (size_t)b * max_light, bm = (size_t)b * max_mass;
-
-  // (a) table entries: adjoints of (Q0, Q1, a_y) -> nu0_k, c0_k, C_j, e2_j, sin^2 i, cos^2 i, b
-  {
-    const D5 s2 = D5::var(dp.s2, 2), c2 = D5::var(dp.c2, 3), bb = D5::var(dp.b, 4);
-    for (int e = tid; e < S.n_ent; e += blockDim.x) {
-      const int kj = e / S.n_gl;
-      const int j = kj % nMt, k = kj / nMt;
-      const double *ga = gw.entadj + ((size_t)b * max_ent + e) * 3;
-      const double GQ0 = ga[0], GQ1 = ga[1], Gay = ga[2];
-      const double u = S.gl_u[e], wu = S.gl_wu[e];
-      const double sj = S.sig_mass[j], sk = S.sig_light[k];
-      const D5 e2 = D5::var(ws.e2[bm + j], 1);
-      const D5 c0 = D5::var(ws.c0[bl + k], 0);
-      const double a = u * u / (2.0 * sj * sj);
-      const D5 h = 1.0 - e2 * (u * u);
-      const double p = 1.0 / (2.0 * sk * sk) + a;
-      const D5 c = c0 + a / h;
-      const D5 al = p * s2 + c * c2;
-      const D5 sh = dsqrt(h);
-      const D5 A = a / (h * sh * c);
-      const D5 P0 = A * (bb * s2 + c2);
-      const D5 P1 = s2 * (2.0 * a / sh - 2.0 * p * bb * A);
-      const D5 wsq = wu * dsqrt(PI_D / al);
-      const D5 R0 = wsq * P0, R1 = wsq * P1;
-      const D5 ayn = -p * c / al;
-      const double nu = ws.nu0[bl + k], Cj = ws.Cj[bm + j];
-      const double gR = GQ0 * R0.v + GQ1 * R1.v;
-      atomicAdd(&a_nu0[k], Cj * gR);
-      atomicAdd(&a_C[j], nu * gR);
-      const double nc = nu * Cj;
-      double d[5];
-#pragma unroll
-      for (int i = 0; i < 5; ++i) d[i] = nc * (GQ0 * R0.d[i] + GQ1 * R1.d[i]) + Gay * ayn.d[i];
-      atomicAdd(&a_c0[k], d[0]);
-      atomicAdd(&a_e2[j], d[1]);
-      atomicAdd(&a_glob[0], d[2]);
-      atomicAdd(&a_glob[1], d[3]);
-      atomicAdd(&a_glob[2], d[4]);
-    }
-  }
-  __syncthreads();
+  const size_t bl = (size_t)b * max_light;
 
   // (b) per Gaussian: MGE amplitudes (analytic partials of F), deprojection, C_j, e2_j
   const double tE = th[0], g = th[1], q = th[2], inc = th[15];
@@ -815,7 +861,9 @@ cudaError_t grad_ws_ensure(glad_ctx *c, int B) {
   const bool ok = galloc(w, w.resid, b * c->max_pix) && galloc(w, w.gpix, b * c->max_pix) &&
                   galloc(w, w.pt, b * c->max_sub) && galloc(w, w.adjpt, 2 * b * c->max_apts) &&
                   galloc(w, w.entadj, b * c->max_ent * 3) && galloc(w, w.adjI0, b * c->max_light);
-  if (!ok) {
+  w.tstride = 2 * c->max_light + 2 * c->max_mass_tot + 3;
+  const bool ok2 = ok && galloc(w, w.tadj, b * w.tstride);
+  if (!ok2) {
     grad_ws_free(c);
     return cudaErrorMemoryAllocation;
   }
@@ -840,6 +888,7 @@ cudaError_t launch_grad(glad_ctx *c, const int *sys_id, const double *theta, int
   GradWs &g = *c->gws;
   cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(double) * GLAD_NTHETA * (size_t)B, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(g.adjI0, 0, sizeof(double) * c->max_light * (size_t)B, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g.tadj, 0, sizeof(double) * g.tstride * (size_t)B, st);
   // tile padding beyond the sky grid must read as g_N = 0
   if (e == cudaSuccess) e = cudaMemsetAsync(g.adjpt, 0, sizeof(float4) * 2 * c->max_apts * (size_t)B, st);
   if (e != cudaSuccess) return e;
@@ -880,6 +929,12 @@ cudaError_t launch_grad(glad_ctx *c, const int *sys_id, const double *theta, int
   }()));
   if (e != cudaSuccess) return e;
   e = GLAD_PROF(c, st, KID_GRAD_CHAIN, ([&]() -> cudaError_t {
+    int pairs = 0;
+    for (auto &sd : c->h_sysdev) pairs = std::max(pairs, sd.n_light * sd.n_mass_tot);
+    k_table_adj<<<dim3((pairs + 7) / 8, B), 256, 0, st>>>(c->d_sys, sys_id, c->ws.d, g, c->max_light,
+                                                         c->max_mass_tot, c->max_ent);
+    cudaError_t r0 = cudaGetLastError();
+    if (r0 != cudaSuccess) return r0;
     k_grad_chain<<<B, 256, 0, st>>>(c->d_sys, sys_id, theta, c->ws.d, g, c->max_light,
                                     c->max_mass_tot, c->max_ent, grad);
     cudaError_t r = cudaGetLastError();
