@@ -195,7 +195,8 @@ glad_status glad_set_tuning(glad_ctx *ctx, int jam_code, int adj_ept);
  * entries that underflow to zero.  mode 0: exact skipping only; 1 (the default): with
  * negligible terms left out; 2: as 1 but every tile's check is failed (for tests: the
  * tiles are summed twice and the results equal mode 0).  Applies to glad_loglike,
- * glad_loglike_static, glad_vrms; the gradient pass uses exact skipping only.
+ * glad_loglike_static, glad_vrms and the derivative pass of glad_loglike_grad (there the
+ * check also covers d(Sigma v^2)/d(x'^2) and d(Sigma v^2)/d(y'^2) at every point).
  * GLAD_EINVAL for other modes. */
 glad_status glad_set_negligible(glad_ctx *ctx, int mode);
 

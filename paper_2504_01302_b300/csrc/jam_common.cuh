@@ -135,6 +135,44 @@ struct JamStager {
       wcount[1][warp] = __popc(c1);
     }
   }
+  // count_rel() for the derivative pass: the left-out bounds of the term, of its X
+  // derivative (|Q1| 2^bound + ln2 |ax| M) and of its Y derivative (ln2 |ay| M), M the term
+  // bound, each relative to the reference, go to dv, dx, dy.
+  __device__ __forceinline__ void count_rel_grad(const float4 *gt, int n_ent, int base,
+                                                 const volatile float *tb,
+                                                 int (*wcount)[JAM_THREADS / 32], float &dv,
+                                                 float &dx, float &dy) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float Xmin = tb[0], Ymin = tb[1], Xmax = tb[2], lref = tb[3], lrel = tb[4];
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int e0 = base + tid, e1 = base + tid + JAM_THREADS;
+    v0 = e0 < n_ent ? gt[e0] : z;
+    v1 = e1 < n_ent ? gt[e1] : z;
+    const float b0 = fmaf(v0.y, Ymin, v0.x * Xmin), b1 = fmaf(v1.y, Ymin, v1.x * Xmin);
+    const float m0 = b0 + __log2f(fabsf(v0.z) + fabsf(v0.w) * Xmax) - lref;
+    const float m1 = b1 + __log2f(fabsf(v1.z) + fabsf(v1.w) * Xmax) - lref;
+    const bool x0 = e0 < n_ent && b0 >= JAM_SKIP_LOG2, x1 = e1 < n_ent && b1 >= JAM_SKIP_LOG2;
+    k0 = x0 && m0 >= lrel;
+    k1 = x1 && m1 >= lrel;
+    constexpr float L2 = 0.6931471805599453f;
+    if (x0 && !k0) {
+      const float M = jam_ex2(m0);
+      dv += M;
+      dx += jam_ex2(b0 + __log2f(fabsf(v0.w)) - lref) + L2 * fabsf(v0.x) * M;
+      dy += L2 * fabsf(v0.y) * M;
+    }
+    if (x1 && !k1) {
+      const float M = jam_ex2(m1);
+      dv += M;
+      dx += jam_ex2(b1 + __log2f(fabsf(v1.w)) - lref) + L2 * fabsf(v1.x) * M;
+      dy += L2 * fabsf(v1.y) * M;
+    }
+    const unsigned c0 = __ballot_sync(0xffffffffu, k0), c1 = __ballot_sync(0xffffffffu, k1);
+    if (lane == 0) {
+      wcount[0][warp] = __popc(c0);
+      wcount[1][warp] = __popc(c1);
+    }
+  }
   __device__ __forceinline__ void write(float4 *tab, int (*wcount)[JAM_THREADS / 32], int *n_kept) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;

@@ -274,9 +274,63 @@ __global__ void __launch_bounds__(JAM_THREADS, 3) k_jam_fg(const SysDev *__restr
   }
   float Xmin, Ymin;
   jam_tile_bounds(S, dp, c0, c1, r0, r1, Xmin, Ymin);
+  const float Xmax = jam_tile_xmax(S, dp, c0, c1, r0, r1);
   const float cphi = (float)dp.cphi, sphi = (float)dp.sphi;
   const float xc = (float)dp.xc, yc = (float)dp.yc;
   const float hx = 0.5f * (S.nsx - 1), hy = 0.5f * (S.nsy - 1);
+  const float4 *gt = ws.tab + (size_t)b * max_ent;
+  const int n_ent = S.n_ent;
+  const int n_chunks = (n_ent + JAM_CHUNK - 1) / JAM_CHUNK;
+  const int lane = tid & 31, warp = tid >> 5;
+  // Negligible terms as in the forward pass (reference: the full sum at the tile's corners),
+  // with the a-posteriori check covering V, dV/dX and dV/dY at every point of the tile.
+  float lref = 0.0f, lrel = -INFINITY;
+  if (ws.neg_mode != 0) {
+    float cX[4], cY[4], cv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float x = ((q & 1 ? c1 : c0) - hx) * S.dsub - xc;
+      const float y = ((q & 2 ? r1 : r0) - hy) * S.dsub - yc;
+      const float xp = cphi * x + sphi * y, yp = -sphi * x + cphi * y;
+      cX[q] = xp * xp;
+      cY[q] = yp * yp;
+      cv[q] = 0.0f;
+    }
+    for (int e = tid; e < n_ent; e += JAM_THREADS) {
+      const float4 c = gt[e];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        cv[q] = fmaf(fmaf(c.w, cX[q], c.z), jam_ex2(fmaf(c.y, cY[q], c.x * cX[q])), cv[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      for (int off = 16; off > 0; off >>= 1) cv[q] += __shfl_xor_sync(0xffffffffu, cv[q], off);
+      if (lane == 0) sm.red[q][warp] = cv[q];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float ref = 3.4e38f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float t = 0.0f;
+        for (int w = 0; w < JAM_THREADS / 32; ++w) t += sm.red[q][w];
+        ref = fminf(ref, t);
+      }
+      sm.flag = (ref > 0.0f && ref < 3.4e38f) ? __float_as_int(__log2f(ref)) : 0x7fffffff;
+    }
+    __syncthreads();
+    const int f = sm.flag;
+    lref = f == 0x7fffffff ? 0.0f : __int_as_float(f);
+    lrel = f == 0x7fffffff ? -INFINITY : -(JAM_REL_MARGIN + __log2f((float)max(n_ent, 1)));
+  }
+  if (tid == 0) {
+    sm.tb[0] = Xmin;
+    sm.tb[1] = Ymin;
+    sm.tb[2] = Xmax;
+    sm.tb[3] = lref;
+    sm.tb[4] = lrel;
+  }
+  __syncthreads();
   const int col = c0 + (tid % JAM_TW);
   const int row0 = r0 + (tid / JAM_TW) * PTS;
   float2 X[NP], Y[NP];
@@ -295,58 +349,106 @@ __global__ void __launch_bounds__(JAM_THREADS, 3) k_jam_fg(const SysDev *__restr
       X[i >> 1].x = xp * xp;
       Y[i >> 1].x = yp * yp;
     }
-    dV[i] = d1[i] = d2[i] = d3[i] = 0.0;
   }
   const float2 z2 = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int p = 0; p < NP; ++p) aV[p] = a1[p] = a2[p] = a3[p] = z2;
-  const float4 *gt = ws.tab + (size_t)b * max_ent;
-  const int n_ent = S.n_ent;
-  const int n_chunks = (n_ent + JAM_CHUNK - 1) / JAM_CHUNK;
   const unsigned long long npts = (unsigned long long)(c1 - c0 + 1) * (unsigned long long)(r1 - r0 + 1);
   unsigned long long n_eval = 0;  // evaluations this tile executes (thread 0 keeps the count)
-  JamStager stg;
-  stg.count(gt, n_ent, 0, Xmin, Ymin, sm.wcount[0]);
-  __syncthreads();
-  stg.write(sm.tab[0], sm.wcount[0], &sm.n_kept[0]);
-  __syncthreads();
-  for (int ch = 0; ch < n_chunks; ++ch) {
-    const int cur = ch & 1;
-    const bool more = ch + 1 < n_chunks;
-    if (more) stg.count(gt, n_ent, (ch + 1) * JAM_CHUNK, Xmin, Ymin, sm.wcount[cur ^ 1]);
-    const float4 *tt = sm.tab[cur];
-    const int nk = sm.n_kept[cur];
-    n_eval += (unsigned long long)nk * npts;
+  for (;;) {
+#pragma unroll
+    for (int i = 0; i < PTS; ++i) dV[i] = d1[i] = d2[i] = d3[i] = 0.0;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) aV[p] = a1[p] = a2[p] = a3[p] = z2;
+    float rv = 0.0f, rx = 0.0f, ry = 0.0f;  // left-out bounds relative to the reference
+    JamStager stg;
+    stg.count_rel_grad(gt, n_ent, 0, sm.tb, sm.wcount[0], rv, rx, ry);
+    __syncthreads();
+    stg.write(sm.tab[0], sm.wcount[0], &sm.n_kept[0]);
+    __syncthreads();
+    for (int ch = 0; ch < n_chunks; ++ch) {
+      const int cur = ch & 1;
+      const bool more = ch + 1 < n_chunks;
+      if (more)
+        stg.count_rel_grad(gt, n_ent, (ch + 1) * JAM_CHUNK, sm.tb, sm.wcount[cur ^ 1], rv, rx, ry);
+      const float4 *tt = sm.tab[cur];
+      const int nk = sm.n_kept[cur];
+      n_eval += (unsigned long long)nk * npts;
 #pragma unroll 2
-    for (int e = 0; e < nk; ++e) {
-      const float4 c = tt[e];
-      const float2 cx = make_float2(c.x, c.x), cy = make_float2(c.y, c.y);
-      const float2 cz = make_float2(c.z, c.z), cw = make_float2(c.w, c.w);
+      for (int e = 0; e < nk; ++e) {
+        const float4 c = tt[e];
+        const float2 cx = make_float2(c.x, c.x), cy = make_float2(c.y, c.y);
+        const float2 cz = make_float2(c.z, c.z), cw = make_float2(c.w, c.w);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+          const float2 arg = __ffma2_rn(cy, Y[p], __fmul2_rn(cx, X[p]));
+          const float2 E = make_float2(jam_ex2(arg.x), jam_ex2(arg.y));
+          const float2 tv = __fmul2_rn(__ffma2_rn(cw, X[p], cz), E);
+          aV[p] = __fadd2_rn(aV[p], tv);
+          a1[p] = __ffma2_rn(cw, E, a1[p]);
+          a2[p] = __ffma2_rn(cx, tv, a2[p]);
+          a3[p] = __ffma2_rn(cy, tv, a3[p]);
+        }
+      }
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
-        const float2 arg = __ffma2_rn(cy, Y[p], __fmul2_rn(cx, X[p]));
-        const float2 E = make_float2(jam_ex2(arg.x), jam_ex2(arg.y));
-        const float2 tv = __fmul2_rn(__ffma2_rn(cw, X[p], cz), E);
-        aV[p] = __fadd2_rn(aV[p], tv);
-        a1[p] = __ffma2_rn(cw, E, a1[p]);
-        a2[p] = __ffma2_rn(cx, tv, a2[p]);
-        a3[p] = __ffma2_rn(cy, tv, a3[p]);
+        dV[2 * p] += aV[p].x;
+        dV[2 * p + 1] += aV[p].y;
+        d1[2 * p] += a1[p].x;
+        d1[2 * p + 1] += a1[p].y;
+        d2[2 * p] += a2[p].x;
+        d2[2 * p + 1] += a2[p].y;
+        d3[2 * p] += a3[p].x;
+        d3[2 * p + 1] += a3[p].y;
+        aV[p] = a1[p] = a2[p] = a3[p] = z2;
       }
+      __syncthreads();
+      if (more) stg.write(sm.tab[cur ^ 1], sm.wcount[cur ^ 1], &sm.n_kept[cur ^ 1]);
+      __syncthreads();
     }
+    if (lrel == -INFINITY) break;
+    // a-posteriori check of V, dV/dX, dV/dY against the smallest magnitudes in the tile
+    float mv = 3.4e38f, mx = 3.4e38f, my = 3.4e38f;
 #pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      dV[2 * p] += aV[p].x;
-      dV[2 * p + 1] += aV[p].y;
-      d1[2 * p] += a1[p].x;
-      d1[2 * p + 1] += a1[p].y;
-      d2[2 * p] += a2[p].x;
-      d2[2 * p + 1] += a2[p].y;
-      d3[2 * p] += a3[p].x;
-      d3[2 * p + 1] += a3[p].y;
-      aV[p] = a1[p] = a2[p] = a3[p] = z2;
+    for (int i = 0; i < PTS; ++i)
+      if (col <= c1 && row0 + i <= r1) {
+        mv = fminf(mv, fabsf((float)dV[i]));
+        mx = fminf(mx, fabsf((float)(d1[i] + LN2D * d2[i])));
+        my = fminf(my, fabsf((float)(LN2D * d3[i])));
+      }
+    for (int off = 16; off > 0; off >>= 1) {
+      mv = fminf(mv, __shfl_xor_sync(0xffffffffu, mv, off));
+      mx = fminf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+      my = fminf(my, __shfl_xor_sync(0xffffffffu, my, off));
+      rv += __shfl_xor_sync(0xffffffffu, rv, off);
+      rx += __shfl_xor_sync(0xffffffffu, rx, off);
+      ry += __shfl_xor_sync(0xffffffffu, ry, off);
+    }
+    __shared__ float chk[6][JAM_THREADS / 32];
+    if (lane == 0) {
+      chk[0][warp] = mv;
+      chk[1][warp] = mx;
+      chk[2][warp] = my;
+      chk[3][warp] = rv;
+      chk[4][warp] = rx;
+      chk[5][warp] = ry;
     }
     __syncthreads();
-    if (more) stg.write(sm.tab[cur ^ 1], sm.wcount[cur ^ 1], &sm.n_kept[cur ^ 1]);
+    if (tid == 0) {
+      float m[3] = {3.4e38f, 3.4e38f, 3.4e38f}, r[3] = {0.f, 0.f, 0.f};
+      for (int w = 0; w < JAM_THREADS / 32; ++w)
+        for (int q = 0; q < 3; ++q) {
+          m[q] = fminf(m[q], chk[q][w]);
+          r[q] += chk[3 + q][w];
+        }
+      bool ok = ws.neg_mode == 1;
+      for (int q = 0; q < 3; ++q) ok = ok && (__log2f(r[q]) + lref <= __log2f(m[q]) - JAM_REL_CHECK);
+      sm.flag = ok ? 1 : 0;
+    }
+    __syncthreads();
+    const bool ok = sm.flag != 0;
+    __syncthreads();
+    if (ok) break;
+    lrel = -INFINITY;  // sum the tile again with the exact skipping only
+    if (tid == 0) sm.tb[4] = -INFINITY;
     __syncthreads();
   }
   if (tid == 0 && ws.evals) atomicAdd(ws.evals, n_eval);

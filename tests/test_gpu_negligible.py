@@ -1,8 +1,8 @@
-"""Negligible-term skipping of the forward JAM pair sum (glad_set_negligible) against the
-exact-skipping-only sum, at the full RXJ1131-scale size: the results agree to the FP32
-rounding of the sums (1e-5 relative per v_rms bin, ten times inside the oracle tolerance),
-fewer integrand evaluations run, and the forced-recheck mode runs each tile twice (its
-evaluation count is exactly the sum of the other two)."""
+"""Negligible-term skipping of the JAM pair sums (glad_set_negligible) against the
+exact-skipping-only sums, at the full RXJ1131-scale size: the results agree to the FP32
+rounding of the sums (1e-5 relative per v_rms bin and per gradient component, well inside
+the oracle tolerances), fewer integrand evaluations run, and the forced-recheck mode runs
+each tile twice (its evaluation count is exactly the sum of the other two)."""
 import numpy as np
 import pytest
 
@@ -58,6 +58,26 @@ def test_vrms_agree_per_bin(w1):
         ctx.set_negligible(1)
         v1 = ctx.vrms(th).cpu().numpy().astype(np.float64)
         assert np.max(np.abs(v1 / v0 - 1)) < 1e-5
+
+
+def test_gradient_modes_agree(w1):
+    s, ctx = w1
+    th = torch.as_tensor(systems.near_truth_thetas(4, seed=77), device="cuda")
+    out = {}
+    for mode in (0, 1, 2):
+        ctx.set_negligible(mode)
+        logL, g, st = ctx.loglike_grad(th)
+        out[mode] = (logL.cpu().numpy(), g.cpu().numpy(), st.cpu().numpy(), ctx.jam_evaluations())
+    ctx.set_negligible(1)
+    (l0, g0, s0, n0), (l1, g1, s1, n1), (l2, g2, s2, n2) = out[0], out[1], out[2]
+    assert np.all(s0 == 0) and np.all(s1 == 0) and np.all(s2 == 0)
+    scale = np.max(np.abs(g0), axis=1, keepdims=True)
+    assert np.all(np.abs(g1 - g0) <= 1e-5 * np.abs(g0) + 1e-6 * scale)
+    assert np.all(np.abs(g2 - g0) <= 1e-6 * np.abs(g0) + 1e-7 * scale)
+    assert np.all(np.abs(l1 - l0) <= 1e-6 * np.abs(l0) + 1e-3)
+    # mode 2 sums every tile twice; mode 1 sums a tile twice only where its check failed
+    # (here the derivative check may fail where dV/dX or dV/dY nears zero)
+    assert 0 < n1 < n0 < n2 <= n0 + n1
 
 
 def test_bad_mode_is_refused(w1):
