@@ -55,6 +55,19 @@ def test_every_launch_shape_gives_the_same_logl(code):
     assert np.all(np.abs(g[ok] - r[ok]) < 1e-6 * np.abs(r[ok]))
 
 
+def test_every_adjoint_shape_gives_the_same_gradient():
+    from paper_2504_01302_b300.glad import GladContext
+    ctx = GladContext([systems.small_system(7)])
+    th = torch.as_tensor(systems.near_truth_thetas(3, seed=65), device="cuda")
+    out = []
+    for ept in (2, 4):
+        ctx.set_tuning(8042, ept)
+        out.append(ctx.loglike_grad(th)[1].cpu().numpy())
+    scale = np.max(np.abs(out[0]), axis=1, keepdims=True)
+    for g in out[1:]:
+        assert np.all(np.abs(g - out[0]) <= 1e-6 * np.abs(out[0]) + 1e-7 * scale)
+
+
 def test_bad_launch_shape_is_refused():
     from paper_2504_01302_b300 import _lib
     from paper_2504_01302_b300.glad import GladContext
