@@ -515,15 +515,23 @@ __global__ void __launch_bounds__(JAM_THREADS) k_kin_adj(const SysDev *__restric
   const DynP dp = ws.dp[b];
   const float cphi = (float)dp.cphi, sphi = (float)dp.sphi;
   const float xc = (float)dp.xc, yc = (float)dp.yc;
+  const int lane = tid & 31;
   float gphi = 0.0f, gxc = 0.0f, gyc = 0.0f;
+  // this thread's points (strided by the block), their coordinates and bin adjoints
+  float X[JAM_PTS], Y[JAM_PTS], xpv[JAM_PTS], ypv[JAM_PTS], gnv[JAM_PTS], gdv[JAM_PTS];
+  float dsx[JAM_PTS], dsy[JAM_PTS];
+#pragma unroll
   for (int i = 0; i < JAM_PTS; ++i) {
     const int s = tile0 + tid + i * JAM_THREADS;
+    X[i] = Y[i] = xpv[i] = ypv[i] = gnv[i] = gdv[i] = dsx[i] = dsy[i] = 0.0f;
     if (s >= S.n_sub) continue;
     const int I = s / S.nsx, J = s - I * S.nsx;
     const float x = (J - 0.5f * (S.nsx - 1)) * S.dsub - xc;
     const float y = (I - 0.5f * (S.nsy - 1)) * S.dsub - yc;
-    const float xp = cphi * x + sphi * y, yp = -sphi * x + cphi * y;
-    const float X = xp * xp, Y = yp * yp;
+    xpv[i] = cphi * x + sphi * y;
+    ypv[i] = -sphi * x + cphi * y;
+    X[i] = xpv[i] * xpv[i];
+    Y[i] = ypv[i] * ypv[i];
     float gn = 0.0f, gd = 0.0f;
     for (int e = S.w_off[s]; e < S.w_off[s + 1]; ++e) {
       const int l = S.w_bin[e];
@@ -531,19 +539,33 @@ __global__ void __launch_bounds__(JAM_THREADS) k_kin_adj(const SysDev *__restric
       gn = fmaf(w, gN[l], gn);
       gd = fmaf(w, gD[l], gd);
     }
-    const float4 pv = gw.pt[(size_t)b * max_sub + s];
-    // tracer surface brightness derivatives
-    float dsx = 0.0f, dsy = 0.0f;
-    if (gd != 0.0f) {
-      for (int k = 0; k < S.n_light; ++k) {
-        const float E = ex2(-fmaf(scy[k], Y, scx[k] * X));
-        atomicAdd(&aI0[k], gd * E);
-        dsx = fmaf(sI0[k] * scx[k], E, dsx);
-        dsy = fmaf(sI0[k] * scy[k], E, dsy);
-      }
+    gnv[i] = gn;
+    gdv[i] = gd;
+  }
+  // tracer surface brightness derivatives; d logL / d I0_k summed over the warp's points
+  // (warp shuffles, one shared atomic per warp and Gaussian)
+  for (int k = 0; k < S.n_light; ++k) {
+    const float cxk = scx[k], cyk = scy[k], ik = sI0[k];
+    float a = 0.0f;
+#pragma unroll
+    for (int i = 0; i < JAM_PTS; ++i) {
+      const float E = ex2(-fmaf(cyk, Y[i], cxk * X[i]));
+      a = fmaf(gdv[i], E, a);
+      dsx[i] = fmaf(ik * cxk, E, dsx[i]);
+      dsy[i] = fmaf(ik * cyk, E, dsy[i]);
     }
-    const float aX = gn * pv.y - gd * LN2F * dsx;
-    const float aY = gn * pv.z - gd * LN2F * dsy;
+    for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+    if (lane == 0 && a != 0.0f) atomicAdd(&aI0[k], a);
+  }
+#pragma unroll
+  for (int i = 0; i < JAM_PTS; ++i) {
+    const int s = tile0 + tid + i * JAM_THREADS;
+    if (s >= S.n_sub) continue;
+    const int I = s / S.nsx, J = s - I * S.nsx;
+    const float4 pv = gw.pt[(size_t)b * max_sub + s];
+    const float gn = gnv[i], gd = gdv[i], xp = xpv[i], yp = ypv[i];
+    const float aX = gn * pv.y - gd * LN2F * dsx[i];
+    const float aY = gn * pv.z - gd * LN2F * dsy[i];
     // X = x'^2, Y = y'^2; dx'/dphi = y', dy'/dphi = -x'; dx'/dxc = -c, dy'/dxc = s;
     // dx'/dyc = -s, dy'/dyc = -c
     gphi += 2.0f * xp * yp * (aX - aY);
@@ -552,10 +574,10 @@ __global__ void __launch_bounds__(JAM_THREADS) k_kin_adj(const SysDev *__restric
     // position in 16 x 16 point tiles (tile-major), the adjoint's chunk order
     const size_t pos = (size_t)b * max_apts +
                        (size_t)((I >> 4) * S.atx + (J >> 4)) * 256 + (I & 15) * 16 + (J & 15);
-    gw.adjpt[2 * pos] = make_float4(X, X, Y, Y);
-    gw.adjpt[2 * pos + 1] = make_float4(X * Y, X * Y, gn, gn);
+    gw.adjpt[2 * pos] = make_float4(X[i], X[i], Y[i], Y[i]);
+    gw.adjpt[2 * pos + 1] = make_float4(X[i] * Y[i], X[i] * Y[i], gn, gn);
   }
-  const int lane = tid & 31, warp = tid >> 5;
+  const int warp = tid >> 5;
   for (int off = 16; off > 0; off >>= 1) {
     gphi += __shfl_down_sync(0xffffffffu, gphi, off);
     gxc += __shfl_down_sync(0xffffffffu, gxc, off);
@@ -691,7 +713,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_jam_adj(const SysDev *__restric
 
 typedef Dual<5, double> D5;   // tangents: c0_k, e2_j, s2, c2, b
 typedef Dual<9, double> D9;   // tangents: theta 0,1,2,13,14,15,16,17,18
-typedef Dual<9, double> DT;   // tangents: theta 0..7 and H0 (delays)
+typedef Dual<1, double> DT1;  // one tangent of the delay term (theta 0..7 or H0)
 
 struct cplx {
   double r, i;
@@ -915,15 +937,16 @@ __global__ void __launch_bounds__(256) k_grad_chain(const SysDev *__restrict__ s
     const double bb = 1.0 / (1.0 - th[16]);
     gsm[16] += a_glob[2] * bb * bb;
   }
-  if (tid == 32) {
-    // time delays: -chi2_tmd/2 by duals through the FP64 lens model
-    DT tt[8];
-    for (int i = 0; i < 8; ++i) tt[i] = DT::var(th[i], i);
-    const DT h0 = DT::var(th[19], 8);
-    const DT chi = chi2_tmd_t<DT>(tt, h0, S.img_xy, S.n_img, S.dt_obs, S.dt_sig,
-                                  S.dt_per_arcsec2_H0, S.sis, S.n_sis);
-    for (int i = 0; i < 8; ++i) atomicAdd(&gsm[i], -0.5 * chi.d[i]);
-    atomicAdd(&gsm[19], -0.5 * chi.d[8]);
+  if (tid >= 32 && tid < 41) {
+    // time delays: -chi2_tmd/2 by duals through the FP64 lens model, one tangent per thread
+    // (theta 0..7 and H0 = theta 19)
+    const int q = tid - 32;
+    DT1 tt[8];
+    for (int i = 0; i < 8; ++i) tt[i] = i == q ? DT1::var(th[i], 0) : DT1(th[i]);
+    const DT1 h0 = q == 8 ? DT1::var(th[19], 0) : DT1(th[19]);
+    const DT1 chi = chi2_tmd_t<DT1>(tt, h0, S.img_xy, S.n_img, S.dt_obs, S.dt_sig,
+                                    S.dt_per_arcsec2_H0, S.sis, S.n_sis);
+    atomicAdd(&gsm[q < 8 ? q : 19], -0.5 * chi.d[0]);
   }
   __syncthreads();
   if (tid < GLAD_NTHETA) grad[(size_t)b * GLAD_NTHETA + tid] += gsm[tid];

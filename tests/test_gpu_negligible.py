@@ -73,7 +73,9 @@ def test_gradient_modes_agree(w1):
     assert np.all(s0 == 0) and np.all(s1 == 0) and np.all(s2 == 0)
     scale = np.max(np.abs(g0), axis=1, keepdims=True)
     assert np.all(np.abs(g1 - g0) <= 1e-5 * np.abs(g0) + 1e-6 * scale)
-    assert np.all(np.abs(g2 - g0) <= 1e-6 * np.abs(g0) + 1e-7 * scale)
+    # (mode 2 repeats mode 0's sums; the remaining differences are float atomics in a
+    # run-dependent order)
+    assert np.all(np.abs(g2 - g0) <= 1e-5 * np.abs(g0) + 1e-6 * scale)
     assert np.all(np.abs(l1 - l0) <= 1e-6 * np.abs(l0) + 1e-3)
     # mode 2 sums every tile twice; mode 1 sums a tile twice only where its check failed
     # (here the derivative check may fail where dV/dX or dV/dY nears zero)
