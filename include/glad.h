@@ -188,15 +188,17 @@ glad_status glad_set_tuning(glad_ctx *ctx, int jam_code, int adj_ept);
 
 /* Negligible terms in the forward JAM pair sum (the project's own, no counterpart in the
  * paper).  For every sky tile the full sum at the tile's four corners gives a reference
- * value; a table entry whose term stays below 2^-(30 + log2 n_entries) of that reference
- * over the whole tile is not evaluated there, and the summed bound of everything left out
+ * value; a table entry whose term stays below 2^-(22 + log2 n_entries) of that reference
+ * (2^-(30 + log2 n_entries) in the derivative pass) over the whole tile is not evaluated
+ * there, and the summed bound of everything left out
  * must come to at most 2^-26 of the smallest |Sigma v^2| in the tile (below the FP32
  * rounding of each sum), else the tile is summed again with only the exact skipping of
  * entries that underflow to zero.  mode 0: exact skipping only; 1 (the default): with
  * negligible terms left out; 2: as 1 but every tile's check is failed (for tests: the
  * tiles are summed twice and the results equal mode 0).  Applies to glad_loglike,
  * glad_loglike_static, glad_vrms and the derivative pass of glad_loglike_grad (there the
- * check also covers d(Sigma v^2)/d(x'^2) and d(Sigma v^2)/d(y'^2) at every point).
+ * check also covers d(Sigma v^2)/d(x'^2) and d(Sigma v^2)/d(y'^2), each against 2^-26 of
+ * its largest magnitude in the tile: below the FP32 rounding of those sums).
  * GLAD_EINVAL for other modes. */
 glad_status glad_set_negligible(glad_ctx *ctx, int mode);
 

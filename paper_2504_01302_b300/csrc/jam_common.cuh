@@ -24,7 +24,10 @@ __device__ __forceinline__ float jam_ex2(float x) {
 // bound on everything left out must come to at most 2^-JAM_REL_CHECK of the smallest |sum|
 // in the tile (2^-26: below the FP32 rounding of each sum), else the tile is summed again
 // without it.
-#define JAM_REL_MARGIN 30.0f
+#define JAM_REL_MARGIN 22.0f
+// the derivative pass keeps more (its left-out bounds also cover the derivatives, whose
+// factor ln2 |ax| is largest for the narrow Gaussians that this rule leaves out)
+#define JAM_REL_MARGIN_GRAD 30.0f
 #define JAM_REL_CHECK 26.0f
 
 struct JamSmem {

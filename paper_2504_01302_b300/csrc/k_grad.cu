@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(JAM_THREADS, 3) k_jam_fg(const SysDev *__restr
   const int n_chunks = (n_ent + JAM_CHUNK - 1) / JAM_CHUNK;
   const int lane = tid & 31, warp = tid >> 5;
   // Negligible terms as in the forward pass (reference: the full sum at the tile's corners),
-  // with the a-posteriori check covering V, dV/dX and dV/dY at every point of the tile.
+  // with the a-posteriori check covering V, dV/dX and dV/dY.
   float lref = 0.0f, lrel = -INFINITY;
   if (ws.neg_mode != 0) {
     float cX[4], cY[4], cv[4];
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(JAM_THREADS, 3) k_jam_fg(const SysDev *__restr
     __syncthreads();
     const int f = sm.flag;
     lref = f == 0x7fffffff ? 0.0f : __int_as_float(f);
-    lrel = f == 0x7fffffff ? -INFINITY : -(JAM_REL_MARGIN + __log2f((float)max(n_ent, 1)));
+    lrel = f == 0x7fffffff ? -INFINITY : -(JAM_REL_MARGIN_GRAD + __log2f((float)max(n_ent, 1)));
   }
   if (tid == 0) {
     sm.tb[0] = Xmin;
@@ -405,19 +405,21 @@ __global__ void __launch_bounds__(JAM_THREADS, 3) k_jam_fg(const SysDev *__restr
       __syncthreads();
     }
     if (lrel == -INFINITY) break;
-    // a-posteriori check of V, dV/dX, dV/dY against the smallest magnitudes in the tile
-    float mv = 3.4e38f, mx = 3.4e38f, my = 3.4e38f;
+    // a-posteriori check: the left-out bound of V against the smallest |V| in the tile; those
+    // of dV/dX and dV/dY (sums of mixed signs, which can pass through zero) against their
+    // largest magnitude in the tile, i.e. below the FP32 rounding of those sums
+    float mv = 3.4e38f, mx = 0.0f, my = 0.0f;
 #pragma unroll
     for (int i = 0; i < PTS; ++i)
       if (col <= c1 && row0 + i <= r1) {
         mv = fminf(mv, fabsf((float)dV[i]));
-        mx = fminf(mx, fabsf((float)(d1[i] + LN2D * d2[i])));
-        my = fminf(my, fabsf((float)(LN2D * d3[i])));
+        mx = fmaxf(mx, fabsf((float)(d1[i] + LN2D * d2[i])));
+        my = fmaxf(my, fabsf((float)(LN2D * d3[i])));
       }
     for (int off = 16; off > 0; off >>= 1) {
       mv = fminf(mv, __shfl_xor_sync(0xffffffffu, mv, off));
-      mx = fminf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-      my = fminf(my, __shfl_xor_sync(0xffffffffu, my, off));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+      my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, off));
       rv += __shfl_xor_sync(0xffffffffu, rv, off);
       rx += __shfl_xor_sync(0xffffffffu, rx, off);
       ry += __shfl_xor_sync(0xffffffffu, ry, off);
@@ -433,12 +435,13 @@ __global__ void __launch_bounds__(JAM_THREADS, 3) k_jam_fg(const SysDev *__restr
     }
     __syncthreads();
     if (tid == 0) {
-      float m[3] = {3.4e38f, 3.4e38f, 3.4e38f}, r[3] = {0.f, 0.f, 0.f};
-      for (int w = 0; w < JAM_THREADS / 32; ++w)
-        for (int q = 0; q < 3; ++q) {
-          m[q] = fminf(m[q], chk[q][w]);
-          r[q] += chk[3 + q][w];
-        }
+      float m[3] = {3.4e38f, 0.f, 0.f}, r[3] = {0.f, 0.f, 0.f};
+      for (int w = 0; w < JAM_THREADS / 32; ++w) {
+        m[0] = fminf(m[0], chk[0][w]);
+        m[1] = fmaxf(m[1], chk[1][w]);
+        m[2] = fmaxf(m[2], chk[2][w]);
+        for (int q = 0; q < 3; ++q) r[q] += chk[3 + q][w];
+      }
       bool ok = ws.neg_mode == 1;
       for (int q = 0; q < 3; ++q) ok = ok && (__log2f(r[q]) + lref <= __log2f(m[q]) - JAM_REL_CHECK);
       sm.flag = ok ? 1 : 0;
