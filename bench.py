@@ -36,6 +36,12 @@ N_SM = 148
 # ex2.approx results per clock per SM on B300 (MUFU), measured by a throughput probe
 # (paper_2504_01302_b300/rates/probe_rates.cu): 32.3-32.8 ex2/clk/SM.
 MUFU_EX2_PER_CLK_SM = 32
+# FP32 FMA lanes per clock per SM (the same probe measures 3.5-3.8e13 FFMA/s at 2032 MHz)
+FFMA_LANES_PER_CLK_SM = 128
+# FMA-pipe operations per integrand evaluation in the gradient's JAM kernels: derivative pass
+# (exponent 2, prefactor 1, term 1, value and two derivative sums 4), table adjoint (exponent
+# 2, weighted term 1, four moment sums 4)
+FMA_OPS_PER_EVAL = {"k_jam_fwd_grad": 8, "k_jam_adjoint": 7}
 
 
 def parse():
@@ -425,14 +431,16 @@ def main():
     # integrand evaluations the JAM kernels actually execute per step (exact and negligible
     # terms skipped), from one more untimed full-batch step
     step()
-    n_exec = ctx.jam_evaluations()
-    # ---- roofline of the dominant kernel (JAM pair sum): integrand evaluations per launch,
-    # one ex2 each, against the MUFU ex2 rate
+    n_exec = {"k_jam": ctx.jam_evaluations(), "k_jam_fwd_grad": ctx.jam_evaluations(),
+              "k_jam_adjoint": ctx.jam_evaluations(adjoint=True)}
+    # ---- roofline of the dominant kernel (the JAM pair sum, its derivative pass or the
+    # table adjoint, whichever takes longest per step): integrand evaluations per launch
+    # against the pipe that bounds that kernel
     names = [lib.glad_kernel_name(i).decode() for i in range(nk)]
     per_kernel = {names[i]: kms[i] / max(kl[i], 1) for i in range(nk) if kl[i]}
-    jam_id = names.index("k_jam_fwd_grad") if args.grad and kl[names.index("k_jam_fwd_grad")] \
-        else names.index("k_jam")
-    jam_ms = kms[jam_id] / max(kl[jam_id], 1)
+    jam_name = max((n for n in ("k_jam", "k_jam_fwd_grad", "k_jam_adjoint") if n in per_kernel),
+                   key=lambda n: per_kernel[n])
+    jam_ms = per_kernel[jam_name]
     evals = 0
     for b in range(B):
         s = systems[sid_np[b]]
@@ -442,7 +450,18 @@ def main():
     achieved = evals / (jam_ms / 1000.0) / 1e9
     clocks = clk.summary()
     sm_max = clocks["sm_max_mhz"] or 2032.0
-    peak = N_SM * MUFU_EX2_PER_CLK_SM * sm_max * 1e6 / 1e9
+    if jam_name == "k_jam":
+        # one ex2 per evaluation; the 4 FMA-pipe operations per evaluation allow the same rate
+        peak = N_SM * MUFU_EX2_PER_CLK_SM * sm_max * 1e6 / 1e9
+        peak_unit = "Gexp2/s"
+        peak_basis = (f"{N_SM} SM x {MUFU_EX2_PER_CLK_SM} ex2/clk/SM (measured) x "
+                      f"{sm_max:.0f} MHz max SM clock")
+    else:
+        ops = FMA_OPS_PER_EVAL[jam_name]
+        peak = N_SM * FFMA_LANES_PER_CLK_SM * sm_max * 1e6 / ops / 1e9
+        peak_unit = "Geval/s"
+        peak_basis = (f"{N_SM} SM x {FFMA_LANES_PER_CLK_SM} FP32 lanes/clk/SM x {sm_max:.0f} MHz "
+                      f"/ {ops} FMA-pipe operations per evaluation")
     unit = "logL+grad/s" if args.grad else "logL/s"
     line = {
         "metric": METRIC, "value": value, "unit": unit,
@@ -453,19 +472,19 @@ def main():
                    "precision": "f32 bulk; f64 MGE, tables and chi^2 reductions",
                    "l2": "flushed (256 MB write) before each timed step", "valid_samples": n_valid,
                    "tuning": tuning, "cuda_graph": bool(use_graph),
-                   "jam_skipping": "terms that underflow to 0 over a sky tile, and (forward pass) "
-                                   "terms whose bound over the tile stays below 2^-26 of its "
-                                   "smallest sum (checked after the sum)"},
-        "roofline": {"bound": "alu", "kernel": names[jam_id], "achieved": achieved, "peak": peak,
-                     "unit": "Gexp2/s", "frac": achieved / peak,
-                     "traffic": ncu_traffic(names[jam_id], w, args.grad, B),
+                   "jam_skipping": "terms that underflow to 0 over a sky tile, and (pair sum and "
+                                   "derivative pass) terms whose bounded total over the tile "
+                                   "stays below 2^-26 of its smallest sum (checked after the sum)"},
+        "roofline": {"bound": "alu", "kernel": jam_name, "achieved": achieved, "peak": peak,
+                     "unit": peak_unit, "frac": achieved / peak,
+                     "traffic": ncu_traffic(jam_name, w, args.grad, B),
                      "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
                                       "small-batch capture, scaled by samples to this batch",
-                     "algorithmic_units": f"{evals} JAM integrand evaluations per launch (1 ex2 each)",
-                     "executed_evaluations": n_exec,
-                     "executed_frac": n_exec / (jam_ms / 1000.0) / 1e9 / peak,
-                     "peak_basis": f"{N_SM} SM x {MUFU_EX2_PER_CLK_SM} ex2/clk/SM (measured) x "
-                                   f"{sm_max:.0f} MHz max SM clock"},
+                     "algorithmic_units": f"{evals} JAM integrand evaluations per launch "
+                                          f"(sky sub-samples x table entries)",
+                     "executed_evaluations": n_exec[jam_name],
+                     "executed_frac": n_exec[jam_name] / (jam_ms / 1000.0) / 1e9 / peak,
+                     "peak_basis": peak_basis},
         "kernels_ms_per_step": per_kernel,
         "plain_form": {"value": n_plain / (plain_ms / 1000.0), "unit": unit, "samples": n_plain,
                        "form": "one sample per call (B = 1), same kernels, no graph"},

@@ -202,10 +202,12 @@ glad_status glad_set_tuning(glad_ctx *ctx, int jam_code, int adj_ept);
  * GLAD_EINVAL for other modes. */
 glad_status glad_set_negligible(glad_ctx *ctx, int mode);
 
-/* Integrand evaluations the JAM pair-sum kernels executed in the last glad_loglike,
- * glad_loglike_grad or glad_vrms call on this context (skipped terms excluded).
- * Synchronises the device. */
-glad_status glad_jam_evaluations(glad_ctx *ctx, unsigned long long *count);
+/* Integrand evaluations executed in the last glad_loglike, glad_loglike_grad or glad_vrms
+ * call on this context (skipped terms excluded): *count by the JAM pair sum (forward or
+ * derivative pass), *count_adjoint (may be NULL) by the table adjoint of the gradient, as
+ * (entry, sky point) pairs.  Synchronises the device. */
+glad_status glad_jam_evaluations(glad_ctx *ctx, unsigned long long *count,
+                                 unsigned long long *count_adjoint);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *glad_last_error(void);

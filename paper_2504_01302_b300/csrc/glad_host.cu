@@ -399,7 +399,7 @@ glad_status ws_ensure(glad_ctx *c, int B) {
             ws_alloc(w, w.d.img, b * c->max_pix) && ws_alloc(w, w.d.binacc, b * c->max_bins * 2) &&
             ws_alloc(w, w.d.terms, b * 3) && ws_alloc(w, w.d.status, b) &&
             ws_alloc(w, w.d.wl_off, b + 1) && ws_alloc(w, w.d.wl_counter, 1) &&
-            ws_alloc(w, w.d.evals, 1);
+            ws_alloc(w, w.d.evals, 2);
   if (!ok) {
     ws_free(w);
     return fail(GLAD_ENOMEM, "workspace for B=%d does not fit on the device", B);
@@ -417,7 +417,7 @@ glad_status forward(glad_ctx *c, const int *sys_id, const double *theta, int B, 
   cudaError_t e;
   c->ws.d.neg_mode = c->tune.neg_mode;
   e = cudaMemsetAsync(c->ws.d.terms, 0, sizeof(double) * 3 * B, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->ws.d.evals, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->ws.d.evals, 0, 2 * sizeof(unsigned long long), st);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(c->ws.d.binacc, 0, sizeof(double) * 2 * c->max_bins * (size_t)B, st);
   if (e == cudaSuccess) e = GLAD_PROF(c, st, KID_PREP, launch_prep(c, sys_id, theta, B, st));
@@ -483,14 +483,18 @@ glad_status glad_set_negligible(glad_ctx *c, int mode) {
   return GLAD_OK;
 }
 
-glad_status glad_jam_evaluations(glad_ctx *c, unsigned long long *count) {
+glad_status glad_jam_evaluations(glad_ctx *c, unsigned long long *count,
+                                 unsigned long long *count_adjoint) {
   if (!c || !count) return fail(GLAD_EINVAL, "glad_jam_evaluations: bad arguments");
   *count = 0;
+  if (count_adjoint) *count_adjoint = 0;
   if (!c->ws.d.evals) return GLAD_OK;
+  unsigned long long n[2] = {0, 0};
   cudaError_t e = cudaDeviceSynchronize();
-  if (e == cudaSuccess)
-    e = cudaMemcpy(count, c->ws.d.evals, sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(n, c->ws.d.evals, sizeof(n), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return fail(GLAD_ECUDA, "glad_jam_evaluations: %s", cudaGetErrorString(e));
+  *count = n[0];
+  if (count_adjoint) *count_adjoint = n[1];
   return GLAD_OK;
 }
 

@@ -115,7 +115,8 @@ struct WsDev {
   int *status;                 // [B]
   int *wl_off;                 // [B+1] persistent JAM work list (first item of each sample)
   int *wl_counter;             // [1]   next work item
-  unsigned long long *evals;   // [1]   JAM integrand evaluations executed (null: not counted)
+  unsigned long long *evals;   // [2]   JAM integrand evaluations executed: pair sum (forward or
+                               //       derivative pass), table adjoint (null: not counted)
   int neg_mode;                // negligible-term skipping in the forward JAM pass: 0 off,
                                // 1 on, 2 on with every tile's check failed (summed again)
 };

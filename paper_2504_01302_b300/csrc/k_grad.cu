@@ -648,6 +648,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_jam_adj(const SysDev *__restric
   for (int k = 0; k < EPT; ++k) S0[k] = SX[k] = SY[k] = SXY[k] = 0.0;
   const float4 *gp = gw.adjpt + 2 * (size_t)b * max_apts;
   const int n_chunks = S.n_atile;
+  unsigned long long n_eval = 0;  // (entry, point) pairs this thread evaluates
   for (int i = tid; i < 2 * ADJ_PCHUNK; i += ADJ_THREADS) pts[0][i] = gp[i];
   __syncthreads();
   for (int ch = 0; ch < n_chunks; ++ch) {
@@ -673,6 +674,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_jam_adj(const SysDev *__restric
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
       if (!need[p]) continue;  // warp-uniform
+      n_eval += ((ent[2 * p] >= 0) + (ent[2 * p + 1] >= 0)) * ADJ_PCHUNK;
 #pragma unroll 4
       for (int i = 0; i < ADJ_PCHUNK; ++i) {
         const float4 A = pp[2 * i], Bq = pp[2 * i + 1];  // (X, X, Y, Y), (XY, XY, g, g)
@@ -699,6 +701,10 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_jam_adj(const SysDev *__restric
       s0[p] = sx[p] = sy[p] = sxy[p] = z2;
     }
     __syncthreads();
+  }
+  if (ws.evals) {
+    for (int off = 16; off > 0; off >>= 1) n_eval += __shfl_xor_sync(0xffffffffu, n_eval, off);
+    if ((tid & 31) == 0 && n_eval) atomicAdd(&ws.evals[1], n_eval);
   }
 #pragma unroll
   for (int k = 0; k < EPT; ++k) {

@@ -151,11 +151,13 @@ class GladContext:
         """Negligible-term skipping of the forward JAM pass (glad_set_negligible)."""
         _lib.check(self.lib.glad_set_negligible(self.handle, int(mode)), "glad_set_negligible")
 
-    def jam_evaluations(self):
-        """Integrand evaluations the JAM kernels executed in the last call."""
-        n = C.c_ulonglong()
-        _lib.check(self.lib.glad_jam_evaluations(self.handle, C.byref(n)), "glad_jam_evaluations")
-        return n.value
+    def jam_evaluations(self, adjoint=False):
+        """Integrand evaluations the JAM pair-sum kernel (or, with adjoint, the table
+        adjoint) executed in the last call."""
+        n, na = C.c_ulonglong(), C.c_ulonglong()
+        _lib.check(self.lib.glad_jam_evaluations(self.handle, C.byref(n), C.byref(na)),
+                   "glad_jam_evaluations")
+        return na.value if adjoint else n.value
 
     def kernel_times(self):
         """{kernel name: (ms, launches)} recorded since profiling was enabled."""

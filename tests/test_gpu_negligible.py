@@ -68,6 +68,11 @@ def test_gradient_modes_agree(w1):
         ctx.set_negligible(mode)
         logL, g, st = ctx.loglike_grad(th)
         out[mode] = (logL.cpu().numpy(), g.cpu().numpy(), st.cpu().numpy(), ctx.jam_evaluations())
+        # the table adjoint is summed with exact skipping only, in every mode
+        n_adj = ctx.jam_evaluations(adjoint=True)
+        nl = sum(s["n_mge_light"])
+        n_alg = 4 * (s["kx"] * s["kss"]) * (s["ky"] * s["kss"]) * nl * (s["n_mge_mass"] + 1) * s["n_gl"]
+        assert 0 < n_adj <= 1.1 * n_alg  # (tiles padded to 16 x 16 points)
     ctx.set_negligible(1)
     (l0, g0, s0, n0), (l1, g1, s1, n1), (l2, g2, s2, n2) = out[0], out[1], out[2]
     assert np.all(s0 == 0) and np.all(s1 == 0) and np.all(s2 == 0)
