@@ -486,6 +486,9 @@ def main():
                      "executed_frac": n_exec[jam_name] / (jam_ms / 1000.0) / 1e9 / peak,
                      "peak_basis": peak_basis},
         "kernels_ms_per_step": per_kernel,
+        "kernels_note": "CUDA-event time per launch unit in profiled steps; the lensing branch "
+                        "(k_image+k_conv, k_grad_lens) runs on a second stream concurrently "
+                        "with the dynamics branch, so those times overlap",
         "plain_form": {"value": n_plain / (plain_ms / 1000.0), "unit": unit, "samples": n_plain,
                        "form": "one sample per call (B = 1), same kernels, no graph"},
         "e2e": {"value": world * B * args.steps / (e2e_ms / 1000.0), "unit": unit,

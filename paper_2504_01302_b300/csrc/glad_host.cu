@@ -11,8 +11,6 @@
 
 #include "glad_internal.cuh"
 
-cudaError_t launch_grad(glad_ctx *c, const int *sys_id, const double *theta, int B, double *grad,
-                        cudaStream_t st);
 cudaError_t grad_ws_ensure(glad_ctx *c, int B);
 void grad_ws_free(glad_ctx *c);
 float *grad_resid_buffer(glad_ctx *c);
@@ -408,10 +406,10 @@ glad_status ws_ensure(glad_ctx *c, int B) {
   return GLAD_OK;
 }
 
-// Forward launch sequence.  With `grad`, k_conv also leaves the residual weights and the
-// JAM pass keeps the per-point derivatives that the adjoint kernels need.
+// One sample's model image (image_out) or binned v_rms (vrms_out): the part of the forward
+// sequence that output needs, on the caller's stream.
 glad_status forward(glad_ctx *c, const int *sys_id, const double *theta, int B, cudaStream_t st,
-                    float *image_out, float *vrms_out, bool grad = false) {
+                    float *image_out, float *vrms_out) {
   glad_status s = ws_ensure(c, B);
   if (s != GLAD_OK) return s;
   cudaError_t e;
@@ -421,17 +419,54 @@ glad_status forward(glad_ctx *c, const int *sys_id, const double *theta, int B, 
   if (e == cudaSuccess)
     e = cudaMemsetAsync(c->ws.d.binacc, 0, sizeof(double) * 2 * c->max_bins * (size_t)B, st);
   if (e == cudaSuccess) e = GLAD_PROF(c, st, KID_PREP, launch_prep(c, sys_id, theta, B, st));
-  if (e == cudaSuccess && !image_out)
+  if (e == cudaSuccess && image_out)
+    e = GLAD_PROF(c, st, KID_IMAGE_CONV, launch_lens(c, sys_id, B, image_out, st, nullptr));
+  if (e == cudaSuccess && vrms_out) {
     e = GLAD_PROF(c, st, KID_TABLE, launch_table(c, sys_id, B, st));
-  if (e == cudaSuccess && !vrms_out)
-    e = GLAD_PROF(c, st, KID_IMAGE_CONV,
-                  launch_lens(c, sys_id, B, image_out, st, grad ? grad_resid_buffer(c) : nullptr));
-  if (e == cudaSuccess && !image_out) {
+    if (e == cudaSuccess) e = GLAD_PROF(c, st, KID_JAM, launch_jam(c, sys_id, B, st));
+    if (e == cudaSuccess) e = GLAD_PROF(c, st, KID_KIN, launch_kin_finalize(c, sys_id, B, vrms_out, st));
+  }
+  if (e != cudaSuccess) return fail(GLAD_ECUDA, "launch failed: %s", cudaGetErrorString(e));
+  return GLAD_OK;
+}
+
+// The full likelihood (and with `grad` its gradient): after k_prep the lensing branch
+// (k_image, k_conv and, for the gradient, its adjoint) runs on the context's second stream
+// while the dynamics branch (table, JAM pair sum, v_rms, dynamics adjoint) runs on the
+// caller's; an event joins them before the combination.
+glad_status full_path(glad_ctx *c, const int *sys_id, const double *theta, int B, cudaStream_t st,
+                      double *logL, int *sample_status, double *terms, double *grad) {
+  glad_status s = ws_ensure(c, B);
+  if (s != GLAD_OK) return s;
+  cudaError_t e;
+  c->ws.d.neg_mode = c->tune.neg_mode;
+  e = cudaMemsetAsync(c->ws.d.terms, 0, sizeof(double) * 3 * B, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->ws.d.evals, 0, 2 * sizeof(unsigned long long), st);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(c->ws.d.binacc, 0, sizeof(double) * 2 * c->max_bins * (size_t)B, st);
+  if (e == cudaSuccess && grad) e = grad_prepare(c, B, grad, st);
+  if (e == cudaSuccess) e = GLAD_PROF(c, st, KID_PREP, launch_prep(c, sys_id, theta, B, st));
+  // fork
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev_fork, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+  if (e == cudaSuccess)
+    e = GLAD_PROF(c, c->side, KID_IMAGE_CONV,
+                  launch_lens(c, sys_id, B, nullptr, c->side, grad ? grad_resid_buffer(c) : nullptr));
+  if (e == cudaSuccess && grad) e = launch_grad_lens(c, sys_id, B, grad, c->side);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
+  // dynamics on the caller's stream
+  if (e == cudaSuccess) e = GLAD_PROF(c, st, KID_TABLE, launch_table(c, sys_id, B, st));
+  if (e == cudaSuccess) {
     if (grad) e = GLAD_PROF(c, st, KID_GRAD_JAM_FWD, launch_jam_fg(c, sys_id, B, st));
     else e = GLAD_PROF(c, st, KID_JAM, launch_jam(c, sys_id, B, st));
   }
-  if (e == cudaSuccess && !image_out)
-    e = GLAD_PROF(c, st, KID_KIN, launch_kin_finalize(c, sys_id, B, vrms_out, st));
+  if (e == cudaSuccess) e = GLAD_PROF(c, st, KID_KIN, launch_kin_finalize(c, sys_id, B, nullptr, st));
+  if (e == cudaSuccess && grad) e = launch_grad_dyn(c, sys_id, theta, B, grad, st);
+  // join
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->ev_join, 0);
+  if (e == cudaSuccess && grad) e = launch_grad_finish(c, B, grad, st);
+  if (e == cudaSuccess)
+    e = GLAD_PROF(c, st, KID_COMBINE, launch_combine(c, B, logL, sample_status, terms, st));
   if (e != cudaSuccess) return fail(GLAD_ECUDA, "launch failed: %s", cudaGetErrorString(e));
   return GLAD_OK;
 }
@@ -570,6 +605,12 @@ glad_status glad_create(const glad_system_desc *sys, int n_sys, glad_ctx **out) 
   cudaMemcpy(c->d_one_sys, ids.data(), sizeof(int) * n_sys, cudaMemcpyHostToDevice);
   set_conv_smem_limit();
   set_grad_smem_limit();
+  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    glad_destroy(c);
+    return fail(GLAD_ECUDA, "glad_create: stream or event creation failed");
+  }
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     glad_destroy(c);
@@ -594,6 +635,9 @@ void glad_destroy(glad_ctx *c) {
     cudaEventDestroy(r.b);
   }
   for (auto e : c->ev_pool) cudaEventDestroy(e);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side) cudaStreamDestroy(c->side);
   delete c;
 }
 
@@ -602,13 +646,7 @@ glad_status glad_loglike(glad_ctx *c, const int *sys_id, const double *theta, in
   g_err.clear();
   if (!c || !sys_id || !theta || !logL || !sample_status || B < 1)
     return fail(GLAD_EINVAL, "glad_loglike: bad arguments");
-  cudaStream_t st = (cudaStream_t)stream;
-  glad_status s = forward(c, sys_id, theta, B, st, nullptr, nullptr);
-  if (s != GLAD_OK) return s;
-  cudaError_t e =
-      GLAD_PROF(c, st, KID_COMBINE, launch_combine(c, B, logL, sample_status, terms, st));
-  if (e != cudaSuccess) return fail(GLAD_ECUDA, "launch failed: %s", cudaGetErrorString(e));
-  return GLAD_OK;
+  return full_path(c, sys_id, theta, B, (cudaStream_t)stream, logL, sample_status, terms, nullptr);
 }
 
 glad_status glad_loglike_grad(glad_ctx *c, const int *sys_id, const double *theta, int B,
@@ -617,16 +655,9 @@ glad_status glad_loglike_grad(glad_ctx *c, const int *sys_id, const double *thet
   g_err.clear();
   if (!c || !sys_id || !theta || !logL || !grad || !sample_status || B < 1)
     return fail(GLAD_EINVAL, "glad_loglike_grad: bad arguments");
-  cudaStream_t st = (cudaStream_t)stream;
   if (grad_ws_ensure(c, B) != cudaSuccess)
     return fail(GLAD_ENOMEM, "gradient workspace for B=%d does not fit", B);
-  glad_status s = forward(c, sys_id, theta, B, st, nullptr, nullptr, true);
-  if (s != GLAD_OK) return s;
-  cudaError_t e = launch_grad(c, sys_id, theta, B, grad, st);
-  if (e == cudaSuccess)
-    e = GLAD_PROF(c, st, KID_COMBINE, launch_combine(c, B, logL, sample_status, terms, st));
-  if (e != cudaSuccess) return fail(GLAD_ECUDA, "gradient launch failed: %s", cudaGetErrorString(e));
-  return GLAD_OK;
+  return full_path(c, sys_id, theta, B, (cudaStream_t)stream, logL, sample_status, terms, grad);
 }
 
 glad_status glad_model_image(glad_ctx *c, int sys, const double *theta, float *image,

@@ -149,6 +149,10 @@ struct glad_ctx {
     int adj_ept = 4;      // table entries per thread in the JAM adjoint
   } tune;
   int *d_one_sys = nullptr;      // scratch sys id for single-sample calls
+  // the lensing branch runs on a second stream, forked from and joined back into the
+  // caller's stream by events (capturable into a CUDA graph)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // kernel timing (glad_profile)
   int prof = 0;
   struct Rec {
@@ -187,6 +191,12 @@ cudaError_t launch_table(glad_ctx *c, const int *sys_id, int B, cudaStream_t st)
 cudaError_t launch_lens(glad_ctx *c, const int *sys_id, int B, float *image_out,
                         cudaStream_t st, float *resid_out = nullptr);
 cudaError_t launch_jam(glad_ctx *c, const int *sys_id, int B, cudaStream_t st);
+// gradient pieces (k_grad.cu): zeroing, lensing adjoint, dynamics adjoint + chain, final fix-up
+cudaError_t grad_prepare(glad_ctx *c, int B, double *grad, cudaStream_t st);
+cudaError_t launch_grad_lens(glad_ctx *c, const int *sys_id, int B, double *grad, cudaStream_t st);
+cudaError_t launch_grad_dyn(glad_ctx *c, const int *sys_id, const double *theta, int B,
+                            double *grad, cudaStream_t st);
+cudaError_t launch_grad_finish(glad_ctx *c, int B, double *grad, cudaStream_t st);
 cudaError_t launch_kin_finalize(glad_ctx *c, const int *sys_id, int B, float *vrms_out,
                                 cudaStream_t st);
 cudaError_t launch_combine(glad_ctx *c, int B, double *logL, int *status, double *terms,

@@ -15,8 +15,6 @@
 
 glad_status glad_set_error(glad_status s, const char *msg);
 cudaError_t grad_ws_ensure(glad_ctx *c, int B);
-cudaError_t launch_grad(glad_ctx *c, const int *sys_id, const double *theta, int B, double *grad,
-                        cudaStream_t st);
 cudaError_t launch_jam_fg(glad_ctx *c, const int *sys_id, int B, cudaStream_t st);
 float *grad_resid_buffer(glad_ctx *c);
 cudaError_t time_jam_adj(glad_ctx *c, const int *sys_id, int B, cudaStream_t st);

@@ -958,7 +958,8 @@ __global__ void __launch_bounds__(256) k_grad_chain(const SysDev *__restrict__ s
     atomicAdd(&gsm[q < 8 ? q : 19], -0.5 * chi.d[0]);
   }
   __syncthreads();
-  if (tid < GLAD_NTHETA) grad[(size_t)b * GLAD_NTHETA + tid] += gsm[tid];
+  // atomic: the lensing adjoint, on the other stream, may be adding into the same entries
+  if (tid < GLAD_NTHETA && gsm[tid] != 0.0) atomicAdd(&grad[(size_t)b * GLAD_NTHETA + tid], gsm[tid]);
 }
 
 __global__ void k_grad_zero_invalid(const WsDev ws, int B, double *grad) {
@@ -1016,18 +1017,21 @@ cudaError_t launch_jam_fg(glad_ctx *c, const int *sys_id, int B, cudaStream_t st
   return cudaGetLastError();
 }
 
-// after the forward pass (with k_jam_fg and the residual output of k_conv)
-cudaError_t launch_grad(glad_ctx *c, const int *sys_id, const double *theta, int B, double *grad,
-                        cudaStream_t st) {
+// the accumulators the gradient kernels add into start at zero (before the forward pass)
+cudaError_t grad_prepare(glad_ctx *c, int B, double *grad, cudaStream_t st) {
   GradWs &g = *c->gws;
   cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(double) * GLAD_NTHETA * (size_t)B, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(g.adjI0, 0, sizeof(double) * c->max_light * (size_t)B, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(g.tadj, 0, sizeof(double) * g.tstride * (size_t)B, st);
   // tile padding beyond the sky grid must read as g_N = 0
   if (e == cudaSuccess) e = cudaMemsetAsync(g.adjpt, 0, sizeof(float4) * 2 * c->max_apts * (size_t)B, st);
-  if (e != cudaSuccess) return e;
-  // lensing
-  e = GLAD_PROF(c, st, KID_GRAD_LENS, ([&]() -> cudaError_t {
+  return e;
+}
+
+// lensing adjoint (after k_conv has left the residual weights)
+cudaError_t launch_grad_lens(glad_ctx *c, const int *sys_id, int B, double *grad, cudaStream_t st) {
+  GradWs &g = *c->gws;
+  return GLAD_PROF(c, st, KID_GRAD_LENS, ([&]() -> cudaError_t {
     int max_conv_tiles = 0, max_k = 1;
     for (auto &s : c->sys) {
       const int t = ((s.d.nx + CONV_TX - 1) / CONV_TX) * ((s.d.ny + CONV_TY - 1) / CONV_TY);
@@ -1044,11 +1048,15 @@ cudaError_t launch_grad(glad_ctx *c, const int *sys_id, const double *theta, int
                                                                      c->max_pix, grad);
     return cudaGetLastError();
   }()));
-  if (e != cudaSuccess) return e;
-  // dynamics
+}
+
+// dynamics adjoint and the per-sample chain (after k_jam_fg and k_kin_finalize)
+cudaError_t launch_grad_dyn(glad_ctx *c, const int *sys_id, const double *theta, int B,
+                            double *grad, cudaStream_t st) {
+  GradWs &g = *c->gws;
   k_kin_adj<<<dim3(c->max_sky_tiles, B), JAM_THREADS, 0, st>>>(
       c->d_sys, sys_id, c->ws.d, g, c->max_light, c->max_bins, c->max_sub, c->max_apts, grad);
-  e = cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = GLAD_PROF(c, st, KID_GRAD_JAM_ADJ, ([&]() -> cudaError_t {
     const int ept = c->tune.adj_ept;
@@ -1062,7 +1070,7 @@ cudaError_t launch_grad(glad_ctx *c, const int *sys_id, const double *theta, int
     return cudaGetLastError();
   }()));
   if (e != cudaSuccess) return e;
-  e = GLAD_PROF(c, st, KID_GRAD_CHAIN, ([&]() -> cudaError_t {
+  return GLAD_PROF(c, st, KID_GRAD_CHAIN, ([&]() -> cudaError_t {
     int pairs = 0;
     for (auto &sd : c->h_sysdev) pairs = std::max(pairs, sd.n_light * sd.n_mass_tot);
     k_table_adj<<<dim3((pairs + 7) / 8, B), 256, 0, st>>>(c->d_sys, sys_id, c->ws.d, g, c->max_light,
@@ -1071,12 +1079,14 @@ cudaError_t launch_grad(glad_ctx *c, const int *sys_id, const double *theta, int
     if (r0 != cudaSuccess) return r0;
     k_grad_chain<<<B, 256, 0, st>>>(c->d_sys, sys_id, theta, c->ws.d, g, c->max_light,
                                     c->max_mass_tot, c->max_ent, grad);
-    cudaError_t r = cudaGetLastError();
-    if (r != cudaSuccess) return r;
-    k_grad_zero_invalid<<<(B * GLAD_NTHETA + 255) / 256, 256, 0, st>>>(c->ws.d, B, grad);
     return cudaGetLastError();
   }()));
-  return e;
+}
+
+// zero the gradient of invalid samples (after both branches)
+cudaError_t launch_grad_finish(glad_ctx *c, int B, double *grad, cudaStream_t st) {
+  k_grad_zero_invalid<<<(B * GLAD_NTHETA + 255) / 256, 256, 0, st>>>(c->ws.d, B, grad);
+  return cudaGetLastError();
 }
 
 // the entry-parallel adjoint alone, with the context's current shape (for the autotuner)
