@@ -1,0 +1,70 @@
+"""Error behaviour of the C ABI that needs no GPU: glad_create validates every system
+descriptor on the host before it touches the device, and the entry points reject null
+contexts and empty batches.  Each invalid descriptor differs from a valid one in a single
+field."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from . import systems
+
+GLAD_EINVAL, GLAD_EUNSUPPORTED = 1, 5
+
+
+def _create(mutate):
+    from paper_2504_01302_b300 import _lib
+    from paper_2504_01302_b300.glad import GladContext
+    s = dict(systems.small_system(7))
+    mutate(s)
+    with pytest.raises(_lib.GladError) as ei:
+        GladContext([s])
+    return str(ei.value)
+
+
+def _set(key, value):
+    def m(s):
+        s[key] = value
+    return m
+
+
+@pytest.mark.parametrize("mutate, status, words", [
+    (_set("psf", np.ones((4, 4), np.float32) / 16), GLAD_EINVAL, "psf_k must be odd"),
+    (_set("kpsf", np.ones((2, 2), np.float32) / 4), GLAD_EINVAL, "kpsf_k must be odd"),
+    (_set("nx", 0), GLAD_EINVAL, "bad image geometry"),
+    (_set("kss", 0), GLAD_EINVAL, "bad sky geometry"),
+    (_set("n_gl", 1), GLAD_EINVAL, "quadrature order"),
+    (_set("mass_rmax", 0.001), GLAD_EINVAL, "bad MGE ranges"),
+    (_set("img_xy", np.zeros((1, 2))), GLAD_EINVAL, "need >= 2 images"),
+    (_set("z_s", 0.1), GLAD_EINVAL, "bad cosmology"),
+    (_set("n_mge_light", [1, 4]), GLAD_EINVAL, "n_mge_light < 2"),
+    (_set("psf", np.ones((65, 65), np.float32) / 65 ** 2), GLAD_EUNSUPPORTED, "psf_k >"),
+    (_set("n_mge_mass", 200), GLAD_EUNSUPPORTED, "n_mge_mass >"),
+    (_set("mge_P", 40), GLAD_EUNSUPPORTED, "mge_P >"),
+    (_set("n_mge_light", [100, 40]), GLAD_EUNSUPPORTED, "tracer Gaussians >"),
+    (_set("img_xy", np.zeros((9, 2))), GLAD_EUNSUPPORTED, "n_img >"),
+])
+def test_create_rejects_invalid_descriptors(mutate, status, words):
+    msg = _create(mutate)
+    assert f"status {status}" in msg and words in msg, msg
+
+
+def test_create_rejects_bin_indices_beyond_n_bins():
+    def m(s):
+        b = np.array(s["bins"], np.int32, copy=True)
+        b[b >= 0] = s["n_bins"]  # every binned spaxel points past the last bin
+        s["bins"] = b
+    msg = _create(m)
+    assert f"status {GLAD_EINVAL}" in msg and "bin index >= n_bins" in msg, msg
+
+
+def test_entry_points_reject_null_context_and_empty_batch():
+    from paper_2504_01302_b300 import _lib
+    lib = _lib.lib()
+    p = C.c_void_p(8)  # never dereferenced: the checks come first
+    assert lib.glad_loglike(None, p, p, 4, p, p, None, None) == GLAD_EINVAL
+    assert lib.glad_loglike_grad(None, p, p, 4, p, p, p, None, None) == GLAD_EINVAL
+    assert lib.glad_set_negligible(None, 1) == GLAD_EINVAL
+    assert lib.glad_set_tuning(None, 4052, 2) == GLAD_EINVAL
+    assert lib.glad_create(None, 1, C.byref(C.c_void_p())) == GLAD_EINVAL
+    assert "glad_create" in lib.glad_last_error().decode()

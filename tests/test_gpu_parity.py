@@ -163,6 +163,50 @@ def test_psf_sides_in_every_convolution_form():
         assert_image_close(ctx.model_image(_th(th[b]), b).cpu().numpy(), ev["image"])
 
 
+def test_degenerate_parameters_match_oracle(small):
+    # the method's special cases: a round EPL (q = 1, no series terms), the SIE (gamma' = 2),
+    # isotropy (beta = 0), edge-on (i = 90 deg), no black hole mass (f_BH = 0), no external
+    # shear, the galaxy frame on the sky axes with the lens at the origin; one sample alone
+    # (B = 1) and all together
+    s, ctx = small
+    I = synth.IDX
+    base = systems.near_truth_thetas(1, seed=17)[0]
+    cases = []
+    for changes in ({"q": 1.0, "gamma": 2.0, "beta": 0.0},
+                    {"inc": math.pi / 2, "f_bh": 0.0, "gamma_ext": 0.0},
+                    {"phi": 0.0, "x_c": 0.0, "y_c": 0.0, "q": 1.0},
+                    {"gamma": 2.0, "beta": 0.0, "inc": math.pi / 2, "f_bh": 0.0}):
+        t = base.copy()
+        for k, v in changes.items():
+            t[I[k]] = v
+        cases.append(t)
+    th = np.array(cases)
+    logL, st = ctx.loglike(_th(th))
+    logL, st = logL.cpu().numpy(), st.cpu().numpy()
+    for b, t in enumerate(th):
+        ev = model.evaluate(t, s)
+        assert st[b] == ev["status"] == model.ST_OK, (b, st[b], ev["status"])
+        assert abs(logL[b] - ev["logL"]) < systems.logl_tol(ev["logL"]), (b, logL[b], ev["logL"])
+        one, st1 = ctx.loglike(_th(t[None]))
+        assert int(st1[0]) == 0 and abs(float(one[0]) - logL[b]) < 1e-6 * abs(logL[b])
+        assert_image_close(ctx.model_image(_th(t)).cpu().numpy(), ev["image"])
+        assert_vrms_close(ctx.vrms(_th(t)).cpu().numpy(), ev["vrms"])
+
+
+def test_degenerate_parameters_gradient(small):
+    # interior special cases (gamma' = 2, beta = 0, f_BH = 0 away from its bound for the FD
+    # step: the oracle differences are central) against oracle central differences
+    from .test_gpu_grad import assert_grad_close
+    s, ctx = small
+    I = synth.IDX
+    t = systems.near_truth_thetas(1, seed=19)[0]
+    t[I["gamma"]] = 2.0
+    t[I["beta"]] = 0.0
+    logL, g, st = ctx.loglike_grad(_th(t[None]))
+    assert int(st[0]) == 0
+    assert_grad_close(g.cpu().numpy()[0], model.grad_fd(t, s))
+
+
 def test_batch_independence(small):
     # a sample's logL does not depend on which other samples share the launch
     s, ctx = small
