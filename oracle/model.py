@@ -2,8 +2,9 @@
 
 Eq. chi_general / Eq. Posterior_LD: the joint chi^2 of the terms built here is
 chi^2 = chi^2_pix (Eq. chi2 of lens_light over the whole extended image) +
-chi^2_dyn (Eq. chi2_dyn) + chi^2_tmd (Eq. chi2_tmd), and logL = -chi^2/2 (the
-Gaussian normalisation constant is dropped, as chi^2_LD has none).
+chi^2_dyn (Eq. chi2_dyn) + chi^2_tmd (Eq. chi2_tmd) [+ chi^2_img (Eq. chi2_img) when the
+system gives image-position uncertainties], and logL = -chi^2/2 (the Gaussian
+normalisation constant is dropped, as chi^2_LD has none).
 
 Dynamics chain (Sect. 3.2 and App. A): 1-D MGE of the App. C convergence and of
 each lens-light Sersic -> a black-hole Gaussian (sigma_BH, M_BH = f_BH * M_*,
@@ -159,12 +160,14 @@ def evaluate(th, sysd, want=False):
     c_pix = imaging.chi2_pix(img, sysd)
     c_dyn = kin.chi2_dyn(v, sysd)
     c_tmd = tdelay.chi2_tmd(dt, sysd)
-    logL = -0.5 * (c_pix + c_dyn + c_tmd)
+    # image positions (Eq. chi2_img) when the system gives their uncertainties
+    c_img = tdelay.chi2_img(th, sysd) if sysd.get("img_sig") is not None else 0.0
+    logL = -0.5 * (c_pix + c_dyn + c_tmd + c_img)
     if not np.isfinite(logL):
         out["status"] = ST_NONFINITE
         return out
-    out.update(logL=logL, chi2_pix=c_pix, chi2_dyn=c_dyn, chi2_tmd=c_tmd, image=img, vrms=v,
-               delays=dt, extra=extra)
+    out.update(logL=logL, chi2_pix=c_pix, chi2_dyn=c_dyn, chi2_tmd=c_tmd, chi2_img=c_img, image=img,
+               vrms=v, delays=dt, extra=extra)
     return out
 
 
