@@ -72,6 +72,9 @@ enum {
  *
  * Delays (Eqs. fermat potential, chi2_tmd): n_img observed image positions
  * (img_xy[n_img*2]) and n_img-1 delays relative to image 0 (dt_obs, dt_sig, days).
+ * Image positions (Eq. chi2_img): with img_sig[n_img] (arcsec) given, chi^2_img of the
+ * observed images against beta_hat mapped back to the image plane (Newton iterations on
+ * the lens equation from each observed image) joins the likelihood; NULL leaves it out.
  */
 typedef struct glad_system_desc {
   int nx, ny, ss;
@@ -102,6 +105,7 @@ typedef struct glad_system_desc {
   double bh_sigma, L_scale;
   int n_img;
   const double *img_xy, *dt_obs, *dt_sig;
+  const double *img_sig;           /* [n_img] or NULL: no image-position term */
   double z_d, z_s, omega_m, kappa_ext;
 } glad_system_desc;
 
@@ -117,9 +121,11 @@ glad_status glad_create(const glad_system_desc *sys, int n_sys, glad_ctx **out);
 void glad_destroy(glad_ctx *ctx);
 
 /* Batched joint log-likelihood, Eq. chi_general / Eq. Posterior_LD:
- *   logL[b] = -(chi2_pix + chi2_dyn + chi2_tmd)/2   for sample b in [0, B).
+ *   logL[b] = -(chi2_pix + chi2_dyn + chi2_tmd + chi2_img)/2   for sample b in [0, B)
+ * (chi2_img = 0 for systems without img_sig).
  * sys_id [dev, int32 B], theta [dev, float64 B*20], logL [dev, float64 B],
- * sample_status [dev, int32 B], terms [dev, float64 B*3] or NULL: the three chi^2 terms.
+ * sample_status [dev, int32 B], terms [dev, float64 B*4] or NULL: the four chi^2 terms in
+ * that order.
  * The per-sample workspace is allocated (cudaMalloc) the first time a batch of this
  * size is seen and kept by the context.
  * Errors: GLAD_EINVAL (B < 1, NULL output), GLAD_ENOMEM (workspace), GLAD_ECUDA. */

@@ -30,7 +30,7 @@ class SystemDesc(C.Structure):
         ("mass_rmin", C.c_double), ("mass_rmax", C.c_double),
         ("light_rmin", C.c_double), ("light_rmax", C.c_double),
         ("has_bh", C.c_int), ("bh_sigma", C.c_double), ("L_scale", C.c_double),
-        ("n_img", C.c_int), ("img_xy", _d), ("dt_obs", _d), ("dt_sig", _d),
+        ("n_img", C.c_int), ("img_xy", _d), ("dt_obs", _d), ("dt_sig", _d), ("img_sig", _d),
         ("z_d", C.c_double), ("z_s", C.c_double), ("omega_m", C.c_double), ("kappa_ext", C.c_double),
     ]
 

@@ -107,6 +107,8 @@ glad_status validate(const glad_system_desc &d, int idx) {
   REQ(d.mass_rmin > 0 && d.mass_rmax > d.mass_rmin && d.light_rmin > 0 &&
           d.light_rmax > d.light_rmin, "bad MGE ranges", idx);
   REQ(d.n_img >= 2 && d.img_xy && d.dt_obs && d.dt_sig, "need >= 2 images with delays", idx);
+  if (d.img_sig)
+    for (int i = 0; i < d.n_img; ++i) REQ(d.img_sig[i] > 0, "img_sig must be positive", idx);
   REQ(d.n_ll2 >= 0 && (d.n_ll2 == 0 || d.ll2), "bad extra lens lights", idx);
   REQ(d.n_sis >= 0 && (d.n_sis == 0 || d.sis), "bad SIS list", idx);
   REQ(d.z_s > d.z_d && d.z_d > 0 && d.omega_m > 0 && d.omega_m < 1, "bad cosmology", idx);
@@ -356,6 +358,7 @@ glad_status build_system(int idx, const glad_system_desc &d, SysHost &sh, SysDev
   sd.img_xy = upload(sh, d.img_xy, 2 * (size_t)d.n_img);
   sd.dt_obs = upload(sh, d.dt_obs, d.n_img - 1);
   sd.dt_sig = upload(sh, d.dt_sig, d.n_img - 1);
+  sd.img_sig = d.img_sig ? upload(sh, d.img_sig, d.n_img) : nullptr;
   sd.atx = (sd.nsx + 15) / 16;
   sd.n_atile = sd.atx * ((sd.nsy + 15) / 16);
   sd.n_img_tiles = (npix + LENS_THREADS - 1) / LENS_THREADS;
@@ -395,7 +398,7 @@ glad_status ws_ensure(glad_ctx *c, int B) {
             ws_alloc(w, w.d.Cj, b * c->max_mass_tot) && ws_alloc(w, w.d.e2, b * c->max_mass_tot) &&
             ws_alloc(w, w.d.I0f, b * c->max_light) && ws_alloc(w, w.d.tab, b * c->max_ent) &&
             ws_alloc(w, w.d.img, b * c->max_pix) && ws_alloc(w, w.d.binacc, b * c->max_bins * 2) &&
-            ws_alloc(w, w.d.terms, b * 3) && ws_alloc(w, w.d.status, b) &&
+            ws_alloc(w, w.d.terms, b * 4) && ws_alloc(w, w.d.status, b) &&
             ws_alloc(w, w.d.wl_off, b + 1) && ws_alloc(w, w.d.wl_counter, 1) &&
             ws_alloc(w, w.d.evals, 2);
   if (!ok) {
@@ -414,7 +417,7 @@ glad_status forward(glad_ctx *c, const int *sys_id, const double *theta, int B, 
   if (s != GLAD_OK) return s;
   cudaError_t e;
   c->ws.d.neg_mode = c->tune.neg_mode;
-  e = cudaMemsetAsync(c->ws.d.terms, 0, sizeof(double) * 3 * B, st);
+  e = cudaMemsetAsync(c->ws.d.terms, 0, sizeof(double) * 4 * B, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->ws.d.evals, 0, 2 * sizeof(unsigned long long), st);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(c->ws.d.binacc, 0, sizeof(double) * 2 * c->max_bins * (size_t)B, st);
@@ -440,7 +443,7 @@ glad_status full_path(glad_ctx *c, const int *sys_id, const double *theta, int B
   if (s != GLAD_OK) return s;
   cudaError_t e;
   c->ws.d.neg_mode = c->tune.neg_mode;
-  e = cudaMemsetAsync(c->ws.d.terms, 0, sizeof(double) * 3 * B, st);
+  e = cudaMemsetAsync(c->ws.d.terms, 0, sizeof(double) * 4 * B, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->ws.d.evals, 0, 2 * sizeof(unsigned long long), st);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(c->ws.d.binacc, 0, sizeof(double) * 2 * c->max_bins * (size_t)B, st);

@@ -64,6 +64,7 @@ struct SysDev {
   double dt_per_arcsec2_H0;                 // days per arcsec^2 times H0
   int n_img;
   const double *img_xy, *dt_obs, *dt_sig;
+  const double *img_sig;                    // [n_img] or null: no image-position term
   // tile counts
   int n_img_tiles, n_sky_tiles, n_tab_blocks;
   // gradient adjoint: table entries in ascending order of their x exponent p (fixed per

@@ -61,7 +61,7 @@ size_t carve(const glad_ctx *c, int B, unsigned char *base, WsDev *w) {
   w->tab = (float4 *)take(b * c->max_ent * sizeof(float4));
   w->img = (float *)take(b * c->max_pix * sizeof(float));
   w->binacc = (double *)take(b * c->max_bins * 2 * sizeof(double));
-  w->terms = (double *)take(b * 3 * sizeof(double));
+  w->terms = (double *)take(b * 4 * sizeof(double));
   w->status = (int *)take(b * sizeof(int));
   return off;
 }
@@ -98,7 +98,7 @@ extern "C" glad_status glad_loglike_static(glad_ctx *c, const int *sys_id, const
   const WsDev saved = c->ws.d;
   c->ws.d = w;
   // accumulators that the kernels add into start at zero on every call
-  e = cudaMemsetAsync(w.terms, 0, sizeof(double) * 3 * (size_t)B, st);
+  e = cudaMemsetAsync(w.terms, 0, sizeof(double) * 4 * (size_t)B, st);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(w.binacc, 0, sizeof(double) * 2 * c->max_bins * (size_t)B, st);
   if (e == cudaSuccess) e = launch_prep(c, sys_id, theta, B, st);

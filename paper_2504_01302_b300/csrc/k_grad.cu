@@ -947,14 +947,16 @@ __global__ void __launch_bounds__(256) k_grad_chain(const SysDev *__restrict__ s
     gsm[16] += a_glob[2] * bb * bb;
   }
   if (tid >= 32 && tid < 41) {
-    // time delays: -chi2_tmd/2 by duals through the FP64 lens model, one tangent per thread
-    // (theta 0..7 and H0 = theta 19)
+    // time delays and image positions: -(chi2_tmd + chi2_img)/2 by duals through the FP64
+    // lens model, one tangent per thread (theta 0..7 and H0 = theta 19)
     const int q = tid - 32;
     DT1 tt[8];
     for (int i = 0; i < 8; ++i) tt[i] = i == q ? DT1::var(th[i], 0) : DT1(th[i]);
     const DT1 h0 = q == 8 ? DT1::var(th[19], 0) : DT1(th[19]);
-    const DT1 chi = chi2_tmd_t<DT1>(tt, h0, S.img_xy, S.n_img, S.dt_obs, S.dt_sig,
-                                    S.dt_per_arcsec2_H0, S.sis, S.n_sis);
+    DT1 chi = chi2_tmd_t<DT1>(tt, h0, S.img_xy, S.n_img, S.dt_obs, S.dt_sig,
+                              S.dt_per_arcsec2_H0, S.sis, S.n_sis);
+    // image positions: lens parameters only
+    if (S.img_sig && q < 8) chi = chi + chi2_img_t<DT1>(tt, S.img_xy, S.n_img, S.img_sig, S.sis, S.n_sis);
     atomicAdd(&gsm[q < 8 ? q : 19], -0.5 * chi.d[0]);
   }
   __syncthreads();

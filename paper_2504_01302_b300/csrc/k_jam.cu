@@ -8,7 +8,7 @@
 //    operator W (bin sums of the PSF_kin-blurred maps, Eq. binned) into per-bin
 //    FP64 accumulators, so the maps are never stored.
 //  k_kin_finalize: v_rms,l = sqrt(num_l/den_l) (Eq. Vrms) and chi^2_dyn (Eq. chi2_dyn).
-//  k_combine: logL = -(chi2_pix + chi2_dyn + chi2_tmd)/2 (Eq. chi_general).
+//  k_combine: logL = -(chi2_pix + chi2_dyn + chi2_tmd + chi2_img)/2 (Eq. chi_general).
 #include <algorithm>
 
 #include "glad_internal.cuh"
@@ -330,7 +330,7 @@ __global__ void k_kin_finalize(const SysDev *__restrict__ sysv, const int *__res
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += red[w];
-    ws.terms[3 * (size_t)b + 1] = t;
+    ws.terms[4 * (size_t)b + 1] = t;
   }
 }
 
@@ -338,19 +338,21 @@ __global__ void k_combine(WsDev ws, int B, double *logL, int *status, double *te
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   int st = ws.status[b];
-  const double t0 = ws.terms[3 * b], t1 = ws.terms[3 * b + 1], t2 = ws.terms[3 * b + 2];
+  const double t0 = ws.terms[4 * b], t1 = ws.terms[4 * b + 1], t2 = ws.terms[4 * b + 2],
+               t3 = ws.terms[4 * b + 3];
   double L = -INFINITY;
   if (st == GLAD_SAMPLE_OK) {
-    const double s = t0 + t1 + t2;
+    const double s = t0 + t1 + t2 + t3;
     if (isfinite(s)) L = -0.5 * s;
     else st = GLAD_SAMPLE_NONFINITE;
   }
   logL[b] = L;
   status[b] = st;
   if (terms) {
-    terms[3 * b] = st == GLAD_SAMPLE_OK ? t0 : NAN;
-    terms[3 * b + 1] = st == GLAD_SAMPLE_OK ? t1 : NAN;
-    terms[3 * b + 2] = st == GLAD_SAMPLE_OK ? t2 : NAN;
+    terms[4 * b] = st == GLAD_SAMPLE_OK ? t0 : NAN;
+    terms[4 * b + 1] = st == GLAD_SAMPLE_OK ? t1 : NAN;
+    terms[4 * b + 2] = st == GLAD_SAMPLE_OK ? t2 : NAN;
+    terms[4 * b + 3] = st == GLAD_SAMPLE_OK ? t3 : NAN;
   }
 }
 

@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(CONV_TX *CONV_TY) k_conv(const SysDev *__restr
   if (tid < 32) {
     double v = tid < CONV_TX * CONV_TY / 32 ? red[tid] : 0.0;
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if (tid == 0 && v != 0.0) atomicAdd(&ws.terms[3 * (size_t)b], v);
+    if (tid == 0 && v != 0.0) atomicAdd(&ws.terms[4 * (size_t)b], v);
   }
 }
 
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(CONV_TX *CONV_TY) k_conv_r(const SysDev *__res
   if (tid < 32) {
     double v = tid < CONV_TX * CONV_TY / 32 ? red[tid] : 0.0;
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if (tid == 0 && v != 0.0) atomicAdd(&ws.terms[3 * (size_t)b], v);
+    if (tid == 0 && v != 0.0) atomicAdd(&ws.terms[4 * (size_t)b], v);
   }
 }
 

@@ -8,7 +8,8 @@
 //  * per-Gaussian JAM inputs nu_k, 1/(2 s_k^2 q_k^2), C_j = 4 pi G rho_j q_j s_j^2, e_j^2;
 //  * FP32 lensing parameter block (EPL series coefficients, shear, light);
 //  * time delays (Eqs. fermat potential, time delay between multiple images, chi2_tmd)
-//    with the magnification-weighted source estimate of Sect. 3.1.1.
+//    with the magnification-weighted source estimate of Sect. 3.1.1, and the
+//    image-position term (Eq. chi2_img) for systems that give image-position errors.
 // A second kernel expands the (tracer k, mass j, node g) JAM coefficient table.
 #include "glad_internal.cuh"
 #include "lensmath.cuh"
@@ -253,7 +254,11 @@ __global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
     // ---- time delays (FP64)
     const double chi2 = chi2_tmd_t<double>(th, th[19], S.img_xy, S.n_img, S.dt_obs, S.dt_sig,
                                            S.dt_per_arcsec2_H0, S.sis, S.n_sis);
-    ws.terms[3 * (size_t)b + 2] = chi2;
+    ws.terms[4 * (size_t)b + 2] = chi2;
+  }
+  if (tid == 32 && S.img_sig) {
+    // ---- image positions (FP64), beside thread 0's block
+    ws.terms[4 * (size_t)b + 3] = chi2_img_t<double>(th, S.img_xy, S.n_img, S.img_sig, S.sis, S.n_sis);
   }
 }
 

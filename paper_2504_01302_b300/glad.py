@@ -81,6 +81,8 @@ class GladContext:
         d.n_img, d.img_xy = img.shape[0], _ptr(img, C.c_double)
         d.dt_obs = _ptr(self._arr(s["dt_obs"], f64), C.c_double)
         d.dt_sig = _ptr(self._arr(s["dt_sig"], f64), C.c_double)
+        if s.get("img_sig") is not None:
+            d.img_sig = _ptr(self._arr(s["img_sig"], f64), C.c_double)
         d.z_d, d.z_s = float(s["z_d"]), float(s["z_s"])
         d.omega_m, d.kappa_ext = float(s["omega_m"]), float(s["kappa_ext"])
 
@@ -95,12 +97,13 @@ class GladContext:
         return theta, sys_id.contiguous(), B
 
     def loglike(self, theta, sys_id=None, terms=False):
-        """logL [B] (float64), status [B] (int32) and optionally the chi^2 terms [B, 3]."""
+        """logL [B] (float64), status [B] (int32) and optionally the chi^2 terms [B, 4]
+        (pixels, dynamics, delays, image positions)."""
         theta, sys_id, B = self._check_theta(theta, sys_id)
         dev = theta.device
         logL = torch.empty(B, dtype=torch.float64, device=dev)
         status = torch.empty(B, dtype=torch.int32, device=dev)
-        tr = torch.empty(B, 3, dtype=torch.float64, device=dev) if terms else None
+        tr = torch.empty(B, 4, dtype=torch.float64, device=dev) if terms else None
         rc = self.lib.glad_loglike(self.handle, _dptr(sys_id), _dptr(theta), B, _dptr(logL),
                                    _dptr(status), _dptr(tr) if terms else None, _stream())
         _lib.check(rc, "glad_loglike")
@@ -113,7 +116,7 @@ class GladContext:
         logL = torch.empty(B, dtype=torch.float64, device=dev)
         grad = torch.empty(B, NTHETA, dtype=torch.float64, device=dev)
         status = torch.empty(B, dtype=torch.int32, device=dev)
-        tr = torch.empty(B, 3, dtype=torch.float64, device=dev) if terms else None
+        tr = torch.empty(B, 4, dtype=torch.float64, device=dev) if terms else None
         rc = self.lib.glad_loglike_grad(self.handle, _dptr(sys_id), _dptr(theta), B, _dptr(logL),
                                         _dptr(grad), _dptr(status), _dptr(tr) if terms else None,
                                         _stream())

@@ -43,6 +43,7 @@ def _set(key, value):
     (_set("mge_P", 40), GLAD_EUNSUPPORTED, "mge_P >"),
     (_set("n_mge_light", [100, 40]), GLAD_EUNSUPPORTED, "tracer Gaussians >"),
     (_set("img_xy", np.zeros((9, 2))), GLAD_EUNSUPPORTED, "n_img >"),
+    (_set("img_sig", np.array([0.005, 0.0, 0.005, 0.005])), GLAD_EINVAL, "img_sig must be positive"),
 ])
 def test_create_rejects_invalid_descriptors(mutate, status, words):
     msg = _create(mutate)

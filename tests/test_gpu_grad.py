@@ -118,3 +118,13 @@ def test_w1_grad_full_batch_sampled(w1):
     for i in which:
         assert abs(g5[i] - ref[i]) <= 1e-3 * max(abs(ref[i]), 1e-3 * np.max(np.abs(ref))), \
             (synth.THETA_NAMES[i], g5[i], ref[i])
+
+
+def test_grad_with_image_position_term():
+    s = dict(systems.small_system(7))
+    s["img_sig"] = np.full(len(s["img_xy"]), 0.003)
+    ctx = _ctx([s])
+    th = systems.near_truth_thetas(1, seed=53)
+    _, g, st = ctx.loglike_grad(_th(th))
+    assert int(st.cpu().numpy()[0]) == 0
+    assert_grad_close(g.cpu().numpy()[0], model.grad_fd(th[0], s))

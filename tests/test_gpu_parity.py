@@ -207,6 +207,32 @@ def test_degenerate_parameters_gradient(small):
     assert_grad_close(g.cpu().numpy()[0], model.grad_fd(t, s))
 
 
+def test_image_position_term():
+    # a system that gives image-position errors: chi^2_img joins logL (fourth term)
+    s = dict(systems.small_system(7))
+    s["img_sig"] = np.full(len(s["img_xy"]), 0.003)
+    ctx = _ctx([s])
+    th = np.vstack([systems.near_truth_thetas(3, seed=23), synth.theta_truth(1)[None]])
+    logL, st, terms = ctx.loglike(_th(th), terms=True)
+    logL, terms = logL.cpu().numpy(), terms.cpu().numpy()
+    for b in range(len(th)):
+        ev = model.evaluate(th[b], s)
+        assert abs(terms[b, 3] - ev["chi2_img"]) <= 1e-9 * ev["chi2_img"] + 1e-12, (b, terms[b, 3], ev["chi2_img"])
+        assert abs(logL[b] - ev["logL"]) < 0.05, (b, logL[b], ev["logL"])
+    assert terms[3, 3] < 1e-12  # exact images at the truth
+    # the same system without img_sig: fourth term 0, logL higher by chi^2_img / 2
+    s0 = dict(s)
+    del s0["img_sig"]
+    l0, _, t0 = _ctx([s0]).loglike(_th(th), terms=True)
+    t0 = t0.cpu().numpy()
+    assert np.all(t0[:, 3] == 0.0)
+    # the other three terms agree (to the run-to-run order of float atomics) and each logL
+    # is -1/2 the sum of its terms
+    assert np.allclose(t0[:, :3], terms[:, :3], rtol=1e-6, atol=1e-4)
+    assert np.allclose(logL, -0.5 * terms.sum(axis=1), rtol=1e-12)
+    assert np.allclose(l0.cpu().numpy(), -0.5 * t0.sum(axis=1), rtol=1e-12)
+
+
 def test_batch_independence(small):
     # a sample's logL does not depend on which other samples share the launch
     s, ctx = small

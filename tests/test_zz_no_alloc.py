@@ -18,7 +18,7 @@ torch = pytest.importorskip("torch")
 def _call_static(ctx, sid, th, B):
     logL = torch.empty(B, dtype=torch.float64, device="cuda")
     st = torch.empty(B, dtype=torch.int32, device="cuda")
-    terms = torch.empty(B, 3, dtype=torch.float64, device="cuda")
+    terms = torch.empty(B, 4, dtype=torch.float64, device="cuda")
     P = lambda t: C.c_void_p(t.data_ptr())
     rc = ctx.lib.glad_loglike_static(ctx.handle, P(sid), P(th), B, P(logL), P(st), P(terms),
                                      C.c_void_p(torch.cuda.current_stream().cuda_stream))
@@ -44,7 +44,7 @@ def test_static_scratch_matches_allocating_entry_point_twice():
             assert abs(a[i] - b[i]) < systems.logl_tol(a[i]), (i, a[i], b[i])
         ts, ta = terms_s.cpu().numpy(), terms_a.cpu().numpy()
         for i in range(4):
-            for k in range(3):
+            for k in range(4):
                 assert abs(ts[i, k] - ta[i, k]) < systems.logl_tol(ta[i, k]), (i, k, ts[i], ta[i])
     ctx.close()
 
