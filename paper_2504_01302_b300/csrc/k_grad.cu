@@ -243,15 +243,21 @@ __global__ void __launch_bounds__(LENS_THREADS) k_image_grad(const SysDev *__res
 
 // ------------------------------------------------------------------ dynamics adjoint
 
+// Launch shape of the derivative pass: 2 points per thread, at least 4 CTAs per SM (64
+// registers); measured at B = 64 against 4 points / 3 CTAs (7.45 vs 8.23 ms) and 8 points /
+// 2 CTAs (9.81 ms).
+#define FG_PTS 2
+#define FG_MINB 4
+
 // JAM pair sum with dV/dX and dV/dY per point (X = x'^2, Y = y'^2), plus the same bin
 // scatter as the forward kernel so that v_rms and chi2_dyn come out of this pass too.
 // Same 2-D sky tiles and exact skipping of entries flushed to zero as the forward kernel
-// (4 points per thread).
-__global__ void __launch_bounds__(JAM_THREADS, 3) k_jam_fg(const SysDev *__restrict__ sysv,
+// (FG_PTS points per thread).
+__global__ void __launch_bounds__(JAM_THREADS, FG_MINB) k_jam_fg(const SysDev *__restrict__ sysv,
                                                         const int *__restrict__ sys_id, WsDev ws,
                                                         GradWs gw, int max_light, int max_ent,
                                                         int max_bins, int max_sub) {
-  constexpr int PTS = 4, NP = PTS / 2, TH = (JAM_THREADS / JAM_TW) * PTS;
+  constexpr int PTS = FG_PTS, NP = PTS / 2, TH = (JAM_THREADS / JAM_TW) * PTS;
   const int b = blockIdx.y;
   if (ws.status[b] != GLAD_SAMPLE_OK) return;
   const SysDev &S = sysv[sys_id[b]];
@@ -1012,7 +1018,7 @@ float *grad_resid_buffer(glad_ctx *c) { return c->gws ? c->gws->resid : nullptr;
 
 cudaError_t launch_jam_fg(glad_ctx *c, const int *sys_id, int B, cudaStream_t st) {
   int tiles = 0;
-  for (auto &sd : c->h_sysdev) tiles = std::max(tiles, jam_tiles(sd.nsx, sd.nsy, 4));
+  for (auto &sd : c->h_sysdev) tiles = std::max(tiles, jam_tiles(sd.nsx, sd.nsy, FG_PTS));
   dim3 grid(tiles, B);
   k_jam_fg<<<grid, JAM_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, *c->gws, c->max_light,
                                          c->max_ent, c->max_bins, c->max_sub);
