@@ -434,9 +434,10 @@ glad_status forward(glad_ctx *c, const int *sys_id, const double *theta, int B, 
 }
 
 // The full likelihood (and with `grad` its gradient): after k_prep the lensing branch
-// (k_image, k_conv and, for the gradient, its adjoint) runs on the context's second stream
-// while the dynamics branch (table, JAM pair sum, v_rms, dynamics adjoint) runs on the
-// caller's; an event joins them before the combination.
+// (k_image, k_conv and, for the gradient, its adjoint) runs on the context's low-priority
+// stream and the dynamics branch (table, JAM pair sum, v_rms, dynamics adjoint) on its
+// high-priority stream; events fork both from the caller's stream and join them back before
+// the combination.
 glad_status full_path(glad_ctx *c, const int *sys_id, const double *theta, int B, cudaStream_t st,
                       double *logL, int *sample_status, double *terms, double *grad) {
   glad_status s = ws_ensure(c, B);
@@ -450,23 +451,28 @@ glad_status full_path(glad_ctx *c, const int *sys_id, const double *theta, int B
   if (e == cudaSuccess && grad) e = grad_prepare(c, B, grad, st);
   if (e == cudaSuccess) e = GLAD_PROF(c, st, KID_PREP, launch_prep(c, sys_id, theta, B, st));
   // fork
+  cudaStream_t dy = c->dyn;
   if (e == cudaSuccess) e = cudaEventRecord(c->ev_fork, st);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(dy, c->ev_fork, 0);
+  // lensing, low priority
   if (e == cudaSuccess)
     e = GLAD_PROF(c, c->side, KID_IMAGE_CONV,
                   launch_lens(c, sys_id, B, nullptr, c->side, grad ? grad_resid_buffer(c) : nullptr));
   if (e == cudaSuccess && grad) e = launch_grad_lens(c, sys_id, B, grad, c->side);
   if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
-  // dynamics on the caller's stream
-  if (e == cudaSuccess) e = GLAD_PROF(c, st, KID_TABLE, launch_table(c, sys_id, B, st));
+  // dynamics, high priority
+  if (e == cudaSuccess) e = GLAD_PROF(c, dy, KID_TABLE, launch_table(c, sys_id, B, dy));
   if (e == cudaSuccess) {
-    if (grad) e = GLAD_PROF(c, st, KID_GRAD_JAM_FWD, launch_jam_fg(c, sys_id, B, st));
-    else e = GLAD_PROF(c, st, KID_JAM, launch_jam(c, sys_id, B, st));
+    if (grad) e = GLAD_PROF(c, dy, KID_GRAD_JAM_FWD, launch_jam_fg(c, sys_id, B, dy));
+    else e = GLAD_PROF(c, dy, KID_JAM, launch_jam(c, sys_id, B, dy));
   }
-  if (e == cudaSuccess) e = GLAD_PROF(c, st, KID_KIN, launch_kin_finalize(c, sys_id, B, nullptr, st));
-  if (e == cudaSuccess && grad) e = launch_grad_dyn(c, sys_id, theta, B, grad, st);
+  if (e == cudaSuccess) e = GLAD_PROF(c, dy, KID_KIN, launch_kin_finalize(c, sys_id, B, nullptr, dy));
+  if (e == cudaSuccess && grad) e = launch_grad_dyn(c, sys_id, theta, B, grad, dy);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev_join_dyn, dy);
   // join
   if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->ev_join, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->ev_join_dyn, 0);
   if (e == cudaSuccess && grad) e = launch_grad_finish(c, B, grad, st);
   if (e == cudaSuccess)
     e = GLAD_PROF(c, st, KID_COMBINE, launch_combine(c, B, logL, sample_status, terms, st));
@@ -608,9 +614,13 @@ glad_status glad_create(const glad_system_desc *sys, int n_sys, glad_ctx **out) 
   cudaMemcpy(c->d_one_sys, ids.data(), sizeof(int) * n_sys, cudaMemcpyHostToDevice);
   set_conv_smem_limit();
   set_grad_smem_limit();
-  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&c->dyn, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join_dyn, cudaEventDisableTiming) != cudaSuccess) {
     glad_destroy(c);
     return fail(GLAD_ECUDA, "glad_create: stream or event creation failed");
   }
@@ -640,7 +650,9 @@ void glad_destroy(glad_ctx *c) {
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_join_dyn) cudaEventDestroy(c->ev_join_dyn);
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->dyn) cudaStreamDestroy(c->dyn);
   delete c;
 }
 

@@ -150,10 +150,12 @@ struct glad_ctx {
     int adj_ept = 4;      // table entries per thread in the JAM adjoint
   } tune;
   int *d_one_sys = nullptr;      // scratch sys id for single-sample calls
-  // the lensing branch runs on a second stream, forked from and joined back into the
-  // caller's stream by events (capturable into a CUDA graph)
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // after k_prep the dynamics branch runs on a high-priority stream and the lensing branch
+  // on a low-priority one, both forked from and joined back into the caller's stream by
+  // events (capturable into a CUDA graph): the lensing work fills the dynamics kernels'
+  // tails without delaying the next kernel of the dynamics chain
+  cudaStream_t side = nullptr, dyn = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join_dyn = nullptr;
   // kernel timing (glad_profile)
   int prof = 0;
   struct Rec {
