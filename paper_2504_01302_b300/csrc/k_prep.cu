@@ -85,34 +85,32 @@ __global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
   const int nL = S.n_light, nM = S.n_mass, nMt = S.n_mass_tot;
   const int P2 = 2 * S.mge_P + 1;
 
-  // ---- 1-D MGE (Euler inversion), FP64
+  // ---- 1-D MGE (Euler inversion), FP64: the (Gaussian, Euler node) terms are spread over
+  // the block and summed per Gaussian in shared memory
+  const double coef_m = (3.0 - g) / (1.0 + q) * pow(tE, g - 1.0);
   for (int k = tid; k < nL + nM; k += blockDim.x) {
-    double f = 0.0;
+    sh_A[k] = 0.0;
+    sh_q[k] = k < nL ? S.qp_light[k] : q;
+  }
+  __syncthreads();
+  for (int it = tid; it < (nL + nM) * P2; it += blockDim.x) {
+    const int k = it / P2, m = it - k * P2;
+    const double2 ch = S.chi[m];
+    double v;
     if (k < nL) {
       const int c = S.lcomp_of[k];
       const double Ie = c == 0 ? th[13] : S.lcomp[4 * c];
       const double Re = c == 0 ? th[14] : S.lcomp[4 * c + 1];
       const double n = S.lcomp[4 * c + 2];
-      const double bn = sersic_bn_d(n);
       const double sg = S.sig_light[k];
-      for (int m = 0; m < P2; ++m) {
-        const double2 ch = S.chi[m];
-        f += S.eta[m] * sersic_re({sg * ch.x, sg * ch.y}, Ie, Re, n, bn);
-      }
-      sh_A[k] = S.mw_light[k] * f;
-      sh_q[k] = S.qp_light[k];
+      v = S.mw_light[k] * S.eta[m] * sersic_re({sg * ch.x, sg * ch.y}, Ie, Re, n, sersic_bn_d(n));
     } else {
-      const int j = k - nL;
       // (3-g)/2 b^(g-1) with b = (2/(1+q))^(1/(g-1)) theta_E
-      const double coef = (3.0 - g) / (1.0 + q) * pow(tE, g - 1.0);
-      const double sg = S.sig_mass[j];
-      for (int m = 0; m < P2; ++m) {
-        const double2 ch = S.chi[m];
-        f += S.eta[m] * epl_kappa_re({sg * ch.x, sg * ch.y}, coef, g, S.r_soft * S.r_soft);
-      }
-      sh_A[k] = S.mw_mass[j] * f;
-      sh_q[k] = q;
+      const double sg = S.sig_mass[k - nL];
+      v = S.mw_mass[k - nL] * S.eta[m] *
+          epl_kappa_re({sg * ch.x, sg * ch.y}, coef_m, g, S.r_soft * S.r_soft);
     }
+    atomicAdd(&sh_A[k], v);
   }
   if (tid == 0) sh_flag = 0;
   __syncthreads();
@@ -180,6 +178,30 @@ __global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
     return;
   }
 
+  // ---- lens model at the observed images (FP64), one image per thread of the second warp
+  __shared__ double im_ax[GLAD_MAX_IMG], im_ay[GLAD_MAX_IMG], im_w[GLAD_MAX_IMG], im_psi[GLAD_MAX_IMG];
+  if (tid >= 32 && tid < 32 + S.n_img) {
+    const int i = tid - 32;
+    LensEvalT<double> e = lens_eval_t<double>(S.img_xy[2 * i], S.img_xy[2 * i + 1], th, S.sis, S.n_sis);
+    im_ax[i] = e.ax;
+    im_ay[i] = e.ay;
+    im_psi[i] = e.psi;
+    im_w[i] = 1.0 / fabs((1.0 - e.a11) * (1.0 - e.a22) - e.a12 * e.a21);
+  }
+  // ---- EPL series coefficients of the FP32 lensing block, one per thread
+  const double tq = g - 1.0;
+  const double fq = (1.0 - q) / (1.0 + q);
+  int nt = 0;
+  if (fq > 0.0) nt = (int)ceil(log(1e-9) / log(fq));
+  if (nt > GLAD_MAX_TM) nt = GLAD_MAX_TM;
+  LensP &L = ws.lp[b];
+  for (int n = 1 + tid; n <= nt; n += blockDim.x) {
+    const double num = 2.0 * n - (2.0 - tq), den = 2.0 * n + (2.0 - tq);
+    L.rho[n - 1] = (float)(-fq * num / den);
+    L.drho_t[n - 1] = (float)(-fq * 4.0 * n / (den * den));
+    L.drho_q[n - 1] = (float)(2.0 * num / (den * (1.0 + q) * (1.0 + q)));
+  }
+  __syncthreads();
   if (tid == 0) {
     ws.status[b] = GLAD_SAMPLE_OK;
     // ---- dynamics scalars
@@ -192,35 +214,21 @@ __global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
     sincos(th[3], &dp.sphi, &dp.cphi);
     ws.dp[b] = dp;
     // ---- FP32 lensing block
-    LensP &L = ws.lp[b];
-    const double t = g - 1.0;
-    const double bb = pow(2.0 / (1.0 + q), 1.0 / t) * tE;
+    const double bb = pow(2.0 / (1.0 + q), 1.0 / tq) * tE;
     const double bt = q * bb;
-    const double f = (1.0 - q) / (1.0 + q);
-    int nt = 0;
-    if (f > 0.0) nt = (int)ceil(log(1e-9) / log(f));
-    if (nt > GLAD_MAX_TM) nt = GLAD_MAX_TM;
     L.xc = (float)th[4];
     L.yc = (float)th[5];
     L.cphi = (float)dp.cphi;
     L.sphi = (float)dp.sphi;
     L.q = (float)q;
-    L.t = (float)t;
-    L.pref = (float)(2.0 * bt / (1.0 + q) * pow(bt, t - 1.0));
+    L.t = (float)tq;
+    // ln pref = ln 2 + t ln b_TM - ln(1+q), b_TM = q (2/(1+q))^(1/t) theta_E
+    const double pref = 2.0 * bt / (1.0 + q) * pow(bt, tq - 1.0);
+    L.pref = (float)pref;
     L.nterms = nt;
-    for (int n = 1; n <= nt; ++n) {
-      const double num = 2.0 * n - (2.0 - t), den = 2.0 * n + (2.0 - t);
-      L.rho[n - 1] = (float)(-f * num / den);
-      L.drho_t[n - 1] = (float)(-f * 4.0 * n / (den * den));
-      L.drho_q[n - 1] = (float)(2.0 * num / (den * (1.0 + q) * (1.0 + q)));
-    }
-    {
-      // ln pref = ln 2 + t ln b_TM - ln(1+q), b_TM = q (2/(1+q))^(1/t) theta_E
-      const double pref = 2.0 * bt / (1.0 + q) * pow(bt, t - 1.0);
-      L.pref_d[0] = (float)(pref * t / tE);
-      L.pref_d[1] = (float)(pref * (log(bt) - log(2.0 / (1.0 + q)) / t));
-      L.pref_d[2] = (float)(pref * (t / q - 2.0 / (1.0 + q)));
-    }
+    L.pref_d[0] = (float)(pref * tq / tE);
+    L.pref_d[1] = (float)(pref * (log(bt) - log(2.0 / (1.0 + q)) / tq));
+    L.pref_d[2] = (float)(pref * (tq / q - 2.0 / (1.0 + q)));
     double s2p, c2p;
     sincos(2.0 * th[7], &s2p, &c2p);
     L.g1 = (float)(th[6] * c2p);
@@ -251,13 +259,33 @@ __global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
       L.ll_qi2[c] = (float)(1.0 / (ql * ql));
     }
     L.valid = 1;
-    // ---- time delays (FP64)
-    const double chi2 = chi2_tmd_t<double>(th, th[19], S.img_xy, S.n_img, S.dt_obs, S.dt_sig,
-                                           S.dt_per_arcsec2_H0, S.sis, S.n_sis);
+  }
+  if (tid == 32) {
+    // ---- time delays (FP64): beta_hat, Fermat potentials, chi^2_tmd from the images
+    double wsum = 0.0, bhx = 0.0, bhy = 0.0;
+    for (int i = 0; i < S.n_img; ++i) {
+      wsum += im_w[i];
+      bhx += im_w[i] * (S.img_xy[2 * i] - im_ax[i]);
+      bhy += im_w[i] * (S.img_xy[2 * i + 1] - im_ay[i]);
+    }
+    bhx /= wsum;
+    bhy /= wsum;
+    const double kdt = S.dt_per_arcsec2_H0 / th[19];
+    double phi0 = 0.0, chi2 = 0.0;
+    for (int i = 0; i < S.n_img; ++i) {
+      const double x = S.img_xy[2 * i], y = S.img_xy[2 * i + 1];
+      const double ph = 0.5 * ((x - bhx) * (x - bhx) + (y - bhy) * (y - bhy)) - im_psi[i];
+      if (i == 0) {
+        phi0 = ph;
+      } else {
+        const double r = (S.dt_obs[i - 1] - kdt * (ph - phi0)) / S.dt_sig[i - 1];
+        chi2 += r * r;
+      }
+    }
     ws.terms[4 * (size_t)b + 2] = chi2;
   }
-  if (tid == 32 && S.img_sig) {
-    // ---- image positions (FP64), beside thread 0's block
+  if (tid == 64 && S.img_sig) {
+    // ---- image positions (FP64), beside the delays
     ws.terms[4 * (size_t)b + 3] = chi2_img_t<double>(th, S.img_xy, S.n_img, S.img_sig, S.sis, S.n_sis);
   }
 }
