@@ -326,6 +326,19 @@ glad_status build_system(int idx, const glad_system_desc &d, SysHost &sh, SysDev
           const int e = (k * nMt + j) * G + g;
           pe[e] = 1.0 / (2.0 * sig_l[k] * sig_l[k]) + gu[e] * gu[e] / (2.0 * sig_m[j] * sig_m[j]);
         }
+    // per-entry constants of the table formula: a = u^2/(2 s_j^2), p = 1/(2 s_k^2) + a, u^2
+    std::vector<double> ga(n_ent), gp(n_ent), gu2(n_ent);
+    for (int k = 0; k < nL; ++k)
+      for (int j = 0; j < nMt; ++j)
+        for (int g = 0; g < G; ++g) {
+          const int e = (k * nMt + j) * G + g;
+          gu2[e] = gu[e] * gu[e];
+          ga[e] = gu2[e] / (2.0 * sig_m[j] * sig_m[j]);
+          gp[e] = 1.0 / (2.0 * sig_l[k] * sig_l[k]) + ga[e];
+        }
+    sd.gl_a = upload(sh, ga.data(), n_ent);
+    sd.gl_p = upload(sh, gp.data(), n_ent);
+    sd.gl_u2 = upload(sh, gu2.data(), n_ent);
     std::vector<int> perm(n_ent);
     for (int e = 0; e < n_ent; ++e) perm[e] = e;
     std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return pe[a] < pe[b]; });

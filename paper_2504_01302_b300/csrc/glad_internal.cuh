@@ -57,6 +57,7 @@ struct SysDev {
   // JAM pair table geometry
   int n_gl, n_ent;                          // n_ent = n_light * n_mass_tot * n_gl
   const double *gl_u, *gl_wu;               // [n_ent]: u node, weight * du/dt
+  const double *gl_a, *gl_p, *gl_u2;        // [n_ent]: u^2/(2 s_j^2), 1/(2 s_k^2) + a, u^2
   const float *sb_cx, *sb_cy;               // [n_light]: log2(e)/(2 s^2), log2(e)/(2 s^2 q'^2)
   int has_bh;
   double bh_sigma, L_scale;

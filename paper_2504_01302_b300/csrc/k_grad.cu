@@ -764,7 +764,6 @@ __global__ void __launch_bounds__(256) k_table_adj(const SysDev *__restrict__ sy
     j = kj % nMt;
     k = kj / nMt;
     const D5 s2 = D5::var(dp.s2, 2), c2 = D5::var(dp.c2, 3), bb = D5::var(dp.b, 4);
-    const double sj = S.sig_mass[j], sk = S.sig_light[k];
     const D5 e2 = D5::var(ws.e2[bm + j], 1);
     const D5 c0 = D5::var(ws.c0[bl + k], 0);
     const double nc = ws.nu0[bl + k] * ws.Cj[bm + j];
@@ -772,10 +771,9 @@ __global__ void __launch_bounds__(256) k_table_adj(const SysDev *__restrict__ sy
       const int e = kj * S.n_gl + g;
       const double *ga = gw.entadj + ((size_t)b * max_ent + e) * 3;
       const double GQ0 = ga[0], GQ1 = ga[1], Gay = ga[2];
-      const double u = S.gl_u[e], wu = S.gl_wu[e];
-      const double a = u * u / (2.0 * sj * sj);
-      const D5 h = 1.0 - e2 * (u * u);
-      const double p = 1.0 / (2.0 * sk * sk) + a;
+      const double wu = S.gl_wu[e];
+      const double a = S.gl_a[e], p = S.gl_p[e];  // u^2/(2 s_j^2), 1/(2 s_k^2) + a
+      const D5 h = 1.0 - e2 * S.gl_u2[e];
       const D5 c = c0 + a / h;
       const D5 al = p * s2 + c * c2;
       const D5 sh = dsqrt(h);

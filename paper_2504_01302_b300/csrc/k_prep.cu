@@ -304,22 +304,22 @@ __global__ void __launch_bounds__(TAB_THREADS) k_table(const SysDev *__restrict_
   const int j = kj % S.n_mass_tot;
   const int k = kj / S.n_mass_tot;
   const DynP dp = ws.dp[b];
-  const double u = S.gl_u[e], wu = S.gl_wu[e];
-  const double sj = S.sig_mass[j], sk = S.sig_light[k];
+  // a = u^2/(2 s_j^2), p = 1/(2 s_k^2) + a and u^2 are per-entry constants of the system
+  const double a = S.gl_a[e], p = S.gl_p[e], wu = S.gl_wu[e];
   const double e2 = ws.e2[(size_t)b * max_mass + j];
-  const double a = u * u / (2.0 * sj * sj);
-  const double h = 1.0 - e2 * u * u;
-  const double p = 1.0 / (2.0 * sk * sk) + a;
-  const double c = ws.c0[(size_t)b * max_light + k] + a / h;
+  const double h = 1.0 - e2 * S.gl_u2[e];
+  const double ih = 1.0 / h, rsh = rsqrt(h);
+  const double c = ws.c0[(size_t)b * max_light + k] + a * ih;
+  const double ic = 1.0 / c;
   const double al = p * dp.s2 + c * dp.c2;
-  const double sh = sqrt(h);
-  const double A = a / (h * sh * c);
+  const double ial = 1.0 / al;
+  const double A = a * ih * rsh * ic;  // a / (h^(3/2) c)
   const double P0 = A * (dp.b * dp.s2 + dp.c2);
-  const double P1 = dp.s2 * (2.0 * a / sh - 2.0 * p * dp.b * A);
+  const double P1 = dp.s2 * (2.0 * a * rsh - 2.0 * p * dp.b * A);
   const double T = ws.nu0[(size_t)b * max_light + k] * ws.Cj[(size_t)b * max_mass + j] * wu *
-                   sqrt(PI_D / al);
+                   sqrt(PI_D * ial);
   ws.tab[(size_t)b * max_ent + e] =
-      make_float4((float)(-p * LOG2E_D), (float)(-p * c / al * LOG2E_D), (float)(T * P0),
+      make_float4((float)(-p * LOG2E_D), (float)(-p * c * ial * LOG2E_D), (float)(T * P0),
                   (float)(T * P1));
 }
 
