@@ -853,25 +853,57 @@ __global__ void __launch_bounds__(256) k_grad_chain(const SysDev *__restrict__ s
   const D9 si = dsin(Di), ci = dcos(Di);
   const D9 S2 = si * si, C2 = ci * ci;
   const int P2 = 2 * S.mge_P + 1;
+  // Euler-inversion sums of each Gaussian and of its partial (R_e for the first lens light,
+  // gamma' for the mass), the (Gaussian, node) terms spread over the block
+  __shared__ double mf[GLAD_MAX_LIGHT + GLAD_MAX_MASS][2];
+  for (int k = tid; k < nL + nM; k += blockDim.x) mf[k][0] = mf[k][1] = 0.0;
+  __syncthreads();
+  {
+    const double coef = (3.0 - g) / (1.0 + q) * pow(tE, g - 1.0);
+    const double rs2 = S.r_soft * S.r_soft;
+    for (int it = tid; it < (nL + nM) * P2; it += blockDim.x) {
+      const int k = it / P2, m = it - k * P2;
+      const double2 ch = S.chi[m];
+      double f, f2;
+      if (k < nL) {
+        const int cc = S.lcomp_of[k];
+        const double Ie = cc == 0 ? th[13] : S.lcomp[4 * cc];
+        const double Re = cc == 0 ? th[14] : S.lcomp[4 * cc + 1];
+        const double n = S.lcomp[4 * cc + 2];
+        const double bn = sersic_bn_d(n);
+        const double sg = S.sig_light[k];
+        const cplx z = {sg * ch.x, sg * ch.y};
+        const cplx l = clog_({z.r / Re, z.i / Re});
+        const cplx w = cexp_({l.r / n, l.i / n});
+        const cplx F = cexp_({-bn * (w.r - 1.0), -bn * w.i});
+        // dF/dRe = F bn w / (n Re)
+        const cplx Fw = cmul(F, w);
+        f = S.eta[m] * Ie * F.r;
+        f2 = S.eta[m] * Ie * Fw.r * bn / (n * Re);
+      } else {
+        const double sg = S.sig_mass[k - nL];
+        const cplx z = {sg * ch.x, sg * ch.y};
+        cplx z2 = cmul(z, z);
+        z2.r += rs2;
+        const cplx lz = clog_(z2);
+        const double ex = -0.5 * (g - 1.0);
+        const cplx F = cexp_({ex * lz.r, ex * lz.i});
+        // dF/dg = F (-1/(3-g) + ln tE - log(z^2 + rs^2)/2)
+        const cplx fac = {-1.0 / (3.0 - g) + log(tE) - 0.5 * lz.r, -0.5 * lz.i};
+        const cplx Fg = cmul(F, fac);
+        f = S.eta[m] * coef * F.r;
+        f2 = S.eta[m] * coef * Fg.r;
+      }
+      atomicAdd(&mf[k][0], f);
+      atomicAdd(&mf[k][1], f2);
+    }
+  }
+  __syncthreads();
   for (int k = tid; k < nL; k += blockDim.x) {
     const int cc = S.lcomp_of[k];
     const double Ie = cc == 0 ? th[13] : S.lcomp[4 * cc];
-    const double Re = cc == 0 ? th[14] : S.lcomp[4 * cc + 1];
-    const double n = S.lcomp[4 * cc + 2];
-    const double bn = sersic_bn_d(n);
     const double sg = S.sig_light[k];
-    double f = 0.0, fRe = 0.0;
-    for (int m = 0; m < P2; ++m) {
-      const double2 ch = S.chi[m];
-      const cplx z = {sg * ch.x, sg * ch.y};
-      const cplx l = clog_({z.r / Re, z.i / Re});
-      const cplx w = cexp_({l.r / n, l.i / n});
-      const cplx F = cexp_({-bn * (w.r - 1.0), -bn * w.i});
-      // dF/dRe = F bn w / (n Re)
-      const cplx Fw = cmul(F, w);
-      f += S.eta[m] * Ie * F.r;
-      fRe += S.eta[m] * Ie * Fw.r * bn / (n * Re);
-    }
+    const double f = mf[k][0], fRe = mf[k][1];
     D9 A(S.mw_light[k] * f);
     if (cc == 0) {
       A.d[3] = S.mw_light[k] * f / Ie;
@@ -893,23 +925,7 @@ __global__ void __launch_bounds__(256) k_grad_chain(const SysDev *__restrict__ s
   }
   for (int j = tid; j < nM; j += blockDim.x) {
     const double sg = S.sig_mass[j];
-    const double coef = (3.0 - g) / (1.0 + q) * pow(tE, g - 1.0);
-    const double rs2 = S.r_soft * S.r_soft;
-    double f = 0.0, fg = 0.0;
-    for (int m = 0; m < P2; ++m) {
-      const double2 ch = S.chi[m];
-      const cplx z = {sg * ch.x, sg * ch.y};
-      cplx z2 = cmul(z, z);
-      z2.r += rs2;
-      const cplx lz = clog_(z2);
-      const double ex = -0.5 * (g - 1.0);
-      const cplx F = cexp_({ex * lz.r, ex * lz.i});
-      // dF/dg = F (-1/(3-g) + ln tE - log(z^2 + rs^2)/2)
-      const cplx fac = {-1.0 / (3.0 - g) + log(tE) - 0.5 * lz.r, -0.5 * lz.i};
-      const cplx Fg = cmul(F, fac);
-      f += S.eta[m] * coef * F.r;
-      fg += S.eta[m] * coef * Fg.r;
-    }
+    const double f = mf[nL + j][0], fg = mf[nL + j][1];
     D9 A(S.mw_mass[j] * f);
     A.d[0] = A.v * (g - 1.0) / tE;
     A.d[1] = S.mw_mass[j] * fg;
