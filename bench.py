@@ -97,11 +97,43 @@ def workload_name(w, grad, B):
                 "JAM 20+2x10+BH, 60^2 sky x4ss, GL32, 50 bins, 4 images",
              3: "8 uneven systems (64..256 px, ss 1-3, 8-30 Gaussians, 20-120 bins, GL 24-64)",
              4: "IFU-scale: 400^2 x3ss, 31^2 PSF, EPL+shear+2 SIS, JAM 40+2x20+BH, 128^2 sky x4, "
-                "GL64, 400 bins"}
+                "GL64, 400 bins",
+             5: "RXJ1131-scale with the spherically aligned Jeans model (Eqs. J1/J2): 200^2 x2ss, "
+                "21^2 PSF, EPL+shear+SIS, JAM 20+2x10+BH, polar grid 96x8, 64 LOS nodes, "
+                "60^2 sky x4ss, 50 bins"}
     n = names.get(w, str(w)) + f"; B={B}"
     if grad:
         n += " (forward + gradient)"
     return n
+
+
+SPH_NODES = 64  # characteristic nodes per polar grid point of the spherically aligned model
+
+
+def sph_exp2_counts(systems, sid_np, B, kernel):
+    """Algorithmic work of one launch of `kernel` over the batch: for the pair sum and its
+    passes, (sky sub-sample, table entry) integrand evaluations (one ex2 each); for the
+    spherically aligned model, its integrand exponentials: per polar grid point
+    64 x (mass Gaussians x n_gl + tracer Gaussians) along the characteristic plus the same
+    at the point itself; per sky sub-sample n_los x (tracer Gaussians + 1) along the line of
+    sight plus the tracer surface brightness."""
+    n = 0
+    for b in range(B):
+        s = systems[sid_np[b]]
+        nl = sum(s["n_mge_light"])
+        nm = s["n_mge_mass"] + (1 if s["has_bh"] else 0)
+        nsub = (s["kx"] * s["kss"]) * (s["ky"] * s["kss"])
+        if kernel == "k_sph_coef+k_sph_grid":
+            n += s["sph_nr"] * s["sph_nw"] * (SPH_NODES + 1) * (nm * s["n_gl"] + nl)
+        elif kernel == "k_sph_los":
+            n += nsub * (s["sph_nlos"] * (nl + 1) + nl)
+        else:
+            n += nsub * nl * nm * s["n_gl"]
+    if kernel == "k_sph_coef+k_sph_grid":
+        return n, f"{n} exponentials per launch (grid points x 65 x (mass x u nodes + tracer))"
+    if kernel == "k_sph_los":
+        return n, f"{n} exponentials per launch (sky sub-samples x (n_los x (tracer + 1) + tracer))"
+    return n, f"{n} JAM integrand evaluations per launch (sky sub-samples x table entries)"
 
 
 def bench_systems(w):
@@ -424,6 +456,7 @@ def main():
 
     prof_steps = min(args.steps, 3) if use_graph else args.steps
     extra = kl[names_idx("k_image+k_conv", lib, nk)] + kl[names_idx("k_grad_lens", lib, nk)] + \
+        kl[names_idx("k_sph_coef+k_sph_grid", lib, nk)] + \
         (kl[names_idx("k_jam", lib, nk)] if tuning["jam_pts"] >= 10000 else 0)
     launches_per_step = (int(sum(kl[i] for i in range(nk))) + int(extra)) // max(prof_steps, 1)
     if args.grad:
@@ -438,19 +471,16 @@ def main():
     # against the pipe that bounds that kernel
     names = [lib.glad_kernel_name(i).decode() for i in range(nk)]
     per_kernel = {names[i]: kms[i] / max(kl[i], 1) for i in range(nk) if kl[i]}
-    jam_name = max((n for n in ("k_jam", "k_jam_fwd_grad", "k_jam_adjoint") if n in per_kernel),
+    jam_name = max((n for n in ("k_jam", "k_jam_fwd_grad", "k_jam_adjoint", "k_sph_coef+k_sph_grid",
+                                "k_sph_los") if n in per_kernel),
                    key=lambda n: per_kernel[n])
     jam_ms = per_kernel[jam_name]
-    evals = 0
-    for b in range(B):
-        s = systems[sid_np[b]]
-        nl = sum(s["n_mge_light"])
-        nm = s["n_mge_mass"] + (1 if s["has_bh"] else 0)
-        evals += (s["kx"] * s["kss"]) * (s["ky"] * s["kss"]) * nl * nm * s["n_gl"]
+    evals, units = sph_exp2_counts(systems, sid_np, B, jam_name)
+    n_exec["k_sph_coef+k_sph_grid"] = n_exec["k_sph_los"] = evals  # no terms are skipped there
     achieved = evals / (jam_ms / 1000.0) / 1e9
     clocks = clk.summary()
     sm_max = clocks["sm_max_mhz"] or 2032.0
-    if jam_name == "k_jam":
+    if jam_name in ("k_jam", "k_sph_coef+k_sph_grid", "k_sph_los"):
         # one ex2 per evaluation; the 4 FMA-pipe operations per evaluation allow the same rate
         peak = N_SM * MUFU_EX2_PER_CLK_SM * sm_max * 1e6 / 1e9
         peak_unit = "Gexp2/s"
@@ -480,8 +510,7 @@ def main():
                      "traffic": ncu_traffic(jam_name, w, args.grad, B),
                      "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
                                       "small-batch capture, scaled by samples to this batch",
-                     "algorithmic_units": f"{evals} JAM integrand evaluations per launch "
-                                          f"(sky sub-samples x table entries)",
+                     "algorithmic_units": units,
                      "executed_evaluations": n_exec[jam_name],
                      "executed_frac": n_exec[jam_name] / (jam_ms / 1000.0) / 1e9 / peak,
                      "peak_basis": peak_basis},

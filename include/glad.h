@@ -75,6 +75,16 @@ enum {
  * Image positions (Eq. chi2_img): with img_sig[n_img] (arcsec) given, chi^2_img of the
  * observed images against beta_hat mapped back to the image plane (Newton iterations on
  * the lens equation from each observed image) joins the likelihood; NULL leaves it out.
+ *
+ * Jeans model (Sect. 3.2): jam_align 0 takes the cylindrically aligned velocity ellipsoid
+ * (constant beta_z, the pair form over (tracer, mass, u node) terms); jam_align 1 the
+ * spherically aligned one of Eqs. J1/J2 (constant beta = 1 - v_theta^2/v_r^2), solved
+ * along the characteristics of J1/J2 on a polar grid of sph_nr radii (log-spaced from a
+ * quarter sky sub-sample to 9 x the largest tracer sigma) x sph_nw values of sin^2 theta,
+ * and projected with sph_nlos nodes per line of sight; 0 selects the defaults 96, 8, 64.
+ * Limits: sph_nr * sph_nw <= 4096 and (mass Gaussians incl. the black hole) x n_gl <= 4096
+ * (GLAD_EUNSUPPORTED beyond).  glad_loglike_grad (and glad_autotune with_grad) return
+ * GLAD_EUNSUPPORTED for a context that holds a spherically aligned system.
  */
 typedef struct glad_system_desc {
   int nx, ny, ss;
@@ -107,6 +117,8 @@ typedef struct glad_system_desc {
   const double *img_xy, *dt_obs, *dt_sig;
   const double *img_sig;           /* [n_img] or NULL: no image-position term */
   double z_d, z_s, omega_m, kappa_ext;
+  int jam_align;                   /* 0 cylindrically, 1 spherically aligned Jeans model */
+  int sph_nr, sph_nw, sph_nlos;    /* rule of the spherically aligned model (0: defaults) */
 } glad_system_desc;
 
 typedef struct glad_ctx glad_ctx;

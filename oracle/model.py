@@ -9,8 +9,10 @@ normalisation constant is dropped, as chi^2_LD has none).
 Dynamics chain (Sect. 3.2 and App. A): 1-D MGE of the App. C convergence and of
 each lens-light Sersic -> a black-hole Gaussian (sigma_BH, M_BH = f_BH * M_*,
 M_* = Upsilon * L_tot, L_tot the total light of the tracer MGE in
-convergence units via L_scale) -> deprojection -> pair-form JAM on the
-sub-sampled sky grid -> PSF_kin, binning, v_rms.
+convergence units via L_scale) -> deprojection -> JAM on the sub-sampled sky grid
+(the cylindrically aligned pair form, or, for systems with jam_align = 1, the
+spherically aligned solution of Eqs. J1/J2 by the discrete rule of jam_sph) ->
+PSF_kin, binning, v_rms.
 
 An invalid sample (parameter outside its domain, impossible deprojection
 cos^2 i >= q'^2 (App. A), or a non-positive deprojected density at the probe
@@ -21,7 +23,7 @@ import math
 import numpy as np
 
 from paper_2504_01302_b300 import synth
-from . import cosmo, imaging, jam, kin, lens, mge, tdelay
+from . import cosmo, imaging, jam, jam_sph, kin, lens, mge, tdelay
 
 IDX = synth.IDX
 
@@ -102,8 +104,30 @@ def dynamics_setup(th, sysd):
     v2u = cosmo.v2_unit(sysd["z_d"], sysd["z_s"], sysd["omega_m"], sysd["kappa_ext"])
     X, Y, r_max = sky_geometry(sysd)
     xp, yp = lens.frame(X, Y, th[IDX["x_c"]], th[IDX["y_c"]], th[IDX["phi"]])
-    tab = jam.table(tr, ms, inc, th[IDX["beta"]], v2u, r_max, sysd["n_gl"])
-    return ST_OK, dict(tr=tr, ms=ms, v2u=v2u, r_max=r_max, X=X, xp=xp, yp=yp, tab=tab)
+    d = dict(tr=tr, ms=ms, v2u=v2u, r_max=r_max, X=X, xp=xp, yp=yp)
+    if sysd.get("jam_align", 0) == 1:
+        m = jam_sph.SphModel(tr, ms, inc, th[IDX["beta"]], v2u)
+        rule = sph_rule(sysd, tr["sig"], ms["sig"])
+        d.update(sph=(m, rule, jam_sph.grid_moments(m, rule)))
+    else:
+        d.update(tab=jam.table(tr, ms, inc, th[IDX["beta"]], v2u, r_max, sysd["n_gl"]))
+    return ST_OK, d
+
+
+def sph_rule(sysd, sig_light, sig_mass):
+    """Discrete rule of the spherically aligned model for this system."""
+    dn = jam_sph.DEFAULT_RULE
+    return jam_sph.SphRule(sig_light, sig_mass, sysd["kpix"] / sysd["kss"],
+                           int(sysd.get("sph_nr", 0) or dn[0]), int(sysd.get("sph_nw", 0) or dn[1]),
+                           int(sysd.get("sph_nlos", 0) or dn[2]), sysd["n_gl"])
+
+
+def sigma_v2(d, xp, yp, chunk=2048):
+    """Sigma v_los^2 at galaxy-frame sky points for the system's alignment."""
+    if "sph" in d:
+        m, rule, grids = d["sph"]
+        return jam_sph.sigma_v2_sph(xp, yp, m, rule, grids)
+    return jam.sigma_v2_fast(xp, yp, d["tab"], chunk=chunk)
 
 
 def dynamics(th, sysd, want_maps=False):
@@ -111,14 +135,14 @@ def dynamics(th, sysd, want_maps=False):
     st, d = dynamics_setup(th, sysd)
     if st != ST_OK:
         return None, st, {}
-    xp, yp, tr, tab = d["xp"], d["yp"], d["tr"], d["tab"]
-    sv2 = jam.sigma_v2_fast(xp, yp, tab).reshape(d["X"].shape)
+    xp, yp, tr = d["xp"], d["yp"], d["tr"]
+    sv2 = sigma_v2(d, xp, yp).reshape(d["X"].shape)
     sb = jam.surface_brightness(xp, yp, tr)
     num, den = kin.bin_moments(sv2, sb, sysd)
     v = np.sqrt(num / den)
     extra = dict(tr=tr, ms=d["ms"], v2u=d["v2u"], r_max=d["r_max"], num=num, den=den)
     if want_maps:
-        extra.update(sv2=sv2, sb=sb, xp=xp, yp=yp, tab=tab)
+        extra.update(sv2=sv2, sb=sb, xp=xp, yp=yp, tab=d.get("tab"), sph=d.get("sph"))
     return v, ST_OK, extra
 
 
@@ -138,7 +162,7 @@ def vrms_bins(th, sysd, which, chunk=64):
     sup = maximum_filter(np.isin(lab, list(which)).astype(np.uint8), size=K, mode="constant") > 0
     sv2 = np.zeros(lab.shape)
     sb = np.zeros(lab.shape)
-    sv2[sup] = jam.sigma_v2_fast(d["xp"][sup], d["yp"][sup], d["tab"], chunk=chunk)
+    sv2[sup] = sigma_v2(d, d["xp"][sup], d["yp"][sup], chunk=chunk)
     sb[sup] = jam.surface_brightness(d["xp"][sup], d["yp"][sup], d["tr"])
     num, den = kin.bin_moments(sv2, sb, sysd)
     return np.sqrt(num[list(which)] / den[list(which)]), ST_OK

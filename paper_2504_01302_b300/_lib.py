@@ -32,6 +32,7 @@ class SystemDesc(C.Structure):
         ("has_bh", C.c_int), ("bh_sigma", C.c_double), ("L_scale", C.c_double),
         ("n_img", C.c_int), ("img_xy", _d), ("dt_obs", _d), ("dt_sig", _d), ("img_sig", _d),
         ("z_d", C.c_double), ("z_s", C.c_double), ("omega_m", C.c_double), ("kappa_ext", C.c_double),
+        ("jam_align", C.c_int), ("sph_nr", C.c_int), ("sph_nw", C.c_int), ("sph_nlos", C.c_int),
     ]
 
 

@@ -112,6 +112,10 @@ glad_status validate(const glad_system_desc &d, int idx) {
   REQ(d.n_ll2 >= 0 && (d.n_ll2 == 0 || d.ll2), "bad extra lens lights", idx);
   REQ(d.n_sis >= 0 && (d.n_sis == 0 || d.sis), "bad SIS list", idx);
   REQ(d.z_s > d.z_d && d.z_d > 0 && d.omega_m > 0 && d.omega_m < 1, "bad cosmology", idx);
+  REQ(d.jam_align == 0 || d.jam_align == 1, "jam_align must be 0 or 1", idx);
+  REQ(d.sph_nr == 0 || d.sph_nr >= 4, "sph_nr must be 0 (default) or >= 4", idx);
+  REQ(d.sph_nw == 0 || d.sph_nw >= 2, "sph_nw must be 0 (default) or >= 2", idx);
+  REQ(d.sph_nlos >= 0, "sph_nlos must be >= 0", idx);
 #undef REQ
 #define SUP(cond, ...) \
   if (!(cond)) return fail(GLAD_EUNSUPPORTED, "system %d: " __VA_ARGS__)
@@ -129,6 +133,13 @@ glad_status validate(const glad_system_desc &d, int idx) {
   SUP(nl <= GLAD_MAX_LIGHT, "tracer Gaussians > %d", idx, GLAD_MAX_LIGHT);
   for (int i = 0; i < d.kx * d.ky; ++i)
     if (d.bins[i] >= d.n_bins) return fail(GLAD_EINVAL, "system %d: bin index >= n_bins", idx);
+  if (d.jam_align == 1) {
+    const int nr = d.sph_nr ? d.sph_nr : SPH_DEFAULT_NR, nw = d.sph_nw ? d.sph_nw : SPH_DEFAULT_NW;
+    SUP(nr * nw <= GLAD_SPH_MAX_GRID, "sph_nr * sph_nw > %d", idx, GLAD_SPH_MAX_GRID);
+    SUP((d.n_mge_mass + (d.has_bh ? 1 : 0)) * d.n_gl <= GLAD_SPH_MAX_MG,
+        "mass Gaussians x n_gl > %d for the spherically aligned model", idx, GLAD_SPH_MAX_MG);
+    SUP(d.sph_nlos <= 4096, "sph_nlos > 4096", idx);
+  }
 #undef SUP
   return GLAD_OK;
 }
@@ -353,6 +364,37 @@ glad_status build_system(int idx, const glad_system_desc &d, SysHost &sh, SysDev
     sd.sb_cx = upload(sh, cx.data(), nL);
     sd.sb_cy = upload(sh, cy.data(), nL);
   }
+  // spherically aligned model: polar grid r in [r_lo, r_end] (r_lo = d_sub/4, r_end = 9 x the
+  // largest tracer sigma) and the u rule of mass Gaussian j: u = u_s (exp(lam t) - 1),
+  // lam = ln(1 + 1/u_s), u_s = min(1, sigma_j / r_end), n_gl-point Gauss-Legendre in t
+  sd.jam_align = d.jam_align;
+  if (d.jam_align == 1) {
+    sd.sph_nr = d.sph_nr ? d.sph_nr : SPH_DEFAULT_NR;
+    sd.sph_nw = d.sph_nw ? d.sph_nw : SPH_DEFAULT_NW;
+    sd.sph_nlos = d.sph_nlos ? d.sph_nlos : SPH_DEFAULT_NLOS;
+    double smax = 0.0;
+    for (int k = 0; k < nL; ++k) smax = std::max(smax, sig_l[k]);
+    sd.sph_r_lo = 0.25 * d.kpix / d.kss;
+    sd.sph_r_end = 9.0 * smax;
+    if (!(sd.sph_r_end > sd.sph_r_lo))
+      return fail(GLAD_EINVAL, "system %d: tracer too compact for the sky sampling", idx);
+    sd.sph_lr0 = log(sd.sph_r_lo);
+    sd.sph_dlr = (log(sd.sph_r_end) - sd.sph_lr0) / (sd.sph_nr - 1);
+    const int G = d.n_gl;
+    std::vector<double> x, w, su(nMt * G), sw(nMt * G);
+    gauss_legendre(G, x, w);
+    for (int j = 0; j < nMt; ++j) {
+      const double us = std::min(1.0, sig_m[j] / sd.sph_r_end);
+      const double lam = log1p(1.0 / us);
+      for (int g = 0; g < G; ++g) {
+        const double t = 0.5 * (x[g] + 1.0), e = exp(lam * t);
+        su[j * G + g] = us * (e - 1.0);
+        sw[j * G + g] = 0.5 * w[g] * us * lam * e;
+      }
+    }
+    sd.sph_u = upload(sh, su.data(), su.size());
+    sd.sph_wu = upload(sh, sw.data(), sw.size());
+  }
   sd.has_bh = d.has_bh;
   sd.bh_sigma = d.bh_sigma;
   sd.L_scale = d.L_scale;
@@ -413,7 +455,9 @@ glad_status ws_ensure(glad_ctx *c, int B) {
             ws_alloc(w, w.d.img, b * c->max_pix) && ws_alloc(w, w.d.binacc, b * c->max_bins * 2) &&
             ws_alloc(w, w.d.terms, b * 4) && ws_alloc(w, w.d.status, b) &&
             ws_alloc(w, w.d.wl_off, b + 1) && ws_alloc(w, w.d.wl_counter, 1) &&
-            ws_alloc(w, w.d.evals, 2);
+            ws_alloc(w, w.d.evals, 2) && ws_alloc(w, w.d.sph_mt, b * c->max_smg) &&
+            ws_alloc(w, w.d.sph_mrz, b * c->max_smg) && ws_alloc(w, w.d.sph_tr, b * c->max_light) &&
+            ws_alloc(w, w.d.sgrid, b * c->max_sgrid);
   if (!ok) {
     ws_free(w);
     return fail(GLAD_ENOMEM, "workspace for B=%d does not fit on the device", B);
@@ -438,8 +482,8 @@ glad_status forward(glad_ctx *c, const int *sys_id, const double *theta, int B, 
   if (e == cudaSuccess && image_out)
     e = GLAD_PROF(c, st, KID_IMAGE_CONV, launch_lens(c, sys_id, B, image_out, st, nullptr));
   if (e == cudaSuccess && vrms_out) {
-    e = GLAD_PROF(c, st, KID_TABLE, launch_table(c, sys_id, B, st));
-    if (e == cudaSuccess) e = GLAD_PROF(c, st, KID_JAM, launch_jam(c, sys_id, B, st));
+    e = launch_dyn_tables(c, sys_id, B, st);
+    if (e == cudaSuccess) e = launch_dyn_sums(c, sys_id, B, st);
     if (e == cudaSuccess) e = GLAD_PROF(c, st, KID_KIN, launch_kin_finalize(c, sys_id, B, vrms_out, st));
   }
   if (e != cudaSuccess) return fail(GLAD_ECUDA, "launch failed: %s", cudaGetErrorString(e));
@@ -475,10 +519,10 @@ glad_status full_path(glad_ctx *c, const int *sys_id, const double *theta, int B
   if (e == cudaSuccess && grad) e = launch_grad_lens(c, sys_id, B, grad, c->side);
   if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
   // dynamics, high priority
-  if (e == cudaSuccess) e = GLAD_PROF(c, dy, KID_TABLE, launch_table(c, sys_id, B, dy));
+  if (e == cudaSuccess) e = launch_dyn_tables(c, sys_id, B, dy);
   if (e == cudaSuccess) {
     if (grad) e = GLAD_PROF(c, dy, KID_GRAD_JAM_FWD, launch_jam_fg(c, sys_id, B, dy));
-    else e = GLAD_PROF(c, dy, KID_JAM, launch_jam(c, sys_id, B, dy));
+    else e = launch_dyn_sums(c, sys_id, B, dy);
   }
   if (e == cudaSuccess) e = GLAD_PROF(c, dy, KID_KIN, launch_kin_finalize(c, sys_id, B, nullptr, dy));
   if (e == cudaSuccess && grad) e = launch_grad_dyn(c, sys_id, theta, B, grad, dy);
@@ -495,9 +539,24 @@ glad_status full_path(glad_ctx *c, const int *sys_id, const double *theta, int B
 
 const char *kKernelNames[KID_N] = {
     "k_prep", "k_table", "k_image+k_conv", "k_jam", "k_kin_finalize", "k_combine",
-    "k_grad_lens", "k_jam_fwd_grad", "k_jam_adjoint", "k_grad_chain"};
+    "k_grad_lens", "k_jam_fwd_grad", "k_jam_adjoint", "k_grad_chain", "k_sph_coef+k_sph_grid",
+    "k_sph_los"};
 
 }  // namespace
+
+cudaError_t launch_dyn_tables(glad_ctx *c, const int *sys_id, int B, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  if (c->n_cyl) e = GLAD_PROF(c, st, KID_TABLE, launch_table(c, sys_id, B, st));
+  if (e == cudaSuccess && c->n_sph) e = GLAD_PROF(c, st, KID_SPH_GRID, launch_sph_grid(c, sys_id, B, st));
+  return e;
+}
+
+cudaError_t launch_dyn_sums(glad_ctx *c, const int *sys_id, int B, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  if (c->n_cyl) e = GLAD_PROF(c, st, KID_JAM, launch_jam(c, sys_id, B, st));
+  if (e == cudaSuccess && c->n_sph) e = GLAD_PROF(c, st, KID_SPH_LOS, launch_sph_los(c, sys_id, B, st));
+  return e;
+}
 
 // error reporting for entry points defined in other files
 glad_status glad_set_error(glad_status s, const char *msg) { return fail(s, "%s", msg); }
@@ -614,6 +673,13 @@ glad_status glad_create(const glad_system_desc *sys, int n_sys, glad_ctx **out) 
     c->max_sky_tiles = std::max(c->max_sky_tiles, d.n_sky_tiles);
     c->max_tab_blocks = std::max(c->max_tab_blocks, d.n_tab_blocks);
     c->max_apts = std::max(c->max_apts, d.n_atile * 256);
+    if (d.jam_align == 1) {
+      ++c->n_sph;
+      c->max_sgrid = std::max(c->max_sgrid, d.sph_nr * d.sph_nw);
+      c->max_smg = std::max(c->max_smg, d.n_mass_tot * d.n_gl);
+    } else {
+      ++c->n_cyl;
+    }
   }
   if (cudaMalloc(&c->d_sys, sizeof(SysDev) * n_sys) != cudaSuccess ||
       cudaMemcpy(c->d_sys, c->h_sysdev.data(), sizeof(SysDev) * n_sys, cudaMemcpyHostToDevice) !=
@@ -627,6 +693,7 @@ glad_status glad_create(const glad_system_desc *sys, int n_sys, glad_ctx **out) 
   cudaMemcpy(c->d_one_sys, ids.data(), sizeof(int) * n_sys, cudaMemcpyHostToDevice);
   set_conv_smem_limit();
   set_grad_smem_limit();
+  set_sph_smem_limit();
   int prio_lo = 0, prio_hi = 0;
   cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
   if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
@@ -683,6 +750,9 @@ glad_status glad_loglike_grad(glad_ctx *c, const int *sys_id, const double *thet
   g_err.clear();
   if (!c || !sys_id || !theta || !logL || !grad || !sample_status || B < 1)
     return fail(GLAD_EINVAL, "glad_loglike_grad: bad arguments");
+  if (c->n_sph)
+    return fail(GLAD_EUNSUPPORTED,
+                "glad_loglike_grad: no gradient for the spherically aligned Jeans model");
   if (grad_ws_ensure(c, B) != cudaSuccess)
     return fail(GLAD_ENOMEM, "gradient workspace for B=%d does not fit", B);
   return full_path(c, sys_id, theta, B, (cudaStream_t)stream, logL, sample_status, terms, grad);

@@ -16,6 +16,11 @@
 #define GLAD_MAX_PSF 63       // imaging PSF side
 #define GLAD_MAX_P 20         // Euler order
 #define GLAD_MAX_IMG 8        // quasar images
+#define GLAD_SPH_MAX_GRID 4096  // polar grid points of the spherically aligned model
+#define GLAD_SPH_MAX_MG 4096    // (mass Gaussian, u node) pairs of the spherically aligned model
+#define SPH_DEFAULT_NR 96       // default polar grid and line-of-sight rule of that model
+#define SPH_DEFAULT_NW 8
+#define SPH_DEFAULT_NLOS 64
 
 // ---------------------------------------------------------------------------
 // device-resident description of one system (all pointers are device memory)
@@ -72,6 +77,12 @@ struct SysDev {
   // system) and the sky grid in 16 x 16 point tiles (atx across, n_atile in all)
   const int *adj_perm;                      // [n_ent]
   int atx, n_atile;
+  // spherically aligned JAM (jam_align 1): polar grid of sph_nr radii log-spaced on
+  // [sph_r_lo, sph_r_end] (ln r = sph_lr0 + a sph_dlr) x sph_nw values of sin^2 theta,
+  // sph_nlos line-of-sight nodes, and the u rule of each mass Gaussian
+  int jam_align, sph_nr, sph_nw, sph_nlos;
+  double sph_r_lo, sph_r_end, sph_lr0, sph_dlr;
+  const double *sph_u, *sph_wu;             // [n_mass_tot * n_gl]
 };
 
 // per-sample lensing parameters (FP32), written by the prep kernel
@@ -119,6 +130,10 @@ struct WsDev {
   int *wl_counter;             // [1]   next work item
   unsigned long long *evals;   // [2]   JAM integrand evaluations executed: pair sum (forward or
                                //       derivative pass), table adjoint (null: not counted)
+  float4 *sph_mt;              // [B*max_smg] spherical model: (mass Gaussian, u node) coefficients
+  float *sph_mrz;              // [B*max_smg] their F_R - F_z weights
+  float4 *sph_tr;              // [B*max_light] tracer Gaussians (nu0, exponent coefficients, dnu factor)
+  float2 *sgrid;               // [B*max_sgrid] (v_r^2, d) on the polar grid
   int neg_mode;                // negligible-term skipping in the forward JAM pass: 0 off,
                                // 1 on, 2 on with every tile's check failed (summed again)
 };
@@ -139,6 +154,8 @@ struct glad_ctx {
   int max_light = 0, max_mass_tot = 0, max_ent = 0, max_pix = 0, max_bins = 0, max_sub = 0;
   int max_apts = 0;  // largest 16 x 16-tiled sky grid (points, padded)
   int max_img_tiles = 0, max_sky_tiles = 0, max_tab_blocks = 0;
+  int n_cyl = 0, n_sph = 0;        // systems with the cylindrically / spherically aligned model
+  int max_sgrid = 0, max_smg = 0;  // largest polar grid and (mass Gaussian, u node) count
   Workspace ws;
   GradWs *gws = nullptr;
   // launch shapes chosen by glad_autotune (defaults until it runs)
@@ -170,7 +187,8 @@ struct glad_ctx {
 // kernel ids for glad_kernel_times
 enum {
   KID_PREP = 0, KID_TABLE, KID_IMAGE_CONV, KID_JAM, KID_KIN, KID_COMBINE,
-  KID_GRAD_LENS, KID_GRAD_JAM_FWD, KID_GRAD_JAM_ADJ, KID_GRAD_CHAIN, KID_N
+  KID_GRAD_LENS, KID_GRAD_JAM_FWD, KID_GRAD_JAM_ADJ, KID_GRAD_CHAIN, KID_SPH_GRID, KID_SPH_LOS,
+  KID_N
 };
 
 // record an event pair around `call` when profiling is on
@@ -205,6 +223,14 @@ cudaError_t launch_kin_finalize(glad_ctx *c, const int *sys_id, int B, float *vr
                                 cudaStream_t st);
 cudaError_t launch_combine(glad_ctx *c, int B, double *logL, int *status, double *terms,
                            cudaStream_t st);
+// spherically aligned model (k_sph.cu): coefficients + polar grid, then the line-of-sight sums
+cudaError_t launch_sph_grid(glad_ctx *c, const int *sys_id, int B, cudaStream_t st);
+cudaError_t launch_sph_los(glad_ctx *c, const int *sys_id, int B, cudaStream_t st);
+void set_sph_smem_limit();
+// the dynamics sum of either model for the systems of the context (glad_host.cu): the
+// table/grid stage and the sky-point stage, each recorded under its kernel id
+cudaError_t launch_dyn_tables(glad_ctx *c, const int *sys_id, int B, cudaStream_t st);
+cudaError_t launch_dyn_sums(glad_ctx *c, const int *sys_id, int B, cudaStream_t st);
 void set_conv_smem_limit();
 bool jam_shape_supported(int pts, int minb, int unr);
 int jam_shape_list(int (*out)[3], int cap);

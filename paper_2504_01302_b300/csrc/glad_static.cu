@@ -63,6 +63,10 @@ size_t carve(const glad_ctx *c, int B, unsigned char *base, WsDev *w) {
   w->binacc = (double *)take(b * c->max_bins * 2 * sizeof(double));
   w->terms = (double *)take(b * 4 * sizeof(double));
   w->status = (int *)take(b * sizeof(int));
+  w->sph_mt = (float4 *)take(b * c->max_smg * sizeof(float4));
+  w->sph_mrz = (float *)take(b * c->max_smg * sizeof(float));
+  w->sph_tr = (float4 *)take(b * c->max_light * sizeof(float4));
+  w->sgrid = (float2 *)take(b * c->max_sgrid * sizeof(float2));
   return off;
 }
 
@@ -102,9 +106,9 @@ extern "C" glad_status glad_loglike_static(glad_ctx *c, const int *sys_id, const
   if (e == cudaSuccess)
     e = cudaMemsetAsync(w.binacc, 0, sizeof(double) * 2 * c->max_bins * (size_t)B, st);
   if (e == cudaSuccess) e = launch_prep(c, sys_id, theta, B, st);
-  if (e == cudaSuccess) e = launch_table(c, sys_id, B, st);
+  if (e == cudaSuccess) e = launch_dyn_tables(c, sys_id, B, st);
   if (e == cudaSuccess) e = launch_lens(c, sys_id, B, nullptr, st);
-  if (e == cudaSuccess) e = launch_jam(c, sys_id, B, st);
+  if (e == cudaSuccess) e = launch_dyn_sums(c, sys_id, B, st);
   if (e == cudaSuccess) e = launch_kin_finalize(c, sys_id, B, nullptr, st);
   if (e == cudaSuccess) e = launch_combine(c, B, logL, sample_status, terms, st);
   c->ws.d = saved;

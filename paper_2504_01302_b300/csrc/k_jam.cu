@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(JAM_THREADS, MINB) k_jam(const SysDev *__restr
   const int b = blockIdx.y;
   if (ws.status[b] != GLAD_SAMPLE_OK) return;
   const SysDev &S = sysv[sys_id[b]];
-  if ((int)blockIdx.x >= jam_tiles(S.nsx, S.nsy, PTS)) return;
+  if (S.jam_align != 0 || (int)blockIdx.x >= jam_tiles(S.nsx, S.nsy, PTS)) return;
   __shared__ JamSmem sm;
   jam_tile<PTS, UNR>(S, ws, sm, b, blockIdx.x, max_light, max_ent, max_bins);
 }
@@ -253,7 +253,7 @@ __global__ void k_worklist(const SysDev *__restrict__ sysv, const int *__restric
     int n = 0;
     if (b < B && ws.status[b] == GLAD_SAMPLE_OK) {
       const SysDev &S = sysv[sys_id[b]];
-      n = jam_tiles(S.nsx, S.nsy, pts);
+      n = S.jam_align == 0 ? jam_tiles(S.nsx, S.nsy, pts) : 0;
     }
     part[threadIdx.x] = n;
     __syncthreads();

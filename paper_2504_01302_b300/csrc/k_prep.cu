@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(TAB_THREADS) k_table(const SysDev *__restrict_
   if (ws.status[b] != GLAD_SAMPLE_OK) return;
   const SysDev &S = sysv[sys_id[b]];
   const int e = blockIdx.x * TAB_THREADS + threadIdx.x;
-  if (e >= S.n_ent) return;
+  if (e >= S.n_ent || S.jam_align != 0) return;  // the spherically aligned model has no table
   const int kj = e / S.n_gl;
   const int j = kj % S.n_mass_tot;
   const int k = kj / S.n_mass_tot;

@@ -85,6 +85,9 @@ class GladContext:
             d.img_sig = _ptr(self._arr(s["img_sig"], f64), C.c_double)
         d.z_d, d.z_s = float(s["z_d"]), float(s["z_s"])
         d.omega_m, d.kappa_ext = float(s["omega_m"]), float(s["kappa_ext"])
+        d.jam_align = int(s.get("jam_align", 0))
+        d.sph_nr, d.sph_nw = int(s.get("sph_nr", 0)), int(s.get("sph_nw", 0))
+        d.sph_nlos = int(s.get("sph_nlos", 0))
 
     # ------------------------------------------------------------------ calls
     def _check_theta(self, theta, sys_id):

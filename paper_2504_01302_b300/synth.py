@@ -211,18 +211,22 @@ def workload_systems(w: int, small: bool = False):
     2: workload 1's system, B=64, forward + gradient
     3: 8 uneven systems, 1024 samples split multinomially
     4: IFU-scale (400^2 x3, 31^2 PSF, 40+2x20+BH, 128^2 sky x4, GL64, 400 bins), B=4096
+    5: workload 1's system with the spherically aligned Jeans model (Eqs. J1/J2; polar
+       grid 96 x 8, 64 line-of-sight nodes), B=256
     """
-    rng = np.random.Generator(np.random.PCG64(1000 + w))
+    rng = np.random.Generator(np.random.PCG64(1000 + (1 if w == 5 else w)))
     if w == 0:
         s = base_system("w0", n_img_px=64, ss=1, psf_k=11, sky=32, kss=1, n_mass=10,
                         n_light=10, n_gl=32, n_bins=20, bins="annular", rng=rng,
                         has_bh=False, n_sis=0, second_light=False)
         return [s], 1
-    if w in (1, 2):
+    if w in (1, 2, 5):
         s = base_system("w1", n_img_px=200, ss=2, psf_k=21, sky=60, kss=4, n_mass=20,
                         n_light=10, n_gl=32, n_bins=50, bins="voronoi", rng=rng,
                         has_bh=True, n_sis=1, second_light=True)
-        return [s], (256 if w == 1 else 64)
+        if w == 5:
+            s.update(name="w5", jam_align=1, sph_nr=96, sph_nw=8, sph_nlos=64)
+        return [s], (64 if w == 2 else 256)
     if w == 3:
         systems = []
         for si in range(8):

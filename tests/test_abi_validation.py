@@ -28,6 +28,12 @@ def _set(key, value):
     return m
 
 
+def _sph(**kw):
+    def m(s):
+        s.update(jam_align=1, **kw)
+    return m
+
+
 @pytest.mark.parametrize("mutate, status, words", [
     (_set("psf", np.ones((4, 4), np.float32) / 16), GLAD_EINVAL, "psf_k must be odd"),
     (_set("kpsf", np.ones((2, 2), np.float32) / 4), GLAD_EINVAL, "kpsf_k must be odd"),
@@ -44,6 +50,13 @@ def _set(key, value):
     (_set("n_mge_light", [100, 40]), GLAD_EUNSUPPORTED, "tracer Gaussians >"),
     (_set("img_xy", np.zeros((9, 2))), GLAD_EUNSUPPORTED, "n_img >"),
     (_set("img_sig", np.array([0.005, 0.0, 0.005, 0.005])), GLAD_EINVAL, "img_sig must be positive"),
+    (_set("jam_align", 2), GLAD_EINVAL, "jam_align must be 0 or 1"),
+    (_sph(sph_nr=3), GLAD_EINVAL, "sph_nr must be"),
+    (_sph(sph_nw=1), GLAD_EINVAL, "sph_nw must be"),
+    (_sph(sph_nlos=-1), GLAD_EINVAL, "sph_nlos must be"),
+    (_sph(sph_nr=128, sph_nw=64), GLAD_EUNSUPPORTED, "sph_nr * sph_nw >"),
+    (_sph(sph_nlos=5000), GLAD_EUNSUPPORTED, "sph_nlos >"),
+    (_sph(n_gl=512), GLAD_EUNSUPPORTED, "for the spherically aligned model"),
 ])
 def test_create_rejects_invalid_descriptors(mutate, status, words):
     msg = _create(mutate)
