@@ -99,7 +99,7 @@ def workload_name(w, grad, B):
              4: "IFU-scale: 400^2 x3ss, 31^2 PSF, EPL+shear+2 SIS, JAM 40+2x20+BH, 128^2 sky x4, "
                 "GL64, 400 bins",
              5: "RXJ1131-scale with the spherically aligned Jeans model (Eqs. J1/J2): 200^2 x2ss, "
-                "21^2 PSF, EPL+shear+SIS, JAM 20+2x10+BH, polar grid 96x8, 64 LOS nodes, "
+                "21^2 PSF, EPL+shear+SIS, JAM 20+2x10+BH, polar grid 128x8, 32 LOS nodes, "
                 "60^2 sky x4ss, 50 bins"}
     n = names.get(w, str(w)) + f"; B={B}"
     if grad:

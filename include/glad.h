@@ -81,7 +81,7 @@ enum {
  * spherically aligned one of Eqs. J1/J2 (constant beta = 1 - v_theta^2/v_r^2), solved
  * along the characteristics of J1/J2 on a polar grid of sph_nr radii (log-spaced from a
  * quarter sky sub-sample to 9 x the largest tracer sigma) x sph_nw values of sin^2 theta,
- * and projected with sph_nlos nodes per line of sight; 0 selects the defaults 96, 8, 64.
+ * and projected with sph_nlos nodes per line of sight; 0 selects the defaults 128, 8, 32.
  * Limits: sph_nr * sph_nw <= 4096 and (mass Gaussians incl. the black hole) x n_gl <= 4096
  * (GLAD_EUNSUPPORTED beyond).  glad_loglike_grad (and glad_autotune with_grad) return
  * GLAD_EUNSUPPORTED for a context that holds a spherically aligned system.

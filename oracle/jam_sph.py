@@ -53,9 +53,10 @@ Two forms are written out:
            c = max(rho, r_lo), rho = sqrt(x'^2 + y'^2), tau_m = asinh(r_end / c);
            v_r^2 and d cubic in ln r (4-point Lagrange) and linear in w = R^2/r^2,
            clamped to the grid; nu exact at the node.
-  Defaults n_r = 96, n_w = 8, n_los = 64: against the cylindrical pair form at beta = 0
-  (the two models coincide there) the RXJ1131-scale sky maps agree to 5e-4 (2.5e-4 in
-  v_rms); the error falls as n_r^-3.3 and is set by the radial grid.
+  Defaults n_r = 128, n_w = 8, n_los = 32: against the cylindrical pair form at beta = 0
+  (the two models coincide there) the RXJ1131-scale sky maps agree to 2.9e-4 (1.5e-4 in
+  v_rms); the error is set by the radial grid and falls as n_r^-3.3 (6.2e-4 at n_r = 96,
+  1.8e-4 at 160); beyond 24 line-of-sight nodes it no longer depends on n_los.
 
 Pins (tests/test_oracle_sph.py): the plain solution satisfies J1 and J2 (finite
 differences); at beta = 0 it equals the cylindrical isotropic solution (nu v_z^2 and
@@ -74,7 +75,7 @@ R_END_FAC = 9.0     # r_end = R_END_FAC * largest tracer sigma
 R_LO_FRAC = 0.25    # r_lo = R_LO_FRAC * sky sub-sample spacing
 CHAR_PIECES = 16    # pieces of the characteristic's s range
 CHAR_GL = 4         # Gauss-Legendre points per piece
-DEFAULT_RULE = (96, 8, 64)  # n_r, n_w, n_los
+DEFAULT_RULE = (128, 8, 32)  # n_r, n_w, n_los
 
 
 class SphModel:

@@ -18,9 +18,9 @@
 #define GLAD_MAX_IMG 8        // quasar images
 #define GLAD_SPH_MAX_GRID 4096  // polar grid points of the spherically aligned model
 #define GLAD_SPH_MAX_MG 4096    // (mass Gaussian, u node) pairs of the spherically aligned model
-#define SPH_DEFAULT_NR 96       // default polar grid and line-of-sight rule of that model
+#define SPH_DEFAULT_NR 128      // default polar grid and line-of-sight rule of that model
 #define SPH_DEFAULT_NW 8
-#define SPH_DEFAULT_NLOS 64
+#define SPH_DEFAULT_NLOS 32
 
 // ---------------------------------------------------------------------------
 // device-resident description of one system (all pointers are device memory)

@@ -33,6 +33,9 @@ namespace {
 #define SPH_THREADS 256
 #define SPH_WARPS (SPH_THREADS / 32)
 #define SPH_PIECES 16
+#ifndef SPH_LOS_MINB
+#define SPH_LOS_MINB 4  // resident CTAs per SM asked of the register allocator (line of sight)
+#endif
 
 __device__ __forceinline__ float sph_ex2(float x) {
   float y;
@@ -175,7 +178,32 @@ __global__ void __launch_bounds__(SPH_THREADS) k_sph_grid(const SysDev *__restri
   }
 }
 
-__global__ void __launch_bounds__(SPH_THREADS) k_sph_los(const SysDev *__restrict__ sysv,
+// (v_r^2, d) of grid radius a at w columns c and c+1, for one node's interpolation
+__device__ __forceinline__ float2 sph_interp(const float4 *g4, int nr, int nwm, float lr0,
+                                             float idlr, float r2, float ir2, float R2) {
+  const float fa = fminf(fmaxf((0.5f * 0.69314718055994531f * __log2f(r2) - lr0) * idlr, 0.f),
+                         (float)(nr - 1));
+  const float fc = fminf(fmaxf(R2 * ir2 * (float)nwm, 0.f), (float)nwm);
+  const int i0 = min(max((int)floorf(fa) - 1, 0), nr - 4);
+  const int c0 = min((int)fc, nwm - 1);
+  const float t = fa - (float)i0, tc = fc - (float)c0, uc = 1.f - tc;
+  // 4-point Lagrange weights on the stencil nodes 0..3
+  const float t1 = t - 1.f, t2 = t - 2.f, t3 = t - 3.f;
+  const float L0 = -t1 * t2 * t3 * (1.f / 6.f), L1 = 0.5f * t * t2 * t3;
+  const float L2 = -0.5f * t * t1 * t3, L3 = t * t1 * t2 * (1.f / 6.f);
+  const float4 *gp = g4 + i0 * nwm + c0;
+  const float4 a0 = gp[0], a1 = gp[nwm], a2 = gp[2 * nwm], a3 = gp[3 * nwm];
+  float2 g;
+  g.x = L0 * (uc * a0.x + tc * a0.z) + L1 * (uc * a1.x + tc * a1.z) +
+        L2 * (uc * a2.x + tc * a2.z) + L3 * (uc * a3.x + tc * a3.z);
+  g.y = L0 * (uc * a0.y + tc * a0.w) + L1 * (uc * a1.y + tc * a1.w) +
+        L2 * (uc * a2.y + tc * a2.w) + L3 * (uc * a3.y + tc * a3.w);
+  return g;
+}
+
+// The midpoint nodes come in pairs tau_i, tau_{n-1-i} = -tau_i that share e^tau and
+// e^-tau; each pair is one packed FP32 step (the middle node of an odd n is done alone).
+__global__ void __launch_bounds__(SPH_THREADS, SPH_LOS_MINB) k_sph_los(const SysDev *__restrict__ sysv,
                                                          const int *__restrict__ sys_id, WsDev ws,
                                                          int max_light, int max_sgrid, int max_bins) {
   const int b = blockIdx.y;
@@ -183,13 +211,20 @@ __global__ void __launch_bounds__(SPH_THREADS) k_sph_los(const SysDev *__restric
   const SysDev &S = sysv[sys_id[b]];
   if (S.jam_align != 1) return;
   if ((int)blockIdx.x * SPH_THREADS >= S.n_sub) return;
-  __shared__ float2 grid[GLAD_SPH_MAX_GRID];
-  __shared__ float4 trc[GLAD_MAX_LIGHT];
-  __shared__ float4 sbc[GLAD_MAX_LIGHT];
-  __shared__ float bnum[GLAD_MAX_BINS], bden[GLAD_MAX_BINS];
+  extern __shared__ float4 sph_smem[];
   const int tid = threadIdx.x;
-  const int nr = S.sph_nr, nw = S.sph_nw, nL = S.n_light;
-  for (int i = tid; i < nr * nw; i += SPH_THREADS) grid[i] = ws.sgrid[(size_t)b * max_sgrid + i];
+  const int nr = S.sph_nr, nw = S.sph_nw, nwm = nw - 1, nL = S.n_light;
+  float4 *g4 = sph_smem;                 // [nr * (nw - 1)]: (v, d) at columns c and c + 1
+  float4 *trc = g4 + nr * nwm;           // [nL]
+  float4 *sbc = trc + nL;                // [nL]
+  float *bnum = (float *)(sbc + nL);     // [n_bins]
+  float *bden = bnum + S.n_bins;         // [n_bins]
+  const float2 *gsrc = ws.sgrid + (size_t)b * max_sgrid;
+  for (int i = tid; i < nr * nwm; i += SPH_THREADS) {
+    const int a = i / nwm, c = i - a * nwm;
+    const float2 u = gsrc[a * nw + c], v = gsrc[a * nw + c + 1];
+    g4[i] = make_float4(u.x, u.y, v.x, v.y);
+  }
   for (int k = tid; k < nL; k += SPH_THREADS) {
     trc[k] = ws.sph_tr[(size_t)b * max_light + k];
     sbc[k] = make_float4(ws.I0f[(size_t)b * max_light + k], S.sb_cx[k], S.sb_cy[k], 0.f);
@@ -216,44 +251,45 @@ __global__ void __launch_bounds__(SPH_THREADS) k_sph_los(const SysDev *__restric
     const float tm = asinhf(r_end / c);
     const int n = S.sph_nlos;
     const float dtau = 2.0f * tm / (float)n;
-    const float X2 = xp * xp, omb = 1.0f - beta, fmax_a = (float)(nr - 1), fmax_c = (float)(nw - 1);
+    const float X2 = xp * xp, omb = 1.0f - beta, dX = s2 * X2;
+    const float ya = yp * ci, za = yp * si;
     float acc = 0.f;
-    for (int i = 0; i < n; ++i) {
+    for (int i = 0; i < (n >> 1); ++i) {
       const float tau = ((float)i + 0.5f) * dtau - tm;
       const float et = sph_ex2(tau * (float)LOG2E_D), eti = __fdividef(1.0f, et);
       const float zp = 0.5f * c * (et - eti), wt = 0.5f * dtau * c * (et + eti);
-      const float yy = yp * ci - zp * si, zz = yp * si + zp * ci;
-      const float R2 = X2 + yy * yy, Z2 = zz * zz;
-      const float r2 = fmaxf(R2 + Z2, 1e-30f);
-      const float ir2 = __fdividef(1.0f, r2);
-      const float fa = fminf(fmaxf((0.5f * 0.69314718055994531f * __log2f(r2) - lr0) * idlr, 0.f), fmax_a);
-      const float fc = fminf(fmaxf(R2 * ir2 * fmax_c, 0.f), fmax_c);
-      const int i0 = min(max((int)floorf(fa) - 1, 0), nr - 4);
-      const int c0 = min((int)fc, nw - 2);
-      const float t = fa - (float)i0, tc = fc - (float)c0;
-      // 4-point Lagrange weights on the stencil nodes 0..3
-      const float t1 = t - 1.f, t2 = t - 2.f, t3 = t - 3.f;
-      const float L0 = -t1 * t2 * t3 * (1.f / 6.f), L1 = 0.5f * t * t2 * t3;
-      const float L2 = -0.5f * t * t1 * t3, L3 = t * t1 * t2 * (1.f / 6.f);
-      const float2 *gp = grid + i0 * nw + c0;
-      float2 g;
-      {
-        const float2 a0 = gp[0], b0 = gp[1], a1 = gp[nw], b1 = gp[nw + 1];
-        const float2 a2 = gp[2 * nw], b2 = gp[2 * nw + 1], a3 = gp[3 * nw], b3 = gp[3 * nw + 1];
-        const float uc = 1.f - tc;
-        g.x = L0 * (uc * a0.x + tc * b0.x) + L1 * (uc * a1.x + tc * b1.x) +
-              L2 * (uc * a2.x + tc * b2.x) + L3 * (uc * a3.x + tc * b3.x);
-        g.y = L0 * (uc * a0.y + tc * b0.y) + L1 * (uc * a1.y + tc * b1.y) +
-              L2 * (uc * a2.y + tc * b2.y) + L3 * (uc * a3.y + tc * b3.y);
+      // nodes +z' and -z'
+      const float2 yy = make_float2(ya - zp * si, ya + zp * si);
+      const float2 zz = make_float2(za + zp * ci, za - zp * ci);
+      const float2 R2 = make_float2(fmaf(yy.x, yy.x, X2), fmaf(yy.y, yy.y, X2));
+      const float2 Z2 = make_float2(zz.x * zz.x, zz.y * zz.y);
+      const float2 r2 = make_float2(fmaxf(R2.x + Z2.x, 1e-30f), fmaxf(R2.y + Z2.y, 1e-30f));
+      const float2 ir2 = make_float2(__fdividef(1.0f, r2.x), __fdividef(1.0f, r2.y));
+      const float2 ga = sph_interp(g4, nr, nwm, lr0, idlr, r2.x, ir2.x, R2.x);
+      const float2 gb = sph_interp(g4, nr, nwm, lr0, idlr, r2.y, ir2.y, R2.y);
+      float2 nu = make_float2(0.f, 0.f);
+#pragma unroll 4
+      for (int k = 0; k < nL; ++k) {
+        const float4 q = trc[k];
+        const float2 arg = __ffma2_rn(make_float2(q.z, q.z), Z2, __fmul2_rn(make_float2(q.y, q.y), R2));
+        nu = __ffma2_rn(make_float2(q.x, q.x), make_float2(sph_ex2(arg.x), sph_ex2(arg.y)), nu);
       }
+      const float mua = zz.x * ci - yy.x * si, mub = zz.y * ci - yy.y * si;
+      const float fa = nu.x * (ga.x * fmaf(beta * mua * mua, ir2.x, omb) + ga.y * dX);
+      const float fb = nu.y * (gb.x * fmaf(beta * mub * mub, ir2.y, omb) + gb.y * dX);
+      acc = fmaf(wt, fa + fb, acc);
+    }
+    if (n & 1) {  // middle node, z' = 0
+      const float R2 = fmaf(ya, ya, X2), Z2 = za * za;
+      const float r2 = fmaxf(R2 + Z2, 1e-30f), ir2 = __fdividef(1.0f, r2);
+      const float2 g = sph_interp(g4, nr, nwm, lr0, idlr, r2, ir2, R2);
       float nu = 0.f;
       for (int k = 0; k < nL; ++k) {
         const float4 q = trc[k];
         nu = fmaf(q.x, sph_ex2(fmaf(q.z, Z2, q.y * R2)), nu);
       }
-      const float mu = zz * ci - yy * si;
-      const float f = nu * (g.x * fmaf(beta * mu * mu, ir2, omb) + g.y * s2 * X2);
-      acc = fmaf(wt, f, acc);
+      const float mu = za * ci - ya * si;
+      acc = fmaf(dtau * c, nu * (g.x * fmaf(beta * mu * mu, ir2, omb) + g.y * dX), acc);
     }
     // tracer surface brightness and the binning-after-PSF scatter
     const float Y2 = yp * yp;
@@ -276,11 +312,18 @@ __global__ void __launch_bounds__(SPH_THREADS) k_sph_los(const SysDev *__restric
 
 size_t sph_grid_smem(int mg, int nl) { return (size_t)mg * (sizeof(float4) + sizeof(float)) + (size_t)nl * sizeof(float4); }
 
+// paired grid, tracer and surface-brightness coefficients, bin accumulators
+size_t sph_los_smem(int g4, int nl, int nb) {
+  return (size_t)(g4 + 2 * nl) * sizeof(float4) + (size_t)2 * nb * sizeof(float);
+}
+
 }  // namespace
 
 void set_sph_smem_limit() {
   cudaFuncSetAttribute(k_sph_grid, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)sph_grid_smem(GLAD_SPH_MAX_MG, GLAD_MAX_LIGHT));
+  cudaFuncSetAttribute(k_sph_los, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sph_los_smem(GLAD_SPH_MAX_GRID, GLAD_MAX_LIGHT, GLAD_MAX_BINS));
 }
 
 cudaError_t launch_sph_grid(glad_ctx *c, const int *sys_id, int B, cudaStream_t st) {
@@ -301,11 +344,16 @@ cudaError_t launch_sph_grid(glad_ctx *c, const int *sys_id, int B, cudaStream_t 
 }
 
 cudaError_t launch_sph_los(glad_ctx *c, const int *sys_id, int B, cudaStream_t st) {
-  int sub = 0;
+  int sub = 0, g4 = 0, nb = 0;
   for (auto &sd : c->h_sysdev)
-    if (sd.jam_align == 1) sub = std::max(sub, sd.n_sub);
+    if (sd.jam_align == 1) {
+      sub = std::max(sub, sd.n_sub);
+      g4 = std::max(g4, sd.sph_nr * (sd.sph_nw - 1));
+      nb = std::max(nb, sd.n_bins);
+    }
   if (sub == 0) return cudaSuccess;
-  k_sph_los<<<dim3((sub + SPH_THREADS - 1) / SPH_THREADS, B), SPH_THREADS, 0, st>>>(
+  k_sph_los<<<dim3((sub + SPH_THREADS - 1) / SPH_THREADS, B), SPH_THREADS,
+              sph_los_smem(g4, c->max_light, nb), st>>>(
       c->d_sys, sys_id, c->ws.d, c->max_light, c->max_sgrid, c->max_bins);
   return cudaGetLastError();
 }

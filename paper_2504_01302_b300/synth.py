@@ -212,7 +212,7 @@ def workload_systems(w: int, small: bool = False):
     3: 8 uneven systems, 1024 samples split multinomially
     4: IFU-scale (400^2 x3, 31^2 PSF, 40+2x20+BH, 128^2 sky x4, GL64, 400 bins), B=4096
     5: workload 1's system with the spherically aligned Jeans model (Eqs. J1/J2; polar
-       grid 96 x 8, 64 line-of-sight nodes), B=256
+       grid 128 x 8, 32 line-of-sight nodes), B=256
     """
     rng = np.random.Generator(np.random.PCG64(1000 + (1 if w == 5 else w)))
     if w == 0:
@@ -225,7 +225,7 @@ def workload_systems(w: int, small: bool = False):
                         n_light=10, n_gl=32, n_bins=50, bins="voronoi", rng=rng,
                         has_bh=True, n_sis=1, second_light=True)
         if w == 5:
-            s.update(name="w5", jam_align=1, sph_nr=96, sph_nw=8, sph_nlos=64)
+            s.update(name="w5", jam_align=1, sph_nr=128, sph_nw=8, sph_nlos=32)
         return [s], (64 if w == 2 else 256)
     if w == 3:
         systems = []

@@ -95,7 +95,7 @@ def test_degenerate_parameters(small, name, value):
 
 def test_default_rule_and_isotropic_limit_against_cylindrical():
     # same system, both alignments, beta = 0: the models coincide, so the GPU v_rms differ
-    # only by the spherical rule's discretisation (<= 5e-4 in Sigma v^2 on the default rule)
+    # only by the spherical rule's discretisation (<= 3e-4 in Sigma v^2 on the default rule)
     cyl = systems.small_system(7)
     sph = dict(cyl, jam_align=1)
     ctx = _ctx([cyl, sph])

@@ -133,7 +133,7 @@ def test_beta0_projection_matches_cylindrical_pair_form():
     m = jam_sph.SphModel(d["tr"], d["ms"], t[synth.IDX["inc"]], 0.0, d["v2u"])
     rule = model.sph_rule(dict(s, jam_align=1), d["tr"]["sig"], d["ms"]["sig"])
     got = jam_sph.sigma_v2_sph(X, Y, m, rule, jam_sph.grid_moments(m, rule))
-    # the default rule's discretisation error (5e-4 measured); it falls as n_r^-3.3
+    # the default rule's discretisation error (2.9e-4 measured); it falls as n_r^-3.3
     assert np.max(np.abs(got / ref - 1)) < 1e-3
 
 
