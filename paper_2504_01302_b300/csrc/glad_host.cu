@@ -139,6 +139,13 @@ glad_status validate(const glad_system_desc &d, int idx) {
     SUP((d.n_mge_mass + (d.has_bh ? 1 : 0)) * d.n_gl <= GLAD_SPH_MAX_MG,
         "mass Gaussians x n_gl > %d for the spherically aligned model", idx, GLAD_SPH_MAX_MG);
     SUP(d.sph_nlos <= 4096, "sph_nlos > 4096", idx);
+    // shared memory of the gradient kernels (grid adjoint: coefficients and their accumulators;
+    // line-of-sight adjoint: grid, grid adjoint and per-thread tracer accumulators)
+    const size_t mg = (size_t)(d.n_mge_mass + (d.has_bh ? 1 : 0)) * d.n_gl;
+    const size_t ladj = (size_t)nr * (nw - 1) * 16 + (size_t)nr * nw * 8 + (size_t)nl * (16 + 128 * 8);
+    const size_t gadj = mg * 40 + 8 * 64 * 16 + (size_t)nl * 24 + 16;
+    SUP(ladj <= 227 * 1024 && gadj <= 227 * 1024,
+        "spherically aligned model too large for the gradient kernels' shared memory", idx);
   }
 #undef SUP
   return GLAD_OK;
@@ -521,8 +528,15 @@ glad_status full_path(glad_ctx *c, const int *sys_id, const double *theta, int B
   // dynamics, high priority
   if (e == cudaSuccess) e = launch_dyn_tables(c, sys_id, B, dy);
   if (e == cudaSuccess) {
-    if (grad) e = GLAD_PROF(c, dy, KID_GRAD_JAM_FWD, launch_jam_fg(c, sys_id, B, dy));
-    else e = launch_dyn_sums(c, sys_id, B, dy);
+    if (!grad) {
+      e = launch_dyn_sums(c, sys_id, B, dy);
+    } else {
+      // the pair sum with its derivative moments; the spherically aligned model's forward sums
+      // (its adjoint recomputes what it needs)
+      if (c->n_cyl) e = GLAD_PROF(c, dy, KID_GRAD_JAM_FWD, launch_jam_fg(c, sys_id, B, dy));
+      if (e == cudaSuccess && c->n_sph)
+        e = GLAD_PROF(c, dy, KID_SPH_LOS, launch_sph_los(c, sys_id, B, dy));
+    }
   }
   if (e == cudaSuccess) e = GLAD_PROF(c, dy, KID_KIN, launch_kin_finalize(c, sys_id, B, nullptr, dy));
   if (e == cudaSuccess && grad) e = launch_grad_dyn(c, sys_id, theta, B, grad, dy);
@@ -540,7 +554,7 @@ glad_status full_path(glad_ctx *c, const int *sys_id, const double *theta, int B
 const char *kKernelNames[KID_N] = {
     "k_prep", "k_table", "k_image+k_conv", "k_jam", "k_kin_finalize", "k_combine",
     "k_grad_lens", "k_jam_fwd_grad", "k_jam_adjoint", "k_grad_chain", "k_sph_coef+k_sph_grid",
-    "k_sph_los"};
+    "k_sph_los", "k_sph_adjoint"};
 
 }  // namespace
 
@@ -694,6 +708,7 @@ glad_status glad_create(const glad_system_desc *sys, int n_sys, glad_ctx **out) 
   set_conv_smem_limit();
   set_grad_smem_limit();
   set_sph_smem_limit();
+  set_sph_grad_smem_limit();
   int prio_lo = 0, prio_hi = 0;
   cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
   if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
@@ -750,9 +765,6 @@ glad_status glad_loglike_grad(glad_ctx *c, const int *sys_id, const double *thet
   g_err.clear();
   if (!c || !sys_id || !theta || !logL || !grad || !sample_status || B < 1)
     return fail(GLAD_EINVAL, "glad_loglike_grad: bad arguments");
-  if (c->n_sph)
-    return fail(GLAD_EUNSUPPORTED,
-                "glad_loglike_grad: no gradient for the spherically aligned Jeans model");
   if (grad_ws_ensure(c, B) != cudaSuccess)
     return fail(GLAD_ENOMEM, "gradient workspace for B=%d does not fit", B);
   return full_path(c, sys_id, theta, B, (cudaStream_t)stream, logL, sample_status, terms, grad);

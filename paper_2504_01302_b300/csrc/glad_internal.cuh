@@ -188,7 +188,7 @@ struct glad_ctx {
 enum {
   KID_PREP = 0, KID_TABLE, KID_IMAGE_CONV, KID_JAM, KID_KIN, KID_COMBINE,
   KID_GRAD_LENS, KID_GRAD_JAM_FWD, KID_GRAD_JAM_ADJ, KID_GRAD_CHAIN, KID_SPH_GRID, KID_SPH_LOS,
-  KID_N
+  KID_GRAD_SPH, KID_N
 };
 
 // record an event pair around `call` when profiling is on
@@ -227,6 +227,9 @@ cudaError_t launch_combine(glad_ctx *c, int B, double *logL, int *status, double
 cudaError_t launch_sph_grid(glad_ctx *c, const int *sys_id, int B, cudaStream_t st);
 cudaError_t launch_sph_los(glad_ctx *c, const int *sys_id, int B, cudaStream_t st);
 void set_sph_smem_limit();
+// its adjoint (k_sph_grad.cu): line-of-sight and grid adjoints, carried to the JAM inputs
+cudaError_t launch_grad_sph(glad_ctx *c, const int *sys_id, int B, double *grad, cudaStream_t st);
+void set_sph_grad_smem_limit();
 // the dynamics sum of either model for the systems of the context (glad_host.cu): the
 // table/grid stage and the sky-point stage, each recorded under its kernel id
 cudaError_t launch_dyn_tables(glad_ctx *c, const int *sys_id, int B, cudaStream_t st);

@@ -19,23 +19,9 @@
 
 #include "dual.cuh"
 #include "glad_internal.cuh"
+#include "grad_ws.cuh"
 #include "jam_common.cuh"
 #include "lensmath.cuh"
-
-struct GradWs {
-  int B = 0;
-  float *resid = nullptr;    // [B*max_pix]  d logL / d m (blurred model)
-  float *gpix = nullptr;     // [B*max_pix]  d logL / d img (unblurred)
-  float4 *pt = nullptr;      // [B*max_sub]  V, dV/dX, dV/dY (X = x'^2, Y = y'^2)
-  float4 *adjpt = nullptr;   // [B*max_apts*2] (X, X, Y, Y), (XY, XY, g_N, g_N), 16x16-tile order
-  double *entadj = nullptr;  // [B*max_ent*3] d logL / d (Q0, Q1, a_y)
-  double *adjI0 = nullptr;   // [B*max_light] d logL / d I0_k (tracer amplitudes)
-  // per sample, the table adjoint carried to the per-Gaussian JAM inputs: d logL / d nu0_k,
-  // c0_k [max_light each], C_j, e2_j [max_mass_tot each], sin^2 i, cos^2 i, b [3]
-  double *tadj = nullptr;    // [B*tstride]
-  int tstride = 0;
-  std::vector<void *> allocs;
-};
 
 namespace {
 
@@ -262,7 +248,7 @@ __global__ void __launch_bounds__(JAM_THREADS, FG_MINB) k_jam_fg(const SysDev *_
   if (ws.status[b] != GLAD_SAMPLE_OK) return;
   const SysDev &S = sysv[sys_id[b]];
   const int tile = blockIdx.x;
-  if (tile >= jam_tiles(S.nsx, S.nsy, PTS)) return;
+  if (S.jam_align != 0 || tile >= jam_tiles(S.nsx, S.nsy, PTS)) return;
   __shared__ JamSmem sm;
   const int tid = threadIdx.x;
   const DynP dp = ws.dp[b];
@@ -625,7 +611,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_jam_adj(const SysDev *__restric
   if (ws.status[b] != GLAD_SAMPLE_OK) return;
   const SysDev &S = sysv[sys_id[b]];
   const int e0 = blockIdx.x * ADJ_THREADS * EPT;
-  if (e0 >= S.n_ent) return;
+  if (S.jam_align != 0 || e0 >= S.n_ent) return;
   __shared__ float4 pts[2][2 * ADJ_PCHUNK];
   const int tid = threadIdx.x;
   const DynP dp = ws.dp[b];
@@ -752,6 +738,7 @@ __global__ void __launch_bounds__(256) k_table_adj(const SysDev *__restrict__ sy
   const int b = blockIdx.y;
   if (ws.status[b] != GLAD_SAMPLE_OK) return;
   const SysDev &S = sysv[sys_id[b]];
+  if (S.jam_align != 0) return;  // the spherically aligned model has its own adjoint
   const int nMt = S.n_mass_tot;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int kj = blockIdx.x * 8 + warp;
@@ -825,11 +812,12 @@ __global__ void __launch_bounds__(256) k_grad_chain(const SysDev *__restrict__ s
   const int tid = threadIdx.x;
   __shared__ double a_nu0[GLAD_MAX_LIGHT], a_c0[GLAD_MAX_LIGHT];
   __shared__ double a_C[GLAD_MAX_MASS + 1], a_e2[GLAD_MAX_MASS + 1];
-  __shared__ double a_glob[3];
+  __shared__ double a_glob[4];
   __shared__ double gsm[GLAD_NTHETA];
   __shared__ double Ad[GLAD_MAX_LIGHT][10];  // light amplitudes with tangents (I_e, R_e in slots 3, 4)
   const int nL = S.n_light, nM = S.n_mass, nMt = S.n_mass_tot;
-  // (a) the table adjoint, carried to nu0_k, c0_k, C_j, e2_j, sin^2 i, cos^2 i, b by k_table_adj
+  // (a) the JAM adjoint, carried to nu0_k, c0_k, C_j, e2_j, sin^2 i, cos^2 i, b (and, for the
+  // spherically aligned model, the inclination directly) by k_table_adj or k_sph_coef_adj
   {
     const double *t = gw.tadj + (size_t)b * gw.tstride;
     const int ML = max_light, MM = max_mass;
@@ -841,7 +829,7 @@ __global__ void __launch_bounds__(256) k_grad_chain(const SysDev *__restrict__ s
       a_C[j] = t[2 * ML + j];
       a_e2[j] = t[2 * ML + MM + j];
     }
-    if (tid < 3) a_glob[tid] = t[2 * ML + 2 * MM + tid];
+    if (tid < 4) a_glob[tid] = t[2 * ML + 2 * MM + tid];
   }
   if (tid < GLAD_NTHETA) gsm[tid] = 0.0;
   __syncthreads();
@@ -962,7 +950,7 @@ __global__ void __launch_bounds__(256) k_grad_chain(const SysDev *__restrict__ s
       }
     }
     // globals: sin^2 i, cos^2 i (theta 15) and b = 1/(1-beta) (theta 16)
-    gsm[15] += a_glob[0] * S2.d[5] + a_glob[1] * C2.d[5];
+    gsm[15] += a_glob[0] * S2.d[5] + a_glob[1] * C2.d[5] + a_glob[3];
     const double bb = 1.0 / (1.0 - th[16]);
     gsm[16] += a_glob[2] * bb * bb;
   }
@@ -1018,8 +1006,12 @@ cudaError_t grad_ws_ensure(glad_ctx *c, int B) {
   const bool ok = galloc(w, w.resid, b * c->max_pix) && galloc(w, w.gpix, b * c->max_pix) &&
                   galloc(w, w.pt, b * c->max_sub) && galloc(w, w.adjpt, 2 * b * c->max_apts) &&
                   galloc(w, w.entadj, b * c->max_ent * 3) && galloc(w, w.adjI0, b * c->max_light);
-  w.tstride = 2 * c->max_light + 2 * c->max_mass_tot + 3;
-  const bool ok2 = ok && galloc(w, w.tadj, b * w.tstride);
+  w.tstride = 2 * c->max_light + 2 * c->max_mass_tot + 4;
+  w.sph_cta = (c->max_sgrid + SPH_GADJ_PTS - 1) / SPH_GADJ_PTS;
+  const size_t nc = b * w.sph_cta;
+  const bool ok2 = ok && galloc(w, w.tadj, b * w.tstride) && galloc(w, w.sgadj, b * c->max_sgrid) &&
+                   galloc(w, w.scoef, nc * c->max_smg * SPH_GADJ_NQ) &&
+                   galloc(w, w.strc, nc * c->max_light * 2) && galloc(w, w.sbeta, nc);
   if (!ok2) {
     grad_ws_free(c);
     return cudaErrorMemoryAllocation;
@@ -1047,6 +1039,12 @@ cudaError_t grad_prepare(glad_ctx *c, int B, double *grad, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaMemsetAsync(g.tadj, 0, sizeof(double) * g.tstride * (size_t)B, st);
   // tile padding beyond the sky grid must read as g_N = 0
   if (e == cudaSuccess) e = cudaMemsetAsync(g.adjpt, 0, sizeof(float4) * 2 * c->max_apts * (size_t)B, st);
+  if (c->n_sph) {
+    // samples of the spherically aligned model leave dV/dX, dV/dY at zero for k_kin_adj (their
+    // point-coordinate terms come from k_sph_los_adj); their grid adjoint starts at zero
+    if (e == cudaSuccess) e = cudaMemsetAsync(g.pt, 0, sizeof(float4) * c->max_sub * (size_t)B, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g.sgadj, 0, sizeof(float2) * c->max_sgrid * (size_t)B, st);
+  }
   return e;
 }
 
@@ -1080,7 +1078,11 @@ cudaError_t launch_grad_dyn(glad_ctx *c, const int *sys_id, const double *theta,
       c->d_sys, sys_id, c->ws.d, g, c->max_light, c->max_bins, c->max_sub, c->max_apts, grad);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = GLAD_PROF(c, st, KID_GRAD_JAM_ADJ, ([&]() -> cudaError_t {
+  if (c->n_sph) {
+    e = GLAD_PROF(c, st, KID_GRAD_SPH, launch_grad_sph(c, sys_id, B, grad, st));
+    if (e != cudaSuccess) return e;
+  }
+  if (c->n_cyl) e = GLAD_PROF(c, st, KID_GRAD_JAM_ADJ, ([&]() -> cudaError_t {
     const int ept = c->tune.adj_ept;
     const int nb = (c->max_ent + ADJ_THREADS * ept - 1) / (ADJ_THREADS * ept);
     if (ept == 2)
@@ -1095,10 +1097,12 @@ cudaError_t launch_grad_dyn(glad_ctx *c, const int *sys_id, const double *theta,
   return GLAD_PROF(c, st, KID_GRAD_CHAIN, ([&]() -> cudaError_t {
     int pairs = 0;
     for (auto &sd : c->h_sysdev) pairs = std::max(pairs, sd.n_light * sd.n_mass_tot);
-    k_table_adj<<<dim3((pairs + 7) / 8, B), 256, 0, st>>>(c->d_sys, sys_id, c->ws.d, g, c->max_light,
-                                                         c->max_mass_tot, c->max_ent);
-    cudaError_t r0 = cudaGetLastError();
-    if (r0 != cudaSuccess) return r0;
+    if (c->n_cyl) {
+      k_table_adj<<<dim3((pairs + 7) / 8, B), 256, 0, st>>>(c->d_sys, sys_id, c->ws.d, g,
+                                                           c->max_light, c->max_mass_tot, c->max_ent);
+      cudaError_t r0 = cudaGetLastError();
+      if (r0 != cudaSuccess) return r0;
+    }
     k_grad_chain<<<B, 256, 0, st>>>(c->d_sys, sys_id, theta, c->ws.d, g, c->max_light,
                                     c->max_mass_tot, c->max_ent, grad);
     return cudaGetLastError();

@@ -125,12 +125,44 @@ def test_mixed_alignments_in_one_batch(small):
         one.close()
 
 
-def test_gradient_is_refused(small):
-    from paper_2504_01302_b300 import _lib
+def test_gradient_matches_oracle_fd(small):
+    # every component against FP64 central differences of the oracle (same rule)
+    from .test_gpu_grad import assert_grad_close
     s, ctx = small
-    with pytest.raises(_lib.GladError) as ei:
-        ctx.loglike_grad(_th(systems.near_truth_thetas(1, seed=85)))
-    assert "status 5" in str(ei.value)
+    th = systems.near_truth_thetas(2, seed=85)
+    logL, grad, st = ctx.loglike_grad(_th(th))
+    assert np.all(st.cpu().numpy() == 0)
+    grad = grad.cpu().numpy()
+    for b in range(len(th)):
+        assert_grad_close(grad[b], model.grad_fd(th[b], s))
+
+
+def test_gradient_prior_draw_and_logl(small):
+    from .test_gpu_grad import assert_grad_close
+    s, ctx = small
+    pri = systems.prior_thetas(16, seed=89)
+    th = next(t for t in pri if model.check_domain(t) and model.dynamics_setup(t, s)[0] == 0)
+    l1, grad, st = ctx.loglike_grad(_th(th[None]))
+    l0, _ = ctx.loglike(_th(th[None]))
+    assert int(st[0]) == 0 and abs(float(l1[0]) - float(l0[0])) <= 1e-9 * abs(float(l0[0]))
+    assert_grad_close(grad.cpu().numpy()[0], model.grad_fd(th, s))
+
+
+def test_gradient_mixed_alignments(small):
+    s, _ = small
+    cyl = systems.small_system(7)
+    ctx = _ctx([cyl, s])
+    th = systems.near_truth_thetas(4, seed=91)
+    ids = [1, 0, 1, 0]
+    _, g, st = ctx.loglike_grad(_th(th), torch.as_tensor(np.array(ids, np.int32), device="cuda"))
+    assert np.all(st.cpu().numpy() == 0)
+    g = g.cpu().numpy()
+    for b, i in enumerate(ids):
+        one = _ctx([[cyl, s][i]])
+        _, g1, _ = one.loglike_grad(_th(th[b:b + 1]))
+        g1 = g1.cpu().numpy()[0]
+        assert np.allclose(g[b], g1, rtol=1e-4, atol=1e-4 * np.max(np.abs(g1))), (b, g[b], g1)
+        one.close()
 
 
 @pytest.fixture(scope="module")
