@@ -142,7 +142,7 @@ glad_status validate(const glad_system_desc &d, int idx) {
     // shared memory of the gradient kernels (grid adjoint: coefficients and their accumulators;
     // line-of-sight adjoint: grid, grid adjoint and per-thread tracer accumulators)
     const size_t mg = (size_t)(d.n_mge_mass + (d.has_bh ? 1 : 0)) * d.n_gl;
-    const size_t ladj = (size_t)nr * (nw - 1) * 16 + (size_t)nr * nw * 8 + (size_t)nl * (16 + 128 * 8);
+    const size_t ladj = (size_t)nr * (nw - 1) * 16 + (size_t)nr * (nw | 1) * 8 + (size_t)nl * (16 + 128 * 8);
     const size_t gadj = mg * 40 + 8 * 64 * 16 + (size_t)nl * 24 + 16;
     SUP(ladj <= 227 * 1024 && gadj <= 227 * 1024,
         "spherically aligned model too large for the gradient kernels' shared memory", idx);

@@ -3,8 +3,8 @@
 // inputs (nu0_k, c0_k, C_j, e2_j) that k_grad_chain carries to theta, plus beta (as
 // b = 1/(1 - beta)), the inclination (directly) and the sky-frame terms (x_c, y_c, phi).
 //
-//  k_sph_los_adj: per sky sub-sample, with g_N = d logL / d(Sigma v^2) from k_kin_adj, the
-//    line-of-sight rule again: reverse mode into the grid values (v_r^2, d) of the stencil
+//  k_sph_los_adj: per sky sub-sample (one warp, lanes over its nodes), with g_N = d logL /
+//    d(Sigma v^2) from k_kin_adj, the line-of-sight rule again: reverse mode into the grid values (v_r^2, d) of the stencil
 //    cells and into the tracer inputs nu0_k, c0_k; forward mode (4 tangents) through the
 //    node geometry for x', y' (then x_c, y_c, phi), sin i and cos i; beta explicitly.
 //  k_sph_grid_adj: per polar grid point (one warp), with the grid adjoint: phase 1 (lanes
@@ -23,6 +23,7 @@
 namespace {
 
 #define SPH_LADJ_THREADS 128
+#define SPH_LADJ_PPW 8  // sky sub-samples per warp in the line-of-sight adjoint
 #define SPH_PIECES 16
 constexpr float LN2F = 0.6931471805599453f;
 
@@ -46,9 +47,11 @@ struct LosPt {
 // one line-of-sight node z' = zs (derivative dzs_dc with respect to the node scale c, which
 // depends on x', y' through dc_dxp, dc_dyp) of weight wt (dwt_dc): adds the tangents
 // A[0..3] = d/d(x', y', sin i, cos i) and A[4] = d/d beta of g_N wt f, and scatters the
-// reverse-mode adjoints of the grid cells and of the tracer inputs into shared memory
-__device__ __forceinline__ void los_node_adj(const LosPt &q, const float4 *g4, float2 *gadj,
-                                             const float4 *trc, float2 *tacc, int tid, float zs,
+// reverse-mode adjoints of the grid cells (gax, gay: rows of gst words, gst odd so that
+// different rows fall in different banks) and of the tracer inputs into shared memory
+__device__ __forceinline__ void los_node_adj(const LosPt &q, const float4 *g4, float *gax,
+                                             float *gay, int gst, const float4 *trc, float2 *tacc,
+                                             int tid, float zs,
                                              float dzs_dc, float wt, float dwt_dc, float dc_dxp,
                                              float dc_dyp, float *A) {
   const float dzx = dzs_dc * dc_dxp, dzy = dzs_dc * dc_dyp;
@@ -114,12 +117,12 @@ __device__ __forceinline__ void los_node_adj(const LosPt &q, const float4 *g4, f
   const float av = w_g * nu * fmaf(q.beta, m2, q.omb), ad = w_g * nu * q.s2 * q.X2;
 #pragma unroll
   for (int o = 0; o < 4; ++o) {
-    float2 *p = gadj + (i0 + o) * q.nw + c0;
+    const int cell = (i0 + o) * gst + c0;
     const float lu = L[o] * uc, lt = L[o] * tc;
-    atomicAdd(&p[0].x, lu * av);
-    atomicAdd(&p[0].y, lu * ad);
-    atomicAdd(&p[1].x, lt * av);
-    atomicAdd(&p[1].y, lt * ad);
+    atomicAdd(&gax[cell], lu * av);
+    atomicAdd(&gay[cell], lu * ad);
+    atomicAdd(&gax[cell + 1], lt * av);
+    atomicAdd(&gay[cell + 1], lt * ad);
   }
   // forward tangents
   const float f = nu * Bk;
@@ -139,22 +142,26 @@ __device__ __forceinline__ void los_node_adj(const LosPt &q, const float4 *g4, f
   A[4] = fmaf(w_g * nu, g.x * (m2 - 1.f), A[4]);
 }
 
-__global__ void __launch_bounds__(SPH_LADJ_THREADS) k_sph_los_adj(
+// One warp per sky sub-sample (lanes over its line-of-sight nodes, so that a warp's grid
+// cells differ: the nodes lie at different radii), SPH_LADJ_PPW sub-samples per warp.
+__global__ void __launch_bounds__(SPH_LADJ_THREADS, 6) k_sph_los_adj(
     const SysDev *__restrict__ sysv, const int *__restrict__ sys_id, WsDev ws, GradWs gw,
     int max_light, int max_mass, int max_sgrid, int max_apts, double *grad) {
   const int b = blockIdx.y;
   if (ws.status[b] != GLAD_SAMPLE_OK) return;
   const SysDev &S = sysv[sys_id[b]];
   if (S.jam_align != 1) return;
-  const int nblk = (S.n_sub + SPH_LADJ_THREADS - 1) / SPH_LADJ_THREADS;
-  if ((int)blockIdx.x >= nblk) return;
+  constexpr int PPC = SPH_LADJ_PPW * (SPH_LADJ_THREADS / 32);  // sub-samples per CTA
+  if ((int)blockIdx.x * PPC >= S.n_sub) return;
   extern __shared__ float4 ladj_smem[];
-  const int tid = threadIdx.x;
-  const int nr = S.sph_nr, nw = S.sph_nw, nwm = nw - 1, nL = S.n_light;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nr = S.sph_nr, nw = S.sph_nw, nwm = nw - 1, nL = S.n_light, ng = nr * nw;
+  const int gst = nw | 1;                     // odd row stride of the grid adjoint
   float4 *g4 = ladj_smem;                     // [nr * nwm]
   float4 *trc = g4 + nr * nwm;                // [nL]
-  float2 *gadj = (float2 *)(trc + nL);        // [nr * nw]
-  float2 *tacc = gadj + nr * nw;              // [nL * SPH_LADJ_THREADS]
+  float2 *tacc = (float2 *)(trc + nL);        // [nL * SPH_LADJ_THREADS]
+  float *gax = (float *)(tacc + nL * SPH_LADJ_THREADS);  // [nr * gst]: d/d v_r^2
+  float *gay = gax + nr * gst;                // [nr * gst]: d/d d
   __shared__ double red[SPH_LADJ_THREADS / 32][6];
   const float2 *gsrc = ws.sgrid + (size_t)b * max_sgrid;
   for (int i = tid; i < nr * nwm; i += SPH_LADJ_THREADS) {
@@ -162,75 +169,90 @@ __global__ void __launch_bounds__(SPH_LADJ_THREADS) k_sph_los_adj(
     const float2 u = gsrc[a * nw + c], v = gsrc[a * nw + c + 1];
     g4[i] = make_float4(u.x, u.y, v.x, v.y);
   }
-  for (int i = tid; i < nr * nw; i += SPH_LADJ_THREADS) gadj[i] = make_float2(0.f, 0.f);
+  for (int i = tid; i < 2 * nr * gst; i += SPH_LADJ_THREADS) gax[i] = 0.f;
   for (int k = tid; k < nL; k += SPH_LADJ_THREADS) trc[k] = ws.sph_tr[(size_t)b * max_light + k];
   for (int i = tid; i < nL * SPH_LADJ_THREADS; i += SPH_LADJ_THREADS) tacc[i] = make_float2(0.f, 0.f);
   __syncthreads();
   const DynP dp = ws.dp[b];
-  float A[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  float gphi = 0.f, gxc = 0.f, gyc = 0.f;
-  // points strided over the sky, so that a warp's points (and their grid cells) differ
-  const int s = blockIdx.x + nblk * tid;
-  if (s < S.n_sub) {
+  const float cphi = (float)dp.cphi, sphi = (float)dp.sphi;
+  LosPt q;
+  q.si = (float)sqrt(dp.s2);
+  q.ci = (float)sqrt(dp.c2);
+  q.s2 = (float)dp.s2;
+  q.beta = (float)(1.0 - 1.0 / dp.b);
+  q.omb = 1.f - q.beta;
+  q.lr0 = (float)S.sph_lr0;
+  q.idlr = (float)(1.0 / S.sph_dlr);
+  q.nr = nr;
+  q.nw = nw;
+  q.nwm = nwm;
+  q.nL = nL;
+  const float r_lo = (float)S.sph_r_lo, r_end = (float)S.sph_r_end;
+  const int n = S.sph_nlos;
+  const float inv_n = 1.0f / (float)n;
+  // per-warp sums (lane 0 keeps them): d/d inc, d/d beta, phi, x_c, y_c
+  double wsum[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  // the warp's g_N, loaded up front (lane p holds point p's)
+  float gN_l = 0.f;
+  {
+    const int s = blockIdx.x * PPC + warp * SPH_LADJ_PPW + lane;
+    if (lane < SPH_LADJ_PPW && s < S.n_sub) {
+      const int I = s / S.nsx, J = s - I * S.nsx;
+      const size_t pos = (size_t)b * max_apts + (size_t)((I >> 4) * S.atx + (J >> 4)) * 256 +
+                         (I & 15) * 16 + (J & 15);
+      gN_l = gw.adjpt[2 * pos + 1].z;
+    }
+  }
+  for (int p = 0; p < SPH_LADJ_PPW; ++p) {
+    const int s = blockIdx.x * PPC + warp * SPH_LADJ_PPW + p;
+    if (s >= S.n_sub) break;  // warp-uniform
     const int I = s / S.nsx, J = s - I * S.nsx;
-    const size_t pos = (size_t)b * max_apts + (size_t)((I >> 4) * S.atx + (J >> 4)) * 256 +
-                       (I & 15) * 16 + (J & 15);
-    LosPt q;
-    q.gN = gw.adjpt[2 * pos + 1].z;
-    const float cphi = (float)dp.cphi, sphi = (float)dp.sphi;
+    q.gN = __shfl_sync(0xffffffffu, gN_l, p);
+    if (q.gN == 0.f) continue;
     const float x = (J - 0.5f * (S.nsx - 1)) * S.dsub - (float)dp.xc;
     const float y = (I - 0.5f * (S.nsy - 1)) * S.dsub - (float)dp.yc;
     q.xp = cphi * x + sphi * y;
     q.yp = -sphi * x + cphi * y;
     q.X2 = q.xp * q.xp;
-    q.si = (float)sqrt(dp.s2);
-    q.ci = (float)sqrt(dp.c2);
-    q.s2 = (float)dp.s2;
-    q.beta = (float)(1.0 - 1.0 / dp.b);
-    q.omb = 1.f - q.beta;
-    q.lr0 = (float)S.sph_lr0;
-    q.idlr = (float)(1.0 / S.sph_dlr);
-    q.nr = nr;
-    q.nw = nw;
-    q.nwm = nwm;
-    q.nL = nL;
-    if (q.gN != 0.f) {
-      const float r_lo = (float)S.sph_r_lo, r_end = (float)S.sph_r_end;
-      const float rho = sqrtf(q.X2 + q.yp * q.yp);
-      const bool act = rho > r_lo;
-      const float c = act ? rho : r_lo;
-      const float dc_dxp = act ? q.xp / rho : 0.f, dc_dyp = act ? q.yp / rho : 0.f;
-      const float qq = r_end / c;
-      const float tm = asinhf(qq);
-      const float dtm_dc = -qq / (c * sqrtf(1.f + qq * qq));
-      const int n = S.sph_nlos;
-      const float inv_n = 1.0f / (float)n;
-      for (int i = 0; i < (n + 1) / 2; ++i) {
-        const float kap = (float)(2 * i + 1 - n) * inv_n;
-        const float tau = kap * tm;
-        const float et = ex2f_(tau * 1.4426950408889634f), eti = __fdividef(1.0f, et);
-        const float sh = 0.5f * (et - eti), ch = 0.5f * (et + eti);
-        const float zp = c * sh;
-        const float wt = 2.f * tm * inv_n * c * ch;
-        const float dzp_dc = sh + c * ch * kap * dtm_dc;
-        const float dwt_dc = 2.f * inv_n * (dtm_dc * c * ch + tm * ch + tm * c * sh * kap * dtm_dc);
-        los_node_adj(q, g4, gadj, trc, tacc, tid, zp, dzp_dc, wt, dwt_dc, dc_dxp, dc_dyp, A);
-        if (2 * i + 1 != n)  // the mirrored node -z' (the middle node of an odd n has none)
-          los_node_adj(q, g4, gadj, trc, tacc, tid, -zp, -dzp_dc, wt, dwt_dc, dc_dxp, dc_dyp, A);
-      }
+    const float rho = sqrtf(q.X2 + q.yp * q.yp);
+    const bool act = rho > r_lo;
+    const float c = act ? rho : r_lo;
+    const float dc_dxp = act ? q.xp / rho : 0.f, dc_dyp = act ? q.yp / rho : 0.f;
+    const float qq = r_end / c;
+    const float tm = asinhf(qq);
+    const float dtm_dc = -qq / (c * sqrtf(1.f + qq * qq));
+    float A[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int j = lane; j < n; j += 32) {
+      const float kap = (float)(2 * j + 1 - n) * inv_n;
+      const float tau = kap * tm;
+      const float et = ex2f_(tau * 1.4426950408889634f), eti = __fdividef(1.0f, et);
+      const float sh = 0.5f * (et - eti), ch = 0.5f * (et + eti);
+      const float wt = 2.f * tm * inv_n * c * ch;
+      const float dzp_dc = sh + c * ch * kap * dtm_dc;
+      const float dwt_dc = 2.f * inv_n * (dtm_dc * c * ch + tm * ch + tm * c * sh * kap * dtm_dc);
+      los_node_adj(q, g4, gax, gay, gst, trc, tacc, tid, c * sh, dzp_dc, wt, dwt_dc, dc_dxp, dc_dyp, A);
+    }
+    for (int i = 0; i < 5; ++i)
+      for (int off = 16; off > 0; off >>= 1) A[i] += __shfl_xor_sync(0xffffffffu, A[i], off);
+    if (lane == 0) {
       // x' = c x + s y, y' = -s x + c y with (x, y) = sky - centre
-      gphi = A[0] * q.yp - A[1] * q.xp;
-      gxc = -A[0] * cphi + A[1] * sphi;
-      gyc = -A[0] * sphi - A[1] * cphi;
+      wsum[0] += (double)A[2] * q.ci - (double)A[3] * q.si;
+      wsum[1] += A[4];
+      wsum[2] += A[0] * q.yp - A[1] * q.xp;
+      wsum[3] += -A[0] * cphi + A[1] * sphi;
+      wsum[4] += -A[0] * sphi - A[1] * cphi;
     }
   }
+  if (lane == 0)
+    for (int i = 0; i < 5; ++i) red[warp][i] = wsum[i];
   __syncthreads();
   // grid adjoint to global, tracer adjoints summed over the CTA's threads
   float2 *gg = gw.sgadj + (size_t)b * max_sgrid;
-  for (int i = tid; i < nr * nw; i += SPH_LADJ_THREADS) {
-    const float2 v = gadj[i];
-    if (v.x != 0.f) atomicAdd(&gg[i].x, v.x);
-    if (v.y != 0.f) atomicAdd(&gg[i].y, v.y);
+  for (int i = tid; i < ng; i += SPH_LADJ_THREADS) {
+    const int a = i / nw, cell = a * gst + (i - a * nw);
+    const float vx = gax[cell], vy = gay[cell];
+    if (vx != 0.f) atomicAdd(&gg[i].x, vx);
+    if (vy != 0.f) atomicAdd(&gg[i].y, vy);
   }
   double *t = gw.tadj + (size_t)b * gw.tstride;
   for (int k = tid; k < nL; k += SPH_LADJ_THREADS) {
@@ -243,27 +265,16 @@ __global__ void __launch_bounds__(SPH_LADJ_THREADS) k_sph_los_adj(
     if (a0 != 0.0) atomicAdd(&t[k], a0);
     if (a1 != 0.0) atomicAdd(&t[max_light + k], a1);
   }
-  // d/d inc = d/d sin i cos i - d/d cos i sin i; beta, phi, x_c, y_c
-  {
-    const float si = (float)sqrt(dp.s2), ci = (float)sqrt(dp.c2);
-    double v[6] = {(double)A[2] * ci - (double)A[3] * si, (double)A[4], gphi, gxc, gyc, 0.0};
-    const int lane = tid & 31, warp = tid >> 5;
-    for (int i = 0; i < 5; ++i)
-      for (int off = 16; off > 0; off >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], off);
-    if (lane == 0)
-      for (int i = 0; i < 5; ++i) red[warp][i] = v[i];
-    __syncthreads();
-    if (tid < 5) {
-      double sum = 0.0;
-      for (int w = 0; w < SPH_LADJ_THREADS / 32; ++w) sum += red[w][tid];
-      if (sum != 0.0) {
-        const int base = 2 * max_light + 2 * max_mass;
-        if (tid == 0) atomicAdd(&t[base + 3], sum);                        // inclination
-        if (tid == 1) atomicAdd(&t[base + 2], sum / (dp.b * dp.b));       // b = 1/(1-beta)
-        if (tid == 2) atomicAdd(&grad[(size_t)GLAD_NTHETA * b + 3], sum);  // phi
-        if (tid == 3) atomicAdd(&grad[(size_t)GLAD_NTHETA * b + 4], sum);  // x_c
-        if (tid == 4) atomicAdd(&grad[(size_t)GLAD_NTHETA * b + 5], sum);  // y_c
-      }
+  if (tid < 5) {
+    double sum = 0.0;
+    for (int w = 0; w < SPH_LADJ_THREADS / 32; ++w) sum += red[w][tid];
+    if (sum != 0.0) {
+      const int base = 2 * max_light + 2 * max_mass;
+      if (tid == 0) atomicAdd(&t[base + 3], sum);                        // inclination
+      if (tid == 1) atomicAdd(&t[base + 2], sum / (dp.b * dp.b));       // b = 1/(1-beta)
+      if (tid == 2) atomicAdd(&grad[(size_t)GLAD_NTHETA * b + 3], sum);  // phi
+      if (tid == 3) atomicAdd(&grad[(size_t)GLAD_NTHETA * b + 4], sum);  // x_c
+      if (tid == 4) atomicAdd(&grad[(size_t)GLAD_NTHETA * b + 5], sum);  // y_c
     }
   }
 }
@@ -530,7 +541,7 @@ __global__ void k_sph_coef_adj(const SysDev *__restrict__ sysv, const int *__res
 }
 
 size_t sph_ladj_smem(int g4, int g, int nl) {
-  return (size_t)(g4 + nl) * sizeof(float4) + (size_t)g * sizeof(float2) +
+  return (size_t)(g4 + nl) * sizeof(float4) + (size_t)2 * g * sizeof(float) +
          (size_t)nl * SPH_LADJ_THREADS * sizeof(float2);
 }
 
@@ -544,16 +555,18 @@ void set_sph_grad_smem_limit() {
 
 cudaError_t launch_grad_sph(glad_ctx *c, const int *sys_id, int B, double *grad, cudaStream_t st) {
   GradWs &g = *c->gws;
-  int blk = 0, g4 = 0, gp = 0, mg = 0;
+  int blk = 0, g4 = 0, gp = 0, ga = 0, mg = 0;
   for (auto &sd : c->h_sysdev)
     if (sd.jam_align == 1) {
-      blk = std::max(blk, (sd.n_sub + SPH_LADJ_THREADS - 1) / SPH_LADJ_THREADS);
+      const int ppc = SPH_LADJ_PPW * (SPH_LADJ_THREADS / 32);
+      blk = std::max(blk, (sd.n_sub + ppc - 1) / ppc);
       g4 = std::max(g4, sd.sph_nr * (sd.sph_nw - 1));
       gp = std::max(gp, sd.sph_nr * sd.sph_nw);
+      ga = std::max(ga, sd.sph_nr * (sd.sph_nw | 1));
       mg = std::max(mg, sd.n_mass_tot * sd.n_gl);
     }
   if (blk == 0) return cudaSuccess;
-  k_sph_los_adj<<<dim3(blk, B), SPH_LADJ_THREADS, sph_ladj_smem(g4, gp, c->max_light), st>>>(
+  k_sph_los_adj<<<dim3(blk, B), SPH_LADJ_THREADS, sph_ladj_smem(g4, ga, c->max_light), st>>>(
       c->d_sys, sys_id, c->ws.d, g, c->max_light, c->max_mass_tot, c->max_sgrid, c->max_apts, grad);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
