@@ -23,7 +23,10 @@
 namespace {
 
 #define SPH_LADJ_THREADS 128
-#define SPH_LADJ_PPW 8  // sky sub-samples per warp in the line-of-sight adjoint
+#define SPH_LADJ_PPW 16  // consecutive sky sub-samples per warp in the line-of-sight adjoint
+#ifndef SPH_LADJ_MINB
+#define SPH_LADJ_MINB 5  // resident CTAs per SM asked of the register allocator
+#endif
 #define SPH_PIECES 16
 constexpr float LN2F = 0.6931471805599453f;
 
@@ -39,6 +42,25 @@ __constant__ float kAdjGLx[4] = {0.069431844202973712f, 0.33000947820757187f,
 __constant__ float kAdjGLw[4] = {0.17392742256872693f, 0.32607257743127307f,
                                  0.32607257743127307f, 0.17392742256872693f};
 
+// a lane's pending grid-adjoint contributions for one stencil position (cell = i0 * gst + c0):
+// v[4 o + {0, 1, 2, 3}] = (v_r^2 at c0, d at c0, v_r^2 at c0 + 1, d at c0 + 1) of row i0 + o
+struct GRun {
+  int cell;
+  float v[16];
+};
+
+__device__ __forceinline__ void grun_flush(GRun &r, float *gax, float *gay, int gst) {
+  if (r.cell < 0) return;
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    const int cell = r.cell + o * gst;
+    if (r.v[4 * o] != 0.f) atomicAdd(&gax[cell], r.v[4 * o]);
+    if (r.v[4 * o + 1] != 0.f) atomicAdd(&gay[cell], r.v[4 * o + 1]);
+    if (r.v[4 * o + 2] != 0.f) atomicAdd(&gax[cell + 1], r.v[4 * o + 2]);
+    if (r.v[4 * o + 3] != 0.f) atomicAdd(&gay[cell + 1], r.v[4 * o + 3]);
+  }
+}
+
 struct LosPt {
   float xp, yp, X2, si, ci, s2, beta, omb, lr0, idlr, gN;
   int nr, nw, nwm, nL;
@@ -46,12 +68,13 @@ struct LosPt {
 
 // one line-of-sight node z' = zs (derivative dzs_dc with respect to the node scale c, which
 // depends on x', y' through dc_dxp, dc_dyp) of weight wt (dwt_dc): adds the tangents
-// A[0..3] = d/d(x', y', sin i, cos i) and A[4] = d/d beta of g_N wt f, and scatters the
-// reverse-mode adjoints of the grid cells (gax, gay: rows of gst words, gst odd so that
-// different rows fall in different banks) and of the tracer inputs into shared memory
+// A[0..3] = d/d(x', y', sin i, cos i) and A[4] = d/d beta of g_N wt f, and adds the
+// reverse-mode adjoints of the grid cells to the lane's pending run (flushed into gax, gay,
+// rows of gst words with gst odd so that different rows fall in different banks, whenever
+// the stencil moves) and those of the tracer inputs into shared memory
 __device__ __forceinline__ void los_node_adj(const LosPt &q, const float4 *g4, float *gax,
-                                             float *gay, int gst, const float4 *trc, float2 *tacc,
-                                             int tid, float zs,
+                                             float *gay, int gst, GRun &run, const float4 *trc,
+                                             float2 *tacc, int tid, float zs,
                                              float dzs_dc, float wt, float dwt_dc, float dc_dxp,
                                              float dc_dyp, float *A) {
   const float dzx = dzs_dc * dc_dxp, dzy = dzs_dc * dc_dyp;
@@ -115,14 +138,20 @@ __device__ __forceinline__ void los_node_adj(const LosPt &q, const float4 *g4, f
   }
   // reverse: the 8 stencil cells
   const float av = w_g * nu * fmaf(q.beta, m2, q.omb), ad = w_g * nu * q.s2 * q.X2;
+  const int base = i0 * gst + c0;
+  if (base != run.cell) {
+    grun_flush(run, gax, gay, gst);
+    run.cell = base;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) run.v[i] = 0.f;
+  }
 #pragma unroll
   for (int o = 0; o < 4; ++o) {
-    const int cell = (i0 + o) * gst + c0;
     const float lu = L[o] * uc, lt = L[o] * tc;
-    atomicAdd(&gax[cell], lu * av);
-    atomicAdd(&gay[cell], lu * ad);
-    atomicAdd(&gax[cell + 1], lt * av);
-    atomicAdd(&gay[cell + 1], lt * ad);
+    run.v[4 * o] = fmaf(lu, av, run.v[4 * o]);
+    run.v[4 * o + 1] = fmaf(lu, ad, run.v[4 * o + 1]);
+    run.v[4 * o + 2] = fmaf(lt, av, run.v[4 * o + 2]);
+    run.v[4 * o + 3] = fmaf(lt, ad, run.v[4 * o + 3]);
   }
   // forward tangents
   const float f = nu * Bk;
@@ -143,8 +172,10 @@ __device__ __forceinline__ void los_node_adj(const LosPt &q, const float4 *g4, f
 }
 
 // One warp per sky sub-sample (lanes over its line-of-sight nodes, so that a warp's grid
-// cells differ: the nodes lie at different radii), SPH_LADJ_PPW sub-samples per warp.
-__global__ void __launch_bounds__(SPH_LADJ_THREADS, 6) k_sph_los_adj(
+// cells differ: the nodes lie at different radii), SPH_LADJ_PPW consecutive sub-samples per
+// warp: a lane's node keeps its stencil cells from one sub-sample to the next, so its grid
+// adjoint is summed in registers and reaches shared memory only when the stencil moves.
+__global__ void __launch_bounds__(SPH_LADJ_THREADS, SPH_LADJ_MINB) k_sph_los_adj(
     const SysDev *__restrict__ sysv, const int *__restrict__ sys_id, WsDev ws, GradWs gw,
     int max_light, int max_mass, int max_sgrid, int max_apts, double *grad) {
   const int b = blockIdx.y;
@@ -203,6 +234,10 @@ __global__ void __launch_bounds__(SPH_LADJ_THREADS, 6) k_sph_los_adj(
       gN_l = gw.adjpt[2 * pos + 1].z;
     }
   }
+  // the pending run of the lane's first node slot (node = lane); further slots (n_los > 32)
+  // scatter at once
+  GRun run0, runx;
+  run0.cell = runx.cell = -1;
   for (int p = 0; p < SPH_LADJ_PPW; ++p) {
     const int s = blockIdx.x * PPC + warp * SPH_LADJ_PPW + p;
     if (s >= S.n_sub) break;  // warp-uniform
@@ -230,7 +265,15 @@ __global__ void __launch_bounds__(SPH_LADJ_THREADS, 6) k_sph_los_adj(
       const float wt = 2.f * tm * inv_n * c * ch;
       const float dzp_dc = sh + c * ch * kap * dtm_dc;
       const float dwt_dc = 2.f * inv_n * (dtm_dc * c * ch + tm * ch + tm * c * sh * kap * dtm_dc);
-      los_node_adj(q, g4, gax, gay, gst, trc, tacc, tid, c * sh, dzp_dc, wt, dwt_dc, dc_dxp, dc_dyp, A);
+      if (j < 32) {
+        los_node_adj(q, g4, gax, gay, gst, run0, trc, tacc, tid, c * sh, dzp_dc, wt, dwt_dc, dc_dxp,
+                     dc_dyp, A);
+      } else {
+        los_node_adj(q, g4, gax, gay, gst, runx, trc, tacc, tid, c * sh, dzp_dc, wt, dwt_dc, dc_dxp,
+                     dc_dyp, A);
+        grun_flush(runx, gax, gay, gst);
+        runx.cell = -1;
+      }
     }
     for (int i = 0; i < 5; ++i)
       for (int off = 16; off > 0; off >>= 1) A[i] += __shfl_xor_sync(0xffffffffu, A[i], off);
@@ -243,6 +286,7 @@ __global__ void __launch_bounds__(SPH_LADJ_THREADS, 6) k_sph_los_adj(
       wsum[4] += -A[0] * sphi - A[1] * cphi;
     }
   }
+  grun_flush(run0, gax, gay, gst);
   if (lane == 0)
     for (int i = 0; i < 5; ++i) red[warp][i] = wsum[i];
   __syncthreads();
