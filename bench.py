@@ -127,12 +127,20 @@ def sph_exp2_counts(systems, sid_np, B, kernel):
             n += s["sph_nr"] * s["sph_nw"] * (SPH_NODES + 1) * (nm * s["n_gl"] + nl)
         elif kernel == "k_sph_los":
             n += nsub * (s["sph_nlos"] * (nl + 1) + nl)
+        elif kernel == "k_sph_adjoint":
+            # line of sight again (one ex2 per node and tracer Gaussian, one per node for e^tau);
+            # per grid point, the node sums, the tracer pass and the entry pass over 64 nodes,
+            # and the point itself: 130 x (mass x u nodes + tracer)
+            n += nsub * s["sph_nlos"] * (nl + 1) + s["sph_nr"] * s["sph_nw"] * 130 * (nm * s["n_gl"] + nl)
         else:
             n += nsub * nl * nm * s["n_gl"]
     if kernel == "k_sph_coef+k_sph_grid":
         return n, f"{n} exponentials per launch (grid points x 65 x (mass x u nodes + tracer))"
     if kernel == "k_sph_los":
         return n, f"{n} exponentials per launch (sky sub-samples x (n_los x (tracer + 1) + tracer))"
+    if kernel == "k_sph_adjoint":
+        return n, (f"{n} exponentials per launch (sky sub-samples x n_los x (tracer + 1) + grid "
+                   f"points x 130 x (mass x u nodes + tracer))")
     return n, f"{n} JAM integrand evaluations per launch (sky sub-samples x table entries)"
 
 
@@ -456,7 +464,7 @@ def main():
 
     prof_steps = min(args.steps, 3) if use_graph else args.steps
     extra = kl[names_idx("k_image+k_conv", lib, nk)] + kl[names_idx("k_grad_lens", lib, nk)] + \
-        kl[names_idx("k_sph_coef+k_sph_grid", lib, nk)] + \
+        kl[names_idx("k_sph_coef+k_sph_grid", lib, nk)] + 2 * kl[names_idx("k_sph_adjoint", lib, nk)] + \
         (kl[names_idx("k_jam", lib, nk)] if tuning["jam_pts"] >= 10000 else 0)
     launches_per_step = (int(sum(kl[i] for i in range(nk))) + int(extra)) // max(prof_steps, 1)
     if args.grad:
@@ -472,15 +480,16 @@ def main():
     names = [lib.glad_kernel_name(i).decode() for i in range(nk)]
     per_kernel = {names[i]: kms[i] / max(kl[i], 1) for i in range(nk) if kl[i]}
     jam_name = max((n for n in ("k_jam", "k_jam_fwd_grad", "k_jam_adjoint", "k_sph_coef+k_sph_grid",
-                                "k_sph_los") if n in per_kernel),
+                                "k_sph_los", "k_sph_adjoint") if n in per_kernel),
                    key=lambda n: per_kernel[n])
     jam_ms = per_kernel[jam_name]
     evals, units = sph_exp2_counts(systems, sid_np, B, jam_name)
-    n_exec["k_sph_coef+k_sph_grid"] = n_exec["k_sph_los"] = evals  # no terms are skipped there
+    # no terms are skipped in the spherically aligned kernels
+    n_exec["k_sph_coef+k_sph_grid"] = n_exec["k_sph_los"] = n_exec["k_sph_adjoint"] = evals
     achieved = evals / (jam_ms / 1000.0) / 1e9
     clocks = clk.summary()
     sm_max = clocks["sm_max_mhz"] or 2032.0
-    if jam_name in ("k_jam", "k_sph_coef+k_sph_grid", "k_sph_los"):
+    if jam_name in ("k_jam", "k_sph_coef+k_sph_grid", "k_sph_los", "k_sph_adjoint"):
         # one ex2 per evaluation; the 4 FMA-pipe operations per evaluation allow the same rate
         peak = N_SM * MUFU_EX2_PER_CLK_SM * sm_max * 1e6 / 1e9
         peak_unit = "Gexp2/s"
