@@ -201,6 +201,35 @@ __device__ __forceinline__ float2 sph_interp(const float4 *g4, int nr, int nwm, 
   return g;
 }
 
+// The two nodes of a mirrored pair (+z', -z') lie at the same radius (r^2 = rho^2 + z'^2): one
+// radial stencil and one set of Lagrange weights serve both; only their w columns differ.
+__device__ __forceinline__ void sph_interp_pair(const float4 *g4, int nr, int nwm, float lr0,
+                                                float idlr, float r2, float ir2, float R2a,
+                                                float R2b, float2 &ga, float2 &gb) {
+  const float fa = fminf(fmaxf((0.5f * 0.69314718055994531f * __log2f(r2) - lr0) * idlr, 0.f),
+                         (float)(nr - 1));
+  const int i0 = min(max((int)floorf(fa) - 1, 0), nr - 4);
+  const float t = fa - (float)i0;
+  const float t1 = t - 1.f, t2 = t - 2.f, t3 = t - 3.f;
+  const float L[4] = {-t1 * t2 * t3 * (1.f / 6.f), 0.5f * t * t2 * t3, -0.5f * t * t1 * t3,
+                      t * t1 * t2 * (1.f / 6.f)};
+  const float fca = fminf(fmaxf(R2a * ir2 * (float)nwm, 0.f), (float)nwm);
+  const float fcb = fminf(fmaxf(R2b * ir2 * (float)nwm, 0.f), (float)nwm);
+  const int ca = min((int)fca, nwm - 1), cb = min((int)fcb, nwm - 1);
+  const float ta = fca - (float)ca, tb = fcb - (float)cb;
+  const float4 *pa = g4 + i0 * nwm + ca, *pb = g4 + i0 * nwm + cb;
+  ga = make_float2(0.f, 0.f);
+  gb = ga;
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    const float4 A = pa[o * nwm], Bq = pb[o * nwm];
+    ga.x = fmaf(L[o], fmaf(ta, A.z - A.x, A.x), ga.x);
+    ga.y = fmaf(L[o], fmaf(ta, A.w - A.y, A.y), ga.y);
+    gb.x = fmaf(L[o], fmaf(tb, Bq.z - Bq.x, Bq.x), gb.x);
+    gb.y = fmaf(L[o], fmaf(tb, Bq.w - Bq.y, Bq.y), gb.y);
+  }
+}
+
 // The midpoint nodes come in pairs tau_i, tau_{n-1-i} = -tau_i that share e^tau and
 // e^-tau; each pair is one packed FP32 step (the middle node of an odd n is done alone).
 __global__ void __launch_bounds__(SPH_THREADS, SPH_LOS_MINB) k_sph_los(const SysDev *__restrict__ sysv,
@@ -253,6 +282,7 @@ __global__ void __launch_bounds__(SPH_THREADS, SPH_LOS_MINB) k_sph_los(const Sys
     const float dtau = 2.0f * tm / (float)n;
     const float X2 = xp * xp, omb = 1.0f - beta, dX = s2 * X2;
     const float ya = yp * ci, za = yp * si;
+    const float rho2 = fmaf(yp, yp, X2);  // r^2 of a node = rho^2 + z'^2
     float acc = 0.f;
     for (int i = 0; i < (n >> 1); ++i) {
       const float tau = ((float)i + 0.5f) * dtau - tm;
@@ -263,10 +293,9 @@ __global__ void __launch_bounds__(SPH_THREADS, SPH_LOS_MINB) k_sph_los(const Sys
       const float2 zz = make_float2(za + zp * ci, za - zp * ci);
       const float2 R2 = make_float2(fmaf(yy.x, yy.x, X2), fmaf(yy.y, yy.y, X2));
       const float2 Z2 = make_float2(zz.x * zz.x, zz.y * zz.y);
-      const float2 r2 = make_float2(fmaxf(R2.x + Z2.x, 1e-30f), fmaxf(R2.y + Z2.y, 1e-30f));
-      const float2 ir2 = make_float2(__fdividef(1.0f, r2.x), __fdividef(1.0f, r2.y));
-      const float2 ga = sph_interp(g4, nr, nwm, lr0, idlr, r2.x, ir2.x, R2.x);
-      const float2 gb = sph_interp(g4, nr, nwm, lr0, idlr, r2.y, ir2.y, R2.y);
+      const float r2 = fmaxf(fmaf(zp, zp, rho2), 1e-30f), ir2 = __fdividef(1.0f, r2);
+      float2 ga, gb;
+      sph_interp_pair(g4, nr, nwm, lr0, idlr, r2, ir2, R2.x, R2.y, ga, gb);
       float2 nu = make_float2(0.f, 0.f);
 #pragma unroll 4
       for (int k = 0; k < nL; ++k) {
@@ -275,8 +304,8 @@ __global__ void __launch_bounds__(SPH_THREADS, SPH_LOS_MINB) k_sph_los(const Sys
         nu = __ffma2_rn(make_float2(q.x, q.x), make_float2(sph_ex2(arg.x), sph_ex2(arg.y)), nu);
       }
       const float mua = zz.x * ci - yy.x * si, mub = zz.y * ci - yy.y * si;
-      const float fa = nu.x * (ga.x * fmaf(beta * mua * mua, ir2.x, omb) + ga.y * dX);
-      const float fb = nu.y * (gb.x * fmaf(beta * mub * mub, ir2.y, omb) + gb.y * dX);
+      const float fa = nu.x * (ga.x * fmaf(beta * mua * mua, ir2, omb) + ga.y * dX);
+      const float fb = nu.y * (gb.x * fmaf(beta * mub * mub, ir2, omb) + gb.y * dX);
       acc = fmaf(wt, fa + fb, acc);
     }
     if (n & 1) {  // middle node, z' = 0
