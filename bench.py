@@ -100,7 +100,10 @@ def workload_name(w, grad, B):
                 "GL64, 400 bins",
              5: "RXJ1131-scale with the spherically aligned Jeans model (Eqs. J1/J2): 200^2 x2ss, "
                 "21^2 PSF, EPL+shear+SIS, JAM 20+2x10+BH, polar grid 128x8, 32 LOS nodes, "
-                "60^2 sky x4ss, 50 bins"}
+                "60^2 sky x4ss, 50 bins",
+             6: "IFU-scale with the spherically aligned Jeans model (Eqs. J1/J2): 400^2 x3ss, "
+                "31^2 PSF, EPL+shear+2 SIS, JAM 40+2x20+BH, polar grid 128x8, 32 LOS nodes, "
+                "128^2 sky x4, GL64, 400 bins"}
     n = names.get(w, str(w)) + f"; B={B}"
     if grad:
         n += " (forward + gradient)"

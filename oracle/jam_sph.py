@@ -194,10 +194,18 @@ class SphRule:
         self.wu = wt * us * lam * e
 
 
-def grid_moments(m, rule):
-    """v_r^2 = P/nu and d = Dt/nu on the (n_r, n_w) grid."""
+def grid_moments(m, rule, max_elems=4_000_000):
+    """v_r^2 = P/nu and d = Dt/nu on the (n_r, n_w) grid (in blocks of radii, so that the
+    temporaries over (radius, angle, node, mass Gaussian, u node) stay near max_elems)."""
+    per_row = rule.n_w * CHAR_PIECES * CHAR_GL * rule.u.size
+    step = max(1, max_elems // per_row)
+    parts = [_grid_rows(m, rule, rule.lr[a:a + step]) for a in range(0, rule.n_r, step)]
+    return np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts])
+
+
+def _grid_rows(m, rule, lr):
     b = m.beta
-    r = np.exp(rule.lr)[:, None]                        # [n_r, 1]
+    r = np.exp(lr)[:, None]                             # [rows, 1]
     sth = np.sqrt(rule.w)[None, :]                      # [1, n_w]
     R = r * sth
     z2 = r * r * (1.0 - rule.w)[None, :]

@@ -144,7 +144,7 @@ glad_status validate(const glad_system_desc &d, int idx) {
     const size_t mg = (size_t)(d.n_mge_mass + (d.has_bh ? 1 : 0)) * d.n_gl;
     const size_t ladj = (size_t)nr * (nw - 1) * 16 + (size_t)nr * (nw | 1) * 8 + (size_t)nl * (16 + 128 * 8);
     const size_t gadj = mg * 40 + 8 * 64 * 16 + (size_t)nl * 24 + 16;
-    SUP(ladj <= 227 * 1024 && gadj <= 227 * 1024,
+    SUP(ladj <= 226 * 1024 && gadj <= 226 * 1024,
         "spherically aligned model too large for the gradient kernels' shared memory", idx);
   }
 #undef SUP
@@ -707,8 +707,10 @@ glad_status glad_create(const glad_system_desc *sys, int n_sys, glad_ctx **out) 
   cudaMemcpy(c->d_one_sys, ids.data(), sizeof(int) * n_sys, cudaMemcpyHostToDevice);
   set_conv_smem_limit();
   set_grad_smem_limit();
-  set_sph_smem_limit();
-  set_sph_grad_smem_limit();
+  if (set_sph_smem_limit() != cudaSuccess || set_sph_grad_smem_limit() != cudaSuccess) {
+    glad_destroy(c);
+    return fail(GLAD_ECUDA, "glad_create: shared-memory limits of the spherical kernels not set");
+  }
   int prio_lo = 0, prio_hi = 0;
   cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
   if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||

@@ -226,10 +226,10 @@ cudaError_t launch_combine(glad_ctx *c, int B, double *logL, int *status, double
 // spherically aligned model (k_sph.cu): coefficients + polar grid, then the line-of-sight sums
 cudaError_t launch_sph_grid(glad_ctx *c, const int *sys_id, int B, cudaStream_t st);
 cudaError_t launch_sph_los(glad_ctx *c, const int *sys_id, int B, cudaStream_t st);
-void set_sph_smem_limit();
+cudaError_t set_sph_smem_limit();
 // its adjoint (k_sph_grad.cu): line-of-sight and grid adjoints, carried to the JAM inputs
 cudaError_t launch_grad_sph(glad_ctx *c, const int *sys_id, int B, double *grad, cudaStream_t st);
-void set_sph_grad_smem_limit();
+cudaError_t set_sph_grad_smem_limit();
 // the dynamics sum of either model for the systems of the context (glad_host.cu): the
 // table/grid stage and the sky-point stage, each recorded under its kernel id
 cudaError_t launch_dyn_tables(glad_ctx *c, const int *sys_id, int B, cudaStream_t st);

@@ -348,11 +348,13 @@ size_t sph_los_smem(int g4, int nl, int nb) {
 
 }  // namespace
 
-void set_sph_smem_limit() {
-  cudaFuncSetAttribute(k_sph_grid, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sph_grid_smem(GLAD_SPH_MAX_MG, GLAD_MAX_LIGHT));
-  cudaFuncSetAttribute(k_sph_los, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sph_los_smem(GLAD_SPH_MAX_GRID, GLAD_MAX_LIGHT, GLAD_MAX_BINS));
+cudaError_t set_sph_smem_limit() {
+  cudaError_t e = cudaFuncSetAttribute(k_sph_grid, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sph_grid_smem(GLAD_SPH_MAX_MG, GLAD_MAX_LIGHT));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sph_los, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sph_los_smem(GLAD_SPH_MAX_GRID, GLAD_MAX_LIGHT, GLAD_MAX_BINS));
+  return e;
 }
 
 cudaError_t launch_sph_grid(glad_ctx *c, const int *sys_id, int B, cudaStream_t st) {

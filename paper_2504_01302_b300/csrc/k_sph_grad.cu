@@ -591,10 +591,25 @@ size_t sph_ladj_smem(int g4, int g, int nl) {
 
 }  // namespace
 
-// descriptors whose needs exceed 227 KB are refused at glad_create
-void set_sph_grad_smem_limit() {
-  cudaFuncSetAttribute(k_sph_los_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  cudaFuncSetAttribute(k_sph_grid_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+// the largest dynamic shared memory each kernel may take: the device's opt-in limit less the
+// kernel's static shared memory (descriptors needing more are refused at glad_create)
+template <class K>
+cudaError_t allow_dynamic_smem(K kernel) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
+  return e;
+}
+
+cudaError_t set_sph_grad_smem_limit() {
+  cudaError_t e = allow_dynamic_smem(k_sph_los_adj);
+  if (e == cudaSuccess) e = allow_dynamic_smem(k_sph_grid_adj);
+  return e;
 }
 
 cudaError_t launch_grad_sph(glad_ctx *c, const int *sys_id, int B, double *grad, cudaStream_t st) {

@@ -213,8 +213,9 @@ def workload_systems(w: int, small: bool = False):
     4: IFU-scale (400^2 x3, 31^2 PSF, 40+2x20+BH, 128^2 sky x4, GL64, 400 bins), B=4096
     5: workload 1's system with the spherically aligned Jeans model (Eqs. J1/J2; polar
        grid 128 x 8, 32 line-of-sight nodes), B=256
+    6: workload 4's system with the spherically aligned Jeans model (same rule), B=4096
     """
-    rng = np.random.Generator(np.random.PCG64(1000 + (1 if w == 5 else w)))
+    rng = np.random.Generator(np.random.PCG64(1000 + {5: 1, 6: 4}.get(w, w)))
     if w == 0:
         s = base_system("w0", n_img_px=64, ss=1, psf_k=11, sky=32, kss=1, n_mass=10,
                         n_light=10, n_gl=32, n_bins=20, bins="annular", rng=rng,
@@ -246,10 +247,12 @@ def workload_systems(w: int, small: bool = False):
                             bins="voronoi", rng=r, has_bh=True, n_sis=1, second_light=True)
             systems.append(s)
         return systems, 1024
-    if w == 4:
+    if w in (4, 6):
         s = base_system("w4", n_img_px=400, ss=3, psf_k=31, sky=128, kss=4, n_mass=40,
                         n_light=20, n_gl=64, n_bins=400, bins="voronoi", rng=rng,
                         has_bh=True, n_sis=2, second_light=True)
+        if w == 6:
+            s.update(name="w6", jam_align=1, sph_nr=128, sph_nw=8, sph_nlos=32)
         return [s], 4096
     raise ValueError(w)
 
