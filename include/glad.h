@@ -84,7 +84,7 @@ enum {
  * and projected with sph_nlos nodes per line of sight; 0 selects the defaults 128, 8, 32.
  * Limits: sph_nr * sph_nw <= 4096 and (mass Gaussians incl. the black hole) x n_gl <= 4096
  * (GLAD_EUNSUPPORTED beyond, as for sizes whose gradient kernels would need more than
- * 227 KB of shared memory).  glad_loglike_grad differentiates both models.
+ * 226 KB of shared memory per block).  glad_loglike_grad differentiates both models.
  */
 typedef struct glad_system_desc {
   int nx, ny, ss;
