@@ -5,8 +5,8 @@
 //
 //  k_sph_los_adj: per sky sub-sample (one warp, lanes over its nodes), with g_N = d logL /
 //    d(Sigma v^2) from k_kin_adj, the line-of-sight rule again: reverse mode into the grid values (v_r^2, d) of the stencil
-//    cells and into the tracer inputs nu0_k, c0_k; forward mode (4 tangents) through the
-//    node geometry for x', y' (then x_c, y_c, phi), sin i and cos i; beta explicitly.
+//    cells and into the tracer inputs nu0_k, c0_k; forward mode (3 tangents) through the
+//    node geometry for x', y' (then x_c, y_c, phi) and the inclination; beta explicitly.
 //  k_sph_grid_adj: per polar grid point (one warp), with the grid adjoint: phase 1 (lanes
 //    over the 64 characteristic nodes) recomputes the node sums and turns the adjoints of
 //    v_r^2 = P/nu and d = D/nu + (F_R - F_z) into adjoints of each node's F_z, G, nu, dnu,
@@ -68,7 +68,7 @@ struct LosPt {
 
 // one line-of-sight node z' = zs (derivative dzs_dc with respect to the node scale c, which
 // depends on x', y' through dc_dxp, dc_dyp) of weight wt (dwt_dc): adds the tangents
-// A[0..3] = d/d(x', y', sin i, cos i) and A[4] = d/d beta of g_N wt f, and adds the
+// A[0..2] = d/d(x', y', i) and A[3] = d/d beta of g_N wt f, and adds the
 // reverse-mode adjoints of the grid cells to the lane's pending run (flushed into gax, gay,
 // rows of gst words with gst odd so that different rows fall in different banks, whenever
 // the stencil moves) and those of the tracer inputs into shared memory
@@ -79,12 +79,13 @@ __device__ __forceinline__ void los_node_adj(const LosPt &q, const float4 *g4, f
                                              float dc_dyp, float *A) {
   const float dzx = dzs_dc * dc_dxp, dzy = dzs_dc * dc_dyp;
   const float yy = q.yp * q.ci - zs * q.si, zz = q.yp * q.si + zs * q.ci;
-  const float dyy[4] = {-q.si * dzx, q.ci - q.si * dzy, -zs, q.yp};
-  const float dzz[4] = {q.ci * dzx, q.si + q.ci * dzy, q.yp, zs};
+  // tangents x', y', i (z' does not depend on i; d sin i/di = cos i, d cos i/di = -sin i)
+  const float dyy[3] = {-q.si * dzx, q.ci - q.si * dzy, -q.yp * q.si - zs * q.ci};
+  const float dzz[3] = {q.ci * dzx, q.si + q.ci * dzy, yy};
   const float R2 = fmaf(yy, yy, q.X2), Z2 = zz * zz;
-  float dR2[4], dZ2[4], dr2[4];
+  float dR2[3], dZ2[3], dr2[3];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 3; ++i) {
     dR2[i] = 2.f * yy * dyy[i] + (i == 0 ? 2.f * q.xp : 0.f);
     dZ2[i] = 2.f * zz * dzz[i];
     dr2[i] = dR2[i] + dZ2[i];
@@ -156,19 +157,19 @@ __device__ __forceinline__ void los_node_adj(const LosPt &q, const float4 *g4, f
   // forward tangents
   const float f = nu * Bk;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 3; ++i) {
     const float dfa = fa_in ? 0.5f * q.idlr * ir2 * dr2[i] : 0.f;
     const float dfc = fc_in ? (float)q.nwm * ir2 * (dR2[i] - R2 * ir2 * dr2[i]) : 0.f;
     const float dgx = gt.x * dfa + gc.x * dfc, dgy = gt.y * dfa + gc.y * dfc;
     const float dnu = LN2F * (nua * dR2[i] + nub * dZ2[i]);
-    const float dmu = q.ci * dzz[i] - q.si * dyy[i] + (i == 2 ? -yy : 0.f) + (i == 3 ? zz : 0.f);
+    const float dmu = q.ci * dzz[i] - q.si * dyy[i] + (i == 2 ? -zz * q.si - yy * q.ci : 0.f);
     const float dm2 = fl ? 0.f : 2.f * mu * ir2 * dmu - m2 * ir2 * dr2[i];
     const float dB = dgx * fmaf(q.beta, m2, q.omb) + g.x * q.beta * dm2 + dgy * q.s2 * q.X2 +
-                     g.y * (i == 0 ? 2.f * q.s2 * q.xp : (i == 2 ? 2.f * q.si * q.X2 : 0.f));
+                     g.y * (i == 0 ? 2.f * q.s2 * q.xp : (i == 2 ? 2.f * q.si * q.ci * q.X2 : 0.f));
     const float dwt = i == 0 ? dwt_dc * dc_dxp : (i == 1 ? dwt_dc * dc_dyp : 0.f);
     A[i] = fmaf(q.gN, dwt * f + wt * (dnu * Bk + nu * dB), A[i]);
   }
-  A[4] = fmaf(w_g * nu, g.x * (m2 - 1.f), A[4]);
+  A[3] = fmaf(w_g * nu, g.x * (m2 - 1.f), A[3]);
 }
 
 // One warp per sky sub-sample (lanes over its line-of-sight nodes, so that a warp's grid
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(SPH_LADJ_THREADS, SPH_LADJ_MINB) k_sph_los_adj
     const float qq = r_end / c;
     const float tm = asinhf(qq);
     const float dtm_dc = -qq / (c * sqrtf(1.f + qq * qq));
-    float A[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    float A[4] = {0.f, 0.f, 0.f, 0.f};
     for (int j = lane; j < n; j += 32) {
       const float kap = (float)(2 * j + 1 - n) * inv_n;
       const float tau = kap * tm;
@@ -275,12 +276,12 @@ __global__ void __launch_bounds__(SPH_LADJ_THREADS, SPH_LADJ_MINB) k_sph_los_adj
         runx.cell = -1;
       }
     }
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 4; ++i)
       for (int off = 16; off > 0; off >>= 1) A[i] += __shfl_xor_sync(0xffffffffu, A[i], off);
     if (lane == 0) {
       // x' = c x + s y, y' = -s x + c y with (x, y) = sky - centre
-      wsum[0] += (double)A[2] * q.ci - (double)A[3] * q.si;
-      wsum[1] += A[4];
+      wsum[0] += A[2];
+      wsum[1] += A[3];
       wsum[2] += A[0] * q.yp - A[1] * q.xp;
       wsum[3] += -A[0] * cphi + A[1] * sphi;
       wsum[4] += -A[0] * sphi - A[1] * cphi;
