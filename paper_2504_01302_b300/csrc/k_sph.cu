@@ -33,6 +33,7 @@ namespace {
 #define SPH_THREADS 256
 #define SPH_WARPS (SPH_THREADS / 32)
 #define SPH_PIECES 16
+#define SPH_LOS_BLK 8  // blocks of SPH_THREADS sky sub-samples per line-of-sight CTA
 #ifndef SPH_LOS_MINB
 #define SPH_LOS_MINB 4  // resident CTAs per SM asked of the register allocator (line of sight)
 #endif
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(SPH_THREADS, SPH_LOS_MINB) k_sph_los(const Sys
   if (ws.status[b] != GLAD_SAMPLE_OK) return;
   const SysDev &S = sysv[sys_id[b]];
   if (S.jam_align != 1) return;
-  if ((int)blockIdx.x * SPH_THREADS >= S.n_sub) return;
+  if ((int)blockIdx.x * SPH_THREADS * SPH_LOS_BLK >= S.n_sub) return;
   extern __shared__ float4 sph_smem[];
   const int tid = threadIdx.x;
   const int nr = S.sph_nr, nw = S.sph_nw, nwm = nw - 1, nL = S.n_light;
@@ -264,7 +265,9 @@ __global__ void __launch_bounds__(SPH_THREADS, SPH_LOS_MINB) k_sph_los(const Sys
   }
   __syncthreads();
   const DynP dp = ws.dp[b];
-  const int s = blockIdx.x * SPH_THREADS + tid;
+  // SPH_LOS_BLK consecutive blocks of sky sub-samples per CTA: one grid load and one bin flush
+  for (int blk = 0; blk < SPH_LOS_BLK; ++blk) {
+  const int s = (blockIdx.x * SPH_LOS_BLK + blk) * SPH_THREADS + tid;
   if (s < S.n_sub) {
     const float beta = (float)(1.0 - 1.0 / dp.b);
     const float si = (float)sqrt(dp.s2), ci = (float)sqrt(dp.c2), s2 = (float)dp.s2;
@@ -331,6 +334,7 @@ __global__ void __launch_bounds__(SPH_THREADS, SPH_LOS_MINB) k_sph_los(const Sys
       atomicAdd(&bden[l], w * sb);
     }
   }
+  }
   __syncthreads();
   double *acc_g = ws.binacc + (size_t)b * max_bins * 2;
   for (int l = tid; l < S.n_bins; l += SPH_THREADS) {
@@ -383,7 +387,7 @@ cudaError_t launch_sph_los(glad_ctx *c, const int *sys_id, int B, cudaStream_t s
       nb = std::max(nb, sd.n_bins);
     }
   if (sub == 0) return cudaSuccess;
-  k_sph_los<<<dim3((sub + SPH_THREADS - 1) / SPH_THREADS, B), SPH_THREADS,
+  k_sph_los<<<dim3((sub + SPH_THREADS * SPH_LOS_BLK - 1) / (SPH_THREADS * SPH_LOS_BLK), B), SPH_THREADS,
               sph_los_smem(g4, c->max_light, nb), st>>>(
       c->d_sys, sys_id, c->ws.d, c->max_light, c->max_sgrid, c->max_bins);
   return cudaGetLastError();
