@@ -189,3 +189,23 @@ def test_w5_full_batch_sampled(w5):
     for b in range(2):
         ev = model.evaluate(near[b], s)
         assert int(s2[b]) == 0 and abs(float(l2[b]) - ev["logL"]) <= systems.logl_tol(ev["logL"])
+
+
+@pytest.mark.parametrize("rule", [dict(sph_nr=16, sph_nw=2, sph_nlos=1),   # one node, two angles
+                                  dict(sph_nr=24, sph_nw=5, sph_nlos=33)])  # odd n_los
+def test_rule_edge_cases(rule):
+    # the middle line-of-sight node (z' = 0) of an odd n_los, a single node, and the narrowest
+    # angular grid, forward and gradient, against the oracle's same rule.  (The descriptor also
+    # allows 4 radii; over 0.002" - 180" the cubic radial interpolation then overshoots to
+    # negative moments, in the oracle as on the GPU, and the sample ends non-finite.)
+    from .test_gpu_grad import assert_grad_close
+    s = dict(sph_small(7), **rule)
+    ctx = _ctx([s])
+    th = systems.near_truth_thetas(1, seed=93)[0]
+    ref, st, _ = model.dynamics(th, s)
+    assert st == model.ST_OK
+    assert_vrms_close(ctx.vrms(_th(th)).cpu().numpy(), ref)
+    _, g, stg = ctx.loglike_grad(_th(th[None]))
+    assert int(stg[0]) == 0
+    assert_grad_close(g.cpu().numpy()[0], model.grad_fd(th, s))
+    ctx.close()
