@@ -31,10 +31,11 @@ def subpixel_grid(nx, ny, ss, pix):
     return X, Y
 
 
-def surface_brightness(x, y, th, sysd):
-    """Source (through the lens) + lens light at sky points (x, y)."""
+def surface_brightness(x, y, th, sysd, alpha=None):
+    """Source (through the lens) + lens light at sky points (x, y); alpha: the deflection
+    function (lens.alpha_total unless given)."""
     from paper_2504_01302_b300.synth import IDX
-    ax, ay = lens.alpha_total(x, y, th, sysd["sis"])
+    ax, ay = (alpha or lens.alpha_total)(x, y, th, sysd["sis"])
     bx, by = x - ax, y - ay
     src = light.sersic_xy(bx, by, th[IDX["I_e_src"]], th[IDX["R_e_src"]], th[IDX["n_src"]],
                           sysd["src_q"], th[IDX["x_src"]], th[IDX["y_src"]], sysd["src_phi"])
@@ -46,9 +47,9 @@ def surface_brightness(x, y, th, sysd):
     return src + ll
 
 
-def unblurred_image(th, sysd):
+def unblurred_image(th, sysd, alpha=None):
     X, Y = subpixel_grid(sysd["nx"], sysd["ny"], sysd["ss"], sysd["pix"])
-    return surface_brightness(X, Y, th, sysd).mean(axis=-1)
+    return surface_brightness(X, Y, th, sysd, alpha).mean(axis=-1)
 
 
 def convolve_same(img, psf):
@@ -66,8 +67,8 @@ def convolve_same(img, psf):
     return out
 
 
-def model_image(th, sysd):
-    return convolve_same(unblurred_image(th, sysd), np.asarray(sysd["psf"], np.float64))
+def model_image(th, sysd, alpha=None):
+    return convolve_same(unblurred_image(th, sysd, alpha), np.asarray(sysd["psf"], np.float64))
 
 
 def chi2_pix(model, sysd):
