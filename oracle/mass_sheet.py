@@ -24,15 +24,21 @@ mass-sheet transform (Sect. 2.2, the MSD): beta -> lambda beta + (1 - lambda) c,
 source moved and resized accordingly gives the same images, and Fermat-potential
 differences (time delays) scale by lambda.
 
+For the dynamics the sheet joins the galaxy's mass Gaussians through its own 1-D MGE
+(class_mass); Sigma v_los^2 is linear in the mass Gaussians' amplitudes, so the sheet adds
+its own term to lambda times the galaxy's.
+
 Pins (tests/test_oracle_mass_sheet.py): the deflection against Gauss's theorem by
 quadrature of kappa; the potential's gradient against the deflection; the central
 convergence 1 - lambda; exact invariance of the model image and image positions, and
 lambda-scaled delays, under the ideal sheet; the dPIE sheet's departure from that inside
-the arcs; the MGE of the dPIE convergence.
+the arcs; the MGE of the dPIE convergence; the linearity of Sigma v^2 in the class's mass
+model, and the change of v_rms between two lensing-equivalent models (Sect. 2.2: the
+kinematics break the mass-sheet degeneracy).
 """
 import numpy as np
 
-from . import lens
+from . import lens, mge
 
 R_CORE = 45.0
 R_TR = 45.09
@@ -101,3 +107,19 @@ def psi_fn(sheet):
     def psi(x, y, th, sis):
         return sheet["lam"] * lens.psi_total(x, y, th, sis) + sheet_psi(x - th[4], y - th[5], sheet)
     return psi
+
+
+def sheet_mge(lam, n=40, P=10, rmin=0.1, rmax=1000.0, rc=R_CORE, rt=R_TR):
+    """Round mass Gaussians (kap0, sig, qp) of the dPIE sheet by the 1-D MGE of Sect. 3.2,
+    to join the galaxy's (scaled by lam) as the dynamics' mass model."""
+    a0 = dpie_a0(lam, rc, rt)
+    sig, A = mge.mge_1d(lambda z: dpie_kappa(z, a0, rc, rt), rmin, rmax, n, P)
+    return dict(kap0=A, sig=sig, qp=np.ones_like(sig))
+
+
+def class_mass(ms_gal, lam, **kw):
+    """Mass Gaussians of kappa_int = lam kappa_gal + kappa_dPIE."""
+    sh = sheet_mge(lam, **kw)
+    return dict(kap0=np.concatenate([lam * ms_gal["kap0"], sh["kap0"]]),
+                sig=np.concatenate([ms_gal["sig"], sh["sig"]]),
+                qp=np.concatenate([ms_gal["qp"], sh["qp"]]))

@@ -87,3 +87,27 @@ def test_dpie_mge_reconstruction():
     R = np.geomspace(0.1, 40.0, 200)
     rec = np.sum(A[None, :] * np.exp(-R[:, None] ** 2 / (2 * sig[None, :] ** 2)), -1)
     assert np.max(np.abs(rec / ms.dpie_kappa(R, a0) - 1)) < 1e-4
+
+
+def test_kinematics_break_the_mass_sheet_degeneracy(w0):
+    # Sigma v^2 is linear in the class's mass Gaussians; two models that lensing barely
+    # separates (lambda = 1 and 0.85, test_dpie_sheet_nearly_degenerate_for_lensing) give v_rms
+    # about 7 % apart in every bin, against the 2 % errors of the kinematic data
+    from oracle import jam, kin
+    s, t = w0
+    st, d = model.dynamics_setup(t, s)
+    inc, beta = t[I["inc"]], t[I["beta"]]
+    xp, yp = d["xp"].ravel(), d["yp"].ravel()
+
+    def sv2(msd):
+        tab = jam.table(d["tr"], msd, inc, beta, d["v2u"], d["r_max"], s["n_gl"])
+        return jam.sigma_v2_fast(xp, yp, tab).reshape(d["X"].shape)
+
+    lam = 0.85
+    gal, cls, sh = sv2(d["ms"]), sv2(ms.class_mass(d["ms"], lam)), sv2(ms.sheet_mge(lam))
+    assert np.max(np.abs(cls - (lam * gal + sh))) <= 1e-12 * np.max(np.abs(cls))
+    sb = jam.surface_brightness(d["xp"], d["yp"], d["tr"])
+    n1, d1 = kin.bin_moments(gal, sb, s)
+    n2, d2 = kin.bin_moments(cls, sb, s)
+    ratio = np.sqrt(n2 / d2) / np.sqrt(n1 / d1)
+    assert np.all(np.abs(ratio - 1) > 0.05), ratio
