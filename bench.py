@@ -34,7 +34,7 @@ from paper_2504_01302_b300 import shard, synth  # noqa: E402
 METRIC = "joint logL evals/sec and logL+grad evals/sec at 1 B300, at stated FP64-oracle accuracy"
 N_SM = 148
 # ex2.approx results per clock per SM on B300 (MUFU), measured by a throughput probe
-# (paper_2504_01302_b300/rates/probe_rates.cu): 32.3-32.8 ex2/clk/SM.
+# (profiles/mufu_ffma_rates_b300.md): 32.3-32.8 ex2/clk/SM.
 MUFU_EX2_PER_CLK_SM = 32
 # FP32 FMA lanes per clock per SM (the same probe measures 3.5-3.8e13 FFMA/s at 2032 MHz)
 FFMA_LANES_PER_CLK_SM = 128
@@ -51,7 +51,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="glad", choices=["glad", "reference"])
     p.add_argument("--workload", type=int, default=1)
-    p.add_argument("--grad", action="store_true", help="time logL + gradient (batch 64)")
+    p.add_argument("--grad", action="store_true",
+                   help="time only logL + gradient (batch 64); by default both are timed")
+    p.add_argument("--no-grad", action="store_true", help="time the forward logL only")
     p.add_argument("--batch", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--tuning", default="",
@@ -298,34 +300,14 @@ def names_idx(name, lib, nk):
     raise KeyError(name)
 
 
-def main():
-    args = parse()
-    if args.impl == "reference":
-        return run_reference(args)
-    import torch
-    import torch.distributed as dist
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    from paper_2504_01302_b300 import build as _b
-    if not _b.up_to_date() and rank == 0:
-        _b.build()
-    if world > 1:
-        dist.barrier()
+def measure(args, ctx, lib, systems, th_np, sid_np, B, grad_mode, world, rank, local, torch, dist):
+    """Time K steps of glad_loglike (or glad_loglike_grad) on this rank's B samples.
+    Returns the pieces of the JSON line: device-resident rate, end-to-end rate through the C
+    ABI with pinned host buffers, the one-sample-per-call form, per-kernel times from
+    separate profiled steps with the two branches serialised, and the roofline of the
+    dominant kernel."""
     from paper_2504_01302_b300 import _lib
-    from paper_2504_01302_b300.glad import GladContext
-
     w = args.workload
-    systems, B = bench_systems(w)
-    systems = fill_data_with_gpu_model(systems, w, torch, GladContext)
-    B = args.batch or (64 if args.grad else B)
-    # this rank's share of a global batch of world * B samples (no collective on the data)
-    th_np, sid_np = shard.shard(*synth.workload_thetas(w, world * B, len(systems)), rank, world)
-    ctx = GladContext(systems)
-    lib = ctx.lib
     theta = torch.as_tensor(th_np, device="cuda")
     sid = torch.as_tensor(sid_np, device="cuda")
     logL = torch.empty(B, dtype=torch.float64, device="cuda")
@@ -337,7 +319,7 @@ def main():
     def step():
         # the stream current at call time: torch.cuda.graph captures on its own stream
         hs = C.c_void_p(torch.cuda.current_stream().cuda_stream)
-        if args.grad:
+        if grad_mode:
             rc = lib.glad_loglike_grad(ctx.handle, P(sid), P(theta), B, P(logL), P(grad), P(status),
                                        None, hs)
         else:
@@ -350,7 +332,7 @@ def main():
         ctx.set_tuning(jc, ept)
         tuning = {"jam_pts": jc, "adj_ept": ept}
     else:
-        tuning = ctx.autotune(theta, sid, with_grad=args.grad)
+        tuning = ctx.autotune(theta, sid, with_grad=grad_mode)
     # L2 flush buffer (256 MB > 126 MB L2), written before each timed step, outside its events
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
@@ -358,7 +340,7 @@ def main():
     torch.cuda.synchronize()
     n_valid = int((status == 0).sum())
 
-    # ---- device-resident timing: K steps, events on the launching stream
+    # ---- device-resident timing: K steps, events on the launching stream, no profiling
     use_graph = args.graph == 1 or (args.graph == -1 and w == 3)
     graph = None
     if use_graph:
@@ -372,16 +354,12 @@ def main():
         torch.cuda.synchronize()
         # the replay must reproduce the eager step's results
         assert int((status == 0).sum()) == n_valid and bool(torch.isfinite(logL[status == 0]).all())
-    nk = lib.glad_kernel_times(ctx.handle, 0, None, None)
-    kms = (C.c_double * nk)()
-    kl = (C.c_int * nk)()
+    lib.glad_profile(ctx.handle, 0)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    if not use_graph:
-        lib.glad_profile(ctx.handle, 1)
     with ClockSampler(local) as clk:
         for k in range(args.steps):
             flush.fill_(float(k))
@@ -392,20 +370,25 @@ def main():
                 step()
             ev[k][1].record(stream)
         torch.cuda.synchronize()
-    if use_graph:
-        # per-kernel times from separate profiled (non-graph) steps
-        lib.glad_profile(ctx.handle, 1)
-        for k in range(min(args.steps, 3)):
-            flush.fill_(float(k))
-            step()
-        torch.cuda.synchronize()
-    lib.glad_profile(ctx.handle, 0)
-    lib.glad_kernel_times(ctx.handle, nk, kms, kl)
     t_ms = sum(a.elapsed_time(b) for a, b in ev)
     if world > 1:
         t_ms = shard.max_over_ranks(t_ms, dist, "cuda")
         dist.barrier()
     value = world * B * args.steps / (t_ms / 1000.0)
+
+    # ---- per-kernel times from separate profiled steps (not timed above): both branches on
+    # one stream, so each event pair times its kernel alone
+    nk = lib.glad_kernel_times(ctx.handle, 0, None, None)
+    kms = (C.c_double * nk)()
+    kl = (C.c_int * nk)()
+    prof_steps = 3
+    lib.glad_profile(ctx.handle, 2)
+    for k in range(prof_steps):
+        flush.fill_(float(k))
+        step()
+    torch.cuda.synchronize()
+    lib.glad_profile(ctx.handle, 0)
+    lib.glad_kernel_times(ctx.handle, nk, kms, kl)
 
     # ---- end to end through the public API with pinned host buffers
     th_h = torch.as_tensor(th_np).pin_memory()
@@ -422,7 +405,7 @@ def main():
         step()
         out_h.copy_(logL, non_blocking=True)
         st_h.copy_(status, non_blocking=True)
-        if args.grad:
+        if grad_mode:
             gr_h.copy_(grad, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -430,6 +413,7 @@ def main():
     if world > 1:
         e2e_ms = shard.max_over_ranks(e2e_ms, dist, "cuda")
     h2d = th_h.numel() * 8 + sid_h.numel() * 4
+    d2h = out_h.numel() * 8 + st_h.numel() * 4 + (gr_h.numel() * 8 if grad_mode else 0)
 
     # ---- the plain form: the same kernels called once per sample (B = 1), no graph,
     # on the first n_plain samples of the batch, L2 not flushed between calls
@@ -437,7 +421,7 @@ def main():
 
     def plain_call(b):
         hs = C.c_void_p(stream.cuda_stream)
-        if args.grad:
+        if grad_mode:
             rc = lib.glad_loglike_grad(ctx.handle, P(sid[b:b + 1]), P(theta[b:b + 1]), 1,
                                        P(logL[b:b + 1]), P(grad[b:b + 1]), P(status[b:b + 1]),
                                        None, hs)
@@ -456,30 +440,20 @@ def main():
     p1.record(stream)
     torch.cuda.synchronize()
     plain_ms = p0.elapsed_time(p1)
-    d2h = out_h.numel() * 8 + st_h.numel() * 4 + (gr_h.numel() * 8 if args.grad else 0)
 
-    if rank != 0:
-        ctx.close()
-        if world > 1:
-            dist.barrier()
-            dist.destroy_process_group()
-        return
-
-    prof_steps = min(args.steps, 3) if use_graph else args.steps
     extra = kl[names_idx("k_image+k_conv", lib, nk)] + kl[names_idx("k_grad_lens", lib, nk)] + \
         kl[names_idx("k_sph_coef+k_sph_grid", lib, nk)] + 2 * kl[names_idx("k_sph_adjoint", lib, nk)] + \
-        (kl[names_idx("k_jam", lib, nk)] if tuning["jam_pts"] >= 10000 else 0)
-    launches_per_step = (int(sum(kl[i] for i in range(nk))) + int(extra)) // max(prof_steps, 1)
-    if args.grad:
+        (kl[names_idx("k_jam", lib, nk)] if tuning["jam_pts"] >= 100000 else 0)
+    launches_per_step = (int(sum(kl[i] for i in range(nk))) + int(extra)) // prof_steps
+    if grad_mode:
         launches_per_step += 2  # k_kin_adj and k_grad_zero_invalid run untimed by the profiler
     # integrand evaluations the JAM kernels actually execute per step (exact and negligible
     # terms skipped), from one more untimed full-batch step
     step()
     n_exec = {"k_jam": ctx.jam_evaluations(), "k_jam_fwd_grad": ctx.jam_evaluations(),
               "k_jam_adjoint": ctx.jam_evaluations(adjoint=True)}
-    # ---- roofline of the dominant kernel (the JAM pair sum, its derivative pass or the
-    # table adjoint, whichever takes longest per step): integrand evaluations per launch
-    # against the pipe that bounds that kernel
+    # ---- roofline of the dominant kernel (the JAM pair sum, its derivative pass, the table
+    # adjoint or a kernel of the spherically aligned model, whichever takes longest per step)
     names = [lib.glad_kernel_name(i).decode() for i in range(nk)]
     per_kernel = {names[i]: kms[i] / max(kl[i], 1) for i in range(nk) if kl[i]}
     jam_name = max((n for n in ("k_jam", "k_jam_fwd_grad", "k_jam_adjoint", "k_sph_coef+k_sph_grid",
@@ -489,57 +463,125 @@ def main():
     evals, units = sph_exp2_counts(systems, sid_np, B, jam_name)
     # no terms are skipped in the spherically aligned kernels
     n_exec["k_sph_coef+k_sph_grid"] = n_exec["k_sph_los"] = n_exec["k_sph_adjoint"] = evals
-    achieved = evals / (jam_ms / 1000.0) / 1e9
     clocks = clk.summary()
     sm_max = clocks["sm_max_mhz"] or 2032.0
     if jam_name in ("k_jam", "k_sph_coef+k_sph_grid", "k_sph_los", "k_sph_adjoint"):
         # one ex2 per evaluation; the 4 FMA-pipe operations per evaluation allow the same rate
         peak = N_SM * MUFU_EX2_PER_CLK_SM * sm_max * 1e6 / 1e9
         peak_unit = "Gexp2/s"
-        peak_basis = (f"{N_SM} SM x {MUFU_EX2_PER_CLK_SM} ex2/clk/SM (measured) x "
-                      f"{sm_max:.0f} MHz max SM clock")
+        peak_basis = (f"{N_SM} SM x {MUFU_EX2_PER_CLK_SM} ex2/clk/SM (measured, "
+                      f"profiles/mufu_ffma_rates_b300.md) x {sm_max:.0f} MHz max SM clock")
     else:
         ops = FMA_OPS_PER_EVAL[jam_name]
         peak = N_SM * FFMA_LANES_PER_CLK_SM * sm_max * 1e6 / ops / 1e9
         peak_unit = "Geval/s"
         peak_basis = (f"{N_SM} SM x {FFMA_LANES_PER_CLK_SM} FP32 lanes/clk/SM x {sm_max:.0f} MHz "
                       f"/ {ops} FMA-pipe operations per evaluation")
-    unit = "logL+grad/s" if args.grad else "logL/s"
-    line = {
-        "metric": METRIC, "value": value, "unit": unit,
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name(w, args.grad, B), "batch_per_gpu": B,
-                   "precision": "f32 bulk; f64 MGE, tables and chi^2 reductions",
-                   "l2": "flushed (256 MB write) before each timed step", "valid_samples": n_valid,
-                   "tuning": tuning, "cuda_graph": bool(use_graph),
-                   "jam_skipping": "terms that underflow to 0 over a sky tile, and (pair sum and "
-                                   "derivative pass) terms whose bounded total over the tile "
-                                   "stays below 2^-26 of its smallest sum (checked after the sum)"},
+    executed = n_exec[jam_name]
+    achieved = executed / (jam_ms / 1000.0) / 1e9
+    achieved_alg = evals / (jam_ms / 1000.0) / 1e9
+    unit = "logL+grad/s" if grad_mode else "logL/s"
+    return {
+        "value": value, "unit": unit, "ms_per_step": t_ms / args.steps, "batch_per_gpu": B,
+        "valid_samples": n_valid, "tuning": tuning, "cuda_graph": bool(use_graph),
         "roofline": {"bound": "alu", "kernel": jam_name, "achieved": achieved, "peak": peak,
                      "unit": peak_unit, "frac": achieved / peak,
-                     "traffic": ncu_traffic(jam_name, w, args.grad, B),
+                     "achieved_basis": "integrand evaluations (one ex2 each) the kernel executes "
+                                       "per launch (library counter) / its CUDA-event time alone",
+                     "traffic": ncu_traffic(jam_name, w, grad_mode, B),
                      "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
                                       "small-batch capture, scaled by samples to this batch",
+                     "executed_evaluations": executed,
                      "algorithmic_units": units,
-                     "executed_evaluations": n_exec[jam_name],
-                     "executed_frac": n_exec[jam_name] / (jam_ms / 1000.0) / 1e9 / peak,
+                     "algorithmic_evaluations": evals,
+                     "algorithmic_frac": achieved_alg / peak,
+                     "skip_factor": evals / max(executed, 1),
+                     "kernel_ms": jam_ms,
                      "peak_basis": peak_basis},
         "kernels_ms_per_step": per_kernel,
-        "kernels_note": "CUDA-event time per launch unit in profiled steps; the lensing branch "
-                        "(k_image+k_conv, k_grad_lens) runs on a second stream concurrently "
-                        "with the dynamics branch, so those times overlap",
+        "kernels_note": f"CUDA-event time per launch unit in {prof_steps} profiled steps outside the "
+                        "timed region, with the lensing and dynamics branches serialised on one "
+                        "stream (in the timed steps they run concurrently on two streams)",
         "plain_form": {"value": n_plain / (plain_ms / 1000.0), "unit": unit, "samples": n_plain,
                        "form": "one sample per call (B = 1), same kernels, no graph"},
         "e2e": {"value": world * B * args.steps / (e2e_ms / 1000.0), "unit": unit,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        # launches of the library's kernels inside the timed region (per-step count from the
-        # profiled steps: k_image and k_conv are one timed unit, the gradient's lensing unit
-        # is k_conv_adj + k_image_grad, the persistent JAM form adds k_worklist)
+        # launches of the library's kernels per timed step (count from the profiled steps:
+        # k_image and k_conv are one timed unit, the gradient's lensing unit is k_conv_adj +
+        # k_image_grad, the persistent JAM form adds k_worklist)
         "gpu_launches": args.steps * launches_per_step,
         "clocks": clocks,
     }
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2504_01302_b300 import build as _b
+    if not _b.up_to_date() and rank == 0:
+        _b.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2504_01302_b300.glad import GladContext
+
+    w = args.workload
+    systems, B_w = bench_systems(w)
+    systems = fill_data_with_gpu_model(systems, w, torch, GladContext)
+    ctx = GladContext(systems)
+    lib = ctx.lib
+
+    def batch(grad_mode):
+        B = args.batch if args.batch and (grad_mode == args.grad) else (64 if grad_mode else B_w)
+        # this rank's share of a global batch of world * B samples (no collective on the data)
+        th_np, sid_np = shard.shard(*synth.workload_thetas(w, world * B, len(systems)), rank, world)
+        return B, th_np, sid_np
+
+    # the forward line (logL/s); with --grad only the gradient line; by default the gradient
+    # (logL+grad/s, batch 64) is measured too and reported in the line's "grad" object
+    main_grad = bool(args.grad)
+    B, th_np, sid_np = batch(main_grad)
+    m = measure(args, ctx, lib, systems, th_np, sid_np, B, main_grad, world, rank, local, torch, dist)
+    g = None
+    if not main_grad and not args.no_grad:
+        Bg, thg, sidg = batch(True)
+        g = measure(args, ctx, lib, systems, thg, sidg, Bg, True, world, rank, local, torch, dist)
+        g["config"] = {"workload": workload_name(w, True, Bg)}
+
+    if rank != 0:
+        ctx.close()
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    line = {
+        "metric": METRIC, "value": m["value"], "unit": m["unit"],
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(w, main_grad, B), "batch_per_gpu": B,
+                   "precision": "f32 bulk; f64 MGE, tables and chi^2 reductions",
+                   "l2": "flushed (256 MB write) before each timed step",
+                   "valid_samples": m["valid_samples"],
+                   "tuning": m["tuning"], "cuda_graph": m["cuda_graph"],
+                   "jam_skipping": "terms that underflow to 0 over a sky tile, and (pair sum and "
+                                   "derivative pass) terms whose bounded total over the tile "
+                                   "stays below 2^-26 of its smallest sum (checked after the sum)"},
+    }
+    for k in ("roofline", "kernels_ms_per_step", "kernels_note", "plain_form", "e2e",
+              "gpu_launches", "clocks"):
+        line[k] = m[k]
+    if g is not None:
+        line["grad"] = g
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(systems, th_np, sid_np)
     print(json.dumps(line), flush=True)

@@ -161,6 +161,11 @@ glad_status glad_vrms(glad_ctx *ctx, int sys, const double *theta, float *vrms, 
 
 /* Kernel-level timing, for benchmarks.  glad_profile(ctx, 1) makes every later call
  * record a CUDA event pair on its stream around each kernel it launches (0 stops it).
+ * In mode 1 the lensing and dynamics branches of glad_loglike / glad_loglike_grad still
+ * run concurrently on the context's two streams, so a branch's event time includes the
+ * time it waited for SMs held by the other; mode 2 runs both branches on the caller's
+ * stream, one after the other, so each event pair times its kernel alone.  Returns 0, or
+ * -1 for a null context or another mode.
  * glad_kernel_times(ctx, n, ms, launches) waits for those events, adds the elapsed
  * milliseconds and the launch count of kernel id k (0 <= k < n) into ms[k] and
  * launches[k] [host arrays of n], and forgets the recorded pairs.  Returns the number
@@ -181,7 +186,12 @@ const char *glad_kernel_name(int k);
  * All calls share the one array and each clears the accumulators it needs: calls that
  * overlap on the GPU (different streams, threads or contexts) race and must be serialised.
  * A batch whose scratch exceeds 64 MiB (about 170 samples of the 200x200 RXJ1131-scale
- * system) returns GLAD_EUNSUPPORTED with the limit in glad_last_error(). */
+ * system) returns GLAD_EUNSUPPORTED with the limit in glad_last_error().  It uses the
+ * context's launch shape (glad_autotune / glad_set_tuning, grid or persistent form) and
+ * negligible-term mode, but its integrand evaluations are not counted by
+ * glad_jam_evaluations.  For the length of the call it points the context's workspace view
+ * at the static array: no other host thread may use the same context meanwhile (the
+ * general rule that one context is not thread-safe). */
 glad_status glad_loglike_static(glad_ctx *ctx, const int *sys_id, const double *theta, int B,
                                 double *logL, int *sample_status, double *terms, void *stream);
 

@@ -6,7 +6,10 @@ to 1/H0.  Flat LambdaCDM as in Table 2 (H0=82.5, Om=0.27).  Critical density
 The external-convergence rescaling D_dt,int = (1-kappa_ext) D_dt follows
 Eq. Dt external internal.
 
-Pins: D_d and D_dt printed in Table 2 and its footnote; D_dt proportional to 1/H0.
+Pins: D_d and D_dt printed in Table 2 and its footnote; D_dt proportional to 1/H0;
+v2_unit by the singular isothermal sphere's sigma^2 = theta_E c^2 D_s/(4 pi D_ds) reached
+through the MGE and the Jeans solution; delay_days_per_arcsec2 by the SIS two-image delay
+D_dt (theta_A^2 - theta_B^2)/(2c) in SI units.
 """
 import math
 

@@ -67,6 +67,11 @@ def epl_alpha_frame(xp, yp, theta_E, g, q, nterms=None):
     xp = np.asarray(xp, np.float64)
     yp = np.asarray(yp, np.float64)
     R = np.sqrt(q * q * xp * xp + yp * yp)
+    # at the exact centre the direction of the deflection is undefined (|alpha| ~ R^(1-t));
+    # it is taken as 0, its average over directions (the paper is silent: its lensing EPL
+    # is not softened)
+    at0 = R == 0.0
+    R = np.where(at0, 1.0, R)
     w = (q * xp + 1j * yp) / R
     w2 = w * w
     f = (1.0 - q) / (1.0 + q)
@@ -77,6 +82,7 @@ def epl_alpha_frame(xp, yp, theta_E, g, q, nterms=None):
         om = -f * (2 * n - (2 - t)) / (2 * n + (2 - t)) * w2 * om
         S = S + om
     a = 2.0 * bt / (1.0 + q) * (bt / R) ** (t - 1.0) * S
+    a = np.where(at0, 0.0, a)
     return a.real, a.imag
 
 
@@ -108,9 +114,11 @@ def shear_psi(dx, dy, gamma_ext, phi_ext):
 
 
 def sis_alpha(x, y, tE, xs, ys):
+    """SIS deflection; 0 at the perturber's exact centre (as for the EPL)."""
     dx, dy = x - xs, y - ys
     r = np.sqrt(dx * dx + dy * dy)
-    return tE * dx / r, tE * dy / r
+    ri = np.where(r == 0.0, 0.0, 1.0 / np.where(r == 0.0, 1.0, r))
+    return tE * dx * ri, tE * dy * ri
 
 
 def sis_psi(x, y, tE, xs, ys):

@@ -514,17 +514,19 @@ glad_status full_path(glad_ctx *c, const int *sys_id, const double *theta, int B
     e = cudaMemsetAsync(c->ws.d.binacc, 0, sizeof(double) * 2 * c->max_bins * (size_t)B, st);
   if (e == cudaSuccess && grad) e = grad_prepare(c, B, grad, st);
   if (e == cudaSuccess) e = GLAD_PROF(c, st, KID_PREP, launch_prep(c, sys_id, theta, B, st));
-  // fork
-  cudaStream_t dy = c->dyn;
+  // fork (profiling mode 2 runs both branches on the caller's stream, one after the other,
+  // so that each kernel's event pair times it alone)
+  const bool serial = c->prof == 2;
+  cudaStream_t dy = serial ? st : c->dyn, side = serial ? st : c->side;
   if (e == cudaSuccess) e = cudaEventRecord(c->ev_fork, st);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(dy, c->ev_fork, 0);
+  if (e == cudaSuccess && !serial) e = cudaStreamWaitEvent(side, c->ev_fork, 0);
+  if (e == cudaSuccess && !serial) e = cudaStreamWaitEvent(dy, c->ev_fork, 0);
   // lensing, low priority
   if (e == cudaSuccess)
-    e = GLAD_PROF(c, c->side, KID_IMAGE_CONV,
-                  launch_lens(c, sys_id, B, nullptr, c->side, grad ? grad_resid_buffer(c) : nullptr));
-  if (e == cudaSuccess && grad) e = launch_grad_lens(c, sys_id, B, grad, c->side);
-  if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
+    e = GLAD_PROF(c, side, KID_IMAGE_CONV,
+                  launch_lens(c, sys_id, B, nullptr, side, grad ? grad_resid_buffer(c) : nullptr));
+  if (e == cudaSuccess && grad) e = launch_grad_lens(c, sys_id, B, grad, side);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, side);
   // dynamics, high priority
   if (e == cudaSuccess) e = launch_dyn_tables(c, sys_id, B, dy);
   if (e == cudaSuccess) {
@@ -542,8 +544,8 @@ glad_status full_path(glad_ctx *c, const int *sys_id, const double *theta, int B
   if (e == cudaSuccess && grad) e = launch_grad_dyn(c, sys_id, theta, B, grad, dy);
   if (e == cudaSuccess) e = cudaEventRecord(c->ev_join_dyn, dy);
   // join
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->ev_join, 0);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->ev_join_dyn, 0);
+  if (e == cudaSuccess && !serial) e = cudaStreamWaitEvent(st, c->ev_join, 0);
+  if (e == cudaSuccess && !serial) e = cudaStreamWaitEvent(st, c->ev_join_dyn, 0);
   if (e == cudaSuccess && grad) e = launch_grad_finish(c, B, grad, st);
   if (e == cudaSuccess)
     e = GLAD_PROF(c, st, KID_COMBINE, launch_combine(c, B, logL, sample_status, terms, st));
@@ -630,7 +632,8 @@ glad_status glad_jam_evaluations(glad_ctx *c, unsigned long long *count,
 
 int glad_profile(glad_ctx *c, int enable) {
   if (!c) return -1;
-  c->prof = enable ? 1 : 0;
+  if (enable < 0 || enable > 2) return -1;
+  c->prof = enable;
   return 0;
 }
 

@@ -124,7 +124,7 @@ struct WsDev {
   float4 *tab;                 // [B*max_ent]
   float *img;                  // [B*max_pix]
   double *binacc;              // [B*max_bins*2]
-  double *terms;               // [B*3]
+  double *terms;               // [B*4]: chi2_pix, chi2_dyn, chi2_tmd, chi2_img
   int *status;                 // [B]
   int *wl_off;                 // [B+1] persistent JAM work list (first item of each sample)
   int *wl_counter;             // [1]   next work item

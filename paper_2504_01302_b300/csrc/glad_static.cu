@@ -63,6 +63,9 @@ size_t carve(const glad_ctx *c, int B, unsigned char *base, WsDev *w) {
   w->binacc = (double *)take(b * c->max_bins * 2 * sizeof(double));
   w->terms = (double *)take(b * 4 * sizeof(double));
   w->status = (int *)take(b * sizeof(int));
+  // work list of the persistent JAM form (k_worklist writes every entry and the counter)
+  w->wl_off = (int *)take((b + 1) * sizeof(int));
+  w->wl_counter = (int *)take(sizeof(int));
   w->sph_mt = (float4 *)take(b * c->max_smg * sizeof(float4));
   w->sph_mrz = (float *)take(b * c->max_smg * sizeof(float));
   w->sph_tr = (float4 *)take(b * c->max_light * sizeof(float4));
@@ -75,6 +78,7 @@ size_t carve(const glad_ctx *c, int B, unsigned char *base, WsDev *w) {
 extern "C" glad_status glad_loglike_static(glad_ctx *c, const int *sys_id, const double *theta,
                                            int B, double *logL, int *sample_status, double *terms,
                                            void *stream) {
+  glad_set_error(GLAD_OK, "");  // a successful call leaves glad_last_error() empty
   if (!c || !sys_id || !theta || !logL || !sample_status || B < 1)
     return glad_set_error(GLAD_EINVAL, "glad_loglike_static: bad arguments");
   WsDev w{};
@@ -95,7 +99,9 @@ extern "C" glad_status glad_loglike_static(glad_ctx *c, const int *sys_id, const
     return glad_set_error(GLAD_ECUDA, m.c_str());
   }
   carve(c, B, (unsigned char *)base, &w);
-  w.neg_mode = c->tune.neg_mode;  // same JAM summation as glad_loglike; evaluations not counted
+  // same JAM summation and launch shape as glad_loglike; evaluations are not counted
+  // (w.evals stays null), so glad_jam_evaluations keeps the figure of the last counted call
+  w.neg_mode = c->tune.neg_mode;
   cudaStream_t st = (cudaStream_t)stream;
   // the launchers read the context's workspace view: point it at the scratch for the
   // duration of the launches (kernel arguments are copied at launch) and restore it

@@ -139,7 +139,9 @@ __global__ void __launch_bounds__(LENS_THREADS) k_image_grad(const SysDev *__res
         dy.d[5] = -1.0f;
         const D8 xp = cphi * dx + sphi * dy, yp = cphi * dy - sphi * dx;
         // EPL deflection, Tessore & Metcalf series, with tangents
-        const D8 R = dsqrt(q * q * xp * xp + yp * yp);
+        // at the exact centre alpha is taken as 0 with zero tangents (as in k_image)
+        const bool at0 = !(q.v * q.v * xp.v * xp.v + yp.v * yp.v > 0.0f);
+        const D8 R = at0 ? D8(1.0f) : dsqrt(q * q * xp * xp + yp * yp);
         const D8 iR = 1.0f / R;
         const D8 wr = q * xp * iR, wi = yp * iR;
         const D8 w2r = wr * wr - wi * wi, w2i = 2.0f * wr * wi;
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(LENS_THREADS) k_image_grad(const SysDev *__res
           Sr = Sr + omr;
           Si = Si + omi;
         }
-        const D8 amp = pref * dexp2((1.0f - t) * dlog2(R));
+        const D8 amp = at0 ? D8(0.0f) : pref * dexp2((1.0f - t) * dlog2(R));
         const D8 apx = amp * Sr, apy = amp * Si;
         D8 ax = cphi * apx - sphi * apy;
         D8 ay = sphi * apx + cphi * apy;
@@ -164,7 +166,8 @@ __global__ void __launch_bounds__(LENS_THREADS) k_image_grad(const SysDev *__res
         for (int k = 0; k < S.n_sis; ++k) {
           const float te = (float)S.sis[3 * k];
           const float sx = x - (float)S.sis[3 * k + 1], sy = y - (float)S.sis[3 * k + 2];
-          const float ir = rsqrtf(sx * sx + sy * sy);
+          const float r2 = sx * sx + sy * sy;
+          const float ir = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
           ax.v += te * sx * ir;
           ay.v += te * sy * ir;
         }

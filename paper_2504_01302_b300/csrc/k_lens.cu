@@ -47,8 +47,9 @@ __global__ void __launch_bounds__(LENS_THREADS) k_image(const SysDev *__restrict
       const float dx = x - L.xc, dy = y - L.yc;
       const float xp = L.cphi * dx + L.sphi * dy, yp = -L.sphi * dx + L.cphi * dy;
       // EPL (Tessore & Metcalf series)
+      // at the exact centre alpha is taken as 0 (its direction is undefined there)
       const float R = sqrtf(q * q * xp * xp + yp * yp);
-      const float iR = 1.0f / R;
+      const float iR = R > 0.0f ? 1.0f / R : 0.0f;
       const float wr = q * xp * iR, wi = yp * iR;
       const float w2r = wr * wr - wi * wi, w2i = 2.0f * wr * wi;
       float omr = wr, omi = wi, Sr = wr, Si = wi;
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(LENS_THREADS) k_image(const SysDev *__restrict
         Sr += omr;
         Si += omi;
       }
-      const float amp = L.pref * exp2f(omt * log2f(R));
+      const float amp = R > 0.0f ? L.pref * exp2f(omt * log2f(R)) : 0.0f;
       const float apx = amp * Sr, apy = amp * Si;
       float ax = L.cphi * apx - L.sphi * apy;
       float ay = L.sphi * apx + L.cphi * apy;
@@ -70,7 +71,8 @@ __global__ void __launch_bounds__(LENS_THREADS) k_image(const SysDev *__restrict
       for (int k = 0; k < S.n_sis; ++k) {
         const float te = (float)S.sis[3 * k];
         const float sx = x - (float)S.sis[3 * k + 1], sy = y - (float)S.sis[3 * k + 2];
-        const float ir = rsqrtf(sx * sx + sy * sy);
+        const float r2 = sx * sx + sy * sy;
+        const float ir = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
         ax += te * sx * ir;
         ay += te * sy * ir;
       }

@@ -173,8 +173,10 @@ class GladContext:
         self.lib.glad_kernel_times(self.handle, n, ms, nl)
         return {self.lib.glad_kernel_name(i).decode(): (ms[i], nl[i]) for i in range(n) if nl[i]}
 
-    def profile(self, on=True):
-        self.lib.glad_profile(self.handle, 1 if on else 0)
+    def profile(self, mode=1):
+        """glad_profile: 0 off, 1 event pairs per kernel, 2 the same with the lensing and
+        dynamics branches serialised on the caller's stream (isolated kernel times)."""
+        self.lib.glad_profile(self.handle, int(mode))
 
     def close(self):
         if getattr(self, "handle", None):

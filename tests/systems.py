@@ -80,3 +80,107 @@ def ifu_system():
     s["dt_sig"] = sig
     s["dt_obs"] = dt + sig * nz["dt"][:len(dt)]
     return s
+
+
+@functools.lru_cache(maxsize=None)
+def uneven_systems():
+    """The 8 uneven systems of the uneven-batch workload (64..256 px, ss 1-3, PSF 11-21,
+    8-30 Gaussians per component, 20-120 bins, GL 24-64, sky 32..64 x ss 2/4), with imaging
+    data and delays from the oracle at the truth and v_obs a seeded draw around 300 km/s
+    with 2 % errors (the oracle's full v_rms maps of all eight are not needed: the tests
+    compare the two paths on the same data)."""
+    from oracle import imaging, lens, tdelay
+    bases, _ = synth.workload_systems(3)
+    truth = synth.theta_truth(1)
+    out = []
+    for si, b in enumerate(bases):
+        s = dict(b)
+        nz = synth.noise_draws(s, 3000 + si)
+        s["img_xy"] = lens.solve_images(s["qso_beta"], truth, s["sis"],
+                                        synth.ring_images(truth[synth.IDX["theta_E"]], s["qso_beta"]))
+        m = imaging.model_image(truth, s)
+        s["data"] = (m + np.asarray(s["sigma"], np.float64) * nz["img"]).astype(np.float32)
+        rng = np.random.Generator(np.random.PCG64(3100 + si))
+        v = 300.0 * (1.0 + 0.05 * rng.standard_normal(s["n_bins"]))
+        s["v_obs"] = v.astype(np.float32)
+        s["v_sig"] = (0.02 * v).astype(np.float32)
+        s["dt_obs"] = np.zeros(len(s["img_xy"]) - 1)
+        s["dt_sig"] = np.ones(len(s["img_xy"]) - 1)
+        dt = tdelay.delays(truth, s)
+        sig = 0.016 * np.abs(dt) + 0.1
+        s["dt_sig"] = sig
+        s["dt_obs"] = dt + sig * nz["dt"][:len(dt)]
+        out.append(s)
+    return out
+
+
+def _oracle_loglike(args):
+    th, s = args
+    return model.loglike(th, s)
+
+
+def oracle_grad_fd_pool(th, s, which=None, h_rel=1e-6):
+    """model.grad_fd (FP64 central differences of the oracle, h = h_rel x parameter scale)
+    with the 2 x len(which) oracle evaluations spread over the host cores (spawn pool: the
+    calling process may already hold a CUDA context)."""
+    import multiprocessing as mp
+    import os
+    th = np.asarray(th, np.float64)
+    idx = list(range(len(th))) if which is None else list(which)
+    jobs = []
+    for i in idx:
+        h = h_rel * synth.THETA_SCALE[i]
+        for sgn in (1.0, -1.0):
+            t = th.copy()
+            t[i] += sgn * h
+            jobs.append((t, s))
+    with mp.get_context("spawn").Pool(min(len(jobs), os.cpu_count() or 1)) as pool:
+        vals = pool.map(_oracle_loglike, jobs)
+    g = np.zeros(len(th))
+    for n, i in enumerate(idx):
+        g[i] = (vals[2 * n] - vals[2 * n + 1]) / (2 * h_rel * synth.THETA_SCALE[i])
+    return g
+
+
+def _restricted_chi2_dyn(args):
+    th, s, which = args
+    from oracle import kin
+    v, st = model.vrms_bins(th, s, which)
+    return kin.chi2_dyn(v, s) if st == model.ST_OK else np.nan
+
+
+def keep_bins(s, keep):
+    """A copy of system s whose kinematic data keep only the bins listed (relabelled
+    0..len(keep)-1, every other spaxel unused): chi^2_dyn then runs over those bins alone,
+    which oracle.model.vrms_bins can evaluate at any grid size."""
+    lab = np.asarray(s["bins"])
+    new = np.full_like(lab, -1)
+    for i, k in enumerate(keep):
+        new[lab == k] = i
+    out = dict(s)
+    out.update(bins=new, n_bins=len(keep), v_obs=np.asarray(s["v_obs"])[list(keep)],
+               v_sig=np.asarray(s["v_sig"])[list(keep)])
+    return out
+
+
+def oracle_dyn_grad_fd_pool(th, s, which, h_rel=1e-6):
+    """-1/2 d chi^2_dyn / d theta_i (i in which) by FP64 central differences of the oracle's
+    v_rms restricted to all bins of s (use keep_bins first at large sizes), the evaluations
+    spread over the host cores (spawn pool)."""
+    import multiprocessing as mp
+    import os
+    th = np.asarray(th, np.float64)
+    bins = list(range(int(s["n_bins"])))
+    jobs = []
+    for i in which:
+        h = h_rel * synth.THETA_SCALE[i]
+        for sgn in (1.0, -1.0):
+            t = th.copy()
+            t[i] += sgn * h
+            jobs.append((t, s, bins))
+    with mp.get_context("spawn").Pool(min(len(jobs), os.cpu_count() or 1)) as pool:
+        vals = pool.map(_restricted_chi2_dyn, jobs)
+    g = np.zeros(len(th))
+    for n, i in enumerate(which):
+        g[i] = -0.5 * (vals[2 * n] - vals[2 * n + 1]) / (2 * h_rel * synth.THETA_SCALE[i])
+    return g

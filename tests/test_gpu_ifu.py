@@ -3,10 +3,11 @@ on a 128^2 x 4 sky with GL64, 400 bins) at its full size and batch (B = 4096).
 
 The oracle evaluates this system one output at a time: the model image (1.44 M
 sub-pixels), the delays, and v_rms of chosen bins through oracle.model.vrms_bins.  The
-full v_rms map is out of its reach, so chi^2_dyn is checked through the GPU's own v_rms
-(a property of the reduction) and the gradient through central differences of the
-library's logL for the dynamics parameters, and of the oracle's imaging + delay terms
-for parameters that only enter those.  Tolerances as in test_gpu_parity."""
+full v_rms map is out of its reach, so chi^2_dyn of the full batch is checked through the
+GPU's own v_rms (a property of the reduction); the gradient is checked against central
+differences of the oracle: its imaging + delay terms for parameters that only enter those,
+and, on a copy of the system that keeps two bins, its restricted v_rms for the dynamics
+parameters.  Tolerances as in test_gpu_parity."""
 import numpy as np
 import pytest
 
@@ -106,16 +107,35 @@ def test_ifu_gradient(ifu):
                                  tdelay.chi2_tmd(tdelay.delays(t, s), s)))
             ref = (f[0] - f[1]) / (2 * h)
             assert abs(g[b, i] - ref) <= 1e-3 * abs(ref) + 1e-2, (b, name, g[b, i], ref)
-    # parameters of the dynamics (and theta_E, which enters everything), near the truth:
-    # central differences of the library's own logL, with the FD error of a logL noise of
-    # 0.05 added to the bound
-    for name in ("theta_E", "inc", "beta", "upsilon"):
-        i = I[name]
-        h = 1e-3 * synth.THETA_SCALE[i]
-        tp, tm = th[0].copy(), th[0].copy()
-        tp[i] += h
-        tm[i] -= h
-        lp, _ = ctx.loglike(_th(tp[None]))
-        lm, _ = ctx.loglike(_th(tm[None]))
-        fd = (float(lp[0]) - float(lm[0])) / (2 * h)
-        assert abs(g[0, i] - fd) <= 1e-2 * abs(fd) + 0.05 / h, (name, g[0, i], fd)
+
+
+def test_ifu_gradient_dynamics_against_oracle(ifu):
+    """The dynamics components of the IFU-scale gradient against FP64 central differences of
+    the oracle.  A copy of the system keeps two bins (the central one and the outermost),
+    so chi^2_dyn is a sum the oracle's restricted v_rms evaluates exactly; the gradient of
+    the image and delay terms (which only theta_E of these parameters enters) comes from
+    the oracle's image and delays."""
+    from paper_2504_01302_b300.glad import GladContext
+    s, _ = ifu
+    lab = np.asarray(s["bins"])
+    ky, kx = lab.shape
+    s2 = systems.keep_bins(s, [int(lab[ky // 2, kx // 2]), int(s["n_bins"]) - 1])
+    ctx = GladContext([s2])
+    th = systems.near_truth_thetas(1, seed=65)[0]
+    _, g, st = ctx.loglike_grad(_th(th[None]))
+    assert int(st.cpu().numpy()[0]) == 0
+    g = g.cpu().numpy()[0]
+    which = [I[n] for n in ("theta_E", "inc", "beta", "upsilon", "f_bh")]
+    ref = systems.oracle_dyn_grad_fd_pool(th, s2, which)
+    i = I["theta_E"]
+    h = 1e-6 * synth.THETA_SCALE[i]
+    f = []
+    for sgn in (1, -1):
+        t = th.copy()
+        t[i] += sgn * h
+        f.append(-0.5 * (imaging.chi2_pix(imaging.model_image(t, s2), s2) +
+                         tdelay.chi2_tmd(tdelay.delays(t, s2), s2)))
+    ref[i] += (f[0] - f[1]) / (2 * h)
+    for i in which:
+        assert abs(g[i] - ref[i]) <= 1e-3 * max(abs(ref[i]), 1e-3 * np.max(np.abs(ref[which]))), \
+            (synth.THETA_NAMES[i], g[i], ref[i])

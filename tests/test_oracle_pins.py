@@ -337,12 +337,58 @@ def test_chi2_at_truth_matches_noise(w0):
     assert abs(ev["chi2_dyn"] - nb) < 5 * math.sqrt(2 * nb)
 
 
-def test_dynamics_independent_of_H0_and_sqrt_mass(w0):
+def test_dynamics_independent_of_H0(w0):
     s, th = w0
     v1 = model.evaluate(th, s)["vrms"]
     t2 = th.copy()
     t2[synth.IDX["H0"]] = 55.0
     assert np.allclose(model.evaluate(t2, s)["vrms"], v1, rtol=1e-13)
+
+
+def test_velocity_unit_singular_isothermal_sphere():
+    """The dynamics' velocity scale (G Sigma_crit, Eq. critical_sfd with the distances of
+    Eq. sfd final) against the textbook singular isothermal sphere: a round EPL with
+    gamma' = 2 has kappa = theta_E / (2R), i.e. an SIS of dispersion
+    sigma^2 = theta_E c^2 D_s / (4 pi D_ds) (theta_E in radians), and an isotropic tracer
+    following the same r^-2 density has a constant v_rms = sigma at every radius.  The MGE
+    (60 Gaussians on [1e-3, 300] arcsec) holds the profile to its stated 0.5 %.  A lost
+    4 pi, arcsec taken for radians or D_dt/D_d in place of D_s/D_ds fails by orders of
+    magnitude."""
+    z_d, z_s, om, tE = 0.295, 0.654, 0.27, 1.5
+    s, A = mge.mge_1d(mge.epl_profile(tE, 2.0, 1.0, 0.0), 1e-3, 300.0, 60, 10)
+    ms = dict(kap0=A, sig=s, qp=np.ones_like(s))
+    tr = dict(I0=A.copy(), sig=s, qp=np.ones_like(s))
+    v2u = cosmo.v2_unit(z_d, z_s, om)
+    R = np.array([0.1, 0.3, 0.6, 1.0, 2.0])
+    for inc in (math.radians(60), math.radians(85)):
+        tab = jam.table(tr, ms, inc, 0.0, v2u, R.max(), 64)
+        v = np.sqrt(jam.sigma_v2_fast(R, 0 * R, tab) / jam.surface_brightness(R, 0 * R, tr))
+        _, D_s, D_ds, _ = cosmo.distances(z_d, z_s, 70.0, om)
+        c = 299792.458
+        sig_sis = math.sqrt(tE * math.pi / 648000.0 * c * c * D_s / (4 * math.pi * D_ds))
+        assert np.all(np.abs(v / sig_sis - 1) < 5e-3), (v, sig_sis)
+
+
+def test_delay_unit_sis_two_images():
+    """Days per arcsec^2 of Fermat potential against the SIS two-image delay
+    Delta t = D_dt (theta_A^2 - theta_B^2) / (2c) (Eq. time delay between multiple images
+    for psi = theta_E |theta|, images at beta +- theta_E on the source's axis), written
+    with independently typed SI constants (metres, seconds, arcsec = 1/206264.806 rad)."""
+    z_d, z_s, om, H0 = 0.295, 0.654, 0.27, 82.5
+    tE, beta = 1.65, 0.2
+    th = synth.theta_truth(1).copy()
+    for k, v in (("theta_E", tE), ("gamma", 2.0), ("q", 1.0), ("phi", 0.0), ("x_c", 0.0),
+                 ("y_c", 0.0), ("gamma_ext", 0.0), ("H0", H0)):
+        th[synth.IDX[k]] = v
+    img = np.array([[beta + tE, 0.0], [beta - tE, 0.0]])
+    sysd = dict(img_xy=img, sis=np.zeros((0, 3)), z_d=z_d, z_s=z_s, omega_m=om, kappa_ext=0.0)
+    dt = tdelay.delays(th, sysd)[0]
+    D_dt_m = cosmo.distances(z_d, z_s, H0, om)[3] * 3.0856775814913673e22
+    arcsec = 1.0 / 206264.80624709636
+    ta, tb = (beta + tE) * arcsec, (beta - tE) * arcsec
+    ref = D_dt_m * (ta * ta - tb * tb) / (2 * 2.99792458e8) / (24 * 3600.0)
+    # the image nearer the lens (B) arrives later: Delta t_B0 = t_B - t_A > 0
+    assert dt > 0 and abs(dt - ref) < 1e-9 * ref, (dt, ref)
 
 
 def test_fd_gradient_H0_matches_closed_form(w0):

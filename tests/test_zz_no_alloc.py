@@ -1,18 +1,28 @@
 """glad_loglike_static: the log-likelihood for callers that cannot call cudaMalloc while
 they run (code inside someone else's CUDA-graph capture, samplers under a fixed device
-memory budget).  Its scratch is a static device array, so it must give the same logL as
-glad_loglike -- on two calls in a row, since every call reuses the array's old contents
--- and must refuse batches that do not fit.  Collected last on purpose."""
+memory budget).  Its scratch is a static device array and it launches the kernels of
+glad_loglike, so it must give the same logL and chi^2 terms as glad_loglike up to the
+order of the FP64 atomic sums -- on two calls in a row, since every call reuses the array's
+old contents -- for the cylindrically and the spherically aligned models in one batch, in
+the grid and the persistent form of the JAM pair sum, and must refuse batches that do not
+fit.  Collected last on purpose."""
 import ctypes as C
 
 import numpy as np
 import pytest
+
+from oracle import model
+from paper_2504_01302_b300 import synth
 
 from . import systems
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
+
+# The two entry points run the same kernels on the same inputs; only the order of the FP64
+# atomic additions into bin sums and chi^2 terms can differ between runs.
+REL = 1e-10
 
 
 def _call_static(ctx, sid, th, B):
@@ -25,27 +35,52 @@ def _call_static(ctx, sid, th, B):
     return rc, logL, st, terms
 
 
-def test_static_scratch_matches_allocating_entry_point_twice():
-    from paper_2504_01302_b300.glad import GladContext
-    s = systems.small_system(7)
-    ctx = GladContext([s])
-    for seed in (31, 32):  # two calls in a row on different samples
-        th_np = systems.prior_thetas(4, seed=seed)
-        th_np[:2] = systems.near_truth_thetas(2, seed=seed)
+def _near(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    fin = np.isfinite(a)
+    assert np.array_equal(fin, np.isfinite(b))
+    assert np.all(np.abs(a[fin] - b[fin]) <= REL * np.abs(a[fin]) + 1e-9), (a, b)
+
+
+def _sph_system(seed=7):
+    b = dict(systems.small_base(seed), jam_align=1, sph_nr=40, sph_nw=6, sph_nlos=48)
+    return model.build_system(b, synth.theta_truth(1), synth.noise_draws(b, 9100 + seed))
+
+
+def _compare_twice(ctx, n_sys, B, seeds):
+    for seed in seeds:  # two calls in a row on different samples
+        th_np = systems.prior_thetas(B, seed=seed)
+        th_np[: B // 2] = systems.near_truth_thetas(B // 2, seed=seed)
         th = torch.as_tensor(th_np, device="cuda")
-        sid = torch.zeros(4, dtype=torch.int32, device="cuda")
-        rc, logL_s, st_s, terms_s = _call_static(ctx, sid, th, 4)
+        sid = torch.as_tensor(np.arange(B) % n_sys, dtype=torch.int32, device="cuda")
+        rc, logL_s, st_s, terms_s = _call_static(ctx, sid, th, B)
         assert rc == 0, ctx.lib.glad_last_error().decode()
+        assert ctx.lib.glad_last_error().decode() == ""
         logL_a, st_a, terms_a = ctx.loglike(th, sid, terms=True)
         torch.cuda.synchronize()
         assert torch.equal(st_s, st_a)
-        a, b = logL_a.cpu().numpy(), logL_s.cpu().numpy()
-        for i in range(4):
-            assert abs(a[i] - b[i]) < systems.logl_tol(a[i]), (i, a[i], b[i])
-        ts, ta = terms_s.cpu().numpy(), terms_a.cpu().numpy()
-        for i in range(4):
-            for k in range(4):
-                assert abs(ts[i, k] - ta[i, k]) < systems.logl_tol(ta[i, k]), (i, k, ts[i], ta[i])
+        assert int((st_a == 0).sum()) >= B // 2
+        _near(logL_a.cpu().numpy(), logL_s.cpu().numpy())
+        ok = (st_a == 0).cpu().numpy()
+        _near(terms_a.cpu().numpy()[ok], terms_s.cpu().numpy()[ok])
+
+
+def test_static_scratch_matches_allocating_entry_point_twice():
+    from paper_2504_01302_b300.glad import GladContext
+    ctx = GladContext([systems.small_system(7)])
+    _compare_twice(ctx, 1, 4, (31, 32))
+    ctx.close()
+
+
+def test_static_scratch_mixed_models_and_persistent_form():
+    """A cylindrically and a spherically aligned system in one batch (the spherical model's
+    slices of the scratch), first with the default grid form of the pair sum, then with the
+    persistent work-list form pinned (its work list is carved from the scratch too)."""
+    from paper_2504_01302_b300.glad import GladContext
+    ctx = GladContext([systems.small_system(7), _sph_system(7)])
+    _compare_twice(ctx, 2, 8, (41, 42))
+    ctx.set_tuning(100000 + 8042, 4)  # the default shape (8 points, 4 CTAs, unroll 2), persistent
+    _compare_twice(ctx, 2, 8, (43, 44))
     ctx.close()
 
 
