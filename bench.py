@@ -105,7 +105,10 @@ def workload_name(w, grad, B):
                 "60^2 sky x4ss, 50 bins",
              6: "IFU-scale with the spherically aligned Jeans model (Eqs. J1/J2): 400^2 x3ss, "
                 "31^2 PSF, EPL+shear+2 SIS, JAM 40+2x20+BH, polar grid 128x8, 32 LOS nodes, "
-                "128^2 sky x4, GL64, 400 bins"}
+                "128^2 sky x4, GL64, 400 bins",
+             7: "RXJ1131-scale EPL class with the internal mass sheet (dPIE, 40 Gaussians) and "
+                "sampled D_d, D_dt,int: 200^2 x2ss, 21^2 PSF, EPL+shear+SIS, JAM 20+40+2x10+BH, "
+                "60^2 sky x4ss, GL32, 50 bins"}
     n = names.get(w, str(w)) + f"; B={B}"
     if grad:
         n += " (forward + gradient)"
@@ -312,7 +315,7 @@ def measure(args, ctx, lib, systems, th_np, sid_np, B, grad_mode, world, rank, l
     sid = torch.as_tensor(sid_np, device="cuda")
     logL = torch.empty(B, dtype=torch.float64, device="cuda")
     status = torch.empty(B, dtype=torch.int32, device="cuda")
-    grad = torch.empty(B, 20, dtype=torch.float64, device="cuda")
+    grad = torch.empty(B, synth.N_THETA, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
     P = lambda t: C.c_void_p(t.data_ptr())
 
@@ -395,7 +398,7 @@ def measure(args, ctx, lib, systems, th_np, sid_np, B, grad_mode, world, rank, l
     sid_h = torch.as_tensor(sid_np).pin_memory()
     out_h = torch.empty(B, dtype=torch.float64).pin_memory()
     st_h = torch.empty(B, dtype=torch.int32).pin_memory()
-    gr_h = torch.empty(B, 20, dtype=torch.float64).pin_memory()
+    gr_h = torch.empty(B, synth.N_THETA, dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)

@@ -15,11 +15,15 @@
  *  - One context is not thread-safe: serialise calls that use it.
  *  - On a non-zero return, glad_last_error() holds a message (thread-local).
  *
- * Parameter vector theta (20 float64 per sample, angles in radians):
+ * Parameter vector theta (23 float64 per sample, angles in radians):
  *   0 theta_E  1 gamma'  2 q  3 phi (PA, counter-clockwise from +x)  4 x_c  5 y_c
  *   6 gamma_ext  7 phi_ext  8 I_e,src  9 R_e,src  10 n_src  11 x_src  12 y_src
  *   13 I_e,ll  14 R_e,ll  15 inclination i  16 beta (= beta_z)  17 Upsilon (M/L)
- *   18 f_BH = M_BH/M_*  19 H0 [km/s/Mpc]
+ *   18 f_BH = M_BH/M_*  19 H0 [km/s/Mpc]  20 lambda_int (internal mass sheet)
+ *   21 D_d [Mpc]  22 D_dt,int [Mpc]
+ * An entry a system does not use is ignored (it may hold anything, NaN included) and its
+ * gradient is 0: lambda_int without a sheet; H0 in distance mode 1; D_d and D_dt,int in
+ * distance mode 0.
  */
 #ifndef GLAD_H
 #define GLAD_H
@@ -28,7 +32,7 @@
 extern "C" {
 #endif
 
-#define GLAD_NTHETA 20
+#define GLAD_NTHETA 23
 
 typedef enum {
   GLAD_OK = 0,
@@ -76,13 +80,33 @@ enum {
  * observed images against beta_hat mapped back to the image plane (Newton iterations on
  * the lens equation from each observed image) joins the likelihood; NULL leaves it out.
  *
+ * Internal mass sheet (Sect. 3.3, Eqs. kappa int and dpie_kappa): with sheet != 0 the mass
+ * class becomes kappa_int = (1 - lambda_int) + lambda_int kappa_gal: every deflection of the
+ * galaxy model (EPL, external shear, SIS perturbers) and its mass Gaussians (black hole
+ * included) are scaled by lambda_int = theta[20], and a sheet centred on the lens is added:
+ * sheet 1 the dPIE profile with core sheet_rc and truncation sheet_rt arcsec (0: the paper's
+ * 45 and 45.09) normalised to a central convergence 1 - lambda_int; sheet 2 an ideal uniform
+ * sheet kappa = 1 - lambda_int in the lensing (exactly the mass-sheet transform), with the
+ * dPIE standing in for it in the dynamics.  For the dynamics the dPIE goes through a 1-D MGE
+ * of sheet_n round Gaussians log-spaced on [sheet_rmin, sheet_rmax] (0: 40 on [0.1, 1000]),
+ * computed once at glad_create for 1 - lambda_int = 1 and scaled per sample.  lambda_int must
+ * be > 0; a sheet with lambda_int > 1 is negative and, once the total density turns negative
+ * at a probe radius, the sample gets GLAD_SAMPLE_NEGDENS (Sect. 3.3).
+ *
+ * Distances (Sect. 2.3, Eqs. critical_sfd, sfd final): distance_mode 0 derives them from
+ * H0 = theta[19] in flat LambdaCDM (z_d, z_s, omega_m) with D_dt,int = (1 - kappa_ext) D_dt;
+ * distance_mode 1 takes D_d = theta[21] and D_dt,int = theta[22] (Mpc, both > 0) as sampled
+ * parameters (Table 2).  Delays are D_dt,int / c times Fermat-potential differences; the
+ * dynamics scale as D_dt,int / D_d (G Sigma_crit D_d arcsec = c^2/(4 pi) D_dt,int /
+ * ((1 + z_d) D_d) arcsec).
+ *
  * Jeans model (Sect. 3.2): jam_align 0 takes the cylindrically aligned velocity ellipsoid
  * (constant beta_z, the pair form over (tracer, mass, u node) terms); jam_align 1 the
  * spherically aligned one of Eqs. J1/J2 (constant beta = 1 - v_theta^2/v_r^2), solved
  * along the characteristics of J1/J2 on a polar grid of sph_nr radii (log-spaced from a
  * quarter sky sub-sample to 9 x the largest tracer sigma) x sph_nw values of sin^2 theta,
  * and projected with sph_nlos nodes per line of sight; 0 selects the defaults 128, 8, 32.
- * Limits: sph_nr * sph_nw <= 4096 and (mass Gaussians incl. the black hole) x n_gl <= 4096
+ * Limits: sph_nr * sph_nw <= 4096 and (mass Gaussians incl. sheet and black hole) x n_gl <= 4096
  * (GLAD_EUNSUPPORTED beyond, as for sizes whose gradient kernels would need more than
  * 226 KB of shared memory per block).  glad_loglike_grad differentiates both models.
  */
@@ -119,6 +143,11 @@ typedef struct glad_system_desc {
   double z_d, z_s, omega_m, kappa_ext;
   int jam_align;                   /* 0 cylindrically, 1 spherically aligned Jeans model */
   int sph_nr, sph_nw, sph_nlos;    /* rule of the spherically aligned model (0: defaults) */
+  int sheet;                       /* 0 none, 1 dPIE, 2 ideal uniform sheet (see above) */
+  double sheet_rc, sheet_rt;       /* dPIE core and truncation radii [arcsec] (0: 45, 45.09) */
+  int sheet_n;                     /* Gaussians of the sheet's MGE (0: 40) */
+  double sheet_rmin, sheet_rmax;   /* their sigma range [arcsec] (0: 0.1, 1000) */
+  int distance_mode;               /* 0: H0 = theta[19]; 1: D_d = theta[21], D_dt,int = theta[22] */
 } glad_system_desc;
 
 typedef struct glad_ctx glad_ctx;
@@ -135,7 +164,7 @@ void glad_destroy(glad_ctx *ctx);
 /* Batched joint log-likelihood, Eq. chi_general / Eq. Posterior_LD:
  *   logL[b] = -(chi2_pix + chi2_dyn + chi2_tmd + chi2_img)/2   for sample b in [0, B)
  * (chi2_img = 0 for systems without img_sig).
- * sys_id [dev, int32 B], theta [dev, float64 B*20], logL [dev, float64 B],
+ * sys_id [dev, int32 B], theta [dev, float64 B*23], logL [dev, float64 B],
  * sample_status [dev, int32 B], terms [dev, float64 B*4] or NULL: the four chi^2 terms in
  * that order.
  * The per-sample workspace is allocated (cudaMalloc) the first time a batch of this
@@ -144,19 +173,19 @@ void glad_destroy(glad_ctx *ctx);
 glad_status glad_loglike(glad_ctx *ctx, const int *sys_id, const double *theta, int B,
                          double *logL, int *sample_status, double *terms, void *stream);
 
-/* As glad_loglike, plus the gradient grad [dev, float64 B*20] = d logL / d theta from
+/* As glad_loglike, plus the gradient grad [dev, float64 B*23] = d logL / d theta from
  * hand-written adjoint kernels.  Invalid samples get grad = 0. */
 glad_status glad_loglike_grad(glad_ctx *ctx, const int *sys_id, const double *theta, int B,
                               double *logL, double *grad, int *sample_status, double *terms,
                               void *stream);
 
 /* PSF-blurred model image (Eq. dpre with the parametric source) of one sample of
- * system `sys`: theta [dev, 20 float64], image [dev, float32 ny*nx]. */
+ * system `sys`: theta [dev, 23 float64], image [dev, float32 ny*nx]. */
 glad_status glad_model_image(glad_ctx *ctx, int sys, const double *theta, float *image,
                              void *stream);
 
 /* Binned model v_rms (Eqs. binned and Vrms) of one sample of system `sys`:
- * theta [dev, 20 float64], vrms [dev, float32 n_bins] km/s. */
+ * theta [dev, 23 float64], vrms [dev, float32 n_bins] km/s. */
 glad_status glad_vrms(glad_ctx *ctx, int sys, const double *theta, float *vrms, void *stream);
 
 /* Kernel-level timing, for benchmarks.  glad_profile(ctx, 1) makes every later call

@@ -16,7 +16,7 @@ brute-force 2-D convolution.
 """
 import numpy as np
 
-from . import lens, light
+from . import lens, lensmodel, light
 
 
 def subpixel_grid(nx, ny, ss, pix):
@@ -32,10 +32,10 @@ def subpixel_grid(nx, ny, ss, pix):
 
 
 def surface_brightness(x, y, th, sysd, alpha=None):
-    """Source (through the lens) + lens light at sky points (x, y); alpha: the deflection
-    function (lens.alpha_total unless given)."""
+    """Source (through the lens) + lens light at sky points (x, y); alpha: a deflection
+    function alpha(x, y, th, sis) (default: the system's mass class, lensmodel.alpha)."""
     from paper_2504_01302_b300.synth import IDX
-    ax, ay = (alpha or lens.alpha_total)(x, y, th, sysd["sis"])
+    ax, ay = (alpha(x, y, th, sysd["sis"]) if alpha else lensmodel.alpha(x, y, th, sysd))
     bx, by = x - ax, y - ay
     src = light.sersic_xy(bx, by, th[IDX["I_e_src"]], th[IDX["R_e_src"]], th[IDX["n_src"]],
                           sysd["src_q"], th[IDX["x_src"]], th[IDX["y_src"]], sysd["src_phi"])

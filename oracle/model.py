@@ -23,22 +23,34 @@ import math
 import numpy as np
 
 from paper_2504_01302_b300 import synth
-from . import cosmo, imaging, jam, jam_sph, kin, lens, mge, tdelay
+from . import cosmo, imaging, jam, jam_sph, kin, lens, lensmodel, mge, tdelay
 
 IDX = synth.IDX
 
 ST_OK, ST_DOMAIN, ST_DEPROJ, ST_NEGDENS, ST_NONFINITE = 0, 1, 2, 3, 4
 
 
-def check_domain(th):
+def check_domain(th, sysd=None):
+    """Parameters inside their domain.  Entries a system does not use (lambda_int without a
+    sheet; H0 in distance mode 1, D_d and D_dt,int in mode 0) are not checked."""
+    sysd = sysd or {}
     g = th[IDX["gamma"]]
     q = th[IDX["q"]]
     inc = th[IDX["inc"]]
-    ok = (np.all(np.isfinite(th)) and th[IDX["theta_E"]] > 0 and 1.0 < g < 3.0 and 0.0 < q <= 1.0
+    mode1 = int(sysd.get("distance_mode", 0)) == 1
+    used = [i for i in range(synth.N_THETA)
+            if not (i == IDX["lam_int"] and int(sysd.get("sheet", 0)) == 0)
+            and not (i == IDX["H0"] and mode1)
+            and not (i in (IDX["D_d"], IDX["D_dt_int"]) and not mode1)]
+    ok = (np.all(np.isfinite(th[used])) and th[IDX["theta_E"]] > 0 and 1.0 < g < 3.0
+          and 0.0 < q <= 1.0
           and th[IDX["R_e_src"]] > 0 and th[IDX["n_src"]] > 0 and th[IDX["R_e_ll"]] > 0
           and th[IDX["I_e_ll"]] > 0
           and 0.0 < inc <= math.pi / 2 + 1e-12 and th[IDX["beta"]] < 1.0
-          and th[IDX["upsilon"]] >= 0 and th[IDX["f_bh"]] >= 0 and th[IDX["H0"]] > 0)
+          and th[IDX["upsilon"]] >= 0 and th[IDX["f_bh"]] >= 0
+          and (mode1 or th[IDX["H0"]] > 0)
+          and (int(sysd.get("sheet", 0)) == 0 or th[IDX["lam_int"]] > 0)
+          and (not mode1 or (th[IDX["D_d"]] > 0 and th[IDX["D_dt_int"]] > 0)))
     return bool(ok)
 
 
@@ -62,11 +74,20 @@ def mass_mge(th, sysd, L_tot):
                                       sysd["r_soft"]),
                       sysd["mass_rmin"], sysd["mass_rmax"], sysd["n_mge_mass"], sysd["mge_P"])
     qp = np.full(len(s), th[IDX["q"]])
+    # the internal mass sheet (Sect. 3.3, Eq. kappa int): the galaxy (with its black hole)
+    # scaled by lambda_int, the sheet's own round Gaussians after it, the black hole last
+    lam = lensmodel.lam_of(th, sysd)
+    A = lam * A
+    sh = lensmodel.sheet_mass(th, sysd)
+    if sh is not None:
+        A = np.concatenate([A, sh["kap0"]])
+        s = np.concatenate([s, sh["sig"]])
+        qp = np.concatenate([qp, sh["qp"]])
     if sysd["has_bh"]:
         m_star = th[IDX["upsilon"]] * L_tot * sysd["L_scale"]
         m_bh = th[IDX["f_bh"]] * m_star
         sb = sysd["bh_sigma"]
-        A = np.append(A, m_bh / (2 * math.pi * sb * sb))
+        A = np.append(A, lam * m_bh / (2 * math.pi * sb * sb))
         s = np.append(s, sb)
         qp = np.append(qp, 1.0)
     return dict(kap0=A, sig=s, qp=qp)
@@ -101,7 +122,7 @@ def dynamics_setup(th, sysd):
         return ST_DEPROJ, None
     if not positive_density(tr, ms, inc):
         return ST_NEGDENS, None
-    v2u = cosmo.v2_unit(sysd["z_d"], sysd["z_s"], sysd["omega_m"], sysd["kappa_ext"])
+    v2u = lensmodel.v2_unit(th, sysd)
     X, Y, r_max = sky_geometry(sysd)
     xp, yp = lens.frame(X, Y, th[IDX["x_c"]], th[IDX["y_c"]], th[IDX["phi"]])
     d = dict(tr=tr, ms=ms, v2u=v2u, r_max=r_max, X=X, xp=xp, yp=yp)
@@ -172,7 +193,7 @@ def evaluate(th, sysd, want=False):
     """Full evaluation: dict with logL, the three chi^2 terms, image, v_rms, delays, status."""
     th = np.asarray(th, np.float64)
     out = dict(logL=-np.inf, chi2_pix=np.nan, chi2_dyn=np.nan, chi2_tmd=np.nan, status=ST_OK)
-    if not check_domain(th):
+    if not check_domain(th, sysd):
         out["status"] = ST_DOMAIN
         return out
     v, st, extra = dynamics(th, sysd, want_maps=want)
@@ -199,11 +220,24 @@ def loglike(th, sysd):
     return evaluate(th, sysd)["logL"]
 
 
+def used_params(sysd):
+    """Indices of the parameter entries a system uses: lambda_int only with a sheet, H0 only in
+    distance mode 0, D_d and D_dt,int only in mode 1 (the others do not enter logL)."""
+    mode1 = int(sysd.get("distance_mode", 0)) == 1
+    out = [i for i in range(synth.N_BASE) if not (mode1 and i == IDX["H0"])]
+    if int(sysd.get("sheet", 0)):
+        out.append(IDX["lam_int"])
+    if mode1:
+        out += [IDX["D_d"], IDX["D_dt_int"]]
+    return out
+
+
 def grad_fd(th, sysd, h_rel=1e-6, which=None):
-    """Central finite differences of logL with h = h_rel * parameter scale (FP64)."""
+    """Central finite differences of logL with h = h_rel * parameter scale (FP64), over the
+    parameters the system uses (or those in which); the others are 0."""
     th = np.asarray(th, np.float64)
     g = np.zeros(len(th))
-    idx = range(len(th)) if which is None else which
+    idx = used_params(sysd) if which is None else which
     for i in idx:
         h = h_rel * synth.THETA_SCALE[i]
         tp, tm = th.copy(), th.copy()

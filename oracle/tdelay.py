@@ -22,33 +22,31 @@ small displacement of one image.
 """
 import numpy as np
 
-from . import cosmo, lens
+from . import lensmodel
 
 
-def beta_hat(th, sis, img):
+def beta_hat(th, sysd, img):
     x, y = img[:, 0], img[:, 1]
-    ax, ay = lens.alpha_total(x, y, th, sis)
-    a11, a12, a21, a22 = lens.jac_total(x, y, th, sis)
+    ax, ay = lensmodel.alpha(x, y, th, sysd)
+    a11, a12, a21, a22 = lensmodel.jac(x, y, th, sysd)
     det = (1 - a11) * (1 - a22) - a12 * a21
     w = 1.0 / np.abs(det)
     bx, by = x - ax, y - ay
     return np.array([np.sum(w * bx) / w.sum(), np.sum(w * by) / w.sum()])
 
 
-def fermat(th, sis, img, bh):
+def fermat(th, sysd, img, bh):
     x, y = img[:, 0], img[:, 1]
-    return 0.5 * ((x - bh[0]) ** 2 + (y - bh[1]) ** 2) - lens.psi_total(x, y, th, sis)
+    return 0.5 * ((x - bh[0]) ** 2 + (y - bh[1]) ** 2) - lensmodel.psi(x, y, th, sysd)
 
 
 def delays(th, sysd):
-    """Model delays Delta t_i0 [days], i = 1..N_img-1."""
-    from paper_2504_01302_b300.synth import IDX
+    """Model delays Delta t_i0 [days], i = 1..N_img-1 (the lens model and distances of the
+    system's mass class and distance mode, oracle/lensmodel.py)."""
     img = np.asarray(sysd["img_xy"], np.float64)
-    bh = beta_hat(th, sysd["sis"], img)
-    ph = fermat(th, sysd["sis"], img, bh)
-    k = cosmo.delay_days_per_arcsec2(sysd["z_d"], sysd["z_s"], th[IDX["H0"]],
-                                     sysd["omega_m"], sysd["kappa_ext"])
-    return k * (ph[1:] - ph[0])
+    bh = beta_hat(th, sysd, img)
+    ph = fermat(th, sysd, img, bh)
+    return lensmodel.delay_unit(th, sysd) * (ph[1:] - ph[0])
 
 
 def chi2_tmd(dt, sysd):
@@ -61,14 +59,13 @@ def predicted_images(th, sysd, tol=1e-14, iters=50):
     """theta_pre: beta_hat of the observed images mapped back to the image plane by Newton
     iterations on theta - alpha(theta) = beta_hat started at each observed image."""
     img = np.asarray(sysd["img_xy"], np.float64)
-    sis = sysd["sis"]
-    bh = beta_hat(th, sis, img)
+    bh = beta_hat(th, sysd, img)
     out = np.empty_like(img)
     for j, t0 in enumerate(img):
         t = t0.copy()
         for _ in range(iters):
-            ax, ay = lens.alpha_total(np.array([t[0]]), np.array([t[1]]), th, sis)
-            a11, a12, a21, a22 = lens.jac_total(np.array([t[0]]), np.array([t[1]]), th, sis)
+            ax, ay = lensmodel.alpha(np.array([t[0]]), np.array([t[1]]), th, sysd)
+            a11, a12, a21, a22 = lensmodel.jac(np.array([t[0]]), np.array([t[1]]), th, sysd)
             f = np.array([t[0] - ax[0] - bh[0], t[1] - ay[0] - bh[1]])
             A = np.array([[1 - a11[0], -a12[0]], [-a21[0], 1 - a22[0]]])
             step = np.linalg.solve(A, f)

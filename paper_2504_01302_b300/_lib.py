@@ -33,6 +33,9 @@ class SystemDesc(C.Structure):
         ("n_img", C.c_int), ("img_xy", _d), ("dt_obs", _d), ("dt_sig", _d), ("img_sig", _d),
         ("z_d", C.c_double), ("z_s", C.c_double), ("omega_m", C.c_double), ("kappa_ext", C.c_double),
         ("jam_align", C.c_int), ("sph_nr", C.c_int), ("sph_nw", C.c_int), ("sph_nlos", C.c_int),
+        ("sheet", C.c_int), ("sheet_rc", C.c_double), ("sheet_rt", C.c_double),
+        ("sheet_n", C.c_int), ("sheet_rmin", C.c_double), ("sheet_rmax", C.c_double),
+        ("distance_mode", C.c_int),
     ]
 
 

@@ -116,6 +116,10 @@ __device__ inline Dual<N, double> dlog(const Dual<N, double> &a) {
   return dual_apply(a, log(a.v), 1.0 / a.v);
 }
 template <int N>
+__device__ inline Dual<N, double> dlog1p(const Dual<N, double> &a) {
+  return dual_apply(a, log1p(a.v), 1.0 / (1.0 + a.v));
+}
+template <int N>
 __device__ inline Dual<N, double> dpow(const Dual<N, double> &a, const Dual<N, double> &b) {
   return dexp(b * dlog(a));
 }
@@ -150,6 +154,7 @@ __device__ inline Dual<N, float> dlog2(const Dual<N, float> &a) {
 __device__ inline double dsqrt(double a) { return sqrt(a); }
 __device__ inline double dexp(double a) { return exp(a); }
 __device__ inline double dlog(double a) { return log(a); }
+__device__ inline double dlog1p(double a) { return log1p(a); }
 __device__ inline double dpow(double a, double b) { return pow(a, b); }
 __device__ inline double dsin(double a) { return sin(a); }
 __device__ inline double dcos(double a) { return cos(a); }

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <complex>
 #include <cstdarg>
 #include <string>
 #include <vector>
@@ -80,6 +81,31 @@ double comoving(double z, double H0, double om) {
   return C_KMS / H0 * 0.5 * z * s;
 }
 
+// Euler coefficients (Abate & Whitt 2006) in the Gaussian-mixture scaling of Sect. 3.2:
+// eta_m = (-1)^m 2 sqrt(2 pi) 10^(P/3) xi_m and chi_m = sqrt(2 P ln10 / 3 + 2 pi i m)
+void euler_coefficients(int P, std::vector<double> &eta, std::vector<std::complex<double>> &chi) {
+  std::vector<double> xi(2 * P + 1, 0.0);
+  eta.assign(2 * P + 1, 0.0);
+  chi.assign(2 * P + 1, 0.0);
+  xi[0] = 0.5;
+  for (int m = 1; m <= P; ++m) xi[m] = 1.0;
+  xi[2 * P] = pow(2.0, -P);
+  double binom = 1.0;  // C(P, k)
+  for (int k = 1; k < P; ++k) {
+    binom = binom * (P - k + 1) / k;
+    xi[2 * P - k] = xi[2 * P - k + 1] + pow(2.0, -P) * binom;
+  }
+  const double A = 2.0 * P * log(10.0) / 3.0;
+  for (int m = 0; m <= 2 * P; ++m) {
+    eta[m] = (m % 2 ? -1.0 : 1.0) * 2.0 * SQRT2PI_D * pow(10.0, P / 3.0) * xi[m];
+    // principal square root of A + 2 pi i m
+    const double re = A, im = 2.0 * PI_D * m;
+    const double r = sqrt(hypot(re, im));
+    const double th = 0.5 * atan2(im, re);
+    chi[m] = std::complex<double>(r * cos(th), r * sin(th));
+  }
+}
+
 template <class T>
 T *upload(SysHost &sh, const T *src, size_t n) {
   T *d = nullptr;
@@ -116,12 +142,22 @@ glad_status validate(const glad_system_desc &d, int idx) {
   REQ(d.sph_nr == 0 || d.sph_nr >= 4, "sph_nr must be 0 (default) or >= 4", idx);
   REQ(d.sph_nw == 0 || d.sph_nw >= 2, "sph_nw must be 0 (default) or >= 2", idx);
   REQ(d.sph_nlos >= 0, "sph_nlos must be >= 0", idx);
+  REQ(d.sheet >= 0 && d.sheet <= 2, "sheet must be 0, 1 or 2", idx);
+  REQ(d.distance_mode == 0 || d.distance_mode == 1, "distance_mode must be 0 or 1", idx);
+  if (d.sheet) {
+    const double rc = d.sheet_rc > 0 ? d.sheet_rc : 45.0, rt = d.sheet_rt > 0 ? d.sheet_rt : 45.09;
+    REQ(d.sheet_rc >= 0 && d.sheet_rt >= 0 && rt > rc, "sheet radii need 0 < rc < rt", idx);
+    REQ(d.sheet_n == 0 || d.sheet_n >= 2, "sheet_n must be 0 (default) or >= 2", idx);
+    const double lo = d.sheet_rmin > 0 ? d.sheet_rmin : 0.1, hi = d.sheet_rmax > 0 ? d.sheet_rmax : 1000.0;
+    REQ(d.sheet_rmin >= 0 && d.sheet_rmax >= 0 && hi > lo, "bad sheet MGE range", idx);
+  }
 #undef REQ
 #define SUP(cond, ...) \
   if (!(cond)) return fail(GLAD_EUNSUPPORTED, "system %d: " __VA_ARGS__)
   SUP(d.psf_k <= GLAD_MAX_PSF, "psf_k > %d", idx, GLAD_MAX_PSF);
   SUP(d.n_bins <= GLAD_MAX_BINS, "n_bins > %d", idx, GLAD_MAX_BINS);
-  SUP(d.n_mge_mass <= GLAD_MAX_MASS, "n_mge_mass > %d", idx, GLAD_MAX_MASS);
+  const int n_sheet = d.sheet ? (d.sheet_n ? d.sheet_n : 40) : 0;
+  SUP(d.n_mge_mass + n_sheet <= GLAD_MAX_MASS, "n_mge_mass + sheet Gaussians > %d", idx, GLAD_MAX_MASS);
   SUP(d.mge_P <= GLAD_MAX_P, "mge_P > %d", idx, GLAD_MAX_P);
   SUP(d.n_img <= GLAD_MAX_IMG, "n_img > %d", idx, GLAD_MAX_IMG);
   SUP(1 + d.n_ll2 <= 4, "more than 4 lens-light components", idx);
@@ -136,12 +172,12 @@ glad_status validate(const glad_system_desc &d, int idx) {
   if (d.jam_align == 1) {
     const int nr = d.sph_nr ? d.sph_nr : SPH_DEFAULT_NR, nw = d.sph_nw ? d.sph_nw : SPH_DEFAULT_NW;
     SUP(nr * nw <= GLAD_SPH_MAX_GRID, "sph_nr * sph_nw > %d", idx, GLAD_SPH_MAX_GRID);
-    SUP((d.n_mge_mass + (d.has_bh ? 1 : 0)) * d.n_gl <= GLAD_SPH_MAX_MG,
+    SUP((d.n_mge_mass + n_sheet + (d.has_bh ? 1 : 0)) * d.n_gl <= GLAD_SPH_MAX_MG,
         "mass Gaussians x n_gl > %d for the spherically aligned model", idx, GLAD_SPH_MAX_MG);
     SUP(d.sph_nlos <= 4096, "sph_nlos > 4096", idx);
     // shared memory of the gradient kernels (grid adjoint: coefficients and their accumulators;
     // line-of-sight adjoint: grid, grid adjoint and per-thread tracer accumulators)
-    const size_t mg = (size_t)(d.n_mge_mass + (d.has_bh ? 1 : 0)) * d.n_gl;
+    const size_t mg = (size_t)(d.n_mge_mass + n_sheet + (d.has_bh ? 1 : 0)) * d.n_gl;
     const size_t ladj = (size_t)nr * (nw - 1) * 16 + (size_t)nr * (nw | 1) * 8 + (size_t)nl * (16 + 128 * 8);
     const size_t gadj = mg * 40 + 8 * 64 * 16 + (size_t)nl * 24 + 16;
     SUP(ladj <= 226 * 1024 && gadj <= 226 * 1024,
@@ -242,18 +278,49 @@ glad_status build_system(int idx, const glad_system_desc &d, SysHost &sh, SysDev
   sd.n_bins = d.n_bins;
   sd.v_obs = upload(sh, d.v_obs, d.n_bins);
   sd.v_sig = upload(sh, d.v_sig, d.n_bins);
-  // MGE Gaussians
+  // MGE Gaussians: mass [galaxy nM][internal sheet nS][black hole]
   const int nM = d.n_mge_mass;
-  const int nMt = nM + (d.has_bh ? 1 : 0);
-  std::vector<double> sig_m(nMt), mw_m(nM);
+  const int nS = d.sheet ? (d.sheet_n ? d.sheet_n : 40) : 0;
+  const int nMt = nM + nS + (d.has_bh ? 1 : 0);
+  std::vector<double> sig_m(nMt), mw_m(nM), sheet_a1(std::max(nS, 1), 0.0);
   {
     const double lo = log(d.mass_rmin), hi = log(d.mass_rmax), dl = (hi - lo) / (nM - 1);
     for (int j = 0; j < nM; ++j) {
       sig_m[j] = exp(lo + dl * j);
       mw_m[j] = (j == 0 || j == nM - 1 ? 0.5 : 1.0) * dl / SQRT2PI_D;
     }
-    if (d.has_bh) sig_m[nM] = d.bh_sigma;
+    if (d.has_bh) sig_m[nM + nS] = d.bh_sigma;
   }
+  sd.sheet = d.sheet;
+  sd.sh_rc = d.sheet_rc > 0 ? d.sheet_rc : 45.0;
+  sd.sh_rt = d.sheet_rt > 0 ? d.sheet_rt : 45.09;
+  if (nS) {
+    // the dPIE sheet's 1-D MGE (Sect. 3.2, Euler inversion) at 1 - lambda_int = 1, in FP64 once:
+    // kappa(R) = [1/sqrt(R^2 + rc^2) - 1/sqrt(R^2 + rt^2)] / (1/rc - 1/rt) (Eq. dpie_kappa with
+    // central value 1); per sample the amplitudes are scaled by 1 - lambda_int
+    const double rc = sd.sh_rc, rt = sd.sh_rt;
+    const double lo = log(d.sheet_rmin > 0 ? d.sheet_rmin : 0.1);
+    const double hi = log(d.sheet_rmax > 0 ? d.sheet_rmax : 1000.0);
+    const double dl = (hi - lo) / (nS - 1);
+    const int P = d.mge_P;
+    std::vector<double> eta;
+    std::vector<std::complex<double>> chi;
+    euler_coefficients(P, eta, chi);
+    const double norm = 1.0 / ((rt - rc) / (rc * rt));
+    for (int j = 0; j < nS; ++j) {
+      const double sg = exp(lo + dl * j);
+      double f = 0.0;
+      for (int m = 0; m <= 2 * P; ++m) {
+        const std::complex<double> z = sg * chi[m], z2 = z * z;
+        const std::complex<double> F = norm * (1.0 / std::sqrt(z2 + rc * rc) - 1.0 / std::sqrt(z2 + rt * rt));
+        f += eta[m] * F.real();
+      }
+      sig_m[nM + j] = sg;
+      sheet_a1[j] = (j == 0 || j == nS - 1 ? 0.5 : 1.0) * dl / SQRT2PI_D * f;
+    }
+  }
+  sd.n_sheet = nS;
+  sd.sheet_A1 = upload(sh, sheet_a1.data(), sheet_a1.size());
   std::vector<double> sig_l, mw_l, qp_l;
   std::vector<int> comp_of;
   for (int cc = 0; cc < 1 + d.n_ll2; ++cc) {
@@ -282,25 +349,11 @@ glad_status build_system(int idx, const glad_system_desc &d, SysHost &sh, SysDev
   // Euler coefficients (Abate & Whitt 2006) in the Gaussian-mixture scaling of Sect. 3.2
   {
     const int P = d.mge_P;
-    std::vector<double> xi(2 * P + 1, 0.0), eta(2 * P + 1);
+    std::vector<double> eta;
+    std::vector<std::complex<double>> chic;
+    euler_coefficients(P, eta, chic);
     std::vector<double2> chi(2 * P + 1);
-    xi[0] = 0.5;
-    for (int m = 1; m <= P; ++m) xi[m] = 1.0;
-    xi[2 * P] = pow(2.0, -P);
-    double binom = 1.0;  // C(P, k)
-    for (int k = 1; k < P; ++k) {
-      binom = binom * (P - k + 1) / k;
-      xi[2 * P - k] = xi[2 * P - k + 1] + pow(2.0, -P) * binom;
-    }
-    const double A = 2.0 * P * log(10.0) / 3.0;
-    for (int m = 0; m <= 2 * P; ++m) {
-      eta[m] = (m % 2 ? -1.0 : 1.0) * 2.0 * SQRT2PI_D * pow(10.0, P / 3.0) * xi[m];
-      // principal square root of A + 2 pi i m
-      const double re = A, im = 2.0 * PI_D * m;
-      const double r = sqrt(hypot(re, im));
-      const double th = 0.5 * atan2(im, re);
-      chi[m] = make_double2(r * cos(th), r * sin(th));
-    }
+    for (int m = 0; m <= 2 * P; ++m) chi[m] = make_double2(chic[m].real(), chic[m].imag());
     sd.mge_P = P;
     sd.eta = upload(sh, eta.data(), eta.size());
     sd.chi = upload(sh, chi.data(), chi.size());
@@ -413,8 +466,12 @@ glad_status build_system(int idx, const glad_system_desc &d, SysHost &sh, SysDev
     const double D_d = cd / (1 + d.z_d), D_s = cs / (1 + d.z_s), D_ds = (cs - cd) / (1 + d.z_s);
     const double D_dt = (1 + d.z_d) * D_d * D_s / D_ds;
     const double D_int = (1.0 - d.kappa_ext) * D_dt;
-    sd.v2unit = C_KMS * C_KMS / (4.0 * PI_D) * D_int / ((1 + d.z_d) * D_d) * ARCSEC;
+    sd.distance_mode = d.distance_mode;
+    // mode 1 scales these per sample: v^2 unit by D_dt,int / D_d, delays by D_dt,int [Mpc]
+    sd.v2unit = d.distance_mode == 1 ? C_KMS * C_KMS / (4.0 * PI_D) / (1 + d.z_d) * ARCSEC
+                                     : C_KMS * C_KMS / (4.0 * PI_D) * D_int / ((1 + d.z_d) * D_d) * ARCSEC;
     sd.dt_per_arcsec2_H0 = D_int * H * MPC_KM / C_KMS * ARCSEC * ARCSEC / DAY_S;
+    sd.dt_per_arcsec2_Mpc = MPC_KM / C_KMS * ARCSEC * ARCSEC / DAY_S;
   }
   sd.n_img = d.n_img;
   sd.img_xy = upload(sh, d.img_xy, 2 * (size_t)d.n_img);

@@ -50,8 +50,10 @@ struct SysDev {
   const float *w_val;    // [nnz]
   int n_bins;
   const float *v_obs, *v_sig;
-  // MGE
+  // MGE: mass Gaussians are ordered [galaxy n_mass][sheet n_sheet][black hole]
   int n_mass, n_mass_tot, n_light;
+  int n_sheet;                             // round Gaussians of the internal sheet (0: none)
+  const double *sheet_A1;                  // [n_sheet] their amplitudes at 1 - lambda_int = 1
   const int *lcomp_of;   // [n_light]
   const double *sig_mass, *sig_light;      // [n_mass_tot], [n_light]
   const double *mw_mass, *mw_light;        // w_n * dln(sigma) / sqrt(2 pi)
@@ -66,8 +68,14 @@ struct SysDev {
   const float *sb_cx, *sb_cy;               // [n_light]: log2(e)/(2 s^2), log2(e)/(2 s^2 q'^2)
   int has_bh;
   double bh_sigma, L_scale;
-  double v2unit;                            // km^2/s^2 per (kappa * arcsec)
-  double dt_per_arcsec2_H0;                 // days per arcsec^2 times H0
+  double v2unit;                            // km^2/s^2 per (kappa * arcsec); distance mode 1:
+                                            // per (kappa * arcsec) and unit D_dt,int / D_d
+  double dt_per_arcsec2_H0;                 // days per arcsec^2 times H0 (distance mode 0)
+  double dt_per_arcsec2_Mpc;                // days per arcsec^2 per Mpc of D_dt,int (mode 1)
+  int distance_mode;                        // 0: H0 = theta[19]; 1: theta[21], theta[22]
+  // internal mass sheet: 0 none, 1 dPIE (core sh_rc, truncation sh_rt), 2 ideal (uniform)
+  int sheet;
+  double sh_rc, sh_rt;
   int n_img;
   const double *img_xy, *dt_obs, *dt_sig;
   const double *img_sig;                    // [n_img] or null: no image-position term
@@ -99,6 +107,13 @@ struct LensP {
   float pref_d[3];               // d pref / d (theta_E, t, q)
   float gext, c2pe, s2pe;        // shear strength and cos/sin(2 phi_ext)
   float src_bnp;                 // d b_n / d n of the source
+  // internal mass sheet: the galaxy's deflection is scaled by lam and the sheet's added,
+  // alpha_sheet = (1 - lam) u(R^2) (x - x_c, y - y_c) with u = 1 (ideal) or, for the dPIE,
+  // u = 2 rc rt [1 + (rc + rt)/(Q_c + Q_t)] / ((rc + Q_c)(rt + Q_t)), Q = sqrt(R^2 + r^2)
+  // (the difference of the two cored terms written without cancellation)
+  float lam;
+  int sheet;
+  float sh_rc2, sh_rt2, sh_rc, sh_rt;
 };
 
 // per-sample dynamics scalars (FP64)

@@ -94,7 +94,7 @@ __device__ __forceinline__ SersicD sersic_d(float R2, float Ie, float ninv, floa
   return s;
 }
 
-#define NGL 15  // lensing parameters theta[0..14]
+#define NGL 16  // lensing parameters theta[0..14] and lambda_int (theta[20]) in slot 15
 
 __global__ void __launch_bounds__(LENS_THREADS) k_image_grad(const SysDev *__restrict__ sysv,
                                                              const int *__restrict__ sys_id,
@@ -171,6 +171,23 @@ __global__ void __launch_bounds__(LENS_THREADS) k_image_grad(const SysDev *__res
           ax.v += te * sx * ir;
           ay.v += te * sy * ir;
         }
+        // internal mass sheet: lambda x galaxy + (1 - lambda) u (dx, dy); the sheet follows the
+        // lens centre (tangents 4, 5 through dx, dy); d alpha / d lambda = galaxy - u (dx, dy)
+        float dax_dl = 0.0f, day_dl = 0.0f;
+        if (L.sheet) {
+          D8 u(1.0f);
+          if (L.sheet == 1) {
+            const D8 R2 = dx * dx + dy * dy;
+            const D8 Qc = dsqrt(R2 + L.sh_rc2), Qt = dsqrt(R2 + L.sh_rt2);
+            u = (2.0f * L.sh_rc * L.sh_rt) * (1.0f + (L.sh_rc + L.sh_rt) / (Qc + Qt)) /
+                ((L.sh_rc + Qc) * (L.sh_rt + Qt));
+          }
+          dax_dl = ax.v - u.v * dx.v;
+          day_dl = ay.v - u.v * dy.v;
+          const D8 om = (1.0f - L.lam) * u;
+          ax = L.lam * ax + om * dx;
+          ay = L.lam * ay + om * dy;
+        }
         // source at beta: d beta / d theta_i = -d alpha / d theta_i (i < 8); centre: -1
         const float bx = x - ax.v - L.src_x, by = y - ay.v - L.src_y;
         const float cs = S.src_cphi, sn = S.src_sphi, iq2 = 1.0f / (S.src_q * S.src_q);
@@ -195,6 +212,7 @@ __global__ void __launch_bounds__(LENS_THREADS) k_image_grad(const SysDev *__res
         gsub[12] = -dI_dby;
         gsub[13] = 0.0f;
         gsub[14] = 0.0f;
+        gsub[15] = -(dI_dbx * dax_dl + dI_dby * day_dl);
         // lens light: depends on phi, x_c, y_c through (x', y') and on I_e, R_e of component 0
         for (int c = 0; c < S.n_lcomp; ++c) {
           const float Re2 = L.ll_Rei[c] * L.ll_Rei[c];
@@ -226,7 +244,8 @@ __global__ void __launch_bounds__(LENS_THREADS) k_image_grad(const SysDev *__res
   if (threadIdx.x < NGL) {
     double s = 0.0;
     for (int w = 0; w < LENS_THREADS / 32; ++w) s += (double)red[w][threadIdx.x];
-    atomicAdd(&grad[(size_t)b * GLAD_NTHETA + threadIdx.x], s);
+    const int t = threadIdx.x < 15 ? threadIdx.x : 20;
+    if (s != 0.0) atomicAdd(&grad[(size_t)b * GLAD_NTHETA + t], s);
   }
 }
 
@@ -835,8 +854,14 @@ __global__ void __launch_bounds__(256) k_grad_chain(const SysDev *__restrict__ s
     if (tid < 4) a_glob[tid] = t[2 * ML + 2 * MM + tid];
   }
   if (tid < GLAD_NTHETA) gsm[tid] = 0.0;
+  __shared__ double sumC;  // sum_j adj(C_j) C_j: the dynamics' derivative by ln(velocity^2 unit)
+  if (tid == 0) sumC = 0.0;
   __syncthreads();
   const size_t bl = (size_t)b * max_light;
+  // internal mass sheet and distance mode (as in k_prep)
+  const double lam = S.sheet ? th[20] : 1.0;
+  const double v2u = S.distance_mode == 1 ? S.v2unit * th[22] / th[21] : S.v2unit;
+  const int nS = S.n_sheet;
 
   // (b) per Gaussian: MGE amplitudes (analytic partials of F), deprojection, C_j, e2_j
   const double tE = th[0], g = th[1], q = th[2], inc = th[15];
@@ -923,11 +948,25 @@ __global__ void __launch_bounds__(256) k_grad_chain(const SysDev *__restrict__ s
     A.d[2] = -A.v / (1.0 + q);
     const D9 qp = D9::var(q, 2);
     const D9 qi2 = (qp * qp - C2) / S2;
-    const D9 Cj = 2.0 * SQRT2PI_D * S.v2unit * sg * qp * A;
+    const D9 Cj = (2.0 * SQRT2PI_D * v2u * lam * sg) * qp * A;
     const D9 e2 = 1.0 - qi2;
     for (int i = 0; i < 9; ++i) {
       const double v = a_C[j] * Cj.d[i] + a_e2[j] * e2.d[i];
       if (v != 0.0) atomicAdd(&gsm[i < 3 ? i : 10 + i], v);
+    }
+    const double aC = a_C[j] * Cj.v;
+    if (aC != 0.0) {
+      if (S.sheet) atomicAdd(&gsm[20], aC / lam);  // C_j proportional to lambda
+      atomicAdd(&sumC, aC);
+    }
+  }
+  // the sheet's round Gaussians: C_j = 2 sqrt(2 pi) v2u sigma_j (1 - lambda) A1_j, e2_j = 0
+  for (int j = tid; j < nS; j += blockDim.x) {
+    const double c1 = 2.0 * SQRT2PI_D * v2u * S.sig_mass[nM + j] * S.sheet_A1[j];
+    const double aC = a_C[nM + j];
+    if (aC != 0.0) {
+      atomicAdd(&gsm[20], -aC * c1);
+      atomicAdd(&sumC, aC * c1 * (1.0 - lam));
     }
   }
   __syncthreads();
@@ -943,32 +982,44 @@ __global__ void __launch_bounds__(256) k_grad_chain(const SysDev *__restrict__ s
       }
       const D9 ups = D9::var(th[17], 7), fbh = D9::var(th[18], 8);
       const double sb = S.bh_sigma;
-      const D9 A = fbh * ups * L * (S.L_scale / (2.0 * PI_D * sb * sb));
+      const D9 A = fbh * ups * L * (lam * S.L_scale / (2.0 * PI_D * sb * sb));
       const D9 qi2 = (1.0 - C2) / S2;
-      const D9 Cj = 2.0 * SQRT2PI_D * S.v2unit * sb * A;
+      const D9 Cj = 2.0 * SQRT2PI_D * v2u * sb * A;
       const D9 e2 = 1.0 - qi2;
+      const int jb = nM + nS;
       for (int i = 0; i < 9; ++i) {
-        const double v = a_C[nM] * Cj.d[i] + a_e2[nM] * e2.d[i];
-        if (v != 0.0) gsm[i < 3 ? i : 10 + i] += v;
+        const double v = a_C[jb] * Cj.d[i] + a_e2[jb] * e2.d[i];
+        if (v != 0.0) atomicAdd(&gsm[i < 3 ? i : 10 + i], v);
       }
+      const double aC = a_C[jb] * Cj.v;
+      if (S.sheet) atomicAdd(&gsm[20], aC / lam);
+      atomicAdd(&sumC, aC);
     }
     // globals: sin^2 i, cos^2 i (theta 15) and b = 1/(1-beta) (theta 16)
     gsm[15] += a_glob[0] * S2.d[5] + a_glob[1] * C2.d[5] + a_glob[3];
     const double bb = 1.0 / (1.0 - th[16]);
     gsm[16] += a_glob[2] * bb * bb;
   }
-  if (tid >= 32 && tid < 41) {
+  if (tid >= 32 && tid < 42) {
     // time delays and image positions: -(chi2_tmd + chi2_img)/2 by duals through the FP64
-    // lens model, one tangent per thread (theta 0..7 and H0 = theta 19)
+    // lens model, one tangent per thread: theta 0..7, the delay distance (H0 = theta 19 in
+    // distance mode 0, D_dt,int = theta 22 in mode 1) and lambda_int (theta 20, with a sheet)
     const int q = tid - 32;
-    DT1 tt[8];
-    for (int i = 0; i < 8; ++i) tt[i] = i == q ? DT1::var(th[i], 0) : DT1(th[i]);
-    const DT1 h0 = q == 8 ? DT1::var(th[19], 0) : DT1(th[19]);
-    DT1 chi = chi2_tmd_t<DT1>(tt, h0, S.img_xy, S.n_img, S.dt_obs, S.dt_sig,
-                              S.dt_per_arcsec2_H0, S.sis, S.n_sis);
-    // image positions: lens parameters only
-    if (S.img_sig && q < 8) chi = chi + chi2_img_t<DT1>(tt, S.img_xy, S.n_img, S.img_sig, S.sis, S.n_sis);
-    atomicAdd(&gsm[q < 8 ? q : 19], -0.5 * chi.d[0]);
+    const int t = q < 8 ? q : (q == 8 ? (S.distance_mode == 1 ? 22 : 19) : 20);
+    if (t != 20 || S.sheet) {
+      DT1 tt[GLAD_NTHETA];
+      for (int i = 0; i < GLAD_NTHETA; ++i) tt[i] = i == t ? DT1::var(th[i], 0) : DT1(th[i]);
+      DT1 chi = chi2_tmd_t<DT1>(tt, S);
+      // image positions: lens parameters (and the sheet) only
+      if (S.img_sig && t != 19 && t != 22) chi = chi + chi2_img_t<DT1>(tt, S);
+      atomicAdd(&gsm[t], -0.5 * chi.d[0]);
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && S.distance_mode == 1 && sumC != 0.0) {
+    // C_j proportional to D_dt,int / D_d
+    gsm[22] += sumC / th[22];
+    gsm[21] -= sumC / th[21];
   }
   __syncthreads();
   // atomic: the lensing adjoint, on the other stream, may be adding into the same entries

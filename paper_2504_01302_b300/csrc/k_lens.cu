@@ -1,6 +1,7 @@
 // Lensing half of the likelihood (FP32 bulk, FP64 chi^2):
 //  k_image: one thread per image pixel; each of its ss x ss sub-pixels is ray-shot
-//    through EPL + shear + SIS (lens equation beta = theta - alpha, Sect. 3.1.1),
+//    through EPL + shear + SIS, scaled by lambda_int and joined by the internal mass sheet
+//    for systems that have one (Sect. 3.3) (lens equation beta = theta - alpha, Sect. 3.1.1),
 //    the Sersic source is evaluated at beta and the lens-light Sersics at theta,
 //    and the average is stored.
 //  k_conv: PSF blurring (discrete convolution, zero outside the image) of a 32x8
@@ -75,6 +76,19 @@ __global__ void __launch_bounds__(LENS_THREADS) k_image(const SysDev *__restrict
         const float ir = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
         ax += te * sx * ir;
         ay += te * sy * ir;
+      }
+      if (L.sheet) {
+        // internal mass sheet: lambda x galaxy + (1 - lambda) u(R^2) (x - x_c, y - y_c)
+        float u = 1.0f;
+        if (L.sheet == 1) {
+          const float R2 = dx * dx + dy * dy;
+          const float Qc = sqrtf(R2 + L.sh_rc2), Qt = sqrtf(R2 + L.sh_rt2);
+          u = 2.0f * L.sh_rc * L.sh_rt * (1.0f + (L.sh_rc + L.sh_rt) / (Qc + Qt)) /
+              ((L.sh_rc + Qc) * (L.sh_rt + Qt));
+        }
+        const float om = (1.0f - L.lam) * u;
+        ax = L.lam * ax + om * dx;
+        ay = L.lam * ay + om * dy;
       }
       // source at beta
       const float bx = x - ax - L.src_x, by = y - ay - L.src_y;

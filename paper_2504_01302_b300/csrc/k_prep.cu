@@ -46,14 +46,21 @@ __device__ inline double epl_kappa_re(cplx z, double coef, double g, double rs2)
   return coef * F.r;
 }
 
-__device__ inline int domain_ok(const double *th) {
+// Parameters inside their domain; entries the system does not use (lambda_int without a
+// sheet, H0 in distance mode 1, D_d and D_dt,int in mode 0) are not looked at.
+__device__ inline int domain_ok(const double *th, const SysDev &S) {
   bool ok = true;
-  for (int i = 0; i < GLAD_NTHETA; ++i) ok = ok && isfinite(th[i]);
+  const bool mode1 = S.distance_mode == 1;
+  for (int i = 0; i < 19; ++i) ok = ok && isfinite(th[i]);
   const double g = th[1], q = th[2], inc = th[15];
   ok = ok && th[0] > 0.0 && g > 1.0 && g < 3.0 && q > 0.0 && q <= 1.0 && th[9] > 0.0 &&
        th[10] > 0.0 && th[14] > 0.0 && th[13] > 0.0 && inc > 0.0 &&
-       inc <= 1.5707963267948966 + 1e-12 && th[16] < 1.0 && th[17] >= 0.0 && th[18] >= 0.0 &&
-       th[19] > 0.0;
+       inc <= 1.5707963267948966 + 1e-12 && th[16] < 1.0 && th[17] >= 0.0 && th[18] >= 0.0;
+  if (mode1)
+    ok = ok && isfinite(th[21]) && isfinite(th[22]) && th[21] > 0.0 && th[22] > 0.0;
+  else
+    ok = ok && isfinite(th[19]) && th[19] > 0.0;
+  if (S.sheet) ok = ok && isfinite(th[20]) && th[20] > 0.0;
   return ok ? 1 : 0;
 }
 
@@ -70,7 +77,7 @@ __global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
   __shared__ double sh_q[GLAD_MAX_LIGHT + GLAD_MAX_MASS + 1];
   __shared__ int sh_flag;
 
-  const int ok = domain_ok(th);
+  const int ok = domain_ok(th, S);
   if (!ok) {
     if (tid == 0) {
       ws.status[b] = GLAD_SAMPLE_DOMAIN;
@@ -114,13 +121,26 @@ __global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
   }
   if (tid == 0) sh_flag = 0;
   __syncthreads();
+  // internal mass sheet (Sect. 3.3, Eq. kappa int): the galaxy's Gaussians scaled by lambda,
+  // then the sheet's round Gaussians, (1 - lambda) times their unit amplitudes
+  const int nS = S.n_sheet;
+  const double lam = S.sheet ? th[20] : 1.0;
+  for (int j = tid; j < nM + nS; j += blockDim.x) {
+    if (j < nM) {
+      sh_A[nL + j] *= lam;
+    } else {
+      sh_A[nL + j] = (1.0 - lam) * S.sheet_A1[j - nM];
+      sh_q[nL + j] = 1.0;
+    }
+  }
+  __syncthreads();
   if (tid == 0) {
     double L = 0.0;
     for (int k = 0; k < nL; ++k) L += 2.0 * PI_D * sh_A[k] * S.sig_light[k] * S.sig_light[k] * sh_q[k];
     if (S.has_bh) {
-      const double mbh = th[18] * th[17] * L * S.L_scale;
-      sh_A[nL + nM] = mbh / (2.0 * PI_D * S.bh_sigma * S.bh_sigma);
-      sh_q[nL + nM] = 1.0;
+      const double mbh = lam * th[18] * th[17] * L * S.L_scale;
+      sh_A[nL + nM + nS] = mbh / (2.0 * PI_D * S.bh_sigma * S.bh_sigma);
+      sh_q[nL + nM + nS] = 1.0;
     }
     // deprojection needs cos^2 i < q'^2 for every Gaussian (App. A)
     double qmin = q;
@@ -136,6 +156,8 @@ __global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
     return;
   }
   const int nG = nL + nMt;
+  // velocity^2 unit of the dynamics: fixed (distance mode 0) or times D_dt,int / D_d (mode 1)
+  const double v2u = S.distance_mode == 1 ? S.v2unit * th[22] / th[21] : S.v2unit;
   // ---- deprojection; densities rho0 (tracer nu0 and mass rho0) and intrinsic q
   for (int k = tid; k < nG; k += blockDim.x) {
     const double sg = k < nL ? S.sig_light[k] : S.sig_mass[k - nL];
@@ -149,7 +171,7 @@ __global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
       ws.I0f[bl + k] = (float)sh_A[k];
     } else {
       const int j = k - nL;
-      ws.Cj[bm + j] = 2.0 * SQRT2PI_D * S.v2unit * qp * sh_A[k] * sg;
+      ws.Cj[bm + j] = 2.0 * SQRT2PI_D * v2u * qp * sh_A[k] * sg;
       ws.e2[bm + j] = 1.0 - qi * qi;
     }
   }
@@ -182,7 +204,7 @@ __global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
   __shared__ double im_ax[GLAD_MAX_IMG], im_ay[GLAD_MAX_IMG], im_w[GLAD_MAX_IMG], im_psi[GLAD_MAX_IMG];
   if (tid >= 32 && tid < 32 + S.n_img) {
     const int i = tid - 32;
-    LensEvalT<double> e = lens_eval_t<double>(S.img_xy[2 * i], S.img_xy[2 * i + 1], th, S.sis, S.n_sis);
+    LensEvalT<double> e = lens_eval_t<double>(S.img_xy[2 * i], S.img_xy[2 * i + 1], th, S);
     im_ax[i] = e.ax;
     im_ay[i] = e.ay;
     im_psi[i] = e.psi;
@@ -248,6 +270,12 @@ __global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
     L.src_bn = (float)sersic_bn_d(th[10]);
     L.src_x = (float)th[11];
     L.src_y = (float)th[12];
+    L.sheet = S.sheet;
+    L.lam = (float)lam;
+    L.sh_rc = (float)S.sh_rc;
+    L.sh_rt = (float)S.sh_rt;
+    L.sh_rc2 = (float)(S.sh_rc * S.sh_rc);
+    L.sh_rt2 = (float)(S.sh_rt * S.sh_rt);
     for (int c = 0; c < S.n_lcomp && c < 4; ++c) {
       const double Ie = c == 0 ? th[13] : S.lcomp[4 * c];
       const double Re = c == 0 ? th[14] : S.lcomp[4 * c + 1];
@@ -270,7 +298,7 @@ __global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
     }
     bhx /= wsum;
     bhy /= wsum;
-    const double kdt = S.dt_per_arcsec2_H0 / th[19];
+    const double kdt = delay_unit_t<double>(th, S);
     double phi0 = 0.0, chi2 = 0.0;
     for (int i = 0; i < S.n_img; ++i) {
       const double x = S.img_xy[2 * i], y = S.img_xy[2 * i + 1];
@@ -286,7 +314,7 @@ __global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
   }
   if (tid == 64 && S.img_sig) {
     // ---- image positions (FP64), beside the delays
-    ws.terms[4 * (size_t)b + 3] = chi2_img_t<double>(th, S.img_xy, S.n_img, S.img_sig, S.sis, S.n_sis);
+    ws.terms[4 * (size_t)b + 3] = chi2_img_t<double>(th, S);
   }
 }
 

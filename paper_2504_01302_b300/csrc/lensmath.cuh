@@ -7,12 +7,23 @@
 //    complex shear = ((1-t) alpha - kappa z)/conj(z).
 //  * External shear psi = gamma/2 R^2 cos(2 phi - 2 phi_ext) about the lens centre (Sect. 3.3).
 //  * SIS perturber psi = theta_E |theta - theta_s|.
+//  * Internal mass sheet (Sect. 3.3, Eqs. kappa int, dpie_kappa): the galaxy terms above are
+//    scaled by lambda_int = theta[20] and the sheet centred on the lens added: the dPIE with
+//    central convergence 1 - lambda_int, a0 f = 2 (1 - lambda)/(1/r_c - 1/r_t),
+//      alpha = a0 f [1/(r_c + Q_c) - 1/(r_t + Q_t)] (x - x_c), Q = sqrt(R^2 + r^2)
+//            = (1 - lambda) 2 r_c r_t [1 + (r_c + r_t)/(Q_c + Q_t)] / ((r_c + Q_c)(r_t + Q_t)) (x - x_c),
+//      psi   = a0 f [g(r_c) - g(r_t)],  g(r) = R^2/(Q + r) - r ln(1 + R^2/(2 r (Q + r))),
+//      d alpha_i / d x_j = s delta_ij + 2 s' x_i x_j with s' = d s / d(R^2);
+//    or the ideal sheet alpha = (1 - lambda)(x - x_c), psi = (1 - lambda) R^2 / 2.
 //  * Delays (Eqs. fermat potential, time delay between multiple images, chi2_tmd): source
-//    at the |mu|-weighted mean of the images mapped back (Sect. 3.1.1), image 0 the reference.
+//    at the |mu|-weighted mean of the images mapped back (Sect. 3.1.1), image 0 the reference;
+//    days per arcsec^2 of Fermat potential D_dt,int / c from H0 (distance mode 0) or from
+//    D_dt,int = theta[22] (mode 1).
 #pragma once
 #include <math.h>
 
 #include "dual.cuh"
+#include "glad_internal.cuh"
 
 template <class T>
 struct LensEvalT {
@@ -21,10 +32,13 @@ struct LensEvalT {
   T psi;                 // potential
 };
 
-// EPL + shear + SIS at sky point (x, y); th = parameter vector (entries 0..7 used).  The
-// position may be a plain double or of the parameter type (Newton iterates on positions).
+// EPL + shear + SIS (and the system's internal sheet) at sky point (x, y); th = the full
+// parameter vector (entries 0..7 and, with a sheet, 20 used).  The position may be a plain
+// double or of the parameter type (Newton iterates on positions).
 template <class T, class P = double>
-__device__ inline LensEvalT<T> lens_eval_t(P x, P y, const T *th, const double *sis, int n_sis) {
+__device__ inline LensEvalT<T> lens_eval_t(P x, P y, const T *th, const SysDev &S) {
+  const double *sis = S.sis;
+  const int n_sis = S.n_sis;
   const T tE = th[0], g = th[1], q = th[2], phi = th[3], xc = th[4], yc = th[5];
   const T gext = th[6], pext = th[7];
   const T t = g - 1.0;
@@ -93,19 +107,60 @@ __device__ inline LensEvalT<T> lens_eval_t(P x, P y, const T *th, const double *
     e.a22 = e.a22 + te * sx * sx / r3;
     e.psi = e.psi + te * r;
   }
+  if (S.sheet) {
+    const T lam = th[20], om = 1.0 - lam;
+    e.ax = lam * e.ax;
+    e.ay = lam * e.ay;
+    e.a11 = lam * e.a11;
+    e.a12 = lam * e.a12;
+    e.a21 = lam * e.a21;
+    e.a22 = lam * e.a22;
+    e.psi = lam * e.psi;
+    const T R2 = dx * dx + dy * dy;
+    if (S.sheet == 2) {
+      e.ax = e.ax + om * dx;
+      e.ay = e.ay + om * dy;
+      e.a11 = e.a11 + om;
+      e.a22 = e.a22 + om;
+      e.psi = e.psi + 0.5 * om * R2;
+    } else {
+      const double rc = S.sh_rc, rt = S.sh_rt;
+      const T Qc = dsqrt(R2 + rc * rc), Qt = dsqrt(R2 + rt * rt);
+      const T sv = om * (2.0 * rc * rt) * (1.0 + (rc + rt) / (Qc + Qt)) / ((rc + Qc) * (rt + Qt));
+      const T a0f = om * (2.0 * rc * rt / (rt - rc));
+      const T sp = a0f * (1.0 / (2.0 * Qt * (rt + Qt) * (rt + Qt)) - 1.0 / (2.0 * Qc * (rc + Qc) * (rc + Qc)));
+      e.ax = e.ax + sv * dx;
+      e.ay = e.ay + sv * dy;
+      e.a11 = e.a11 + sv + 2.0 * sp * dx * dx;
+      e.a12 = e.a12 + 2.0 * sp * dx * dy;
+      e.a21 = e.a21 + 2.0 * sp * dx * dy;
+      e.a22 = e.a22 + sv + 2.0 * sp * dy * dy;
+      const T gc = R2 / (Qc + rc) - rc * dlog1p(R2 / (2.0 * rc * (Qc + rc)));
+      const T gt = R2 / (Qt + rt) - rt * dlog1p(R2 / (2.0 * rt * (Qt + rt)));
+      e.psi = e.psi + a0f * (gc - gt);
+    }
+  }
   return e;
 }
 
-// chi^2 of the delays; h0 is the Hubble constant (theta[19]).
+// Days of delay per arcsec^2 of Fermat potential: D_dt,int / c from H0 = theta[19] (distance
+// mode 0) or D_dt,int = theta[22] (mode 1).
 template <class T>
-__device__ inline T chi2_tmd_t(const T *th, T h0, const double *img_xy, int n_img,
-                               const double *dt_obs, const double *dt_sig, double dt_per_arcsec2_H0,
-                               const double *sis, int n_sis) {
-  T w[8], bx[8], by[8], psi[8];
+__device__ inline T delay_unit_t(const T *th, const SysDev &S) {
+  if (S.distance_mode == 1) return S.dt_per_arcsec2_Mpc * th[22];
+  return S.dt_per_arcsec2_H0 / th[19];
+}
+
+// chi^2 of the delays (th: the full parameter vector).
+template <class T>
+__device__ inline T chi2_tmd_t(const T *th, const SysDev &S) {
+  const double *img_xy = S.img_xy;
+  const int n_img = S.n_img;
+  T w[GLAD_MAX_IMG], bx[GLAD_MAX_IMG], by[GLAD_MAX_IMG], psi[GLAD_MAX_IMG];
   T wsum(0.0), bhx(0.0), bhy(0.0);
   for (int i = 0; i < n_img; ++i) {
     const double x = img_xy[2 * i], y = img_xy[2 * i + 1];
-    LensEvalT<T> e = lens_eval_t<T>(x, y, th, sis, n_sis);
+    LensEvalT<T> e = lens_eval_t<T>(x, y, th, S);
     const T det = (1.0 - e.a11) * (1.0 - e.a22) - e.a12 * e.a21;
     w[i] = 1.0 / dfabs(det);
     bx[i] = x - e.ax;
@@ -117,7 +172,7 @@ __device__ inline T chi2_tmd_t(const T *th, T h0, const double *img_xy, int n_im
   }
   bhx = bhx / wsum;
   bhy = bhy / wsum;
-  const T kdt = dt_per_arcsec2_H0 / h0;
+  const T kdt = delay_unit_t<T>(th, S);
   T phi0(0.0), chi2(0.0);
   for (int i = 0; i < n_img; ++i) {
     const double x = img_xy[2 * i], y = img_xy[2 * i + 1];
@@ -126,7 +181,7 @@ __device__ inline T chi2_tmd_t(const T *th, T h0, const double *img_xy, int n_im
       phi0 = ph;
     } else {
       const T dt = kdt * (ph - phi0);
-      const T r = (dt_obs[i - 1] - dt) / dt_sig[i - 1];
+      const T r = (S.dt_obs[i - 1] - dt) / S.dt_sig[i - 1];
       chi2 = chi2 + r * r;
     }
   }
@@ -135,14 +190,15 @@ __device__ inline T chi2_tmd_t(const T *th, T h0, const double *img_xy, int n_im
 
 // beta_hat: the |mu|-weighted mean of the observed images mapped to the source plane.
 template <class T>
-__device__ inline void beta_hat_t(const T *th, const double *img_xy, int n_img, const double *sis,
-                                  int n_sis, T &bhx, T &bhy) {
+__device__ inline void beta_hat_t(const T *th, const SysDev &S, T &bhx, T &bhy) {
+  const double *img_xy = S.img_xy;
+  const int n_img = S.n_img;
   T wsum(0.0);
   bhx = T(0.0);
   bhy = T(0.0);
   for (int i = 0; i < n_img; ++i) {
     const double x = img_xy[2 * i], y = img_xy[2 * i + 1];
-    LensEvalT<T> e = lens_eval_t<T>(x, y, th, sis, n_sis);
+    LensEvalT<T> e = lens_eval_t<T>(x, y, th, S);
     const T det = (1.0 - e.a11) * (1.0 - e.a22) - e.a12 * e.a21;
     const T w = 1.0 / dfabs(det);
     wsum = wsum + w;
@@ -159,16 +215,17 @@ __device__ inline void beta_hat_t(const T *th, const double *img_xy, int n_img, 
 // dual type converge with the values).
 #define GLAD_NEWTON_IT 12
 template <class T>
-__device__ inline T chi2_img_t(const T *th, const double *img_xy, int n_img, const double *img_sig,
-                               const double *sis, int n_sis) {
+__device__ inline T chi2_img_t(const T *th, const SysDev &S) {
+  const double *img_xy = S.img_xy, *img_sig = S.img_sig;
+  const int n_img = S.n_img;
   T bhx, bhy;
-  beta_hat_t<T>(th, img_xy, n_img, sis, n_sis, bhx, bhy);
+  beta_hat_t<T>(th, S, bhx, bhy);
   T chi2(0.0);
   for (int i = 0; i < n_img; ++i) {
     const double x = img_xy[2 * i], y = img_xy[2 * i + 1];
     T tx(x), ty(y);
     for (int it = 0; it < GLAD_NEWTON_IT; ++it) {
-      LensEvalT<T> e = lens_eval_t<T, T>(tx, ty, th, sis, n_sis);
+      LensEvalT<T> e = lens_eval_t<T, T>(tx, ty, th, S);
       const T fx = tx - e.ax - bhx, fy = ty - e.ay - bhy;
       const T m11 = 1.0 - e.a11, m12 = -e.a12, m21 = -e.a21, m22 = 1.0 - e.a22;
       const T det = m11 * m22 - m12 * m21;

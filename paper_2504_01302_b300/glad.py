@@ -9,7 +9,7 @@ import torch
 
 from . import _lib
 
-NTHETA = 20
+NTHETA = 23
 
 
 def _ptr(a, ctype):
@@ -88,6 +88,11 @@ class GladContext:
         d.jam_align = int(s.get("jam_align", 0))
         d.sph_nr, d.sph_nw = int(s.get("sph_nr", 0)), int(s.get("sph_nw", 0))
         d.sph_nlos = int(s.get("sph_nlos", 0))
+        d.sheet = int(s.get("sheet", 0))
+        d.sheet_rc, d.sheet_rt = float(s.get("sheet_rc", 0.0)), float(s.get("sheet_rt", 0.0))
+        d.sheet_n = int(s.get("sheet_n", 0))
+        d.sheet_rmin, d.sheet_rmax = float(s.get("sheet_rmin", 0.0)), float(s.get("sheet_rmax", 0.0))
+        d.distance_mode = int(s.get("distance_mode", 0))
 
     # ------------------------------------------------------------------ calls
     def _check_theta(self, theta, sys_id):
@@ -113,7 +118,7 @@ class GladContext:
         return (logL, status, tr) if terms else (logL, status)
 
     def loglike_grad(self, theta, sys_id=None, terms=False):
-        """logL [B], d logL/d theta [B, 20], status [B] (and the chi^2 terms)."""
+        """logL [B], d logL/d theta [B, 23], status [B] (and the chi^2 terms)."""
         theta, sys_id, B = self._check_theta(theta, sys_id)
         dev = theta.device
         logL = torch.empty(B, dtype=torch.float64, device=dev)

@@ -23,12 +23,16 @@ import math
 
 import numpy as np
 
-# Parameter vector layout (20 values, float64).  Angles are in radians.
+# Parameter vector layout (23 values, float64).  Angles are in radians.  The last three are
+# the internal mass sheet's lambda_int (used by systems with a sheet) and the lens and model
+# time-delay distances D_d, D_dt,int [Mpc] (used by systems in distance mode 1, which then
+# ignore H0).
 THETA_NAMES = (
     "theta_E", "gamma", "q", "phi", "x_c", "y_c", "gamma_ext", "phi_ext",
     "I_e_src", "R_e_src", "n_src", "x_src", "y_src", "I_e_ll", "R_e_ll",
-    "inc", "beta", "upsilon", "f_bh", "H0",
+    "inc", "beta", "upsilon", "f_bh", "H0", "lam_int", "D_d", "D_dt_int",
 )
+N_BASE = 20  # entries drawn by draw_prior (the others stay at their Table 2 mock values)
 N_THETA = len(THETA_NAMES)
 IDX = {n: i for i, n in enumerate(THETA_NAMES)}
 
@@ -36,7 +40,7 @@ IDX = {n: i for i, n in enumerate(THETA_NAMES)}
 THETA_SCALE = np.array([
     1.0, 1.0, 1.0, 1.0, 0.1, 0.1, 0.1, 1.0,
     1.0, 0.1, 1.0, 0.1, 0.1, 1.0, 1.0,
-    1.0, 0.1, 1.0, 0.01, 100.0,
+    1.0, 0.1, 1.0, 0.01, 100.0, 1.0, 100.0, 100.0,
 ])
 
 DEG = math.pi / 180.0
@@ -181,22 +185,39 @@ def theta_truth(workload: int) -> np.ndarray:
     t[IDX["upsilon"]] = 1.0 if workload == 0 else 1.95
     t[IDX["f_bh"]] = 0.0 if workload == 0 else 0.0025
     t[IDX["H0"]] = 82.5
+    # Table 2 mock values: no sheet (lambda_int = 1), D_d = 775 Mpc, D_dt,int = 1823 Mpc
+    t[IDX["lam_int"]] = 1.0
+    t[IDX["D_d"]] = 775.0
+    t[IDX["D_dt_int"]] = 1823.0
     return t
 
 
 PRIOR_LO = np.array([1.60, 1.8, 0.7, 25 * DEG, -0.02, -0.02, 0.07, 1.32,
                      0.9, 0.18, 1.35, 0.04, 0.01, 0.45, 0.9,
-                     80 * DEG, -0.3, 0.5, 0.0, 50.0])
+                     80 * DEG, -0.3, 0.5, 0.0, 50.0, 0.5, 600.0, 1000.0])
 PRIOR_HI = np.array([1.70, 2.2, 0.9, 35 * DEG, 0.02, 0.02, 0.11, 1.52,
                      1.1, 0.22, 1.65, 0.06, 0.03, 0.55, 1.1,
-                     90 * DEG, 0.3, 3.5, 0.005, 120.0])
+                     90 * DEG, 0.3, 3.5, 0.005, 120.0, 1.5, 1000.0, 4000.0])
 
 
 def draw_prior(rng, B: int) -> np.ndarray:
     """B parameter vectors from the uniform priors around the RXJ1131-like truth
-    (inclination, anisotropy, M/L and H0 ranges as in Table 2)."""
+    (inclination, anisotropy, M/L and H0 ranges as in Table 2).  Only the first N_BASE
+    entries are drawn; lambda_int, D_d and D_dt,int keep their mock values (1, 775, 1823)."""
+    u = rng.random((B, N_BASE))
+    th = np.tile(theta_truth(1), (B, 1))
+    th[:, :N_BASE] = PRIOR_LO[:N_BASE] + u * (PRIOR_HI[:N_BASE] - PRIOR_LO[:N_BASE])
+    return th
+
+
+def draw_prior_sheet(rng, B: int, lam_hi: float = 1.5) -> np.ndarray:
+    """B parameter vectors for systems with the internal mass sheet in distance mode 1: every
+    entry drawn, lambda_int in [0.5, lam_hi] (Table 2: [0.5, 1.5]), D_d in [600, 1000] and
+    D_dt,int in [1000, 4000] Mpc (Table 2), H0 drawn too but unused."""
     u = rng.random((B, N_THETA))
-    return PRIOR_LO + u * (PRIOR_HI - PRIOR_LO)
+    hi = PRIOR_HI.copy()
+    hi[IDX["lam_int"]] = lam_hi
+    return PRIOR_LO + u * (hi - PRIOR_LO)
 
 
 # ---------------------------------------------------------------------------
@@ -214,19 +235,24 @@ def workload_systems(w: int, small: bool = False):
     5: workload 1's system with the spherically aligned Jeans model (Eqs. J1/J2; polar
        grid 128 x 8, 32 line-of-sight nodes), B=256
     6: workload 4's system with the spherically aligned Jeans model (same rule), B=4096
+    7: workload 1's system as the EPL mass class with the internal mass sheet (the dPIE of
+       Eq. dpie_kappa, 40 Gaussians on [0.1, 1000]") and sampled distances D_d, D_dt,int
+       (distance mode 1, Table 2), B=256
     """
-    rng = np.random.Generator(np.random.PCG64(1000 + {5: 1, 6: 4}.get(w, w)))
+    rng = np.random.Generator(np.random.PCG64(1000 + {5: 1, 6: 4, 7: 1}.get(w, w)))
     if w == 0:
         s = base_system("w0", n_img_px=64, ss=1, psf_k=11, sky=32, kss=1, n_mass=10,
                         n_light=10, n_gl=32, n_bins=20, bins="annular", rng=rng,
                         has_bh=False, n_sis=0, second_light=False)
         return [s], 1
-    if w in (1, 2, 5):
+    if w in (1, 2, 5, 7):
         s = base_system("w1", n_img_px=200, ss=2, psf_k=21, sky=60, kss=4, n_mass=20,
                         n_light=10, n_gl=32, n_bins=50, bins="voronoi", rng=rng,
                         has_bh=True, n_sis=1, second_light=True)
         if w == 5:
             s.update(name="w5", jam_align=1, sph_nr=128, sph_nw=8, sph_nlos=32)
+        if w == 7:
+            s.update(name="w7", sheet=1, distance_mode=1)
         return [s], (64 if w == 2 else 256)
     if w == 3:
         systems = []
@@ -262,7 +288,9 @@ def workload_thetas(w: int, B: int, n_sys: int):
     rng = np.random.Generator(np.random.PCG64(1000 + w + 77))
     if w == 0:
         return theta_truth(0)[None, :].copy(), np.zeros(1, np.int32)
-    th = draw_prior(rng, B)
+    # the sheet workload draws lambda_int in [0.5, 1]: above 1 the EPL class's outer density
+    # turns negative and the Jeans model rejects the sample (Sect. 3.3)
+    th = draw_prior_sheet(rng, B, lam_hi=1.0) if w == 7 else draw_prior(rng, B)
     if n_sys == 1:
         sid = np.zeros(B, np.int32)
     else:

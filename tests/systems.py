@@ -38,7 +38,9 @@ def near_truth_thetas(n, seed=13, scale=0.002):
     """Draws close to the truth (the posterior region a sampler spends its time in)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     span = synth.PRIOR_HI - synth.PRIOR_LO
-    th = synth.theta_truth(1)[None, :] + scale * span * rng.standard_normal((n, synth.N_THETA))
+    th = np.tile(synth.theta_truth(1), (n, 1))
+    nb = synth.N_BASE
+    th[:, :nb] += scale * span[:nb] * rng.standard_normal((n, nb))
     th[:, synth.IDX["f_bh"]] = np.abs(th[:, synth.IDX["f_bh"]])
     th[:, synth.IDX["inc"]] = np.minimum(th[:, synth.IDX["inc"]], np.pi / 2)
     return th
@@ -121,12 +123,13 @@ def _oracle_loglike(args):
 
 def oracle_grad_fd_pool(th, s, which=None, h_rel=1e-6):
     """model.grad_fd (FP64 central differences of the oracle, h = h_rel x parameter scale)
-    with the 2 x len(which) oracle evaluations spread over the host cores (spawn pool: the
-    calling process may already hold a CUDA context)."""
+    over the parameters the system uses (or those in which), the 2 x len(which) oracle
+    evaluations spread over the host cores (spawn pool: the calling process may already
+    hold a CUDA context)."""
     import multiprocessing as mp
     import os
     th = np.asarray(th, np.float64)
-    idx = list(range(len(th))) if which is None else list(which)
+    idx = model.used_params(s) if which is None else list(which)
     jobs = []
     for i in idx:
         h = h_rel * synth.THETA_SCALE[i]

@@ -45,7 +45,7 @@ def _sph(**kw):
     (_set("z_s", 0.1), GLAD_EINVAL, "bad cosmology"),
     (_set("n_mge_light", [1, 4]), GLAD_EINVAL, "n_mge_light < 2"),
     (_set("psf", np.ones((65, 65), np.float32) / 65 ** 2), GLAD_EUNSUPPORTED, "psf_k >"),
-    (_set("n_mge_mass", 200), GLAD_EUNSUPPORTED, "n_mge_mass >"),
+    (_set("n_mge_mass", 200), GLAD_EUNSUPPORTED, "n_mge_mass + sheet Gaussians >"),
     (_set("mge_P", 40), GLAD_EUNSUPPORTED, "mge_P >"),
     (_set("n_mge_light", [100, 40]), GLAD_EUNSUPPORTED, "tracer Gaussians >"),
     (_set("img_xy", np.zeros((9, 2))), GLAD_EUNSUPPORTED, "n_img >"),
@@ -57,6 +57,12 @@ def _sph(**kw):
     (_sph(sph_nr=128, sph_nw=64), GLAD_EUNSUPPORTED, "sph_nr * sph_nw >"),
     (_sph(sph_nlos=5000), GLAD_EUNSUPPORTED, "sph_nlos >"),
     (_sph(n_gl=512), GLAD_EUNSUPPORTED, "for the spherically aligned model"),
+    (_set("sheet", 3), GLAD_EINVAL, "sheet must be 0, 1 or 2"),
+    (_set("distance_mode", 2), GLAD_EINVAL, "distance_mode must be 0 or 1"),
+    (lambda s: s.update(sheet=1, sheet_rc=50.0, sheet_rt=45.0), GLAD_EINVAL, "sheet radii"),
+    (lambda s: s.update(sheet=1, sheet_n=1), GLAD_EINVAL, "sheet_n must be"),
+    (lambda s: s.update(sheet=1, sheet_rmin=10.0, sheet_rmax=1.0), GLAD_EINVAL, "bad sheet MGE range"),
+    (lambda s: s.update(sheet=1, sheet_n=120), GLAD_EUNSUPPORTED, "n_mge_mass + sheet Gaussians >"),
 ])
 def test_create_rejects_invalid_descriptors(mutate, status, words):
     msg = _create(mutate)

@@ -95,7 +95,7 @@ def test_grad_mixed_systems():
     sid = torch.as_tensor(np.array([1, 0], np.int32), device="cuda")
     _, g, st = ctx.loglike_grad(_th(th), sid)
     g = g.cpu().numpy()
-    which = [i for i in range(20) if synth.THETA_NAMES[i] not in ("upsilon", "f_bh")]
+    which = [i for i in range(synth.N_BASE) if synth.THETA_NAMES[i] not in ("upsilon", "f_bh")]
     assert_grad_close(g[0], model.grad_fd(th[0], sb), which=which)  # no BH: Upsilon, f_BH inert
     assert_grad_close(g[1], model.grad_fd(th[1], sa))
 

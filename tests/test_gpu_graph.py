@@ -19,6 +19,9 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 PERSISTENT = 100000 + 8042  # 8 points per thread, 4 CTAs/SM, unroll 2, persistent form
+# replay against eager call: the same kernels, but FP32 atomic sums (bin accumulators in shared
+# memory) and FP64 atomics reorder between runs, ~1e-7 relative in each chi^2 term
+SAME = 1e-6
 
 
 @pytest.fixture(scope="module")
@@ -69,9 +72,9 @@ def test_graph_replay_matches_eager_and_oracle(uneven):
         l_ref, st_ref, terms_ref = ref[name]
         assert np.array_equal(status.cpu().numpy(), st_ref)
         assert int((st_ref == 0).sum()) > B // 4
-        _near(l_ref, logL.cpu().numpy(), 1e-10)
+        _near(l_ref, logL.cpu().numpy(), SAME)
         ok = st_ref == 0
-        _near(terms_ref[ok].ravel(), terms.cpu().numpy()[ok].ravel(), 1e-10)
+        _near(terms_ref[ok].ravel(), terms.cpu().numpy()[ok].ravel(), SAME)
     # sampled samples of the replayed batch (theta b) against the oracle: the first valid
     # sample of each of the two cheapest systems (fewest sky sub-samples x table entries)
     cost = [(s["kx"] * s["kss"]) * (s["ky"] * s["kss"]) * sum(s["n_mge_light"]) *
@@ -100,7 +103,7 @@ def test_graph_replay_of_the_gradient(uneven):
         ref[name] = (l.cpu().numpy(), g.cpu().numpy(), st.cpu().numpy())
     theta = torch.as_tensor(ta, device="cuda")
     logL = torch.empty(B, dtype=torch.float64, device="cuda")
-    grad = torch.empty(B, 20, dtype=torch.float64, device="cuda")
+    grad = torch.empty(B, synth.N_THETA, dtype=torch.float64, device="cuda")
     status = torch.empty(B, dtype=torch.int32, device="cuda")
     P = lambda t: C.c_void_p(t.data_ptr())
     graph = torch.cuda.CUDAGraph()
@@ -115,7 +118,7 @@ def test_graph_replay_of_the_gradient(uneven):
         torch.cuda.synchronize()
         l_ref, g_ref, st_ref = ref[name]
         assert np.array_equal(status.cpu().numpy(), st_ref) and np.all(st_ref == 0)
-        _near(l_ref, logL.cpu().numpy(), 1e-10)
+        _near(l_ref, logL.cpu().numpy(), SAME)
         g = grad.cpu().numpy()
         # FP64 atomics reorder between calls: bound at the gradient scale of each sample
         for b in range(B):

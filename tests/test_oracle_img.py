@@ -24,7 +24,7 @@ def test_predicted_images_solve_the_lens_equation():
     s = _sys()
     th = systems.near_truth_thetas(1, seed=31)[0]
     pre = tdelay.predicted_images(th, s)
-    bh = tdelay.beta_hat(th, s["sis"], np.asarray(s["img_xy"]))
+    bh = tdelay.beta_hat(th, s, np.asarray(s["img_xy"]))
     ax, ay = lens.alpha_total(pre[:, 0], pre[:, 1], th, s["sis"])
     assert np.max(np.abs(pre[:, 0] - ax - bh[0])) < 1e-12
     assert np.max(np.abs(pre[:, 1] - ay - bh[1])) < 1e-12

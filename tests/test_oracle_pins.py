@@ -319,11 +319,11 @@ def test_delays_inverse_H0_and_exact_images(w0):
     t2[synth.IDX["H0"]] *= 1.5
     assert np.allclose(tdelay.delays(t2, s) * 1.5, d1, rtol=1e-12)
     # images are exact solutions for qso_beta: beta_hat is the true source and grad phi = 0
-    bh = tdelay.beta_hat(th, s["sis"], s["img_xy"])
+    bh = tdelay.beta_hat(th, s, s["img_xy"])
     assert np.max(np.abs(bh - s["qso_beta"])) < 1e-10
     h = 1e-6
     for x, y in s["img_xy"]:
-        F = lambda a, b: tdelay.fermat(th, s["sis"], np.array([[a, b]]), bh)[0]
+        F = lambda a, b: tdelay.fermat(th, s, np.array([[a, b]]), bh)[0]
         assert abs((F(x + h, y) - F(x - h, y)) / (2 * h)) < 1e-8
         assert abs((F(x, y + h) - F(x, y - h)) / (2 * h)) < 1e-8
 

@@ -20,9 +20,10 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-# The two entry points run the same kernels on the same inputs; only the order of the FP64
-# atomic additions into bin sums and chi^2 terms can differ between runs.
-REL = 1e-10
+# The two entry points run the same kernels on the same inputs; only the order of the atomic
+# additions (FP32 bin accumulators in shared memory, FP64 bin sums and chi^2 terms) can differ
+# between runs, ~1e-7 relative in each chi^2 term.
+REL = 1e-6
 
 
 def _call_static(ctx, sid, th, B):
@@ -89,7 +90,7 @@ def test_static_scratch_rejects_batches_beyond_its_size():
     s = systems.small_system(7)
     ctx = GladContext([s])
     B = 200000
-    th = torch.zeros(1, 20, dtype=torch.float64, device="cuda")
+    th = torch.zeros(1, 23, dtype=torch.float64, device="cuda")
     sid = torch.zeros(1, dtype=torch.int32, device="cuda")
     P = lambda t: C.c_void_p(t.data_ptr())
     rc = ctx.lib.glad_loglike_static(ctx.handle, P(sid), P(th), B, P(th), P(sid), None, None)
