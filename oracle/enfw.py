@@ -18,9 +18,15 @@ CSE is -(1/s) d/ds of the softened isothermal ellipsoid's (oracle/chameleon.py, 
     psi = sqrt(q^2 (s^2 + x^2) + y^2),
 which at q = 1 is the round 2 R / (s psi (psi + s)).
 
+CSE potential and Jacobian: -(1/s) d/ds of the softened isothermal ellipsoid's.  For the
+dynamics the exact k(u) is expanded (Sect. 3.2) at complex u by nfw_k_complex, the CSE fit
+being controlled on the real axis only.
+
 Pins (tests/test_oracle_enfw.py): the fit against k(u); div alpha = 2 kappa and curl alpha = 0
 of a flattened CSE by differences; the round eNFW deflection against Gauss's theorem on the
-exact NFW convergence by quadrature.
+exact NFW convergence by quadrature; the CSE potential's gradient and the Jacobian against
+differences of the deflection; nfw_k_complex against nfw_k on the real axis and against its
+own Taylor branch where they meet; the eNFW MGE against the profile.
 """
 import functools
 
@@ -70,6 +76,40 @@ def cse_alpha(x, y, s, q):
     return ax, ay
 
 
+def cse_psi(x, y, s, q):
+    """Potential of the CSE (up to a constant): -(1/s) d/ds of the softened isothermal one
+    (oracle/chameleon.py, A = 1, b = 2q),
+    x alpha_x + y alpha_y + (b/s) L + b (psi + s)(q^2 s/psi + 1) / ((psi + s)^2 + (1 - q^2) x^2),
+    L = ln sqrt((psi + s)^2 + (1 - q^2) x^2)."""
+    b = 2.0 * q
+    e2 = 1.0 - q * q
+    psi = np.sqrt(q * q * (s * s + x * x) + y * y)
+    D = (psi + s) ** 2 + e2 * x * x
+    ax, ay = cse_alpha(x, y, s, q)
+    return x * ax + y * ay + b / s * 0.5 * np.log(D) + b * (psi + s) * (q * q * s / psi + 1.0) / D
+
+
+def cse_jac(x, y, s, q):
+    """d alpha / d (x, y) of the CSE: -(1/s) d/ds of the softened isothermal Jacobian
+    (A = 1, b = 2q; a11 = b N1/D, a12 = -b x y/(psi D), a22 = b N2/(q^2 D), D = (psi + s)^2 +
+    (1 - q^2) x^2, N1 = psi + s - q^2 x^2/psi, N2 = psi + q^2 s - y^2/psi) with d psi/ds =
+    q^2 s / psi."""
+    b = 2.0 * q
+    e2 = 1.0 - q * q
+    psi = np.sqrt(q * q * (s * s + x * x) + y * y)
+    ps = q * q * s / psi
+    D = (psi + s) ** 2 + e2 * x * x
+    Ds = 2.0 * (psi + s) * (ps + 1.0)
+    N1 = psi + s - q * q * x * x / psi
+    N1s = ps + 1.0 + q * q * x * x * ps / (psi * psi)
+    N2 = psi + q * q * s - y * y / psi
+    N2s = ps + q * q + y * y * ps / (psi * psi)
+    d11 = b * (N1s * D - N1 * Ds) / (D * D)
+    d12 = b * x * y * (ps * D + psi * Ds) / (psi * D) ** 2
+    d22 = b * (N2s * D - N2 * Ds) / (q * q * D * D)
+    return -d11 / s, -d12 / s, -d12 / s, -d22 / s
+
+
 def enfw_kappa(x, y, kappa_s, r_s, q):
     return kappa_s * nfw_k(np.sqrt(x * x + y * y / (q * q)) / r_s)
 
@@ -86,3 +126,37 @@ def enfw_alpha(x, y, kappa_s, r_s, q):
         ax = ax + kappa_s * ai * r_s ** 3 * bx
         ay = ay + kappa_s * ai * r_s ** 3 * by
     return ax, ay
+
+
+def _cse_sum(fn, x, y, kappa_s, r_s, q):
+    a, s = cse_decomposition()
+    out = None
+    for ai, si in zip(a, s):
+        if ai == 0.0:
+            continue
+        v = fn(x, y, si * r_s, q)
+        v = tuple(kappa_s * ai * r_s ** 3 * c for c in v) if isinstance(v, tuple) else kappa_s * ai * r_s ** 3 * v
+        out = v if out is None else (tuple(o + c for o, c in zip(out, v)) if isinstance(v, tuple) else out + v)
+    return out
+
+
+def enfw_psi(x, y, kappa_s, r_s, q):
+    return _cse_sum(cse_psi, x, y, kappa_s, r_s, q)
+
+
+def enfw_jac(x, y, kappa_s, r_s, q):
+    return _cse_sum(cse_jac, x, y, kappa_s, r_s, q)
+
+
+def nfw_k_complex(u):
+    """k(u) at complex u (Re u > 0) for the Euler inversion of the 1-D MGE: with w^2 = 1 - u^2,
+    k = 2 (1 - arctanh(w)/w) / (u^2 - 1), an even function of w (so either square root), and
+    k = 2 sum_n w^(2n) / (2n + 3) for |w| < 0.1 (the removable point u = 1)."""
+    u = np.asarray(u, np.complex128)
+    w2 = 1.0 - u * u
+    w = np.sqrt(w2)
+    small = np.abs(w) < 0.1
+    ws = np.where(small, 0.5, w)  # keeps the direct branch free of 0/0
+    direct = 2.0 * (1.0 - np.arctanh(ws) / ws) / (u * u - 1.0 + np.where(small, 1.0, 0.0))
+    series = sum(2.0 * w2 ** n / (2 * n + 3) for n in range(10))
+    return np.where(small, series, direct)

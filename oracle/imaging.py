@@ -16,7 +16,7 @@ brute-force 2-D convolution.
 """
 import numpy as np
 
-from . import lens, lensmodel, light
+from . import chameleon, lens, lensmodel, light
 
 
 def subpixel_grid(nx, ny, ss, pix):
@@ -40,6 +40,13 @@ def surface_brightness(x, y, th, sysd, alpha=None):
     src = light.sersic_xy(bx, by, th[IDX["I_e_src"]], th[IDX["R_e_src"]], th[IDX["n_src"]],
                           sysd["src_q"], th[IDX["x_src"]], th[IDX["y_src"]], sysd["src_phi"])
     xc, yc, phi = th[IDX["x_c"]], th[IDX["y_c"]], th[IDX["phi"]]
+    if lensmodel.is_composite(sysd):
+        # the composite class's lens light: Chameleon profiles (Eq. Chameleon) in the galaxy frame
+        xp, yp = lens.frame(x, y, xc, yc, phi)
+        ll = 0.0
+        for I0, wc, wt, q in lensmodel.chameleons(th, sysd):
+            ll = ll + chameleon.kappa(xp, yp, I0, wc, wt, q)
+        return src + ll
     ll = light.sersic_xy(x, y, th[IDX["I_e_ll"]], th[IDX["R_e_ll"]], sysd["ll_n"], sysd["ll_q"],
                          xc, yc, phi)
     for I_e, R_e, n, q in sysd["ll2"]:

@@ -42,10 +42,16 @@ def check_domain(th, sysd=None):
             if not (i == IDX["lam_int"] and int(sysd.get("sheet", 0)) == 0)
             and not (i == IDX["H0"] and mode1)
             and not (i in (IDX["D_d"], IDX["D_dt_int"]) and not mode1)]
-    ok = (np.all(np.isfinite(th[used])) and th[IDX["theta_E"]] > 0 and 1.0 < g < 3.0
-          and 0.0 < q <= 1.0
-          and th[IDX["R_e_src"]] > 0 and th[IDX["n_src"]] > 0 and th[IDX["R_e_ll"]] > 0
-          and th[IDX["I_e_ll"]] > 0
+    if lensmodel.is_composite(sysd):
+        # composite class: kappa_s >= 0, r_s > 0, q of the halo in (0, 1], first Chameleon
+        # I0 > 0 and w_t > w_c
+        mass_ok = (th[0] >= 0 and th[1] > 0 and 0.0 < q <= 1.0 and th[13] > 0
+                   and th[14] > float(sysd["ll_wc"]))
+    else:
+        mass_ok = (th[IDX["theta_E"]] > 0 and 1.0 < g < 3.0 and 0.0 < q <= 1.0
+                   and th[IDX["R_e_ll"]] > 0 and th[IDX["I_e_ll"]] > 0)
+    ok = (np.all(np.isfinite(th[used])) and mass_ok
+          and th[IDX["R_e_src"]] > 0 and th[IDX["n_src"]] > 0
           and 0.0 < inc <= math.pi / 2 + 1e-12 and th[IDX["beta"]] < 1.0
           and th[IDX["upsilon"]] >= 0 and th[IDX["f_bh"]] >= 0
           and (mode1 or th[IDX["H0"]] > 0)
@@ -55,7 +61,13 @@ def check_domain(th, sysd=None):
 
 
 def light_mge(th, sysd):
-    """Tracer MGE: one 1-D MGE per lens-light Sersic, all sharing centre and PA."""
+    """Tracer MGE: one 1-D MGE per lens-light Sersic (Chameleon in the composite class), all
+    sharing centre and PA."""
+    if lensmodel.is_composite(sysd):
+        parts = lensmodel.chameleon_mges(th, sysd)
+        return dict(I0=np.concatenate([A for A, _, _ in parts]),
+                    sig=np.concatenate([sg for _, sg, _ in parts]),
+                    qp=np.concatenate([np.full(len(sg), q) for _, sg, q in parts]))
     P = sysd["mge_P"]
     comps = [(th[IDX["I_e_ll"]], th[IDX["R_e_ll"]], sysd["ll_n"], sysd["ll_q"])]
     comps += [tuple(r) for r in np.asarray(sysd["ll2"]).reshape(-1, 4)]
@@ -69,11 +81,21 @@ def light_mge(th, sysd):
     return dict(I0=np.concatenate(I0), sig=np.concatenate(sig), qp=np.concatenate(qp))
 
 
-def mass_mge(th, sysd, L_tot):
-    s, A = mge.mge_1d(mge.epl_profile(th[IDX["theta_E"]], th[IDX["gamma"]], th[IDX["q"]],
-                                      sysd["r_soft"]),
-                      sysd["mass_rmin"], sysd["mass_rmax"], sysd["n_mge_mass"], sysd["mge_P"])
-    qp = np.full(len(s), th[IDX["q"]])
+def mass_mge(th, sysd, L_tot, tr=None):
+    """Mass Gaussians of the class (galaxy scaled by lambda_int, then the sheet's, the black hole
+    last).  EPL class: the 1-D MGE of the App. C convergence.  Composite class (Sect. 3.3):
+    Upsilon_* L_scale times the tracer Gaussians (the lens light), then the halo's."""
+    if lensmodel.is_composite(sysd):
+        ups = th[IDX["upsilon"]] * sysd["L_scale"]
+        Ah, sh_, qh = lensmodel.enfw_mass_mge(th, sysd)
+        A = np.concatenate([ups * tr["I0"], Ah])
+        s = np.concatenate([tr["sig"], sh_])
+        qp = np.concatenate([tr["qp"], qh])
+    else:
+        s, A = mge.mge_1d(mge.epl_profile(th[IDX["theta_E"]], th[IDX["gamma"]], th[IDX["q"]],
+                                          sysd["r_soft"]),
+                          sysd["mass_rmin"], sysd["mass_rmax"], sysd["n_mge_mass"], sysd["mge_P"])
+        qp = np.full(len(s), th[IDX["q"]])
     # the internal mass sheet (Sect. 3.3, Eq. kappa int): the galaxy (with its black hole)
     # scaled by lambda_int, the sheet's own round Gaussians after it, the black hole last
     lam = lensmodel.lam_of(th, sysd)
@@ -116,7 +138,7 @@ def dynamics_setup(th, sysd):
     inc = th[IDX["inc"]]
     tr = light_mge(th, sysd)
     L_tot = float(np.sum(2 * math.pi * tr["I0"] * tr["sig"] ** 2 * tr["qp"]))
-    ms = mass_mge(th, sysd, L_tot)
+    ms = mass_mge(th, sysd, L_tot, tr)
     qmin = min(np.min(tr["qp"]), np.min(ms["qp"]))
     if math.cos(inc) ** 2 >= qmin ** 2:
         return ST_DEPROJ, None
@@ -258,8 +280,9 @@ def build_system(base, theta_true, noise):
     s["v_obs"] = np.ones(s["n_bins"], np.float32)
     s["v_sig"] = np.ones(s["n_bins"], np.float32)
     # quasar images: Newton solution of the lens equation for the quasar source point
-    guesses = synth.ring_images(theta_true[IDX["theta_E"]], s["qso_beta"])
-    img = lens.solve_images(s["qso_beta"], theta_true, s["sis"], guesses)
+    guesses = synth.ring_images(1.65 if lensmodel.is_composite(s) else theta_true[IDX["theta_E"]],
+                                s["qso_beta"])
+    img = lensmodel.solve_images(s["qso_beta"], theta_true, s, guesses)
     s["img_xy"] = img
     s["dt_obs"] = np.zeros(len(img) - 1)
     s["dt_sig"] = np.ones(len(img) - 1)
@@ -282,7 +305,7 @@ def workload(w, small=False):
     bases, B = synth.workload_systems(w)
     systems = []
     for si, b in enumerate(bases):
-        truth = synth.theta_truth(0 if w == 0 else 1)
+        truth = synth.theta_truth_composite() if lensmodel.is_composite(b) else synth.theta_truth(0 if w == 0 else 1)
         systems.append(build_system(b, truth, synth.noise_draws(b, 1000 * w + si + 500)))
     th, sid = synth.workload_thetas(w, B, len(systems))
     return systems, th, sid

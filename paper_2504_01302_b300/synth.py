@@ -210,6 +210,42 @@ def draw_prior(rng, B: int) -> np.ndarray:
     return th
 
 
+# The composite mass class (Sect. 3.3) gives entries 0, 1, 2, 13, 14 other meanings: the
+# halo's kappa_s, r_s [arcsec], q (Eq. kappa_enfw; Table 2's rho_s, r_s, q_enfw) and the first
+# Chameleon's I0 and w_t [arcsec] (Eq. Chameleon).  Mock truth and prior ranges: kappa_s 0.09
+# (with the baryons, a mean convergence near 1 inside 1.65"), r_s 23 (Table 2), q 0.56 (Table
+# 2), I0 0.6 and w_t 1.5" (w_c 0.05", q 0.85; a second Chameleon 0.3, 0.3", 3", 0.9 fixed).
+COMPOSITE_TRUTH = {0: 0.09, 1: 23.0, 2: 0.56, 13: 0.6, 14: 1.5}
+COMPOSITE_PRIOR = {0: (0.07, 0.11), 1: (20.4, 25.6), 2: (0.46, 0.66), 13: (0.54, 0.66),
+                   14: (1.35, 1.65)}
+
+
+def theta_truth_composite() -> np.ndarray:
+    t = theta_truth(1)
+    for i, v in COMPOSITE_TRUTH.items():
+        t[i] = v
+    return t
+
+
+def draw_prior_composite(rng, B: int, lam_hi: float = 1.0) -> np.ndarray:
+    """B parameter vectors for the composite class with the sheet in distance mode 1 (the
+    entries of draw_prior_sheet, the class's own entries redrawn from COMPOSITE_PRIOR)."""
+    th = draw_prior_sheet(rng, B, lam_hi=lam_hi)
+    u = rng.random((B, len(COMPOSITE_PRIOR)))
+    for n, (i, (lo, hi)) in enumerate(sorted(COMPOSITE_PRIOR.items())):
+        th[:, i] = lo + u[:, n] * (hi - lo)
+    return th
+
+
+def composite_light(system: dict) -> dict:
+    """Turn a base system into the composite class: Chameleon lens light (first component
+    w_c 0.05", q 0.85; a second fixed Chameleon), the halo expanded on the mass range."""
+    s = dict(system)
+    s.update(mass_class=1, ll_wc=0.05, ll_q=0.85,
+             ll2=np.array([[0.3, 0.3, 3.0, 0.9]], np.float64)[:len(np.asarray(system["ll2"]).reshape(-1, 4))])
+    return s
+
+
 def draw_prior_sheet(rng, B: int, lam_hi: float = 1.5) -> np.ndarray:
     """B parameter vectors for systems with the internal mass sheet in distance mode 1: every
     entry drawn, lambda_int in [0.5, lam_hi] (Table 2: [0.5, 1.5]), D_d in [600, 1000] and
@@ -238,14 +274,17 @@ def workload_systems(w: int, small: bool = False):
     7: workload 1's system as the EPL mass class with the internal mass sheet (the dPIE of
        Eq. dpie_kappa, 40 Gaussians on [0.1, 1000]") and sampled distances D_d, D_dt,int
        (distance mode 1, Table 2), B=256
+    8: workload 1's system as the composite mass class (two Chameleons scaled by Upsilon_*,
+       the elliptical NFW halo, the black hole) with the dPIE sheet in distance mode 1: the
+       paper's own joint model (Sect. 3.3), B=256
     """
-    rng = np.random.Generator(np.random.PCG64(1000 + {5: 1, 6: 4, 7: 1}.get(w, w)))
+    rng = np.random.Generator(np.random.PCG64(1000 + {5: 1, 6: 4, 7: 1, 8: 1}.get(w, w)))
     if w == 0:
         s = base_system("w0", n_img_px=64, ss=1, psf_k=11, sky=32, kss=1, n_mass=10,
                         n_light=10, n_gl=32, n_bins=20, bins="annular", rng=rng,
                         has_bh=False, n_sis=0, second_light=False)
         return [s], 1
-    if w in (1, 2, 5, 7):
+    if w in (1, 2, 5, 7, 8):
         s = base_system("w1", n_img_px=200, ss=2, psf_k=21, sky=60, kss=4, n_mass=20,
                         n_light=10, n_gl=32, n_bins=50, bins="voronoi", rng=rng,
                         has_bh=True, n_sis=1, second_light=True)
@@ -253,6 +292,9 @@ def workload_systems(w: int, small: bool = False):
             s.update(name="w5", jam_align=1, sph_nr=128, sph_nw=8, sph_nlos=32)
         if w == 7:
             s.update(name="w7", sheet=1, distance_mode=1)
+        if w == 8:
+            s = composite_light(s)
+            s.update(name="w8", sheet=1, distance_mode=1)
         return [s], (64 if w == 2 else 256)
     if w == 3:
         systems = []
@@ -290,7 +332,12 @@ def workload_thetas(w: int, B: int, n_sys: int):
         return theta_truth(0)[None, :].copy(), np.zeros(1, np.int32)
     # the sheet workload draws lambda_int in [0.5, 1]: above 1 the EPL class's outer density
     # turns negative and the Jeans model rejects the sample (Sect. 3.3)
-    th = draw_prior_sheet(rng, B, lam_hi=1.0) if w == 7 else draw_prior(rng, B)
+    if w == 7:
+        th = draw_prior_sheet(rng, B, lam_hi=1.0)
+    elif w == 8:
+        th = draw_prior_composite(rng, B)
+    else:
+        th = draw_prior(rng, B)
     if n_sys == 1:
         sid = np.zeros(B, np.int32)
     else:

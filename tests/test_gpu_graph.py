@@ -74,7 +74,10 @@ def test_graph_replay_matches_eager_and_oracle(uneven):
         assert int((st_ref == 0).sum()) > B // 4
         _near(l_ref, logL.cpu().numpy(), SAME)
         ok = st_ref == 0
-        _near(terms_ref[ok].ravel(), terms.cpu().numpy()[ok].ravel(), SAME)
+        # each chi^2 term within SAME of the sample's total chi^2
+        tr, tg = terms_ref[ok], terms.cpu().numpy()[ok]
+        tot = np.sum(np.abs(tr), axis=1, keepdims=True)
+        assert np.all(np.abs(tr - tg) <= SAME * tot + 1e-9)
     # sampled samples of the replayed batch (theta b) against the oracle: the first valid
     # sample of each of the two cheapest systems (fewest sky sub-samples x table entries)
     cost = [(s["kx"] * s["kss"]) * (s["ky"] * s["kss"]) * sum(s["n_mge_light"]) *

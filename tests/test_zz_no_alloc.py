@@ -43,6 +43,13 @@ def _near(a, b):
     assert np.all(np.abs(a[fin] - b[fin]) <= REL * np.abs(a[fin]) + 1e-9), (a, b)
 
 
+def _near_terms(a, b):
+    """chi^2 terms of each sample, each within REL of the sample's total chi^2 (a small term
+    amplifies the rounding of the residuals it squares; logL is what the bound is about)."""
+    tot = np.sum(np.abs(a), axis=1, keepdims=True)
+    assert np.all(np.abs(a - b) <= REL * tot + 1e-9), np.max(np.abs(a - b) / (tot + 1e-300))
+
+
 def _sph_system(seed=7):
     b = dict(systems.small_base(seed), jam_align=1, sph_nr=40, sph_nw=6, sph_nlos=48)
     return model.build_system(b, synth.theta_truth(1), synth.noise_draws(b, 9100 + seed))
@@ -63,7 +70,7 @@ def _compare_twice(ctx, n_sys, B, seeds):
         assert int((st_a == 0).sum()) >= B // 2
         _near(logL_a.cpu().numpy(), logL_s.cpu().numpy())
         ok = (st_a == 0).cpu().numpy()
-        _near(terms_a.cpu().numpy()[ok], terms_s.cpu().numpy()[ok])
+        _near_terms(terms_a.cpu().numpy()[ok], terms_s.cpu().numpy()[ok])
 
 
 def test_static_scratch_matches_allocating_entry_point_twice():
