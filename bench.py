@@ -108,7 +108,11 @@ def workload_name(w, grad, B):
                 "128^2 sky x4, GL64, 400 bins",
              7: "RXJ1131-scale EPL class with the internal mass sheet (dPIE, 40 Gaussians) and "
                 "sampled D_d, D_dt,int: 200^2 x2ss, 21^2 PSF, EPL+shear+SIS, JAM 20+40+2x10+BH, "
-                "60^2 sky x4ss, GL32, 50 bins"}
+                "60^2 sky x4ss, GL32, 50 bins",
+             8: "RXJ1131-scale composite class (2 Chameleons x Upsilon, eNFW halo as 44 CSEs, BH) "
+                "with the dPIE sheet and sampled D_d, D_dt,int (the paper's joint model): 200^2 "
+                "x2ss, 21^2 PSF, +shear+SIS, JAM 2x10 tracer x (20 baryon + 20 halo + 40 sheet + BH) "
+                "mass, 60^2 sky x4ss, GL32, 50 bins"}
     n = names.get(w, str(w)) + f"; B={B}"
     if grad:
         n += " (forward + gradient)"
@@ -158,8 +162,9 @@ def bench_systems(w):
     out = []
     for b in bases:
         s = dict(b)
-        truth = synth.theta_truth(0 if w == 0 else 1)
-        s["img_xy"] = synth.ring_images(truth[0], s["qso_beta"])
+        # quasar images on a ring of the Einstein radius (theta[0] of the composite class is the
+        # halo's kappa_s, not an Einstein radius)
+        s["img_xy"] = synth.ring_images(1.5 if w == 0 else 1.65, s["qso_beta"])
         s["data"] = np.zeros((s["ny"], s["nx"]), np.float32)
         s["v_obs"] = np.ones(s["n_bins"], np.float32)
         s["v_sig"] = np.ones(s["n_bins"], np.float32)
@@ -169,9 +174,15 @@ def bench_systems(w):
     return out, B
 
 
+def bench_truth(w, systems):
+    if int(systems[0].get("mass_class", 0)) == 1:
+        return synth.theta_truth_composite()
+    return synth.theta_truth(0 if w == 0 else 1)
+
+
 def fill_data_with_gpu_model(systems, w, torch, GladContext):
     ctx = GladContext(systems)
-    truth = torch.as_tensor(synth.theta_truth(0 if w == 0 else 1), device="cuda")
+    truth = torch.as_tensor(bench_truth(w, systems), device="cuda")
     for i, s in enumerate(systems):
         nz = synth.noise_draws(s, 1000 * w + i + 500)
         img = ctx.model_image(truth, i).cpu().numpy().astype(np.float64)
@@ -267,7 +278,7 @@ def run_reference(args):
     w = args.workload
     systems, B = bench_systems(w)
     for i, s in enumerate(systems):
-        truth = synth.theta_truth(0 if w == 0 else 1)
+        truth = bench_truth(w, systems)
         s.update(model.build_system(s, truth, synth.noise_draws(s, 1000 * w + i + 500)))
     B = args.batch or (64 if args.grad else B)
     th, sid = synth.workload_thetas(w, B, len(systems))

@@ -24,6 +24,9 @@
  * An entry a system does not use is ignored (it may hold anything, NaN included) and its
  * gradient is 0: lambda_int without a sheet; H0 in distance mode 1; D_d and D_dt,int in
  * distance mode 0.
+ * In the composite mass class (mass_class 1) five entries take that class's parameters:
+ *   0 kappa_s (halo convergence scale, >= 0)  1 r_s (halo scale radius, arcsec)  2 q of the halo
+ *   13 I0 and 14 w_t (arcsec) of the first Chameleon of the lens light; 17 is Upsilon_*.
  */
 #ifndef GLAD_H
 #define GLAD_H
@@ -79,6 +82,19 @@ enum {
  * Image positions (Eq. chi2_img): with img_sig[n_img] (arcsec) given, chi^2_img of the
  * observed images against beta_hat mapped back to the image plane (Newton iterations on
  * the lens equation from each observed image) joins the likelihood; NULL leaves it out.
+ *
+ * Mass class (Sect. 3.3): mass_class 0 is the EPL class above (theta_E, gamma', q; Sersic lens
+ * light).  mass_class 1 is the composite class kappa = Upsilon_* L_scale I_light + kappa_enfw +
+ * kappa_BH: the lens light is Chameleon profiles (Eq. Chameleon) I0/(1+q) [(m^2 + 4 w_c^2/(1+q)^2)^(-1/2)
+ * - (m^2 + 4 w_t^2/(1+q)^2)^(-1/2)], m^2 = x'^2 + y'^2/q^2 in the galaxy frame (the first with
+ * I0 = theta[13], w_t = theta[14], w_c = ll_wc and q = ll_q; ll2 rows are further Chameleons
+ * (I0, w_c, w_t, q)); the baryons are Upsilon_* L_scale times that light; the halo is the
+ * elliptical NFW kappa_s k(m_h / r_s), m_h^2 = x'^2 + y'^2/q_h^2 (Eq. kappa_enfw), deflected as 44
+ * cored steep ellipsoids (App. B, glad_enfw_cse) and expanded for the dynamics by the 1-D MGE of
+ * the exact profile (n_mge_mass Gaussians on [mass_rmin, mass_rmax]); the black hole (mass
+ * f_BH Upsilon_* L_tot L_scale) is the round Gaussian of dispersion bh_sigma in the lensing as in
+ * the dynamics.  The mass Gaussians are then Upsilon_* L_scale times the tracer Gaussians, the
+ * halo's, the sheet's and the black hole.  External shear and SIS perturbers as in class 0.
  *
  * Internal mass sheet (Sect. 3.3, Eqs. kappa int and dpie_kappa): with sheet != 0 the mass
  * class becomes kappa_int = (1 - lambda_int) + lambda_int kappa_gal: every deflection of the
@@ -148,6 +164,8 @@ typedef struct glad_system_desc {
   int sheet_n;                     /* Gaussians of the sheet's MGE (0: 40) */
   double sheet_rmin, sheet_rmax;   /* their sigma range [arcsec] (0: 0.1, 1000) */
   int distance_mode;               /* 0: H0 = theta[19]; 1: D_d = theta[21], D_dt,int = theta[22] */
+  int mass_class;                  /* 0 EPL, 1 composite (see above) */
+  double ll_wc;                    /* composite class: w_c of the first Chameleon [arcsec] */
 } glad_system_desc;
 
 typedef struct glad_ctx glad_ctx;
@@ -265,6 +283,15 @@ glad_status glad_set_negligible(glad_ctx *ctx, int mode);
  * (entry, sky point) pairs.  Synchronises the device. */
 glad_status glad_jam_evaluations(glad_ctx *ctx, unsigned long long *count,
                                  unsigned long long *count_adjoint);
+
+/* The composite class's halo decomposition (App. B: the elliptical NFW convergence
+ * kappa_s k(xi / r_s) as 44 cored steep ellipsoids, kappa_s sum_i a_i r_s^3 (xi^2 + (s_i r_s)^2)^(-3/2)).
+ * The paper takes it from the literature without printing it; the library fits it once per
+ * process (cores log-spaced on [1e-5, 1e4] r_s, amplitudes >= 0 by non-negative least squares
+ * of the relative error on xi / r_s in [1e-4, 1e3]).  Writes a[i], s[i] (i < 44, [host]) and,
+ * if max_rel_err is not NULL, the fit's largest relative error on that range; returns 44
+ * (and writes nothing when n < 44).  Needs no GPU. */
+int glad_enfw_cse(int n, double *a, double *s, double *max_rel_err);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *glad_last_error(void);

@@ -35,7 +35,7 @@ class SystemDesc(C.Structure):
         ("jam_align", C.c_int), ("sph_nr", C.c_int), ("sph_nw", C.c_int), ("sph_nlos", C.c_int),
         ("sheet", C.c_int), ("sheet_rc", C.c_double), ("sheet_rt", C.c_double),
         ("sheet_n", C.c_int), ("sheet_rmin", C.c_double), ("sheet_rmax", C.c_double),
-        ("distance_mode", C.c_int),
+        ("distance_mode", C.c_int), ("mass_class", C.c_int), ("ll_wc", C.c_double),
     ]
 
 
@@ -56,6 +56,7 @@ SIGNATURES = {
     "glad_set_tuning": (C.c_int, [_p, C.c_int, C.c_int]),
     "glad_set_negligible": (C.c_int, [_p, C.c_int]),
     "glad_jam_evaluations": (C.c_int, [_p, C.POINTER(C.c_ulonglong), C.POINTER(C.c_ulonglong)]),
+    "glad_enfw_cse": (C.c_int, [C.c_int, _d, _d, _d]),
     "glad_last_error": (C.c_char_p, []),
 }
 

@@ -120,6 +120,14 @@ __device__ inline Dual<N, double> dlog1p(const Dual<N, double> &a) {
   return dual_apply(a, log1p(a.v), 1.0 / (1.0 + a.v));
 }
 template <int N>
+__device__ inline Dual<N, double> datan(const Dual<N, double> &a) {
+  return dual_apply(a, atan(a.v), 1.0 / (1.0 + a.v * a.v));
+}
+template <int N>
+__device__ inline Dual<N, double> datanh(const Dual<N, double> &a) {
+  return dual_apply(a, atanh(a.v), 1.0 / (1.0 - a.v * a.v));
+}
+template <int N>
 __device__ inline Dual<N, double> dpow(const Dual<N, double> &a, const Dual<N, double> &b) {
   return dexp(b * dlog(a));
 }
@@ -141,6 +149,14 @@ __device__ inline Dual<N, float> dsqrt(const Dual<N, float> &a) {
   return dual_apply(a, s, 0.5f / s);
 }
 template <int N>
+__device__ inline Dual<N, float> datan(const Dual<N, float> &a) {
+  return dual_apply(a, atanf(a.v), 1.0f / (1.0f + a.v * a.v));
+}
+template <int N>
+__device__ inline Dual<N, float> datanh(const Dual<N, float> &a) {
+  return dual_apply(a, atanhf(a.v), 1.0f / (1.0f - a.v * a.v));
+}
+template <int N>
 __device__ inline Dual<N, float> dexp2(const Dual<N, float> &a) {
   const float e = exp2f(a.v);
   return dual_apply(a, e, e * 0.6931471805599453f);
@@ -155,6 +171,8 @@ __device__ inline double dsqrt(double a) { return sqrt(a); }
 __device__ inline double dexp(double a) { return exp(a); }
 __device__ inline double dlog(double a) { return log(a); }
 __device__ inline double dlog1p(double a) { return log1p(a); }
+__device__ inline double datan(double a) { return atan(a); }
+__device__ inline double datanh(double a) { return atanh(a); }
 __device__ inline double dpow(double a, double b) { return pow(a, b); }
 __device__ inline double dsin(double a) { return sin(a); }
 __device__ inline double dcos(double a) { return cos(a); }

@@ -144,6 +144,14 @@ glad_status validate(const glad_system_desc &d, int idx) {
   REQ(d.sph_nlos >= 0, "sph_nlos must be >= 0", idx);
   REQ(d.sheet >= 0 && d.sheet <= 2, "sheet must be 0, 1 or 2", idx);
   REQ(d.distance_mode == 0 || d.distance_mode == 1, "distance_mode must be 0 or 1", idx);
+  REQ(d.mass_class == 0 || d.mass_class == 1, "mass_class must be 0 or 1", idx);
+  if (d.mass_class == 1) {
+    REQ(d.ll_wc > 0 && d.ll_q > 0 && d.ll_q <= 1, "composite class needs ll_wc > 0, 0 < ll_q <= 1", idx);
+    for (int k = 0; k < d.n_ll2; ++k)
+      REQ(d.ll2[4 * k] > 0 && d.ll2[4 * k + 1] > 0 && d.ll2[4 * k + 2] > d.ll2[4 * k + 1] &&
+              d.ll2[4 * k + 3] > 0 && d.ll2[4 * k + 3] <= 1,
+          "Chameleon rows need I0 > 0, 0 < w_c < w_t, 0 < q <= 1", idx);
+  }
   if (d.sheet) {
     const double rc = d.sheet_rc > 0 ? d.sheet_rc : 45.0, rt = d.sheet_rt > 0 ? d.sheet_rt : 45.09;
     REQ(d.sheet_rc >= 0 && d.sheet_rt >= 0 && rt > rc, "sheet radii need 0 < rc < rt", idx);
@@ -157,7 +165,11 @@ glad_status validate(const glad_system_desc &d, int idx) {
   SUP(d.psf_k <= GLAD_MAX_PSF, "psf_k > %d", idx, GLAD_MAX_PSF);
   SUP(d.n_bins <= GLAD_MAX_BINS, "n_bins > %d", idx, GLAD_MAX_BINS);
   const int n_sheet = d.sheet ? (d.sheet_n ? d.sheet_n : 40) : 0;
-  SUP(d.n_mge_mass + n_sheet <= GLAD_MAX_MASS, "n_mge_mass + sheet Gaussians > %d", idx, GLAD_MAX_MASS);
+  int nl_all = 0;
+  for (int c = 0; c < 1 + d.n_ll2 && d.n_mge_light; ++c) nl_all += d.n_mge_light[c];
+  // galaxy mass Gaussians: the EPL's, or (composite) the tracer's copies and the halo's
+  const int n_gal = d.n_mge_mass + (d.mass_class == 1 ? nl_all : 0);
+  SUP(n_gal + n_sheet <= GLAD_MAX_MASS, "n_mge_mass + sheet Gaussians > %d", idx, GLAD_MAX_MASS);
   SUP(d.mge_P <= GLAD_MAX_P, "mge_P > %d", idx, GLAD_MAX_P);
   SUP(d.n_img <= GLAD_MAX_IMG, "n_img > %d", idx, GLAD_MAX_IMG);
   SUP(1 + d.n_ll2 <= 4, "more than 4 lens-light components", idx);
@@ -172,12 +184,12 @@ glad_status validate(const glad_system_desc &d, int idx) {
   if (d.jam_align == 1) {
     const int nr = d.sph_nr ? d.sph_nr : SPH_DEFAULT_NR, nw = d.sph_nw ? d.sph_nw : SPH_DEFAULT_NW;
     SUP(nr * nw <= GLAD_SPH_MAX_GRID, "sph_nr * sph_nw > %d", idx, GLAD_SPH_MAX_GRID);
-    SUP((d.n_mge_mass + n_sheet + (d.has_bh ? 1 : 0)) * d.n_gl <= GLAD_SPH_MAX_MG,
+    SUP((n_gal + n_sheet + (d.has_bh ? 1 : 0)) * d.n_gl <= GLAD_SPH_MAX_MG,
         "mass Gaussians x n_gl > %d for the spherically aligned model", idx, GLAD_SPH_MAX_MG);
     SUP(d.sph_nlos <= 4096, "sph_nlos > 4096", idx);
     // shared memory of the gradient kernels (grid adjoint: coefficients and their accumulators;
     // line-of-sight adjoint: grid, grid adjoint and per-thread tracer accumulators)
-    const size_t mg = (size_t)(d.n_mge_mass + n_sheet + (d.has_bh ? 1 : 0)) * d.n_gl;
+    const size_t mg = (size_t)(n_gal + n_sheet + (d.has_bh ? 1 : 0)) * d.n_gl;
     const size_t ladj = (size_t)nr * (nw - 1) * 16 + (size_t)nr * (nw | 1) * 8 + (size_t)nl * (16 + 128 * 8);
     const size_t gadj = mg * 40 + 8 * 64 * 16 + (size_t)nl * 24 + 16;
     SUP(ladj <= 226 * 1024 && gadj <= 226 * 1024,
@@ -217,10 +229,12 @@ glad_status build_system(int idx, const glad_system_desc &d, SysHost &sh, SysDev
   sd.src_cphi = (float)cos(d.src_phi);
   sd.src_sphi = (float)sin(d.src_phi);
   sd.n_lcomp = 1 + d.n_ll2;
+  // lens-light rows: Sersic (I_e, R_e, n, q) or, in the composite class, Chameleon
+  // (I0, w_c, w_t, q); row 0's I_e, R_e (or I0, w_t) come from theta
   std::vector<double> lcomp(4 * sd.n_lcomp);
   lcomp[0] = 0.0;
-  lcomp[1] = 0.0;
-  lcomp[2] = d.ll_n;
+  lcomp[1] = d.mass_class == 1 ? d.ll_wc : 0.0;
+  lcomp[2] = d.mass_class == 1 ? 0.0 : d.ll_n;
   lcomp[3] = d.ll_q;
   for (int k = 0; k < d.n_ll2; ++k)
     for (int m = 0; m < 4; ++m) lcomp[4 * (k + 1) + m] = d.ll2[4 * k + m];
@@ -278,18 +292,45 @@ glad_status build_system(int idx, const glad_system_desc &d, SysHost &sh, SysDev
   sd.n_bins = d.n_bins;
   sd.v_obs = upload(sh, d.v_obs, d.n_bins);
   sd.v_sig = upload(sh, d.v_sig, d.n_bins);
+  std::vector<double> sig_l, mw_l, qp_l;
+  std::vector<int> comp_of;
+  for (int cc = 0; cc < 1 + d.n_ll2; ++cc) {
+    const int N = d.n_mge_light[cc];
+    const double lo = log(d.light_rmin), hi = log(d.light_rmax), dl = (hi - lo) / (N - 1);
+    const double q = cc == 0 ? d.ll_q : d.ll2[4 * (cc - 1) + 3];
+    for (int k = 0; k < N; ++k) {
+      sig_l.push_back(exp(lo + dl * k));
+      mw_l.push_back((k == 0 || k == N - 1 ? 0.5 : 1.0) * dl / SQRT2PI_D);
+      qp_l.push_back(q);
+      comp_of.push_back(cc);
+    }
+  }
+  const int nL = (int)sig_l.size();
   // MGE Gaussians: mass [galaxy nM][internal sheet nS][black hole]
-  const int nM = d.n_mge_mass;
+  // (composite class: the galaxy's Gaussians are the nL tracer Gaussians, scaled per sample by
+  // Upsilon L_scale, and then the halo's n_mge_mass on the mass range)
+  const int nH = d.n_mge_mass;
+  const int off = d.mass_class == 1 ? nL : 0;
+  const int nM = off + nH;
   const int nS = d.sheet ? (d.sheet_n ? d.sheet_n : 40) : 0;
   const int nMt = nM + nS + (d.has_bh ? 1 : 0);
-  std::vector<double> sig_m(nMt), mw_m(nM), sheet_a1(std::max(nS, 1), 0.0);
+  std::vector<double> sig_m(nMt), mw_m(nM, 0.0), sheet_a1(std::max(nS, 1), 0.0);
   {
-    const double lo = log(d.mass_rmin), hi = log(d.mass_rmax), dl = (hi - lo) / (nM - 1);
-    for (int j = 0; j < nM; ++j) {
-      sig_m[j] = exp(lo + dl * j);
-      mw_m[j] = (j == 0 || j == nM - 1 ? 0.5 : 1.0) * dl / SQRT2PI_D;
+    for (int j = 0; j < off; ++j) sig_m[j] = sig_l[j];
+    const double lo = log(d.mass_rmin), hi = log(d.mass_rmax), dl = (hi - lo) / (nH - 1);
+    for (int j = 0; j < nH; ++j) {
+      sig_m[off + j] = exp(lo + dl * j);
+      mw_m[off + j] = (j == 0 || j == nH - 1 ? 0.5 : 1.0) * dl / SQRT2PI_D;
     }
     if (d.has_bh) sig_m[nM + nS] = d.bh_sigma;
+  }
+  sd.mass_class = d.mass_class;
+  sd.n_halo = d.mass_class == 1 ? nH : 0;
+  {
+    const double *ca = nullptr, *cs = nullptr;
+    if (d.mass_class == 1) cse_table(&ca, &cs);
+    sd.cse_a = upload(sh, ca, GLAD_N_CSE);
+    sd.cse_s = upload(sh, cs, GLAD_N_CSE);
   }
   sd.sheet = d.sheet;
   sd.sh_rc = d.sheet_rc > 0 ? d.sheet_rc : 45.0;
@@ -321,20 +362,6 @@ glad_status build_system(int idx, const glad_system_desc &d, SysHost &sh, SysDev
   }
   sd.n_sheet = nS;
   sd.sheet_A1 = upload(sh, sheet_a1.data(), sheet_a1.size());
-  std::vector<double> sig_l, mw_l, qp_l;
-  std::vector<int> comp_of;
-  for (int cc = 0; cc < 1 + d.n_ll2; ++cc) {
-    const int N = d.n_mge_light[cc];
-    const double lo = log(d.light_rmin), hi = log(d.light_rmax), dl = (hi - lo) / (N - 1);
-    const double q = cc == 0 ? d.ll_q : d.ll2[4 * (cc - 1) + 3];
-    for (int k = 0; k < N; ++k) {
-      sig_l.push_back(exp(lo + dl * k));
-      mw_l.push_back((k == 0 || k == N - 1 ? 0.5 : 1.0) * dl / SQRT2PI_D);
-      qp_l.push_back(q);
-      comp_of.push_back(cc);
-    }
-  }
-  const int nL = (int)sig_l.size();
   sd.n_mass = nM;
   sd.n_mass_tot = nMt;
   sd.n_light = nL;

@@ -18,6 +18,7 @@
 #define GLAD_MAX_IMG 8        // quasar images
 #define GLAD_SPH_MAX_GRID 4096  // polar grid points of the spherically aligned model
 #define GLAD_SPH_MAX_MG 4096    // (mass Gaussian, u node) pairs of the spherically aligned model
+#define GLAD_N_CSE 44           // cored steep ellipsoids of the composite class's halo
 #define SPH_DEFAULT_NR 128      // default polar grid and line-of-sight rule of that model
 #define SPH_DEFAULT_NW 8
 #define SPH_DEFAULT_NLOS 32
@@ -50,7 +51,12 @@ struct SysDev {
   const float *w_val;    // [nnz]
   int n_bins;
   const float *v_obs, *v_sig;
-  // MGE: mass Gaussians are ordered [galaxy n_mass][sheet n_sheet][black hole]
+  // mass class: 0 EPL, 1 composite (Chameleon baryons x Upsilon, elliptical NFW halo, black hole)
+  int mass_class;
+  int n_halo;                              // composite: halo Gaussians (after the nL light copies)
+  const double *cse_a, *cse_s;             // composite: the halo's CSEs, units of r_s [GLAD_N_CSE]
+  // MGE: mass Gaussians are ordered [galaxy n_mass][sheet n_sheet][black hole]; the composite
+  // class's galaxy part is [Upsilon x the n_light tracer Gaussians][halo n_halo]
   int n_mass, n_mass_tot, n_light;
   int n_sheet;                             // round Gaussians of the internal sheet (0: none)
   const double *sheet_A1;                  // [n_sheet] their amplitudes at 1 - lambda_int = 1
@@ -114,6 +120,19 @@ struct LensP {
   float lam;
   int sheet;
   float sh_rc2, sh_rt2, sh_rc, sh_rt;
+  // composite class (mclass 1): Chameleon c of the lens light is li_A[c] [(m^2 + sc^2)^-1/2 -
+  // (m^2 + st^2)^-1/2], m^2 = x'^2 + y'^2/q^2, li_A = I0/(1+q), s = 2w/(1+q); its baryonic
+  // deflection is that of two softened isothermal ellipsoids of amplitude ch_A = Upsilon L_scale
+  // li_A (b = 2 q ch_A), e = sqrt(1 - q^2); the halo's CSE i has amplitude cse_amp = kappa_s a_i
+  // r_s^3 and core cse_sc = s_i r_s (axis ratio h_q); the black hole is a round Gaussian of mass
+  // bh_M (convergence x arcsec^2) and 2 sigma^2 = bh_2s2
+  // (for the gradient: ups = Upsilon L_scale, h_ks = kappa_s, h_rs = r_s, cse_a3 = a_i r_s^3,
+  // bh_dM = d bh_M / d(theta 13, 14, 17, 18))
+  int mclass;
+  float li_A[4], ch_A[4], ch_sc[4], ch_st[4], ch_q[4], ch_e[4];
+  float ups, h_ks, h_rs, h_q, h_e2;
+  float bh_M, bh_2s2, bh_dM[4];
+  float cse_amp[GLAD_N_CSE], cse_sc[GLAD_N_CSE], cse_a3[GLAD_N_CSE];
 };
 
 // per-sample dynamics scalars (FP64)
@@ -245,6 +264,8 @@ cudaError_t set_sph_smem_limit();
 // its adjoint (k_sph_grad.cu): line-of-sight and grid adjoints, carried to the JAM inputs
 cudaError_t launch_grad_sph(glad_ctx *c, const int *sys_id, int B, double *grad, cudaStream_t st);
 cudaError_t set_sph_grad_smem_limit();
+// the halo's CSE decomposition (glad_cse.cu): amplitudes and cores in units of r_s, fitted once
+void cse_table(const double **a, const double **s);
 // the dynamics sum of either model for the systems of the context (glad_host.cu): the
 // table/grid stage and the sky-point stage, each recorded under its kernel id
 cudaError_t launch_dyn_tables(glad_ctx *c, const int *sys_id, int B, cudaStream_t st);

@@ -17,6 +17,7 @@
 // The MGE and table quantities are recomputed here, never stored from the forward pass.
 #include <algorithm>
 
+#include "cplx.cuh"
 #include "dual.cuh"
 #include "glad_internal.cuh"
 #include "grad_ws.cuh"
@@ -103,6 +104,7 @@ __global__ void __launch_bounds__(LENS_THREADS) k_image_grad(const SysDev *__res
   const int b = blockIdx.y;
   if (ws.status[b] != GLAD_SAMPLE_OK) return;
   const SysDev &S = sysv[sys_id[b]];
+  if (S.mass_class != 0) return;  // composite samples: k_image_grad_comp
   const int p = blockIdx.x * LENS_THREADS + threadIdx.x;
   __shared__ LensP L;
   __shared__ float red[LENS_THREADS / 32][NGL];
@@ -245,6 +247,208 @@ __global__ void __launch_bounds__(LENS_THREADS) k_image_grad(const SysDev *__res
     double s = 0.0;
     for (int w = 0; w < LENS_THREADS / 32; ++w) s += (double)red[w][threadIdx.x];
     const int t = threadIdx.x < 15 ? threadIdx.x : 20;
+    if (s != 0.0) atomicAdd(&grad[(size_t)b * GLAD_NTHETA + t], s);
+  }
+}
+
+// Composite class (Sect. 3.3): the same adjoint with duals over the 12 parameters the ray
+// shooting depends on, tangents 0..7 = theta 0..7 (kappa_s, r_s, q of the halo, phi, x_c, y_c,
+// shear), 8 = theta 13 (I0), 9 = theta 14 (w_t), 10 = theta 17 (Upsilon_*), 11 = theta 18 (f_BH);
+// the halo's CSEs, the Chameleons' softened isothermal pairs and the black-hole Gaussian in dual
+// arithmetic; the Chameleon lens light and the Sersic source by analytic partials.
+typedef Dual<12, float> D12;
+#define NGC 18  // theta 0..14, then lambda_int (20), Upsilon_* (17), f_BH (18)
+
+__device__ __forceinline__ void nie_d12(const D12 &x, const D12 &y, const D12 &A, const D12 &s, float q,
+                                        float e, float sg, D12 &ax, D12 &ay) {
+  if (e > 1e-3f) {
+    const D12 ps = dsqrt(q * q * (s * s + x * x) + y * y);
+    const D12 b = (2.0f * q / e) * A;
+    ax = ax + sg * (b * datan(e * x / (ps + s)));
+    ay = ay + sg * (b * datanh(e * y / (ps + (q * q) * s)));
+  } else {
+    const D12 fac = 2.0f * A / (dsqrt(x * x + y * y + s * s) + s);
+    ax = ax + sg * (fac * x);
+    ay = ay + sg * (fac * y);
+  }
+}
+
+__global__ void __launch_bounds__(LENS_THREADS) k_image_grad_comp(const SysDev *__restrict__ sysv,
+                                                                  const int *__restrict__ sys_id,
+                                                                  WsDev ws, GradWs gw, int max_pix,
+                                                                  double *grad) {
+  const int b = blockIdx.y;
+  if (ws.status[b] != GLAD_SAMPLE_OK) return;
+  const SysDev &S = sysv[sys_id[b]];
+  if (S.mass_class != 1) return;
+  const int p = blockIdx.x * LENS_THREADS + threadIdx.x;
+  __shared__ LensP L;
+  __shared__ float red[LENS_THREADS / 32][NGC];
+  load_lensp(&ws.lp[b], L);
+  __syncthreads();
+  float acc[NGC];
+#pragma unroll
+  for (int i = 0; i < NGC; ++i) acc[i] = 0.0f;
+  if (p < S.npix) {
+    const int i = p / S.nx, j = p - i * S.nx;
+    const int ss = S.ss;
+    const float pix = S.pix;
+    const float wpix = gw.gpix[(size_t)b * max_pix + p] / (float)(ss * ss);
+    const float x0 = (j - 0.5f * (S.nx - 1)) * pix;
+    const float y0 = (i - 0.5f * (S.ny - 1)) * pix;
+    D12 cphi(L.cphi), sphi(L.sphi);
+    cphi.d[3] = -L.sphi;
+    sphi.d[3] = L.cphi;
+    D12 g1(L.g1), g2(L.g2);
+    g1.d[6] = L.c2pe;
+    g1.d[7] = -2.0f * L.gext * L.s2pe;
+    g2.d[6] = L.s2pe;
+    g2.d[7] = 2.0f * L.gext * L.c2pe;
+    D12 ups(L.ups);  // Upsilon_* L_scale, d/d Upsilon_* = L_scale
+    ups.d[10] = (float)S.L_scale;
+    D12 bhM(L.bh_M);
+    bhM.d[8] = L.bh_dM[0];
+    bhM.d[9] = L.bh_dM[1];
+    bhM.d[10] = L.bh_dM[2];
+    bhM.d[11] = L.bh_dM[3];
+    const D12 hq = D12::var(L.h_q, 2);
+    const D12 ks = D12::var(L.h_ks, 0), rs = D12::var(L.h_rs, 1);
+    for (int my = 0; my < ss; ++my) {
+      const float y = y0 + ((my + 0.5f) / ss - 0.5f) * pix;
+      for (int mx = 0; mx < ss; ++mx) {
+        const float x = x0 + ((mx + 0.5f) / ss - 0.5f) * pix;
+        D12 dx(x - L.xc), dy(y - L.yc);
+        dx.d[4] = -1.0f;
+        dy.d[5] = -1.0f;
+        const D12 xp = cphi * dx + sphi * dy, yp = cphi * dy - sphi * dx;
+        D12 fx(0.0f), fy(0.0f);
+        // baryons: Upsilon L_scale x each Chameleon's pair of softened isothermal ellipsoids
+        for (int c = 0; c < S.n_lcomp && c < 4; ++c) {
+          D12 A = L.li_A[c] * ups;  // Upsilon_* L_scale I0 / (1 + q)
+          if (c == 0) A.d[8] = ups.v / (1.0f + L.ch_q[0]);
+          D12 st(L.ch_st[c]);
+          if (c == 0) st.d[9] = 2.0f / (1.0f + L.ch_q[c]);
+          nie_d12(xp, yp, A, D12(L.ch_sc[c]), L.ch_q[c], L.ch_e[c], 1.0f, fx, fy);
+          nie_d12(xp, yp, A, st, L.ch_q[c], L.ch_e[c], -1.0f, fx, fy);
+        }
+        // halo: CSE i with amplitude kappa_s a_i r_s^3 and core s_i r_s, axis ratio q of the halo
+        {
+          const D12 q2 = hq * hq, e2 = 1.0f - q2;
+          const D12 base = q2 * xp * xp + yp * yp, ex2 = e2 * xp * xp;
+          D12 hx(0.0f), hy(0.0f);
+          for (int k = 0; k < GLAD_N_CSE; ++k) {
+            if (L.cse_a3[k] == 0.0f) continue;
+            const float s1 = L.cse_sc[k] / L.h_rs;  // core in units of r_s
+            const D12 sc = s1 * rs;
+            const D12 amp = ks * (L.cse_a3[k] / (L.h_rs * L.h_rs * L.h_rs)) * rs * rs * rs;
+            const D12 ps = dsqrt(base + q2 * sc * sc);
+            const D12 D = (ps + sc) * (ps + sc) + ex2;
+            const D12 w = amp / (sc * ps * D);
+            hx = hx + w * (ps + q2 * sc);
+            hy = hy + w * (ps + sc);
+          }
+          fx = fx + 2.0f * hq * xp * hx;
+          fy = fy + 2.0f * hq * yp * hy;
+        }
+        D12 ax = cphi * fx - sphi * fy;
+        D12 ay = sphi * fx + cphi * fy;
+        if (L.bh_M > 0.0f) {
+          // round Gaussian: M h1(t) / (pi 2 sigma^2) (dx, dy), t = R^2 / (2 sigma^2)
+          const D12 t = (dx * dx + dy * dy) / L.bh_2s2;
+          D12 h1;
+          if (t.v < 1e-3f) {
+            h1 = 1.0f - 0.5f * t;
+          } else {
+            const float em = expf(-t.v), hv = -expm1f(-t.v) / t.v;
+            h1 = dual_apply(t, hv, (em * (t.v + 1.0f) - 1.0f) / (t.v * t.v));
+          }
+          const D12 gfac = bhM * h1 / (3.14159265358979f * L.bh_2s2);
+          ax = ax + gfac * dx;
+          ay = ay + gfac * dy;
+        }
+        ax = ax + g1 * dx + g2 * dy;
+        ay = ay + g2 * dx - g1 * dy;
+        for (int k = 0; k < S.n_sis; ++k) {
+          const float te = (float)S.sis[3 * k];
+          const float sx = x - (float)S.sis[3 * k + 1], sy = y - (float)S.sis[3 * k + 2];
+          const float r2 = sx * sx + sy * sy;
+          const float ir = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+          ax.v += te * sx * ir;
+          ay.v += te * sy * ir;
+        }
+        float dax_dl = 0.0f, day_dl = 0.0f;
+        if (L.sheet) {
+          D12 u(1.0f);
+          if (L.sheet == 1) {
+            const D12 R2 = dx * dx + dy * dy;
+            const D12 Qc = dsqrt(R2 + L.sh_rc2), Qt = dsqrt(R2 + L.sh_rt2);
+            u = (2.0f * L.sh_rc * L.sh_rt) * (1.0f + (L.sh_rc + L.sh_rt) / (Qc + Qt)) /
+                ((L.sh_rc + Qc) * (L.sh_rt + Qt));
+          }
+          dax_dl = ax.v - u.v * dx.v;
+          day_dl = ay.v - u.v * dy.v;
+          const D12 om = (1.0f - L.lam) * u;
+          ax = L.lam * ax + om * dx;
+          ay = L.lam * ay + om * dy;
+        }
+        // source at beta = theta - alpha
+        const float bx = x - ax.v - L.src_x, by = y - ay.v - L.src_y;
+        const float cs = S.src_cphi, sn = S.src_sphi, iq2 = 1.0f / (S.src_q * S.src_q);
+        const float xs = cs * bx + sn * by, ys = -sn * bx + cs * by;
+        const float Re2i = L.src_Rei * L.src_Rei;
+        const float Rs2 = (xs * xs + ys * ys * iq2) * Re2i;
+        const SersicD sd = sersic_d(Rs2, L.src_Ie, L.src_ninv, L.src_bn);
+        const float dI_dbx = sd.dI_dR2 * Re2i * 2.0f * (xs * cs - ys * iq2 * sn);
+        const float dI_dby = sd.dI_dR2 * Re2i * 2.0f * (xs * sn + ys * iq2 * cs);
+        float gsub[NGC];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) gsub[k] = -(dI_dbx * ax.d[k] + dI_dby * ay.d[k]);
+        gsub[8] = sd.I / L.src_Ie;
+        gsub[9] = -sd.dI_dR2 * 2.0f * Rs2 / L.src_Rei * Re2i;
+        {
+          const float lnr = Rs2 > 1e-30f ? 0.5f * logf(Rs2) : 0.0f;
+          const float dw_dn = -sd.w * lnr * L.src_ninv * L.src_ninv;
+          gsub[10] = sd.I * (-L.src_bnp * (sd.w - 1.0f) - L.src_bn * dw_dn);
+        }
+        gsub[11] = -dI_dbx;
+        gsub[12] = -dI_dby;
+        gsub[13] = -(dI_dbx * ax.d[8] + dI_dby * ay.d[8]);
+        gsub[14] = -(dI_dbx * ax.d[9] + dI_dby * ay.d[9]);
+        gsub[15] = -(dI_dbx * dax_dl + dI_dby * day_dl);
+        gsub[16] = -(dI_dbx * ax.d[10] + dI_dby * ay.d[10]);
+        gsub[17] = -(dI_dbx * ax.d[11] + dI_dby * ay.d[11]);
+        // Chameleon lens light: li_A [(m^2 + sc^2)^-1/2 - (m^2 + st^2)^-1/2], m^2 = x'^2 + y'^2/q^2
+        for (int c = 0; c < S.n_lcomp && c < 4; ++c) {
+          const float q = L.ch_q[c], iq2c = 1.0f / (q * q);
+          const float m2 = xp.v * xp.v + yp.v * yp.v * iq2c;
+          const float rc = rsqrtf(m2 + L.ch_sc[c] * L.ch_sc[c]), rt = rsqrtf(m2 + L.ch_st[c] * L.ch_st[c]);
+          const float dIdm2 = -0.5f * L.li_A[c] * (rc * rc * rc - rt * rt * rt);
+          const float dxp = dIdm2 * 2.0f * xp.v, dyp = dIdm2 * 2.0f * yp.v * iq2c;
+#pragma unroll
+          for (int k = 3; k < 6; ++k) gsub[k] += dxp * xp.d[k] + dyp * yp.d[k];
+          if (c == 0) {
+            gsub[13] += (rc - rt) / (1.0f + q);                                     // d/d I0
+            gsub[14] += L.li_A[0] * rt * rt * rt * L.ch_st[0] * 2.0f / (1.0f + q);  // d/d w_t
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < NGC; ++k) acc[k] = fmaf(wpix, gsub[k], acc[k]);
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NGC; ++k) {
+    float v = acc[k];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NGC) {
+    double s = 0.0;
+    for (int w = 0; w < LENS_THREADS / 32; ++w) s += (double)red[w][threadIdx.x];
+    const int k = threadIdx.x;
+    const int t = k < 15 ? k : (k == 15 ? 20 : (k == 16 ? 17 : 18));
     if (s != 0.0) atomicAdd(&grad[(size_t)b * GLAD_NTHETA + t], s);
   }
 }
@@ -738,17 +942,6 @@ typedef Dual<5, double> D5;   // tangents: c0_k, e2_j, s2, c2, b
 typedef Dual<9, double> D9;   // tangents: theta 0,1,2,13,14,15,16,17,18
 typedef Dual<1, double> DT1;  // one tangent of the delay term (theta 0..7 or H0)
 
-struct cplx {
-  double r, i;
-};
-__device__ inline cplx cmul(cplx a, cplx b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
-__device__ inline cplx cexp_(cplx a) {
-  double s, c;
-  sincos(a.i, &s, &c);
-  const double e = exp(a.r);
-  return {e * c, e * s};
-}
-__device__ inline cplx clog_(cplx a) { return {log(hypot(a.r, a.i)), atan2(a.i, a.r)}; }
 
 // Table adjoint -> per-Gaussian JAM inputs.  One warp per (tracer k, mass j) pair, lanes
 // over the Gauss-Legendre nodes; FP64 duals through the table formula (tangents c0_k, e2_j,
@@ -872,15 +1065,45 @@ __global__ void __launch_bounds__(256) k_grad_chain(const SysDev *__restrict__ s
   // Euler-inversion sums of each Gaussian and of its partial (R_e for the first lens light,
   // gamma' for the mass), the (Gaussian, node) terms spread over the block
   __shared__ double mf[GLAD_MAX_LIGHT + GLAD_MAX_MASS][2];
+  // composite class: light sums are of the Chameleons (f2: d/dw_t of the first), then the
+  // halo's (f: of k(u) without kappa_s, f2: of u dk/du), at mf[nL + h]
+  const bool comp = S.mass_class == 1;
+  const int nE = comp ? nL + S.n_halo : nL + nM;
   for (int k = tid; k < nL + nM; k += blockDim.x) mf[k][0] = mf[k][1] = 0.0;
   __syncthreads();
   {
     const double coef = (3.0 - g) / (1.0 + q) * pow(tE, g - 1.0);
     const double rs2 = S.r_soft * S.r_soft;
-    for (int it = tid; it < (nL + nM) * P2; it += blockDim.x) {
+    for (int it = tid; it < nE * P2; it += blockDim.x) {
       const int k = it / P2, m = it - k * P2;
       const double2 ch = S.chi[m];
       double f, f2;
+      if (comp) {
+        if (k < nL) {
+          const int cc = S.lcomp_of[k];
+          const double qc = S.lcomp[4 * cc + 3];
+          const double I0 = cc == 0 ? th[13] : S.lcomp[4 * cc];
+          const double wt = cc == 0 ? th[14] : S.lcomp[4 * cc + 2];
+          const double A = I0 / (1.0 + qc), sc = 2.0 * S.lcomp[4 * cc + 1] / (1.0 + qc);
+          const double st = 2.0 * wt / (1.0 + qc);
+          const double sg = S.sig_light[k];
+          const cplx z = {sg * ch.x, sg * ch.y};
+          const cplx z2 = cmul(z, z);
+          const cplx a = cpow_({z2.r + sc * sc, z2.i}, -0.5), bq = cpow_({z2.r + st * st, z2.i}, -0.5);
+          f = S.eta[m] * A * (a.r - bq.r);
+          const cplx p3 = cpow_({z2.r + st * st, z2.i}, -1.5);
+          f2 = cc == 0 ? S.eta[m] * A * st * 2.0 / (1.0 + qc) * p3.r : 0.0;
+        } else {
+          const double sg = S.sig_mass[k];  // halo Gaussian h = k - nL sits at mass index nL + h = k
+          cplx udk;
+          const cplx kk = nfw_k_c({sg * ch.x / th[1], sg * ch.y / th[1]}, &udk);
+          f = S.eta[m] * kk.r;
+          f2 = S.eta[m] * udk.r;
+        }
+        atomicAdd(&mf[k][0], f);
+        atomicAdd(&mf[k][1], f2);
+        continue;
+      }
       if (k < nL) {
         const int cc = S.lcomp_of[k];
         const double Ie = cc == 0 ? th[13] : S.lcomp[4 * cc];
@@ -939,14 +1162,32 @@ __global__ void __launch_bounds__(256) k_grad_chain(const SysDev *__restrict__ s
       }
     }
   }
+  __syncthreads();  // Ad (the tracer amplitudes with tangents) complete
   for (int j = tid; j < nM; j += blockDim.x) {
     const double sg = S.sig_mass[j];
-    const double f = mf[nL + j][0], fg = mf[nL + j][1];
-    D9 A(S.mw_mass[j] * f);
-    A.d[0] = A.v * (g - 1.0) / tE;
-    A.d[1] = S.mw_mass[j] * fg;
-    A.d[2] = -A.v / (1.0 + q);
-    const D9 qp = D9::var(q, 2);
+    D9 A, qp;
+    if (comp && j < nL) {
+      // baryons: Upsilon_* L_scale x tracer Gaussian j (tangents I0, w_t of the tracer, Upsilon)
+      A.v = Ad[j][0];
+      for (int i = 0; i < 9; ++i) A.d[i] = Ad[j][i + 1];
+      A = (th[17] * S.L_scale) * A;
+      A.d[7] = S.L_scale * Ad[j][0];
+      qp = D9(S.qp_light[j]);
+    } else if (comp) {
+      // halo: kappa_s mw sum eta Re k(u), u = z / r_s; d/d r_s = -kappa_s mw sum eta Re(u k'(u)) / r_s
+      const double f = mf[j][0], fu = mf[j][1];
+      A = D9(th[0] * S.mw_mass[j] * f);
+      A.d[0] = S.mw_mass[j] * f;
+      A.d[1] = -th[0] * S.mw_mass[j] * fu / th[1];
+      qp = D9::var(q, 2);
+    } else {
+      const double f = mf[nL + j][0], fg = mf[nL + j][1];
+      A = D9(S.mw_mass[j] * f);
+      A.d[0] = A.v * (g - 1.0) / tE;
+      A.d[1] = S.mw_mass[j] * fg;
+      A.d[2] = -A.v / (1.0 + q);
+      qp = D9::var(q, 2);
+    }
     const D9 qi2 = (qp * qp - C2) / S2;
     const D9 Cj = (2.0 * SQRT2PI_D * v2u * lam * sg) * qp * A;
     const D9 e2 = 1.0 - qi2;
@@ -970,7 +1211,9 @@ __global__ void __launch_bounds__(256) k_grad_chain(const SysDev *__restrict__ s
     }
   }
   __syncthreads();
+  __shared__ double sh_mb[10];  // black-hole mass before lambda and its 9 tangents (composite lens)
   if (tid == 0) {
+    for (int i = 0; i < 10; ++i) sh_mb[i] = 0.0;
     // black hole: A_BH = f_BH Upsilon L_tot L_scale / (2 pi s^2), L_tot = sum 2 pi A_k s_k^2 q'_k
     if (S.has_bh) {
       D9 L(0.0);
@@ -982,6 +1225,9 @@ __global__ void __launch_bounds__(256) k_grad_chain(const SysDev *__restrict__ s
       }
       const D9 ups = D9::var(th[17], 7), fbh = D9::var(th[18], 8);
       const double sb = S.bh_sigma;
+      const D9 Mb = fbh * ups * L * S.L_scale;
+      sh_mb[0] = Mb.v;
+      for (int i = 0; i < 9; ++i) sh_mb[1 + i] = Mb.d[i];
       const D9 A = fbh * ups * L * (lam * S.L_scale / (2.0 * PI_D * sb * sb));
       const D9 qi2 = (1.0 - C2) / S2;
       const D9 Cj = 2.0 * SQRT2PI_D * v2u * sb * A;
@@ -1000,18 +1246,25 @@ __global__ void __launch_bounds__(256) k_grad_chain(const SysDev *__restrict__ s
     const double bb = 1.0 / (1.0 - th[16]);
     gsm[16] += a_glob[2] * bb * bb;
   }
-  if (tid >= 32 && tid < 42) {
+  __syncthreads();
+  if (tid >= 32 && tid < 46) {
     // time delays and image positions: -(chi2_tmd + chi2_img)/2 by duals through the FP64
     // lens model, one tangent per thread: theta 0..7, the delay distance (H0 = theta 19 in
-    // distance mode 0, D_dt,int = theta 22 in mode 1) and lambda_int (theta 20, with a sheet)
+    // distance mode 0, D_dt,int = theta 22 in mode 1), lambda_int (theta 20, with a sheet) and,
+    // in the composite class, I0, w_t, Upsilon_*, f_BH (theta 13, 14, 17, 18: the baryons and
+    // the black hole, whose mass carries its tangent from the chain above)
     const int q = tid - 32;
-    const int t = q < 8 ? q : (q == 8 ? (S.distance_mode == 1 ? 22 : 19) : 20);
-    if (t != 20 || S.sheet) {
+    const int tmap[14] = {0, 1, 2, 3, 4, 5, 6, 7, S.distance_mode == 1 ? 22 : 19, 20, 13, 14, 17, 18};
+    const int t = tmap[q];
+    const bool used = q < 9 || (q == 9 && S.sheet) || (q >= 10 && comp);
+    if (used) {
       DT1 tt[GLAD_NTHETA];
       for (int i = 0; i < GLAD_NTHETA; ++i) tt[i] = i == t ? DT1::var(th[i], 0) : DT1(th[i]);
-      DT1 chi = chi2_tmd_t<DT1>(tt, S);
+      DT1 mbh(sh_mb[0]);
+      if (comp && q >= 10) mbh.d[0] = sh_mb[1 + (t == 13 ? 3 : t == 14 ? 4 : t == 17 ? 7 : 8)];
+      DT1 chi = chi2_tmd_t<DT1>(tt, S, mbh);
       // image positions: lens parameters (and the sheet) only
-      if (S.img_sig && t != 19 && t != 22) chi = chi + chi2_img_t<DT1>(tt, S);
+      if (S.img_sig && t != 19 && t != 22) chi = chi + chi2_img_t<DT1>(tt, S, mbh);
       atomicAdd(&gsm[t], -0.5 * chi.d[0]);
     }
   }
@@ -1118,8 +1371,14 @@ cudaError_t launch_grad_lens(glad_ctx *c, const int *sys_id, int B, double *grad
         c->d_sys, sys_id, c->ws.d, g, c->max_pix);
     cudaError_t r = cudaGetLastError();
     if (r != cudaSuccess) return r;
-    k_image_grad<<<dim3(c->max_img_tiles, B), LENS_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, g,
-                                                                     c->max_pix, grad);
+    bool epl = false, comp = false;
+    for (auto &sd : c->h_sysdev) (sd.mass_class == 1 ? comp : epl) = true;
+    if (epl)
+      k_image_grad<<<dim3(c->max_img_tiles, B), LENS_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, g,
+                                                                       c->max_pix, grad);
+    if (comp)
+      k_image_grad_comp<<<dim3(c->max_img_tiles, B), LENS_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d,
+                                                                            g, c->max_pix, grad);
     return cudaGetLastError();
   }()));
 }

@@ -19,6 +19,57 @@ __device__ __forceinline__ float sersic_f(float R2_scaled, float Ie, float ninv,
   return Ie * expf(-bn * (w - 1.0f));
 }
 
+// Composite galaxy (Sect. 3.3) at frame position (xp, yp): adds to the frame deflection.
+// Softened isothermal ellipsoid pair of each Chameleon, b = 2 q A (A = Upsilon L_scale I0/(1+q)):
+//   alpha = b/e (arctan(e x/(psi + s)), arctanh(e y/(psi + q^2 s))), psi = sqrt(q^2 (s^2 + x^2) + y^2),
+// its round limit 2 A (x, y)/(sqrt(R^2 + s^2) + s) for e < 1e-3; halo CSE i (amplitude amp, core s):
+//   alpha = 2 q amp (x (psi + q^2 s), y (psi + s)) / (s psi D), D = (psi + s)^2 + (1 - q^2) x^2
+// (the y denominator q^2 D written without the cancelling form).
+__device__ __forceinline__ void composite_frame(const LensP &L, int n_lcomp, float xp, float yp,
+                                                float &ax, float &ay) {
+  for (int c = 0; c < n_lcomp && c < 4; ++c) {
+    const float q = L.ch_q[c], e = L.ch_e[c], A = L.ch_A[c];
+    float sx = 0.0f, sy = 0.0f;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const float s = t == 0 ? L.ch_sc[c] : L.ch_st[c];
+      const float sg = t == 0 ? 1.0f : -1.0f;
+      if (e > 1e-3f) {
+        const float ps = sqrtf(q * q * (s * s + xp * xp) + yp * yp);
+        const float b = 2.0f * q * A / e;
+        sx += sg * b * atanf(e * xp / (ps + s));
+        sy += sg * b * atanhf(e * yp / (ps + q * q * s));
+      } else {
+        const float fac = 2.0f * A / (sqrtf(xp * xp + yp * yp + s * s) + s);
+        sx += sg * fac * xp;
+        sy += sg * fac * yp;
+      }
+    }
+    ax += sx;
+    ay += sy;
+  }
+  const float q = L.h_q, q2 = q * q;
+  const float base = q2 * xp * xp + yp * yp, ex2 = L.h_e2 * xp * xp;
+  float hx = 0.0f, hy = 0.0f;
+  for (int i = 0; i < GLAD_N_CSE; ++i) {
+    const float s = L.cse_sc[i], amp = L.cse_amp[i];
+    const float ps = sqrtf(base + q2 * s * s);
+    const float D = (ps + s) * (ps + s) + ex2;
+    const float w = amp / (s * ps * D);
+    hx += w * (ps + q2 * s);
+    hy += w * (ps + s);
+  }
+  ax += 2.0f * q * xp * hx;
+  ay += 2.0f * q * yp * hy;
+}
+
+// Round Gaussian black hole of mass M: alpha = M (1 - e^-t)/(pi R^2) (dx, dy), t = R^2/(2 sigma^2)
+__device__ __forceinline__ float bh_gauss_factor(float M, float s2x2, float dx, float dy) {
+  const float t = (dx * dx + dy * dy) / s2x2;
+  const float h1 = t < 1e-3f ? 1.0f - 0.5f * t : -expm1f(-t) / t;
+  return M * h1 / (3.14159265358979f * s2x2);
+}
+
 __global__ void __launch_bounds__(LENS_THREADS) k_image(const SysDev *__restrict__ sysv,
                                                         const int *__restrict__ sys_id, WsDev ws,
                                                         int max_pix) {
@@ -47,26 +98,37 @@ __global__ void __launch_bounds__(LENS_THREADS) k_image(const SysDev *__restrict
       const float x = x0 + ((mx + 0.5f) / ss - 0.5f) * pix;
       const float dx = x - L.xc, dy = y - L.yc;
       const float xp = L.cphi * dx + L.sphi * dy, yp = -L.sphi * dx + L.cphi * dy;
-      // EPL (Tessore & Metcalf series)
-      // at the exact centre alpha is taken as 0 (its direction is undefined there)
-      const float R = sqrtf(q * q * xp * xp + yp * yp);
-      const float iR = R > 0.0f ? 1.0f / R : 0.0f;
-      const float wr = q * xp * iR, wi = yp * iR;
-      const float w2r = wr * wr - wi * wi, w2i = 2.0f * wr * wi;
-      float omr = wr, omi = wi, Sr = wr, Si = wi;
-      for (int n = 0; n < L.nterms; ++n) {
-        const float rr = L.rho[n];
-        const float nr = rr * (w2r * omr - w2i * omi);
-        const float ni = rr * (w2r * omi + w2i * omr);
-        omr = nr;
-        omi = ni;
-        Sr += omr;
-        Si += omi;
+      float apx = 0.0f, apy = 0.0f;
+      if (L.mclass == 1) {
+        composite_frame(L, S.n_lcomp, xp, yp, apx, apy);
+      } else {
+        // EPL (Tessore & Metcalf series)
+        // at the exact centre alpha is taken as 0 (its direction is undefined there)
+        const float R = sqrtf(q * q * xp * xp + yp * yp);
+        const float iR = R > 0.0f ? 1.0f / R : 0.0f;
+        const float wr = q * xp * iR, wi = yp * iR;
+        const float w2r = wr * wr - wi * wi, w2i = 2.0f * wr * wi;
+        float omr = wr, omi = wi, Sr = wr, Si = wi;
+        for (int n = 0; n < L.nterms; ++n) {
+          const float rr = L.rho[n];
+          const float nr = rr * (w2r * omr - w2i * omi);
+          const float ni = rr * (w2r * omi + w2i * omr);
+          omr = nr;
+          omi = ni;
+          Sr += omr;
+          Si += omi;
+        }
+        const float amp = R > 0.0f ? L.pref * exp2f(omt * log2f(R)) : 0.0f;
+        apx = amp * Sr;
+        apy = amp * Si;
       }
-      const float amp = R > 0.0f ? L.pref * exp2f(omt * log2f(R)) : 0.0f;
-      const float apx = amp * Sr, apy = amp * Si;
       float ax = L.cphi * apx - L.sphi * apy;
       float ay = L.sphi * apx + L.cphi * apy;
+      if (L.mclass == 1 && L.bh_M > 0.0f) {
+        const float g = bh_gauss_factor(L.bh_M, L.bh_2s2, dx, dy);
+        ax += g * dx;
+        ay += g * dy;
+      }
       ax += L.g1 * dx + L.g2 * dy;
       ay += L.g2 * dx - L.g1 * dy;
       for (int k = 0; k < S.n_sis; ++k) {
@@ -95,10 +157,17 @@ __global__ void __launch_bounds__(LENS_THREADS) k_image(const SysDev *__restrict
       const float xs = S.src_cphi * bx + S.src_sphi * by, ys = -S.src_sphi * bx + S.src_cphi * by;
       const float Rs2 = (xs * xs + ys * ys / (S.src_q * S.src_q)) * (L.src_Rei * L.src_Rei);
       float v = sersic_f(Rs2, L.src_Ie, L.src_ninv, L.src_bn);
-      // lens light (same centre and PA as the mass)
-      for (int c = 0; c < S.n_lcomp; ++c) {
-        const float R2 = (xp * xp + yp * yp * L.ll_qi2[c]) * (L.ll_Rei[c] * L.ll_Rei[c]);
-        v += sersic_f(R2, L.ll_Ie[c], L.ll_ninv[c], L.ll_bn[c]);
+      // lens light (same centre and PA as the mass): Sersic, or Chameleon in the composite class
+      if (L.mclass == 1) {
+        for (int c = 0; c < S.n_lcomp && c < 4; ++c) {
+          const float m2 = xp * xp + yp * yp / (L.ch_q[c] * L.ch_q[c]);
+          v += L.li_A[c] * (rsqrtf(m2 + L.ch_sc[c] * L.ch_sc[c]) - rsqrtf(m2 + L.ch_st[c] * L.ch_st[c]));
+        }
+      } else {
+        for (int c = 0; c < S.n_lcomp; ++c) {
+          const float R2 = (xp * xp + yp * yp * L.ll_qi2[c]) * (L.ll_Rei[c] * L.ll_Rei[c]);
+          v += sersic_f(R2, L.ll_Ie[c], L.ll_ninv[c], L.ll_bn[c]);
+        }
       }
       acc += v;
     }

@@ -11,22 +11,11 @@
 //    with the magnification-weighted source estimate of Sect. 3.1.1, and the
 //    image-position term (Eq. chi2_img) for systems that give image-position errors.
 // A second kernel expands the (tracer k, mass j, node g) JAM coefficient table.
+#include "cplx.cuh"
 #include "glad_internal.cuh"
 #include "lensmath.cuh"
 
 namespace {
-
-struct cplx {
-  double r, i;
-};
-__device__ inline cplx cmul(cplx a, cplx b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
-__device__ inline cplx cexp_(cplx a) {
-  double s, c;
-  sincos(a.i, &s, &c);
-  const double e = exp(a.r);
-  return {e * c, e * s};
-}
-__device__ inline cplx clog_(cplx a) { return {log(hypot(a.r, a.i)), atan2(a.i, a.r)}; }
 
 // Sersic profile at complex radius z
 __device__ inline double sersic_re(cplx z, double Ie, double Re, double n, double bn) {
@@ -53,8 +42,11 @@ __device__ inline int domain_ok(const double *th, const SysDev &S) {
   const bool mode1 = S.distance_mode == 1;
   for (int i = 0; i < 19; ++i) ok = ok && isfinite(th[i]);
   const double g = th[1], q = th[2], inc = th[15];
-  ok = ok && th[0] > 0.0 && g > 1.0 && g < 3.0 && q > 0.0 && q <= 1.0 && th[9] > 0.0 &&
-       th[10] > 0.0 && th[14] > 0.0 && th[13] > 0.0 && inc > 0.0 &&
+  if (S.mass_class == 1)  // kappa_s >= 0, r_s > 0, halo q in (0, 1], I0 > 0, w_t > w_c
+    ok = ok && th[0] >= 0.0 && th[1] > 0.0 && q > 0.0 && q <= 1.0 && th[13] > 0.0 && th[14] > S.lcomp[1];
+  else
+    ok = ok && th[0] > 0.0 && g > 1.0 && g < 3.0 && q > 0.0 && q <= 1.0 && th[14] > 0.0 && th[13] > 0.0;
+  ok = ok && th[9] > 0.0 && th[10] > 0.0 && inc > 0.0 &&
        inc <= 1.5707963267948966 + 1e-12 && th[16] < 1.0 && th[17] >= 0.0 && th[18] >= 0.0;
   if (mode1)
     ok = ok && isfinite(th[21]) && isfinite(th[22]) && th[21] > 0.0 && th[22] > 0.0;
@@ -76,6 +68,8 @@ __global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
   __shared__ double sh_rho[GLAD_MAX_LIGHT + GLAD_MAX_MASS + 1];
   __shared__ double sh_q[GLAD_MAX_LIGHT + GLAD_MAX_MASS + 1];
   __shared__ int sh_flag;
+  __shared__ double sh_mbh;  // black-hole mass before lambda_int (the composite lens uses it)
+  __shared__ double sh_dm[4];  // its derivatives by theta 13, 14, 17, 18 (composite class)
 
   const int ok = domain_ok(th, S);
   if (!ok) {
@@ -95,32 +89,68 @@ __global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
   // ---- 1-D MGE (Euler inversion), FP64: the (Gaussian, Euler node) terms are spread over
   // the block and summed per Gaussian in shared memory
   const double coef_m = (3.0 - g) / (1.0 + q) * pow(tE, g - 1.0);
+  // Gaussians expanded here: the tracer's, then the EPL's (or, composite class, the halo's
+  // n_halo, whose mass index is nL + h after the nL copies of the tracer)
+  const bool comp = S.mass_class == 1;
+  const int off = comp ? nL : 0;
+  const int nE = nL + (comp ? S.n_halo : nM);
+  __shared__ double sh_dAw[GLAD_MAX_LIGHT];  // composite: d A_k / d w_t of the first Chameleon
   for (int k = tid; k < nL + nM; k += blockDim.x) {
     sh_A[k] = 0.0;
-    sh_q[k] = k < nL ? S.qp_light[k] : q;
+    sh_q[k] = k < nL ? S.qp_light[k] : (comp && k < 2 * nL ? S.qp_light[k - nL] : q);
+    if (k < nL) sh_dAw[k] = 0.0;
   }
   __syncthreads();
-  for (int it = tid; it < (nL + nM) * P2; it += blockDim.x) {
+  for (int it = tid; it < nE * P2; it += blockDim.x) {
     const int k = it / P2, m = it - k * P2;
     const double2 ch = S.chi[m];
     double v;
+    int dst = k;
     if (k < nL) {
       const int c = S.lcomp_of[k];
-      const double Ie = c == 0 ? th[13] : S.lcomp[4 * c];
-      const double Re = c == 0 ? th[14] : S.lcomp[4 * c + 1];
-      const double n = S.lcomp[4 * c + 2];
       const double sg = S.sig_light[k];
-      v = S.mw_light[k] * S.eta[m] * sersic_re({sg * ch.x, sg * ch.y}, Ie, Re, n, sersic_bn_d(n));
+      if (comp) {
+        const double qc = S.lcomp[4 * c + 3];
+        const double I0 = c == 0 ? th[13] : S.lcomp[4 * c];
+        const double wt = c == 0 ? th[14] : S.lcomp[4 * c + 2];
+        const double st = 2.0 * wt / (1.0 + qc);
+        const cplx z = {sg * ch.x, sg * ch.y};
+        v = S.mw_light[k] * S.eta[m] *
+            chameleon_c(z, I0 / (1.0 + qc), 2.0 * S.lcomp[4 * c + 1] / (1.0 + qc), st).r;
+        if (c == 0) {
+          // d/dw_t: A st (z^2 + st^2)^(-3/2) 2/(1+q)
+          const cplx z2 = cmul(z, z);
+          const cplx p = cpow_({z2.r + st * st, z2.i}, -1.5);
+          atomicAdd(&sh_dAw[k], S.mw_light[k] * S.eta[m] * I0 / (1.0 + qc) * st * 2.0 / (1.0 + qc) * p.r);
+        }
+      } else {
+        const double Ie = c == 0 ? th[13] : S.lcomp[4 * c];
+        const double Re = c == 0 ? th[14] : S.lcomp[4 * c + 1];
+        const double n = S.lcomp[4 * c + 2];
+        v = S.mw_light[k] * S.eta[m] * sersic_re({sg * ch.x, sg * ch.y}, Ie, Re, n, sersic_bn_d(n));
+      }
+    } else if (comp) {
+      // halo: kappa_s k(z / r_s), the exact profile
+      const int j = off + (k - nL);
+      const double sg = S.sig_mass[j];
+      v = th[0] * S.mw_mass[j] * S.eta[m] * nfw_k_c({sg * ch.x / th[1], sg * ch.y / th[1]}, nullptr).r;
+      dst = nL + j;
     } else {
       // (3-g)/2 b^(g-1) with b = (2/(1+q))^(1/(g-1)) theta_E
       const double sg = S.sig_mass[k - nL];
       v = S.mw_mass[k - nL] * S.eta[m] *
           epl_kappa_re({sg * ch.x, sg * ch.y}, coef_m, g, S.r_soft * S.r_soft);
     }
-    atomicAdd(&sh_A[k], v);
+    atomicAdd(&sh_A[dst], v);
   }
   if (tid == 0) sh_flag = 0;
   __syncthreads();
+  if (comp) {
+    // baryons: Upsilon_* L_scale times the tracer Gaussians
+    const double ups = th[17] * S.L_scale;
+    for (int k = tid; k < nL; k += blockDim.x) sh_A[nL + k] = ups * sh_A[k];
+    __syncthreads();
+  }
   // internal mass sheet (Sect. 3.3, Eq. kappa int): the galaxy's Gaussians scaled by lambda,
   // then the sheet's round Gaussians, (1 - lambda) times their unit amplitudes
   const int nS = S.n_sheet;
@@ -137,9 +167,24 @@ __global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
   if (tid == 0) {
     double L = 0.0;
     for (int k = 0; k < nL; ++k) L += 2.0 * PI_D * sh_A[k] * S.sig_light[k] * S.sig_light[k] * sh_q[k];
+    sh_mbh = S.has_bh ? th[18] * th[17] * L * S.L_scale : 0.0;  // before lambda (lensing)
+    if (comp) {
+      // d M_BH / d(I0, w_t, Upsilon, f_BH) for the lensing gradient: L_tot's parts
+      double L0 = 0.0, Lw = 0.0;
+      for (int k = 0; k < nL; ++k)
+        if (S.lcomp_of[k] == 0) {
+          const double w = 2.0 * PI_D * S.sig_light[k] * S.sig_light[k] * sh_q[k];
+          L0 += w * sh_A[k];
+          Lw += w * sh_dAw[k];
+        }
+      const double f = S.has_bh ? th[18] * th[17] * S.L_scale : 0.0;
+      sh_dm[0] = f * L0 / th[13];
+      sh_dm[1] = f * Lw;
+      sh_dm[2] = S.has_bh ? th[18] * L * S.L_scale : 0.0;
+      sh_dm[3] = S.has_bh ? th[17] * L * S.L_scale : 0.0;
+    }
     if (S.has_bh) {
-      const double mbh = lam * th[18] * th[17] * L * S.L_scale;
-      sh_A[nL + nM + nS] = mbh / (2.0 * PI_D * S.bh_sigma * S.bh_sigma);
+      sh_A[nL + nM + nS] = lam * sh_mbh / (2.0 * PI_D * S.bh_sigma * S.bh_sigma);
       sh_q[nL + nM + nS] = 1.0;
     }
     // deprojection needs cos^2 i < q'^2 for every Gaussian (App. A)
@@ -204,7 +249,7 @@ __global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
   __shared__ double im_ax[GLAD_MAX_IMG], im_ay[GLAD_MAX_IMG], im_w[GLAD_MAX_IMG], im_psi[GLAD_MAX_IMG];
   if (tid >= 32 && tid < 32 + S.n_img) {
     const int i = tid - 32;
-    LensEvalT<double> e = lens_eval_t<double>(S.img_xy[2 * i], S.img_xy[2 * i + 1], th, S);
+    LensEvalT<double> e = lens_eval_t<double>(S.img_xy[2 * i], S.img_xy[2 * i + 1], th, S, sh_mbh);
     im_ax[i] = e.ax;
     im_ay[i] = e.ay;
     im_psi[i] = e.psi;
@@ -214,7 +259,7 @@ __global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
   const double tq = g - 1.0;
   const double fq = (1.0 - q) / (1.0 + q);
   int nt = 0;
-  if (fq > 0.0) nt = (int)ceil(log(1e-9) / log(fq));
+  if (fq > 0.0 && !comp) nt = (int)ceil(log(1e-9) / log(fq));
   if (nt > GLAD_MAX_TM) nt = GLAD_MAX_TM;
   LensP &L = ws.lp[b];
   for (int n = 1 + tid; n <= nt; n += blockDim.x) {
@@ -276,7 +321,36 @@ __global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
     L.sh_rt = (float)S.sh_rt;
     L.sh_rc2 = (float)(S.sh_rc * S.sh_rc);
     L.sh_rt2 = (float)(S.sh_rt * S.sh_rt);
-    for (int c = 0; c < S.n_lcomp && c < 4; ++c) {
+    L.mclass = S.mass_class;
+    if (comp) {
+      const double ups = th[17] * S.L_scale;
+      for (int c = 0; c < S.n_lcomp && c < 4; ++c) {
+        const double qc = S.lcomp[4 * c + 3];
+        const double I0 = c == 0 ? th[13] : S.lcomp[4 * c];
+        const double wt = c == 0 ? th[14] : S.lcomp[4 * c + 2];
+        L.li_A[c] = (float)(I0 / (1.0 + qc));
+        L.ch_A[c] = (float)(ups * I0 / (1.0 + qc));
+        L.ch_sc[c] = (float)(2.0 * S.lcomp[4 * c + 1] / (1.0 + qc));
+        L.ch_st[c] = (float)(2.0 * wt / (1.0 + qc));
+        L.ch_q[c] = (float)qc;
+        L.ch_e[c] = (float)sqrt(1.0 - qc * qc);
+      }
+      L.ups = (float)ups;
+      L.h_ks = (float)th[0];
+      L.h_rs = (float)th[1];
+      L.h_q = (float)q;
+      L.h_e2 = (float)(1.0 - q * q);
+      L.bh_M = (float)sh_mbh;
+      L.bh_2s2 = (float)(2.0 * S.bh_sigma * S.bh_sigma);
+      for (int i = 0; i < 4; ++i) L.bh_dM[i] = (float)sh_dm[i];
+      const double rs3 = th[1] * th[1] * th[1];
+      for (int i = 0; i < GLAD_N_CSE; ++i) {
+        L.cse_amp[i] = (float)(th[0] * S.cse_a[i] * rs3);
+        L.cse_sc[i] = (float)(S.cse_s[i] * th[1]);
+        L.cse_a3[i] = (float)(S.cse_a[i] * rs3);
+      }
+    }
+    for (int c = 0; c < S.n_lcomp && c < 4 && !comp; ++c) {  // Sersic lens light (class 0)
       const double Ie = c == 0 ? th[13] : S.lcomp[4 * c];
       const double Re = c == 0 ? th[14] : S.lcomp[4 * c + 1];
       const double n = S.lcomp[4 * c + 2], ql = S.lcomp[4 * c + 3];
@@ -314,7 +388,7 @@ __global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
   }
   if (tid == 64 && S.img_sig) {
     // ---- image positions (FP64), beside the delays
-    ws.terms[4 * (size_t)b + 3] = chi2_img_t<double>(th, S);
+    ws.terms[4 * (size_t)b + 3] = chi2_img_t<double>(th, S, sh_mbh);
   }
 }
 

@@ -93,6 +93,8 @@ class GladContext:
         d.sheet_n = int(s.get("sheet_n", 0))
         d.sheet_rmin, d.sheet_rmax = float(s.get("sheet_rmin", 0.0)), float(s.get("sheet_rmax", 0.0))
         d.distance_mode = int(s.get("distance_mode", 0))
+        d.mass_class = int(s.get("mass_class", 0))
+        d.ll_wc = float(s.get("ll_wc", 0.0))
 
     # ------------------------------------------------------------------ calls
     def _check_theta(self, theta, sys_id):
