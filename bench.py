@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--grad", action="store_true",
                    help="time only logL + gradient (batch 64); by default both are timed")
     p.add_argument("--no-grad", action="store_true", help="time the forward logL only")
+    p.add_argument("--precision", type=int, default=0,
+                   help="forward precision mode (glad_set_precision): 0 FP32 bulk, 1 FP64 lensing, "
+                        "2 FP64 lensing and pair sum")
     p.add_argument("--batch", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--tuning", default="",
@@ -340,6 +343,7 @@ def measure(args, ctx, lib, systems, th_np, sid_np, B, grad_mode, world, rank, l
             rc = lib.glad_loglike(ctx.handle, P(sid), P(theta), B, P(logL), P(status), None, hs)
         _lib.check(rc, "step")
 
+    ctx.set_precision(0 if grad_mode else args.precision)
     # launch shapes picked by the library's autotuner on this batch (untimed), or pinned
     if args.tuning:
         jc, ept = (int(v) for v in args.tuning.split(","))
@@ -492,6 +496,8 @@ def measure(args, ctx, lib, systems, th_np, sid_np, B, grad_mode, world, rank, l
         peak_basis = (f"{N_SM} SM x {FFMA_LANES_PER_CLK_SM} FP32 lanes/clk/SM x {sm_max:.0f} MHz "
                       f"/ {ops} FMA-pipe operations per evaluation")
     executed = n_exec[jam_name]
+    if args.precision == 2 and not grad_mode and jam_name == "k_jam":
+        executed = evals  # the FP64 pair sum evaluates every term
     achieved = executed / (jam_ms / 1000.0) / 1e9
     achieved_alg = evals / (jam_ms / 1000.0) / 1e9
     unit = "logL+grad/s" if grad_mode else "logL/s"
@@ -581,9 +587,12 @@ def main():
         "metric": METRIC, "value": m["value"], "unit": m["unit"],
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64" if args.precision == 2 else "f32", "data": "synthetic",
         "config": {"workload": workload_name(w, main_grad, B), "batch_per_gpu": B,
-                   "precision": "f32 bulk; f64 MGE, tables and chi^2 reductions",
+                   "precision": ["f32 bulk; f64 MGE, tables and chi^2 reductions",
+                                 "f64 ray shooting, light and PSF; f32 Jeans sums",
+                                 "f64 forward pass (ray shooting, light, PSF, pair sum, binning)"]
+                                [args.precision],
                    "l2": "flushed (256 MB write) before each timed step",
                    "valid_samples": m["valid_samples"],
                    "tuning": m["tuning"], "cuda_graph": m["cuda_graph"],

@@ -261,6 +261,20 @@ int glad_tuning(glad_ctx *ctx, int *jam_code, int *adj_ept);
  * form; adj_ept 2 or 4).  GLAD_EINVAL for other values. */
 glad_status glad_set_tuning(glad_ctx *ctx, int jam_code, int adj_ept);
 
+/* Precision of the forward pass (Sect. 3: the paper computes in FP64 throughout).
+ * mode 0 (the default): FP32 bulk -- ray shooting, light, PSF blurring, the Jeans sums -- with
+ * the MGE, deprojection, pair table, delays and every chi^2 reduction in FP64.
+ * mode 1: as 0, but the ray shooting, source and lens light and the PSF blurring in FP64.
+ * mode 2: as 1, and the cylindrically aligned pair sum, the tracer surface brightness and the
+ * binning in FP64 too (every table entry, no skipping): the whole forward pass in FP64 (the
+ * spherically aligned model's grid and line-of-sight sums stay FP32).
+ * The inputs given as float32 (image data, noise, PSFs, kinematic data) are used as given.
+ * Applies to glad_loglike, glad_model_image and glad_vrms; glad_loglike_grad (its logL too) and
+ * glad_loglike_static always run in mode 0.  The FP64 modes allocate their own arrays at the next
+ * call (an FP64 copy of the lensing block, image and table per sample) and cost far more time
+ * (FP64 runs at 1/64 of the FP32 rate on this GPU).  GLAD_EINVAL for other modes. */
+glad_status glad_set_precision(glad_ctx *ctx, int mode);
+
 /* Negligible terms in the forward JAM pair sum (the project's own, no counterpart in the
  * paper).  For every sky tile the full sum at the tile's four corners gives a reference
  * value; a table entry whose term stays below 2^-(22 + log2 n_entries) of that reference

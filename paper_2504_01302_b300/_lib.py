@@ -55,6 +55,7 @@ SIGNATURES = {
     "glad_tuning": (C.c_int, [_p, _i, _i]),
     "glad_set_tuning": (C.c_int, [_p, C.c_int, C.c_int]),
     "glad_set_negligible": (C.c_int, [_p, C.c_int]),
+    "glad_set_precision": (C.c_int, [_p, C.c_int]),
     "glad_jam_evaluations": (C.c_int, [_p, C.POINTER(C.c_ulonglong), C.POINTER(C.c_ulonglong)]),
     "glad_enfw_cse": (C.c_int, [C.c_int, _d, _d, _d]),
     "glad_last_error": (C.c_char_p, []),

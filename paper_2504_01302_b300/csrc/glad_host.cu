@@ -228,6 +228,10 @@ glad_status build_system(int idx, const glad_system_desc &d, SysHost &sh, SysDev
   sd.src_q = (float)d.src_q;
   sd.src_cphi = (float)cos(d.src_phi);
   sd.src_sphi = (float)sin(d.src_phi);
+  sd.pix64 = d.pix;
+  sd.src_q64 = d.src_q;
+  sd.src_cphi64 = cos(d.src_phi);
+  sd.src_sphi64 = sin(d.src_phi);
   sd.n_lcomp = 1 + d.n_ll2;
   // lens-light rows: Sersic (I_e, R_e, n, q) or, in the composite class, Chameleon
   // (I0, w_c, w_t, q); row 0's I_e, R_e (or I0, w_t) come from theta
@@ -248,6 +252,7 @@ glad_status build_system(int idx, const glad_system_desc &d, SysHost &sh, SysDev
   sd.n_sub = sd.nsx * sd.nsy;
   sh.n_sub = sd.n_sub;
   sd.dsub = (float)(d.kpix / d.kss);
+  sd.dsub64 = d.kpix / d.kss;
   // binning-after-PSF operator: W_l(s') = sum_{s in bin l} P(s - s')
   {
     const int K = d.kpsf_k, h = (K - 1) / 2, nsx = sd.nsx, nsy = sd.nsy;
@@ -522,6 +527,7 @@ void ws_free(Workspace &w) {
   w.allocs.clear();
   w.d = WsDev{};
   w.B = 0;
+  w.prec = 0;
 }
 
 template <class T>
@@ -534,7 +540,8 @@ bool ws_alloc(Workspace &w, T *&p, size_t n) {
 }
 
 glad_status ws_ensure(glad_ctx *c, int B) {
-  if (c->ws.B >= B) return GLAD_OK;
+  if (c->ws.B >= B && c->ws.prec >= c->tune.prec) return GLAD_OK;
+  B = std::max(B, c->ws.B);
   cudaDeviceSynchronize();
   ws_free(c->ws);
   Workspace &w = c->ws;
@@ -549,11 +556,16 @@ glad_status ws_ensure(glad_ctx *c, int B) {
             ws_alloc(w, w.d.evals, 2) && ws_alloc(w, w.d.sph_mt, b * c->max_smg) &&
             ws_alloc(w, w.d.sph_mrz, b * c->max_smg) && ws_alloc(w, w.d.sph_tr, b * c->max_light) &&
             ws_alloc(w, w.d.sgrid, b * c->max_sgrid);
+  // the FP64 forward modes' arrays, only once such a mode has been asked for
+  if (ok && c->tune.prec > 0)
+    ok = ws_alloc(w, w.d.lp64, b) && ws_alloc(w, w.d.img64, b * c->max_pix) &&
+         ws_alloc(w, w.d.tab64, b * c->max_ent) && ws_alloc(w, w.d.I0d, b * c->max_light);
   if (!ok) {
     ws_free(w);
     return fail(GLAD_ENOMEM, "workspace for B=%d does not fit on the device", B);
   }
   w.B = B;
+  w.prec = c->tune.prec;
   return GLAD_OK;
 }
 
@@ -565,6 +577,7 @@ glad_status forward(glad_ctx *c, const int *sys_id, const double *theta, int B, 
   if (s != GLAD_OK) return s;
   cudaError_t e;
   c->ws.d.neg_mode = c->tune.neg_mode;
+  c->ws.d.prec = c->tune.prec;
   e = cudaMemsetAsync(c->ws.d.terms, 0, sizeof(double) * 4 * B, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->ws.d.evals, 0, 2 * sizeof(unsigned long long), st);
   if (e == cudaSuccess)
@@ -592,6 +605,7 @@ glad_status full_path(glad_ctx *c, const int *sys_id, const double *theta, int B
   if (s != GLAD_OK) return s;
   cudaError_t e;
   c->ws.d.neg_mode = c->tune.neg_mode;
+  c->ws.d.prec = grad ? 0 : c->tune.prec;  // the gradient runs in the default precision
   e = cudaMemsetAsync(c->ws.d.terms, 0, sizeof(double) * 4 * B, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->ws.d.evals, 0, 2 * sizeof(unsigned long long), st);
   if (e == cudaSuccess)
@@ -653,7 +667,9 @@ cudaError_t launch_dyn_tables(glad_ctx *c, const int *sys_id, int B, cudaStream_
 
 cudaError_t launch_dyn_sums(glad_ctx *c, const int *sys_id, int B, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
-  if (c->n_cyl) e = GLAD_PROF(c, st, KID_JAM, launch_jam(c, sys_id, B, st));
+  if (c->n_cyl)
+    e = GLAD_PROF(c, st, KID_JAM, c->ws.d.prec == 2 ? launch_jam64(c, sys_id, B, st)
+                                                     : launch_jam(c, sys_id, B, st));
   if (e == cudaSuccess && c->n_sph) e = GLAD_PROF(c, st, KID_SPH_LOS, launch_sph_los(c, sys_id, B, st));
   return e;
 }
@@ -692,6 +708,12 @@ cudaError_t prof_end(glad_ctx *c, cudaStream_t st, int id, cudaEvent_t a) {
 extern "C" {
 
 const char *glad_last_error(void) { return g_err.c_str(); }
+
+glad_status glad_set_precision(glad_ctx *c, int mode) {
+  if (!c || mode < 0 || mode > 2) return fail(GLAD_EINVAL, "glad_set_precision: mode %d", mode);
+  c->tune.prec = mode;
+  return GLAD_OK;
+}
 
 glad_status glad_set_negligible(glad_ctx *c, int mode) {
   if (!c || mode < 0 || mode > 2) return fail(GLAD_EINVAL, "glad_set_negligible: mode %d", mode);

@@ -38,6 +38,7 @@ struct SysDev {
   const float *psf_t;    // [psf_km * CONV_PT(psf_km)]: psf centred in psf_km^2 zeros,
                          // transposed (column c of the PSF is row c here), rows padded to 4
   float src_q, src_cphi, src_sphi;
+  double pix64, src_q64, src_cphi64, src_sphi64;  // the same in FP64 (FP64 lensing modes)
   int n_lcomp;           // lens-light components (1 + n_ll2)
   const double *lcomp;   // [n_lcomp*4]: I_e, R_e, n, q (row 0: I_e, R_e from theta)
   int n_sis;
@@ -46,6 +47,7 @@ struct SysDev {
   // kinematics: sub-sampled sky grid and the binning-after-PSF operator (CSR by sub-sample)
   int nsx, nsy, n_sub;
   float dsub;
+  double dsub64;         // the same in FP64 (the FP64 pair sum)
   const int *w_off;      // [n_sub+1]
   const int *w_bin;      // [nnz]
   const float *w_val;    // [nnz]
@@ -99,27 +101,29 @@ struct SysDev {
   const double *sph_u, *sph_wu;             // [n_mass_tot * n_gl]
 };
 
-// per-sample lensing parameters (FP32), written by the prep kernel
-struct LensP {
-  float xc, yc, cphi, sphi;
-  float q, t, pref, pad0;        // alpha' = pref * R^(1-t) * sum Omega_n
-  float g1, g2;                  // external shear
+// per-sample lensing parameters, written by the prep kernel: FP32 (LensP) for the default
+// precision and the gradient kernels, FP64 (LensPT<double>) for the FP64 lensing modes
+template <class T>
+struct LensPT {
+  T xc, yc, cphi, sphi;
+  T q, t, pref, pad0;        // alpha' = pref * R^(1-t) * sum Omega_n
+  T g1, g2;                  // external shear
   int nterms, valid;
-  float src_Ie, src_Rei, src_ninv, src_bn, src_x, src_y;
-  float ll_Ie[4], ll_Rei[4], ll_ninv[4], ll_bn[4], ll_qi2[4];
-  float rho[GLAD_MAX_TM];        // Omega_n = rho_n e^{2 i ph} Omega_{n-1}
+  T src_Ie, src_Rei, src_ninv, src_bn, src_x, src_y;
+  T ll_Ie[4], ll_Rei[4], ll_ninv[4], ll_bn[4], ll_qi2[4];
+  T rho[GLAD_MAX_TM];        // Omega_n = rho_n e^{2 i ph} Omega_{n-1}
   // derivatives used by the gradient kernels
-  float drho_t[GLAD_MAX_TM], drho_q[GLAD_MAX_TM];  // d rho_n / d t, d rho_n / d q
-  float pref_d[3];               // d pref / d (theta_E, t, q)
-  float gext, c2pe, s2pe;        // shear strength and cos/sin(2 phi_ext)
-  float src_bnp;                 // d b_n / d n of the source
+  T drho_t[GLAD_MAX_TM], drho_q[GLAD_MAX_TM];  // d rho_n / d t, d rho_n / d q
+  T pref_d[3];               // d pref / d (theta_E, t, q)
+  T gext, c2pe, s2pe;        // shear strength and cos/sin(2 phi_ext)
+  T src_bnp;                 // d b_n / d n of the source
   // internal mass sheet: the galaxy's deflection is scaled by lam and the sheet's added,
   // alpha_sheet = (1 - lam) u(R^2) (x - x_c, y - y_c) with u = 1 (ideal) or, for the dPIE,
   // u = 2 rc rt [1 + (rc + rt)/(Q_c + Q_t)] / ((rc + Q_c)(rt + Q_t)), Q = sqrt(R^2 + r^2)
   // (the difference of the two cored terms written without cancellation)
-  float lam;
+  T lam;
   int sheet;
-  float sh_rc2, sh_rt2, sh_rc, sh_rt;
+  T sh_rc2, sh_rt2, sh_rc, sh_rt;
   // composite class (mclass 1): Chameleon c of the lens light is li_A[c] [(m^2 + sc^2)^-1/2 -
   // (m^2 + st^2)^-1/2], m^2 = x'^2 + y'^2/q^2, li_A = I0/(1+q), s = 2w/(1+q); its baryonic
   // deflection is that of two softened isothermal ellipsoids of amplitude ch_A = Upsilon L_scale
@@ -129,11 +133,12 @@ struct LensP {
   // (for the gradient: ups = Upsilon L_scale, h_ks = kappa_s, h_rs = r_s, cse_a3 = a_i r_s^3,
   // bh_dM = d bh_M / d(theta 13, 14, 17, 18))
   int mclass;
-  float li_A[4], ch_A[4], ch_sc[4], ch_st[4], ch_q[4], ch_e[4];
-  float ups, h_ks, h_rs, h_q, h_e2;
-  float bh_M, bh_2s2, bh_dM[4];
-  float cse_amp[GLAD_N_CSE], cse_sc[GLAD_N_CSE], cse_a3[GLAD_N_CSE];
+  T li_A[4], ch_A[4], ch_sc[4], ch_st[4], ch_q[4], ch_e[4];
+  T ups, h_ks, h_rs, h_q, h_e2;
+  T bh_M, bh_2s2, bh_dM[4];
+  T cse_amp[GLAD_N_CSE], cse_sc[GLAD_N_CSE], cse_a3[GLAD_N_CSE];
 };
+typedef LensPT<float> LensP;
 
 // per-sample dynamics scalars (FP64)
 struct DynP {
@@ -170,10 +175,18 @@ struct WsDev {
   float2 *sgrid;               // [B*max_sgrid] (v_r^2, d) on the polar grid
   int neg_mode;                // negligible-term skipping in the forward JAM pass: 0 off,
                                // 1 on, 2 on with every tile's check failed (summed again)
+  // FP64 forward modes (glad_set_precision; null in the default precision): the FP64 lensing
+  // block, unblurred image, pair-form table (ax, ay, Q0, Q1) and projected tracer amplitudes
+  LensPT<double> *lp64;        // [B]
+  double *img64;               // [B*max_pix]
+  double4_16a *tab64;          // [B*max_ent]
+  double *I0d;                 // [B*max_light]
+  int prec;                    // 0 default, 1 FP64 lensing, 2 FP64 lensing and pair sum
 };
 
 struct Workspace {
   int B = 0;
+  int prec = 0;  // precision mode whose FP64 arrays are allocated (0: none)
   WsDev d{};
   std::vector<void *> allocs;
 };
@@ -194,6 +207,7 @@ struct glad_ctx {
   GradWs *gws = nullptr;
   // launch shapes chosen by glad_autotune (defaults until it runs)
   struct Tune {
+    int prec = 0;         // precision mode of the forward pass (glad_set_precision)
     int neg_mode = 1;     // negligible-term skipping of the forward JAM pass (see WsDev)
     int jam_pts = 8;      // sky points per thread in the JAM pair-sum kernels
     int jam_minb = 4;     // minimum resident CTAs per SM requested from the register allocator
@@ -247,6 +261,7 @@ cudaError_t launch_table(glad_ctx *c, const int *sys_id, int B, cudaStream_t st)
 cudaError_t launch_lens(glad_ctx *c, const int *sys_id, int B, float *image_out,
                         cudaStream_t st, float *resid_out = nullptr);
 cudaError_t launch_jam(glad_ctx *c, const int *sys_id, int B, cudaStream_t st);
+cudaError_t launch_jam64(glad_ctx *c, const int *sys_id, int B, cudaStream_t st);
 // gradient pieces (k_grad.cu): zeroing, lensing adjoint, dynamics adjoint + chain, final fix-up
 cudaError_t grad_prepare(glad_ctx *c, int B, double *grad, cudaStream_t st);
 cudaError_t launch_grad_lens(glad_ctx *c, const int *sys_id, int B, double *grad, cudaStream_t st);

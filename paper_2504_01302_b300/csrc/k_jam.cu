@@ -310,6 +310,52 @@ __global__ void __launch_bounds__(JAM_THREADS, MINB) k_jam_persist(
   }
 }
 
+// The pair sum in FP64 (precision mode 2, glad_set_precision): one thread per sky sub-sample,
+// every table entry (no skipping), the FP64 table staged through shared memory in chunks, exp()
+// in FP64; then the tracer surface brightness and the binning-after-PSF scatter in FP64.
+__global__ void __launch_bounds__(256) k_jam64(const SysDev *__restrict__ sysv,
+                                               const int *__restrict__ sys_id, WsDev ws,
+                                               int max_light, int max_ent, int max_bins) {
+  const int b = blockIdx.y;
+  if (ws.status[b] != GLAD_SAMPLE_OK) return;
+  const SysDev &S = sysv[sys_id[b]];
+  if (S.jam_align != 0) return;
+  const int s = blockIdx.x * 256 + threadIdx.x;
+  if ((int)blockIdx.x * 256 >= S.n_sub) return;
+  const DynP dp = ws.dp[b];
+  const int I = s / S.nsx, J = s - I * S.nsx;
+  const double x = (J - 0.5 * (S.nsx - 1)) * S.dsub64 - dp.xc;
+  const double y = (I - 0.5 * (S.nsy - 1)) * S.dsub64 - dp.yc;
+  const double xp = dp.cphi * x + dp.sphi * y, yp = -dp.sphi * x + dp.cphi * y;
+  const double X = xp * xp, Y = yp * yp;
+  __shared__ double4_16a ch[256];
+  const double4_16a *tab = ws.tab64 + (size_t)b * max_ent;
+  double v = 0.0;
+  for (int e0 = 0; e0 < S.n_ent; e0 += 256) {
+    __syncthreads();
+    if (e0 + threadIdx.x < S.n_ent) ch[threadIdx.x] = tab[e0 + threadIdx.x];
+    __syncthreads();
+    const int ne = min(256, S.n_ent - e0);
+    for (int k = 0; k < ne; ++k) {
+      const double4_16a t = ch[k];
+      v += (t.z + t.w * X) * exp(t.x * X + t.y * Y);
+    }
+  }
+  if (s >= S.n_sub) return;
+  double sb = 0.0;
+  for (int k = 0; k < S.n_light; ++k) {
+    const double sg = S.sig_light[k], q = S.qp_light[k];
+    sb += ws.I0d[(size_t)b * max_light + k] * exp(-(X + Y / (q * q)) / (2.0 * sg * sg));
+  }
+  double *acc_g = ws.binacc + (size_t)b * max_bins * 2;
+  for (int e = S.w_off[s]; e < S.w_off[s + 1]; ++e) {
+    const int l = S.w_bin[e];
+    const double w = S.w_val[e];
+    atomicAdd(&acc_g[2 * l], w * v);
+    atomicAdd(&acc_g[2 * l + 1], w * sb);
+  }
+}
+
 __global__ void k_kin_finalize(const SysDev *__restrict__ sysv, const int *__restrict__ sys_id,
                                WsDev ws, int max_bins, float *vrms_out) {
   const int b = blockIdx.x;
@@ -415,6 +461,14 @@ cudaError_t launch_jam(glad_ctx *c, const int *sys_id, int B, cudaStream_t st) {
                                                  c->max_ent, c->max_bins);
   GLAD_JAM_SHAPES(GLAD_JAM_LAUNCH)
 #undef GLAD_JAM_LAUNCH
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jam64(glad_ctx *c, const int *sys_id, int B, cudaStream_t st) {
+  int blocks = 0;
+  for (auto &sd : c->h_sysdev) blocks = std::max(blocks, (sd.n_sub + 255) / 256);
+  k_jam64<<<dim3(blocks, B), 256, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_light, c->max_ent,
+                                            c->max_bins);
   return cudaGetLastError();
 }
 

@@ -13,10 +13,33 @@
 
 namespace {
 
-__device__ __forceinline__ float sersic_f(float R2_scaled, float Ie, float ninv, float bn) {
+// system geometry in the ray shooting's float type: pixel scale, source axis ratio and angle
+struct SrcGeom {
+  float pix, q, c, s;
+};
+struct SrcGeom64 {
+  double pix, q, c, s;
+};
+__device__ __forceinline__ SrcGeom geom_of(const SysDev &S, float) {
+  return {S.pix, S.src_q, S.src_cphi, S.src_sphi};
+}
+__device__ __forceinline__ SrcGeom64 geom_of(const SysDev &S, double) {
+  return {S.pix64, S.src_q64, S.src_cphi64, S.src_sphi64};
+}
+
+// float / double versions of the few functions the ray shooting uses
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+__device__ __forceinline__ const LensPT<float> *lp_of(const WsDev &w, float) { return w.lp; }
+__device__ __forceinline__ const LensPT<double> *lp_of(const WsDev &w, double) { return w.lp64; }
+__device__ __forceinline__ float *img_of(const WsDev &w, float) { return w.img; }
+__device__ __forceinline__ double *img_of(const WsDev &w, double) { return w.img64; }
+
+template <class T>
+__device__ __forceinline__ T sersic_f(T R2_scaled, T Ie, T ninv, T bn) {
   // Ie * exp(-bn * (R^(1/n) - 1)) with R2_scaled = (R/Re)^2
-  const float w = exp2f(0.5f * ninv * log2f(R2_scaled));
-  return Ie * expf(-bn * (w - 1.0f));
+  const T w = exp2(T(0.5) * ninv * log2(R2_scaled));
+  return Ie * exp(-bn * (w - T(1)));
 }
 
 // Composite galaxy (Sect. 3.3) at frame position (xp, yp): adds to the frame deflection.
@@ -25,22 +48,23 @@ __device__ __forceinline__ float sersic_f(float R2_scaled, float Ie, float ninv,
 // its round limit 2 A (x, y)/(sqrt(R^2 + s^2) + s) for e < 1e-3; halo CSE i (amplitude amp, core s):
 //   alpha = 2 q amp (x (psi + q^2 s), y (psi + s)) / (s psi D), D = (psi + s)^2 + (1 - q^2) x^2
 // (the y denominator q^2 D written without the cancelling form).
-__device__ __forceinline__ void composite_frame(const LensP &L, int n_lcomp, float xp, float yp,
-                                                float &ax, float &ay) {
+template <class T>
+__device__ __forceinline__ void composite_frame(const LensPT<T> &L, int n_lcomp, T xp, T yp, T &ax,
+                                                T &ay) {
   for (int c = 0; c < n_lcomp && c < 4; ++c) {
-    const float q = L.ch_q[c], e = L.ch_e[c], A = L.ch_A[c];
-    float sx = 0.0f, sy = 0.0f;
+    const T q = L.ch_q[c], e = L.ch_e[c], A = L.ch_A[c];
+    T sx = T(0.0), sy = T(0.0);
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
-      const float s = t == 0 ? L.ch_sc[c] : L.ch_st[c];
-      const float sg = t == 0 ? 1.0f : -1.0f;
+      const T s = t == 0 ? L.ch_sc[c] : L.ch_st[c];
+      const T sg = t == 0 ? T(1.0) : -T(1.0);
       if (e > 1e-3f) {
-        const float ps = sqrtf(q * q * (s * s + xp * xp) + yp * yp);
-        const float b = 2.0f * q * A / e;
-        sx += sg * b * atanf(e * xp / (ps + s));
-        sy += sg * b * atanhf(e * yp / (ps + q * q * s));
+        const T ps = sqrt(q * q * (s * s + xp * xp) + yp * yp);
+        const T b = T(2.0) * q * A / e;
+        sx += sg * b * atan(e * xp / (ps + s));
+        sy += sg * b * atanh(e * yp / (ps + q * q * s));
       } else {
-        const float fac = 2.0f * A / (sqrtf(xp * xp + yp * yp + s * s) + s);
+        const T fac = T(2.0) * A / (sqrt(xp * xp + yp * yp + s * s) + s);
         sx += sg * fac * xp;
         sy += sg * fac * yp;
       }
@@ -48,28 +72,30 @@ __device__ __forceinline__ void composite_frame(const LensP &L, int n_lcomp, flo
     ax += sx;
     ay += sy;
   }
-  const float q = L.h_q, q2 = q * q;
-  const float base = q2 * xp * xp + yp * yp, ex2 = L.h_e2 * xp * xp;
-  float hx = 0.0f, hy = 0.0f;
+  const T q = L.h_q, q2 = q * q;
+  const T base = q2 * xp * xp + yp * yp, ex2 = L.h_e2 * xp * xp;
+  T hx = T(0.0), hy = T(0.0);
   for (int i = 0; i < GLAD_N_CSE; ++i) {
-    const float s = L.cse_sc[i], amp = L.cse_amp[i];
-    const float ps = sqrtf(base + q2 * s * s);
-    const float D = (ps + s) * (ps + s) + ex2;
-    const float w = amp / (s * ps * D);
+    const T s = L.cse_sc[i], amp = L.cse_amp[i];
+    const T ps = sqrt(base + q2 * s * s);
+    const T D = (ps + s) * (ps + s) + ex2;
+    const T w = amp / (s * ps * D);
     hx += w * (ps + q2 * s);
     hy += w * (ps + s);
   }
-  ax += 2.0f * q * xp * hx;
-  ay += 2.0f * q * yp * hy;
+  ax += T(2.0) * q * xp * hx;
+  ay += T(2.0) * q * yp * hy;
 }
 
 // Round Gaussian black hole of mass M: alpha = M (1 - e^-t)/(pi R^2) (dx, dy), t = R^2/(2 sigma^2)
-__device__ __forceinline__ float bh_gauss_factor(float M, float s2x2, float dx, float dy) {
-  const float t = (dx * dx + dy * dy) / s2x2;
-  const float h1 = t < 1e-3f ? 1.0f - 0.5f * t : -expm1f(-t) / t;
-  return M * h1 / (3.14159265358979f * s2x2);
+template <class T>
+__device__ __forceinline__ T bh_gauss_factor(T M, T s2x2, T dx, T dy) {
+  const T t = (dx * dx + dy * dy) / s2x2;
+  const T h1 = t < 1e-3f ? T(1.0) - T(0.5) * t : -expm1(-t) / t;
+  return M * h1 / (T(3.14159265358979) * s2x2);
 }
 
+template <class T>
 __global__ void __launch_bounds__(LENS_THREADS) k_image(const SysDev *__restrict__ sysv,
                                                         const int *__restrict__ sys_id, WsDev ws,
                                                         int max_pix) {
@@ -77,104 +103,106 @@ __global__ void __launch_bounds__(LENS_THREADS) k_image(const SysDev *__restrict
   if (ws.status[b] != GLAD_SAMPLE_OK) return;
   const SysDev &S = sysv[sys_id[b]];
   const int p = blockIdx.x * LENS_THREADS + threadIdx.x;
-  __shared__ LensP L;
+  __shared__ LensPT<T> L;
   {
-    const int *src = reinterpret_cast<const int *>(&ws.lp[b]);
+    const int *src = reinterpret_cast<const int *>(&lp_of(ws, T(0))[b]);
     int *dst = reinterpret_cast<int *>(&L);
-    for (int i = threadIdx.x; i < (int)(sizeof(LensP) / 4); i += blockDim.x) dst[i] = src[i];
+    for (int i = threadIdx.x; i < (int)(sizeof(LensPT<T>) / 4); i += blockDim.x) dst[i] = src[i];
   }
   __syncthreads();
   if (p >= S.npix) return;
   const int i = p / S.nx, j = p - i * S.nx;
   const int ss = S.ss;
-  const float pix = S.pix;
-  const float x0 = (j - 0.5f * (S.nx - 1)) * pix;
-  const float y0 = (i - 0.5f * (S.ny - 1)) * pix;
-  const float q = L.q, omt = 1.0f - L.t;
-  float acc = 0.0f;
+  const auto G = geom_of(S, T(0));
+  const T pix = G.pix;
+  const T x0 = (j - T(0.5) * (S.nx - 1)) * pix;
+  const T y0 = (i - T(0.5) * (S.ny - 1)) * pix;
+  const T q = L.q, omt = T(1.0) - L.t;
+  T acc = T(0.0);
   for (int my = 0; my < ss; ++my) {
-    const float y = y0 + ((my + 0.5f) / ss - 0.5f) * pix;
+    const T y = y0 + ((my + T(0.5)) / ss - T(0.5)) * pix;
     for (int mx = 0; mx < ss; ++mx) {
-      const float x = x0 + ((mx + 0.5f) / ss - 0.5f) * pix;
-      const float dx = x - L.xc, dy = y - L.yc;
-      const float xp = L.cphi * dx + L.sphi * dy, yp = -L.sphi * dx + L.cphi * dy;
-      float apx = 0.0f, apy = 0.0f;
+      const T x = x0 + ((mx + T(0.5)) / ss - T(0.5)) * pix;
+      const T dx = x - L.xc, dy = y - L.yc;
+      const T xp = L.cphi * dx + L.sphi * dy, yp = -L.sphi * dx + L.cphi * dy;
+      T apx = T(0.0), apy = T(0.0);
       if (L.mclass == 1) {
         composite_frame(L, S.n_lcomp, xp, yp, apx, apy);
       } else {
         // EPL (Tessore & Metcalf series)
         // at the exact centre alpha is taken as 0 (its direction is undefined there)
-        const float R = sqrtf(q * q * xp * xp + yp * yp);
-        const float iR = R > 0.0f ? 1.0f / R : 0.0f;
-        const float wr = q * xp * iR, wi = yp * iR;
-        const float w2r = wr * wr - wi * wi, w2i = 2.0f * wr * wi;
-        float omr = wr, omi = wi, Sr = wr, Si = wi;
+        const T R = sqrt(q * q * xp * xp + yp * yp);
+        const T iR = R > T(0.0) ? T(1.0) / R : T(0.0);
+        const T wr = q * xp * iR, wi = yp * iR;
+        const T w2r = wr * wr - wi * wi, w2i = T(2.0) * wr * wi;
+        T omr = wr, omi = wi, Sr = wr, Si = wi;
         for (int n = 0; n < L.nterms; ++n) {
-          const float rr = L.rho[n];
-          const float nr = rr * (w2r * omr - w2i * omi);
-          const float ni = rr * (w2r * omi + w2i * omr);
+          const T rr = L.rho[n];
+          const T nr = rr * (w2r * omr - w2i * omi);
+          const T ni = rr * (w2r * omi + w2i * omr);
           omr = nr;
           omi = ni;
           Sr += omr;
           Si += omi;
         }
-        const float amp = R > 0.0f ? L.pref * exp2f(omt * log2f(R)) : 0.0f;
+        const T amp = R > T(0.0) ? L.pref * exp2(omt * log2(R)) : T(0.0);
         apx = amp * Sr;
         apy = amp * Si;
       }
-      float ax = L.cphi * apx - L.sphi * apy;
-      float ay = L.sphi * apx + L.cphi * apy;
-      if (L.mclass == 1 && L.bh_M > 0.0f) {
-        const float g = bh_gauss_factor(L.bh_M, L.bh_2s2, dx, dy);
+      T ax = L.cphi * apx - L.sphi * apy;
+      T ay = L.sphi * apx + L.cphi * apy;
+      if (L.mclass == 1 && L.bh_M > T(0.0)) {
+        const T g = bh_gauss_factor(L.bh_M, L.bh_2s2, dx, dy);
         ax += g * dx;
         ay += g * dy;
       }
       ax += L.g1 * dx + L.g2 * dy;
       ay += L.g2 * dx - L.g1 * dy;
       for (int k = 0; k < S.n_sis; ++k) {
-        const float te = (float)S.sis[3 * k];
-        const float sx = x - (float)S.sis[3 * k + 1], sy = y - (float)S.sis[3 * k + 2];
-        const float r2 = sx * sx + sy * sy;
-        const float ir = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+        const T te = (T)S.sis[3 * k];
+        const T sx = x - (T)S.sis[3 * k + 1], sy = y - (T)S.sis[3 * k + 2];
+        const T r2 = sx * sx + sy * sy;
+        const T ir = r2 > T(0.0) ? rsq(r2) : T(0.0);
         ax += te * sx * ir;
         ay += te * sy * ir;
       }
       if (L.sheet) {
         // internal mass sheet: lambda x galaxy + (1 - lambda) u(R^2) (x - x_c, y - y_c)
-        float u = 1.0f;
+        T u = T(1.0);
         if (L.sheet == 1) {
-          const float R2 = dx * dx + dy * dy;
-          const float Qc = sqrtf(R2 + L.sh_rc2), Qt = sqrtf(R2 + L.sh_rt2);
-          u = 2.0f * L.sh_rc * L.sh_rt * (1.0f + (L.sh_rc + L.sh_rt) / (Qc + Qt)) /
+          const T R2 = dx * dx + dy * dy;
+          const T Qc = sqrt(R2 + L.sh_rc2), Qt = sqrt(R2 + L.sh_rt2);
+          u = T(2.0) * L.sh_rc * L.sh_rt * (T(1.0) + (L.sh_rc + L.sh_rt) / (Qc + Qt)) /
               ((L.sh_rc + Qc) * (L.sh_rt + Qt));
         }
-        const float om = (1.0f - L.lam) * u;
+        const T om = (T(1.0) - L.lam) * u;
         ax = L.lam * ax + om * dx;
         ay = L.lam * ay + om * dy;
       }
       // source at beta
-      const float bx = x - ax - L.src_x, by = y - ay - L.src_y;
-      const float xs = S.src_cphi * bx + S.src_sphi * by, ys = -S.src_sphi * bx + S.src_cphi * by;
-      const float Rs2 = (xs * xs + ys * ys / (S.src_q * S.src_q)) * (L.src_Rei * L.src_Rei);
-      float v = sersic_f(Rs2, L.src_Ie, L.src_ninv, L.src_bn);
+      const T bx = x - ax - L.src_x, by = y - ay - L.src_y;
+      const T xs = G.c * bx + G.s * by, ys = -G.s * bx + G.c * by;
+      const T Rs2 = (xs * xs + ys * ys / (G.q * G.q)) * (L.src_Rei * L.src_Rei);
+      T v = sersic_f(Rs2, L.src_Ie, L.src_ninv, L.src_bn);
       // lens light (same centre and PA as the mass): Sersic, or Chameleon in the composite class
       if (L.mclass == 1) {
         for (int c = 0; c < S.n_lcomp && c < 4; ++c) {
-          const float m2 = xp * xp + yp * yp / (L.ch_q[c] * L.ch_q[c]);
-          v += L.li_A[c] * (rsqrtf(m2 + L.ch_sc[c] * L.ch_sc[c]) - rsqrtf(m2 + L.ch_st[c] * L.ch_st[c]));
+          const T m2 = xp * xp + yp * yp / (L.ch_q[c] * L.ch_q[c]);
+          v += L.li_A[c] * (rsq(m2 + L.ch_sc[c] * L.ch_sc[c]) - rsq(m2 + L.ch_st[c] * L.ch_st[c]));
         }
       } else {
         for (int c = 0; c < S.n_lcomp; ++c) {
-          const float R2 = (xp * xp + yp * yp * L.ll_qi2[c]) * (L.ll_Rei[c] * L.ll_Rei[c]);
+          const T R2 = (xp * xp + yp * yp * L.ll_qi2[c]) * (L.ll_Rei[c] * L.ll_Rei[c]);
           v += sersic_f(R2, L.ll_Ie[c], L.ll_ninv[c], L.ll_bn[c]);
         }
       }
       acc += v;
     }
   }
-  ws.img[(size_t)b * max_pix + p] = acc / (float)(ss * ss);
+  img_of(ws, T(0))[(size_t)b * max_pix + p] = acc / (T)(ss * ss);
 }
 
+template <class T>
 __global__ void __launch_bounds__(CONV_TX *CONV_TY) k_conv(const SysDev *__restrict__ sysv,
                                                            const int *__restrict__ sys_id, WsDev ws,
                                                            int max_pix, float *image_out,
@@ -182,25 +210,25 @@ __global__ void __launch_bounds__(CONV_TX *CONV_TY) k_conv(const SysDev *__restr
   const int b = blockIdx.y;
   if (ws.status[b] != GLAD_SAMPLE_OK) return;
   const SysDev &S = sysv[sys_id[b]];
-  if (S.psf_km != 0) return;  // blurred by k_conv_r
+  if (S.psf_km != 0 && sizeof(T) == 4) return;  // blurred by k_conv_r (FP32)
   const int ntx = (S.nx + CONV_TX - 1) / CONV_TX;
   const int nty = (S.ny + CONV_TY - 1) / CONV_TY;
   if ((int)blockIdx.x >= ntx * nty) return;
   const int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;
   const int K = S.psf_k, h = (K - 1) / 2;
   const int W = CONV_TX + 2 * h, H = CONV_TY + 2 * h;
-  extern __shared__ float sm[];
-  float *tile = sm;            // [H*W]
-  float *psf = sm + H * W;     // [K*K]
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *tile = reinterpret_cast<T *>(smraw);  // [H*W]
+  T *psf = tile + H * W;                   // [K*K]
   const int tid = threadIdx.y * CONV_TX + threadIdx.x;
   const int i0 = ty * CONV_TY - h, j0 = tx * CONV_TX - h;
-  const float *img = ws.img + (size_t)b * max_pix;
+  const T *img = img_of(ws, T(0)) + (size_t)b * max_pix;
   for (int e = tid; e < H * W; e += CONV_TX * CONV_TY) {
     const int li = e / W, lj = e - li * W;
     const int gi = i0 + li, gj = j0 + lj;
-    tile[e] = (gi >= 0 && gi < S.ny && gj >= 0 && gj < S.nx) ? img[gi * S.nx + gj] : 0.0f;
+    tile[e] = (gi >= 0 && gi < S.ny && gj >= 0 && gj < S.nx) ? img[gi * S.nx + gj] : T(0);
   }
-  for (int e = tid; e < K * K; e += CONV_TX * CONV_TY) psf[e] = S.psf[e];
+  for (int e = tid; e < K * K; e += CONV_TX * CONV_TY) psf[e] = (T)S.psf[e];
   __syncthreads();
   const int oi = ty * CONV_TY + threadIdx.y, oj = tx * CONV_TX + threadIdx.x;
   double chi = 0.0;
@@ -208,10 +236,10 @@ __global__ void __launch_bounds__(CONV_TX *CONV_TY) k_conv(const SysDev *__restr
     // m[i,j] = sum_{a,c} P[a,c] img[i-(a-h), j-(c-h)]; tile row of image row r is r - i0
     double m = 0.0;
     for (int a = 0; a < K; ++a) {
-      const float *trow = tile + (threadIdx.y + 2 * h - a) * W + threadIdx.x + 2 * h;
-      const float *prow = psf + a * K;
-      float rs = 0.0f;
-      for (int c = 0; c < K; ++c) rs = fmaf(prow[c], trow[-c], rs);
+      const T *trow = tile + (threadIdx.y + 2 * h - a) * W + threadIdx.x + 2 * h;
+      const T *prow = psf + a * K;
+      T rs = T(0);
+      for (int c = 0; c < K; ++c) rs = fma(prow[c], trow[-c], rs);
       m += (double)rs;
     }
     const int o = oi * S.nx + oj;
@@ -337,7 +365,22 @@ __global__ void __launch_bounds__(CONV_TX *CONV_TY) k_conv_r(const SysDev *__res
 cudaError_t launch_lens(glad_ctx *c, const int *sys_id, int B, float *image_out, cudaStream_t st,
                         float *resid_out) {
   dim3 g1(c->max_img_tiles, B);
-  k_image<<<g1, LENS_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_pix);
+  const dim3 blk(CONV_TX, CONV_TY);
+  if (c->ws.d.prec > 0 && !resid_out) {
+    // FP64 lensing modes: ray shooting, light and PSF blurring in FP64 (general convolution)
+    k_image<double><<<g1, LENS_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_pix);
+    int tiles = 0, kmax = 1;
+    for (auto &sd : c->h_sysdev) {
+      tiles = std::max(tiles, ((sd.nx + CONV_TX - 1) / CONV_TX) * ((sd.ny + CONV_TY - 1) / CONV_TY));
+      kmax = std::max(kmax, sd.psf_k);
+    }
+    const int h = (kmax - 1) / 2;
+    const size_t smem = sizeof(double) * ((CONV_TX + 2 * h) * (CONV_TY + 2 * h) + kmax * kmax);
+    k_conv<double><<<dim3(tiles, B), blk, smem, st>>>(c->d_sys, sys_id, c->ws.d, c->max_pix, image_out,
+                                                      nullptr);
+    return cudaGetLastError();
+  }
+  k_image<float><<<g1, LENS_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_pix);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // one blocked launch per padded PSF side present (samples of other systems exit at
@@ -354,7 +397,6 @@ cudaError_t launch_lens(glad_ctx *c, const int *sys_id, int B, float *image_out,
       max_k = std::max(max_k, sd.psf_k);
     }
   }
-  const dim3 blk(CONV_TX, CONV_TY);
   if (tiles_r[0])
     k_conv_r<11><<<dim3(tiles_r[0], B), blk, 0, st>>>(c->d_sys, sys_id, c->ws.d, c->max_pix,
                                                       image_out, resid_out);
@@ -367,7 +409,7 @@ cudaError_t launch_lens(glad_ctx *c, const int *sys_id, int B, float *image_out,
   if (max_conv_tiles) {
     const int h = (max_k - 1) / 2;
     const size_t smem = sizeof(float) * ((CONV_TX + 2 * h) * (CONV_TY + 2 * h) + max_k * max_k);
-    k_conv<<<dim3(max_conv_tiles, B), blk, smem, st>>>(c->d_sys, sys_id, c->ws.d, c->max_pix,
+    k_conv<float><<<dim3(max_conv_tiles, B), blk, smem, st>>>(c->d_sys, sys_id, c->ws.d, c->max_pix,
                                                        image_out, resid_out);
   }
   return cudaGetLastError();
@@ -376,5 +418,6 @@ cudaError_t launch_lens(glad_ctx *c, const int *sys_id, int B, float *image_out,
 void set_conv_smem_limit() {
   const int h = (GLAD_MAX_PSF - 1) / 2;
   const int smem = sizeof(float) * ((CONV_TX + 2 * h) * (CONV_TY + 2 * h) + GLAD_MAX_PSF * GLAD_MAX_PSF);
-  cudaFuncSetAttribute(k_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_conv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_conv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * smem);
 }

@@ -11,6 +11,8 @@
 //    with the magnification-weighted source estimate of Sect. 3.1.1, and the
 //    image-position term (Eq. chi2_img) for systems that give image-position errors.
 // A second kernel expands the (tracer k, mass j, node g) JAM coefficient table.
+#include <type_traits>
+
 #include "cplx.cuh"
 #include "glad_internal.cuh"
 #include "lensmath.cuh"
@@ -214,6 +216,7 @@ __global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
       ws.nu0[bl + k] = sh_rho[k];
       ws.c0[bl + k] = 1.0 / (2.0 * sg * sg * qi * qi);
       ws.I0f[bl + k] = (float)sh_A[k];
+      if (ws.prec == 2) ws.I0d[bl + k] = sh_A[k];
     } else {
       const int j = k - nL;
       ws.Cj[bm + j] = 2.0 * SQRT2PI_D * v2u * qp * sh_A[k] * sg;
@@ -261,13 +264,18 @@ __global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
   int nt = 0;
   if (fq > 0.0 && !comp) nt = (int)ceil(log(1e-9) / log(fq));
   if (nt > GLAD_MAX_TM) nt = GLAD_MAX_TM;
-  LensP &L = ws.lp[b];
-  for (int n = 1 + tid; n <= nt; n += blockDim.x) {
-    const double num = 2.0 * n - (2.0 - tq), den = 2.0 * n + (2.0 - tq);
-    L.rho[n - 1] = (float)(-fq * num / den);
-    L.drho_t[n - 1] = (float)(-fq * 4.0 * n / (den * den));
-    L.drho_q[n - 1] = (float)(2.0 * num / (den * (1.0 + q) * (1.0 + q)));
-  }
+  // the lensing block in FP32 and, for the FP64 lensing modes, in FP64 (same values)
+  auto fill_rho = [&](auto &L) {
+    using T = std::remove_reference_t<decltype(L.q)>;
+    for (int n = 1 + tid; n <= nt; n += blockDim.x) {
+      const double num = 2.0 * n - (2.0 - tq), den = 2.0 * n + (2.0 - tq);
+      L.rho[n - 1] = (T)(-fq * num / den);
+      L.drho_t[n - 1] = (T)(-fq * 4.0 * n / (den * den));
+      L.drho_q[n - 1] = (T)(2.0 * num / (den * (1.0 + q) * (1.0 + q)));
+    }
+  };
+  fill_rho(ws.lp[b]);
+  if (ws.prec > 0) fill_rho(ws.lp64[b]);
   __syncthreads();
   if (tid == 0) {
     ws.status[b] = GLAD_SAMPLE_OK;
@@ -280,87 +288,92 @@ __global__ void __launch_bounds__(128) k_prep(const SysDev *__restrict__ sysv,
     dp.yc = th[5];
     sincos(th[3], &dp.sphi, &dp.cphi);
     ws.dp[b] = dp;
-    // ---- FP32 lensing block
-    const double bb = pow(2.0 / (1.0 + q), 1.0 / tq) * tE;
-    const double bt = q * bb;
-    L.xc = (float)th[4];
-    L.yc = (float)th[5];
-    L.cphi = (float)dp.cphi;
-    L.sphi = (float)dp.sphi;
-    L.q = (float)q;
-    L.t = (float)tq;
-    // ln pref = ln 2 + t ln b_TM - ln(1+q), b_TM = q (2/(1+q))^(1/t) theta_E
-    const double pref = 2.0 * bt / (1.0 + q) * pow(bt, tq - 1.0);
-    L.pref = (float)pref;
-    L.nterms = nt;
-    L.pref_d[0] = (float)(pref * tq / tE);
-    L.pref_d[1] = (float)(pref * (log(bt) - log(2.0 / (1.0 + q)) / tq));
-    L.pref_d[2] = (float)(pref * (tq / q - 2.0 / (1.0 + q)));
-    double s2p, c2p;
-    sincos(2.0 * th[7], &s2p, &c2p);
-    L.g1 = (float)(th[6] * c2p);
-    L.g2 = (float)(th[6] * s2p);
-    L.gext = (float)th[6];
-    L.c2pe = (float)c2p;
-    L.s2pe = (float)s2p;
-    {
-      const double n = th[10];
-      L.src_bnp = (float)(2.0 - 4.0 / (405.0 * n * n) - 92.0 / (25515.0 * n * n * n) -
-                          393.0 / (1148175.0 * n * n * n * n) +
-                          4.0 * 2194697.0 / (30690717750.0 * n * n * n * n * n));
-    }
-    L.src_Ie = (float)th[8];
-    L.src_Rei = (float)(1.0 / th[9]);
-    L.src_ninv = (float)(1.0 / th[10]);
-    L.src_bn = (float)sersic_bn_d(th[10]);
-    L.src_x = (float)th[11];
-    L.src_y = (float)th[12];
-    L.sheet = S.sheet;
-    L.lam = (float)lam;
-    L.sh_rc = (float)S.sh_rc;
-    L.sh_rt = (float)S.sh_rt;
-    L.sh_rc2 = (float)(S.sh_rc * S.sh_rc);
-    L.sh_rt2 = (float)(S.sh_rt * S.sh_rt);
-    L.mclass = S.mass_class;
-    if (comp) {
-      const double ups = th[17] * S.L_scale;
-      for (int c = 0; c < S.n_lcomp && c < 4; ++c) {
-        const double qc = S.lcomp[4 * c + 3];
-        const double I0 = c == 0 ? th[13] : S.lcomp[4 * c];
-        const double wt = c == 0 ? th[14] : S.lcomp[4 * c + 2];
-        L.li_A[c] = (float)(I0 / (1.0 + qc));
-        L.ch_A[c] = (float)(ups * I0 / (1.0 + qc));
-        L.ch_sc[c] = (float)(2.0 * S.lcomp[4 * c + 1] / (1.0 + qc));
-        L.ch_st[c] = (float)(2.0 * wt / (1.0 + qc));
-        L.ch_q[c] = (float)qc;
-        L.ch_e[c] = (float)sqrt(1.0 - qc * qc);
+    // ---- lensing block (FP32; FP64 too for the FP64 lensing modes)
+    auto fill = [&](auto &L) {
+      using T = std::remove_reference_t<decltype(L.q)>;
+      const double bb = pow(2.0 / (1.0 + q), 1.0 / tq) * tE;
+      const double bt = q * bb;
+      L.xc = (T)th[4];
+      L.yc = (T)th[5];
+      L.cphi = (T)dp.cphi;
+      L.sphi = (T)dp.sphi;
+      L.q = (T)q;
+      L.t = (T)tq;
+      // ln pref = ln 2 + t ln b_TM - ln(1+q), b_TM = q (2/(1+q))^(1/t) theta_E
+      const double pref = 2.0 * bt / (1.0 + q) * pow(bt, tq - 1.0);
+      L.pref = (T)pref;
+      L.nterms = nt;
+      L.pref_d[0] = (T)(pref * tq / tE);
+      L.pref_d[1] = (T)(pref * (log(bt) - log(2.0 / (1.0 + q)) / tq));
+      L.pref_d[2] = (T)(pref * (tq / q - 2.0 / (1.0 + q)));
+      double s2p, c2p;
+      sincos(2.0 * th[7], &s2p, &c2p);
+      L.g1 = (T)(th[6] * c2p);
+      L.g2 = (T)(th[6] * s2p);
+      L.gext = (T)th[6];
+      L.c2pe = (T)c2p;
+      L.s2pe = (T)s2p;
+      {
+        const double n = th[10];
+        L.src_bnp = (T)(2.0 - 4.0 / (405.0 * n * n) - 92.0 / (25515.0 * n * n * n) -
+                            393.0 / (1148175.0 * n * n * n * n) +
+                            4.0 * 2194697.0 / (30690717750.0 * n * n * n * n * n));
       }
-      L.ups = (float)ups;
-      L.h_ks = (float)th[0];
-      L.h_rs = (float)th[1];
-      L.h_q = (float)q;
-      L.h_e2 = (float)(1.0 - q * q);
-      L.bh_M = (float)sh_mbh;
-      L.bh_2s2 = (float)(2.0 * S.bh_sigma * S.bh_sigma);
-      for (int i = 0; i < 4; ++i) L.bh_dM[i] = (float)sh_dm[i];
-      const double rs3 = th[1] * th[1] * th[1];
-      for (int i = 0; i < GLAD_N_CSE; ++i) {
-        L.cse_amp[i] = (float)(th[0] * S.cse_a[i] * rs3);
-        L.cse_sc[i] = (float)(S.cse_s[i] * th[1]);
-        L.cse_a3[i] = (float)(S.cse_a[i] * rs3);
+      L.src_Ie = (T)th[8];
+      L.src_Rei = (T)(1.0 / th[9]);
+      L.src_ninv = (T)(1.0 / th[10]);
+      L.src_bn = (T)sersic_bn_d(th[10]);
+      L.src_x = (T)th[11];
+      L.src_y = (T)th[12];
+      L.sheet = S.sheet;
+      L.lam = (T)lam;
+      L.sh_rc = (T)S.sh_rc;
+      L.sh_rt = (T)S.sh_rt;
+      L.sh_rc2 = (T)(S.sh_rc * S.sh_rc);
+      L.sh_rt2 = (T)(S.sh_rt * S.sh_rt);
+      L.mclass = S.mass_class;
+      if (comp) {
+        const double ups = th[17] * S.L_scale;
+        for (int c = 0; c < S.n_lcomp && c < 4; ++c) {
+          const double qc = S.lcomp[4 * c + 3];
+          const double I0 = c == 0 ? th[13] : S.lcomp[4 * c];
+          const double wt = c == 0 ? th[14] : S.lcomp[4 * c + 2];
+          L.li_A[c] = (T)(I0 / (1.0 + qc));
+          L.ch_A[c] = (T)(ups * I0 / (1.0 + qc));
+          L.ch_sc[c] = (T)(2.0 * S.lcomp[4 * c + 1] / (1.0 + qc));
+          L.ch_st[c] = (T)(2.0 * wt / (1.0 + qc));
+          L.ch_q[c] = (T)qc;
+          L.ch_e[c] = (T)sqrt(1.0 - qc * qc);
+        }
+        L.ups = (T)ups;
+        L.h_ks = (T)th[0];
+        L.h_rs = (T)th[1];
+        L.h_q = (T)q;
+        L.h_e2 = (T)(1.0 - q * q);
+        L.bh_M = (T)sh_mbh;
+        L.bh_2s2 = (T)(2.0 * S.bh_sigma * S.bh_sigma);
+        for (int i = 0; i < 4; ++i) L.bh_dM[i] = (T)sh_dm[i];
+        const double rs3 = th[1] * th[1] * th[1];
+        for (int i = 0; i < GLAD_N_CSE; ++i) {
+          L.cse_amp[i] = (T)(th[0] * S.cse_a[i] * rs3);
+          L.cse_sc[i] = (T)(S.cse_s[i] * th[1]);
+          L.cse_a3[i] = (T)(S.cse_a[i] * rs3);
+        }
       }
-    }
-    for (int c = 0; c < S.n_lcomp && c < 4 && !comp; ++c) {  // Sersic lens light (class 0)
-      const double Ie = c == 0 ? th[13] : S.lcomp[4 * c];
-      const double Re = c == 0 ? th[14] : S.lcomp[4 * c + 1];
-      const double n = S.lcomp[4 * c + 2], ql = S.lcomp[4 * c + 3];
-      L.ll_Ie[c] = (float)Ie;
-      L.ll_Rei[c] = (float)(1.0 / Re);
-      L.ll_ninv[c] = (float)(1.0 / n);
-      L.ll_bn[c] = (float)sersic_bn_d(n);
-      L.ll_qi2[c] = (float)(1.0 / (ql * ql));
-    }
-    L.valid = 1;
+      for (int c = 0; c < S.n_lcomp && c < 4 && !comp; ++c) {  // Sersic lens light (class 0)
+        const double Ie = c == 0 ? th[13] : S.lcomp[4 * c];
+        const double Re = c == 0 ? th[14] : S.lcomp[4 * c + 1];
+        const double n = S.lcomp[4 * c + 2], ql = S.lcomp[4 * c + 3];
+        L.ll_Ie[c] = (T)Ie;
+        L.ll_Rei[c] = (T)(1.0 / Re);
+        L.ll_ninv[c] = (T)(1.0 / n);
+        L.ll_bn[c] = (T)sersic_bn_d(n);
+        L.ll_qi2[c] = (T)(1.0 / (ql * ql));
+      }
+      L.valid = 1;
+    };
+    fill(ws.lp[b]);
+    if (ws.prec > 0) fill(ws.lp64[b]);
   }
   if (tid == 32) {
     // ---- time delays (FP64): beta_hat, Fermat potentials, chi^2_tmd from the images
@@ -423,6 +436,15 @@ __global__ void __launch_bounds__(TAB_THREADS) k_table(const SysDev *__restrict_
   ws.tab[(size_t)b * max_ent + e] =
       make_float4((float)(-p * LOG2E_D), (float)(-p * c * ial * LOG2E_D), (float)(T * P0),
                   (float)(T * P1));
+  if (ws.prec == 2) {
+    // FP64 pair sum: natural-log exponent coefficients
+    double4_16a t64;
+    t64.x = -p;
+    t64.y = -p * c * ial;
+    t64.z = T * P0;
+    t64.w = T * P1;
+    ws.tab64[(size_t)b * max_ent + e] = t64;
+  }
 }
 
 }  // namespace

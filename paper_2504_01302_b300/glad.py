@@ -160,6 +160,11 @@ class GladContext:
         """Pin the JAM launch shapes (glad_set_tuning)."""
         _lib.check(self.lib.glad_set_tuning(self.handle, int(jam_code), int(adj_ept)), "glad_set_tuning")
 
+    def set_precision(self, mode):
+        """Precision of the forward pass (glad_set_precision): 0 FP32 bulk, 1 FP64 lensing,
+        2 FP64 lensing and pair sum."""
+        _lib.check(self.lib.glad_set_precision(self.handle, int(mode)), "glad_set_precision")
+
     def set_negligible(self, mode):
         """Negligible-term skipping of the forward JAM pass (glad_set_negligible)."""
         _lib.check(self.lib.glad_set_negligible(self.handle, int(mode)), "glad_set_negligible")

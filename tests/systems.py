@@ -55,6 +55,17 @@ def logl_tol(ref):
     return 0.05 + 5e-6 * abs(ref)
 
 
+# Composite class: the halo's 44-CSE decomposition (App. B) is not printed in the paper, so the
+# oracle and the library each fit their own; each is within 2e-7 of the NFW profile and the two
+# differ by up to 4e-7 of it (tests/test_cse_fit.py).  That moves the halo's deflection by
+# 4e-7 of itself (~5e-7") and the model pixels on the arcs by up to ~1e-5 of themselves (the
+# source's logarithmic gradient reaches ~20/"), coherently: |d logL| up to ~2e-5 |logL| far from
+# the data (measured 2.3e-5 at a prior draw, and 0.009 once the oracle is given the library's
+# table), and Fermat-potential differences by ~1e-6 of themselves.
+def logl_tol_comp(ref):
+    return 0.05 + 5e-5 * abs(ref)
+
+
 @functools.lru_cache(maxsize=None)
 def ifu_system():
     """The IFU-scale system (400^2 x 3 image, 31^2 PSF, EPL + shear + 2 SIS, 40 + 2 x 20 MGE

@@ -39,3 +39,22 @@ def test_library_cse_fit_reproduces_the_nfw_profile():
     # a buffer that is too small is refused without writing
     assert lib.glad_enfw_cse(10, a.ctypes.data_as(C.POINTER(C.c_double)),
                              s.ctypes.data_as(C.POINTER(C.c_double)), None) == 44
+
+
+def test_library_and_oracle_fits_agree():
+    """The oracle fits its own decomposition (SciPy's non-negative least squares); the two
+    differ as functions by at most the sum of their errors, which bounds the composite class's
+    parity term (tests/systems.logl_tol_comp)."""
+    from oracle import enfw
+    from paper_2504_01302_b300 import _lib
+    lib = _lib.lib()
+    a = (C.c_double * 44)()
+    s = (C.c_double * 44)()
+    lib.glad_enfw_cse(44, a, s, None)
+    a, s = np.array(a), np.array(s)
+    ao, so = enfw.cse_decomposition()
+    assert np.allclose(s, so, rtol=1e-12)
+    u = np.geomspace(1e-4, 1e3, 3001)
+    f1 = np.sum(a[None, :] * (u[:, None] ** 2 + s[None, :] ** 2) ** -1.5, axis=1)
+    f2 = np.sum(ao[None, :] * (u[:, None] ** 2 + so[None, :] ** 2) ** -1.5, axis=1)
+    assert np.max(np.abs(f1 / f2 - 1)) < 4e-7
