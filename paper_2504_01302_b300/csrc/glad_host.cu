@@ -209,8 +209,9 @@ glad_status build_system(int idx, const glad_system_desc &d, SysHost &sh, SysDev
   sd.ss = d.ss;
   sd.npix = npix;
   sd.pix = (float)d.pix;
-  std::vector<float> wgt(npix);
-  for (int i = 0; i < npix; ++i) wgt[i] = d.mask[i] ? 1.0f / d.sigma[i] : 0.0f;
+  // 1/sigma in FP64: its float32 rounding would scale chi^2_pix coherently by up to ~1e-7
+  std::vector<double> wgt(npix);
+  for (int i = 0; i < npix; ++i) wgt[i] = d.mask[i] ? 1.0 / (double)d.sigma[i] : 0.0;
   sd.data = upload(sh, d.data, npix);
   sd.wgt = upload(sh, wgt.data(), npix);
   sd.psf_k = d.psf_k;

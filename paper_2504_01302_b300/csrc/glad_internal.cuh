@@ -31,7 +31,7 @@ struct SysDev {
   int nx, ny, ss, npix;
   float pix;
   const float *data;     // [npix]
-  const float *wgt;      // [npix] mask / sigma
+  const double *wgt;     // [npix] mask / sigma
   int psf_k;
   const float *psf;      // [psf_k^2]
   int psf_km;            // padded side of psf_t (11, 21 or 31; 0 above 31)

@@ -246,10 +246,10 @@ __global__ void __launch_bounds__(CONV_TX *CONV_TY) k_conv(const SysDev *__restr
     if (image_out) {
       image_out[o] = (float)m;
     } else {
-      const double r = ((double)S.data[o] - m) * (double)S.wgt[o];
+      const double r = ((double)S.data[o] - m) * S.wgt[o];
       chi = r * r;
       // d logL / d m = mask (d - m) / sigma^2, for the adjoint
-      if (resid_out) resid_out[(size_t)b * max_pix + o] = (float)(r * (double)S.wgt[o]);
+      if (resid_out) resid_out[(size_t)b * max_pix + o] = (float)(r * S.wgt[o]);
     }
   }
   if (image_out) return;
@@ -343,9 +343,9 @@ __global__ void __launch_bounds__(CONV_TX *CONV_TY) k_conv_r(const SysDev *__res
     if (image_out) {
       image_out[o] = (float)m;
     } else {
-      const double rr = ((double)S.data[o] - m) * (double)S.wgt[o];
+      const double rr = ((double)S.data[o] - m) * S.wgt[o];
       chi += rr * rr;
-      if (resid_out) resid_out[(size_t)b * max_pix + o] = (float)(rr * (double)S.wgt[o]);
+      if (resid_out) resid_out[(size_t)b * max_pix + o] = (float)(rr * S.wgt[o]);
     }
   }
   if (image_out) return;
