@@ -63,6 +63,8 @@ def parse():
                    help="JAMCODE,EPT: pin the JAM launch shapes instead of autotuning")
     p.add_argument("--graph", type=int, default=-1,
                    help="1: replay the step as a captured CUDA graph (default: on for workload 3)")
+    p.add_argument("--sph-rule", default="",
+                   help="NR,NW,NLOS: rule of the spherically aligned model (default 128,8,32)")
     return p.parse_args()
 
 
@@ -461,7 +463,7 @@ def measure(args, ctx, lib, systems, th_np, sid_np, B, grad_mode, world, rank, l
 
     extra = kl[names_idx("k_image+k_conv", lib, nk)] + kl[names_idx("k_grad_lens", lib, nk)] + \
         kl[names_idx("k_sph_coef+k_sph_grid", lib, nk)] + 2 * kl[names_idx("k_sph_adjoint", lib, nk)] + \
-        (kl[names_idx("k_jam", lib, nk)] if tuning["jam_pts"] >= 100000 else 0)
+        (kl[names_idx("k_jam", lib, nk)] if (tuning["jam_pts"] // 100000) % 10 == 1 else 0)
     launches_per_step = (int(sum(kl[i] for i in range(nk))) + int(extra)) // prof_steps
     if grad_mode:
         launches_per_step += 2  # k_kin_adj and k_grad_zero_invalid run untimed by the profiler
@@ -483,7 +485,15 @@ def measure(args, ctx, lib, systems, th_np, sid_np, B, grad_mode, world, rank, l
     n_exec["k_sph_coef+k_sph_grid"] = n_exec["k_sph_los"] = n_exec["k_sph_adjoint"] = evals
     clocks = clk.summary()
     sm_max = clocks["sm_max_mhz"] or 2032.0
-    if jam_name in ("k_jam", "k_sph_coef+k_sph_grid", "k_sph_los", "k_sph_adjoint"):
+    jam_form = tuning["jam_pts"] // 1000000
+    if jam_name == "k_jam" and jam_form in (1, 3):
+        # recurrence forms: per 8 evaluations 15 packed FMA-pipe operations (2 FP32 lanes each)
+        # and 4 ex2, so the FMA pipe bounds them
+        peak = N_SM * FFMA_LANES_PER_CLK_SM * sm_max * 1e6 / 3.75 / 1e9
+        peak_unit = "Geval/s"
+        peak_basis = (f"{N_SM} SM x {FFMA_LANES_PER_CLK_SM} FP32 lanes/clk/SM x {sm_max:.0f} MHz "
+                      f"/ 3.75 FMA-pipe lane operations per evaluation (recurrence form {jam_form})")
+    elif jam_name in ("k_jam", "k_sph_coef+k_sph_grid", "k_sph_los", "k_sph_adjoint"):
         # one ex2 per evaluation; the 4 FMA-pipe operations per evaluation allow the same rate
         peak = N_SM * MUFU_EX2_PER_CLK_SM * sm_max * 1e6 / 1e9
         peak_unit = "Gexp2/s"
@@ -506,8 +516,8 @@ def measure(args, ctx, lib, systems, th_np, sid_np, B, grad_mode, world, rank, l
         "valid_samples": n_valid, "tuning": tuning, "cuda_graph": bool(use_graph),
         "roofline": {"bound": "alu", "kernel": jam_name, "achieved": achieved, "peak": peak,
                      "unit": peak_unit, "frac": achieved / peak,
-                     "achieved_basis": "integrand evaluations (one ex2 each) the kernel executes "
-                                       "per launch (library counter) / its CUDA-event time alone",
+                     "achieved_basis": "integrand evaluations the kernel executes per launch "
+                                       "(library counter) / its CUDA-event time alone",
                      "traffic": ncu_traffic(jam_name, w, grad_mode, B),
                      "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
                                       "small-batch capture, scaled by samples to this batch",
@@ -555,6 +565,10 @@ def main():
 
     w = args.workload
     systems, B_w = bench_systems(w)
+    if args.sph_rule:
+        nr, nw, nl = (int(v) for v in args.sph_rule.split(","))
+        for s in systems:
+            s.update(sph_nr=nr, sph_nw=nw, sph_nlos=nl)
     systems = fill_data_with_gpu_model(systems, w, torch, GladContext)
     ctx = GladContext(systems)
     lib = ctx.lib
@@ -596,6 +610,7 @@ def main():
                    "l2": "flushed (256 MB write) before each timed step",
                    "valid_samples": m["valid_samples"],
                    "tuning": m["tuning"], "cuda_graph": m["cuda_graph"],
+                   **({"sph_rule": args.sph_rule} if args.sph_rule else {}),
                    "jam_skipping": "terms that underflow to 0 over a sky tile, and (pair sum and "
                                    "derivative pass) terms whose bounded total over the tile "
                                    "stays below 2^-26 of its smallest sum (checked after the sum)"},

@@ -245,20 +245,30 @@ glad_status glad_loglike_static(glad_ctx *ctx, const int *sys_id, const double *
 /* Autotuner (the project's own, no counterpart in the paper): times the candidate
  * launch shapes of the JAM kernels on this batch (arguments as glad_loglike) -- for the
  * pair sum: points per thread, minimum resident CTAs per SM asked of the register
- * allocator, unroll of the table-entry loop, grid or persistent form; with with_grad,
- * table entries per thread of its adjoint (2 or 4) -- and keeps the fastest in the
- * context for later calls.  When the environment variable GLAD_TUNE_CACHE names a file,
+ * allocator, unroll of the table-entry loop, form of the sum, grid or persistent form; with
+ * with_grad, table entries per thread of its adjoint (2 or 4) -- and keeps the fastest in
+ * the context for later calls.  Forms: 0 direct, two sky points per packed f32x2 operation;
+ * 2 direct, two table entries per packed operation; 1 and 3 the recurrence forms of 0 and 2,
+ * which write an entry's exponent at the i-th of 4 consecutive sky rows as
+ * a(i) = a(0) + i B + i^2 C (log2 units) and sum 2^a(i) = 2^a(0) (2^B)^i 2^(C i^2) with two
+ * ex2 per chain, the last factor folded into the entry's prefactors; they take the entries
+ * with |C| <= 1 (the rest are summed directly), can lose terms below 2^-67 of their
+ * prefactor (counted in the negligible-term check) and round differently from the direct
+ * forms (~1e-6 relative per term).  When the environment variable GLAD_TUNE_CACHE names a file,
  * the choice is appended there keyed by device name and batch shape, and later calls
  * with the same key read it back and skip the timing.  Synchronises the stream and
  * allocates a few small scratch arrays.  glad_tuning reports the current choice:
- * *jam_code = 100000 * persistent + 1000 * points + 10 * min CTAs + unroll,
+ * *jam_code = 1000000 * form + 100000 * persistent + 1000 * points + 10 * min CTAs
+ * + unroll,
  * *adj_ept = entries per thread. */
 glad_status glad_autotune(glad_ctx *ctx, const int *sys_id, const double *theta, int B,
                           int with_grad, void *stream);
 int glad_tuning(glad_ctx *ctx, int *jam_code, int *adj_ept);
-/* Pin a launch shape instead of tuning (codes as reported by glad_tuning: shapes
- * 4052, 4054, 4064, 8032, 8042, 8044, 16021, each optionally + 100000 for the persistent
- * form; adj_ept 2 or 4).  GLAD_EINVAL for other values. */
+/* Pin a launch shape instead of tuning (codes as reported by glad_tuning: 4052, 4054, 4064,
+ * 8032, 8042, 8044, 16021 (form 0); 1008032, 1008041, 1008042, 1016021 (form 1); 2004042,
+ * 2004052, 2004051, 2008031 (form 2); 3004042, 3004041, 3004051, 3008031 (form 3); each
+ * optionally + 100000 for the persistent form; adj_ept 2 or 4).  GLAD_EINVAL for other
+ * values. */
 glad_status glad_set_tuning(glad_ctx *ctx, int jam_code, int adj_ept);
 
 /* Precision of the forward pass (Sect. 3: the paper computes in FP64 throughout).

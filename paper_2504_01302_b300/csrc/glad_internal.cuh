@@ -213,6 +213,7 @@ struct glad_ctx {
     int jam_minb = 4;     // minimum resident CTAs per SM requested from the register allocator
     int jam_unroll = 2;   // unroll of the table-entry loop
     int jam_persistent = 0;  // 1: one persistent launch over a (sample, tile) work list
+    int jam_form = 0;        // form of the pair sum (k_jam.cu): 0 .. 3
     int adj_ept = 4;      // table entries per thread in the JAM adjoint
   } tune;
   int *d_one_sys = nullptr;      // scratch sys id for single-sample calls
@@ -286,8 +287,8 @@ void cse_table(const double **a, const double **s);
 cudaError_t launch_dyn_tables(glad_ctx *c, const int *sys_id, int B, cudaStream_t st);
 cudaError_t launch_dyn_sums(glad_ctx *c, const int *sys_id, int B, cudaStream_t st);
 void set_conv_smem_limit();
-bool jam_shape_supported(int pts, int minb, int unr);
-int jam_shape_list(int (*out)[3], int cap);
+bool jam_shape_supported(int pts, int minb, int unr, int form);
+int jam_shape_list(int (*out)[4], int cap);
 
 // tile shapes (shared by launchers and the workspace sizing)
 #define JAM_THREADS 256

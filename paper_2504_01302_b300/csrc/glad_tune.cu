@@ -21,11 +21,26 @@ cudaError_t time_jam_adj(glad_ctx *c, const int *sys_id, int B, cudaStream_t st)
 
 namespace {
 
-// launch shape of the JAM pair sum as one integer:
+// launch shape of the JAM pair sum as one integer: 1000000 * form of the sum +
 // 100000 * persistent + 1000 * points per thread + 10 * min CTAs per SM + unroll
 int jam_code(const glad_ctx *c) {
-  return c->tune.jam_persistent * 100000 + c->tune.jam_pts * 1000 + c->tune.jam_minb * 10 +
-         c->tune.jam_unroll;
+  return c->tune.jam_form * 1000000 + c->tune.jam_persistent * 100000 + c->tune.jam_pts * 1000 +
+         c->tune.jam_minb * 10 + c->tune.jam_unroll;
+}
+
+// decodes a jam_code into the context's tuning; false (nothing changed) for codes this build
+// does not have
+bool set_jam_code(glad_ctx *c, int code) {
+  if (code < 0) return false;
+  const int form = code / 1000000, pers = (code / 100000) % 10, pts = (code % 100000) / 1000;
+  const int minb = (code % 1000) / 10, unr = code % 10;
+  if (form > 3 || pers > 1 || !jam_shape_supported(pts, minb, unr, form)) return false;
+  c->tune.jam_form = form;
+  c->tune.jam_persistent = pers;
+  c->tune.jam_pts = pts;
+  c->tune.jam_minb = minb;
+  c->tune.jam_unroll = unr;
+  return true;
 }
 
 std::string tune_key(glad_ctx *c, int B) {
@@ -95,13 +110,7 @@ extern "C" glad_status glad_autotune(glad_ctx *c, const int *sys_id, const doubl
   int pts = 8, ept = 4;
   int code = 0;
   // a cached choice counts only while this build still has that launch shape
-  if (cache_lookup(key, &code, &ept) &&
-      jam_shape_supported((code % 100000) / 1000, (code % 1000) / 10, code % 10) &&
-      (ept == 2 || ept == 4)) {
-    c->tune.jam_persistent = code / 100000;
-    c->tune.jam_pts = (code % 100000) / 1000;
-    c->tune.jam_minb = (code % 1000) / 10;
-    c->tune.jam_unroll = code % 10;
+  if (cache_lookup(key, &code, &ept) && (ept == 2 || ept == 4) && set_jam_code(c, code)) {
     c->tune.adj_ept = ept;
     return GLAD_OK;
   }
@@ -126,26 +135,30 @@ extern "C" glad_status glad_autotune(glad_ctx *c, const int *sys_id, const doubl
                 : glad_loglike(c, sys_id, theta, B, logL, status, nullptr, stream);
   if (s == GLAD_OK) {
     // (points per thread, minimum CTAs per SM asked of the register allocator)
-    int cand[32][3];
+    int cand[32][4];
     const int ncand = jam_shape_list(cand, 32);
     float best = 1e30f;
-    int minb = 4, unr = 2;
-    for (int ic = 0; ic < ncand; ++ic) {
+    int minb = 4, unr = 2, form = 0;
+    c->tune.jam_persistent = 0;
+    for (int ic = 0; ic < ncand && ic < 32; ++ic) {
       const int *cd = cand[ic];
       c->tune.jam_pts = cd[0];
       c->tune.jam_minb = cd[1];
       c->tune.jam_unroll = cd[2];
+      c->tune.jam_form = cd[3];
       const float ms = time_ms(st, [&]() { launch_jam(c, sys_id, B, st); }, 2);
       if (ms < best) {
         best = ms;
         pts = cd[0];
         minb = cd[1];
         unr = cd[2];
+        form = cd[3];
       }
     }
     c->tune.jam_pts = pts;
     c->tune.jam_minb = minb;
     c->tune.jam_unroll = unr;
+    c->tune.jam_form = form;
     // the same shape as one persistent launch over the (sample, tile) work list
     c->tune.jam_persistent = 1;
     const float ms_p = time_ms(st, [&]() { launch_jam(c, sys_id, B, st); }, 2);
@@ -183,15 +196,8 @@ extern "C" int glad_tuning(glad_ctx *c, int *jam_pts, int *adj_ept) {
 
 extern "C" glad_status glad_set_tuning(glad_ctx *c, int jam_code, int adj_ept) {
   if (!c) return glad_set_error(GLAD_EINVAL, "glad_set_tuning: null context");
-  const int pers = jam_code / 100000, pts = (jam_code % 100000) / 1000;
-  const int minb = (jam_code % 1000) / 10, unr = jam_code % 10;
-  const bool ok_jam = (pers == 0 || pers == 1) && jam_shape_supported(pts, minb, unr);
-  if (!ok_jam || (adj_ept != 2 && adj_ept != 4))
+  if ((adj_ept != 2 && adj_ept != 4) || !set_jam_code(c, jam_code))
     return glad_set_error(GLAD_EINVAL, "glad_set_tuning: unsupported launch shape");
-  c->tune.jam_persistent = pers;
-  c->tune.jam_pts = pts;
-  c->tune.jam_minb = minb;
-  c->tune.jam_unroll = unr;
   c->tune.adj_ept = adj_ept;
   return GLAD_OK;
 }

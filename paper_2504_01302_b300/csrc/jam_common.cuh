@@ -31,9 +31,11 @@ __device__ __forceinline__ float jam_ex2(float x) {
 #define JAM_REL_CHECK 26.0f
 
 struct JamSmem {
-  float4 tab[2][JAM_CHUNK];
+  float4 tab[2][JAM_CHUNK + 4];        // (+4: the entry-paired forms pad two odd lists)
   int wcount[2][2][JAM_THREADS / 32];  // [buffer][half of the chunk][warp]
+  int wc[2][2][2][JAM_THREADS / 32];   // [buffer][half][direct, recurrence][warp] (k_jam forms 1-3)
   int n_kept[2];
+  int n_direct[2];
   float red[4][JAM_THREADS / 32];      // block reductions of the negligible-term test
   int flag;
   float tb[5];                         // tile constants: Xmin, Ymin, Xmax, lref, lrel

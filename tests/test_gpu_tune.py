@@ -7,6 +7,8 @@ from . import systems
 pytestmark = pytest.mark.gpu
 
 SHAPES = [4052, 4054, 4064, 8032, 8042, 8044, 16021]
+OTHER_FORMS = [1008032, 1008041, 1008042, 1016021, 2004042, 2004052, 2004051, 2008031,
+               3004042, 3004041, 3004051, 3008031]
 
 torch = pytest.importorskip("torch")
 
@@ -20,10 +22,12 @@ def test_autotune_keeps_results(tmp_path, monkeypatch):
     before = ctx.loglike(th)[0].cpu().numpy()
     g_before = ctx.loglike_grad(th)[1].cpu().numpy()
     t = ctx.autotune(th, with_grad=True)
-    assert t["jam_pts"] % 100000 in SHAPES and t["adj_ept"] in (2, 4)
+    code = t["jam_pts"]
+    assert code % 100000 + 1000000 * (code // 1000000) in SHAPES + OTHER_FORMS and t["adj_ept"] in (2, 4)
     after = ctx.loglike(th)[0].cpu().numpy()
     g_after = ctx.loglike_grad(th)[1].cpu().numpy()
-    assert np.all(np.abs(after - before) < 1e-6 * np.abs(before))
+    # the other forms of the pair sum round differently from the default one
+    assert np.all(np.abs(after - before) < (1e-6 if code < 1000000 else 1e-5) * np.abs(before))
     assert np.allclose(g_after, g_before, rtol=1e-4, atol=1e-6 * np.max(np.abs(g_before)))
     # the cache file now holds the choice; a second context reads it back
     assert (tmp_path / "tune.txt").read_text().strip()
