@@ -54,9 +54,10 @@ Two forms are written out:
            v_r^2 and d cubic in ln r (4-point Lagrange) and linear in w = R^2/r^2,
            clamped to the grid; nu exact at the node.
   Defaults n_r = 128, n_w = 8, n_los = 32: against the cylindrical pair form at beta = 0
-  (the two models coincide there) the RXJ1131-scale sky maps agree to 2.9e-4 (1.5e-4 in
-  v_rms); the error is set by the radial grid and falls as n_r^-3.3 (6.2e-4 at n_r = 96,
-  1.8e-4 at 160); beyond 24 line-of-sight nodes it no longer depends on n_los.
+  (the two models coincide there) the RXJ1131-scale sky maps agree to 2.9e-4 at sampled
+  points and the binned v_rms to 3e-5 - 6e-5; the radial grid sets the error up to
+  n_r ~ 160 (falling as n_r^-3.3), the angular grid beyond it (192 x 16 x 32: 6e-6 - 1.1e-5
+  in v_rms); beyond 24 line-of-sight nodes it no longer depends on n_los.
 
 Pins (tests/test_oracle_sph.py): the plain solution satisfies J1 and J2 (finite
 differences); at beta = 0 it equals the cylindrical isotropic solution (nu v_z^2 and
