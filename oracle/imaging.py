@@ -31,14 +31,17 @@ def subpixel_grid(nx, ny, ss, pix):
     return X, Y
 
 
-def surface_brightness(x, y, th, sysd, alpha=None):
+def surface_brightness(x, y, th, sysd, alpha=None, source=True):
     """Source (through the lens) + lens light at sky points (x, y); alpha: a deflection
-    function alpha(x, y, th, sis) (default: the system's mass class, lensmodel.alpha)."""
+    function alpha(x, y, th, sis) (default: the system's mass class, lensmodel.alpha);
+    source=False: the lens light alone."""
     from paper_2504_01302_b300.synth import IDX
-    ax, ay = (alpha(x, y, th, sysd["sis"]) if alpha else lensmodel.alpha(x, y, th, sysd))
-    bx, by = x - ax, y - ay
-    src = light.sersic_xy(bx, by, th[IDX["I_e_src"]], th[IDX["R_e_src"]], th[IDX["n_src"]],
-                          sysd["src_q"], th[IDX["x_src"]], th[IDX["y_src"]], sysd["src_phi"])
+    src = 0.0
+    if source:
+        ax, ay = (alpha(x, y, th, sysd["sis"]) if alpha else lensmodel.alpha(x, y, th, sysd))
+        bx, by = x - ax, y - ay
+        src = light.sersic_xy(bx, by, th[IDX["I_e_src"]], th[IDX["R_e_src"]], th[IDX["n_src"]],
+                              sysd["src_q"], th[IDX["x_src"]], th[IDX["y_src"]], sysd["src_phi"])
     xc, yc, phi = th[IDX["x_c"]], th[IDX["y_c"]], th[IDX["phi"]]
     if lensmodel.is_composite(sysd):
         # the composite class's lens light: Chameleon profiles (Eq. Chameleon) in the galaxy frame
@@ -54,9 +57,9 @@ def surface_brightness(x, y, th, sysd, alpha=None):
     return src + ll
 
 
-def unblurred_image(th, sysd, alpha=None):
+def unblurred_image(th, sysd, alpha=None, source=True):
     X, Y = subpixel_grid(sysd["nx"], sysd["ny"], sysd["ss"], sysd["pix"])
-    return surface_brightness(X, Y, th, sysd, alpha).mean(axis=-1)
+    return surface_brightness(X, Y, th, sysd, alpha, source).mean(axis=-1)
 
 
 def convolve_same(img, psf):
@@ -74,8 +77,9 @@ def convolve_same(img, psf):
     return out
 
 
-def model_image(th, sysd, alpha=None):
-    return convolve_same(unblurred_image(th, sysd, alpha), np.asarray(sysd["psf"], np.float64))
+def model_image(th, sysd, alpha=None, source=True):
+    return convolve_same(unblurred_image(th, sysd, alpha, source),
+                         np.asarray(sysd["psf"], np.float64))
 
 
 def chi2_pix(model, sysd):

@@ -4,7 +4,10 @@ Eq. chi_general / Eq. Posterior_LD: the joint chi^2 of the terms built here is
 chi^2 = chi^2_pix (Eq. chi2 of lens_light over the whole extended image) +
 chi^2_dyn (Eq. chi2_dyn) + chi^2_tmd (Eq. chi2_tmd) [+ chi^2_img (Eq. chi2_img) when the
 system gives image-position uncertainties], and logL = -chi^2/2 (the Gaussian
-normalisation constant is dropped, as chi^2_LD has none).
+normalisation constant is dropped, as chi^2_LD has none).  For a system with a pixelated
+source (src_pix = 1, Sect. 3.1.1) the image term is the log-evidence of the source
+reconstruction at its optimal regularisation (Eq. evi_ext, oracle/pixsrc.py) in place of
+-chi^2_pix / 2, reported as chi2_pix = -2 ln P.
 
 Dynamics chain (Sect. 3.2 and App. A): 1-D MGE of the App. C convergence and of
 each lens-light Sersic -> a black-hole Gaussian (sigma_BH, M_BH = f_BH * M_*,
@@ -23,7 +26,7 @@ import math
 import numpy as np
 
 from paper_2504_01302_b300 import synth
-from . import cosmo, imaging, jam, jam_sph, kin, lens, lensmodel, mge, tdelay
+from . import cosmo, imaging, jam, jam_sph, kin, lens, lensmodel, mge, pixsrc, tdelay
 
 IDX = synth.IDX
 
@@ -222,9 +225,14 @@ def evaluate(th, sysd, want=False):
     if st != ST_OK:
         out["status"] = st
         return out
-    img = imaging.model_image(th, sysd)
+    if sysd.get("src_pix", 0):
+        # pixelated source (Sect. 3.1.1): the evidence takes the place of -chi^2_pix / 2
+        lnP, lam, s_mp = pixsrc.evidence_term(th, sysd)
+        img, c_pix = None, -2.0 * lnP
+    else:
+        img = imaging.model_image(th, sysd)
+        c_pix = imaging.chi2_pix(img, sysd)
     dt = tdelay.delays(th, sysd)
-    c_pix = imaging.chi2_pix(img, sysd)
     c_dyn = kin.chi2_dyn(v, sysd)
     c_tmd = tdelay.chi2_tmd(dt, sysd)
     # image positions (Eq. chi2_img) when the system gives their uncertainties
@@ -235,6 +243,8 @@ def evaluate(th, sysd, want=False):
         return out
     out.update(logL=logL, chi2_pix=c_pix, chi2_dyn=c_dyn, chi2_tmd=c_tmd, chi2_img=c_img, image=img,
                vrms=v, delays=dt, extra=extra)
+    if sysd.get("src_pix", 0):
+        out.update(lnP=lnP, lam=lam, s_mp=s_mp)
     return out
 
 

@@ -34,7 +34,7 @@ import math
 import numpy as np
 from scipy.optimize import minimize_scalar
 
-from . import imaging, lens
+from . import imaging, lens, lensmodel
 
 
 class SourceGrid:
@@ -64,9 +64,10 @@ class SourceGrid:
 
 
 def lens_matrix(th, sysd, grid, alpha=None):
-    """L [ny*nx, N_s]: each image pixel's mean over its sub-pixel rays of the bilinear weights."""
+    """L [ny*nx, N_s]: each image pixel's mean over its sub-pixel rays of the bilinear weights
+    (alpha(x, y, th, sis) if given, else the system's mass class)."""
     X, Y = imaging.subpixel_grid(sysd["nx"], sysd["ny"], sysd["ss"], sysd["pix"])
-    ax, ay = (alpha or lens.alpha_total)(X, Y, th, sysd["sis"])
+    ax, ay = alpha(X, Y, th, sysd["sis"]) if alpha else lensmodel.alpha(X, Y, th, sysd)
     idx, w = grid.bilinear(X - ax, Y - ay)            # [ny, nx, ss^2, 4]
     npix = sysd["nx"] * sysd["ny"]
     rows = np.broadcast_to(np.arange(npix).reshape(sysd["ny"], sysd["nx"], 1, 1), idx.shape)
@@ -139,3 +140,25 @@ def best_lambda(f, d, sig, C, lo=1e-6, hi=1e6):
     lam = math.exp(res.x)
     s, lnP = solve(f, d, sig, C, lam)
     return lam, s, lnP
+
+
+def grid_of(sysd):
+    """The system's source grid (descriptor entries spx_box = (x0, x1, y0, y1), spx_n = (nx, ny))."""
+    x0, x1, y0, y1 = sysd["spx_box"]
+    return SourceGrid(x0, x1, y0, y1, int(sysd["spx_n"][0]), int(sysd["spx_n"][1]))
+
+
+def evidence_term(th, sysd):
+    """The extended-image term of a pixelated-source system (Sect. 3.1.1): the arcs
+    d_esr = data - B (lens light) on the mask's pixels are reconstructed on the system's source
+    grid and scored by the evidence at the optimal regularisation (Eq. evi_ext); returns
+    (ln P, lambda_hat, s_MP)."""
+    grid = grid_of(sysd)
+    m = np.asarray(sysd["mask"]).ravel() != 0
+    ll = imaging.model_image(th, sysd, source=False).ravel()
+    d = np.asarray(sysd["data"], np.float64).ravel()[m] - ll[m]
+    sig = np.asarray(sysd["sigma"], np.float64).ravel()[m]
+    f = response(th, sysd, grid)
+    lo, hi = sysd.get("spx_lam", (1e-6, 1e6))
+    lam, s, lnP = best_lambda(f, d, sig, curvature(grid), lo, hi)
+    return lnP, lam, s
