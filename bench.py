@@ -42,6 +42,7 @@ FFMA_LANES_PER_CLK_SM = 128
 # (exponent 2, prefactor 1, term 1, value and two derivative sums 4), table adjoint (exponent
 # 2, weighted term 1, four moment sums 4)
 FMA_OPS_PER_EVAL = {"k_jam_fwd_grad": 8, "k_jam_adjoint": 7}
+DFMA_PER_CLK_SM = 1.75  # FP64 FMA per clock per SM, measured (profiles/mufu_ffma_rates_b300.md)
 
 
 def parse():
@@ -117,7 +118,11 @@ def workload_name(w, grad, B):
              8: "RXJ1131-scale composite class (2 Chameleons x Upsilon, eNFW halo as 44 CSEs, BH) "
                 "with the dPIE sheet and sampled D_d, D_dt,int (the paper's joint model): 200^2 "
                 "x2ss, 21^2 PSF, +shear+SIS, JAM 2x10 tracer x (20 baryon + 20 halo + 40 sheet + BH) "
-                "mass, 60^2 sky x4ss, GL32, 50 bins"}
+                "mass, 60^2 sky x4ss, GL32, 50 bins",
+             9: "RXJ1131-scale with the pixelated source (Sect. 3.1.1): 200^2 x2ss, 21^2 PSF, "
+                "EPL+shear+SIS, 30x30 source grid (N_s = 900), arcs in 0.9-2.5 arcsec (N_d = 6840), "
+                "evidence maximised over ln lambda (FP64 Cholesky per evaluation), JAM 20+2x10+BH, "
+                "60^2 sky x4ss, GL32, 50 bins"}
     n = names.get(w, str(w)) + f"; B={B}"
     if grad:
         n += " (forward + gradient)"
@@ -186,7 +191,8 @@ def bench_truth(w, systems):
 
 
 def fill_data_with_gpu_model(systems, w, torch, GladContext):
-    ctx = GladContext(systems)
+    # the data come from the Sersic source; pixelated-source systems then fit them
+    ctx = GladContext([dict(s, src_pix=0) for s in systems])
     truth = torch.as_tensor(bench_truth(w, systems), device="cuda")
     for i, s in enumerate(systems):
         nz = synth.noise_draws(s, 1000 * w + i + 500)
@@ -437,7 +443,7 @@ def measure(args, ctx, lib, systems, th_np, sid_np, B, grad_mode, world, rank, l
 
     # ---- the plain form: the same kernels called once per sample (B = 1), no graph,
     # on the first n_plain samples of the batch, L2 not flushed between calls
-    n_plain = min(B, 32)
+    n_plain = min(B, 4 if any(s.get("src_pix", 0) for s in systems) else 32)
 
     def plain_call(b):
         hs = C.c_void_p(stream.cuda_stream)
@@ -463,30 +469,50 @@ def measure(args, ctx, lib, systems, th_np, sid_np, B, grad_mode, world, rank, l
 
     extra = kl[names_idx("k_image+k_conv", lib, nk)] + kl[names_idx("k_grad_lens", lib, nk)] + \
         kl[names_idx("k_sph_coef+k_sph_grid", lib, nk)] + 2 * kl[names_idx("k_sph_adjoint", lib, nk)] + \
-        (kl[names_idx("k_jam", lib, nk)] if (tuning["jam_pts"] // 100000) % 10 == 1 else 0)
+        (kl[names_idx("k_jam", lib, nk)] if (tuning["jam_pts"] // 100000) % 10 == 1 else 0) + \
+        kl[names_idx("k_pix_operator", lib, nk)] + kl[names_idx("k_pix_evidence", lib, nk)] * (
+            max((s.get("spx_iters", 0) or 40) for s in systems) + 1)
     launches_per_step = (int(sum(kl[i] for i in range(nk))) + int(extra)) // prof_steps
     if grad_mode:
         launches_per_step += 2  # k_kin_adj and k_grad_zero_invalid run untimed by the profiler
     # integrand evaluations the JAM kernels actually execute per step (exact and negligible
     # terms skipped), from one more untimed full-batch step
+    if any(s.get("src_pix", 0) for s in systems):
+        ctx.pix_factorizations()  # reset the count: the next step alone is counted
     step()
     n_exec = {"k_jam": ctx.jam_evaluations(), "k_jam_fwd_grad": ctx.jam_evaluations(),
               "k_jam_adjoint": ctx.jam_evaluations(adjoint=True)}
+    n_fac = ctx.pix_factorizations() if any(s.get("src_pix", 0) for s in systems) else 0
     # ---- roofline of the dominant kernel (the JAM pair sum, its derivative pass, the table
     # adjoint or a kernel of the spherically aligned model, whichever takes longest per step)
     names = [lib.glad_kernel_name(i).decode() for i in range(nk)]
     per_kernel = {names[i]: kms[i] / max(kl[i], 1) for i in range(nk) if kl[i]}
     jam_name = max((n for n in ("k_jam", "k_jam_fwd_grad", "k_jam_adjoint", "k_sph_coef+k_sph_grid",
-                                "k_sph_los", "k_sph_adjoint") if n in per_kernel),
+                                "k_sph_los", "k_sph_adjoint", "k_pix_evidence") if n in per_kernel),
                    key=lambda n: per_kernel[n])
     jam_ms = per_kernel[jam_name]
-    evals, units = sph_exp2_counts(systems, sid_np, B, jam_name)
+    if jam_name == "k_pix_evidence":
+        # FP64 flops of the evidence evaluations: per factorisation of F + lambda C (N_s^2)
+        # N_s^3 / 3 for the Cholesky, N_s^2 for y = L^-1 D, N_s^2 for assembling F + lambda C
+        ns = next(int(np.prod(systems[k]["spx_n"])) for k in sid_np if systems[k].get("src_pix", 0))
+        per = ns ** 3 / 3.0 + 2.0 * ns ** 2
+        evals = n_fac * per
+        units = (f"{evals:.4g} FP64 flops per launch: {n_fac} factorisations of F + lambda C "
+                 f"(N_s = {ns}) x (N_s^3/3 + 2 N_s^2)")
+        n_exec["k_pix_evidence"] = evals
+    else:
+        evals, units = sph_exp2_counts(systems, sid_np, B, jam_name)
     # no terms are skipped in the spherically aligned kernels
     n_exec["k_sph_coef+k_sph_grid"] = n_exec["k_sph_los"] = n_exec["k_sph_adjoint"] = evals
     clocks = clk.summary()
     sm_max = clocks["sm_max_mhz"] or 2032.0
     jam_form = tuning["jam_pts"] // 1000000
-    if jam_name == "k_jam" and jam_form in (1, 3):
+    if jam_name == "k_pix_evidence":
+        peak = N_SM * DFMA_PER_CLK_SM * 2 * sm_max * 1e6 / 1e12
+        peak_unit = "TFLOP/s"
+        peak_basis = (f"{N_SM} SM x {DFMA_PER_CLK_SM} DFMA/clk/SM (measured, "
+                      f"profiles/mufu_ffma_rates_b300.md) x 2 flops x {sm_max:.0f} MHz max SM clock")
+    elif jam_name == "k_jam" and jam_form in (1, 3):
         # recurrence forms: per 8 evaluations 15 packed FMA-pipe operations (2 FP32 lanes each)
         # and 4 ex2, so the FMA pipe bounds them
         peak = N_SM * FFMA_LANES_PER_CLK_SM * sm_max * 1e6 / 3.75 / 1e9
@@ -508,16 +534,20 @@ def measure(args, ctx, lib, systems, th_np, sid_np, B, grad_mode, world, rank, l
     executed = n_exec[jam_name]
     if args.precision == 2 and not grad_mode and jam_name == "k_jam":
         executed = evals  # the FP64 pair sum evaluates every term
-    achieved = executed / (jam_ms / 1000.0) / 1e9
-    achieved_alg = evals / (jam_ms / 1000.0) / 1e9
+    scale = 1e12 if peak_unit == "TFLOP/s" else 1e9
+    achieved = executed / (jam_ms / 1000.0) / scale
+    achieved_alg = evals / (jam_ms / 1000.0) / scale
     unit = "logL+grad/s" if grad_mode else "logL/s"
     return {
         "value": value, "unit": unit, "ms_per_step": t_ms / args.steps, "batch_per_gpu": B,
         "valid_samples": n_valid, "tuning": tuning, "cuda_graph": bool(use_graph),
         "roofline": {"bound": "alu", "kernel": jam_name, "achieved": achieved, "peak": peak,
                      "unit": peak_unit, "frac": achieved / peak,
-                     "achieved_basis": "integrand evaluations the kernel executes per launch "
-                                       "(library counter) / its CUDA-event time alone",
+                     "achieved_basis": ("FP64 flops of the factorisations the search ran (library "
+                                        "counter) / the evidence kernels' CUDA-event time alone"
+                                        if jam_name == "k_pix_evidence" else
+                                        "integrand evaluations the kernel executes per launch "
+                                        "(library counter) / its CUDA-event time alone"),
                      "traffic": ncu_traffic(jam_name, w, grad_mode, B),
                      "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
                                       "small-batch capture, scaled by samples to this batch",
@@ -582,10 +612,13 @@ def main():
     # the forward line (logL/s); with --grad only the gradient line; by default the gradient
     # (logL+grad/s, batch 64) is measured too and reported in the line's "grad" object
     main_grad = bool(args.grad)
+    pix = any(s.get("src_pix", 0) for s in systems)
+    if main_grad and pix:
+        raise SystemExit("the pixelated source has no gradient (glad_loglike_grad refuses it)")
     B, th_np, sid_np = batch(main_grad)
     m = measure(args, ctx, lib, systems, th_np, sid_np, B, main_grad, world, rank, local, torch, dist)
     g = None
-    if not main_grad and not args.no_grad:
+    if not main_grad and not args.no_grad and not pix:
         Bg, thg, sidg = batch(True)
         g = measure(args, ctx, lib, systems, thg, sidg, Bg, True, world, rank, local, torch, dist)
         g["config"] = {"workload": workload_name(w, True, Bg)}

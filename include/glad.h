@@ -125,6 +125,28 @@ enum {
  * Limits: sph_nr * sph_nw <= 4096 and (mass Gaussians incl. sheet and black hole) x n_gl <= 4096
  * (GLAD_EUNSUPPORTED beyond, as for sizes whose gradient kernels would need more than
  * 226 KB of shared memory per block).  glad_loglike_grad differentiates both models.
+ *
+ * Source (Sect. 3.1.1): src_pix 0 takes the Sersic source of theta[8..12]; src_pix 1
+ * reconstructs the source on a grid of spx_nx x spx_ny pixels (3 <= each, product <= 4624)
+ * covering [spx_x0, spx_x1] x [spx_y0, spx_y1] of the source plane: the response
+ * f = B L maps the grid to the masked image pixels (each image pixel averages its ss^2 rays,
+ * each ray the bilinear interpolation of the four grid pixels around beta; rays outside the
+ * grid contribute nothing; B the PSF blurring), the arcs d_esr = data - B (lens light) are
+ * fitted by s_MP = (F + lambda C)^-1 D (Eq. s_MP; F = f^T C_D^-1 f, D = f^T C_D^-1 d_esr,
+ * C = H^T H the curvature regularisation, second differences along x and y with zero outside
+ * the grid), and the image term is the log-evidence at the lambda that maximises it (Eq.
+ * evi_ext, the marginal likelihood of the linear Gaussian model):
+ *   ln P = -E_D - lambda E_S - ln det(F + lambda C)/2 + (N_s/2) ln lambda
+ *          + ln det C / 2 - (N_d/2) ln 2 pi - ln det C_D / 2,
+ * E_D = (f s_MP - d)^T C_D^-1 (f s_MP - d) / 2 and E_S = s_MP^T C s_MP / 2,
+ * maximised over ln lambda in [ln spx_lam_lo, ln spx_lam_hi] by Brent's method to 1e-5 in
+ * ln lambda or spx_iters evaluations.  terms[0] then holds -2 ln P (so that logL is still
+ * -(sum of terms)/2) and theta[8..12] are not used.  Arithmetic: rays and the response in
+ * FP32; the Gram matrix [F D; D^T d^T C_D^-1 d] from FP32 products summed in FP32 over 256
+ * rows and in FP64 across them, its data row (D, d^T C_D^-1 d) summed in FP64; the
+ * factorisation, the solves and E_D (from the residuals of the masked pixels), E_S in FP64.
+ * glad_loglike_grad, glad_model_image and glad_loglike_static refuse contexts or systems with
+ * a pixelated source (GLAD_EUNSUPPORTED); glad_pixsrc returns the search's result.
  */
 typedef struct glad_system_desc {
   int nx, ny, ss;
@@ -166,6 +188,11 @@ typedef struct glad_system_desc {
   int distance_mode;               /* 0: H0 = theta[19]; 1: D_d = theta[21], D_dt,int = theta[22] */
   int mass_class;                  /* 0 EPL, 1 composite (see above) */
   double ll_wc;                    /* composite class: w_c of the first Chameleon [arcsec] */
+  int src_pix;                     /* 0 Sersic source, 1 pixelated source (see above) */
+  int spx_nx, spx_ny;              /* pixelated source: grid pixels along x and y */
+  double spx_x0, spx_x1, spx_y0, spx_y1;  /* its extent on the source plane [arcsec] */
+  double spx_lam_lo, spx_lam_hi;   /* regularisation search range (0, 0: 1e-6, 1e6) */
+  int spx_iters;                   /* at most this many evidence evaluations (0: 40) */
 } glad_system_desc;
 
 typedef struct glad_ctx glad_ctx;
@@ -270,6 +297,17 @@ int glad_tuning(glad_ctx *ctx, int *jam_code, int *adj_ept);
  * optionally + 100000 for the persistent form; adj_ept 2 or 4).  GLAD_EINVAL for other
  * values. */
 glad_status glad_set_tuning(glad_ctx *ctx, int jam_code, int adj_ept);
+
+/* The pixelated-source reconstruction of a batch (the systems with src_pix 1; other samples
+ * are left untouched): lam [dev, float64 B] the regularisation that maximises the evidence,
+ * lnP [dev, float64 B] the log-evidence there, s [dev, float64 B * 4624] (row b holds sample
+ * b's s_MP, spx_nx * spx_ny values, grid row-major from (spx_x0, spx_y0)) or NULL.
+ * Arguments and errors as glad_loglike; the arrays of invalid samples are not written. */
+glad_status glad_pixsrc(glad_ctx *ctx, const int *sys_id, const double *theta, int B,
+                        double *lam, double *lnP, double *s, void *stream);
+/* Cholesky factorisations of F + lambda C run since the last call (each evidence evaluation
+ * of the regularisation search is one), and reset the count. */
+unsigned long long glad_pix_factorizations(glad_ctx *ctx);
 
 /* Precision of the forward pass (Sect. 3: the paper computes in FP64 throughout).
  * mode 0 (the default): FP32 bulk -- ray shooting, light, PSF blurring, the Jeans sums -- with

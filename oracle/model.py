@@ -296,7 +296,8 @@ def build_system(base, theta_true, noise):
     s["img_xy"] = img
     s["dt_obs"] = np.zeros(len(img) - 1)
     s["dt_sig"] = np.ones(len(img) - 1)
-    ev = evaluate(theta_true, s)
+    # the data come from the Sersic source; a pixelated-source system then fits them
+    ev = evaluate(theta_true, dict(s, src_pix=0))
     assert ev["status"] == ST_OK, ev["status"]
     m = ev["image"]
     s["data"] = (m + np.asarray(s["sigma"], np.float64) * noise["img"]).astype(np.float32)

@@ -36,6 +36,9 @@ class SystemDesc(C.Structure):
         ("sheet", C.c_int), ("sheet_rc", C.c_double), ("sheet_rt", C.c_double),
         ("sheet_n", C.c_int), ("sheet_rmin", C.c_double), ("sheet_rmax", C.c_double),
         ("distance_mode", C.c_int), ("mass_class", C.c_int), ("ll_wc", C.c_double),
+        ("src_pix", C.c_int), ("spx_nx", C.c_int), ("spx_ny", C.c_int),
+        ("spx_x0", C.c_double), ("spx_x1", C.c_double), ("spx_y0", C.c_double), ("spx_y1", C.c_double),
+        ("spx_lam_lo", C.c_double), ("spx_lam_hi", C.c_double), ("spx_iters", C.c_int),
     ]
 
 
@@ -56,6 +59,8 @@ SIGNATURES = {
     "glad_set_tuning": (C.c_int, [_p, C.c_int, C.c_int]),
     "glad_set_negligible": (C.c_int, [_p, C.c_int]),
     "glad_set_precision": (C.c_int, [_p, C.c_int]),
+    "glad_pixsrc": (C.c_int, [_p, _p, _p, C.c_int, _p, _p, _p, _p]),
+    "glad_pix_factorizations": (C.c_ulonglong, [_p]),
     "glad_jam_evaluations": (C.c_int, [_p, C.POINTER(C.c_ulonglong), C.POINTER(C.c_ulonglong)]),
     "glad_enfw_cse": (C.c_int, [C.c_int, _d, _d, _d]),
     "glad_last_error": (C.c_char_p, []),

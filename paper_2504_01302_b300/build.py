@@ -7,7 +7,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libglad.so")
 SOURCES = ["glad_host.cu", "k_prep.cu", "k_lens.cu", "k_jam.cu", "k_grad.cu", "glad_static.cu", "glad_tune.cu",
-           "k_sph.cu", "k_sph_grad.cu", "glad_cse.cu"]
+           "k_sph.cu", "k_sph_grad.cu", "glad_cse.cu", "k_pixsrc.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-shared"]

@@ -159,6 +159,17 @@ glad_status validate(const glad_system_desc &d, int idx) {
     const double lo = d.sheet_rmin > 0 ? d.sheet_rmin : 0.1, hi = d.sheet_rmax > 0 ? d.sheet_rmax : 1000.0;
     REQ(d.sheet_rmin >= 0 && d.sheet_rmax >= 0 && hi > lo, "bad sheet MGE range", idx);
   }
+  REQ(d.src_pix == 0 || d.src_pix == 1, "src_pix must be 0 or 1", idx);
+  if (d.src_pix) {
+    REQ(d.spx_nx >= 3 && d.spx_ny >= 3, "source grid needs >= 3 pixels along x and y", idx);
+    REQ(d.spx_x1 > d.spx_x0 && d.spx_y1 > d.spx_y0, "bad source grid extent", idx);
+    REQ((d.spx_lam_lo == 0 && d.spx_lam_hi == 0) || (d.spx_lam_lo > 0 && d.spx_lam_hi > d.spx_lam_lo),
+        "regularisation range needs 0 < spx_lam_lo < spx_lam_hi (or both 0)", idx);
+    REQ(d.spx_iters >= 0 && d.spx_iters <= 200, "spx_iters must be in [0, 200]", idx);
+    int nm = 0;
+    for (int i = 0; i < d.nx * d.ny; ++i) nm += d.mask[i] != 0;
+    REQ(nm > 0, "pixelated source needs a non-empty mask", idx);
+  }
 #undef REQ
 #define SUP(cond, ...) \
   if (!(cond)) return fail(GLAD_EUNSUPPORTED, "system %d: " __VA_ARGS__)
@@ -181,6 +192,11 @@ glad_status validate(const glad_system_desc &d, int idx) {
   SUP(nl <= GLAD_MAX_LIGHT, "tracer Gaussians > %d", idx, GLAD_MAX_LIGHT);
   for (int i = 0; i < d.kx * d.ky; ++i)
     if (d.bins[i] >= d.n_bins) return fail(GLAD_EINVAL, "system %d: bin index >= n_bins", idx);
+  if (d.src_pix) {
+    SUP((long long)d.spx_nx * d.spx_ny <= GLAD_MAX_SRCPIX, "source grid > %d pixels", idx,
+        GLAD_MAX_SRCPIX);
+    SUP(d.ss <= 4, "pixelated source with more than 4 x 4 rays per pixel", idx);
+  }
   if (d.jam_align == 1) {
     const int nr = d.sph_nr ? d.sph_nr : SPH_DEFAULT_NR, nw = d.sph_nw ? d.sph_nw : SPH_DEFAULT_NW;
     SUP(nr * nw <= GLAD_SPH_MAX_GRID, "sph_nr * sph_nw > %d", idx, GLAD_SPH_MAX_GRID);
@@ -488,6 +504,70 @@ glad_status build_system(int idx, const glad_system_desc &d, SysHost &sh, SysDev
     sd.sph_u = upload(sh, su.data(), su.size());
     sd.sph_wu = upload(sh, sw.data(), sw.size());
   }
+  // pixelated source: the mask's pixel list, C = H^T H (H: second differences along x and y,
+  // zero outside the grid) and ln det C by a banded Cholesky (half-bandwidth 2 nx), and the
+  // evidence's lambda-free constant
+  sd.src_pix = d.src_pix;
+  if (d.src_pix) {
+    const int gx = d.spx_nx, gy = d.spx_ny, ns = gx * gy;
+    sd.spx_nx = gx;
+    sd.spx_ny = gy;
+    sd.spx_ns = ns;
+    sd.spx_x0 = (float)d.spx_x0;
+    sd.spx_y0 = (float)d.spx_y0;
+    sd.spx_idx = (float)(gx / (d.spx_x1 - d.spx_x0));
+    sd.spx_idy = (float)(gy / (d.spx_y1 - d.spx_y0));
+    sd.spx_iters = d.spx_iters ? d.spx_iters : SPX_DEFAULT_ITERS;
+    sd.spx_tlo = log(d.spx_lam_lo > 0 ? d.spx_lam_lo : 1e-6);
+    sd.spx_thi = log(d.spx_lam_hi > 0 ? d.spx_lam_hi : 1e6);
+    std::vector<int> ml;
+    double sum_lninv = 0.0;
+    for (int i = 0; i < npix; ++i)
+      if (d.mask[i]) {
+        ml.push_back(i);
+        sum_lninv -= log((double)d.sigma[i]);
+      }
+    sd.n_mask = (int)ml.size();
+    sd.mask_list = upload(sh, ml.data(), ml.size());
+    std::vector<double> C((size_t)ns * ns, 0.0);
+    for (int i = 0; i < gy; ++i)
+      for (int j = 0; j < gx; ++j) {
+        const int p = i * gx + j;
+        for (int dir = 0; dir < 2; ++dir) {
+          // one row of H: -2 at p, +1 at the neighbours along the direction inside the grid
+          int idx3[3] = {p, -1, -1};
+          double h3[3] = {-2.0, 1.0, 1.0};
+          if (dir == 0) {
+            if (j > 0) idx3[1] = p - 1;
+            if (j + 1 < gx) idx3[2] = p + 1;
+          } else {
+            if (i > 0) idx3[1] = p - gx;
+            if (i + 1 < gy) idx3[2] = p + gx;
+          }
+          for (int u = 0; u < 3; ++u)
+            for (int v = 0; v < 3; ++v)
+              if (idx3[u] >= 0 && idx3[v] >= 0) C[(size_t)idx3[u] * ns + idx3[v]] += h3[u] * h3[v];
+        }
+      }
+    const int bw = 2 * gx;
+    std::vector<double> Lc((size_t)ns * ns, 0.0);
+    double logdetC = 0.0;
+    for (int jj = 0; jj < ns; ++jj) {
+      double dsum = C[(size_t)jj * ns + jj];
+      for (int k = std::max(0, jj - bw); k < jj; ++k) dsum -= Lc[(size_t)jj * ns + k] * Lc[(size_t)jj * ns + k];
+      if (!(dsum > 0.0)) return fail(GLAD_EINVAL, "system %d: curvature matrix not positive definite", idx);
+      const double ljj = sqrt(dsum);
+      Lc[(size_t)jj * ns + jj] = ljj;
+      logdetC += 2.0 * log(ljj);
+      for (int ii = jj + 1; ii < std::min(ns, jj + bw + 1); ++ii) {
+        double t = C[(size_t)ii * ns + jj];
+        for (int k = std::max(0, ii - bw); k < jj; ++k) t -= Lc[(size_t)ii * ns + k] * Lc[(size_t)jj * ns + k];
+        Lc[(size_t)ii * ns + jj] = t / ljj;
+      }
+    }
+    sd.spx_C = upload(sh, C.data(), C.size());
+    sd.spx_const = 0.5 * logdetC - 0.5 * sd.n_mask * log(2.0 * PI_D) + sum_lninv;
+  }
   sd.has_bh = d.has_bh;
   sd.bh_sigma = d.bh_sigma;
   sd.L_scale = d.L_scale;
@@ -557,6 +637,11 @@ glad_status ws_ensure(glad_ctx *c, int B) {
             ws_alloc(w, w.d.evals, 2) && ws_alloc(w, w.d.sph_mt, b * c->max_smg) &&
             ws_alloc(w, w.d.sph_mrz, b * c->max_smg) && ws_alloc(w, w.d.sph_tr, b * c->max_light) &&
             ws_alloc(w, w.d.sgrid, b * c->max_sgrid);
+  // the pixelated source's ray entries and arcs, for contexts with such systems
+  if (ok && c->n_pix)
+    ok = ws_alloc(w, w.d.pix_Li, b * c->max_lpix) && ws_alloc(w, w.d.pix_Lw, b * c->max_lpix) &&
+         ws_alloc(w, w.d.pix_dres, b * c->max_pix);
+  w.d.max_lpix = c->max_lpix;
   // the FP64 forward modes' arrays, only once such a mode has been asked for
   if (ok && c->tune.prec > 0)
     ok = ws_alloc(w, w.d.lp64, b) && ws_alloc(w, w.d.img64, b * c->max_pix) &&
@@ -602,7 +687,11 @@ glad_status forward(glad_ctx *c, const int *sys_id, const double *theta, int B, 
 // the combination.
 glad_status full_path(glad_ctx *c, const int *sys_id, const double *theta, int B, cudaStream_t st,
                       double *logL, int *sample_status, double *terms, double *grad) {
+  if (grad && c->n_pix)
+    return fail(GLAD_EUNSUPPORTED, "glad_loglike_grad: no gradient for pixelated-source systems");
   glad_status s = ws_ensure(c, B);
+  if (s == GLAD_OK && c->n_pix && pixsrc_ws_ensure(c, B) != cudaSuccess)
+    s = fail(GLAD_ENOMEM, "pixelated-source workspace for B=%d does not fit on the device", B);
   if (s != GLAD_OK) return s;
   cudaError_t e;
   c->ws.d.neg_mode = c->tune.neg_mode;
@@ -625,6 +714,8 @@ glad_status full_path(glad_ctx *c, const int *sys_id, const double *theta, int B
     e = GLAD_PROF(c, side, KID_IMAGE_CONV,
                   launch_lens(c, sys_id, B, nullptr, side, grad ? grad_resid_buffer(c) : nullptr));
   if (e == cudaSuccess && grad) e = launch_grad_lens(c, sys_id, B, grad, side);
+  if (e == cudaSuccess && c->n_pix && !grad)
+    e = launch_pixsrc(c, sys_id, B, side, nullptr, nullptr, nullptr);
   if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, side);
   // dynamics, high priority
   if (e == cudaSuccess) e = launch_dyn_tables(c, sys_id, B, dy);
@@ -655,7 +746,7 @@ glad_status full_path(glad_ctx *c, const int *sys_id, const double *theta, int B
 const char *kKernelNames[KID_N] = {
     "k_prep", "k_table", "k_image+k_conv", "k_jam", "k_kin_finalize", "k_combine",
     "k_grad_lens", "k_jam_fwd_grad", "k_jam_adjoint", "k_grad_chain", "k_sph_coef+k_sph_grid",
-    "k_sph_los", "k_sph_adjoint"};
+    "k_sph_los", "k_sph_adjoint", "k_pix_operator", "k_pix_evidence"};
 
 }  // namespace
 
@@ -804,6 +895,12 @@ glad_status glad_create(const glad_system_desc *sys, int n_sys, glad_ctx **out) 
     } else {
       ++c->n_cyl;
     }
+    if (d.src_pix) {
+      ++c->n_pix;
+      c->max_ns = std::max(c->max_ns, d.spx_ns);
+      c->max_nd = std::max(c->max_nd, d.n_mask);
+      c->max_lpix = std::max(c->max_lpix, d.npix * 4 * d.ss * d.ss);
+    }
   }
   if (cudaMalloc(&c->d_sys, sizeof(SysDev) * n_sys) != cudaSuccess ||
       cudaMemcpy(c->d_sys, c->h_sysdev.data(), sizeof(SysDev) * n_sys, cudaMemcpyHostToDevice) !=
@@ -845,6 +942,7 @@ void glad_destroy(glad_ctx *c) {
   cudaDeviceSynchronize();
   ws_free(c->ws);
   grad_ws_free(c);
+  pixsrc_ws_free(c);
   for (auto &s : c->sys)
     for (void *p : s.allocs)
       if (p) cudaFree(p);
@@ -887,8 +985,32 @@ glad_status glad_model_image(glad_ctx *c, int sys, const double *theta, float *i
   g_err.clear();
   if (!c || !theta || !image || sys < 0 || sys >= c->n_sys)
     return fail(GLAD_EINVAL, "glad_model_image: bad arguments");
+  if (c->h_sysdev[sys].src_pix)
+    return fail(GLAD_EUNSUPPORTED, "glad_model_image: system %d has a pixelated source", sys);
   return forward(c, c->d_one_sys + sys, theta, 1, (cudaStream_t)stream, image, nullptr);
 }
+
+glad_status glad_pixsrc(glad_ctx *c, const int *sys_id, const double *theta, int B, double *lam,
+                        double *lnP, double *s_out, void *stream) {
+  g_err.clear();
+  if (!c || !sys_id || !theta || B < 1) return fail(GLAD_EINVAL, "glad_pixsrc: bad arguments");
+  if (!c->n_pix) return fail(GLAD_EINVAL, "glad_pixsrc: no system with a pixelated source");
+  cudaStream_t st = (cudaStream_t)stream;
+  glad_status s = ws_ensure(c, B);
+  if (s != GLAD_OK) return s;
+  if (pixsrc_ws_ensure(c, B) != cudaSuccess)
+    return fail(GLAD_ENOMEM, "pixelated-source workspace for B=%d does not fit on the device", B);
+  c->ws.d.neg_mode = c->tune.neg_mode;
+  c->ws.d.prec = c->tune.prec;
+  cudaError_t e = cudaMemsetAsync(c->ws.d.terms, 0, sizeof(double) * 4 * B, st);
+  if (e == cudaSuccess) e = GLAD_PROF(c, st, KID_PREP, launch_prep(c, sys_id, theta, B, st));
+  if (e == cudaSuccess) e = GLAD_PROF(c, st, KID_IMAGE_CONV, launch_lens(c, sys_id, B, nullptr, st, nullptr));
+  if (e == cudaSuccess) e = launch_pixsrc(c, sys_id, B, st, lam, lnP, s_out);
+  if (e != cudaSuccess) return fail(GLAD_ECUDA, "launch failed: %s", cudaGetErrorString(e));
+  return GLAD_OK;
+}
+
+unsigned long long glad_pix_factorizations(glad_ctx *c) { return c ? pixsrc_factorizations(c) : 0; }
 
 glad_status glad_vrms(glad_ctx *c, int sys, const double *theta, float *vrms, void *stream) {
   g_err.clear();

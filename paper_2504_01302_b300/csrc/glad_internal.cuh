@@ -22,6 +22,8 @@
 #define SPH_DEFAULT_NR 128      // default polar grid and line-of-sight rule of that model
 #define SPH_DEFAULT_NW 8
 #define SPH_DEFAULT_NLOS 32
+#define GLAD_MAX_SRCPIX 4624    // source pixels of a pixelated-source grid (68 x 68)
+#define SPX_DEFAULT_ITERS 40    // evidence evaluations of the regularisation search
 
 // ---------------------------------------------------------------------------
 // device-resident description of one system (all pointers are device memory)
@@ -99,6 +101,16 @@ struct SysDev {
   int jam_align, sph_nr, sph_nw, sph_nlos;
   double sph_r_lo, sph_r_end, sph_lr0, sph_dlr;
   const double *sph_u, *sph_wu;             // [n_mass_tot * n_gl]
+  // pixelated source (src_pix 1, Sect. 3.1.1): spx_nx x spx_ny pixels of size spx_dx x spx_dy
+  // from (spx_x0, spx_y0) on the source plane; the fit runs over the n_mask pixels listed in
+  // mask_list; spx_C = H^T H the curvature regularisation [spx_ns^2]; the evidence's
+  // lambda-free constant spx_const = ln det C / 2 - (N_d / 2) ln 2 pi + sum ln(1 / sigma);
+  // the search over ln lambda in [spx_tlo, spx_thi] takes at most spx_iters evaluations
+  int src_pix, spx_nx, spx_ny, spx_ns, n_mask, spx_iters;
+  float spx_x0, spx_y0, spx_idx, spx_idy;   // origin and inverse pixel sizes
+  const int *mask_list;                     // [n_mask] pixel indices, ascending
+  const double *spx_C;                      // [spx_ns * spx_ns]
+  double spx_const, spx_tlo, spx_thi;
 };
 
 // per-sample lensing parameters, written by the prep kernel: FP32 (LensP) for the default
@@ -182,6 +194,13 @@ struct WsDev {
   double4_16a *tab64;          // [B*max_ent]
   double *I0d;                 // [B*max_light]
   int prec;                    // 0 default, 1 FP64 lensing, 2 FP64 lensing and pair sum
+  // pixelated source (null without such systems): each image pixel's 4 ss^2 bilinear source
+  // entries (index, weight / ss^2) written by k_image, and the arcs data - B (lens light)
+  // written by the PSF kernels
+  int *pix_Li;                 // [B*max_lpix]
+  float *pix_Lw;               // [B*max_lpix]
+  float *pix_dres;             // [B*max_pix]
+  int max_lpix;                // npix * 4 ss^2 of the largest pixelated-source system
 };
 
 struct Workspace {
@@ -192,6 +211,7 @@ struct Workspace {
 };
 
 struct GradWs;  // gradient workspace (k_grad.cu)
+struct PixWs;   // pixelated-source workspace (k_pixsrc.cu)
 
 struct glad_ctx {
   int n_sys = 0;
@@ -203,7 +223,11 @@ struct glad_ctx {
   int max_img_tiles = 0, max_sky_tiles = 0, max_tab_blocks = 0;
   int n_cyl = 0, n_sph = 0;        // systems with the cylindrically / spherically aligned model
   int max_sgrid = 0, max_smg = 0;  // largest polar grid and (mass Gaussian, u node) count
+  int n_pix = 0;                    // systems with a pixelated source
+  int max_ns = 0, max_nd = 0;       // their largest source grid and mask
+  int max_lpix = 0;                 // their largest npix * 4 ss^2 (bilinear ray entries)
   Workspace ws;
+  PixWs *pws = nullptr;             // pixelated-source workspace (k_pixsrc.cu)
   GradWs *gws = nullptr;
   // launch shapes chosen by glad_autotune (defaults until it runs)
   struct Tune {
@@ -237,7 +261,7 @@ struct glad_ctx {
 enum {
   KID_PREP = 0, KID_TABLE, KID_IMAGE_CONV, KID_JAM, KID_KIN, KID_COMBINE,
   KID_GRAD_LENS, KID_GRAD_JAM_FWD, KID_GRAD_JAM_ADJ, KID_GRAD_CHAIN, KID_SPH_GRID, KID_SPH_LOS,
-  KID_GRAD_SPH, KID_N
+  KID_GRAD_SPH, KID_PIX_OP, KID_PIX_EV, KID_N
 };
 
 // record an event pair around `call` when profiling is on
@@ -287,6 +311,13 @@ void cse_table(const double **a, const double **s);
 cudaError_t launch_dyn_tables(glad_ctx *c, const int *sys_id, int B, cudaStream_t st);
 cudaError_t launch_dyn_sums(glad_ctx *c, const int *sys_id, int B, cudaStream_t st);
 void set_conv_smem_limit();
+// pixelated source (k_pixsrc.cu): response rows, Gram matrix, then the evidence search over
+// the regularisation; lam/lnP/s outputs (any may be null) for glad_pixsrc
+cudaError_t launch_pixsrc(glad_ctx *c, const int *sys_id, int B, cudaStream_t st,
+                          double *lam_out, double *lnP_out, double *s_out);
+cudaError_t pixsrc_ws_ensure(glad_ctx *c, int B);
+void pixsrc_ws_free(glad_ctx *c);
+unsigned long long pixsrc_factorizations(glad_ctx *c);
 bool jam_shape_supported(int pts, int minb, int unr, int form);
 int jam_shape_list(int (*out)[4], int cap);
 

@@ -81,6 +81,9 @@ extern "C" glad_status glad_loglike_static(glad_ctx *c, const int *sys_id, const
   glad_set_error(GLAD_OK, "");  // a successful call leaves glad_last_error() empty
   if (!c || !sys_id || !theta || !logL || !sample_status || B < 1)
     return glad_set_error(GLAD_EINVAL, "glad_loglike_static: bad arguments");
+  if (c->n_pix)
+    return glad_set_error(GLAD_EUNSUPPORTED, "glad_loglike_static: pixelated-source systems need "
+                                             "the allocating entry points");
   WsDev w{};
   const size_t need = carve(c, B, nullptr, &w);
   if (need > kStaticScratchBytes) {

@@ -179,11 +179,35 @@ __global__ void __launch_bounds__(LENS_THREADS) k_image(const SysDev *__restrict
         ax = L.lam * ax + om * dx;
         ay = L.lam * ay + om * dy;
       }
-      // source at beta
-      const T bx = x - ax - L.src_x, by = y - ay - L.src_y;
-      const T xs = G.c * bx + G.s * by, ys = -G.s * bx + G.c * by;
-      const T Rs2 = (xs * xs + ys * ys / (G.q * G.q)) * (L.src_Rei * L.src_Rei);
-      T v = sersic_f(Rs2, L.src_Ie, L.src_ninv, L.src_bn);
+      T v = T(0.0);
+      if (S.src_pix) {
+        // pixelated source: the ray's bilinear entries into the grid (weight / ss^2; zero
+        // outside the span of the pixel centres) for the response f = B L
+        T u = (x - ax - (T)S.spx_x0) * (T)S.spx_idx - T(0.5);
+        T w = (y - ay - (T)S.spx_y0) * (T)S.spx_idy - T(0.5);
+        u = fmin(fmax(u, T(-2.0)), (T)(S.spx_nx + 2));
+        w = fmin(fmax(w, T(-2.0)), (T)(S.spx_ny + 2));
+        const T fu = floor(u), fw = floor(w);
+        const int j0 = (int)fu, i0 = (int)fw;
+        const bool in = j0 >= 0 && j0 + 1 < S.spx_nx && i0 >= 0 && i0 + 1 < S.spx_ny;
+        const T tu = u - fu, tv = w - fw, sc = in ? T(1.0) / (T)(ss * ss) : T(0.0);
+        const int e0 = in ? i0 * S.spx_nx + j0 : 0;
+        const size_t o = (size_t)b * ws.max_lpix + ((size_t)p * ss * ss + my * ss + mx) * 4;
+        ws.pix_Li[o] = e0;
+        ws.pix_Li[o + 1] = e0 + 1;
+        ws.pix_Li[o + 2] = e0 + S.spx_nx;
+        ws.pix_Li[o + 3] = e0 + S.spx_nx + 1;
+        ws.pix_Lw[o] = (float)(sc * (T(1.0) - tu) * (T(1.0) - tv));
+        ws.pix_Lw[o + 1] = (float)(sc * tu * (T(1.0) - tv));
+        ws.pix_Lw[o + 2] = (float)(sc * (T(1.0) - tu) * tv);
+        ws.pix_Lw[o + 3] = (float)(sc * tu * tv);
+      } else {
+        // source at beta
+        const T bx = x - ax - L.src_x, by = y - ay - L.src_y;
+        const T xs = G.c * bx + G.s * by, ys = -G.s * bx + G.c * by;
+        const T Rs2 = (xs * xs + ys * ys / (G.q * G.q)) * (L.src_Rei * L.src_Rei);
+        v = sersic_f(Rs2, L.src_Ie, L.src_ninv, L.src_bn);
+      }
       // lens light (same centre and PA as the mass): Sersic, or Chameleon in the composite class
       if (L.mclass == 1) {
         for (int c = 0; c < S.n_lcomp && c < 4; ++c) {
@@ -245,6 +269,9 @@ __global__ void __launch_bounds__(CONV_TX *CONV_TY) k_conv(const SysDev *__restr
     const int o = oi * S.nx + oj;
     if (image_out) {
       image_out[o] = (float)m;
+    } else if (S.src_pix) {
+      // the arcs left by the lens light, fitted by the pixelated source (k_pixsrc.cu)
+      ws.pix_dres[(size_t)b * max_pix + o] = (float)((double)S.data[o] - m);
     } else {
       const double r = ((double)S.data[o] - m) * S.wgt[o];
       chi = r * r;
@@ -342,6 +369,8 @@ __global__ void __launch_bounds__(CONV_TX *CONV_TY) k_conv_r(const SysDev *__res
     const int o = oi * S.nx + oj;
     if (image_out) {
       image_out[o] = (float)m;
+    } else if (S.src_pix) {
+      ws.pix_dres[(size_t)b * max_pix + o] = (float)((double)S.data[o] - m);
     } else {
       const double rr = ((double)S.data[o] - m) * S.wgt[o];
       chi += rr * rr;

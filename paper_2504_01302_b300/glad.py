@@ -95,6 +95,12 @@ class GladContext:
         d.distance_mode = int(s.get("distance_mode", 0))
         d.mass_class = int(s.get("mass_class", 0))
         d.ll_wc = float(s.get("ll_wc", 0.0))
+        d.src_pix = int(s.get("src_pix", 0))
+        if d.src_pix:
+            d.spx_nx, d.spx_ny = (int(v) for v in s["spx_n"])
+            d.spx_x0, d.spx_x1, d.spx_y0, d.spx_y1 = (float(v) for v in s["spx_box"])
+            d.spx_lam_lo, d.spx_lam_hi = (float(v) for v in s.get("spx_lam", (0.0, 0.0)))
+            d.spx_iters = int(s.get("spx_iters", 0))
 
     # ------------------------------------------------------------------ calls
     def _check_theta(self, theta, sys_id):
@@ -146,6 +152,25 @@ class GladContext:
         v = torch.empty(self.n_bins[sys], dtype=torch.float32, device=theta.device)
         _lib.check(self.lib.glad_vrms(self.handle, sys, _dptr(theta), _dptr(v), _stream()), "glad_vrms")
         return v
+
+    def pixsrc(self, theta, sys_id=None, want_s=False):
+        """Pixelated-source reconstruction (glad_pixsrc): the regularisation lambda that
+        maximises the evidence [B], the log-evidence there [B] and, with want_s, s_MP
+        [B, 4624] (row b: the first spx_nx * spx_ny entries)."""
+        theta, sys_id, B = self._check_theta(theta, sys_id)
+        dev = theta.device
+        lam = torch.full((B,), float("nan"), dtype=torch.float64, device=dev)
+        lnP = torch.full((B,), float("nan"), dtype=torch.float64, device=dev)
+        s = torch.zeros(B, 4624, dtype=torch.float64, device=dev) if want_s else None
+        _lib.check(self.lib.glad_pixsrc(self.handle, _dptr(sys_id), _dptr(theta), B, _dptr(lam),
+                                        _dptr(lnP), _dptr(s) if want_s else None, _stream()),
+                   "glad_pixsrc")
+        return (lam, lnP, s) if want_s else (lam, lnP)
+
+    def pix_factorizations(self):
+        """Cholesky factorisations of F + lambda C since the last call (glad_pix_factorizations)."""
+        torch.cuda.synchronize()
+        return int(self.lib.glad_pix_factorizations(self.handle))
 
     def autotune(self, theta, sys_id=None, with_grad=False):
         """Time the JAM launch shapes on this batch and keep the fastest (glad_autotune)."""

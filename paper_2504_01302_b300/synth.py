@@ -260,6 +260,14 @@ def draw_prior_sheet(rng, B: int, lam_hi: float = 1.5) -> np.ndarray:
 # workloads
 # ---------------------------------------------------------------------------
 
+def arc_mask(n_px: int, pix: float, r_in: float, r_out: float) -> np.ndarray:
+    """Pixels whose centres lie in the annulus r_in <= r < r_out around the image centre (the
+    arcs that a pixelated source is fitted to)."""
+    c = (np.arange(n_px) - 0.5 * (n_px - 1)) * pix
+    r = np.hypot(c[None, :], c[:, None])
+    return ((r >= r_in) & (r < r_out)).astype(np.uint8)
+
+
 def workload_systems(w: int, small: bool = False):
     """Fixed parts of the mock systems of workload w (0..4) and the batch size.
 
@@ -277,17 +285,27 @@ def workload_systems(w: int, small: bool = False):
     8: workload 1's system as the composite mass class (two Chameleons scaled by Upsilon_*,
        the elliptical NFW halo, the black hole) with the dPIE sheet in distance mode 1: the
        paper's own joint model (Sect. 3.3), B=256
+    9: workload 1's system with the pixelated source (Sect. 3.1.1): a 30 x 30 grid over
+       +-0.6" around the source, fitted to the arcs in the annulus 0.9" - 2.5" (N_d = 6,840
+       pixels, N_s = 900: Table 1's O(10^4) and O(10^3)), B=148 (one sample per SM)
     """
-    rng = np.random.Generator(np.random.PCG64(1000 + {5: 1, 6: 4, 7: 1, 8: 1}.get(w, w)))
+    rng = np.random.Generator(np.random.PCG64(1000 + {5: 1, 6: 4, 7: 1, 8: 1, 9: 1}.get(w, w)))
     if w == 0:
         s = base_system("w0", n_img_px=64, ss=1, psf_k=11, sky=32, kss=1, n_mass=10,
                         n_light=10, n_gl=32, n_bins=20, bins="annular", rng=rng,
                         has_bh=False, n_sis=0, second_light=False)
         return [s], 1
-    if w in (1, 2, 5, 7, 8):
+    if w in (1, 2, 5, 7, 8, 9):
         s = base_system("w1", n_img_px=200, ss=2, psf_k=21, sky=60, kss=4, n_mass=20,
                         n_light=10, n_gl=32, n_bins=50, bins="voronoi", rng=rng,
                         has_bh=True, n_sis=1, second_light=True)
+        if w == 9:
+            t = theta_truth(1)
+            c = (float(t[IDX["x_src"]]), float(t[IDX["y_src"]]))
+            s.update(name="w9", src_pix=1, spx_n=(30, 30),
+                     spx_box=(c[0] - 0.6, c[0] + 0.6, c[1] - 0.6, c[1] + 0.6),
+                     mask=arc_mask(s["nx"], s["pix"], 0.9, 2.5))
+            return [s], 148
         if w == 5:
             s.update(name="w5", jam_align=1, sph_nr=128, sph_nw=8, sph_nlos=32)
         if w == 7:

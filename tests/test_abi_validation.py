@@ -28,6 +28,13 @@ def _set(key, value):
     return m
 
 
+def _pix(**kw):
+    def m(s):
+        s.update(src_pix=1, spx_n=(10, 10), spx_box=(-0.5, 0.5, -0.5, 0.5))
+        s.update(**kw)
+    return m
+
+
 def _sph(**kw):
     def m(s):
         s.update(jam_align=1, **kw)
@@ -63,6 +70,13 @@ def _sph(**kw):
     (lambda s: s.update(sheet=1, sheet_n=1), GLAD_EINVAL, "sheet_n must be"),
     (lambda s: s.update(sheet=1, sheet_rmin=10.0, sheet_rmax=1.0), GLAD_EINVAL, "bad sheet MGE range"),
     (lambda s: s.update(sheet=1, sheet_n=120), GLAD_EUNSUPPORTED, "n_mge_mass + sheet Gaussians >"),
+    (_pix(src_pix=2), GLAD_EINVAL, "src_pix must be 0 or 1"),
+    (_pix(spx_n=(2, 10)), GLAD_EINVAL, "source grid needs >= 3 pixels"),
+    (_pix(spx_box=(0.5, -0.5, -0.5, 0.5)), GLAD_EINVAL, "bad source grid extent"),
+    (_pix(spx_lam=(1.0, 0.5)), GLAD_EINVAL, "regularisation range"),
+    (_pix(spx_iters=500), GLAD_EINVAL, "spx_iters must be"),
+    (_pix(mask=np.zeros((48, 48), np.uint8)), GLAD_EINVAL, "non-empty mask"),
+    (_pix(spx_n=(70, 70)), GLAD_EUNSUPPORTED, "source grid > 4624"),
 ])
 def test_create_rejects_invalid_descriptors(mutate, status, words):
     msg = _create(mutate)
@@ -86,5 +100,7 @@ def test_entry_points_reject_null_context_and_empty_batch():
     assert lib.glad_loglike_grad(None, p, p, 4, p, p, p, None, None) == GLAD_EINVAL
     assert lib.glad_set_negligible(None, 1) == GLAD_EINVAL
     assert lib.glad_set_tuning(None, 4052, 2) == GLAD_EINVAL
+    assert lib.glad_pixsrc(None, p, p, 4, p, p, None, None) == GLAD_EINVAL
+    assert lib.glad_pix_factorizations(None) == 0
     assert lib.glad_create(None, 1, C.byref(C.c_void_p())) == GLAD_EINVAL
     assert "glad_create" in lib.glad_last_error().decode()

@@ -1,0 +1,145 @@
+"""Pixelated source reconstruction on the GPU (Sect. 3.1.1, Eqs. s_MP and evi_ext) against the
+oracle (oracle/pixsrc.py): the optimal regularisation, the log-evidence there, s_MP, and the
+joint logL whose image term the evidence becomes, on the small all-features system with a
+square grid and with a ragged one (13 x 11), for the 48^2 and 64^2 systems (PSF sides 7 and
+11), in a batch mixed with Sersic-source samples and invalid ones, for a sweep over three grid
+resolutions of the same data in one context, and at the RXJ1131-scale workload on a sampled
+sample.  Tolerances: ln P and logL 0.05 + 5e-6 |ln P| (the FP32 rays leave ~1e-7 arcsec in
+beta, ~1e-6 of a bilinear weight over a source pixel, so a poor fit's data term moves by ~1e-6
+of itself, as for the Sersic source, tests/systems.logl_tol), and 0.05 absolute with the rays
+in FP64 (precision mode 1); the optimum within 0.05 in ln lambda; s_MP at the GPU's lambda
+within 1e-3 of max |s| of the oracle's solution at the same lambda."""
+import numpy as np
+import pytest
+
+from oracle import model, pixsrc
+from paper_2504_01302_b300 import synth
+
+from . import systems
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+I = synth.IDX
+
+
+def _th(t):
+    return torch.as_tensor(np.asarray(t, np.float64), device="cuda")
+
+
+def _ctx(sys_list):
+    from paper_2504_01302_b300.glad import GladContext
+    return GladContext(sys_list)
+
+
+def pix_system(base, n=(10, 10), half=0.45, th=None):
+    th = synth.theta_truth(1) if th is None else th
+    c = (th[I["x_src"]], th[I["y_src"]])
+    return dict(base, src_pix=1, spx_n=n, spx_box=(c[0] - half, c[0] + half, c[1] - half, c[1] + half))
+
+
+def oracle_solution_at(th, s, lam):
+    grid = pixsrc.grid_of(s)
+    m = np.asarray(s["mask"]).ravel() != 0
+    from oracle import imaging
+    ll = imaging.model_image(th, s, source=False).ravel()
+    d = np.asarray(s["data"], np.float64).ravel()[m] - ll[m]
+    sig = np.asarray(s["sigma"], np.float64).ravel()[m]
+    return pixsrc.solve(pixsrc.response(th, s, grid), d, sig, pixsrc.curvature(grid), lam)
+
+
+def lnp_tol(ref, rel=5e-6):
+    return 0.05 + rel * abs(ref)
+
+
+def check_against_oracle(ctx, s, th, sys_id=None, b=0, check_s=True, rel=5e-6):
+    lam, lnP, sg = ctx.pixsrc(_th(th), sys_id, want_s=True)
+    ev = model.evaluate(th[b], s)
+    assert ev["status"] == 0
+    got_lam, got_lnP = float(lam[b]), float(lnP[b])
+    assert abs(got_lnP - ev["lnP"]) < lnp_tol(ev["lnP"], rel), (got_lnP, ev["lnP"])
+    assert abs(np.log(got_lam) - np.log(ev["lam"])) < 0.05, (got_lam, ev["lam"])
+    if check_s:
+        s_ref, _ = oracle_solution_at(th[b], s, got_lam)
+        ns = int(np.prod(s["spx_n"]))
+        s_gpu = sg.cpu().numpy()[b, :ns]
+        assert np.max(np.abs(s_gpu - s_ref)) <= 1e-3 * np.max(np.abs(s_ref)), np.max(np.abs(s_gpu - s_ref))
+    return ev
+
+
+@pytest.fixture(scope="module")
+def small():
+    s = pix_system(systems.small_system(7))
+    return s, _ctx([s])
+
+
+def test_square_grid_against_oracle(small):
+    s, ctx = small
+    th = systems.near_truth_thetas(2, seed=201)
+    for b in range(2):
+        check_against_oracle(ctx, s, th, b=b)
+    # the evidence is the image term of logL
+    logL, st, terms = ctx.loglike(_th(th), terms=True)
+    for b in range(2):
+        ev = model.evaluate(th[b], s)
+        assert int(st[b]) == 0
+        assert abs(float(terms[b, 0]) + 2 * ev["lnP"]) < 2 * lnp_tol(ev["lnP"])
+        assert abs(float(logL[b]) - ev["logL"]) < lnp_tol(ev["logL"]), (float(logL[b]), ev["logL"])
+    assert ctx.pix_factorizations() > 0
+
+
+def test_ragged_grid_and_64px_system():
+    s = pix_system(systems.small_system(7), n=(13, 11), half=0.5)
+    check_against_oracle(_ctx([s]), s, systems.near_truth_thetas(1, seed=203))
+    sys_list, ths, _ = model.workload(0)
+    s0 = pix_system(sys_list[0], n=(12, 12), half=0.45, th=ths[0])
+    ctx = _ctx([s0])
+    check_against_oracle(ctx, s0, ths[:1])
+    # a poor fit (ln P ~ -8e4): with the rays in FP64 the evidence meets 0.05 absolute
+    ctx.set_precision(1)
+    check_against_oracle(ctx, s0, ths[:1], rel=0.0)
+
+
+def test_mixed_batch_sersic_invalid_and_grid_sweep():
+    base = systems.small_system(7)
+    sweep = [pix_system(base, n=(n, n)) for n in (8, 10, 12)]
+    ctx = _ctx([base] + sweep)
+    th = systems.near_truth_thetas(6, seed=205)
+    th[4, I["q"]] = 1.3  # outside the domain
+    sid_np = np.array([0, 1, 2, 3, 2, 0], np.int32)
+    sid = torch.as_tensor(sid_np, device="cuda")
+    logL, st, terms = ctx.loglike(_th(th), sid, terms=True)
+    st = st.cpu().numpy()
+    assert st[4] == model.ST_DOMAIN and np.isneginf(float(logL[4]))
+    # the Sersic samples are those of a context without the pixelated systems
+    ref = _ctx([base]).loglike(_th(th[[0, 5]]))[0].cpu().numpy()
+    # same kernels; FP32 shared-memory atomics of the bin sums reorder between launches
+    assert np.allclose(logL.cpu().numpy()[[0, 5]], ref, rtol=1e-6, atol=0)
+    # every grid of the sweep against the oracle
+    for b, si in ((1, 1), (2, 2), (3, 3)):
+        check_against_oracle(ctx, sweep[si - 1], th, sid, b=b, check_s=(si == 2))
+
+
+def test_refusals():
+    from paper_2504_01302_b300 import _lib
+    s = pix_system(systems.small_system(7))
+    ctx = _ctx([s])
+    th = _th(systems.near_truth_thetas(1, seed=207))
+    with pytest.raises(_lib.GladError):
+        ctx.loglike_grad(th)
+    with pytest.raises(_lib.GladError):
+        ctx.model_image(th[0])
+
+
+def test_rxj1131_scale_sampled_against_oracle():
+    sys_list, th, _ = systems.workload(9)
+    s = sys_list[0]
+    ctx = _ctx(sys_list)
+    B = 16
+    lam, lnP = ctx.pixsrc(_th(th[:B]))
+    logL, st = ctx.loglike(_th(th[:B]))
+    assert np.all(st.cpu().numpy() == 0)
+    ev = model.evaluate(th[0], s)
+    assert abs(float(lnP[0]) - ev["lnP"]) < lnp_tol(ev["lnP"]), (float(lnP[0]), ev["lnP"])
+    assert abs(float(logL[0]) - ev["logL"]) < lnp_tol(ev["logL"]), (float(logL[0]), ev["logL"])
