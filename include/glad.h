@@ -139,7 +139,7 @@ enum {
  *   ln P = -E_D - lambda E_S - ln det(F + lambda C)/2 + (N_s/2) ln lambda
  *          + ln det C / 2 - (N_d/2) ln 2 pi - ln det C_D / 2,
  * E_D = (f s_MP - d)^T C_D^-1 (f s_MP - d) / 2 and E_S = s_MP^T C s_MP / 2,
- * maximised over ln lambda in [ln spx_lam_lo, ln spx_lam_hi] by Brent's method to 1e-5 in
+ * maximised over ln lambda in [ln spx_lam_lo, ln spx_lam_hi] by Brent's method to 1e-3 in
  * ln lambda or spx_iters evaluations.  terms[0] then holds -2 ln P (so that logL is still
  * -(sum of terms)/2) and theta[8..12] are not used.  Arithmetic: rays and the response in
  * FP32; the Gram matrix [F D; D^T d^T C_D^-1 d] from FP32 products summed in FP32 over 256

@@ -16,9 +16,11 @@
 //    ln lambda; its last pass writes s_MP for the caller.  E_D + lambda E_S is stationary at
 //    s_MP, so an error in s_MP moves it only at second order; written as the difference
 //    d^T C_D^-1 d - D^T s_MP it would lose ~1e-8 of two sums that reach N_d (S/N)^2.
-// The factorisation is FP64 because the evidence needs ln det(F + lambda C) to ~1e-2 absolute
-// over N_s ~ 1e3 pivots of a matrix whose conditioning grows as lambda falls; on this GPU FP64
-// runs on the same units with or without tensor cores, so it is written as SIMT DFMA.
+// The factorisation keeps ~FP64 accuracy because the evidence needs ln det(F + lambda C) to
+// ~1e-2 absolute over N_s ~ 1e3 pivots of a matrix whose conditioning grows as lambda falls:
+// the matrix, the diagonal blocks, the panels and the solves are FP64, and the trailing update
+// (nearly all of the N_s^3/3 flops) runs in double-float on the FP32 pipes, since this GPU's
+// FP64 rate is 1/73 of its FP32 rate with or without tensor cores.
 #include <math.h>
 
 #include <algorithm>
@@ -37,7 +39,8 @@ struct PixSearch {
 struct PixDev {
   float *g;             // [B * max_nd * ldg] rows [f_q / sigma_q, d_q / sigma_q]
   double *F;            // [B * ldg * ldg] Gram matrix, lower triangle
-  double *A;            // [B * max_ns * max_ns] F + lambda C and its factor (row stride N_s)
+  double *A;            // [B * max_ns * max_ns] F + lambda C and its factor (row stride N_s),
+                        // held as double-float (hi, lo) pairs of floats
   double *y;            // [B * max_ns]
   PixSearch *srch;      // [B]
   unsigned long long *nfac;  // [1] factorisations run
@@ -53,7 +56,7 @@ struct PixWs {
 namespace {
 
 constexpr double GOLD = 0.3819660112501051;  // (3 - sqrt 5) / 2
-constexpr double TTOL = 1e-5;                // tolerance in ln lambda
+constexpr double TTOL = 1e-3;                // tolerance in ln lambda (ln P moves by ~P"/2 TTOL^2)
 
 #define PIX_F_WARPS 8
 #define PIX_THREADS 256
@@ -132,6 +135,42 @@ __device__ void brent_step(PixSearch &s, double f, int max_it) {
     s.d = GOLD * s.e;
   }
   s.u = s.x + (fabs(s.d) >= tol1 ? s.d : (s.d > 0.0 ? tol1 : -tol1));
+}
+
+// ---------------------------------------------------------------------------------------
+// Double-float arithmetic for the trailing update of the factorisation (an unevaluated sum
+// hi + lo of two FP32 numbers carries ~48 bits): B300 runs FP32 at 73x its FP64 rate, so a
+// multiply-add in ~12 FP32 operations is ~6x faster than a DFMA.  The product's rounding
+// error comes exactly from an FMA (TwoProduct), the sum's from Knuth's TwoSum; the low parts
+// are summed plainly (their rounding is ~2^-48 of the result over 32 terms).
+__device__ __forceinline__ float2 df_split(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
+
+__device__ __forceinline__ double df_val(float2 v) { return (double)v.x + (double)v.y; }
+
+// (a.x + a.y) - (hi + lo), renormalised
+__device__ __forceinline__ float2 df_sub(float2 a, float hi, float lo) {
+  const float s = __fsub_rn(a.x, hi);
+  const float v = __fsub_rn(s, a.x);
+  const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, v)), __fsub_rn(-hi, v));
+  const float l = __fadd_rn(__fsub_rn(a.y, lo), e);
+  const float h = __fadd_rn(s, l);
+  return make_float2(h, __fsub_rn(l, __fsub_rn(h, s)));
+}
+
+// (hi, lo) += a * b
+__device__ __forceinline__ void df_fma(float &hi, float &lo, float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float pe = __fmaf_rn(a.x, b.x, -p);
+  pe = __fmaf_rn(a.x, b.y, pe);
+  pe = __fmaf_rn(a.y, b.x, pe);
+  const float s = __fadd_rn(hi, p);
+  const float v = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, v)), __fsub_rn(p, v));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(pe, e));
 }
 
 // ---------------------------------------------------------------------------------------
@@ -292,16 +331,17 @@ __global__ void __launch_bounds__(PIX_THREADS) k_pix_eval(const SysDev *__restri
   const int n = S.spx_ns, ldg = pd.ldg;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const double *F = pd.F + (size_t)b * ldg * ldg;
-  double *A = pd.A + (size_t)b * pd.max_ns * pd.max_ns;
+  // the matrix and its factor as double-float (hi, lo) pairs (8 bytes, as a double)
+  float2 *A = reinterpret_cast<float2 *>(pd.A + (size_t)b * pd.max_ns * pd.max_ns);
   double *y = pd.y + (size_t)b * pd.max_ns;
   // A = F + lambda C (lower triangle), y = D (row N_s of the Gram matrix)
   for (size_t e = tid; e < (size_t)n * n; e += PIX_THREADS) {
     const int i = (int)(e / n), j = (int)(e - (size_t)i * n);
-    if (j <= i) A[e] = F[(size_t)i * ldg + j] + lam * S.spx_C[e];
+    if (j <= i) A[e] = df_split(F[(size_t)i * ldg + j] + lam * S.spx_C[e]);
   }
   for (int i = tid; i < n; i += PIX_THREADS) y[i] = F[(size_t)n * ldg + i];
   __shared__ double Dg[32][33];
-  __shared__ double Pi[64][33], Pj[64][33];
+  __shared__ float2 Pi[64][33], Pj[64][33];  // (hi, lo) pairs of the panel rows
   __shared__ double red[PIX_THREADS / 32];
   __shared__ int bad;
   if (tid == 0) bad = 0;
@@ -312,7 +352,7 @@ __global__ void __launch_bounds__(PIX_THREADS) k_pix_eval(const SysDev *__restri
     // diagonal block, factored by warp 0
     for (int e = tid; e < 32 * 32; e += PIX_THREADS) {
       const int i = e >> 5, j = e & 31;
-      Dg[i][j] = (i < kb && j <= i) ? A[(size_t)(k0 + i) * n + k0 + j] : (i == j ? 1.0 : 0.0);
+      Dg[i][j] = (i < kb && j <= i) ? df_val(A[(size_t)(k0 + i) * n + k0 + j]) : (i == j ? 1.0 : 0.0);
     }
     __syncthreads();
     if (warp == 0) {
@@ -336,31 +376,35 @@ __global__ void __launch_bounds__(PIX_THREADS) k_pix_eval(const SysDev *__restri
       }
     }
     __syncthreads();
-    for (int e = tid; e < 32 * 32; e += PIX_THREADS) {
-      const int i = e >> 5, j = e & 31;
-      if (i < kb && j <= i) A[(size_t)(k0 + i) * n + k0 + j] = Dg[i][j];
-    }
     if (tid == 0)
       for (int j = 0; j < kb; ++j) half_logdet += log(Dg[j][j]);
-    // panel below the block: x L11^T = a, row by row
+    // panel below the block: x L11^T = a, row by row; the sums in double-float against the
+    // block's (hi, lo) copy (kept in Pi's space until the trailing update), the divisions in
+    // FP64
+    float2(*Dgs)[33] = Pi;
+    for (int e = tid; e < 32 * 32; e += PIX_THREADS) {
+      const int i = e >> 5, j = e & 31;
+      Dgs[i][j] = df_split(Dg[i][j]);
+      if (i < kb && j <= i) A[(size_t)(k0 + i) * n + k0 + j] = Dgs[i][j];
+    }
+    __syncthreads();
     const int r0 = k0 + kb;
     for (int i = r0 + tid; i < n; i += PIX_THREADS) {
-      double x[32];
-      double *ai = A + (size_t)i * n + k0;
-#pragma unroll
-      for (int m = 0; m < 32; ++m) x[m] = m < kb ? ai[m] : 0.0;
+      float2 xs[32];
+      float2 *ai = A + (size_t)i * n + k0;
 #pragma unroll
       for (int m = 0; m < 32; ++m) {
+        xs[m] = make_float2(0.0f, 0.0f);
         if (m < kb) {
-          double sacc = x[m];
+          float hi = 0.0f, lo = 0.0f;
 #pragma unroll
-          for (int qd = 0; qd < m; ++qd) sacc -= x[qd] * Dg[m][qd];
-          x[m] = sacc / Dg[m][m];
+          for (int qd = 0; qd < m; ++qd) df_fma(hi, lo, xs[qd], Dgs[m][qd]);
+          xs[m] = df_split((df_val(ai[m]) - ((double)hi + (double)lo)) / Dg[m][m]);
         }
       }
 #pragma unroll
       for (int m = 0; m < 32; ++m)
-        if (m < kb) ai[m] = x[m];
+        if (m < kb) ai[m] = xs[m];
     }
     __syncthreads();
     // trailing update A22 -= L21 L21^T, lower triangle, 64 x 64 tiles
@@ -371,18 +415,19 @@ __global__ void __launch_bounds__(PIX_THREADS) k_pix_eval(const SysDev *__restri
         for (int e = tid; e < 64 * 32; e += PIX_THREADS) {
           const int r = e >> 5, m = e & 31;
           const int gi = r0 + ti * 64 + r, gj = r0 + tj * 64 + r;
-          Pi[r][m] = (gi < n && m < kb) ? A[(size_t)gi * n + k0 + m] : 0.0;
-          Pj[r][m] = (gj < n && m < kb) ? A[(size_t)gj * n + k0 + m] : 0.0;
+          const float2 z = make_float2(0.0f, 0.0f);
+          Pi[r][m] = (gi < n && m < kb) ? A[(size_t)gi * n + k0 + m] : z;
+          Pj[r][m] = (gj < n && m < kb) ? A[(size_t)gj * n + k0 + m] : z;
         }
         __syncthreads();
-        double acc[4][4];
+        float ah[4][4], al[4][4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
-          for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+          for (int v = 0; v < 4; ++v) ah[u][v] = al[u][v] = 0.0f;
 #pragma unroll 4
         for (int m = 0; m < 32; ++m) {
-          double av[4], bv[4];
+          float2 av[4], bv[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             av[u] = Pi[ty * 4 + u][m];
@@ -391,14 +436,14 @@ __global__ void __launch_bounds__(PIX_THREADS) k_pix_eval(const SysDev *__restri
 #pragma unroll
           for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
+            for (int v = 0; v < 4; ++v) df_fma(ah[u][v], al[u][v], av[u], bv[v]);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
             const int gi = r0 + ti * 64 + ty * 4 + u, gj = r0 + tj * 64 + tx * 4 + v;
-            if (gi < n && gj <= gi) A[(size_t)gi * n + gj] -= acc[u][v];
+            if (gi < n && gj <= gi) A[(size_t)gi * n + gj] = df_sub(A[(size_t)gi * n + gj], ah[u][v], al[u][v]);
           }
         __syncthreads();
       }
@@ -409,17 +454,17 @@ __global__ void __launch_bounds__(PIX_THREADS) k_pix_eval(const SysDev *__restri
     if (warp == 0) {
       double yv = lane < kb ? y[k0 + lane] : 0.0;
       for (int j = 0; j < kb; ++j) {
-        const double yj = __shfl_sync(0xffffffffu, yv, j) / A[(size_t)(k0 + j) * n + k0 + j];
+        const double yj = __shfl_sync(0xffffffffu, yv, j) / df_val(A[(size_t)(k0 + j) * n + k0 + j]);
         if (lane == j) yv = yj;
-        if (lane > j && lane < kb) yv -= A[(size_t)(k0 + lane) * n + k0 + j] * yj;
+        if (lane > j && lane < kb) yv -= df_val(A[(size_t)(k0 + lane) * n + k0 + j]) * yj;
       }
       if (lane < kb) y[k0 + lane] = yv;
     }
     __syncthreads();
     for (int i = k0 + kb + tid; i < n; i += PIX_THREADS) {
-      const double *ai = A + (size_t)i * n + k0;
+      const float2 *ai = A + (size_t)i * n + k0;
       double sacc = 0.0;
-      for (int m = 0; m < kb; ++m) sacc = fma(ai[m], y[k0 + m], sacc);
+      for (int m = 0; m < kb; ++m) sacc = fma(df_val(ai[m]), y[k0 + m], sacc);
       y[i] -= sacc;
     }
     __syncthreads();
@@ -430,16 +475,16 @@ __global__ void __launch_bounds__(PIX_THREADS) k_pix_eval(const SysDev *__restri
     if (warp == 0) {
       double sv = lane < kb ? y[k0 + lane] : 0.0;
       for (int j = kb - 1; j >= 0; --j) {
-        const double sj = __shfl_sync(0xffffffffu, sv, j) / A[(size_t)(k0 + j) * n + k0 + j];
+        const double sj = __shfl_sync(0xffffffffu, sv, j) / df_val(A[(size_t)(k0 + j) * n + k0 + j]);
         if (lane == j) sv = sj;
-        if (lane < j) sv -= A[(size_t)(k0 + j) * n + k0 + lane] * sj;
+        if (lane < j) sv -= df_val(A[(size_t)(k0 + j) * n + k0 + lane]) * sj;
       }
       if (lane < kb) y[k0 + lane] = sv;
     }
     __syncthreads();
     for (int i = tid; i < k0; i += PIX_THREADS) {
       double sacc = 0.0;
-      for (int m = 0; m < kb; ++m) sacc = fma(A[(size_t)(k0 + m) * n + i], y[k0 + m], sacc);
+      for (int m = 0; m < kb; ++m) sacc = fma(df_val(A[(size_t)(k0 + m) * n + i]), y[k0 + m], sacc);
       y[i] -= sacc;
     }
     __syncthreads();
@@ -460,12 +505,21 @@ __global__ void __launch_bounds__(PIX_THREADS) k_pix_eval(const SysDev *__restri
   }
   // E_D = |f s - d|^2 / 2 in units of sigma, from the residuals themselves: the difference
   // d^T C_D^-1 d - D^T s_MP of two sums ~ N_d (S/N)^2 would cancel to ~1e-8 of them
+  // (the rows' dot products in double-float against s_MP split in place into (hi, lo))
+  __syncthreads();
+  float2 *ys = reinterpret_cast<float2 *>(y);
+  for (int i = tid; i < n; i += PIX_THREADS) {
+    const double v = y[i];
+    ys[i] = df_split(v);
+  }
+  __syncthreads();
   double ed = 0.0;
   const float *g = pd.g + (size_t)b * pd.max_nd * ldg;
   for (int q = warp; q < S.n_mask; q += PIX_THREADS / 32) {
     const float *gq = g + (size_t)q * ldg;
-    double r = 0.0;
-    for (int k = lane; k < n; k += 32) r = fma((double)gq[k], y[k], r);
+    float hi = 0.0f, lo = 0.0f;
+    for (int k = lane; k < n; k += 32) df_fma(hi, lo, make_float2(gq[k], 0.0f), ys[k]);
+    double r = (double)hi + (double)lo;
     for (int off = 16; off > 0; off >>= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
     r -= (double)gq[n];
     if (lane == 0) ed = fma(r, r, ed);

@@ -6,7 +6,7 @@ from . import systems
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [4052, 4054, 4064, 8032, 8042, 8044, 16021]
+SHAPES = [2064, 2084, 4052, 4054, 4064, 8032, 8042, 8044, 16021]
 OTHER_FORMS = [1008032, 1008041, 1008042, 1016021, 2004042, 2004052, 2004051, 2008031,
                3004042, 3004041, 3004051, 3008031]
 
