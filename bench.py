@@ -43,6 +43,7 @@ FFMA_LANES_PER_CLK_SM = 128
 # 2, weighted term 1, four moment sums 4)
 FMA_OPS_PER_EVAL = {"k_jam_fwd_grad": 8, "k_jam_adjoint": 7}
 DFMA_PER_CLK_SM = 1.75  # FP64 FMA per clock per SM, measured (profiles/mufu_ffma_rates_b300.md)
+DF_OPS_PER_FMA = 12  # FP32 operations of one double-float multiply-add (csrc/k_pixsrc.cu df_fma)
 
 
 def parse():
@@ -508,10 +509,14 @@ def measure(args, ctx, lib, systems, th_np, sid_np, B, grad_mode, world, rank, l
     sm_max = clocks["sm_max_mhz"] or 2032.0
     jam_form = tuning["jam_pts"] // 1000000
     if jam_name == "k_pix_evidence":
-        peak = N_SM * DFMA_PER_CLK_SM * 2 * sm_max * 1e6 / 1e12
+        # the factorisation's multiply-adds run in double-float on the FP32 pipe, 12 FP32
+        # operations each (the GPU's native FP64 rate, 1.75 DFMA/clk/SM, is 6x lower)
+        peak = N_SM * FFMA_LANES_PER_CLK_SM / DF_OPS_PER_FMA * 2 * sm_max * 1e6 / 1e12
         peak_unit = "TFLOP/s"
-        peak_basis = (f"{N_SM} SM x {DFMA_PER_CLK_SM} DFMA/clk/SM (measured, "
-                      f"profiles/mufu_ffma_rates_b300.md) x 2 flops x {sm_max:.0f} MHz max SM clock")
+        peak_basis = (f"{N_SM} SM x {FFMA_LANES_PER_CLK_SM} FP32 lanes/clk/SM / {DF_OPS_PER_FMA} "
+                      f"FP32 operations per double-float multiply-add x 2 flops x {sm_max:.0f} MHz "
+                      f"(FP64-equivalent flops; native FP64: {N_SM} SM x {DFMA_PER_CLK_SM} DFMA/clk "
+                      f"= {N_SM * DFMA_PER_CLK_SM * 2 * sm_max * 1e6 / 1e12:.2f} TFLOP/s)")
     elif jam_name == "k_jam" and jam_form in (1, 3):
         # recurrence forms: per 8 evaluations 15 packed FMA-pipe operations (2 FP32 lanes each)
         # and 4 ex2, so the FMA pipe bounds them

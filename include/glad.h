@@ -144,7 +144,10 @@ enum {
  * -(sum of terms)/2) and theta[8..12] are not used.  Arithmetic: rays and the response in
  * FP32; the Gram matrix [F D; D^T d^T C_D^-1 d] from FP32 products summed in FP32 over 256
  * rows and in FP64 across them, its data row (D, d^T C_D^-1 d) summed in FP64; the
- * factorisation, the solves and E_D (from the residuals of the masked pixels), E_S in FP64.
+ * factorisation in double-float (the matrix held as pairs of floats, ~48 bits; every
+ * multiply-add exact to that precision on the FP32 pipes) with FP64 pivots and triangular
+ * solves; E_D (from the residuals of the masked pixels) by double-float dot products, E_S in
+ * FP64.
  * glad_loglike_grad, glad_model_image and glad_loglike_static refuse contexts or systems with
  * a pixelated source (GLAD_EUNSUPPORTED); glad_pixsrc returns the search's result.
  */

@@ -8,7 +8,7 @@
 //  k_pix_gram: [F D; D^T d^T C_D^-1 d] = g^T g, lower triangle, 64 x 64 tiles: FP32 products
 //    summed in FP32 over 256 rows and in FP64 across them; k_pix_dcol then redoes the data
 //    row (D and d^T C_D^-1 d) with FP64 sums.
-//  k_pix_eval: one CTA per sample: A = F + lambda C (FP64), blocked Cholesky (32-wide panels,
+//  k_pix_eval: one CTA per sample (two resident per SM): A = F + lambda C, blocked Cholesky (32-wide panels,
 //    64 x 64 trailing tiles), s_MP by the two triangular solves, and the log-evidence
 //      ln P = -E_D - lambda E_S - sum ln L_ii + (N_s/2) ln lambda + const,
 //    E_D = |f s_MP - d|^2 / 2 (units of sigma) from the residuals of the masked pixels,
@@ -195,15 +195,27 @@ __global__ void __launch_bounds__(PIX_F_WARPS * 32) k_pix_f(const SysDev *__rest
   const int K = S.psf_k, h = (K - 1) / 2, nr = 4 * S.ss * S.ss;
   const int *Li = ws.pix_Li + (size_t)b * ws.max_lpix;
   const float *Lw = ws.pix_Lw + (size_t)b * ws.max_lpix;
-  for (int t = lane; t < K * K; t += 32) {
+  // the lanes take taps 32 apart in the K^2 window (32 is coprime to the odd K^2, so t0 -> t
+  // is a permutation): neighbouring taps land on neighbouring rays and the same grid pixels,
+  // and would collide in the shared row's atomics
+  const int KK = K * K;
+  for (int t0 = lane; t0 < KK; t0 += 32) {
+    const int t = (int)(((long long)t0 * 32) % KK);
     const int a = t / K, c = t - a * K;
     const int pi = qi - (a - h), pj = qj - (c - h);
     if (pi < 0 || pi >= S.ny || pj < 0 || pj >= S.nx) continue;
     const float P = S.psf[t];
-    const size_t o = (size_t)(pi * S.nx + pj) * nr;
-    for (int e = 0; e < nr; ++e) {
-      const float w = Lw[o + e];
-      if (w != 0.0f) atomicAdd(&row[Li[o + e]], P * w);
+    // a pixel's entries: ss^2 rays x 4, 16-byte aligned (nr is a multiple of 4)
+    const int4 *li = reinterpret_cast<const int4 *>(Li + (size_t)(pi * S.nx + pj) * nr);
+    const float4 *lw = reinterpret_cast<const float4 *>(Lw + (size_t)(pi * S.nx + pj) * nr);
+    for (int r = 0; r < nr / 4; ++r) {
+      const float4 w = lw[r];
+      if (w.x == 0.0f && w.y == 0.0f && w.z == 0.0f && w.w == 0.0f) continue;
+      const int4 ix = li[r];
+      atomicAdd(&row[ix.x], P * w.x);
+      atomicAdd(&row[ix.y], P * w.y);
+      atomicAdd(&row[ix.z], P * w.z);
+      atomicAdd(&row[ix.w], P * w.w);
     }
   }
   __syncwarp();
@@ -315,7 +327,7 @@ __global__ void k_pix_init(const SysDev *__restrict__ sysv, const int *__restric
 
 // One evidence evaluation per sample at its pending ln lambda (final_pass: at the best one,
 // with s_MP written to s_out[b * s_stride ..]).
-__global__ void __launch_bounds__(PIX_THREADS) k_pix_eval(const SysDev *__restrict__ sysv,
+__global__ void __launch_bounds__(PIX_THREADS, 2) k_pix_eval(const SysDev *__restrict__ sysv,
                                                           const int *__restrict__ sys_id, WsDev ws,
                                                           PixDev pd, int final_pass, double *s_out,
                                                           int s_stride) {

@@ -287,7 +287,7 @@ def workload_systems(w: int, small: bool = False):
        paper's own joint model (Sect. 3.3), B=256
     9: workload 1's system with the pixelated source (Sect. 3.1.1): a 30 x 30 grid over
        +-0.6" around the source, fitted to the arcs in the annulus 0.9" - 2.5" (N_d = 6,840
-       pixels, N_s = 900: Table 1's O(10^4) and O(10^3)), B=148 (one sample per SM)
+       pixels, N_s = 900: Table 1's O(10^4) and O(10^3)), B=296 (two samples per SM)
     """
     rng = np.random.Generator(np.random.PCG64(1000 + {5: 1, 6: 4, 7: 1, 8: 1, 9: 1}.get(w, w)))
     if w == 0:
@@ -305,7 +305,7 @@ def workload_systems(w: int, small: bool = False):
             s.update(name="w9", src_pix=1, spx_n=(30, 30),
                      spx_box=(c[0] - 0.6, c[0] + 0.6, c[1] - 0.6, c[1] + 0.6),
                      mask=arc_mask(s["nx"], s["pix"], 0.9, 2.5))
-            return [s], 148
+            return [s], 296
         if w == 5:
             s.update(name="w5", jam_align=1, sph_nr=128, sph_nw=8, sph_nlos=32)
         if w == 7:
