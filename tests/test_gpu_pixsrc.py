@@ -143,3 +143,35 @@ def test_rxj1131_scale_sampled_against_oracle():
     ev = model.evaluate(th[0], s)
     assert abs(float(lnP[0]) - ev["lnP"]) < lnp_tol(ev["lnP"]), (float(lnP[0]), ev["lnP"])
     assert abs(float(logL[0]) - ev["logL"]) < lnp_tol(ev["logL"]), (float(logL[0]), ev["logL"])
+
+
+def test_graph_replay_and_static_refusal(small):
+    # the whole search (a fixed number of evaluation passes, converged samples returning at
+    # once) is a fixed launch sequence: it captures into a CUDA graph and replays with theta
+    # rewritten in place; the allocation-free entry point refuses pixelated-source contexts
+    import ctypes as C
+    from paper_2504_01302_b300 import _lib
+    s, ctx = small
+    ta = systems.near_truth_thetas(4, seed=211)
+    tb = systems.near_truth_thetas(4, seed=212)
+    B = len(ta)
+    sid = torch.zeros(B, dtype=torch.int32, device="cuda")
+    ref = {k: ctx.loglike(_th(t), sid)[0].cpu().numpy() for k, t in (("a", ta), ("b", tb))}
+    theta = _th(ta)
+    logL = torch.empty(B, dtype=torch.float64, device="cuda")
+    status = torch.empty(B, dtype=torch.int32, device="cuda")
+    P = lambda t: C.c_void_p(t.data_ptr())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        rc = ctx.lib.glad_loglike(ctx.handle, P(sid), P(theta), B, P(logL), P(status), None,
+                                  C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0, ctx.lib.glad_last_error().decode()
+    for k, t in (("a", ta), ("b", tb)):
+        theta.copy_(_th(t))
+        graph.replay()
+        torch.cuda.synchronize()
+        assert np.all(status.cpu().numpy() == 0)
+        # shared-memory atomics in the response rows reorder between launches (~1e-7 of F)
+        assert np.allclose(logL.cpu().numpy(), ref[k], rtol=1e-6, atol=1e-3)
+    rc = ctx.lib.glad_loglike_static(ctx.handle, P(sid), P(theta), B, P(logL), P(status), None, None)
+    assert rc == 5 and "pixelated" in ctx.lib.glad_last_error().decode()
