@@ -175,3 +175,12 @@ def test_graph_replay_and_static_refusal(small):
         assert np.allclose(logL.cpu().numpy(), ref[k], rtol=1e-6, atol=1e-3)
     rc = ctx.lib.glad_loglike_static(ctx.handle, P(sid), P(theta), B, P(logL), P(status), None, None)
     assert rc == 5 and "pixelated" in ctx.lib.glad_last_error().decode()
+
+
+@pytest.mark.parametrize("n", [40, 68])
+def test_large_grids_against_oracle(n):
+    # grids whose response rows need more than the default 48 KB of shared memory (40 x 40)
+    # and the largest grid the library takes (68 x 68 = 4,624 pixels, the top of the paper's
+    # 60^2 - 68^2 sweep)
+    s = pix_system(systems.small_system(7), n=(n, n), half=0.6)
+    check_against_oracle(_ctx([s]), s, systems.near_truth_thetas(1, seed=213), check_s=(n == 40))
