@@ -311,6 +311,13 @@ glad_status glad_pixsrc(glad_ctx *ctx, const int *sys_id, const double *theta, i
 /* Cholesky factorisations of F + lambda C run since the last call (each evidence evaluation
  * of the regularisation search is one), and reset the count. */
 unsigned long long glad_pix_factorizations(glad_ctx *ctx);
+/* How each evidence evaluation of the pixelated source runs (the results agree to rounding):
+ * mode 1: one CTA per sample does the whole evaluation (for batches that fill the GPU); mode 2:
+ * a sequence of launches per evaluation, each 32-column panel step of the factorisation spread
+ * over many CTAs per sample (for small batches: one sample then uses the whole GPU); mode 0
+ * (the default): mode 2 for batches of fewer than two samples per SM, else mode 1.
+ * GLAD_EINVAL for other modes. */
+glad_status glad_set_pix_path(glad_ctx *ctx, int mode);
 
 /* Precision of the forward pass (Sect. 3: the paper computes in FP64 throughout).
  * mode 0 (the default): FP32 bulk -- ray shooting, light, PSF blurring, the Jeans sums -- with

@@ -239,6 +239,8 @@ struct glad_ctx {
     int jam_persistent = 0;  // 1: one persistent launch over a (sample, tile) work list
     int jam_form = 0;        // form of the pair sum (k_jam.cu): 0 .. 3
     int adj_ept = 4;      // table entries per thread in the JAM adjoint
+    int pix_path = 0;     // evidence evaluation (k_pixsrc.cu): 0 by batch size, 1 one CTA per
+                          // sample, 2 multi-launch
   } tune;
   int *d_one_sys = nullptr;      // scratch sys id for single-sample calls
   // after k_prep the dynamics branch runs on a high-priority stream and the lensing branch
@@ -318,6 +320,7 @@ cudaError_t launch_pixsrc(glad_ctx *c, const int *sys_id, int B, cudaStream_t st
 cudaError_t pixsrc_ws_ensure(glad_ctx *c, int B);
 void pixsrc_ws_free(glad_ctx *c);
 unsigned long long pixsrc_factorizations(glad_ctx *c);
+bool pixsrc_multi_launch(glad_ctx *c, int B);
 bool jam_shape_supported(int pts, int minb, int unr, int form);
 int jam_shape_list(int (*out)[4], int cap);
 

@@ -8,19 +8,21 @@
 //  k_pix_gram: [F D; D^T d^T C_D^-1 d] = g^T g, lower triangle, 64 x 64 tiles: FP32 products
 //    summed in FP32 over 256 rows and in FP64 across them; k_pix_dcol then redoes the data
 //    row (D and d^T C_D^-1 d) with FP64 sums.
-//  k_pix_eval: one CTA per sample (two resident per SM): A = F + lambda C, blocked Cholesky (32-wide panels,
-//    64 x 64 trailing tiles), s_MP by the two triangular solves, and the log-evidence
+//  k_pix_eval: one CTA per sample (two resident per SM), or for small batches the k_pixm_*
+//    sequence that spreads each step over many CTAs: M = [F + lambda C; D^T], blocked Cholesky
+//    (32-wide panels, 64 x 64 trailing tiles) whose last row is y = L^-1 D, s_MP by the
+//    backward solve L^T s = y, and the log-evidence
 //      ln P = -E_D - lambda E_S - sum ln L_ii + (N_s/2) ln lambda + const,
 //    E_D = |f s_MP - d|^2 / 2 (units of sigma) from the residuals of the masked pixels,
-//    E_S = |H s_MP|^2 / 2 (both in FP64), then one step of Brent's minimisation of -ln P over
-//    ln lambda; its last pass writes s_MP for the caller.  E_D + lambda E_S is stationary at
-//    s_MP, so an error in s_MP moves it only at second order; written as the difference
+//    E_S = |H s_MP|^2 / 2, then one step of Brent's minimisation of -ln P over ln lambda; its
+//    last pass writes s_MP for the caller.  E_D + lambda E_S is stationary at s_MP, so an
+//    error in s_MP moves it only at second order; written as the difference
 //    d^T C_D^-1 d - D^T s_MP it would lose ~1e-8 of two sums that reach N_d (S/N)^2.
 // The factorisation keeps ~FP64 accuracy because the evidence needs ln det(F + lambda C) to
-// ~1e-2 absolute over N_s ~ 1e3 pivots of a matrix whose conditioning grows as lambda falls:
-// the matrix, the diagonal blocks, the panels and the solves are FP64, and the trailing update
-// (nearly all of the N_s^3/3 flops) runs in double-float on the FP32 pipes, since this GPU's
-// FP64 rate is 1/73 of its FP32 rate with or without tensor cores.
+// ~1e-2 absolute over N_s ~ 1e3 pivots of a matrix whose conditioning grows as lambda falls.
+// It runs in double-float (~48 bits) on the FP32 pipes throughout, since this GPU's FP64
+// rate is 1/73 of its FP32 rate with or without tensor cores; FP64 is left to the Gram
+// matrix's sums, the assembly, the energies and one logarithm per evaluation.
 #include <math.h>
 
 #include <algorithm>
@@ -39,12 +41,20 @@ struct PixSearch {
 struct PixDev {
   float *g;             // [B * max_nd * ldg] rows [f_q / sigma_q, d_q / sigma_q]
   double *F;            // [B * ldg * ldg] Gram matrix, lower triangle
-  double *A;            // [B * max_ns * max_ns] F + lambda C and its factor (row stride N_s),
-                        // held as double-float (hi, lo) pairs of floats
-  double *y;            // [B * max_ns]
+  float2 *A;            // [B * (max_ns + 1)^2] M = [F + lambda C; D^T] (row stride N_s + 1) and
+                        // its factor, lower triangle, double-float (hi, lo) pairs of floats
+  float2 *s;            // [B * max_ns] s_MP
+  float2 *rd;           // [B * max_ns] 1 / L_ii, for the backward solve
   PixSearch *srch;      // [B]
   unsigned long long *nfac;  // [1] factorisations run
-  int ldg, max_ns, max_nd;
+  // the multi-launch form's per-sample state
+  float2 *pm;           // [B] product of the pivots so far, pm * 2^pe
+  int *pe;              // [B]
+  int *bad;             // [B] a pivot was not positive
+  double *es;           // [B] |H s_MP|^2
+  double *edp;          // [B * ed_chunks] partial sums of the squared residuals
+  float2 *dgf;          // [B * 32 * 32] the factored diagonal block of the current panel step
+  int ldg, max_ns, max_nd, ed_chunks;
 };
 
 struct PixWs {
@@ -60,6 +70,7 @@ constexpr double TTOL = 1e-3;                // tolerance in ln lambda (ln P mov
 
 #define PIX_F_WARPS 8
 #define PIX_THREADS 256
+#define PIXM_ED_ROWS 64
 
 // ---------------------------------------------------------------------------------------
 // Brent's method (Brent 1973, "Algorithms for Minimization without Derivatives", ch. 5):
@@ -171,6 +182,16 @@ __device__ __forceinline__ void df_fma(float &hi, float &lo, float2 a, float2 b)
   const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, v)), __fsub_rn(p, v));
   hi = s;
   lo = __fadd_rn(lo, __fadd_rn(pe, e));
+}
+
+// (a.x + a.y) * (b.x + b.y), renormalised (the product's error by FMA, the cross terms added)
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  const float h = __fadd_rn(p, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, p)));
 }
 
 // ---------------------------------------------------------------------------------------
@@ -325,209 +346,290 @@ __global__ void k_pix_init(const SysDev *__restrict__ sysv, const int *__restric
   brent_start(pd.srch[b], S.spx_tlo, S.spx_thi);
 }
 
-// One evidence evaluation per sample at its pending ln lambda (final_pass: at the best one,
-// with s_MP written to s_out[b * s_stride ..]).
-__global__ void __launch_bounds__(PIX_THREADS, 2) k_pix_eval(const SysDev *__restrict__ sysv,
-                                                          const int *__restrict__ sys_id, WsDev ws,
-                                                          PixDev pd, int final_pass, double *s_out,
-                                                          int s_stride) {
-  const int b = blockIdx.x;
-  if (ws.status[b] != GLAD_SAMPLE_OK) return;
-  const SysDev &S = sysv[sys_id[b]];
-  if (!S.src_pix) return;
-  PixSearch *sp = pd.srch + b;
+// ---------------------------------------------------------------------------------------
+// The evidence evaluation.  The factorisation runs on the augmented matrix
+//     M = [ F + lambda C    . ]     (N_s + 1 rows, row stride N_s + 1, lower triangle)
+//         [ D^T             . ]
+// whose Cholesky factor's last row is y^T = (L^-1 D)^T: row N_s is one more panel row of
+// every step (its pivot is never taken), so the forward solve comes out of the factorisation.
+// Everything on a step's critical path is double-float on the FP32 pipes (a warp's FP64
+// instruction holds this GPU's FP64 unit for ~64 cycles, and these paths are sequential): the
+// pivots' square roots and reciprocals (FP32 seeds refined by one Newton step in double-float,
+// doubling their 24 bits), the pivots' log-product (mantissas multiplied in double-float,
+// binary exponents summed, one FP64 log per evaluation), the panels and the backward solve.
+
+// sqrt(d) for d > 0: s0 = sqrt(d.hi) in FP32, then s0 + (d - s0^2) / (2 s0) (Newton's step for
+// s^2 = d), the residual exact to its last bits: s0^2 = p + pe exactly (FMA), and d.hi - p is
+// exact because p lies within an ulp or two of d.hi (Sterbenz)
+__device__ __forceinline__ float2 df_sqrt(float2 d) {
+  const float s0 = sqrtf(d.x);
+  const float p = __fmul_rn(s0, s0);
+  const float pe = __fmaf_rn(s0, s0, -p);
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(d.x, p), pe), d.y);
+  const float c = __fmul_rn(r, __frcp_rn(__fmul_rn(2.0f, s0)));
+  const float h = __fadd_rn(s0, c);
+  return make_float2(h, __fsub_rn(c, __fsub_rn(h, s0)));
+}
+
+// 1 / l: r0 = 1 / l.hi in FP32, then r0 + r0 (1 - l r0) (Newton's step for 1/x), the residual
+// 1 - l.hi r0 exact by FMA
+__device__ __forceinline__ float2 df_rcp(float2 l) {
+  const float r0 = __frcp_rn(l.x);
+  float e = __fmaf_rn(-l.x, r0, 1.0f);
+  e = __fmaf_rn(-l.y, r0, e);
+  const float c = __fmul_rn(r0, e);
+  const float h = __fadd_rn(r0, c);
+  return make_float2(h, __fsub_rn(c, __fsub_rn(h, r0)));
+}
+
+__device__ __forceinline__ float2 shfl_f2(float2 v, int src) {
+  return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// is sample b evaluated in this pass, and at which ln lambda
+__device__ __forceinline__ bool pix_active(const SysDev &S, const WsDev &ws, const PixDev &pd,
+                                          int b, int final_pass, double &t) {
+  if (ws.status[b] != GLAD_SAMPLE_OK || !S.src_pix) return false;
+  const PixSearch *sp = pd.srch + b;
   const int phase = sp->phase;
-  if (!final_pass && phase == 2) return;
-  const double t = (final_pass || phase == 0) ? sp->x : sp->u;
-  const double lam = exp(t);
-  const int n = S.spx_ns, ldg = pd.ldg;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (!final_pass && phase == 2) return false;
+  t = (final_pass || phase == 0) ? sp->x : sp->u;
+  return true;
+}
+
+__device__ __forceinline__ float2 *pix_A(const PixDev &pd, int b) {
+  return pd.A + (size_t)b * (pd.max_ns + 1) * (pd.max_ns + 1);
+}
+
+// M: rows i < N_s get F + lambda C, row N_s gets D (row N_s of the Gram matrix), lower
+// triangle without column N_s, over the elements first, first + step, ...
+__device__ __forceinline__ void pix_assemble(const SysDev &S, const PixDev &pd, int b, double lam,
+                                             size_t first, size_t step) {
+  const int n = S.spx_ns, ldg = pd.ldg, lda = n + 1;
   const double *F = pd.F + (size_t)b * ldg * ldg;
-  // the matrix and its factor as double-float (hi, lo) pairs (8 bytes, as a double)
-  float2 *A = reinterpret_cast<float2 *>(pd.A + (size_t)b * pd.max_ns * pd.max_ns);
-  double *y = pd.y + (size_t)b * pd.max_ns;
-  // A = F + lambda C (lower triangle), y = D (row N_s of the Gram matrix)
-  for (size_t e = tid; e < (size_t)n * n; e += PIX_THREADS) {
+  float2 *A = pix_A(pd, b);
+  for (size_t e = first; e < (size_t)(n + 1) * n; e += step) {
     const int i = (int)(e / n), j = (int)(e - (size_t)i * n);
-    if (j <= i) A[e] = df_split(F[(size_t)i * ldg + j] + lam * S.spx_C[e]);
+    if (j > i) continue;
+    const double v = i < n ? F[(size_t)i * ldg + j] + lam * S.spx_C[(size_t)i * n + j] : F[(size_t)n * ldg + j];
+    A[(size_t)i * lda + j] = df_split(v);
   }
-  for (int i = tid; i < n; i += PIX_THREADS) y[i] = F[(size_t)n * ldg + i];
-  __shared__ double Dg[32][33];
-  __shared__ float2 Pi[64][33], Pj[64][33];  // (hi, lo) pairs of the panel rows
-  __shared__ double red[PIX_THREADS / 32];
-  __shared__ int bad;
-  if (tid == 0) bad = 0;
-  double half_logdet = 0.0;  // sum ln L_ii (thread 0)
+}
+
+// the diagonal block at (k0, k0) (kb <= 32 pivots) factored in shared memory by the whole CTA
+// in double-float, right-looking with one barrier per pivot: every thread computes pivot j
+// itself (sqrt and reciprocal of the updated diagonal entry, which step j does not write) and
+// updates its elements (i, c), j < c <= i, by L_ij L_cj with L_xj = a_xj / L_jj formed on the
+// fly; the columns are scaled at the end.  Ds holds the block's factor on return (identity
+// beyond kb), Rs the pivots' reciprocals; *bad is set on a pivot that is not positive (taken
+// as 1).
+template <int NT>
+__device__ __forceinline__ void pix_diag(const float2 *A, int lda, int k0, int kb, float2 (*Ds)[33],
+                                         float2 *Rs, int *bad) {
+  static_assert(NT % 32 == 0 && 1024 % NT == 0, "CTA size");
+  constexpr int EPT = 1024 / NT;  // block elements per thread
+  const int tid = threadIdx.x;
+  __shared__ float2 Ls[32];
+  for (int e = tid; e < 32 * 32; e += NT) {
+    const int i = e >> 5, j = e & 31;
+    Ds[i][j] = (i < kb && j <= i) ? A[(size_t)(k0 + i) * lda + k0 + j]
+                                  : make_float2(i == j ? 1.0f : 0.0f, 0.0f);
+  }
   __syncthreads();
-  for (int k0 = 0; k0 < n; k0 += 32) {
-    const int kb = min(32, n - k0);
-    // diagonal block, factored by warp 0
-    for (int e = tid; e < 32 * 32; e += PIX_THREADS) {
-      const int i = e >> 5, j = e & 31;
-      Dg[i][j] = (i < kb && j <= i) ? df_val(A[(size_t)(k0 + i) * n + k0 + j]) : (i == j ? 1.0 : 0.0);
+  for (int j = 0; j < kb; ++j) {
+    float2 d = Ds[j][j];
+    if (!(d.x > 0.0f)) d = make_float2(1.0f, 0.0f);
+    const float2 l = df_sqrt(d);
+    const float2 r = df_rcp(l);
+    if (tid == 0) {
+      if (!(Ds[j][j].x > 0.0f)) *bad = 1;
+      Ls[j] = l;
+      Rs[j] = r;
     }
-    __syncthreads();
-    if (warp == 0) {
-      for (int j = 0; j < kb; ++j) {
-        if (lane == j) {
-          double d = Dg[j][j];
-          if (!(d > 0.0)) {
-            bad = 1;
-            d = 1.0;
-          }
-          Dg[j][j] = sqrt(d);
-        }
-        __syncwarp();
-        if (lane > j && lane < kb) Dg[lane][j] /= Dg[j][j];
-        __syncwarp();
-        if (lane > j && lane < kb) {
-          const double lij = Dg[lane][j];
-          for (int cc = j + 1; cc <= lane; ++cc) Dg[lane][cc] -= lij * Dg[cc][j];
-        }
-        __syncwarp();
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      const int e = tid + q * NT, i = e >> 5, c = e & 31;
+      if (c > j && c <= i && i < kb) {
+        const float2 lij = df_mul(Ds[i][j], r), lcj = df_mul(Ds[c][j], r);
+        float hi = 0.0f, lo = 0.0f;
+        df_fma(hi, lo, lij, lcj);
+        Ds[i][c] = df_sub(Ds[i][c], hi, lo);
       }
     }
     __syncthreads();
-    if (tid == 0)
-      for (int j = 0; j < kb; ++j) half_logdet += log(Dg[j][j]);
-    // panel below the block: x L11^T = a, row by row; the sums in double-float against the
-    // block's (hi, lo) copy (kept in Pi's space until the trailing update), the divisions in
-    // FP64
-    float2(*Dgs)[33] = Pi;
-    for (int e = tid; e < 32 * 32; e += PIX_THREADS) {
-      const int i = e >> 5, j = e & 31;
-      Dgs[i][j] = df_split(Dg[i][j]);
-      if (i < kb && j <= i) A[(size_t)(k0 + i) * n + k0 + j] = Dgs[i][j];
+  }
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int e = tid + q * NT, i = e >> 5, j = e & 31;
+    if (j < kb && i < kb) {
+      if (i == j) Ds[i][j] = Ls[j];
+      else if (i > j) Ds[i][j] = df_mul(Ds[i][j], Rs[j]);
     }
-    __syncthreads();
-    const int r0 = k0 + kb;
-    for (int i = r0 + tid; i < n; i += PIX_THREADS) {
-      float2 xs[32];
-      float2 *ai = A + (size_t)i * n + k0;
+  }
+  __syncthreads();
+}
+
+// warp 0: the product of the block's pivots folded into (pm, pe) = pm * 2^pe held by lane 0
+// (each pivot's mantissa in [1/2, 1) and exponent apart, a product tree over the lanes)
+__device__ __forceinline__ void pix_pivot_product(const float2 (*Ds)[33], int kb, float2 &pm, int &pe) {
+  const int lane = threadIdx.x & 31;
+  float2 v = make_float2(1.0f, 0.0f);
+  int e = 0;
+  if (lane < kb) {
+    const float2 l = Ds[lane][lane];
+    const float f = frexpf(l.x, &e);
+    v = make_float2(f, ldexpf(l.y, -e));
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    v = df_mul(v, make_float2(__shfl_xor_sync(0xffffffffu, v.x, off),
+                              __shfl_xor_sync(0xffffffffu, v.y, off)));
+    e += __shfl_xor_sync(0xffffffffu, e, off);
+  }
+  if (lane == 0) {
+    pm = df_mul(pm, v);
+    int e2;
+    const float f = frexpf(pm.x, &e2);
+    pm = make_float2(f, ldexpf(pm.y, -e2));
+    pe += e + e2;
+  }
+}
+
+// sum ln L_ii from the pivots' product pm * 2^pe
+__device__ __forceinline__ double pix_half_logdet(float2 pm, int pe) {
+  return log((double)pm.x + (double)pm.y) + pe * M_LN2;
+}
+
+// panel rows i = first, first + step, ... below last: x L11^T = a, in double-float (the
+// divisions as products with the pivots' reciprocals)
+__device__ __forceinline__ void pix_panel_rows(float2 *A, int lda, int k0, int kb,
+                                               const float2 (*Ds)[33], const float2 *Rs, int first,
+                                               int last, int step) {
+  for (int i = first; i < last; i += step) {
+    float2 xs[32];
+    float2 *ai = A + (size_t)i * lda + k0;
 #pragma unroll
-      for (int m = 0; m < 32; ++m) {
-        xs[m] = make_float2(0.0f, 0.0f);
-        if (m < kb) {
-          float hi = 0.0f, lo = 0.0f;
+    for (int m = 0; m < 32; ++m) {
+      xs[m] = make_float2(0.0f, 0.0f);
+      if (m < kb) {
+        float hi = 0.0f, lo = 0.0f;
 #pragma unroll
-          for (int qd = 0; qd < m; ++qd) df_fma(hi, lo, xs[qd], Dgs[m][qd]);
-          xs[m] = df_split((df_val(ai[m]) - ((double)hi + (double)lo)) / Dg[m][m]);
-        }
+        for (int qd = 0; qd < m; ++qd) df_fma(hi, lo, xs[qd], Ds[m][qd]);
+        xs[m] = df_mul(df_sub(ai[m], hi, lo), Rs[m]);
       }
-#pragma unroll
-      for (int m = 0; m < 32; ++m)
-        if (m < kb) ai[m] = xs[m];
     }
-    __syncthreads();
-    // trailing update A22 -= L21 L21^T, lower triangle, 64 x 64 tiles
-    const int T = (n - r0 + 63) / 64;
-    const int ty = tid >> 4, tx = tid & 15;
-    for (int ti = 0; ti < T; ++ti)
-      for (int tj = 0; tj <= ti; ++tj) {
-        for (int e = tid; e < 64 * 32; e += PIX_THREADS) {
-          const int r = e >> 5, m = e & 31;
-          const int gi = r0 + ti * 64 + r, gj = r0 + tj * 64 + r;
-          const float2 z = make_float2(0.0f, 0.0f);
-          Pi[r][m] = (gi < n && m < kb) ? A[(size_t)gi * n + k0 + m] : z;
-          Pj[r][m] = (gj < n && m < kb) ? A[(size_t)gj * n + k0 + m] : z;
-        }
-        __syncthreads();
-        float ah[4][4], al[4][4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+    for (int m = 0; m < 32; ++m)
+      if (m < kb) ai[m] = xs[m];
+  }
+}
+
+// trailing tile (ti, tj) of the panel step at k0, rows from r0 = k0 + kb below nr = N_s + 1,
+// columns below N_s: M[gi][gj] -= sum_m L[gi][k0 + m] L[gj][k0 + m], in double-float
+template <int NT>
+__device__ __forceinline__ void pix_tile(float2 *A, int lda, int n, int k0, int kb, int r0, int ti,
+                                         int tj, float2 (*Pi)[33], float2 (*Pj)[33]) {
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  for (int e = tid; e < 64 * 32; e += NT) {
+    const int r = e >> 5, m = e & 31;
+    const int gi = r0 + ti * 64 + r, gj = r0 + tj * 64 + r;
+    const float2 z = make_float2(0.0f, 0.0f);
+    Pi[r][m] = (gi <= n && m < kb) ? A[(size_t)gi * lda + k0 + m] : z;
+    Pj[r][m] = (gj < n && m < kb) ? A[(size_t)gj * lda + k0 + m] : z;
+  }
+  __syncthreads();
+  float ah[4][4], al[4][4];
 #pragma unroll
-          for (int v = 0; v < 4; ++v) ah[u][v] = al[u][v] = 0.0f;
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) ah[u][v] = al[u][v] = 0.0f;
 #pragma unroll 4
-        for (int m = 0; m < 32; ++m) {
-          float2 av[4], bv[4];
+  for (int m = 0; m < 32; ++m) {
+    float2 av[4], bv[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            av[u] = Pi[ty * 4 + u][m];
-            bv[u] = Pj[tx * 4 + u][m];
-          }
+    for (int u = 0; u < 4; ++u) {
+      av[u] = Pi[ty * 4 + u][m];
+      bv[u] = Pj[tx * 4 + u][m];
+    }
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) df_fma(ah[u][v], al[u][v], av[u], bv[v]);
-        }
+      for (int v = 0; v < 4; ++v) df_fma(ah[u][v], al[u][v], av[u], bv[v]);
+  }
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < 4; ++u)
 #pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            const int gi = r0 + ti * 64 + ty * 4 + u, gj = r0 + tj * 64 + tx * 4 + v;
-            if (gi < n && gj <= gi) A[(size_t)gi * n + gj] = df_sub(A[(size_t)gi * n + gj], ah[u][v], al[u][v]);
-          }
-        __syncthreads();
+    for (int v = 0; v < 4; ++v) {
+      const int gi = r0 + ti * 64 + ty * 4 + u, gj = r0 + tj * 64 + tx * 4 + v;
+      if (gi <= n && gj <= gi && gj < n)
+        A[(size_t)gi * lda + gj] = df_sub(A[(size_t)gi * lda + gj], ah[u][v], al[u][v]);
+    }
+  __syncthreads();
+}
+
+// one block of the backward solve L^T s = y (y in row N_s of M, updated in place): warp 0
+// solves the block's kb unknowns into sb (and into s when s is given), then rows i = first,
+// first + step, ... below k0 take y_i -= sum_m L[k0 + m][i] s[k0 + m]; all in double-float
+template <int NT>
+__device__ __forceinline__ void pix_bsolve_block(const float2 *A, int lda, int n, const float2 *rd,
+                                                 float2 *s, int k0, int kb, int first, int step,
+                                                 float2 (*Lb)[33], float2 *rb, float2 *sb) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float2 *y = const_cast<float2 *>(A) + (size_t)n * lda;
+  // the block's factor and reciprocals staged first (Lb[32][33], rb[32] in shared memory): no
+  // global load inside the sequential loop
+  for (int e = threadIdx.x; e < 32 * 32; e += NT) {
+    const int i = e >> 5, c = e & 31;
+    if (i < kb && c <= i) Lb[i][c] = A[(size_t)(k0 + i) * lda + k0 + c];
+  }
+  if (threadIdx.x < kb) rb[threadIdx.x] = rd[k0 + threadIdx.x];
+  __syncthreads();
+  if (warp == 0) {
+    float2 v = lane < kb ? y[k0 + lane] : make_float2(0.0f, 0.0f);
+    for (int j = kb - 1; j >= 0; --j) {
+      const float2 sj = df_mul(shfl_f2(v, j), rb[j]);
+      if (lane == j) v = sj;
+      if (lane < j) {
+        float hi = 0.0f, lo = 0.0f;
+        df_fma(hi, lo, Lb[j][lane], sj);
+        v = df_sub(v, hi, lo);
       }
-  }
-  // y = L^-1 D, 32 rows at a time: warp 0 solves the block, the CTA updates the rows below
-  for (int k0 = 0; k0 < n; k0 += 32) {
-    const int kb = min(32, n - k0);
-    if (warp == 0) {
-      double yv = lane < kb ? y[k0 + lane] : 0.0;
-      for (int j = 0; j < kb; ++j) {
-        const double yj = __shfl_sync(0xffffffffu, yv, j) / df_val(A[(size_t)(k0 + j) * n + k0 + j]);
-        if (lane == j) yv = yj;
-        if (lane > j && lane < kb) yv -= df_val(A[(size_t)(k0 + lane) * n + k0 + j]) * yj;
-      }
-      if (lane < kb) y[k0 + lane] = yv;
     }
-    __syncthreads();
-    for (int i = k0 + kb + tid; i < n; i += PIX_THREADS) {
-      const float2 *ai = A + (size_t)i * n + k0;
-      double sacc = 0.0;
-      for (int m = 0; m < kb; ++m) sacc = fma(df_val(ai[m]), y[k0 + m], sacc);
-      y[i] -= sacc;
-    }
-    __syncthreads();
+    sb[lane] = lane < kb ? v : make_float2(0.0f, 0.0f);
+    if (s && lane < kb) s[k0 + lane] = v;
   }
-  // s_MP: L^T s = y from the bottom, 32 rows at a time
-  for (int k0 = ((n - 1) / 32) * 32; k0 >= 0; k0 -= 32) {
-    const int kb = min(32, n - k0);
-    if (warp == 0) {
-      double sv = lane < kb ? y[k0 + lane] : 0.0;
-      for (int j = kb - 1; j >= 0; --j) {
-        const double sj = __shfl_sync(0xffffffffu, sv, j) / df_val(A[(size_t)(k0 + j) * n + k0 + j]);
-        if (lane == j) sv = sj;
-        if (lane < j) sv -= df_val(A[(size_t)(k0 + j) * n + k0 + lane]) * sj;
-      }
-      if (lane < kb) y[k0 + lane] = sv;
-    }
-    __syncthreads();
-    for (int i = tid; i < k0; i += PIX_THREADS) {
-      double sacc = 0.0;
-      for (int m = 0; m < kb; ++m) sacc = fma(df_val(A[(size_t)(k0 + m) * n + i]), y[k0 + m], sacc);
-      y[i] -= sacc;
-    }
-    __syncthreads();
+  __syncthreads();
+  for (int i = first; i < k0; i += step) {
+    float hi = 0.0f, lo = 0.0f;
+    for (int m = 0; m < kb; ++m) df_fma(hi, lo, A[(size_t)(k0 + m) * lda + i], sb[m]);
+    y[i] = df_sub(y[i], hi, lo);
   }
-  if (final_pass) {
-    if (s_out)
-      for (int i = tid; i < n; i += PIX_THREADS) s_out[(size_t)b * s_stride + i] = y[i];
-    return;
-  }
-  // E_S = |H s|^2 / 2 (C = H^T H: second differences along x and y, zero outside the grid)
+  __syncthreads();
+}
+
+// this thread's share of |H s|^2 (C = H^T H: second differences along x and y, zero outside
+// the grid) over the pixels first, first + step, ...
+__device__ __forceinline__ double pix_es_part(const SysDev &S, const float2 *s, int first, int step) {
   double es = 0.0;
-  for (int p = tid; p < n; p += PIX_THREADS) {
+  auto sv = [&](int p) { return df_val(s[p]); };
+  for (int p = first; p < S.spx_ns; p += step) {
     const int i = p / S.spx_nx, j = p - i * S.spx_nx;
-    const double c2 = -2.0 * y[p];
-    const double hx = c2 + (j > 0 ? y[p - 1] : 0.0) + (j + 1 < S.spx_nx ? y[p + 1] : 0.0);
-    const double hy = c2 + (i > 0 ? y[p - S.spx_nx] : 0.0) + (i + 1 < S.spx_ny ? y[p + S.spx_nx] : 0.0);
+    const double c2 = -2.0 * sv(p);
+    const double hx = c2 + (j > 0 ? sv(p - 1) : 0.0) + (j + 1 < S.spx_nx ? sv(p + 1) : 0.0);
+    const double hy = c2 + (i > 0 ? sv(p - S.spx_nx) : 0.0) + (i + 1 < S.spx_ny ? sv(p + S.spx_nx) : 0.0);
     es = fma(hx, hx, fma(hy, hy, es));
   }
-  // E_D = |f s - d|^2 / 2 in units of sigma, from the residuals themselves: the difference
-  // d^T C_D^-1 d - D^T s_MP of two sums ~ N_d (S/N)^2 would cancel to ~1e-8 of them
-  // (the rows' dot products in double-float against s_MP split in place into (hi, lo))
-  __syncthreads();
-  float2 *ys = reinterpret_cast<float2 *>(y);
-  for (int i = tid; i < n; i += PIX_THREADS) {
-    const double v = y[i];
-    ys[i] = df_split(v);
-  }
-  __syncthreads();
-  double ed = 0.0;
+  return es;
+}
+
+// the sum of squared residuals (f_q s - d_q)^2 / sigma_q^2 over the masked rows q0, q0 + qstep,
+// ... below q1, one warp per row (lane 0 holds the warp's share): the dot products in
+// double-float against s_MP
+__device__ __forceinline__ double pix_ed_rows(const SysDev &S, const PixDev &pd, int b,
+                                              const float2 *ys, int q0, int q1, int qstep) {
+  const int lane = threadIdx.x & 31, n = S.spx_ns, ldg = pd.ldg;
   const float *g = pd.g + (size_t)b * pd.max_nd * ldg;
-  for (int q = warp; q < S.n_mask; q += PIX_THREADS / 32) {
+  double ed = 0.0;
+  for (int q = q0; q < q1; q += qstep) {
     const float *gq = g + (size_t)q * ldg;
     float hi = 0.0f, lo = 0.0f;
     for (int k = lane; k < n; k += 32) df_fma(hi, lo, make_float2(gq[k], 0.0f), ys[k]);
@@ -536,29 +638,251 @@ __global__ void __launch_bounds__(PIX_THREADS, 2) k_pix_eval(const SysDev *__res
     r -= (double)gq[n];
     if (lane == 0) ed = fma(r, r, ed);
   }
-  for (int off = 16; off > 0; off >>= 1) {
-    es += __shfl_xor_sync(0xffffffffu, es, off);
-    ed += __shfl_xor_sync(0xffffffffu, ed, off);
-  }
-  __shared__ double red2[PIX_THREADS / 32];
-  if (lane == 0) {
-    red[warp] = es;
-    red2[warp] = ed;
-  }
+  return ed;
+}
+
+// sum over the CTA of v (the result in thread 0)
+template <int NT>
+__device__ __forceinline__ double pix_block_sum(double v, double *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   __syncthreads();
-  if (tid == 0) {
-    double ES = 0.0, ED = 0.0;
-    for (int w = 0; w < PIX_THREADS / 32; ++w) {
-      ES += red[w];
-      ED += red2[w];
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < NT / 32; ++w) s += red[w];
+  return s;
+}
+
+// ln P from its parts, then one step of the search (thread 0 of the sample's last kernel)
+__device__ __forceinline__ void pix_conclude(const SysDev &S, const PixDev &pd, int b, double t,
+                                             double half_logdet, int bad, double ES, double ED) {
+  const double lnP = -ED - exp(t) * ES - half_logdet + 0.5 * S.spx_ns * t + S.spx_const;
+  const double phi = (bad || !isfinite(lnP)) ? INFINITY : -lnP;
+  brent_step(pd.srch[b], phi, S.spx_iters);
+  if (pd.nfac) atomicAdd(pd.nfac, 1ull);
+}
+
+// ---------------------------------------------------------------------------------------
+// One evidence evaluation per sample at its pending ln lambda, one CTA per sample (the form for
+// batches that fill the GPU; final_pass: at the best point, with s_MP written to
+// s_out[b * s_stride ..]).
+__global__ void __launch_bounds__(PIX_THREADS, 2) k_pix_eval(const SysDev *__restrict__ sysv,
+                                                          const int *__restrict__ sys_id, WsDev ws,
+                                                          PixDev pd, int final_pass, double *s_out,
+                                                          int s_stride) {
+  const int b = blockIdx.x;
+  const SysDev &S = sysv[sys_id[b]];
+  double t;
+  if (!pix_active(S, ws, pd, b, final_pass, t)) return;
+  const int n = S.spx_ns, lda = n + 1, tid = threadIdx.x;
+  float2 *A = pix_A(pd, b);
+  float2 *rd = pd.rd + (size_t)b * pd.max_ns, *s = pd.s + (size_t)b * pd.max_ns;
+  pix_assemble(S, pd, b, exp(t), tid, PIX_THREADS);
+  __shared__ float2 Ds[32][33], Rs[32], sb[32];
+  __shared__ float2 Pi[64][33], Pj[64][33];  // (hi, lo) pairs of the panel rows
+  __shared__ double red[PIX_THREADS / 32];
+  __shared__ int bad;
+  if (tid == 0) bad = 0;
+  float2 pm = make_float2(1.0f, 0.0f);  // product of the pivots, pm * 2^pe (thread 0)
+  int pe = 0;
+  __syncthreads();
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    const int kb = min(32, n - k0), r0 = k0 + kb;
+    pix_diag<PIX_THREADS>(A, lda, k0, kb, Ds, Rs, &bad);
+    if (tid < 32) pix_pivot_product(Ds, kb, pm, pe);
+    if (tid < kb) rd[k0 + tid] = Rs[tid];
+    for (int e = tid; e < 32 * 32; e += PIX_THREADS) {
+      const int i = e >> 5, j = e & 31;
+      if (i < kb && j <= i) A[(size_t)(k0 + i) * lda + k0 + j] = Ds[i][j];
     }
-    ES *= 0.5;
-    ED *= 0.5;
-    const double lnP = -ED - lam * ES - half_logdet + 0.5 * n * t + S.spx_const;
-    const double phi = (bad || !isfinite(lnP)) ? INFINITY : -lnP;
-    brent_step(*sp, phi, S.spx_iters);
-    if (pd.nfac) atomicAdd(pd.nfac, 1ull);
+    pix_panel_rows(A, lda, k0, kb, Ds, Rs, r0 + tid, n + 1, PIX_THREADS);
+    __syncthreads();
+    // trailing update M22 -= L21 L21^T, 64 x 64 tiles
+    const int T = (n + 1 - r0 + 63) / 64;
+    for (int ti = 0; ti < T; ++ti)
+      for (int tj = 0; tj <= ti; ++tj) pix_tile<PIX_THREADS>(A, lda, n, k0, kb, r0, ti, tj, Pi, Pj);
   }
+  for (int k0 = ((n - 1) / 32) * 32; k0 >= 0; k0 -= 32)
+    pix_bsolve_block<PIX_THREADS>(A, lda, n, rd, s, k0, min(32, n - k0), tid, PIX_THREADS, Pi, Pj[0],
+                                  sb);
+  if (final_pass) {
+    if (s_out)
+      for (int i = tid; i < n; i += PIX_THREADS) s_out[(size_t)b * s_stride + i] = df_val(s[i]);
+    return;
+  }
+  const double es = pix_es_part(S, s, tid, PIX_THREADS);
+  const double ed = pix_ed_rows(S, pd, b, s, tid >> 5, S.n_mask, PIX_THREADS / 32);
+  const double ES = pix_block_sum<PIX_THREADS>(es, red);
+  const double ED = pix_block_sum<PIX_THREADS>(ed, red);
+  if (tid == 0) pix_conclude(S, pd, b, t, pix_half_logdet(pm, pe), bad, 0.5 * ES, 0.5 * ED);
+}
+
+// ---------------------------------------------------------------------------------------
+// The same evaluation as a sequence of launches, for batches too small to fill the GPU with one
+// CTA per sample: the kernel boundaries order the steps, and each step spreads over many CTAs
+// per sample (grid y = sample).
+//   k_pixm_begin    M assembled; the sample's pivot product and flag reset
+//   per 32-column panel step k0:
+//     k_pixm_panel    every CTA factors the diagonal block (read from M, which nothing writes
+//                     in this launch) and solves its share of the panel rows (row N_s among
+//                     them); CTA 0 keeps the factored block in dgf, the reciprocals in rd, and
+//                     folds the pivots into the sample's product
+//     k_pixm_trail    one 64 x 64 tile of the trailing update per CTA; CTA 0 also moves dgf
+//                     into M's diagonal block (which nothing else touches in this launch)
+//   per 32-row block of the backward solve, from the bottom:
+//     k_pixm_bsolve   every CTA solves the block (its y entries are not written in this
+//                     launch), CTA 0 writes s_MP there, each CTA updates its share of y above
+//   k_pixm_es       E_S (or, in the final pass, s_MP to the caller)
+//   k_pixm_ed       E_D over chunks of PIXM_ED_ROWS masked rows, one partial sum per chunk
+//   k_pixm_fin      the partials summed in order, ln P, one search step
+
+__global__ void __launch_bounds__(PIX_THREADS) k_pixm_begin(const SysDev *__restrict__ sysv,
+                                                          const int *__restrict__ sys_id, WsDev ws,
+                                                          PixDev pd, int final_pass) {
+  const int b = blockIdx.y;
+  const SysDev &S = sysv[sys_id[b]];
+  double t;
+  if (!pix_active(S, ws, pd, b, final_pass, t)) return;
+  pix_assemble(S, pd, b, exp(t), (size_t)blockIdx.x * PIX_THREADS + threadIdx.x,
+               (size_t)gridDim.x * PIX_THREADS);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    pd.pm[b] = make_float2(1.0f, 0.0f);
+    pd.pe[b] = 0;
+    pd.bad[b] = 0;
+  }
+}
+
+__global__ void __launch_bounds__(PIX_THREADS) k_pixm_panel(const SysDev *__restrict__ sysv,
+                                                          const int *__restrict__ sys_id, WsDev ws,
+                                                          PixDev pd, int final_pass, int k0) {
+  const int b = blockIdx.y;
+  const SysDev &S = sysv[sys_id[b]];
+  double t;
+  if (!pix_active(S, ws, pd, b, final_pass, t)) return;
+  const int n = S.spx_ns;
+  if (k0 >= n) return;
+  const int kb = min(32, n - k0), r0 = k0 + kb, lda = n + 1, tid = threadIdx.x;
+  if (blockIdx.x > 0 && r0 + (int)blockIdx.x * PIX_THREADS > n) return;
+  float2 *A = pix_A(pd, b);
+  __shared__ float2 Ds[32][33], Rs[32];
+  __shared__ int bad;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  pix_diag<PIX_THREADS>(A, lda, k0, kb, Ds, Rs, &bad);
+  if (blockIdx.x == 0) {
+    float2 *dst = pd.dgf + (size_t)b * 32 * 32;
+    for (int e = tid; e < 32 * 32; e += PIX_THREADS) dst[e] = Ds[e >> 5][e & 31];
+    if (tid < kb) pd.rd[(size_t)b * pd.max_ns + k0 + tid] = Rs[tid];
+    if (tid < 32) {
+      float2 pm = pd.pm[b];
+      int pe = pd.pe[b];
+      pix_pivot_product(Ds, kb, pm, pe);
+      if (tid == 0) {
+        pd.pm[b] = pm;
+        pd.pe[b] = pe;
+        if (bad) pd.bad[b] = 1;
+      }
+    }
+  }
+  pix_panel_rows(A, lda, k0, kb, Ds, Rs, r0 + blockIdx.x * PIX_THREADS + tid, n + 1,
+                 gridDim.x * PIX_THREADS);
+}
+
+__global__ void __launch_bounds__(PIX_THREADS, 2) k_pixm_trail(const SysDev *__restrict__ sysv,
+                                                             const int *__restrict__ sys_id, WsDev ws,
+                                                             PixDev pd, int final_pass, int k0) {
+  const int b = blockIdx.y;
+  const SysDev &S = sysv[sys_id[b]];
+  double t;
+  if (!pix_active(S, ws, pd, b, final_pass, t)) return;
+  const int n = S.spx_ns;
+  if (k0 >= n) return;
+  const int kb = min(32, n - k0), r0 = k0 + kb, lda = n + 1;
+  float2 *A = pix_A(pd, b);
+  if (blockIdx.x == 0) {
+    const float2 *src = pd.dgf + (size_t)b * 32 * 32;
+    for (int e = threadIdx.x; e < 32 * 32; e += PIX_THREADS) {
+      const int i = e >> 5, j = e & 31;
+      if (i < kb && j <= i) A[(size_t)(k0 + i) * lda + k0 + j] = src[e];
+    }
+  }
+  const int T = (n + 1 - r0 + 63) / 64;
+  const int idx = blockIdx.x;
+  if (idx >= T * (T + 1) / 2) return;
+  // tile idx of the lower triangle, row-major: ti (ti + 1) / 2 <= idx < (ti + 1) (ti + 2) / 2
+  int ti = (int)((sqrt(8.0 * idx + 1.0) - 1.0) * 0.5);
+  while (ti * (ti + 1) / 2 > idx) --ti;
+  while ((ti + 1) * (ti + 2) / 2 <= idx) ++ti;
+  const int tj = idx - ti * (ti + 1) / 2;
+  __shared__ float2 Pi[64][33], Pj[64][33];
+  pix_tile<PIX_THREADS>(A, lda, n, k0, kb, r0, ti, tj, Pi, Pj);
+}
+
+__global__ void __launch_bounds__(PIX_THREADS) k_pixm_bsolve(const SysDev *__restrict__ sysv,
+                                                           const int *__restrict__ sys_id, WsDev ws,
+                                                           PixDev pd, int final_pass, int k0) {
+  const int b = blockIdx.y;
+  const SysDev &S = sysv[sys_id[b]];
+  double t;
+  if (!pix_active(S, ws, pd, b, final_pass, t)) return;
+  const int n = S.spx_ns;
+  if (k0 >= n) return;
+  if (blockIdx.x > 0 && (int)blockIdx.x * PIX_THREADS >= k0) return;
+  __shared__ float2 Lb[32][33], rb[32], sb[32];
+  pix_bsolve_block<PIX_THREADS>(pix_A(pd, b), n + 1, n, pd.rd + (size_t)b * pd.max_ns,
+                                blockIdx.x == 0 ? pd.s + (size_t)b * pd.max_ns : nullptr, k0,
+                                min(32, n - k0), blockIdx.x * PIX_THREADS + threadIdx.x,
+                                gridDim.x * PIX_THREADS, Lb, rb, sb);
+}
+
+__global__ void __launch_bounds__(PIX_THREADS) k_pixm_es(const SysDev *__restrict__ sysv,
+                                                       const int *__restrict__ sys_id, WsDev ws,
+                                                       PixDev pd, int final_pass, double *s_out,
+                                                       int s_stride) {
+  const int b = blockIdx.x;
+  const SysDev &S = sysv[sys_id[b]];
+  double t;
+  if (!pix_active(S, ws, pd, b, final_pass, t)) return;
+  const float2 *s = pd.s + (size_t)b * pd.max_ns;
+  if (final_pass) {
+    if (s_out)
+      for (int i = threadIdx.x; i < S.spx_ns; i += PIX_THREADS) s_out[(size_t)b * s_stride + i] = df_val(s[i]);
+    return;
+  }
+  __shared__ double red[PIX_THREADS / 32];
+  const double ES = pix_block_sum<PIX_THREADS>(pix_es_part(S, s, threadIdx.x, PIX_THREADS), red);
+  if (threadIdx.x == 0) pd.es[b] = ES;
+}
+
+__global__ void __launch_bounds__(PIX_THREADS) k_pixm_ed(const SysDev *__restrict__ sysv,
+                                                       const int *__restrict__ sys_id, WsDev ws,
+                                                       PixDev pd) {
+  const int b = blockIdx.y;
+  const SysDev &S = sysv[sys_id[b]];
+  double t;
+  if (!pix_active(S, ws, pd, b, 0, t)) return;
+  const int q0 = blockIdx.x * PIXM_ED_ROWS;
+  if (q0 >= S.n_mask) return;
+  __shared__ double red[PIX_THREADS / 32];
+  const double ed = pix_ed_rows(S, pd, b, pd.s + (size_t)b * pd.max_ns, q0 + (threadIdx.x >> 5),
+                                min(S.n_mask, q0 + PIXM_ED_ROWS), PIX_THREADS / 32);
+  const double ED = pix_block_sum<PIX_THREADS>(ed, red);
+  if (threadIdx.x == 0) pd.edp[(size_t)b * pd.ed_chunks + blockIdx.x] = ED;
+}
+
+__global__ void k_pixm_fin(const SysDev *__restrict__ sysv, const int *__restrict__ sys_id,
+                           WsDev ws, PixDev pd, int B) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const SysDev &S = sysv[sys_id[b]];
+  double t;
+  if (!pix_active(S, ws, pd, b, 0, t)) return;
+  const int nch = (S.n_mask + PIXM_ED_ROWS - 1) / PIXM_ED_ROWS;
+  double ED = 0.0;
+  for (int c = 0; c < nch; ++c) ED += pd.edp[(size_t)b * pd.ed_chunks + c];
+  pix_conclude(S, pd, b, t, pix_half_logdet(pd.pm[b], pd.pe[b]), pd.bad[b], 0.5 * pd.es[b], 0.5 * ED);
 }
 
 // the image term of logL: terms[0] = -2 ln P at the best lambda
@@ -600,12 +924,20 @@ cudaError_t pixsrc_ws_ensure(glad_ctx *c, int B) {
   d.ldg = ldg;
   d.max_ns = c->max_ns;
   d.max_nd = c->max_nd;
+  d.ed_chunks = (c->max_nd + PIXM_ED_ROWS - 1) / PIXM_ED_ROWS;
   const bool ok = take((void **)&d.g, sizeof(float) * b * c->max_nd * ldg) &&
                   take((void **)&d.F, sizeof(double) * b * ldg * ldg) &&
-                  take((void **)&d.A, sizeof(double) * b * c->max_ns * c->max_ns) &&
-                  take((void **)&d.y, sizeof(double) * b * c->max_ns) &&
+                  take((void **)&d.A, sizeof(float2) * b * (c->max_ns + 1) * (c->max_ns + 1)) &&
+                  take((void **)&d.s, sizeof(float2) * b * c->max_ns) &&
+                  take((void **)&d.rd, sizeof(float2) * b * c->max_ns) &&
                   take((void **)&d.srch, sizeof(PixSearch) * b) &&
-                  take((void **)&d.nfac, sizeof(unsigned long long));
+                  take((void **)&d.nfac, sizeof(unsigned long long)) &&
+                  take((void **)&d.pm, sizeof(float2) * b) &&
+                  take((void **)&d.pe, sizeof(int) * b) &&
+                  take((void **)&d.bad, sizeof(int) * b) &&
+                  take((void **)&d.es, sizeof(double) * b) &&
+                  take((void **)&d.edp, sizeof(double) * b * d.ed_chunks) &&
+                  take((void **)&d.dgf, sizeof(float2) * b * 32 * 32);
   if (!ok) {
     for (void *p : w.allocs) cudaFree(p);
     w.allocs.clear();
@@ -621,6 +953,17 @@ void pixsrc_ws_free(glad_ctx *c) {
   for (void *p : c->pws->allocs) cudaFree(p);
   delete c->pws;
   c->pws = nullptr;
+}
+
+// the multi-launch form for batches with fewer samples than two per SM (the one-CTA-per-sample
+// kernel holds two CTAs per SM), unless the context fixes the form
+bool pixsrc_multi_launch(glad_ctx *c, int B) {
+  if (c->tune.pix_path == 1) return false;
+  if (c->tune.pix_path == 2) return true;
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  return B < 2 * nsm;
 }
 
 unsigned long long pixsrc_factorizations(glad_ctx *c) {
@@ -654,14 +997,41 @@ cudaError_t launch_pixsrc(glad_ctx *c, const int *sys_id, int B, cudaStream_t st
         c->d_sys, sys_id, c->ws.d, pd);
     return cudaGetLastError();
   };
+  // one evaluation per sample: one CTA per sample, or the multi-launch form
+  const bool multi = pixsrc_multi_launch(c, B);
+  auto eval = [&](int final_pass, double *so) {
+    if (!multi) {
+      k_pix_eval<<<B, PIX_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, pd, final_pass, so,
+                                            GLAD_MAX_SRCPIX);
+      return;
+    }
+    // the grids from the largest system (smaller ones leave the extra CTAs idle)
+    const int ns = pd.max_ns;
+    const int nbeg = std::max(1, (int)(((size_t)(ns + 1) * ns + PIX_THREADS * 16 - 1) / (PIX_THREADS * 16)));
+    k_pixm_begin<<<dim3(nbeg, B), PIX_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, pd, final_pass);
+    for (int k0 = 0; k0 < ns; k0 += 32) {
+      const int rows = std::max(1, ns + 1 - k0 - 32);  // panel rows, row N_s among them
+      const int T = (rows + 63) / 64;
+      const int np = (rows + PIX_THREADS - 1) / PIX_THREADS;
+      k_pixm_panel<<<dim3(np, B), PIX_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, pd, final_pass, k0);
+      k_pixm_trail<<<dim3(T * (T + 1) / 2, B), PIX_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, pd,
+                                                                      final_pass, k0);
+    }
+    for (int k0 = ((ns - 1) / 32) * 32; k0 >= 0; k0 -= 32)
+      k_pixm_bsolve<<<dim3(std::max(1, (k0 + PIX_THREADS - 1) / PIX_THREADS), B), PIX_THREADS, 0, st>>>(
+          c->d_sys, sys_id, c->ws.d, pd, final_pass, k0);
+    k_pixm_es<<<B, PIX_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, pd, final_pass, so, GLAD_MAX_SRCPIX);
+    if (!final_pass) {
+      k_pixm_ed<<<dim3(pd.ed_chunks, B), PIX_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, pd);
+      k_pixm_fin<<<(B + 127) / 128, 128, 0, st>>>(c->d_sys, sys_id, c->ws.d, pd, B);
+    }
+  };
   auto ev = [&]() -> cudaError_t {
     k_pix_init<<<(B + 127) / 128, 128, 0, st>>>(c->d_sys, sys_id, c->ws.d, pd, B);
     // the first pass evaluates the starting point, each later one a trial point
-    for (int it = 0; it < max_iter; ++it)
-      k_pix_eval<<<B, PIX_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, pd, 0, nullptr, 0);
+    for (int it = 0; it < max_iter; ++it) eval(0, nullptr);
     k_pix_finish<<<(B + 127) / 128, 128, 0, st>>>(c->d_sys, sys_id, c->ws.d, pd, B, lam_out, lnP_out);
-    if (s_out)
-      k_pix_eval<<<B, PIX_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, pd, 1, s_out, GLAD_MAX_SRCPIX);
+    if (s_out) eval(1, s_out);
     return cudaGetLastError();
   };
   e = GLAD_PROF(c, st, KID_PIX_OP, op());

@@ -172,6 +172,11 @@ class GladContext:
         torch.cuda.synchronize()
         return int(self.lib.glad_pix_factorizations(self.handle))
 
+    def set_pix_path(self, mode):
+        """Form of the pixelated source's evidence evaluations (glad_set_pix_path): 0 by batch
+        size, 1 one CTA per sample, 2 multi-launch."""
+        _lib.check(self.lib.glad_set_pix_path(self.handle, int(mode)), "glad_set_pix_path")
+
     def autotune(self, theta, sys_id=None, with_grad=False):
         """Time the JAM launch shapes on this batch and keep the fastest (glad_autotune)."""
         theta, sys_id, B = self._check_theta(theta, sys_id)

@@ -288,14 +288,17 @@ def workload_systems(w: int, small: bool = False):
     9: workload 1's system with the pixelated source (Sect. 3.1.1): a 30 x 30 grid over
        +-0.6" around the source, fitted to the arcs in the annulus 0.9" - 2.5" (N_d = 6,840
        pixels, N_s = 900: Table 1's O(10^4) and O(10^3)), B=296 (two samples per SM)
+    10: Table 3's timing configuration: workload 8's composite system with a 64 x 64 source grid
+       over +-0.6" around the source, fitted to the arcs in 0.8" - 2.95" (N_d = 10,148,
+       N_s = 4,096), one sample per call (B=1)
     """
-    rng = np.random.Generator(np.random.PCG64(1000 + {5: 1, 6: 4, 7: 1, 8: 1, 9: 1}.get(w, w)))
+    rng = np.random.Generator(np.random.PCG64(1000 + {5: 1, 6: 4, 7: 1, 8: 1, 9: 1, 10: 1}.get(w, w)))
     if w == 0:
         s = base_system("w0", n_img_px=64, ss=1, psf_k=11, sky=32, kss=1, n_mass=10,
                         n_light=10, n_gl=32, n_bins=20, bins="annular", rng=rng,
                         has_bh=False, n_sis=0, second_light=False)
         return [s], 1
-    if w in (1, 2, 5, 7, 8, 9):
+    if w in (1, 2, 5, 7, 8, 9, 10):
         s = base_system("w1", n_img_px=200, ss=2, psf_k=21, sky=60, kss=4, n_mass=20,
                         n_light=10, n_gl=32, n_bins=50, bins="voronoi", rng=rng,
                         has_bh=True, n_sis=1, second_light=True)
@@ -310,9 +313,16 @@ def workload_systems(w: int, small: bool = False):
             s.update(name="w5", jam_align=1, sph_nr=128, sph_nw=8, sph_nlos=32)
         if w == 7:
             s.update(name="w7", sheet=1, distance_mode=1)
-        if w == 8:
+        if w in (8, 10):
             s = composite_light(s)
             s.update(name="w8", sheet=1, distance_mode=1)
+        if w == 10:
+            t = theta_truth_composite()
+            c = (float(t[IDX["x_src"]]), float(t[IDX["y_src"]]))
+            s.update(name="w10", src_pix=1, spx_n=(64, 64),
+                     spx_box=(c[0] - 0.6, c[0] + 0.6, c[1] - 0.6, c[1] + 0.6),
+                     mask=arc_mask(s["nx"], s["pix"], 0.8, 2.95))
+            return [s], 1
         return [s], (64 if w == 2 else 256)
     if w == 3:
         systems = []
@@ -354,6 +364,10 @@ def workload_thetas(w: int, B: int, n_sys: int):
         th = draw_prior_sheet(rng, B, lam_hi=1.0)
     elif w == 8:
         th = draw_prior_composite(rng, B)
+    elif w == 10:
+        # the timing configuration's sample: the mock's own parameters (the regularisation
+        # search then ends inside its interval, as near a posterior mode)
+        th = np.tile(theta_truth_composite(), (B, 1))
     else:
         th = draw_prior(rng, B)
     if n_sys == 1:

@@ -8,7 +8,9 @@ sample.  Tolerances: ln P and logL 0.05 + 5e-6 |ln P| (the FP32 rays leave ~1e-7
 beta, ~1e-6 of a bilinear weight over a source pixel, so a poor fit's data term moves by ~1e-6
 of itself, as for the Sersic source, tests/systems.logl_tol), and 0.05 absolute with the rays
 in FP64 (precision mode 1); the optimum within 0.05 in ln lambda; s_MP at the GPU's lambda
-within 1e-3 of max |s| of the oracle's solution at the same lambda."""
+within 1e-3 of max |s| of the oracle's solution at the same lambda.  Both forms of the evidence
+evaluation (one CTA per sample, and the multi-launch form that small batches take by default)
+are run on the square, ragged, mixed and RXJ1131-scale cases, and agree with each other."""
 import numpy as np
 import pytest
 
@@ -74,8 +76,10 @@ def small():
     return s, _ctx([s])
 
 
-def test_square_grid_against_oracle(small):
+@pytest.mark.parametrize("path", [1, 2])
+def test_square_grid_against_oracle(small, path):
     s, ctx = small
+    ctx.set_pix_path(path)
     th = systems.near_truth_thetas(2, seed=201)
     for b in range(2):
         check_against_oracle(ctx, s, th, b=b)
@@ -87,24 +91,31 @@ def test_square_grid_against_oracle(small):
         assert abs(float(terms[b, 0]) + 2 * ev["lnP"]) < 2 * lnp_tol(ev["lnP"])
         assert abs(float(logL[b]) - ev["logL"]) < lnp_tol(ev["logL"]), (float(logL[b]), ev["logL"])
     assert ctx.pix_factorizations() > 0
+    ctx.set_pix_path(0)
 
 
-def test_ragged_grid_and_64px_system():
+@pytest.mark.parametrize("path", [1, 2])
+def test_ragged_grid_and_64px_system(path):
     s = pix_system(systems.small_system(7), n=(13, 11), half=0.5)
-    check_against_oracle(_ctx([s]), s, systems.near_truth_thetas(1, seed=203))
+    ctx = _ctx([s])
+    ctx.set_pix_path(path)
+    check_against_oracle(ctx, s, systems.near_truth_thetas(1, seed=203))
     sys_list, ths, _ = model.workload(0)
     s0 = pix_system(sys_list[0], n=(12, 12), half=0.45, th=ths[0])
     ctx = _ctx([s0])
+    ctx.set_pix_path(path)
     check_against_oracle(ctx, s0, ths[:1])
     # a poor fit (ln P ~ -8e4): with the rays in FP64 the evidence meets 0.05 absolute
     ctx.set_precision(1)
     check_against_oracle(ctx, s0, ths[:1], rel=0.0)
 
 
-def test_mixed_batch_sersic_invalid_and_grid_sweep():
+@pytest.mark.parametrize("path", [1, 2])
+def test_mixed_batch_sersic_invalid_and_grid_sweep(path):
     base = systems.small_system(7)
     sweep = [pix_system(base, n=(n, n)) for n in (8, 10, 12)]
     ctx = _ctx([base] + sweep)
+    ctx.set_pix_path(path)
     th = systems.near_truth_thetas(6, seed=205)
     th[4, I["q"]] = 1.3  # outside the domain
     sid_np = np.array([0, 1, 2, 3, 2, 0], np.int32)
@@ -137,12 +148,20 @@ def test_rxj1131_scale_sampled_against_oracle():
     s = sys_list[0]
     ctx = _ctx(sys_list)
     B = 16
-    lam, lnP = ctx.pixsrc(_th(th[:B]))
-    logL, st = ctx.loglike(_th(th[:B]))
-    assert np.all(st.cpu().numpy() == 0)
-    ev = model.evaluate(th[0], s)
-    assert abs(float(lnP[0]) - ev["lnP"]) < lnp_tol(ev["lnP"]), (float(lnP[0]), ev["lnP"])
-    assert abs(float(logL[0]) - ev["logL"]) < lnp_tol(ev["logL"]), (float(logL[0]), ev["logL"])
+    out = {}
+    for path in (1, 2):
+        ctx.set_pix_path(path)
+        lam, lnP = ctx.pixsrc(_th(th[:B]))
+        logL, st = ctx.loglike(_th(th[:B]))
+        assert np.all(st.cpu().numpy() == 0)
+        ev = model.evaluate(th[0], s)
+        assert abs(float(lnP[0]) - ev["lnP"]) < lnp_tol(ev["lnP"]), (float(lnP[0]), ev["lnP"])
+        assert abs(float(logL[0]) - ev["logL"]) < lnp_tol(ev["logL"]), (float(logL[0]), ev["logL"])
+        out[path] = (np.log(lam.cpu().numpy()), lnP.cpu().numpy())
+    # the two forms: the same arithmetic in another order (the factor's double-float sums,
+    # the residual sums' reduction order), so the searches end at the same optimum
+    assert np.allclose(out[1][1], out[2][1], rtol=1e-9, atol=1e-3)
+    assert np.allclose(out[1][0], out[2][0], rtol=0, atol=1e-3)
 
 
 def test_graph_replay_and_static_refusal(small):
@@ -183,4 +202,30 @@ def test_large_grids_against_oracle(n):
     # and the largest grid the library takes (68 x 68 = 4,624 pixels, the top of the paper's
     # 60^2 - 68^2 sweep)
     s = pix_system(systems.small_system(7), n=(n, n), half=0.6)
-    check_against_oracle(_ctx([s]), s, systems.near_truth_thetas(1, seed=213), check_s=(n == 40))
+    ctx = _ctx([s])
+    th = systems.near_truth_thetas(1, seed=213)
+    check_against_oracle(ctx, s, th, check_s=(n == 40))
+    if n == 40:
+        # one CTA per sample on the same case: the same optimum
+        lam2, lnP2 = ctx.pixsrc(_th(th))
+        ctx.set_pix_path(1)
+        lam1, lnP1 = ctx.pixsrc(_th(th))
+        assert abs(float(lnP1[0]) - float(lnP2[0])) < 1e-3 + 1e-9 * abs(float(lnP2[0]))
+        assert abs(np.log(float(lam1[0]) / float(lam2[0]))) < 1e-3
+
+
+def test_composite_class_with_the_dpie_sheet():
+    # the pixelated source behind Table 3's joint model: the composite mass class (Chameleons,
+    # elliptical NFW halo, black hole) with the internal sheet in distance mode 1
+    from .test_gpu_composite import comp_small, near
+    s = dict(comp_small(7))
+    th = near(2, 215)
+    c = (th[0, I["x_src"]], th[0, I["y_src"]])
+    # a 12 x 12 grid over +-0.6": lambda ~ 12 at the optimum, F + lambda C conditioned ~2e4.
+    # (Over +-0.45" the search ends near lambda ~ 1e-4 with the condition ~3e9: ln P still
+    # agrees, being stationary in s, but s_MP then moves by ~1e-3 of max |s| under the FP32
+    # Gram entries' ~1e-7 rounding.)
+    s.update(src_pix=1, spx_n=(12, 12), spx_box=(c[0] - 0.6, c[0] + 0.6, c[1] - 0.6, c[1] + 0.6))
+    ctx = _ctx([s])
+    for b in range(2):
+        check_against_oracle(ctx, s, th, b=b, check_s=(b == 0))
