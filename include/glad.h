@@ -315,7 +315,7 @@ unsigned long long glad_pix_factorizations(glad_ctx *ctx);
  * mode 1: one CTA per sample does the whole evaluation (for batches that fill the GPU); mode 2:
  * a sequence of launches per evaluation, each 32-column panel step of the factorisation spread
  * over many CTAs per sample (for small batches: one sample then uses the whole GPU); mode 0
- * (the default): mode 2 for batches of fewer than two samples per SM, else mode 1.
+ * (the default): mode 2 for batches of at most two samples per SM, else mode 1.
  * GLAD_EINVAL for other modes. */
 glad_status glad_set_pix_path(glad_ctx *ctx, int mode);
 

@@ -61,6 +61,12 @@ struct PixWs {
   int B = 0;
   PixDev d{};
   std::vector<void *> allocs;
+  // the multi-launch form's streams: hi (the critical path: panels, tile column 0, solves) at
+  // the greatest priority, aux (the other trailing tiles) at the least, so that a panel's CTAs
+  // take the first SMs that the tiles free; forked from and joined back into the caller's
+  // stream by events
+  cudaStream_t hi = nullptr, aux = nullptr;
+  cudaEvent_t ev_p = nullptr, ev_r = nullptr, ev_in = nullptr, ev_out = nullptr;
 };
 
 namespace {
@@ -71,6 +77,7 @@ constexpr double TTOL = 1e-3;                // tolerance in ln lambda (ln P mov
 #define PIX_F_WARPS 8
 #define PIX_THREADS 256
 #define PIXM_ED_ROWS 64
+#define PIXM_PANEL_THREADS 128
 
 // ---------------------------------------------------------------------------------------
 // Brent's method (Brent 1973, "Algorithms for Minimization without Derivatives", ch. 5):
@@ -430,8 +437,9 @@ __device__ __forceinline__ void pix_diag(const float2 *A, int lda, int k0, int k
   constexpr int EPT = 1024 / NT;  // block elements per thread
   const int tid = threadIdx.x;
   __shared__ float2 Ls[32];
-  for (int e = tid; e < 32 * 32; e += NT) {
-    const int i = e >> 5, j = e & 31;
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int e = tid + q * NT, i = e >> 5, j = e & 31;
     Ds[i][j] = (i < kb && j <= i) ? A[(size_t)(k0 + i) * lda + k0 + j]
                                   : make_float2(i == j ? 1.0f : 0.0f, 0.0f);
   }
@@ -500,7 +508,33 @@ __device__ __forceinline__ double pix_half_logdet(float2 pm, int pe) {
 }
 
 // panel rows i = first, first + step, ... below last: x L11^T = a, in double-float (the
-// divisions as products with the pivots' reciprocals)
+// divisions as products with the pivots' reciprocals), each thread's row staged in its column
+// of X[32][NT] in shared memory: the loops stay rolled (a fully unrolled 32-column triangle in
+// registers is ~7k instructions, which the instruction cache does not hold)
+template <int NT>
+__device__ __forceinline__ void pix_panel_rows_smem(float2 *A, int lda, int k0, int kb,
+                                                    const float2 (*Ds)[33], const float2 *Rs,
+                                                    float2 (*X)[NT], int first, int last, int step) {
+  const int t = threadIdx.x;
+  for (int i = first; i < last; i += step) {
+    float2 *ai = A + (size_t)i * lda + k0;
+#pragma unroll
+    for (int m = 0; m < 32; ++m)
+      if (m < kb) X[m][t] = ai[m];
+    for (int m = 0; m < kb; ++m) {
+      float hi = 0.0f, lo = 0.0f;
+#pragma unroll 4
+      for (int q = 0; q < m; ++q) df_fma(hi, lo, X[q][t], Ds[m][q]);
+      X[m][t] = df_mul(df_sub(X[m][t], hi, lo), Rs[m]);
+    }
+#pragma unroll
+    for (int m = 0; m < 32; ++m)
+      if (m < kb) ai[m] = X[m][t];
+  }
+}
+
+// the same with the row in registers (fully unrolled; the one-CTA-per-sample kernel, which has
+// no room for X, and whose other CTA on the SM covers the instruction fetches)
 __device__ __forceinline__ void pix_panel_rows(float2 *A, int lda, int k0, int kb,
                                                const float2 (*Ds)[33], const float2 *Rs, int first,
                                                int last, int step) {
@@ -528,9 +562,11 @@ __device__ __forceinline__ void pix_panel_rows(float2 *A, int lda, int k0, int k
 template <int NT>
 __device__ __forceinline__ void pix_tile(float2 *A, int lda, int n, int k0, int kb, int r0, int ti,
                                          int tj, float2 (*Pi)[33], float2 (*Pj)[33]) {
+  static_assert(NT == 256, "16 x 16 threads, 4 x 4 outputs each");
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  for (int e = tid; e < 64 * 32; e += NT) {
-    const int r = e >> 5, m = e & 31;
+#pragma unroll
+  for (int q = 0; q < 64 * 32 / NT; ++q) {
+    const int e = tid + q * NT, r = e >> 5, m = e & 31;
     const int gi = r0 + ti * 64 + r, gj = r0 + tj * 64 + r;
     const float2 z = make_float2(0.0f, 0.0f);
     Pi[r][m] = (gi <= n && m < kb) ? A[(size_t)gi * lda + k0 + m] : z;
@@ -577,8 +613,9 @@ __device__ __forceinline__ void pix_bsolve_block(const float2 *A, int lda, int n
   float2 *y = const_cast<float2 *>(A) + (size_t)n * lda;
   // the block's factor and reciprocals staged first (Lb[32][33], rb[32] in shared memory): no
   // global load inside the sequential loop
-  for (int e = threadIdx.x; e < 32 * 32; e += NT) {
-    const int i = e >> 5, c = e & 31;
+#pragma unroll
+  for (int q = 0; q < 32 * 32 / NT; ++q) {
+    const int e = threadIdx.x + q * NT, i = e >> 5, c = e & 31;
     if (i < kb && c <= i) Lb[i][c] = A[(size_t)(k0 + i) * lda + k0 + c];
   }
   if (threadIdx.x < kb) rb[threadIdx.x] = rd[k0 + threadIdx.x];
@@ -600,7 +637,9 @@ __device__ __forceinline__ void pix_bsolve_block(const float2 *A, int lda, int n
   __syncthreads();
   for (int i = first; i < k0; i += step) {
     float hi = 0.0f, lo = 0.0f;
-    for (int m = 0; m < kb; ++m) df_fma(hi, lo, A[(size_t)(k0 + m) * lda + i], sb[m]);
+#pragma unroll
+    for (int m = 0; m < 32; ++m)
+      if (m < kb) df_fma(hi, lo, A[(size_t)(k0 + m) * lda + i], sb[m]);
     y[i] = df_sub(y[i], hi, lo);
   }
   __syncthreads();
@@ -754,9 +793,11 @@ __global__ void __launch_bounds__(PIX_THREADS) k_pixm_begin(const SysDev *__rest
   }
 }
 
-__global__ void __launch_bounds__(PIX_THREADS) k_pixm_panel(const SysDev *__restrict__ sysv,
-                                                          const int *__restrict__ sys_id, WsDev ws,
-                                                          PixDev pd, int final_pass, int k0) {
+__global__ void __launch_bounds__(PIXM_PANEL_THREADS) k_pixm_panel(const SysDev *__restrict__ sysv,
+                                                                 const int *__restrict__ sys_id,
+                                                                 WsDev ws, PixDev pd, int final_pass,
+                                                                 int k0) {
+  constexpr int NT = PIXM_PANEL_THREADS;
   const int b = blockIdx.y;
   const SysDev &S = sysv[sys_id[b]];
   double t;
@@ -764,16 +805,17 @@ __global__ void __launch_bounds__(PIX_THREADS) k_pixm_panel(const SysDev *__rest
   const int n = S.spx_ns;
   if (k0 >= n) return;
   const int kb = min(32, n - k0), r0 = k0 + kb, lda = n + 1, tid = threadIdx.x;
-  if (blockIdx.x > 0 && r0 + (int)blockIdx.x * PIX_THREADS > n) return;
+  if (blockIdx.x > 0 && r0 + (int)blockIdx.x * NT > n) return;
   float2 *A = pix_A(pd, b);
   __shared__ float2 Ds[32][33], Rs[32];
+  __shared__ float2 X[32][NT];
   __shared__ int bad;
   if (tid == 0) bad = 0;
   __syncthreads();
-  pix_diag<PIX_THREADS>(A, lda, k0, kb, Ds, Rs, &bad);
+  pix_diag<NT>(A, lda, k0, kb, Ds, Rs, &bad);
   if (blockIdx.x == 0) {
     float2 *dst = pd.dgf + (size_t)b * 32 * 32;
-    for (int e = tid; e < 32 * 32; e += PIX_THREADS) dst[e] = Ds[e >> 5][e & 31];
+    for (int e = tid; e < 32 * 32; e += NT) dst[e] = Ds[e >> 5][e & 31];
     if (tid < kb) pd.rd[(size_t)b * pd.max_ns + k0 + tid] = Rs[tid];
     if (tid < 32) {
       float2 pm = pd.pm[b];
@@ -786,13 +828,15 @@ __global__ void __launch_bounds__(PIX_THREADS) k_pixm_panel(const SysDev *__rest
       }
     }
   }
-  pix_panel_rows(A, lda, k0, kb, Ds, Rs, r0 + blockIdx.x * PIX_THREADS + tid, n + 1,
-                 gridDim.x * PIX_THREADS);
+  pix_panel_rows_smem<NT>(A, lda, k0, kb, Ds, Rs, X, r0 + blockIdx.x * NT + tid, n + 1, gridDim.x * NT);
 }
 
-__global__ void __launch_bounds__(PIX_THREADS, 2) k_pixm_trail(const SysDev *__restrict__ sysv,
+// part 0: the tiles of tile column 0 (the next diagonal block and panel among them); part 1:
+// the others, which the next panel step does not read
+__global__ void __launch_bounds__(PIX_THREADS, 3) k_pixm_trail(const SysDev *__restrict__ sysv,
                                                              const int *__restrict__ sys_id, WsDev ws,
-                                                             PixDev pd, int final_pass, int k0) {
+                                                             PixDev pd, int final_pass, int k0,
+                                                             int part) {
   const int b = blockIdx.y;
   const SysDev &S = sysv[sys_id[b]];
   double t;
@@ -801,7 +845,7 @@ __global__ void __launch_bounds__(PIX_THREADS, 2) k_pixm_trail(const SysDev *__r
   if (k0 >= n) return;
   const int kb = min(32, n - k0), r0 = k0 + kb, lda = n + 1;
   float2 *A = pix_A(pd, b);
-  if (blockIdx.x == 0) {
+  if (part == 0 && blockIdx.x == 0) {
     const float2 *src = pd.dgf + (size_t)b * 32 * 32;
     for (int e = threadIdx.x; e < 32 * 32; e += PIX_THREADS) {
       const int i = e >> 5, j = e & 31;
@@ -810,12 +854,21 @@ __global__ void __launch_bounds__(PIX_THREADS, 2) k_pixm_trail(const SysDev *__r
   }
   const int T = (n + 1 - r0 + 63) / 64;
   const int idx = blockIdx.x;
-  if (idx >= T * (T + 1) / 2) return;
-  // tile idx of the lower triangle, row-major: ti (ti + 1) / 2 <= idx < (ti + 1) (ti + 2) / 2
-  int ti = (int)((sqrt(8.0 * idx + 1.0) - 1.0) * 0.5);
-  while (ti * (ti + 1) / 2 > idx) --ti;
-  while ((ti + 1) * (ti + 2) / 2 <= idx) ++ti;
-  const int tj = idx - ti * (ti + 1) / 2;
+  int ti, tj;
+  if (part == 0) {
+    if (idx >= T) return;
+    ti = idx;
+    tj = 0;
+  } else {
+    // tile idx of the lower triangle with tj >= 1, row-major over (ti - 1, tj - 1):
+    // u (u + 1) / 2 <= idx < (u + 1) (u + 2) / 2 for u = ti - 1
+    if (idx >= T * (T - 1) / 2) return;
+    int u = (int)((sqrt(8.0 * idx + 1.0) - 1.0) * 0.5);
+    while (u * (u + 1) / 2 > idx) --u;
+    while ((u + 1) * (u + 2) / 2 <= idx) ++u;
+    ti = u + 1;
+    tj = idx - u * (u + 1) / 2 + 1;
+  }
   __shared__ float2 Pi[64][33], Pj[64][33];
   pix_tile<PIX_THREADS>(A, lda, n, k0, kb, r0, ti, tj, Pi, Pj);
 }
@@ -904,6 +957,17 @@ cudaError_t pixsrc_ws_ensure(glad_ctx *c, int B) {
   if (!c->n_pix) return cudaSuccess;
   if (!c->pws) c->pws = new PixWs();
   PixWs &w = *c->pws;
+  if (!w.aux) {
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    if (cudaStreamCreateWithPriority(&w.hi, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&w.aux, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
+        cudaEventCreateWithFlags(&w.ev_p, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&w.ev_r, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&w.ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&w.ev_out, cudaEventDisableTiming) != cudaSuccess)
+      return cudaErrorMemoryAllocation;
+  }
   if (w.B >= B) return cudaSuccess;
   B = std::max(B, w.B);
   cudaDeviceSynchronize();
@@ -951,11 +1015,15 @@ cudaError_t pixsrc_ws_ensure(glad_ctx *c, int B) {
 void pixsrc_ws_free(glad_ctx *c) {
   if (!c->pws) return;
   for (void *p : c->pws->allocs) cudaFree(p);
+  for (cudaEvent_t e : {c->pws->ev_p, c->pws->ev_r, c->pws->ev_in, c->pws->ev_out})
+    if (e) cudaEventDestroy(e);
+  if (c->pws->hi) cudaStreamDestroy(c->pws->hi);
+  if (c->pws->aux) cudaStreamDestroy(c->pws->aux);
   delete c->pws;
   c->pws = nullptr;
 }
 
-// the multi-launch form for batches with fewer samples than two per SM (the one-CTA-per-sample
+// the multi-launch form for batches of at most two samples per SM (the one-CTA-per-sample
 // kernel holds two CTAs per SM), unless the context fixes the form
 bool pixsrc_multi_launch(glad_ctx *c, int B) {
   if (c->tune.pix_path == 1) return false;
@@ -963,7 +1031,7 @@ bool pixsrc_multi_launch(glad_ctx *c, int B) {
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  return B < 2 * nsm;
+  return B <= 2 * nsm;
 }
 
 unsigned long long pixsrc_factorizations(glad_ctx *c) {
@@ -976,7 +1044,8 @@ unsigned long long pixsrc_factorizations(glad_ctx *c) {
 
 cudaError_t launch_pixsrc(glad_ctx *c, const int *sys_id, int B, cudaStream_t st,
                           double *lam_out, double *lnP_out, double *s_out) {
-  const PixDev &pd = c->pws->d;
+  PixWs &w = *c->pws;
+  const PixDev &pd = w.d;
   int max_iter = 0, max_tri = 0;
   for (auto &sd : c->h_sysdev)
     if (sd.src_pix) {
@@ -999,39 +1068,65 @@ cudaError_t launch_pixsrc(glad_ctx *c, const int *sys_id, int B, cudaStream_t st
   };
   // one evaluation per sample: one CTA per sample, or the multi-launch form
   const bool multi = pixsrc_multi_launch(c, B);
+  // the multi-launch form runs on the context's high-priority stream q, forked from st
+  const cudaStream_t q = multi ? w.hi : st;
   auto eval = [&](int final_pass, double *so) {
     if (!multi) {
-      k_pix_eval<<<B, PIX_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, pd, final_pass, so,
-                                            GLAD_MAX_SRCPIX);
+      k_pix_eval<<<B, PIX_THREADS, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd, final_pass, so,
+                                           GLAD_MAX_SRCPIX);
       return;
     }
     // the grids from the largest system (smaller ones leave the extra CTAs idle)
     const int ns = pd.max_ns;
     const int nbeg = std::max(1, (int)(((size_t)(ns + 1) * ns + PIX_THREADS * 16 - 1) / (PIX_THREADS * 16)));
-    k_pixm_begin<<<dim3(nbeg, B), PIX_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, pd, final_pass);
+    k_pixm_begin<<<dim3(nbeg, B), PIX_THREADS, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd, final_pass);
+    // Lookahead: the tiles of tile column 0 of step k (which hold step k + 1's diagonal block
+    // and panel) run on q, then panel k + 1, while the other tiles of step k run on the
+    // low-priority stream beside them.  Tile column 0 of step k + 1 waits for those: its
+    // columns, 32 to the right of step k's, overlap step k's tile column 1.  (Each wait
+    // follows a record of the same pass: the sequence captures into a graph.)
+    bool side_work = false;
     for (int k0 = 0; k0 < ns; k0 += 32) {
       const int rows = std::max(1, ns + 1 - k0 - 32);  // panel rows, row N_s among them
       const int T = (rows + 63) / 64;
-      const int np = (rows + PIX_THREADS - 1) / PIX_THREADS;
-      k_pixm_panel<<<dim3(np, B), PIX_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, pd, final_pass, k0);
-      k_pixm_trail<<<dim3(T * (T + 1) / 2, B), PIX_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, pd,
-                                                                      final_pass, k0);
+      const int np = (rows + PIXM_PANEL_THREADS - 1) / PIXM_PANEL_THREADS;
+      k_pixm_panel<<<dim3(np, B), PIXM_PANEL_THREADS, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd,
+                                                              final_pass, k0);
+      if (T > 1) cudaEventRecord(w.ev_p, q);
+      if (side_work) cudaStreamWaitEvent(q, w.ev_r, 0);
+      k_pixm_trail<<<dim3(T, B), PIX_THREADS, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd, final_pass, k0, 0);
+      side_work = T > 1;
+      if (side_work) {
+        cudaStreamWaitEvent(w.aux, w.ev_p, 0);
+        k_pixm_trail<<<dim3(T * (T - 1) / 2, B), PIX_THREADS, 0, w.aux>>>(c->d_sys, sys_id, c->ws.d,
+                                                                          pd, final_pass, k0, 1);
+        cudaEventRecord(w.ev_r, w.aux);
+      }
     }
+    if (side_work) cudaStreamWaitEvent(q, w.ev_r, 0);
     for (int k0 = ((ns - 1) / 32) * 32; k0 >= 0; k0 -= 32)
-      k_pixm_bsolve<<<dim3(std::max(1, (k0 + PIX_THREADS - 1) / PIX_THREADS), B), PIX_THREADS, 0, st>>>(
+      k_pixm_bsolve<<<dim3(std::max(1, (k0 + PIX_THREADS - 1) / PIX_THREADS), B), PIX_THREADS, 0, q>>>(
           c->d_sys, sys_id, c->ws.d, pd, final_pass, k0);
-    k_pixm_es<<<B, PIX_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, pd, final_pass, so, GLAD_MAX_SRCPIX);
+    k_pixm_es<<<B, PIX_THREADS, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd, final_pass, so, GLAD_MAX_SRCPIX);
     if (!final_pass) {
-      k_pixm_ed<<<dim3(pd.ed_chunks, B), PIX_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, pd);
-      k_pixm_fin<<<(B + 127) / 128, 128, 0, st>>>(c->d_sys, sys_id, c->ws.d, pd, B);
+      k_pixm_ed<<<dim3(pd.ed_chunks, B), PIX_THREADS, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd);
+      k_pixm_fin<<<(B + 127) / 128, 128, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd, B);
     }
   };
   auto ev = [&]() -> cudaError_t {
-    k_pix_init<<<(B + 127) / 128, 128, 0, st>>>(c->d_sys, sys_id, c->ws.d, pd, B);
+    if (multi) {
+      cudaEventRecord(w.ev_in, st);
+      cudaStreamWaitEvent(q, w.ev_in, 0);
+    }
+    k_pix_init<<<(B + 127) / 128, 128, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd, B);
     // the first pass evaluates the starting point, each later one a trial point
     for (int it = 0; it < max_iter; ++it) eval(0, nullptr);
-    k_pix_finish<<<(B + 127) / 128, 128, 0, st>>>(c->d_sys, sys_id, c->ws.d, pd, B, lam_out, lnP_out);
+    k_pix_finish<<<(B + 127) / 128, 128, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd, B, lam_out, lnP_out);
     if (s_out) eval(1, s_out);
+    if (multi) {
+      cudaEventRecord(w.ev_out, q);
+      cudaStreamWaitEvent(st, w.ev_out, 0);
+    }
     return cudaGetLastError();
   };
   e = GLAD_PROF(c, st, KID_PIX_OP, op());
