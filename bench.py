@@ -365,12 +365,12 @@ def measure(args, ctx, lib, systems, th_np, sid_np, B, grad_mode, world, rank, l
 
     ctx.set_precision(0 if grad_mode else args.precision)
     ctx.set_pix_path(args.pix_path)
-    # the evidence evaluation's launches (the library's rule: the multi-launch form for at most
-    # two samples per SM): one, or assembly + per 32-column panel step the panel, tile column 0
+    # the evidence evaluation's launches (the library's default is the multi-launch form): one,
+    # or assembly + per 32-column panel step the panel, tile column 0
     # and (when there are more) the other tiles + one per 32-row block of the backward solve +
     # E_S, E_D, ln P
     pix_ns = pix_ns_max(systems)
-    pix_multi = args.pix_path == 2 or (args.pix_path == 0 and B <= 2 * N_SM)
+    pix_multi = args.pix_path != 1
     pix_launches_per_eval = 1
     if pix_multi:
         pix_launches_per_eval = 4 + (pix_ns + 31) // 32
@@ -672,7 +672,7 @@ def main():
                    "valid_samples": m["valid_samples"],
                    "tuning": m["tuning"], "cuda_graph": m["cuda_graph"],
                    **({"sph_rule": args.sph_rule} if args.sph_rule else {}),
-                   **({"pix_path": ("multi-launch" if args.pix_path == 2 or (args.pix_path == 0 and B <= 2 * N_SM)
+                   **({"pix_path": ("multi-launch" if args.pix_path != 1
                                     else "one CTA per sample")}
                       if any(s.get("src_pix", 0) for s in systems) else {}),
                    "jam_skipping": "terms that underflow to 0 over a sky tile, and (pair sum and "

@@ -312,11 +312,14 @@ glad_status glad_pixsrc(glad_ctx *ctx, const int *sys_id, const double *theta, i
  * of the regularisation search is one), and reset the count. */
 unsigned long long glad_pix_factorizations(glad_ctx *ctx);
 /* How each evidence evaluation of the pixelated source runs (the results agree to rounding):
- * mode 1: one CTA per sample does the whole evaluation (for batches that fill the GPU); mode 2:
- * a sequence of launches per evaluation, each 32-column panel step of the factorisation spread
- * over many CTAs per sample (for small batches: one sample then uses the whole GPU); mode 0
- * (the default): mode 2 for batches of at most two samples per SM, else mode 1.
- * GLAD_EINVAL for other modes. */
+ * mode 1: one CTA per sample does the whole evaluation in one launch; mode 2: a sequence of
+ * launches per evaluation, each 32-column panel step of the factorisation spread over many CTAs
+ * per sample (one sample alone then uses the whole GPU); mode 0 (the default): mode 2, the
+ * faster at every batch size measured (16 to 1,184 samples).  GLAD_EINVAL for other modes.
+ * Outside graph capture the search's passes are enqueued in groups and the call waits on the
+ * device for each group before the next but one, ending as soon as every search has converged
+ * (so the call returns when the search is nearly done); under capture the full fixed pass
+ * count is recorded.  This applies to glad_pixsrc and to glad_loglike on such systems. */
 glad_status glad_set_pix_path(glad_ctx *ctx, int mode);
 
 /* Precision of the forward pass (Sect. 3: the paper computes in FP64 throughout).

@@ -165,7 +165,7 @@ glad_status validate(const glad_system_desc &d, int idx) {
     REQ(d.spx_x1 > d.spx_x0 && d.spx_y1 > d.spx_y0, "bad source grid extent", idx);
     REQ((d.spx_lam_lo == 0 && d.spx_lam_hi == 0) || (d.spx_lam_lo > 0 && d.spx_lam_hi > d.spx_lam_lo),
         "regularisation range needs 0 < spx_lam_lo < spx_lam_hi (or both 0)", idx);
-    REQ(d.spx_iters >= 0 && d.spx_iters <= 200, "spx_iters must be in [0, 200]", idx);
+    REQ(d.spx_iters >= 0 && d.spx_iters <= SPX_MAX_ITERS, "spx_iters must be in [0, 200]", idx);
     int nm = 0;
     for (int i = 0; i < d.nx * d.ny; ++i) nm += d.mask[i] != 0;
     REQ(nm > 0, "pixelated source needs a non-empty mask", idx);
@@ -714,9 +714,6 @@ glad_status full_path(glad_ctx *c, const int *sys_id, const double *theta, int B
     e = GLAD_PROF(c, side, KID_IMAGE_CONV,
                   launch_lens(c, sys_id, B, nullptr, side, grad ? grad_resid_buffer(c) : nullptr));
   if (e == cudaSuccess && grad) e = launch_grad_lens(c, sys_id, B, grad, side);
-  if (e == cudaSuccess && c->n_pix && !grad)
-    e = launch_pixsrc(c, sys_id, B, side, nullptr, nullptr, nullptr);
-  if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, side);
   // dynamics, high priority
   if (e == cudaSuccess) e = launch_dyn_tables(c, sys_id, B, dy);
   if (e == cudaSuccess) {
@@ -733,6 +730,11 @@ glad_status full_path(glad_ctx *c, const int *sys_id, const double *theta, int B
   if (e == cudaSuccess) e = GLAD_PROF(c, dy, KID_KIN, launch_kin_finalize(c, sys_id, B, nullptr, dy));
   if (e == cudaSuccess && grad) e = launch_grad_dyn(c, sys_id, theta, B, grad, dy);
   if (e == cudaSuccess) e = cudaEventRecord(c->ev_join_dyn, dy);
+  // the pixelated source's evidence search last on the lensing stream: enqueueing it waits on
+  // the device for the search to converge, by which time the dynamics are queued beside it
+  if (e == cudaSuccess && c->n_pix && !grad)
+    e = launch_pixsrc(c, sys_id, B, side, nullptr, nullptr, nullptr);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, side);
   // join
   if (e == cudaSuccess && !serial) e = cudaStreamWaitEvent(st, c->ev_join, 0);
   if (e == cudaSuccess && !serial) e = cudaStreamWaitEvent(st, c->ev_join_dyn, 0);

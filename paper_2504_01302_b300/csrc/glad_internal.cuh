@@ -24,6 +24,7 @@
 #define SPH_DEFAULT_NLOS 32
 #define GLAD_MAX_SRCPIX 4624    // source pixels of a pixelated-source grid (68 x 68)
 #define SPX_DEFAULT_ITERS 40    // evidence evaluations of the regularisation search
+#define SPX_MAX_ITERS 200       // the largest spx_iters taken
 
 // ---------------------------------------------------------------------------
 // device-resident description of one system (all pointers are device memory)

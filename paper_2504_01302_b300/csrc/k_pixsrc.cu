@@ -67,6 +67,10 @@ struct PixWs {
   // stream by events
   cudaStream_t hi = nullptr, aux = nullptr;
   cudaEvent_t ev_p = nullptr, ev_r = nullptr, ev_in = nullptr, ev_out = nullptr;
+  // the search's early end (not under graph capture): per pass the count of samples still
+  // searching, copied to pinned host memory, and two events for the groups of passes
+  int *d_open = nullptr, *h_open = nullptr;
+  cudaEvent_t ev_grp[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -78,6 +82,7 @@ constexpr double TTOL = 1e-3;                // tolerance in ln lambda (ln P mov
 #define PIX_THREADS 256
 #define PIXM_ED_ROWS 64
 #define PIXM_PANEL_THREADS 128
+#define PIX_GROUP 2          // search passes per group between the host's convergence checks
 
 // ---------------------------------------------------------------------------------------
 // Brent's method (Brent 1973, "Algorithms for Minimization without Derivatives", ch. 5):
@@ -454,11 +459,13 @@ __device__ __forceinline__ void pix_diag(const float2 *A, int lda, int k0, int k
       Ls[j] = l;
       Rs[j] = r;
     }
-#pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-      const int e = tid + q * NT, i = e >> 5, c = e & 31;
-      if (c > j && c <= i && i < kb) {
-        const float2 lij = df_mul(Ds[i][j], r), lcj = df_mul(Ds[c][j], r);
+    // warp w takes rows i > j with i = w mod (NT / 32), lane c column c (active for c in (j, i])
+    constexpr int NW = NT / 32;
+    const int w = tid >> 5, c = tid & 31;
+    const float2 lcj = df_mul(Ds[c][j], r);
+    for (int i = j + 1 + ((w - (j + 1)) % NW + NW) % NW; i < kb; i += NW) {
+      if (c > j && c <= i) {
+        const float2 lij = df_mul(Ds[i][j], r);
         float hi = 0.0f, lo = 0.0f;
         df_fma(hi, lo, lij, lcj);
         Ds[i][c] = df_sub(Ds[i][c], hi, lo);
@@ -578,13 +585,15 @@ __device__ __forceinline__ void pix_tile(float2 *A, int lda, int n, int k0, int 
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v) ah[u][v] = al[u][v] = 0.0f;
+  // thread (ty, tx) owns rows ty + 16u and columns tx + 16v: a warp's Pj reads then fall on
+  // consecutive rows (row stride 33 pairs: distinct banks) and its stores on consecutive columns
 #pragma unroll 4
   for (int m = 0; m < 32; ++m) {
     float2 av[4], bv[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      av[u] = Pi[ty * 4 + u][m];
-      bv[u] = Pj[tx * 4 + u][m];
+      av[u] = Pi[ty + 16 * u][m];
+      bv[u] = Pj[tx + 16 * u][m];
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u)
@@ -595,7 +604,7 @@ __device__ __forceinline__ void pix_tile(float2 *A, int lda, int n, int k0, int 
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      const int gi = r0 + ti * 64 + ty * 4 + u, gj = r0 + tj * 64 + tx * 4 + v;
+      const int gi = r0 + ti * 64 + ty + 16 * u, gj = r0 + tj * 64 + tx + 16 * v;
       if (gi <= n && gj <= gi && gj < n)
         A[(size_t)gi * lda + gj] = df_sub(A[(size_t)gi * lda + gj], ah[u][v], al[u][v]);
     }
@@ -694,13 +703,16 @@ __device__ __forceinline__ double pix_block_sum(double v, double *red) {
   return s;
 }
 
-// ln P from its parts, then one step of the search (thread 0 of the sample's last kernel)
+// ln P from its parts, then one step of the search (thread 0 of the sample's last kernel);
+// *open counts the samples whose search goes on after this pass
 __device__ __forceinline__ void pix_conclude(const SysDev &S, const PixDev &pd, int b, double t,
-                                             double half_logdet, int bad, double ES, double ED) {
+                                             double half_logdet, int bad, double ES, double ED,
+                                             int *open) {
   const double lnP = -ED - exp(t) * ES - half_logdet + 0.5 * S.spx_ns * t + S.spx_const;
   const double phi = (bad || !isfinite(lnP)) ? INFINITY : -lnP;
   brent_step(pd.srch[b], phi, S.spx_iters);
   if (pd.nfac) atomicAdd(pd.nfac, 1ull);
+  if (open && pd.srch[b].phase != 2) atomicAdd(open, 1);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -710,7 +722,7 @@ __device__ __forceinline__ void pix_conclude(const SysDev &S, const PixDev &pd, 
 __global__ void __launch_bounds__(PIX_THREADS, 2) k_pix_eval(const SysDev *__restrict__ sysv,
                                                           const int *__restrict__ sys_id, WsDev ws,
                                                           PixDev pd, int final_pass, double *s_out,
-                                                          int s_stride) {
+                                                          int s_stride, int *open) {
   const int b = blockIdx.x;
   const SysDev &S = sysv[sys_id[b]];
   double t;
@@ -755,7 +767,7 @@ __global__ void __launch_bounds__(PIX_THREADS, 2) k_pix_eval(const SysDev *__res
   const double ed = pix_ed_rows(S, pd, b, s, tid >> 5, S.n_mask, PIX_THREADS / 32);
   const double ES = pix_block_sum<PIX_THREADS>(es, red);
   const double ED = pix_block_sum<PIX_THREADS>(ed, red);
-  if (tid == 0) pix_conclude(S, pd, b, t, pix_half_logdet(pm, pe), bad, 0.5 * ES, 0.5 * ED);
+  if (tid == 0) pix_conclude(S, pd, b, t, pix_half_logdet(pm, pe), bad, 0.5 * ES, 0.5 * ED, open);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -926,7 +938,7 @@ __global__ void __launch_bounds__(PIX_THREADS) k_pixm_ed(const SysDev *__restric
 }
 
 __global__ void k_pixm_fin(const SysDev *__restrict__ sysv, const int *__restrict__ sys_id,
-                           WsDev ws, PixDev pd, int B) {
+                           WsDev ws, PixDev pd, int B, int *open) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   const SysDev &S = sysv[sys_id[b]];
@@ -935,7 +947,8 @@ __global__ void k_pixm_fin(const SysDev *__restrict__ sysv, const int *__restric
   const int nch = (S.n_mask + PIXM_ED_ROWS - 1) / PIXM_ED_ROWS;
   double ED = 0.0;
   for (int c = 0; c < nch; ++c) ED += pd.edp[(size_t)b * pd.ed_chunks + c];
-  pix_conclude(S, pd, b, t, pix_half_logdet(pd.pm[b], pd.pe[b]), pd.bad[b], 0.5 * pd.es[b], 0.5 * ED);
+  pix_conclude(S, pd, b, t, pix_half_logdet(pd.pm[b], pd.pe[b]), pd.bad[b], 0.5 * pd.es[b], 0.5 * ED,
+               open);
 }
 
 // the image term of logL: terms[0] = -2 ln P at the best lambda
@@ -965,7 +978,11 @@ cudaError_t pixsrc_ws_ensure(glad_ctx *c, int B) {
         cudaEventCreateWithFlags(&w.ev_p, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&w.ev_r, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&w.ev_in, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&w.ev_out, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&w.ev_out, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&w.ev_grp[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&w.ev_grp[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaMalloc(&w.d_open, sizeof(int) * (SPX_MAX_ITERS + 1)) != cudaSuccess ||
+        cudaHostAlloc(&w.h_open, sizeof(int) * (SPX_MAX_ITERS + 1), cudaHostAllocDefault) != cudaSuccess)
       return cudaErrorMemoryAllocation;
   }
   if (w.B >= B) return cudaSuccess;
@@ -1015,23 +1032,23 @@ cudaError_t pixsrc_ws_ensure(glad_ctx *c, int B) {
 void pixsrc_ws_free(glad_ctx *c) {
   if (!c->pws) return;
   for (void *p : c->pws->allocs) cudaFree(p);
-  for (cudaEvent_t e : {c->pws->ev_p, c->pws->ev_r, c->pws->ev_in, c->pws->ev_out})
+  for (cudaEvent_t e : {c->pws->ev_p, c->pws->ev_r, c->pws->ev_in, c->pws->ev_out, c->pws->ev_grp[0],
+                        c->pws->ev_grp[1]})
     if (e) cudaEventDestroy(e);
+  if (c->pws->d_open) cudaFree(c->pws->d_open);
+  if (c->pws->h_open) cudaFreeHost(c->pws->h_open);
   if (c->pws->hi) cudaStreamDestroy(c->pws->hi);
   if (c->pws->aux) cudaStreamDestroy(c->pws->aux);
   delete c->pws;
   c->pws = nullptr;
 }
 
-// the multi-launch form for batches of at most two samples per SM (the one-CTA-per-sample
-// kernel holds two CTAs per SM), unless the context fixes the form
+// the multi-launch form unless the context fixes the one-CTA-per-sample kernel: measured at
+// 16 to 1,184 samples of the 30 x 30 grid (RXJ1131 scale), it is the faster one throughout,
+// by 3.6x at 16 samples and 7 % at 1,184
 bool pixsrc_multi_launch(glad_ctx *c, int B) {
-  if (c->tune.pix_path == 1) return false;
-  if (c->tune.pix_path == 2) return true;
-  int dev = 0, nsm = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  return B <= 2 * nsm;
+  (void)B;
+  return c->tune.pix_path != 1;
 }
 
 unsigned long long pixsrc_factorizations(glad_ctx *c) {
@@ -1070,10 +1087,10 @@ cudaError_t launch_pixsrc(glad_ctx *c, const int *sys_id, int B, cudaStream_t st
   const bool multi = pixsrc_multi_launch(c, B);
   // the multi-launch form runs on the context's high-priority stream q, forked from st
   const cudaStream_t q = multi ? w.hi : st;
-  auto eval = [&](int final_pass, double *so) {
+  auto eval = [&](int final_pass, double *so, int *open) {
     if (!multi) {
       k_pix_eval<<<B, PIX_THREADS, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd, final_pass, so,
-                                           GLAD_MAX_SRCPIX);
+                                           GLAD_MAX_SRCPIX, open);
       return;
     }
     // the grids from the largest system (smaller ones leave the extra CTAs idle)
@@ -1110,7 +1127,7 @@ cudaError_t launch_pixsrc(glad_ctx *c, const int *sys_id, int B, cudaStream_t st
     k_pixm_es<<<B, PIX_THREADS, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd, final_pass, so, GLAD_MAX_SRCPIX);
     if (!final_pass) {
       k_pixm_ed<<<dim3(pd.ed_chunks, B), PIX_THREADS, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd);
-      k_pixm_fin<<<(B + 127) / 128, 128, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd, B);
+      k_pixm_fin<<<(B + 127) / 128, 128, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd, B, open);
     }
   };
   auto ev = [&]() -> cudaError_t {
@@ -1119,10 +1136,34 @@ cudaError_t launch_pixsrc(glad_ctx *c, const int *sys_id, int B, cudaStream_t st
       cudaStreamWaitEvent(q, w.ev_in, 0);
     }
     k_pix_init<<<(B + 127) / 128, 128, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd, B);
-    // the first pass evaluates the starting point, each later one a trial point
-    for (int it = 0; it < max_iter; ++it) eval(0, nullptr);
+    // The first pass evaluates the starting point, each later one a trial point.  Under graph
+    // capture all max_iter passes are recorded (converged samples return at once).  Otherwise
+    // the passes go out in groups of PIX_GROUP, each group's last count of open searches is
+    // copied to the host, and after enqueueing group g + 1 the host waits for group g: when no
+    // search is open the call ends there, so at most one group of idle passes runs.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    if (cs != cudaStreamCaptureStatusNone) {
+      for (int it = 0; it < max_iter; ++it) eval(0, nullptr, nullptr);
+    } else {
+      cudaError_t e2 = cudaMemsetAsync(w.d_open, 0, sizeof(int) * max_iter, q);
+      if (e2 != cudaSuccess) return e2;
+      int it = 0, g = 0;
+      auto group = [&](int gi) -> cudaError_t {
+        for (int k = 0; k < PIX_GROUP && it < max_iter; ++k, ++it) eval(0, nullptr, w.d_open + it);
+        cudaMemcpyAsync(w.h_open + gi % 2, w.d_open + it - 1, sizeof(int), cudaMemcpyDeviceToHost, q);
+        return cudaEventRecord(w.ev_grp[gi % 2], q);
+      };
+      if ((e2 = group(0)) != cudaSuccess) return e2;
+      while (it < max_iter) {
+        if ((e2 = group(g + 1)) != cudaSuccess) return e2;
+        if ((e2 = cudaEventSynchronize(w.ev_grp[g % 2])) != cudaSuccess) return e2;
+        if (w.h_open[g % 2] == 0) break;
+        ++g;
+      }
+    }
     k_pix_finish<<<(B + 127) / 128, 128, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd, B, lam_out, lnP_out);
-    if (s_out) eval(1, s_out);
+    if (s_out) eval(1, s_out, nullptr);
     if (multi) {
       cudaEventRecord(w.ev_out, q);
       cudaStreamWaitEvent(st, w.ev_out, 0);

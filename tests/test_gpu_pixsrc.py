@@ -229,3 +229,40 @@ def test_composite_class_with_the_dpie_sheet():
     ctx = _ctx([s])
     for b in range(2):
         check_against_oracle(ctx, s, th, b=b, check_s=(b == 0))
+
+
+@pytest.mark.parametrize("iters", [0, 3])
+def test_search_ends_early_as_under_capture(iters):
+    # eager calls stop enqueueing search passes once no search is open (the host checks a
+    # per-pass count); a captured graph records all of them.  Both must give the same optimum
+    # and run the same factorisations.  iters 0 is the default cap (40), 3 a cap that ends
+    # the searches before they converge.
+    import ctypes as C
+    s = pix_system(systems.small_system(7), n=(12, 12))
+    if iters:
+        s = dict(s, spx_iters=iters)
+    ctx = _ctx([s])
+    th = _th(systems.near_truth_thetas(3, seed=217))
+    B = th.shape[0]
+    sid = torch.zeros(B, dtype=torch.int32, device="cuda")
+    ctx.pix_factorizations()
+    lam_e, lnP_e = ctx.pixsrc(th, sid)
+    n_e = ctx.pix_factorizations()
+    lam = torch.empty(B, dtype=torch.float64, device="cuda")
+    lnP = torch.empty(B, dtype=torch.float64, device="cuda")
+    P = lambda t: C.c_void_p(t.data_ptr())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        rc = ctx.lib.glad_pixsrc(ctx.handle, P(sid), P(th), B, P(lam), P(lnP), None,
+                                 C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0, ctx.lib.glad_last_error().decode()
+    ctx.pix_factorizations()
+    graph.replay()
+    torch.cuda.synchronize()
+    n_g = ctx.pix_factorizations()
+    assert n_e == n_g and n_e >= B
+    # the response rows' shared-memory atomics reorder between launches (~1e-7 of F)
+    assert np.allclose(lnP.cpu().numpy(), lnP_e.cpu().numpy(), rtol=1e-9, atol=1e-4)
+    assert np.allclose(np.log(lam.cpu().numpy()), np.log(lam_e.cpu().numpy()), rtol=0, atol=1e-3)
+    if iters:
+        assert n_e == iters * B
