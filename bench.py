@@ -365,17 +365,6 @@ def measure(args, ctx, lib, systems, th_np, sid_np, B, grad_mode, world, rank, l
 
     ctx.set_precision(0 if grad_mode else args.precision)
     ctx.set_pix_path(args.pix_path)
-    # the evidence evaluation's launches (the library's default is the multi-launch form): one,
-    # or assembly + per 32-column panel step the panel, tile column 0
-    # and (when there are more) the other tiles + one per 32-row block of the backward solve +
-    # E_S, E_D, ln P
-    pix_ns = pix_ns_max(systems)
-    pix_multi = args.pix_path != 1
-    pix_launches_per_eval = 1
-    if pix_multi:
-        pix_launches_per_eval = 4 + (pix_ns + 31) // 32
-        for k0 in range(0, pix_ns, 32):
-            pix_launches_per_eval += 2 + (((max(1, pix_ns + 1 - k0 - 32) + 63) // 64) > 1)
     # launch shapes picked by the library's autotuner on this batch (untimed), or pinned
     if args.tuning:
         jc, ept = (int(v) for v in args.tuning.split(","))
@@ -433,10 +422,12 @@ def measure(args, ctx, lib, systems, th_np, sid_np, B, grad_mode, world, rank, l
     kl = (C.c_int * nk)()
     prof_steps = 3
     lib.glad_profile(ctx.handle, 2)
+    lib.glad_pix_launches(ctx.handle)  # reset: the pixelated source's launches vary with its search
     for k in range(prof_steps):
         flush.fill_(float(k))
         step()
     torch.cuda.synchronize()
+    pix_launches = int(lib.glad_pix_launches(ctx.handle))
     lib.glad_profile(ctx.handle, 0)
     lib.glad_kernel_times(ctx.handle, nk, kms, kl)
 
@@ -494,8 +485,7 @@ def measure(args, ctx, lib, systems, th_np, sid_np, B, grad_mode, world, rank, l
     extra = kl[names_idx("k_image+k_conv", lib, nk)] + kl[names_idx("k_grad_lens", lib, nk)] + \
         kl[names_idx("k_sph_coef+k_sph_grid", lib, nk)] + 2 * kl[names_idx("k_sph_adjoint", lib, nk)] + \
         (kl[names_idx("k_jam", lib, nk)] if (tuning["jam_pts"] // 100000) % 10 == 1 else 0) + \
-        2 * kl[names_idx("k_pix_operator", lib, nk)] + kl[names_idx("k_pix_evidence", lib, nk)] * (
-            max((s.get("spx_iters", 0) or 40) for s in systems) * pix_launches_per_eval + 1)
+        pix_launches - kl[names_idx("k_pix_operator", lib, nk)] - kl[names_idx("k_pix_evidence", lib, nk)]
     launches_per_step = (int(sum(kl[i] for i in range(nk))) + int(extra)) // prof_steps
     if grad_mode:
         launches_per_step += 2  # k_kin_adj and k_grad_zero_invalid run untimed by the profiler

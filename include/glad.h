@@ -311,6 +311,10 @@ glad_status glad_pixsrc(glad_ctx *ctx, const int *sys_id, const double *theta, i
 /* Cholesky factorisations of F + lambda C run since the last call (each evidence evaluation
  * of the regularisation search is one), and reset the count. */
 unsigned long long glad_pix_factorizations(glad_ctx *ctx);
+/* Kernel launches the pixelated-source stage enqueued since the last call (the response, the
+ * Gram matrix and every pass of the search; their number varies with the passes the search
+ * needed, see glad_set_pix_path), and reset the count.  0 for a NULL context. */
+unsigned long long glad_pix_launches(glad_ctx *ctx);
 /* How each evidence evaluation of the pixelated source runs (the results agree to rounding):
  * mode 1: one CTA per sample does the whole evaluation in one launch; mode 2: a sequence of
  * launches per evaluation, each 32-column panel step of the factorisation spread over many CTAs

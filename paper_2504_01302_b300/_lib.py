@@ -61,6 +61,7 @@ SIGNATURES = {
     "glad_set_precision": (C.c_int, [_p, C.c_int]),
     "glad_pixsrc": (C.c_int, [_p, _p, _p, C.c_int, _p, _p, _p, _p]),
     "glad_pix_factorizations": (C.c_ulonglong, [_p]),
+    "glad_pix_launches": (C.c_ulonglong, [_p]),
     "glad_set_pix_path": (C.c_int, [_p, C.c_int]),
     "glad_jam_evaluations": (C.c_int, [_p, C.POINTER(C.c_ulonglong), C.POINTER(C.c_ulonglong)]),
     "glad_enfw_cse": (C.c_int, [C.c_int, _d, _d, _d]),

@@ -1014,6 +1014,8 @@ glad_status glad_pixsrc(glad_ctx *c, const int *sys_id, const double *theta, int
 
 unsigned long long glad_pix_factorizations(glad_ctx *c) { return c ? pixsrc_factorizations(c) : 0; }
 
+unsigned long long glad_pix_launches(glad_ctx *c) { return c ? pixsrc_launches(c) : 0; }
+
 glad_status glad_set_pix_path(glad_ctx *c, int mode) {
   if (!c || mode < 0 || mode > 2) return fail(GLAD_EINVAL, "glad_set_pix_path: mode %d", mode);
   c->tune.pix_path = mode;

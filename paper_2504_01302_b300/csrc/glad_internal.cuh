@@ -321,6 +321,7 @@ cudaError_t launch_pixsrc(glad_ctx *c, const int *sys_id, int B, cudaStream_t st
 cudaError_t pixsrc_ws_ensure(glad_ctx *c, int B);
 void pixsrc_ws_free(glad_ctx *c);
 unsigned long long pixsrc_factorizations(glad_ctx *c);
+unsigned long long pixsrc_launches(glad_ctx *c);
 bool pixsrc_multi_launch(glad_ctx *c, int B);
 bool jam_shape_supported(int pts, int minb, int unr, int form);
 int jam_shape_list(int (*out)[4], int cap);

@@ -71,6 +71,8 @@ struct PixWs {
   // searching, copied to pinned host memory, and two events for the groups of passes
   int *d_open = nullptr, *h_open = nullptr;
   cudaEvent_t ev_grp[2] = {nullptr, nullptr};
+  unsigned long long launches = 0;  // kernels enqueued (glad_pix_launches)
+  int slots = 444;                  // resident k_pixm_rest CTAs on the GPU (three per SM)
 };
 
 namespace {
@@ -83,6 +85,8 @@ constexpr double TTOL = 1e-3;                // tolerance in ln lambda (ln P mov
 #define PIXM_ED_ROWS 64
 #define PIXM_PANEL_THREADS 128
 #define PIX_GROUP 2          // search passes per group between the host's convergence checks
+#define PIXM_REST_SMEM (2 * 2 * 64 * 33 * (int)sizeof(float2))
+#define PIXM_REST_TPC 8      // most tiles per CTA of k_pixm_rest
 
 // ---------------------------------------------------------------------------------------
 // Brent's method (Brent 1973, "Algorithms for Minimization without Derivatives", ch. 5):
@@ -567,10 +571,14 @@ __device__ __forceinline__ void pix_panel_rows(float2 *A, int lda, int k0, int k
 // trailing tile (ti, tj) of the panel step at k0, rows from r0 = k0 + kb below nr = N_s + 1,
 // columns below N_s: M[gi][gj] -= sum_m L[gi][k0 + m] L[gj][k0 + m], in double-float
 template <int NT>
+__device__ __forceinline__ void pix_tile_compute(float2 *A, int lda, int n, int r0, int ti, int tj,
+                                                 const float2 (*Pi)[33], const float2 (*Pj)[33]);
+
+template <int NT>
 __device__ __forceinline__ void pix_tile(float2 *A, int lda, int n, int k0, int kb, int r0, int ti,
                                          int tj, float2 (*Pi)[33], float2 (*Pj)[33]) {
   static_assert(NT == 256, "16 x 16 threads, 4 x 4 outputs each");
-  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int tid = threadIdx.x;
 #pragma unroll
   for (int q = 0; q < 64 * 32 / NT; ++q) {
     const int e = tid + q * NT, r = e >> 5, m = e & 31;
@@ -580,6 +588,52 @@ __device__ __forceinline__ void pix_tile(float2 *A, int lda, int n, int k0, int 
     Pj[r][m] = (gj < n && m < kb) ? A[(size_t)gj * lda + k0 + m] : z;
   }
   __syncthreads();
+  pix_tile_compute<NT>(A, lda, n, r0, ti, tj, Pi, Pj);
+  __syncthreads();
+}
+
+// 8-byte asynchronous copies global -> shared (cp.async; zero-filled when !pred, the source
+// address then only has to be valid), their commit and wait
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem, bool pred) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(pred ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// the panel rows of tile (ti, tj) into Pi, Pj by asynchronous copies (one commit group)
+template <int NT>
+__device__ __forceinline__ void pix_tile_fetch(const float2 *A, int lda, int n, int k0, int kb, int r0,
+                                               int ti, int tj, float2 (*Pi)[33], float2 (*Pj)[33]) {
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < 64 * 32 / NT; ++q) {
+    const int e = tid + q * NT, r = e >> 5, m = e & 31;
+    const int gi = r0 + ti * 64 + r, gj = r0 + tj * 64 + r;
+    const bool pi = gi <= n && m < kb, pj = gj < n && m < kb;
+    cp_async8(&Pi[r][m], pi ? A + (size_t)gi * lda + k0 + m : A, pi);
+    cp_async8(&Pj[r][m], pj ? A + (size_t)gj * lda + k0 + m : A, pj);
+  }
+  cp_async_commit();
+}
+
+// tile idx of the lower triangle with tj >= 1, row-major over (ti - 1, tj - 1)
+__device__ __forceinline__ void pix_rest_tile(int idx, int &ti, int &tj) {
+  int u = (int)((sqrt(8.0 * idx + 1.0) - 1.0) * 0.5);
+  while (u * (u + 1) / 2 > idx) --u;
+  while ((u + 1) * (u + 2) / 2 <= idx) ++u;
+  ti = u + 1;
+  tj = idx - u * (u + 1) / 2 + 1;
+}
+
+template <int NT>
+__device__ __forceinline__ void pix_tile_compute(float2 *A, int lda, int n, int r0, int ti, int tj,
+                                                 const float2 (*Pi)[33], const float2 (*Pj)[33]) {
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   float ah[4][4], al[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
@@ -608,7 +662,6 @@ __device__ __forceinline__ void pix_tile(float2 *A, int lda, int n, int k0, int 
       if (gi <= n && gj <= gi && gj < n)
         A[(size_t)gi * lda + gj] = df_sub(A[(size_t)gi * lda + gj], ah[u][v], al[u][v]);
     }
-  __syncthreads();
 }
 
 // one block of the backward solve L^T s = y (y in row N_s of M, updated in place): warp 0
@@ -843,12 +896,11 @@ __global__ void __launch_bounds__(PIXM_PANEL_THREADS) k_pixm_panel(const SysDev 
   pix_panel_rows_smem<NT>(A, lda, k0, kb, Ds, Rs, X, r0 + blockIdx.x * NT + tid, n + 1, gridDim.x * NT);
 }
 
-// part 0: the tiles of tile column 0 (the next diagonal block and panel among them); part 1:
-// the others, which the next panel step does not read
+// The tiles of tile column 0 (the next diagonal block and panel among them), one per CTA; CTA 0
+// also moves the factored diagonal block from dgf into M.
 __global__ void __launch_bounds__(PIX_THREADS, 3) k_pixm_trail(const SysDev *__restrict__ sysv,
                                                              const int *__restrict__ sys_id, WsDev ws,
-                                                             PixDev pd, int final_pass, int k0,
-                                                             int part) {
+                                                             PixDev pd, int final_pass, int k0) {
   const int b = blockIdx.y;
   const SysDev &S = sysv[sys_id[b]];
   double t;
@@ -857,7 +909,7 @@ __global__ void __launch_bounds__(PIX_THREADS, 3) k_pixm_trail(const SysDev *__r
   if (k0 >= n) return;
   const int kb = min(32, n - k0), r0 = k0 + kb, lda = n + 1;
   float2 *A = pix_A(pd, b);
-  if (part == 0 && blockIdx.x == 0) {
+  if (blockIdx.x == 0) {
     const float2 *src = pd.dgf + (size_t)b * 32 * 32;
     for (int e = threadIdx.x; e < 32 * 32; e += PIX_THREADS) {
       const int i = e >> 5, j = e & 31;
@@ -865,24 +917,52 @@ __global__ void __launch_bounds__(PIX_THREADS, 3) k_pixm_trail(const SysDev *__r
     }
   }
   const int T = (n + 1 - r0 + 63) / 64;
-  const int idx = blockIdx.x;
-  int ti, tj;
-  if (part == 0) {
-    if (idx >= T) return;
-    ti = idx;
-    tj = 0;
-  } else {
-    // tile idx of the lower triangle with tj >= 1, row-major over (ti - 1, tj - 1):
-    // u (u + 1) / 2 <= idx < (u + 1) (u + 2) / 2 for u = ti - 1
-    if (idx >= T * (T - 1) / 2) return;
-    int u = (int)((sqrt(8.0 * idx + 1.0) - 1.0) * 0.5);
-    while (u * (u + 1) / 2 > idx) --u;
-    while ((u + 1) * (u + 2) / 2 <= idx) ++u;
-    ti = u + 1;
-    tj = idx - u * (u + 1) / 2 + 1;
-  }
+  if ((int)blockIdx.x >= T) return;
   __shared__ float2 Pi[64][33], Pj[64][33];
-  pix_tile<PIX_THREADS>(A, lda, n, k0, kb, r0, ti, tj, Pi, Pj);
+  pix_tile<PIX_THREADS>(A, lda, n, k0, kb, r0, blockIdx.x, 0, Pi, Pj);
+}
+
+// The other tiles (tj >= 1), which the next panel step does not read: CTA x takes tiles x,
+// x + gridDim.x, ... of its sample, the next tile's panel rows copied into the second shared
+// buffer (cp.async) while the current one is computed.  Dynamic shared memory: two stages of
+// Pi, Pj (PIXM_REST_SMEM bytes).
+__global__ void __launch_bounds__(PIX_THREADS, 3) k_pixm_rest(const SysDev *__restrict__ sysv,
+                                                            const int *__restrict__ sys_id, WsDev ws,
+                                                            PixDev pd, int final_pass, int k0) {
+  const int b = blockIdx.y;
+  const SysDev &S = sysv[sys_id[b]];
+  double t;
+  if (!pix_active(S, ws, pd, b, final_pass, t)) return;
+  const int n = S.spx_ns;
+  if (k0 >= n) return;
+  const int kb = min(32, n - k0), r0 = k0 + kb, lda = n + 1;
+  const int T = (n + 1 - r0 + 63) / 64, ntile = T * (T - 1) / 2;
+  int idx = blockIdx.x;
+  if (idx >= ntile) return;
+  float2 *A = pix_A(pd, b);
+  extern __shared__ float2 pbuf[];
+  auto P = [&](int stage, int which) {
+    return reinterpret_cast<float2(*)[33]>(pbuf + (size_t)(2 * stage + which) * 64 * 33);
+  };
+  int ti, tj;
+  pix_rest_tile(idx, ti, tj);
+  pix_tile_fetch<PIX_THREADS>(A, lda, n, k0, kb, r0, ti, tj, P(0, 0), P(0, 1));
+  for (int stage = 0; idx < ntile; idx += gridDim.x, stage ^= 1) {
+    const int next = idx + gridDim.x;
+    int ni = 0, nj = 0;
+    if (next < ntile) {
+      pix_rest_tile(next, ni, nj);
+      pix_tile_fetch<PIX_THREADS>(A, lda, n, k0, kb, r0, ni, nj, P(stage ^ 1, 0), P(stage ^ 1, 1));
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    pix_tile_compute<PIX_THREADS>(A, lda, n, r0, ti, tj, P(stage, 0), P(stage, 1));
+    __syncthreads();  // this stage is refilled two tiles on
+    ti = ni;
+    tj = nj;
+  }
 }
 
 __global__ void __launch_bounds__(PIX_THREADS) k_pixm_bsolve(const SysDev *__restrict__ sysv,
@@ -971,6 +1051,13 @@ cudaError_t pixsrc_ws_ensure(glad_ctx *c, int B) {
   if (!c->pws) c->pws = new PixWs();
   PixWs &w = *c->pws;
   if (!w.aux) {
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    w.slots = 3 * nsm;
+    if (cudaFuncSetAttribute(k_pixm_rest, cudaFuncAttributeMaxDynamicSharedMemorySize, PIXM_REST_SMEM) !=
+        cudaSuccess)
+      return cudaErrorInvalidValue;
     int prio_lo = 0, prio_hi = 0;
     cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     if (cudaStreamCreateWithPriority(&w.hi, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
@@ -1051,6 +1138,13 @@ bool pixsrc_multi_launch(glad_ctx *c, int B) {
   return c->tune.pix_path != 1;
 }
 
+unsigned long long pixsrc_launches(glad_ctx *c) {
+  if (!c->pws) return 0;
+  const unsigned long long n = c->pws->launches;
+  c->pws->launches = 0;
+  return n;
+}
+
 unsigned long long pixsrc_factorizations(glad_ctx *c) {
   if (!c->pws || !c->pws->d.nfac) return 0;
   unsigned long long n = 0;
@@ -1078,9 +1172,12 @@ cudaError_t launch_pixsrc(glad_ctx *c, const int *sys_id, int B, cudaStream_t st
   auto op = [&]() -> cudaError_t {
     k_pix_f<<<dim3((c->max_nd + PIX_F_WARPS - 1) / PIX_F_WARPS, B), PIX_F_WARPS * 32, fsm, st>>>(
         c->d_sys, sys_id, c->ws.d, pd, c->max_pix);
+    ++w.launches;
     k_pix_gram<<<dim3(max_tri, B), PIX_THREADS, 0, st>>>(c->d_sys, sys_id, c->ws.d, pd);
+    ++w.launches;
     k_pix_dcol<<<dim3((c->max_ns + PIX_THREADS) / PIX_THREADS, B), PIX_THREADS, 0, st>>>(
         c->d_sys, sys_id, c->ws.d, pd);
+    ++w.launches;
     return cudaGetLastError();
   };
   // one evaluation per sample: one CTA per sample, or the multi-launch form
@@ -1091,12 +1188,14 @@ cudaError_t launch_pixsrc(glad_ctx *c, const int *sys_id, int B, cudaStream_t st
     if (!multi) {
       k_pix_eval<<<B, PIX_THREADS, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd, final_pass, so,
                                            GLAD_MAX_SRCPIX, open);
+      ++w.launches;
       return;
     }
     // the grids from the largest system (smaller ones leave the extra CTAs idle)
     const int ns = pd.max_ns;
     const int nbeg = std::max(1, (int)(((size_t)(ns + 1) * ns + PIX_THREADS * 16 - 1) / (PIX_THREADS * 16)));
     k_pixm_begin<<<dim3(nbeg, B), PIX_THREADS, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd, final_pass);
+    ++w.launches;
     // Lookahead: the tiles of tile column 0 of step k (which hold step k + 1's diagonal block
     // and panel) run on q, then panel k + 1, while the other tiles of step k run on the
     // low-priority stream beside them.  Tile column 0 of step k + 1 waits for those: its
@@ -1109,25 +1208,39 @@ cudaError_t launch_pixsrc(glad_ctx *c, const int *sys_id, int B, cudaStream_t st
       const int np = (rows + PIXM_PANEL_THREADS - 1) / PIXM_PANEL_THREADS;
       k_pixm_panel<<<dim3(np, B), PIXM_PANEL_THREADS, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd,
                                                               final_pass, k0);
+      ++w.launches;
       if (T > 1) cudaEventRecord(w.ev_p, q);
       if (side_work) cudaStreamWaitEvent(q, w.ev_r, 0);
-      k_pixm_trail<<<dim3(T, B), PIX_THREADS, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd, final_pass, k0, 0);
+      k_pixm_trail<<<dim3(T, B), PIX_THREADS, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd, final_pass, k0);
+      ++w.launches;
       side_work = T > 1;
       if (side_work) {
+        // tiles per CTA: enough CTAs for one wave of three per SM, at most PIXM_REST_TPC tiles
+        // each for small batches and two for larger ones (late in the search only a few
+        // samples are still open, and their tiles then need many CTAs each)
+        const long rest = (long)T * (T - 1) / 2;
+        const long cap = B <= 32 ? PIXM_REST_TPC : 2;
+        const int tpc = (int)std::min<long>(cap, std::max<long>(1, (rest * B + w.slots - 1) / w.slots));
         cudaStreamWaitEvent(w.aux, w.ev_p, 0);
-        k_pixm_trail<<<dim3(T * (T - 1) / 2, B), PIX_THREADS, 0, w.aux>>>(c->d_sys, sys_id, c->ws.d,
-                                                                          pd, final_pass, k0, 1);
+        k_pixm_rest<<<dim3((int)((rest + tpc - 1) / tpc), B), PIX_THREADS, PIXM_REST_SMEM, w.aux>>>(
+            c->d_sys, sys_id, c->ws.d, pd, final_pass, k0);
+        ++w.launches;
         cudaEventRecord(w.ev_r, w.aux);
       }
     }
     if (side_work) cudaStreamWaitEvent(q, w.ev_r, 0);
-    for (int k0 = ((ns - 1) / 32) * 32; k0 >= 0; k0 -= 32)
+    for (int k0 = ((ns - 1) / 32) * 32; k0 >= 0; k0 -= 32) {
       k_pixm_bsolve<<<dim3(std::max(1, (k0 + PIX_THREADS - 1) / PIX_THREADS), B), PIX_THREADS, 0, q>>>(
           c->d_sys, sys_id, c->ws.d, pd, final_pass, k0);
+      ++w.launches;
+    }
     k_pixm_es<<<B, PIX_THREADS, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd, final_pass, so, GLAD_MAX_SRCPIX);
+    ++w.launches;
     if (!final_pass) {
       k_pixm_ed<<<dim3(pd.ed_chunks, B), PIX_THREADS, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd);
+      ++w.launches;
       k_pixm_fin<<<(B + 127) / 128, 128, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd, B, open);
+      ++w.launches;
     }
   };
   auto ev = [&]() -> cudaError_t {
@@ -1136,6 +1249,7 @@ cudaError_t launch_pixsrc(glad_ctx *c, const int *sys_id, int B, cudaStream_t st
       cudaStreamWaitEvent(q, w.ev_in, 0);
     }
     k_pix_init<<<(B + 127) / 128, 128, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd, B);
+    ++w.launches;
     // The first pass evaluates the starting point, each later one a trial point.  Under graph
     // capture all max_iter passes are recorded (converged samples return at once).  Otherwise
     // the passes go out in groups of PIX_GROUP, each group's last count of open searches is
@@ -1163,6 +1277,7 @@ cudaError_t launch_pixsrc(glad_ctx *c, const int *sys_id, int B, cudaStream_t st
       }
     }
     k_pix_finish<<<(B + 127) / 128, 128, 0, q>>>(c->d_sys, sys_id, c->ws.d, pd, B, lam_out, lnP_out);
+    ++w.launches;
     if (s_out) eval(1, s_out, nullptr);
     if (multi) {
       cudaEventRecord(w.ev_out, q);

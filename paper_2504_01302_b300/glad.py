@@ -172,6 +172,11 @@ class GladContext:
         torch.cuda.synchronize()
         return int(self.lib.glad_pix_factorizations(self.handle))
 
+    def pix_launches(self):
+        """Kernel launches of the pixelated-source stage since the last call (glad_pix_launches)."""
+        torch.cuda.synchronize()
+        return int(self.lib.glad_pix_launches(self.handle))
+
     def set_pix_path(self, mode):
         """Form of the pixelated source's evidence evaluations (glad_set_pix_path): 0 by batch
         size, 1 one CTA per sample, 2 multi-launch."""

@@ -102,6 +102,7 @@ def test_entry_points_reject_null_context_and_empty_batch():
     assert lib.glad_set_tuning(None, 4052, 2) == GLAD_EINVAL
     assert lib.glad_pixsrc(None, p, p, 4, p, p, None, None) == GLAD_EINVAL
     assert lib.glad_pix_factorizations(None) == 0
+    assert lib.glad_pix_launches(None) == 0
     assert lib.glad_set_pix_path(None, 1) == GLAD_EINVAL
     assert lib.glad_create(None, 1, C.byref(C.c_void_p())) == GLAD_EINVAL
     assert "glad_create" in lib.glad_last_error().decode()
