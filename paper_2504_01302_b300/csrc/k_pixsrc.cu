@@ -6,8 +6,8 @@
 //    around q gather their pixels' ray entries into a shared row of N_s) and stores
 //    g_q = [f_q, d_q] / sigma_q in FP32.
 //  k_pix_gram: [F D; D^T d^T C_D^-1 d] = g^T g, lower triangle, 64 x 64 tiles: FP32 products
-//    summed in FP32 over 256 rows and in FP64 across them; k_pix_dcol then redoes the data
-//    row (D and d^T C_D^-1 d) with FP64 sums.
+//    summed in FP32 over 256 rows and in double-float across them; k_pix_dcol then redoes the data
+//    row (D and d^T C_D^-1 d) with double-float sums of the exact products.
 //  k_pix_eval: one CTA per sample (two resident per SM), or for small batches the k_pixm_*
 //    sequence that spreads each step over many CTAs: M = [F + lambda C; D^T], blocked Cholesky
 //    (32-wide panels, 64 x 64 trailing tiles) whose last row is y = L^-1 D, s_MP by the
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(PIX_F_WARPS * 32) k_pix_f(const SysDev *__rest
 }
 
 // lower triangle of g^T g over the (N_s + 1) columns: tile (ti, tj), tj <= ti
-__global__ void __launch_bounds__(PIX_THREADS) k_pix_gram(const SysDev *__restrict__ sysv,
+__global__ void __launch_bounds__(PIX_THREADS, 3) k_pix_gram(const SysDev *__restrict__ sysv,
                                                           const int *__restrict__ sys_id, WsDev ws,
                                                           PixDev pd) {
   const int b = blockIdx.y;
@@ -282,24 +282,39 @@ __global__ void __launch_bounds__(PIX_THREADS) k_pix_gram(const SysDev *__restri
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   const int nd = S.n_mask;
   const float *g = pd.g + (size_t)b * pd.max_nd * pd.ldg;
-  float acc[4][4];
-  double acc64[4][4];
+  // FP32 sums over 256 rows, carried across them in double-float (hi, lo) pairs (FP32
+  // TwoSum: FP64 adds would hold the FP64 unit ~64 cycles per warp instruction, all warps at
+  // once at every flush)
+  float acc[4][4], sh[4][4], sl[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      acc[u][v] = 0.0f;
-      acc64[u][v] = 0.0;
-    }
+    for (int v = 0; v < 4; ++v) acc[u][v] = sh[u][v] = sl[u][v] = 0.0f;
   const int lr = tid >> 4, lc = (tid & 15) * 4;  // loader: row lr, columns lc .. lc + 3
+  const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   for (int q0 = 0, ch = 0; q0 < nd; q0 += 16, ++ch) {
     const int qq = q0 + lr;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int ca = ti * 64 + lc + k, cb = tj * 64 + lc + k;
-      As[lr][lc + k] = (qq < nd && ca < n1) ? g[(size_t)qq * pd.ldg + ca] : 0.0f;
-      Bs[lr][lc + k] = (qq < nd && cb < n1) ? g[(size_t)qq * pd.ldg + cb] : 0.0f;
+    // g's rows start on 16-byte boundaries (ldg a multiple of 4) and lc is a multiple of 4:
+    // one float4 per matrix where the four columns exist, else element by element
+    const int ca = ti * 64 + lc, cb = tj * 64 + lc;
+    const float *ga = g + (size_t)qq * pd.ldg + ca, *gb = g + (size_t)qq * pd.ldg + cb;
+    float4 a4 = z4, b4 = z4;
+    if (qq < nd) {
+      if (ca + 3 < n1) a4 = *reinterpret_cast<const float4 *>(ga);
+      else {
+        a4.x = ca < n1 ? ga[0] : 0.0f;
+        a4.y = ca + 1 < n1 ? ga[1] : 0.0f;
+        a4.z = ca + 2 < n1 ? ga[2] : 0.0f;
+      }
+      if (cb + 3 < n1) b4 = *reinterpret_cast<const float4 *>(gb);
+      else {
+        b4.x = cb < n1 ? gb[0] : 0.0f;
+        b4.y = cb + 1 < n1 ? gb[1] : 0.0f;
+        b4.z = cb + 2 < n1 ? gb[2] : 0.0f;
+      }
     }
+    *reinterpret_cast<float4 *>(&As[lr][lc]) = a4;
+    *reinterpret_cast<float4 *>(&Bs[lr][lc]) = b4;
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
@@ -317,7 +332,12 @@ __global__ void __launch_bounds__(PIX_THREADS) k_pix_gram(const SysDev *__restri
       for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          acc64[u][v] += (double)acc[u][v];
+          // (sh, sl) += acc: TwoSum of sh and acc, the error into sl
+          const float t = __fadd_rn(sh[u][v], acc[u][v]);
+          const float w = __fsub_rn(t, sh[u][v]);
+          const float e = __fadd_rn(__fsub_rn(sh[u][v], __fsub_rn(t, w)), __fsub_rn(acc[u][v], w));
+          sh[u][v] = t;
+          sl[u][v] = __fadd_rn(sl[u][v], e);
           acc[u][v] = 0.0f;
         }
     }
@@ -328,11 +348,12 @@ __global__ void __launch_bounds__(PIX_THREADS) k_pix_gram(const SysDev *__restri
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const int i = ti * 64 + ty * 4 + u, j = tj * 64 + tx * 4 + v;
-      if (i < n1 && j <= i) F[(size_t)i * pd.ldg + j] = acc64[u][v] + (double)acc[u][v];
+      if (i < n1 && j <= i)
+        F[(size_t)i * pd.ldg + j] = ((double)sh[u][v] + (double)sl[u][v]) + (double)acc[u][v];
     }
 }
 
-// the data row of the Gram matrix again in FP64: D_j = sum_q g_qj g_qn and d^T C_D^-1 d
+// the data row of the Gram matrix again, to ~48 bits: D_j = sum_q g_qj g_qn and d^T C_D^-1 d
 // (the data term -(d^T C_D^-1 d - D^T s_MP)/2 of ln P is a difference of sums that each reach
 // ~N_d times the noise level: their FP32 rounding would move ln P by ~1e-6 of them)
 __global__ void __launch_bounds__(PIX_THREADS) k_pix_dcol(const SysDev *__restrict__ sysv,
@@ -345,12 +366,19 @@ __global__ void __launch_bounds__(PIX_THREADS) k_pix_dcol(const SysDev *__restri
   const int n = S.spx_ns, j = blockIdx.x * PIX_THREADS + threadIdx.x;
   if (j > n) return;
   const float *g = pd.g + (size_t)b * pd.max_nd * pd.ldg;
-  double acc = 0.0;
+  // each product of two floats is exact as p + pe (FMA); the sum runs in double-float (Knuth's
+  // TwoSum, errors gathered in lo) on the FP32 pipe rather than as FP64 multiply-adds
+  float hi = 0.0f, lo = 0.0f;
   for (int q = 0; q < S.n_mask; ++q) {
     const float *gq = g + (size_t)q * pd.ldg;
-    acc = fma((double)gq[j], (double)gq[n], acc);
+    const float a = gq[j], c = gq[n];
+    const float p = __fmul_rn(a, c), pe = __fmaf_rn(a, c, -p);
+    const float t = __fadd_rn(hi, p), w = __fsub_rn(t, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, w)), __fsub_rn(p, w));
+    hi = t;
+    lo = __fadd_rn(lo, __fadd_rn(pe, e));
   }
-  pd.F[(size_t)b * pd.ldg * pd.ldg + (size_t)n * pd.ldg + j] = acc;
+  pd.F[(size_t)b * pd.ldg * pd.ldg + (size_t)n * pd.ldg + j] = (double)hi + (double)lo;
 }
 
 __global__ void k_pix_init(const SysDev *__restrict__ sysv, const int *__restrict__ sys_id,
