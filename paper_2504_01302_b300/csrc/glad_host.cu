@@ -529,7 +529,13 @@ glad_status build_system(int idx, const glad_system_desc &d, SysHost &sh, SysDev
       }
     sd.n_mask = (int)ml.size();
     sd.mask_list = upload(sh, ml.data(), ml.size());
-    std::vector<double> C((size_t)ns * ns, 0.0);
+    // C = H^T H (for ln det C; the kernels form its entries themselves) in band storage: its
+    // entries lie within 2 gx of the diagonal, and so do its Cholesky factor's
+    const int bw = 2 * gx;
+    std::vector<double> Cb((size_t)ns * (bw + 1), 0.0), Lb((size_t)ns * (bw + 1), 0.0);
+    auto band = [&](std::vector<double> &m, int r, int c) -> double & {
+      return m[(size_t)r * (bw + 1) + (r - c)];
+    };
     for (int i = 0; i < gy; ++i)
       for (int j = 0; j < gx; ++j) {
         const int p = i * gx + j;
@@ -546,26 +552,24 @@ glad_status build_system(int idx, const glad_system_desc &d, SysHost &sh, SysDev
           }
           for (int u = 0; u < 3; ++u)
             for (int v = 0; v < 3; ++v)
-              if (idx3[u] >= 0 && idx3[v] >= 0) C[(size_t)idx3[u] * ns + idx3[v]] += h3[u] * h3[v];
+              if (idx3[u] >= 0 && idx3[v] >= 0 && idx3[u] >= idx3[v])
+                band(Cb, idx3[u], idx3[v]) += h3[u] * h3[v];
         }
       }
-    const int bw = 2 * gx;
-    std::vector<double> Lc((size_t)ns * ns, 0.0);
     double logdetC = 0.0;
     for (int jj = 0; jj < ns; ++jj) {
-      double dsum = C[(size_t)jj * ns + jj];
-      for (int k = std::max(0, jj - bw); k < jj; ++k) dsum -= Lc[(size_t)jj * ns + k] * Lc[(size_t)jj * ns + k];
+      double dsum = band(Cb, jj, jj);
+      for (int k = std::max(0, jj - bw); k < jj; ++k) dsum -= band(Lb, jj, k) * band(Lb, jj, k);
       if (!(dsum > 0.0)) return fail(GLAD_EINVAL, "system %d: curvature matrix not positive definite", idx);
       const double ljj = sqrt(dsum);
-      Lc[(size_t)jj * ns + jj] = ljj;
+      band(Lb, jj, jj) = ljj;
       logdetC += 2.0 * log(ljj);
       for (int ii = jj + 1; ii < std::min(ns, jj + bw + 1); ++ii) {
-        double t = C[(size_t)ii * ns + jj];
-        for (int k = std::max(0, ii - bw); k < jj; ++k) t -= Lc[(size_t)ii * ns + k] * Lc[(size_t)jj * ns + k];
-        Lc[(size_t)ii * ns + jj] = t / ljj;
+        double t = band(Cb, ii, jj);
+        for (int k = std::max(0, ii - bw); k < jj; ++k) t -= band(Lb, ii, k) * band(Lb, jj, k);
+        band(Lb, ii, jj) = t / ljj;
       }
     }
-    sd.spx_C = upload(sh, C.data(), C.size());
     sd.spx_const = 0.5 * logdetC - 0.5 * sd.n_mask * log(2.0 * PI_D) + sum_lninv;
   }
   sd.has_bh = d.has_bh;

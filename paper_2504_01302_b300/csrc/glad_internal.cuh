@@ -104,13 +104,12 @@ struct SysDev {
   const double *sph_u, *sph_wu;             // [n_mass_tot * n_gl]
   // pixelated source (src_pix 1, Sect. 3.1.1): spx_nx x spx_ny pixels of size spx_dx x spx_dy
   // from (spx_x0, spx_y0) on the source plane; the fit runs over the n_mask pixels listed in
-  // mask_list; spx_C = H^T H the curvature regularisation [spx_ns^2]; the evidence's
+  // mask_list; the curvature regularisation C = H^T H is formed where it is needed; the evidence's
   // lambda-free constant spx_const = ln det C / 2 - (N_d / 2) ln 2 pi + sum ln(1 / sigma);
   // the search over ln lambda in [spx_tlo, spx_thi] takes at most spx_iters evaluations
   int src_pix, spx_nx, spx_ny, spx_ns, n_mask, spx_iters;
   float spx_x0, spx_y0, spx_idx, spx_idy;   // origin and inverse pixel sizes
   const int *mask_list;                     // [n_mask] pixel indices, ascending
-  const double *spx_C;                      // [spx_ns * spx_ns]
   double spx_const, spx_tlo, spx_thi;
 };
 

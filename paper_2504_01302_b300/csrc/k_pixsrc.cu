@@ -445,6 +445,18 @@ __device__ __forceinline__ float2 *pix_A(const PixDev &pd, int b) {
   return pd.A + (size_t)b * (pd.max_ns + 1) * (pd.max_ns + 1);
 }
 
+// C = H^T H entry (p, q): H stacks the second differences along x and along y (zero outside
+// the grid), so C = I (x) Dx^T Dx + Dy^T Dy (x) I with D the 1-D second difference, whose
+// D^T D has 6 on the diagonal (5 at the two ends), -4 one off it and 1 two off it
+__device__ __forceinline__ double pix_curv(const SysDev &S, int p, int q) {
+  const int nx = S.spx_nx, pi = p / nx, pj = p - pi * nx, qi = q / nx, qj = q - qi * nx;
+  auto dtd = [](int a, int b, int m) {
+    const int k = abs(a - b);
+    return k == 0 ? 4 + (a > 0) + (a + 1 < m) : k == 1 ? -4 : k == 2 ? 1 : 0;
+  };
+  return (double)((pi == qi ? dtd(pj, qj, nx) : 0) + (pj == qj ? dtd(pi, qi, S.spx_ny) : 0));
+}
+
 // M: rows i < N_s get F + lambda C, row N_s gets D (row N_s of the Gram matrix), lower
 // triangle without column N_s, over the elements first, first + step, ...
 __device__ __forceinline__ void pix_assemble(const SysDev &S, const PixDev &pd, int b, double lam,
@@ -455,7 +467,7 @@ __device__ __forceinline__ void pix_assemble(const SysDev &S, const PixDev &pd, 
   for (size_t e = first; e < (size_t)(n + 1) * n; e += step) {
     const int i = (int)(e / n), j = (int)(e - (size_t)i * n);
     if (j > i) continue;
-    const double v = i < n ? F[(size_t)i * ldg + j] + lam * S.spx_C[(size_t)i * n + j] : F[(size_t)n * ldg + j];
+    const double v = i < n ? F[(size_t)i * ldg + j] + lam * pix_curv(S, i, j) : F[(size_t)n * ldg + j];
     A[(size_t)i * lda + j] = df_split(v);
   }
 }
