@@ -8,8 +8,8 @@
 //  k_pix_gram: [F D; D^T d^T C_D^-1 d] = g^T g, lower triangle, 64 x 64 tiles: FP32 products
 //    summed in FP32 over 256 rows and in double-float across them; k_pix_dcol then redoes the data
 //    row (D and d^T C_D^-1 d) with double-float sums of the exact products.
-//  k_pix_eval: one CTA per sample (two resident per SM), or for small batches the k_pixm_*
-//    sequence that spreads each step over many CTAs: M = [F + lambda C; D^T], blocked Cholesky
+//  the k_pixm_* sequence (the default), which spreads each panel step over many CTAs per
+//    sample, or k_pix_eval, one CTA per sample: M = [F + lambda C; D^T], blocked Cholesky
 //    (32-wide panels, 64 x 64 trailing tiles) whose last row is y = L^-1 D, s_MP by the
 //    backward solve L^T s = y, and the log-evidence
 //      ln P = -E_D - lambda E_S - sum ln L_ii + (N_s/2) ln lambda + const,
@@ -809,8 +809,8 @@ __device__ __forceinline__ void pix_conclude(const SysDev &S, const PixDev &pd, 
 }
 
 // ---------------------------------------------------------------------------------------
-// One evidence evaluation per sample at its pending ln lambda, one CTA per sample (the form for
-// batches that fill the GPU; final_pass: at the best point, with s_MP written to
+// One evidence evaluation per sample at its pending ln lambda, one CTA per sample, in one
+// launch (glad_set_pix_path mode 1; final_pass: at the best point, with s_MP written to
 // s_out[b * s_stride ..]).
 __global__ void __launch_bounds__(PIX_THREADS, 2) k_pix_eval(const SysDev *__restrict__ sysv,
                                                           const int *__restrict__ sys_id, WsDev ws,
@@ -864,17 +864,20 @@ __global__ void __launch_bounds__(PIX_THREADS, 2) k_pix_eval(const SysDev *__res
 }
 
 // ---------------------------------------------------------------------------------------
-// The same evaluation as a sequence of launches, for batches too small to fill the GPU with one
-// CTA per sample: the kernel boundaries order the steps, and each step spreads over many CTAs
-// per sample (grid y = sample).
+// The same evaluation as a sequence of launches (the default form, faster than one CTA per
+// sample at every batch size measured): the kernel boundaries order the steps, and each step
+// spreads over many CTAs per sample (grid y = sample).
 //   k_pixm_begin    M assembled; the sample's pivot product and flag reset
 //   per 32-column panel step k0:
 //     k_pixm_panel    every CTA factors the diagonal block (read from M, which nothing writes
 //                     in this launch) and solves its share of the panel rows (row N_s among
 //                     them); CTA 0 keeps the factored block in dgf, the reciprocals in rd, and
 //                     folds the pivots into the sample's product
-//     k_pixm_trail    one 64 x 64 tile of the trailing update per CTA; CTA 0 also moves dgf
-//                     into M's diagonal block (which nothing else touches in this launch)
+//     k_pixm_trail    the 64 x 64 tiles of tile column 0 (next diagonal block and panel), one
+//                     per CTA; CTA 0 also moves dgf into M's diagonal block (which nothing
+//                     else touches in this launch)
+//     k_pixm_rest     the other tiles, several per CTA, on a second, low-priority stream
+//                     beside tile column 0 and the next panel (the lookahead)
 //   per 32-row block of the backward solve, from the bottom:
 //     k_pixm_bsolve   every CTA solves the block (its y entries are not written in this
 //                     launch), CTA 0 writes s_MP there, each CTA updates its share of y above
