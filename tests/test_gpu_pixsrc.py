@@ -162,6 +162,12 @@ def test_rxj1131_scale_sampled_against_oracle():
     # the residual sums' reduction order), so the searches end at the same optimum
     assert np.allclose(out[1][1], out[2][1], rtol=1e-9, atol=1e-3)
     assert np.allclose(out[1][0], out[2][0], rtol=0, atol=1e-3)
+    # a batch above 32 samples takes other launch shapes for the trailing tiles (one per CTA):
+    # its first 16 samples end where the 16-sample batch did
+    ctx.set_pix_path(2)
+    lam40, lnP40 = ctx.pixsrc(_th(th[:40]))
+    assert np.allclose(lnP40.cpu().numpy()[:B], out[2][1], rtol=1e-9, atol=1e-3)
+    assert np.allclose(np.log(lam40.cpu().numpy()[:B]), out[2][0], rtol=0, atol=1e-3)
 
 
 def test_graph_replay_and_static_refusal(small):
